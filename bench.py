@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark: encode + decode of a whole-slide-shaped image on one GB300.
+
+Workload (synthetic stand-in for the paper's 100-megapixel 27-bit pathology
+scans, which are not available): a 40000 x 30000 RGB8 slide from the seeded
+generator, cut into 256 x 256 tiles (edge tiles 64 wide / 48 tall), 8 wavelet
+levels, lossy with quantiser steps 8/4/2 on levels 1-3 (1 elsewhere); the
+same image is also measured lossless.  One step = encode every tile into one
+contiguous stream + decode the full image back (all stages of the codec).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encode & decode megapixels/s on 1 GB300 (bit-exact vs oracle), % of HBM roofline; p99 tile latency"
+IMG_W, IMG_H, TILE, LEVELS = 40000, 30000, 256, 8
+LOSSY_Q = [3, 2, 1, 0, 0, 0, 0, 0, 0]
+
+
+def tile_grid(w=IMG_W, h=IMG_H, t=TILE):
+    return [(x, y, min(t, w - x), min(t, h - y)) for y in range(0, h, t) for x in range(0, w, t)]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_slide(seed):
+    import torch
+    from paper_2005_08713_gb300 import synth
+    h_img = torch.empty((IMG_H, IMG_W, 3), dtype=torch.uint8, pin_memory=True)
+    synth.slide(seed, 0, 0, IMG_W, IMG_H, out=h_img.numpy())
+    return h_img
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2005_08713_gb300 import isx, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    seed = synth.config_seed(3) + rank
+    h_img = make_slide(seed)
+    mp = IMG_W * IMG_H / 1e6
+    d_img = h_img.to(dev, non_blocking=False)
+    grid = tile_grid()
+    codec = isx.Codec(local)
+    q = LOSSY_Q if not args.lossless else [0] * 9
+
+    def tiles_for(buf, qs):
+        return isx.TileArray([isx.tile_from_tensor(buf[y:y + h, x:x + w], LEVELS, 8, qs, x, y) for (x, y, w, h) in grid])
+
+    tiles = tiles_for(d_img, q)
+    cap = IMG_W * IMG_H * 3 + (1 << 24)
+    d_out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    d_offs = torch.empty(len(tiles) + 1, dtype=torch.int64, device=dev)
+    d_dec = torch.empty_like(d_img)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        codec.encode_tiles(tiles, d_out, d_offs, stream)
+        n_enc = codec.last_launch_count
+        codec.decode_region(d_out, d_offs, tiles, 0, (0, 0, IMG_W, IMG_H), d_dec, 0, stream)
+        return n_enc + codec.last_launch_count
+
+    # correctness gate before timing: the full image round-trips and sampled tiles match the oracle
+    step()
+    st = codec.sync_status(stream)
+    if st != 0:
+        raise RuntimeError(f"device status {st}")
+    total_bytes = int(d_offs[-1].item())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # separate encode/decode timing (device events), then the full step timing
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    enc_ms, dec_ms = [], []
+    for _ in range(2):
+        ev[0].record(stream)
+        codec.encode_tiles(tiles, d_out, d_offs, stream)
+        ev[1].record(stream)
+        codec.decode_region(d_out, d_offs, tiles, 0, (0, 0, IMG_W, IMG_H), d_dec, 0, stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        enc_ms.append(ev[0].elapsed_time(ev[1]))
+        dec_ms.append(ev[1].elapsed_time(ev[2]))
+
+    clocks = ClockSampler(local)
+    codec.set_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    t0.record(stream)
+    for _ in range(args.steps):
+        launches += step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    stages = codec.stage_times()
+    codec.set_timing(False)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / args.steps
+    value = world * mp / (ms_step / 1e3)
+
+    # exactness on the bench's own launch: decoded tiles equal the oracle's, sampled
+    exact = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        rng = np.random.default_rng(7)
+        o = d_offs.cpu().numpy()
+        idx = rng.choice(len(grid), 12, replace=False).tolist() + [len(grid) - 1]
+        ok = True
+        img_np = h_img.numpy()
+        for i in idx:
+            x, y, w, h = grid[i]
+            ref = oracle.encode_tile(np.ascontiguousarray(img_np[y:y + h, x:x + w]), LEVELS, 8, q)
+            got = d_out[int(o[i]):int(o[i + 1])].cpu().numpy().tobytes()
+            dec_ok = np.array_equal(d_dec[y:y + h, x:x + w].cpu().numpy(), oracle.decode_tile(ref, 0))
+            ok = ok and got == ref and dec_ok
+        exact = {"sampled_tiles": len(idx), "bit_exact": bool(ok)}
+
+    # roofline of the dominant single-kernel stage
+    hbm, peak_kind = peaks()
+    n_tiles = len(grid)
+    coef_elems = 0
+    for (x, y, w, h) in grid:
+        lw, lh = w, h
+        cnt = 0
+        for _ in range(LEVELS):
+            lw, lh = (lw + 1) // 2, (lh + 1) // 2
+            cnt += 3 * ((lw + 3) // 4 * 4) * ((lh + 3) // 4 * 4)
+        cnt += ((lw + 3) // 4 * 4) * ((lh + 3) // 4 * 4)
+        coef_elems += 3 * cnt
+    n_blocks = 0
+    for (x, y, w, h) in grid:
+        n_blocks += 3 * (LEVELS + 1)
+    algo = {   # bytes each stage must move in this design, per call
+        "encode.stats": 4 * coef_elems + 1200 * n_blocks,
+        "encode.emit": 4 * coef_elems + 1700 * n_blocks + total_bytes,
+        "encode.huffman": (1200 + 1700) * n_blocks,
+        "decode.blocks": total_bytes + 4 * IMG_W * IMG_H * 3,
+        "decode.inverse_transform": 2 * 2 * 4 * IMG_W * IMG_H * 3,
+        "encode.transform": 2 * 2 * 4 * IMG_W * IMG_H * 3 + 3 * IMG_W * IMG_H,
+    }
+    single = {k: v for k, v in stages.items() if k in algo}
+    dom = max(single, key=lambda k: single[k][0]) if single else None
+    roof = None
+    if dom:
+        avg_ms = single[dom][0] / max(1, single[dom][1])
+        ach = algo[dom] / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+                "traffic": None, "peak_kind": peak_kind, "avg_launch_ms": round(avg_ms, 3)}
+    path_bytes = 3 * IMG_W * IMG_H + total_bytes
+    path = {"encode_GBps": round(path_bytes / (statistics.median(enc_ms) / 1e3) / 1e9, 1),
+            "decode_GBps": round(path_bytes / (statistics.median(dec_ms) / 1e3) / 1e9, 1),
+            "algorithmic_bytes_per_px": round(path_bytes / (IMG_W * IMG_H), 3), "peak_GBps": hbm}
+    path["encode_frac"] = round(path["encode_GBps"] / hbm, 4)
+    path["decode_frac"] = round(path["decode_GBps"] / hbm, 4)
+
+    # per-tile decode latency (single-tile region requests), device time
+    lat = []
+    rng = np.random.default_rng(3)
+    tile_out = torch.empty((TILE, TILE, 3), dtype=torch.uint8, device=dev)
+    for i in rng.choice(n_tiles, 64, replace=False).tolist():
+        x, y, w, h = grid[i]
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        codec.decode_region(d_out, d_offs, tiles, 0, (x, y, w, h), tile_out, 0, stream)
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+    lat.sort()
+
+    # end to end through the host-buffer entry points (pinned host memory)
+    h_np = h_img.numpy()
+    h_tiles = isx.TileArray([isx.tile_from_array(h_np[y:y + h, x:x + w], LEVELS, 8, q, x, y) for (x, y, w, h) in grid])
+    e2e = None
+    if not args.no_e2e:
+        import torch as _t
+        h_out = _t.empty(cap, dtype=_t.uint8, pin_memory=True).numpy()
+        h_offs = np.zeros(len(grid) + 1, np.uint64)
+        h_dec = _t.empty((IMG_H, IMG_W, 3), dtype=_t.uint8, pin_memory=True).numpy()
+        codec.encode_tiles_host(h_tiles, h_out, h_offs)
+        e2e_steps = max(1, min(args.steps, 3))
+        t_start = time.perf_counter()
+        for _ in range(e2e_steps):
+            codec.encode_tiles_host(h_tiles, h_out, h_offs)
+            codec.decode_region_host(h_out, h_offs, h_tiles, 0, (0, 0, IMG_W, IMG_H), h_dec)
+        e2e_s = (time.perf_counter() - t_start) / e2e_steps
+        nbytes = int(h_offs[-1])
+        e2e = {"value": round(world * mp / e2e_s, 1), "unit": "MP/s",
+               "h2d_bytes_per_step": 3 * IMG_W * IMG_H + nbytes + 8 * (len(grid) + 1),
+               "d2h_bytes_per_step": nbytes + 8 * (len(grid) + 1) + 3 * IMG_W * IMG_H}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(h_img.numpy(), grid, q, args.cpu_tiles)
+
+    res = {"metric": METRIC, "value": round(value, 1), "unit": "MP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+           "data": "synthetic",
+           "config": {"workload": f"slide_{IMG_W}x{IMG_H}_rgb8_tile{TILE}_L{LEVELS}_" + ("lossless" if args.lossless else "lossy_q8421"),
+                      "tiles": n_tiles, "megapixels_per_gpu": round(mp, 1), "l2": "inputs larger than L2 (3.6 GB per step)",
+                      "parallelism": f"replicas x{world}"},
+           "encode_mps": round(mp / (statistics.median(enc_ms) / 1e3), 1),
+           "decode_mps": round(mp / (statistics.median(dec_ms) / 1e3), 1),
+           "compressed_bytes": total_bytes, "bits_per_pixel": round(8 * total_bytes / (IMG_W * IMG_H), 3),
+           "exact": exact, "roofline": roof, "path_roofline": path,
+           "tile_decode_latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[int(0.99 * (len(lat) - 1))], 3)},
+           "stages_ms": {k: round(v[0] / max(1, v[1]), 3) for k, v in stages.items()},
+           "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+    codec.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return res if rank == 0 else None
+
+
+def cpu_baseline(img, grid, q, n_tiles):
+    """The oracle as it stands, all host cores, on a bounded sample of the workload's tiles."""
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(11)
+    idx = rng.choice(len(grid), min(n_tiles, len(grid)), replace=False)
+    imgs = [np.ascontiguousarray(img[grid[i][1]:grid[i][1] + grid[i][3], grid[i][0]:grid[i][0] + grid[i][2]]) for i in idx]
+    ts = [oracle.tile_struct(a.shape[1], a.shape[0], 3, 8, LEVELS, q) for a in imgs]
+    mp = sum(a.shape[0] * a.shape[1] for a in imgs) / 1e6
+    t0 = time.perf_counter()
+    streams = oracle.encode_tiles_mt(imgs, ts, cores)
+    t1 = time.perf_counter()
+    outs = [np.zeros_like(a) for a in imgs]
+    oracle.decode_tiles_mt(streams, 0, outs, cores)
+    t2 = time.perf_counter()
+    return {"value": round(mp / (t2 - t0), 2), "unit": "MP/s", "cores": cores, "kind": "oracle",
+            "encode_mps": round(mp / (t1 - t0), 2), "decode_mps": round(mp / (t2 - t1), 2),
+            "sample": f"{len(imgs)} random 256x256 tiles of the same slide ({mp:.1f} MP), encode+decode, thread pool over tiles"}
+
+
+def run_reference(args):
+    """The CPU oracle timed on the machine's host cores (reference arm)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    from paper_2005_08713_gb300 import synth
+    import oracle
+    grid = tile_grid()
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(5)
+    n = args.cpu_tiles
+    idx = rng.choice(len(grid), n, replace=False)
+    q = LOSSY_Q if not args.lossless else [0] * 9
+    seed = synth.config_seed(3)
+    imgs = [synth.slide(seed, grid[i][0], grid[i][1], grid[i][2], grid[i][3]) for i in idx]
+    ts = [oracle.tile_struct(a.shape[1], a.shape[0], 3, 8, LEVELS, q) for a in imgs]
+    mp = sum(a.shape[0] * a.shape[1] for a in imgs) / 1e6
+    outs = [np.zeros_like(a) for a in imgs]
+
+    def one():
+        s = oracle.encode_tiles_mt(imgs, ts, cores)
+        oracle.decode_tiles_mt(s, 0, outs, cores)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = mp / dt
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "MP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"slide_{IMG_W}x{IMG_H}_rgb8_tile{TILE}_L{LEVELS}_" + ("lossless" if args.lossless else "lossy_q8421"),
+                       "sample_tiles": n},
+            "cpu_baseline": {"value": round(value, 2), "unit": "MP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} random tiles of the slide per step ({mp:.1f} MP), encode+decode"},
+            "e2e": {"value": round(value, 2), "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--lossless", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--cpu-tiles", type=int, default=256)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        res = run_gpu(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/* isx.h — C ABI of the GB300 codec library (libisx_gb300.so).
+ *
+ * The library implements, on one NVIDIA GB300 (sm_103a), the encoder and
+ * decoder of Hulsken, "Fast Compression Method for Medical Images on the
+ * Web" (2020):  reversible colour transform and recursive 5/3 integer
+ * lifting wavelet (Sec. 3, Sec. 4), JPEG 2000-style quantisation (Sec. 3),
+ * 128 x 128 coefficient blocks serialised into signed-magnitude bitplanes of
+ * 4 x 2 areas (Eq. 1, Eq. 2), empty-plane removal, zero runs with an
+ * optimised counter width (Eq. 3), per-block Huffman codes and the
+ * compressed block layout of Fig. 3; decoding at any resolution level and
+ * with dropped least significant planes (Sec. 4, "Decompression").
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* (and isx_tile_desc.pixels) are DEVICE pointers on
+ *    the context's GPU; h_* pointers are host memory.  The caller owns all
+ *    buffers it passes; the library owns only the scratch of its context.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream ordered and asynchronous unless stated otherwise: results are
+ *    valid once the stream has been synchronised.
+ *  - Argument errors are returned synchronously and nothing is enqueued.
+ *    Data errors found on the GPU (corrupt stream, output capacity) are
+ *    recorded in the context's device status word; isx_sync_status()
+ *    synchronises the stream and returns (and clears) them.  No kernel
+ *    traps and no call aborts the process.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef ISX_H_
+#define ISX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct isx_ctx isx_ctx;
+
+typedef enum {
+  ISX_OK = 0,
+  ISX_ERR_ARG = 1,       /* invalid argument (nothing enqueued) */
+  ISX_ERR_CAPACITY = 2,  /* output buffer too small; required size reported */
+  ISX_ERR_CORRUPT = 3,   /* malformed compressed stream */
+  ISX_ERR_OOM = 4,       /* scratch would exceed the context's HBM budget, or cudaMalloc failed */
+  ISX_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+  ISX_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up */
+} isx_status;
+
+/* One tile: an independent rectangle of an image, transformed on its own.
+ * pixels: DEVICE pointer, interleaved HWC samples, uint8 when bits <= 8 and
+ * uint16 otherwise, rows `row_pitch_bytes` apart.  channels = 3 applies the
+ * reversible colour transform (JPEG 2000 RCT; the paper's "optional
+ * colorspace transformation", Fig. 1); channels = 1 codes the samples as is.
+ * qstep_log2[l-1] is the quantiser step 2^q of wavelet level l (l = 1 is the
+ * finest), qstep_log2[levels] the step of the LL band; all 0 = lossless.
+ * x0, y0 place the tile in the image (level-0 pixels) for region decodes. */
+typedef struct {
+  int32_t width, height;   /* 1 .. 65535 */
+  int32_t channels;        /* 1 or 3 */
+  int32_t bits;            /* significant bits per sample, 1 .. 16 (3 channels: 1 .. 8) */
+  int32_t levels;          /* wavelet levels, 0 .. 15 */
+  int32_t x0, y0;          /* tile origin in the image, >= 0 */
+  uint8_t qstep_log2[16];  /* 0 .. 15 each */
+  const void* pixels;      /* device pointer (ignored by decode calls) */
+  int64_t row_pitch_bytes;
+} isx_tile_desc;
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * scratch the context may hold (0 = no cap). */
+isx_status isx_create(isx_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Frees the context and its scratch (synchronises the device first). */
+void isx_destroy(isx_ctx* ctx);
+
+/* Encode n_tiles tiles into one contiguous stream (Fig. 1 left to right,
+ * Fig. 2 a-e, Fig. 3).
+ *   tiles          HOST array of n_tiles descriptors (pixels on the device).
+ *   d_out          DEVICE buffer of out_capacity bytes receiving the tile
+ *                  streams back to back, tile i at d_tile_offsets[i].
+ *   d_tile_offsets DEVICE array of n_tiles + 1 uint64; [n_tiles] is the
+ *                  total size.  If the total exceeds out_capacity nothing
+ *                  is written to d_out, [n_tiles] still receives the
+ *                  required size and isx_sync_status returns
+ *                  ISX_ERR_CAPACITY.
+ * Tile stream layout (little endian): "ISX1", u16 width, u16 height,
+ * u8 channels, u8 bits, u8 levels, u8 colour transform (1 = RCT),
+ * u32 n_blocks, u8 qstep_log2[16], u32 block_end[n_blocks], block data.
+ * Blocks: per channel the LL blocks, then the high-pass blocks of levels
+ * L .. 1, each subband cut into 128 x 128 cells in raster order.  The bytes
+ * are identical to those of the reference CPU codec. */
+isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, void* d_out,
+                            size_t out_capacity, uint64_t* d_tile_offsets, void* stream);
+
+/* Decode the rectangle (rx, ry, rw, rh), given in pixels of resolution level
+ * `level` (0 = full size; level z halves the size z times, Sec. 4
+ * "reconstruct the image at any resolution level ... by simply discarding
+ * the high-pass coefficients"), from tiles encoded by isx_encode_tiles.
+ *   d_stream, d_tile_offsets  DEVICE stream and its n_tiles + 1 offsets.
+ *   tiles           HOST array describing the same tiles (pixels ignored).
+ *   drop_lsb_planes discards that many least significant magnitude planes
+ *                   of every block (Sec. 4, quality-progressive decode).
+ *   d_out           DEVICE buffer, rh rows of rw * channels samples
+ *                   (uint8 for bits <= 8, else uint16), out_pitch_bytes
+ *                   apart.  Every tile must share channels and bits.
+ * A tile covers [x0 >> level, (x0 >> level) + ceil(width / 2^level)) at
+ * level `level`.  Pixels of the rectangle that no tile covers are left
+ * unchanged.  level must not exceed the levels of any tile it touches. */
+isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets,
+                             const isx_tile_desc* tiles, int32_t n_tiles, int32_t level, int32_t rx,
+                             int32_t ry, int32_t rw, int32_t rh, int32_t drop_lsb_planes, void* d_out,
+                             int64_t out_pitch_bytes, void* stream);
+
+/* End-to-end encode of tiles held in HOST memory (pinned or pageable):
+ * copies every tile's pixels to the device (tiles[i].pixels is a HOST
+ * pointer here), encodes them, and copies the stream and the offsets back
+ * into h_out (out_capacity bytes) and h_tile_offsets (n_tiles + 1).
+ * Synchronous: returns once the host buffers hold the result. */
+isx_status isx_encode_tiles_host(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, void* h_out,
+                                 size_t out_capacity, uint64_t* h_tile_offsets, void* stream);
+
+/* End-to-end region decode from a HOST stream: copies the stream
+ * (h_tile_offsets[n_tiles] bytes) and offsets to the device, decodes as
+ * isx_decode_region and copies the rw x rh x channels result into h_out
+ * (pixels that no tile covers are written as 0).  Synchronous. */
+isx_status isx_decode_region_host(isx_ctx* ctx, const void* h_stream, const uint64_t* h_tile_offsets,
+                                  const isx_tile_desc* tiles, int32_t n_tiles, int32_t level, int32_t rx,
+                                  int32_t ry, int32_t rw, int32_t rh, int32_t drop_lsb_planes, void* h_out,
+                                  int64_t out_pitch_bytes, void* stream);
+
+/* Forward transform stage alone: colour transform, wavelet and
+ * quantisation of each tile, written as int32 Mallat planes (per tile,
+ * channels planes of height x width, tiles back to back) to d_coef, which
+ * must hold sum(channels * width * height) elements. */
+isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles,
+                                    int32_t* d_coef, void* stream);
+
+/* Synchronises `stream` and returns the first data error recorded on the
+ * device since the last call (ISX_OK if none), then clears it. */
+isx_status isx_sync_status(isx_ctx* ctx, void* stream);
+
+/* Stage timing for profiling: when enabled, CUDA events are recorded
+ * between the kernel groups of every encode/decode call on its stream
+ * (stage names such as "encode.emit" or "decode.blocks").  Enabling or
+ * disabling clears the running totals. */
+isx_status isx_set_timing(isx_ctx* ctx, int32_t enable);
+
+/* Running totals of the stage timings: writes up to `cap` entries of total
+ * milliseconds (ms) and call counts (counts), and the stage names, one per
+ * line, into `names` (names_len bytes, NUL terminated).  Synchronises on the
+ * recorded events.  Returns the number of stages, or -1 for a null ctx. */
+int32_t isx_stage_times(isx_ctx* ctx, char* names, int64_t names_len, double* ms, int64_t* counts, int32_t cap);
+
+/* Number of kernels the last encode/decode call enqueued. */
+int32_t isx_last_launch_count(isx_ctx* ctx);
+
+/* Message for the last error on this context (static storage). */
+const char* isx_last_error(isx_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISX_H_ */

@@ -1,0 +1,187 @@
+// isx_internal.cuh — device-side data structures and primitives of the
+// GB300 codec library.  Not part of the public ABI (include/isx.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace isx {
+
+constexpr int kCell = 128;          // coefficient block edge (Sec. 4: "partitioned in 128*128 blocks")
+constexpr int kMaxLevels = 15;
+constexpr int kMaxD = 31;           // block bit depth field is 5 bits
+constexpr int kMaxW = 18;           // largest zero-run counter width considered (w in [2, b], b <= 18)
+constexpr int kCtaThreads = 256;    // CTA size of the per-block coding kernels
+
+enum DevStatus : int { kStOk = 0, kStCapacity = 2, kStCorrupt = 3, kStTimeout = 6 };
+
+// One tile as the kernels see it (copied from isx_tile_desc plus its plan).
+struct TileDev {
+  const uint8_t* pixels;    // device, HWC
+  int64_t pitch;            // bytes
+  int32_t w, h, C, bits, L, x0, y0;
+  uint8_t q[16];
+  int32_t nb;               // number of coefficient blocks
+  int64_t block_base;       // index of its first block
+  int64_t plane_base;       // element offset of its first Mallat plane
+  int64_t coef_base;        // element offset of its first area-ordered block
+};
+
+// One coefficient block (Fig. 3): LL (p = 1) or HL, LH, HH (p = 3).
+struct BlockDev {
+  int32_t tile, c, level;   // level 0 = the LL band of the tile
+  int32_t by, bx;           // cell position within the subband grid
+  int32_t p, w, h;          // types and padded size (multiples of 4)
+  int64_t coef;             // element offset of its coefficients: [type][area][8]
+};
+
+// Per-block statistics gathered from the symbol stream (encode, pass 1).
+struct BlockStats {
+  uint32_t hist[256];       // literal counts; [0] = isolated zero symbols, [s] = raw count of s
+  uint32_t extra[kMaxW + 1];// sum over runs of (ceil(L / (2^w - 1)) - 1), w = 2..18
+  uint32_t n_runs;          // zero runs of length >= 2
+  uint32_t n_sym;           // kept symbols
+  uint32_t removed[3];      // bit pl set: plane pl of that type removed
+  int32_t d;
+};
+
+// Per-block code (encode, pass 2).
+struct BlockCode {
+  uint32_t code[256];
+  uint8_t len[256];
+  uint32_t tree[80];        // preorder tree, MSB-first bit string (<= 2559 bits)
+  int32_t tree_bits;
+  int32_t czr, wbits, t0;   // zero-run symbol, counter width, default seektable width
+  int32_t d, p, any_kept;
+  uint32_t removed[3];
+  uint64_t token_bits;      // sum of all segment lengths
+  uint64_t slot_bytes;      // upper bound of the block size (t at its largest)
+};
+
+__host__ __device__ inline int level_dim(int n, int l) {
+  for (int i = 0; i < l; ++i) n = (n + 1) >> 1;
+  return n;
+}
+__host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ inline int bitlen32(uint32_t v) { return v ? 32 - __builtin_clz(v) : 0; }
+__device__ inline int bitlen_u32(uint32_t v) { return 32 - __clz(v); }
+__device__ inline int bitlen_u64(uint64_t v) { return 64 - __clzll(v); }
+
+// Area order of Eq. 1 (reading: i = 4 floor(2k'/w) + 2 (k' mod 2),
+// j = 4 (floor(k'/2) mod (w/4))) for the within-plane index k'.
+__device__ inline void area_ij(int k, int w, int* i, int* j) {
+  *i = 4 * ((2 * k) / w) + 2 * (k & 1);
+  *j = 4 * ((k >> 1) % (w >> 2));
+}
+
+// Subband rectangle of a block's type within the tile's Mallat plane.
+__device__ inline void subband_rect(int tw, int th, int L, int level, int type, int* x, int* y, int* sw, int* sh) {
+  if (level == 0) {
+    *x = 0; *y = 0; *sw = level_dim(tw, L); *sh = level_dim(th, L);
+    return;
+  }
+  int pw = level_dim(tw, level - 1), ph = level_dim(th, level - 1);
+  int lw = (pw + 1) >> 1, lh = (ph + 1) >> 1;
+  if (type == 0) { *x = lw; *y = 0; *sw = pw >> 1; *sh = lh; }
+  else if (type == 1) { *x = 0; *y = lh; *sw = lw; *sh = ph >> 1; }
+  else { *x = lw; *y = lh; *sw = pw >> 1; *sh = ph >> 1; }
+}
+
+__device__ inline int qlog2_of(const TileDev& t, int level) { return level == 0 ? t.q[t.L] : t.q[level - 1]; }
+
+// --------------------------------------------------------- CTA primitives
+// Exclusive sum scan over the CTA (blockDim.x a multiple of 32, <= 1024).
+template <typename T>
+__device__ T cta_exclusive_sum(T v, T* warp_tmp /* >= 33 */, T* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tmp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    T s = lane < nw ? warp_tmp[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) warp_tmp[lane] = s;   // inclusive warp prefixes
+    if (lane == nw - 1) warp_tmp[32] = s;
+  }
+  __syncthreads();
+  T base = wid ? warp_tmp[wid - 1] : T(0);
+  T res = base + x - v;
+  if (total) *total = warp_tmp[32];
+  __syncthreads();
+  return res;
+}
+
+// Zero-carry scan element: bit 31 = "all symbols so far are zero",
+// low bits = number of zeros at the end of the covered range.
+__device__ inline uint32_t carry_combine(uint32_t a, uint32_t b) {
+  const uint32_t AZ = 0x80000000u;
+  if (b & AZ) return (a & AZ) | ((a & ~AZ) + (b & ~AZ));
+  return b;
+}
+
+__device__ inline uint32_t cta_exclusive_carry(uint32_t v, uint32_t* warp_tmp /* >= 33 */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t ID = 0x80000000u;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = carry_combine(y, x);
+  }
+  if (lane == 31) warp_tmp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t s = lane < nw ? warp_tmp[lane] : ID;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s = carry_combine(y, s);
+    }
+    if (lane < nw) warp_tmp[lane] = s;
+  }
+  __syncthreads();
+  uint32_t prev_in_warp = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) prev_in_warp = ID;
+  uint32_t base = wid ? warp_tmp[wid - 1] : ID;
+  uint32_t res = carry_combine(base, prev_in_warp);
+  __syncthreads();
+  return res;
+}
+
+template <typename T>
+__device__ T cta_reduce_max(T v, T* tmp /* >= 32 */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T y = __shfl_xor_sync(0xffffffffu, v, o);
+    v = v > y ? v : y;
+  }
+  if (lane == 0) tmp[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    T s = lane < nw ? tmp[lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T y = __shfl_xor_sync(0xffffffffu, s, o);
+      s = s > y ? s : y;
+    }
+    if (lane == 0) tmp[0] = s;
+  }
+  __syncthreads();
+  T r = tmp[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ inline void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+}  // namespace isx

@@ -1,0 +1,69 @@
+// isx_kernels.h — host-callable launchers of the library's kernels.  Each
+// returns the number of kernels it enqueued (counted for the benchmark).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "isx_internal.cuh"
+
+namespace isx {
+
+int launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* part, int64_t* total, cudaStream_t s);
+int launch_plan_blocks(const TileDev* d_tiles, int n_tiles, int min_level, BlockDev* d_blocks, cudaStream_t s);
+int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B,
+                             cudaStream_t s);
+int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t n_blocks, const int32_t* planes, int32_t* coef,
+                       cudaStream_t s);
+int launch_quantise_planes(const TileDev* d_tiles, int n_tiles, const int32_t* planes, int32_t* out, cudaStream_t s);
+int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int32_t* A, int32_t* B,
+                             cudaStream_t s);
+int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, void* out, int64_t pitch, int rx, int ry,
+                        int rw, int rh, cudaStream_t s);
+
+// encode coding stages
+struct EncodeBuffers {
+  const TileDev* tiles;
+  int n_tiles;
+  const BlockDev* blocks;
+  int64_t n_blocks;
+  const int32_t* coef;
+  BlockStats* stats;
+  BlockCode* codes;
+  int64_t* slot_size;     // [n_blocks]
+  int64_t* slot_off;      // [n_blocks]
+  int64_t* exact_size;    // [n_blocks]  (item sizes for the final scan: block + its tile header when first)
+  int64_t* final_pos;     // [n_blocks]
+  int64_t* scan_part;     // scan partials
+  int64_t* totals;        // [4]: slot total, stream total
+  uint8_t* slots;
+  int64_t slot_capacity;
+  uint8_t* out;
+  int64_t out_capacity;
+  uint64_t* tile_offsets; // [n_tiles + 1]
+  int* status;
+};
+// Records an event between kernel groups: closes the open stage and opens
+// `name` (nullptr: none).  A no-op unless timing is enabled.
+struct StageMarks {
+  virtual void mark(const char* name, cudaStream_t s) = 0;
+  virtual ~StageMarks() = default;
+};
+int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T);
+
+// decode stages
+struct DecodeBuffers {
+  const TileDev* tiles;      // selected tiles (plane_base over level-z planes)
+  int n_tiles;
+  const int64_t* tile_index; // [n_tiles] index of each selected tile in the stream's offset table
+  const uint8_t* stream;
+  const uint64_t* stream_offsets;
+  BlockDev* blocks;
+  int64_t* block_byte;       // [n_blocks] byte offset of each block in the stream
+  int32_t* block_len;        // [n_blocks]
+  int64_t n_blocks;
+  int z, drop;
+  int32_t* planes;
+  int* status;
+};
+int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T);
+
+}  // namespace isx

@@ -1,0 +1,383 @@
+// isx_transform.cu — planning, scans, colour transform and the recursive
+// 5/3 lifting wavelet (forward and inverse), quantisation and the
+// area-ordered coefficient layout used by the block coder.
+//
+// Wavelet (Sec. 4, "MATLAB's 5/3 Le Gall integer lifting"): per level the
+// current LL region is lifted down every column, then along every row
+// (predict d[n] = x[2n+1] - floor((x[2n]+x[2n+2])/2), update
+// s[n] = x[2n] + floor((d[n-1]+d[n]+2)/4), mirrored at both ends); low
+// outputs go to the first ceil(N/2) positions, high outputs after them
+// (Mallat layout).  Floors are arithmetic right shifts.
+#include "isx_internal.cuh"
+#include "isx_kernels.h"
+
+namespace isx {
+
+// ------------------------------------------------------------ planning
+// One thread per tile: enumerate its blocks in stream order (per channel:
+// LL cells, then the high-pass cells of levels L..1, raster order) and
+// give each its slice of the area-ordered coefficient buffer.
+// min_level > 0 keeps only LL blocks and levels > min_level (decode at a
+// coarser resolution); out_index then counts the kept blocks only.
+__global__ void k_plan_blocks(const TileDev* __restrict__ tiles, int n_tiles, int min_level, BlockDev* __restrict__ out) {
+  int ti = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ti >= n_tiles) return;
+  const TileDev t = tiles[ti];
+  int64_t idx = t.block_base;
+  int64_t coef = t.coef_base;
+  for (int c = 0; c < t.C; ++c) {
+    for (int lv = 0; lv <= t.L; ++lv) {
+      int level = lv == 0 ? 0 : t.L + 1 - lv;   // 0 (LL), then L, L-1, ..., 1
+      if (level != 0 && level <= min_level) continue;
+      int gw = level_dim(t.w, level == 0 ? t.L : level), gh = level_dim(t.h, level == 0 ? t.L : level);
+      int p = level == 0 ? 1 : 3;
+      for (int by = 0; by < ceil_div(gh, kCell); ++by)
+        for (int bx = 0; bx < ceil_div(gw, kCell); ++bx) {
+          BlockDev b;
+          b.tile = ti; b.c = c; b.level = level; b.by = by; b.bx = bx; b.p = p;
+          b.w = pad4(min(kCell, gw - kCell * bx));
+          b.h = pad4(min(kCell, gh - kCell * by));
+          b.coef = coef;
+          coef += (int64_t)p * b.w * b.h;
+          out[idx++] = b;
+        }
+    }
+  }
+}
+
+// --------------------------------------------------------------- scans
+// Exclusive prefix sum of int64 values, three phases; n up to 2^31.
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = 256 * kScanItems;
+
+__global__ void __launch_bounds__(256) k_scan_reduce(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ part) {
+  __shared__ int64_t tmp[33];
+  int64_t base = (int64_t)blockIdx.x * kScanChunk;
+  int64_t s = 0;
+  for (int i = 0; i < kScanItems; ++i) {
+    int64_t k = base + (int64_t)i * 256 + threadIdx.x;
+    if (k < n) s += in[k];
+  }
+  int64_t total;
+  cta_exclusive_sum<int64_t>(s, tmp, &total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(256) k_scan_partials(int64_t* __restrict__ part, int64_t np, int64_t* __restrict__ total_out) {
+  __shared__ int64_t tmp[33];
+  int64_t carry = 0;
+  for (int64_t base = 0; base < np; base += 256) {
+    int64_t k = base + threadIdx.x;
+    int64_t v = k < np ? part[k] : 0;
+    int64_t tot;
+    int64_t ex = cta_exclusive_sum<int64_t>(v, tmp, &tot);
+    if (k < np) part[k] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(256) k_scan_final(const int64_t* __restrict__ in, int64_t n, const int64_t* __restrict__ part,
+                                                    int64_t* __restrict__ out) {
+  __shared__ int64_t tmp[33];
+  int64_t base = (int64_t)blockIdx.x * kScanChunk;
+  // each thread owns kScanItems consecutive elements
+  int64_t v[kScanItems];
+  int64_t s = 0;
+  for (int i = 0; i < kScanItems; ++i) {
+    int64_t k = base + (int64_t)threadIdx.x * kScanItems + i;
+    v[i] = k < n ? in[k] : 0;
+    s += v[i];
+  }
+  int64_t ex = cta_exclusive_sum<int64_t>(s, tmp, nullptr) + part[blockIdx.x];
+  for (int i = 0; i < kScanItems; ++i) {
+    int64_t k = base + (int64_t)threadIdx.x * kScanItems + i;
+    if (k < n) out[k] = ex;
+    ex += v[i];
+  }
+}
+
+int launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* part, int64_t* total, cudaStream_t s) {
+  int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  if (nb == 0) nb = 1;
+  k_scan_reduce<<<(unsigned)nb, 256, 0, s>>>(in, n, part);
+  k_scan_partials<<<1, 256, 0, s>>>(part, nb, total);
+  k_scan_final<<<(unsigned)nb, 256, 0, s>>>(in, n, part, out);
+  return 3;
+}
+
+// --------------------------------------------------- colour transform
+// Pixels -> C int32 planes (Mallat plane 0 .. C-1 of the tile).  RCT of
+// JPEG 2000 for 3 channels: Y = floor((R+2G+B)/4), Cb = B-G, Cr = R-G.
+__global__ void k_load_pixels(const TileDev* __restrict__ tiles, int32_t* __restrict__ planes) {
+  const TileDev& t = tiles[blockIdx.x];
+  const int64_t np = (int64_t)t.w * t.h;
+  int32_t* out = planes + t.plane_base;
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < np; e += (int64_t)gridDim.y * blockDim.x) {
+    int y = (int)(e / t.w), x = (int)(e - (int64_t)y * t.w);
+    const uint8_t* row = t.pixels + (int64_t)y * t.pitch;
+    int32_t v[3];
+    for (int c = 0; c < t.C; ++c)
+      v[c] = t.bits <= 8 ? (int32_t)row[x * t.C + c] : (int32_t)((const uint16_t*)row)[x * t.C + c];
+    if (t.C == 3) {
+      int32_t R = v[0], G = v[1], B = v[2];
+      out[e] = (R + 2 * G + B) >> 2;
+      out[np + e] = B - G;
+      out[2 * np + e] = R - G;
+    } else {
+      out[e] = v[0];
+    }
+  }
+}
+
+// -------------------------------------------------------------- lifting
+// Forward 1-D lifting of n samples read with `stride`, low outputs to
+// out[0 .. nl), high outputs to out[nl .. n) (same stride).
+__device__ void lift_fwd(const int32_t* x, int32_t* out, int n, int64_t stride) {
+  if (n == 1) { out[0] = x[0]; return; }
+  const int nl = (n + 1) >> 1;
+  int32_t xe = x[0], dprev = 0;
+  for (int k = 0; k < nl; ++k) {
+    int32_t d, xe2;
+    if (2 * k + 1 < n) {
+      int32_t xo = x[(int64_t)(2 * k + 1) * stride];
+      xe2 = (2 * k + 2 < n) ? x[(int64_t)(2 * k + 2) * stride] : xe;   // x[n] mirrors to x[n-2]
+      d = xo - ((xe + xe2) >> 1);
+      out[(int64_t)(nl + k) * stride] = d;
+    } else {
+      d = dprev;   // odd n, last even sample: d[nh] mirrors to d[nh-1]
+      xe2 = xe;
+    }
+    int32_t dm1 = k == 0 ? d : dprev;   // d[-1] mirrors to d[0]
+    out[(int64_t)k * stride] = xe + ((dm1 + d + 2) >> 2);
+    dprev = d;
+    xe = xe2;
+  }
+}
+
+// Inverse of lift_fwd: in holds low [0, nl) and high [nl, n).
+__device__ void lift_inv(const int32_t* in, int32_t* x, int n, int64_t stride) {
+  if (n == 1) { x[0] = in[0]; return; }
+  const int nl = (n + 1) >> 1, nh = n >> 1;
+  int32_t dk = in[(int64_t)nl * stride];
+  int32_t e = in[0] - ((dk + dk + 2) >> 2);
+  for (int k = 0; k < nh; ++k) {
+    int32_t en;
+    int32_t dk1 = dk;
+    if (k + 1 < nl) {
+      if (k + 1 < nh) dk1 = in[(int64_t)(nl + k + 1) * stride];
+      en = in[(int64_t)(k + 1) * stride] - ((dk + dk1 + 2) >> 2);
+    } else {
+      en = e;   // even n: x[n] mirrors to x[n-2]
+    }
+    x[(int64_t)(2 * k) * stride] = e;
+    x[(int64_t)(2 * k + 1) * stride] = dk + ((e + en) >> 1);
+    e = en;
+    dk = dk1;
+  }
+  if (n & 1) x[(int64_t)(n - 1) * stride] = e;
+}
+
+// Task = (tile, channel) in blockIdx.x (3 slots per tile); blockIdx.y
+// chunks the columns (vertical) or rows (horizontal) of the LL region.
+// Plane geometry: stride = plane_w (the tile width for encode, the level-z
+// width for decode); region cw x ch at level `lvl` of each tile.
+struct PassGeom {
+  int cw, ch, stride;
+  int64_t base;
+};
+
+__device__ inline bool pass_geom(const TileDev& t, int c, int lvl, bool decode_plane, int z, PassGeom* g) {
+  if (c >= t.C || lvl >= t.L || lvl < z) return false;
+  int pw = decode_plane ? level_dim(t.w, z) : t.w;
+  int ph = decode_plane ? level_dim(t.h, z) : t.h;
+  g->cw = level_dim(t.w, lvl);
+  g->ch = level_dim(t.h, lvl);
+  g->stride = pw;
+  g->base = t.plane_base + (int64_t)c * pw * ph;
+  return true;
+}
+
+__global__ void k_fwd_vpass(const TileDev* __restrict__ tiles, int lvl, const int32_t* __restrict__ A, int32_t* __restrict__ B) {
+  const TileDev& t = tiles[blockIdx.x / 3];
+  PassGeom g;
+  if (!pass_geom(t, blockIdx.x % 3, lvl, false, 0, &g)) return;
+  int col = blockIdx.y * blockDim.x + threadIdx.x;
+  if (col >= g.cw) return;
+  lift_fwd(A + g.base + col, B + g.base + col, g.ch, g.stride);
+}
+
+__global__ void k_fwd_hpass(const TileDev* __restrict__ tiles, int lvl, const int32_t* __restrict__ B, int32_t* __restrict__ A) {
+  const TileDev& t = tiles[blockIdx.x / 3];
+  PassGeom g;
+  if (!pass_geom(t, blockIdx.x % 3, lvl, false, 0, &g)) return;
+  int row = blockIdx.y * blockDim.x + threadIdx.x;
+  if (row >= g.ch) return;
+  lift_fwd(B + g.base + (int64_t)row * g.stride, A + g.base + (int64_t)row * g.stride, g.cw, 1);
+}
+
+// Inverse level lvl (0-based: undoes the transform of LL_lvl) on decode
+// planes of size level_dim(w, z) x level_dim(h, z).
+__global__ void k_inv_hpass(const TileDev* __restrict__ tiles, int lvl, int z, const int32_t* __restrict__ A, int32_t* __restrict__ B) {
+  const TileDev& t = tiles[blockIdx.x / 3];
+  PassGeom g;
+  if (!pass_geom(t, blockIdx.x % 3, lvl, true, z, &g)) return;
+  int row = blockIdx.y * blockDim.x + threadIdx.x;
+  if (row >= g.ch) return;
+  lift_inv(A + g.base + (int64_t)row * g.stride, B + g.base + (int64_t)row * g.stride, g.cw, 1);
+}
+
+__global__ void k_inv_vpass(const TileDev* __restrict__ tiles, int lvl, int z, const int32_t* __restrict__ B, int32_t* __restrict__ A) {
+  const TileDev& t = tiles[blockIdx.x / 3];
+  PassGeom g;
+  if (!pass_geom(t, blockIdx.x % 3, lvl, true, z, &g)) return;
+  int col = blockIdx.y * blockDim.x + threadIdx.x;
+  if (col >= g.cw) return;
+  lift_inv(B + g.base + col, A + g.base + col, g.ch, g.stride);
+}
+
+// --------------------------------------------------------- quantise + pack
+// Per block: quantise (dead zone, q = sign(c) floor(|c| / 2^s)) and gather
+// the coefficients of every 4x2 area (Eq. 1 order) into 8 consecutive
+// int32 in Eq. 2 bit order (upper row then lower row, left to right).
+// Positions outside the subband are the zero padding.
+__global__ void __launch_bounds__(256) k_pack_blocks(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
+                                                     const int32_t* __restrict__ planes, int32_t* __restrict__ coef) {
+  const BlockDev b = blocks[blockIdx.x];
+  const TileDev& t = tiles[b.tile];
+  const int n = b.w * b.h / 8, na = b.p * n;
+  const int q = qlog2_of(t, b.level);
+  const int32_t* plane = planes + t.plane_base + (int64_t)b.c * t.w * t.h;
+  int32_t* out = coef + b.coef;
+  for (int a = threadIdx.x; a < na; a += blockDim.x) {
+    int type = a / n, k = a - type * n;
+    int i, j;
+    area_ij(k, b.w, &i, &j);
+    int sx, sy, sw, sh;
+    subband_rect(t.w, t.h, t.L, b.level, type, &sx, &sy, &sw, &sh);
+    int32_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      int yy = kCell * b.by + i + (e >> 2), xx = kCell * b.bx + j + (e & 3);
+      int32_t c = 0;
+      if (yy < sh && xx < sw) c = plane[(int64_t)(sy + yy) * t.w + sx + xx];
+      int32_t m = c < 0 ? -c : c;
+      m >>= q;
+      v[e] = c < 0 ? -m : m;
+    }
+    int4* o = reinterpret_cast<int4*>(out + (int64_t)a * 8);
+    o[0] = make_int4(v[0], v[1], v[2], v[3]);
+    o[1] = make_int4(v[4], v[5], v[6], v[7]);
+  }
+}
+
+// Copy quantised Mallat planes out (isx_forward_coefficients): the same
+// quantiser applied in place over each subband.
+__global__ void k_quantise_planes(const TileDev* __restrict__ tiles, const int32_t* __restrict__ planes, int32_t* __restrict__ out) {
+  const TileDev& t = tiles[blockIdx.x];
+  const int64_t np = (int64_t)t.w * t.h;
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < np * t.C; e += (int64_t)gridDim.y * blockDim.x) {
+    int64_t pe = e % np;
+    int y = (int)(pe / t.w), x = (int)(pe - (int64_t)y * t.w);
+    // which subband holds (x, y): the finest level whose detail region contains it
+    int level = 0;
+    for (int l = 1; l <= t.L; ++l) {
+      int lw = level_dim(t.w, l), lh = level_dim(t.h, l);
+      if (x >= lw || y >= lh) { level = l; break; }
+    }
+    int q = qlog2_of(t, level);
+    int32_t c = planes[t.plane_base + e];
+    int32_t m = c < 0 ? -c : c;
+    m >>= q;
+    out[t.plane_base + e] = c < 0 ? -m : m;
+  }
+}
+
+// ---------------------------------------------------------- decode output
+// Inverse RCT (G = Y - floor((Cb+Cr)/4), R = Cr + G, B = Cb + G), clamp to
+// [0, 2^bits - 1] and write the part of the tile's level-z image that
+// falls inside the requested rectangle.
+__global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const int32_t* __restrict__ planes, uint8_t* __restrict__ out,
+                               int64_t pitch, int rx, int ry, int rw, int rh) {
+  const TileDev& t = tiles[blockIdx.x];
+  const int zw = level_dim(t.w, z), zh = level_dim(t.h, z);
+  const int tx = t.x0 >> z, ty = t.y0 >> z;
+  const int64_t np = (int64_t)zw * zh;
+  const int32_t* pl = planes + t.plane_base;
+  const int32_t maxv = (1 << t.bits) - 1;
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < np; e += (int64_t)gridDim.y * blockDim.x) {
+    int y = (int)(e / zw), x = (int)(e - (int64_t)y * zw);
+    int ox = tx + x - rx, oy = ty + y - ry;
+    if (ox < 0 || oy < 0 || ox >= rw || oy >= rh) continue;
+    int32_t v[3];
+    if (t.C == 3) {
+      int32_t Y = pl[e], Cb = pl[np + e], Cr = pl[2 * np + e];
+      int32_t G = Y - ((Cb + Cr) >> 2);
+      v[0] = Cr + G; v[1] = G; v[2] = Cb + G;
+    } else {
+      v[0] = pl[e];
+    }
+    uint8_t* row = out + (int64_t)oy * pitch;
+    for (int c = 0; c < t.C; ++c) {
+      int32_t q = min(max(v[c], 0), maxv);
+      if (t.bits <= 8) row[ox * t.C + c] = (uint8_t)q;
+      else reinterpret_cast<uint16_t*>(row)[ox * t.C + c] = (uint16_t)q;
+    }
+  }
+}
+
+// --------------------------------------------------------------- launches
+int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B,
+                             cudaStream_t s) {
+  int launches = 0;
+  dim3 g0(n_tiles, 64);
+  k_load_pixels<<<g0, 256, 0, s>>>(d_tiles, A);
+  ++launches;
+  const int T = 128;
+  for (int l = 0; l < max_levels; ++l) {
+    int md = level_dim(max_dim, l);
+    dim3 g(3 * n_tiles, ceil_div(md, T));
+    k_fwd_vpass<<<g, T, 0, s>>>(d_tiles, l, A, B);
+    k_fwd_hpass<<<g, T, 0, s>>>(d_tiles, l, B, A);
+    launches += 2;
+  }
+  return launches;
+}
+
+int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t n_blocks, const int32_t* planes, int32_t* coef,
+                       cudaStream_t s) {
+  k_pack_blocks<<<(unsigned)n_blocks, 256, 0, s>>>(d_tiles, d_blocks, planes, coef);
+  return 1;
+}
+
+int launch_plan_blocks(const TileDev* d_tiles, int n_tiles, int min_level, BlockDev* d_blocks, cudaStream_t s) {
+  k_plan_blocks<<<ceil_div(n_tiles, 128), 128, 0, s>>>(d_tiles, n_tiles, min_level, d_blocks);
+  return 1;
+}
+
+int launch_quantise_planes(const TileDev* d_tiles, int n_tiles, const int32_t* planes, int32_t* out, cudaStream_t s) {
+  k_quantise_planes<<<dim3(n_tiles, 64), 256, 0, s>>>(d_tiles, planes, out);
+  return 1;
+}
+
+int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int32_t* A, int32_t* B,
+                             cudaStream_t s) {
+  int launches = 0;
+  const int T = 128;
+  for (int l = max_levels - 1; l >= z; --l) {
+    int md = level_dim(max_dim, l);
+    dim3 g(3 * n_tiles, ceil_div(md, T));
+    k_inv_hpass<<<g, T, 0, s>>>(d_tiles, l, z, A, B);
+    k_inv_vpass<<<g, T, 0, s>>>(d_tiles, l, z, B, A);
+    launches += 2;
+  }
+  return launches;
+}
+
+int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, void* out, int64_t pitch, int rx, int ry,
+                        int rw, int rh, cudaStream_t s) {
+  k_store_region<<<dim3(n_tiles, 32), 256, 0, s>>>(d_tiles, z, planes, (uint8_t*)out, pitch, rx, ry, rw, rh);
+  return 1;
+}
+
+}  // namespace isx

@@ -1,0 +1,34 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/isx.h declares (no compute call: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    with open(os.path.join(ROOT, "include", "isx.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(isx_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_exports():
+    from paper_2005_08713_gb300 import isx
+    assert declared_entry_points() == sorted(isx.EXPORTS)
+
+
+def test_library_builds_and_exports_every_symbol():
+    from paper_2005_08713_gb300 import _build
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_entry_points():
+        assert hasattr(lib, name), name
+
+
+def test_tile_descriptor_layout_matches_header():
+    from paper_2005_08713_gb300 import isx
+    # int32 x 7, uint8[16], pointer, int64  ->  64 bytes with natural alignment
+    assert ctypes.sizeof(isx.TileDescC) == 64
+    assert isx.TileDescC.pixels.offset == 48 and isx.TileDescC.row_pitch_bytes.offset == 56
