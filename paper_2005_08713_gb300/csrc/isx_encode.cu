@@ -553,15 +553,18 @@ __global__ void __launch_bounds__(kCtaThreads) k_block_emit(const TileDev* __res
 }
 
 // ------------------------------------------------------------- pass 4
-// Stream offsets, tile headers (little endian) and the capacity check.
-__global__ void k_finalize_tiles(const TileDev* __restrict__ tiles, int n_tiles, const int64_t* __restrict__ final_pos,
-                                 const int64_t* __restrict__ item_size, const int64_t* __restrict__ totals, int64_t slot_cap,
-                                 int64_t header_total, int64_t n_blocks, uint8_t* __restrict__ out, int64_t out_cap,
-                                 uint64_t* __restrict__ tile_offsets, int* __restrict__ status) {
+// One CTA per tile: its stream offset, its header (little endian) and its
+// blocks copied from their slots into the contiguous output.  Every output
+// byte of a tile is written by that tile's CTA only.
+__global__ void __launch_bounds__(256) k_assemble_tiles(const TileDev* tiles, int n_tiles, const int64_t* final_pos,
+                                                       const int64_t* item_size, const int64_t* slot_off, const int64_t* totals,
+                                                       int64_t slot_cap, int64_t header_total, const uint8_t* slots, uint8_t* out,
+                                                       int64_t out_cap, uint64_t* tile_offsets, int* status) {
   const int ti = blockIdx.x;
   const TileDev& t = tiles[ti];
-  const bool scratch_ok = totals[0] <= slot_cap;
-  const int64_t total = scratch_ok ? totals[1] : totals[0] + header_total;
+  const int64_t tot_slots = totals[0], tot_stream = totals[1];
+  const bool scratch_ok = tot_slots <= slot_cap;
+  const int64_t total = scratch_ok ? tot_stream : tot_slots + header_total;
   if (ti == n_tiles - 1 && threadIdx.x == 0) {
     tile_offsets[n_tiles] = (uint64_t)total;
     if (!scratch_ok || total > out_cap) set_status(status, kStCapacity);
@@ -581,24 +584,17 @@ __global__ void k_finalize_tiles(const TileDev* __restrict__ tiles, int n_tiles,
   }
   for (int j = threadIdx.x; j < t.nb; j += blockDim.x) {
     const int64_t bi = t.block_base + j;
-    const int64_t end = final_pos[bi] + item_size[bi] - (toff + hdr);   // first item includes the header
+    const int64_t end = final_pos[bi] + item_size[bi] - (toff + hdr);   // the first item includes the header
     for (int k = 0; k < 4; ++k) o[32 + 4 * j + k] = (uint8_t)((uint64_t)end >> (8 * k));
   }
-}
-
-__global__ void __launch_bounds__(256) k_copy_blocks(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
-                                                    const int64_t* __restrict__ slot_off, const int64_t* __restrict__ final_pos,
-                                                    const int64_t* __restrict__ item_size, const int64_t* __restrict__ totals,
-                                                    int64_t slot_cap, const uint8_t* __restrict__ slots, uint8_t* __restrict__ out,
-                                                    int64_t out_cap) {
-  if (totals[0] > slot_cap || totals[1] > out_cap) return;
-  const int64_t bi = blockIdx.x;
-  const TileDev& t = tiles[blocks[bi].tile];
-  const int64_t extra = bi == t.block_base ? 32 + 4 * (int64_t)t.nb : 0;
-  const int64_t size = item_size[bi] - extra;
-  const uint8_t* src = slots + slot_off[bi];
-  uint8_t* dst = out + final_pos[bi] + extra;
-  for (int64_t k = threadIdx.x; k < size; k += blockDim.x) dst[k] = src[k];
+  for (int j = 0; j < t.nb; ++j) {
+    const int64_t bi = t.block_base + j;
+    const int64_t extra = j == 0 ? hdr : 0;
+    const int64_t size = item_size[bi] - extra;
+    const uint8_t* src = slots + slot_off[bi];
+    uint8_t* dst = out + final_pos[bi] + extra;
+    for (int64_t k = threadIdx.x; k < size; k += blockDim.x) dst[k] = src[k];
+  }
 }
 
 int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T) {
@@ -622,11 +618,9 @@ int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T)
 }
 
 int launch_encode_finalize(const EncodeBuffers& eb, int64_t header_total, cudaStream_t s) {
-  k_finalize_tiles<<<eb.n_tiles, 256, 0, s>>>(eb.tiles, eb.n_tiles, eb.final_pos, eb.exact_size, eb.totals, eb.slot_capacity,
-                                              header_total, eb.n_blocks, eb.out, eb.out_capacity, eb.tile_offsets, eb.status);
-  k_copy_blocks<<<(unsigned)eb.n_blocks, 256, 0, s>>>(eb.tiles, eb.blocks, eb.slot_off, eb.final_pos, eb.exact_size, eb.totals,
-                                                      eb.slot_capacity, eb.slots, eb.out, eb.out_capacity);
-  return 2;
+  k_assemble_tiles<<<eb.n_tiles, 256, 0, s>>>(eb.tiles, eb.n_tiles, eb.final_pos, eb.exact_size, eb.slot_off, eb.totals, eb.slot_capacity,
+                                              header_total, eb.slots, eb.out, eb.out_capacity, eb.tile_offsets, eb.status);
+  return 1;
 }
 
 void encode_set_attributes() {

@@ -262,3 +262,13 @@ def test_host_buffer_entry_points(codec, orc, synth):
         d = orc.decode_tile(out[offs[k]:offs[k + 1]].tobytes(), 0)
         ref[t.y0:t.y0 + d.shape[0], t.x0:t.x0 + d.shape[1]] = d
     assert np.array_equal(res, ref)
+
+
+def test_repeated_encodes_are_identical(codec, orc, synth):
+    """Intermittent races show up as run-to-run differences: encode one batch
+    several times and require the oracle's bytes every time."""
+    imgs, origins = slide_tiles(synth, 40, 5)
+    refs = orc.encode_tiles_mt(imgs, [orc.tile_struct(a.shape[1], a.shape[0], 3, 8, 8, CONFIG3_Q) for a in imgs], 8)
+    for rep in range(6):
+        streams, _, _, _ = gpu_encode(codec, imgs, 8, 8, CONFIG3_Q, origins=[(i * 256, 0) for i in range(len(imgs))])
+        assert_streams_equal(streams, refs, f"repeat {rep}")
