@@ -71,6 +71,8 @@ struct isx_ctx {
   size_t h_tiles_cap = 0;
   int64_t* h_index = nullptr;      // pinned staging for decode tile indices
   size_t h_index_cap = 0;
+  int32_t* h_task = nullptr;       // pinned staging: tiles taking the fused shared-memory path
+  size_t h_task_cap = 0;
   cudaEvent_t staging_free = nullptr;
   int* d_status = nullptr;
   uint8_t* d_io = nullptr;         // device staging of the host-buffer calls
@@ -134,6 +136,13 @@ isx_status ensure_staging(isx_ctx* ctx, size_t n_tiles) {
     ISX_CUDA(cudaMallocHost(&ctx->h_tiles, cap * sizeof(TileDev)));
     ctx->h_tiles_cap = cap;
   }
+  if (n_tiles > ctx->h_task_cap) {
+    if (ctx->h_task) cudaFreeHost(ctx->h_task);
+    ctx->h_task = nullptr;
+    size_t cap = std::max<size_t>(n_tiles, 1024);
+    ISX_CUDA(cudaMallocHost(&ctx->h_task, cap * sizeof(int32_t)));
+    ctx->h_task_cap = cap;
+  }
   if (n_tiles > ctx->h_index_cap) {
     if (ctx->h_index) cudaFreeHost(ctx->h_index);
     ctx->h_index = nullptr;
@@ -179,11 +188,12 @@ void fill_tiledev(TileDev& d, const isx_tile_desc& t) {
 }
 
 struct EncodePlan {
-  int64_t n_blocks = 0, coef_total = 0, plane_total = 0, header_total = 0;
+  int64_t n_blocks = 0, coef_bytes = 0, plane_total = 0, header_total = 0;
   int max_levels = 0, max_dim = 1;
+  int n_fused = 0, max_plane_bytes = 0;
 };
 
-isx_status plan_encode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n, bool need_pixels, EncodePlan& P) {
+isx_status plan_encode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n, bool need_pixels, bool allow_fused, EncodePlan& P) {
   isx_status st = ensure_staging(ctx, (size_t)n);
   if (st != ISX_OK) return st;
   for (int32_t i = 0; i < n; ++i) {
@@ -198,11 +208,17 @@ isx_status plan_encode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n, bool
     fill_tiledev(d, t);
     d.nb = (int32_t)nb;
     d.block_base = P.n_blocks;
-    d.coef_base = P.coef_total;
-    d.plane_base = P.plane_total;
+    d.coef_base = P.coef_bytes;
+    d.fused = allow_fused && fused_tile(t.width, t.height, t.bits) ? 1 : 0;
+    d.plane_base = d.fused ? 0 : P.plane_total;
+    if (d.fused) {
+      ctx->h_task[P.n_fused++] = i;
+      P.max_plane_bytes = std::max(P.max_plane_bytes, t.width * t.height * 2);
+    } else {
+      P.plane_total += (int64_t)t.channels * t.width * t.height;
+    }
     P.n_blocks += nb;
-    P.coef_total += nc;
-    P.plane_total += (int64_t)t.channels * t.width * t.height;
+    P.coef_bytes += nc * (t.bits <= 12 ? 2 : 4);
     P.header_total += 32 + 4 * nb;
     P.max_levels = std::max(P.max_levels, t.levels);
     P.max_dim = std::max(P.max_dim, std::max(t.width, t.height));
@@ -231,6 +247,7 @@ isx_status isx_create(isx_ctx** out, int device, size_t hbm_budget_bytes) {
   }
   encode_set_attributes();
   decode_set_attributes();
+  transform_set_attributes();
   *out = ctx;
   return ISX_OK;
 }
@@ -244,6 +261,7 @@ void isx_destroy(isx_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_tiles) cudaFreeHost(ctx->h_tiles);
   if (ctx->h_index) cudaFreeHost(ctx->h_index);
+  if (ctx->h_task) cudaFreeHost(ctx->h_task);
   if (ctx->staging_free) cudaEventDestroy(ctx->staging_free);
   for (cudaEvent_t e : ctx->timer.pool) cudaEventDestroy(e);
   delete ctx;
@@ -303,7 +321,7 @@ isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, in
   cudaStream_t s = (cudaStream_t)stream;
   ISX_CUDA(cudaSetDevice(ctx->device));
   EncodePlan P;
-  isx_status st = plan_encode(ctx, tiles, n_tiles, true, P);
+  isx_status st = plan_encode(ctx, tiles, n_tiles, true, false, P);
   if (st != ISX_OK) return st;
   Carve cv;
   size_t o_tiles = cv.take(sizeof(TileDev) * n_tiles);
@@ -331,17 +349,18 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   cudaStream_t s = (cudaStream_t)stream;
   ISX_CUDA(cudaSetDevice(ctx->device));
   EncodePlan P;
-  isx_status st = plan_encode(ctx, tiles, n_tiles, true, P);
+  isx_status st = plan_encode(ctx, tiles, n_tiles, true, true, P);
   if (st != ISX_OK) return st;
   const int64_t NB = P.n_blocks;
   const int64_t n_part = NB / 2048 + 2;
   const int64_t slot_cap = (int64_t)out_capacity + 32 * NB + 4096;
   Carve cv;
   size_t o_tiles = cv.take(sizeof(TileDev) * n_tiles);
+  size_t o_task = cv.take(sizeof(int32_t) * (size_t)std::max(P.n_fused, 1));
   size_t o_blocks = cv.take(sizeof(BlockDev) * NB);
   size_t o_A = cv.take(4 * (size_t)P.plane_total);
   size_t o_B = cv.take(4 * (size_t)P.plane_total);
-  size_t o_coef = cv.take(4 * (size_t)P.coef_total);
+  size_t o_coef = cv.take((size_t)P.coef_bytes);
   size_t o_stats = cv.take(sizeof(BlockStats) * NB);
   size_t o_codes = cv.take(sizeof(BlockCode) * NB);
   size_t o_ss = cv.take(8 * NB), o_so = cv.take(8 * NB), o_es = cv.take(8 * NB), o_fp = cv.take(8 * NB);
@@ -351,20 +370,26 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   if (st != ISX_OK) return st;
   uint8_t* ar = ctx->arena;
   TileDev* d_tiles = (TileDev*)(ar + o_tiles);
+  int32_t* d_task = (int32_t*)(ar + o_task);
   ISX_CUDA(cudaMemcpyAsync(d_tiles, ctx->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
+  if (P.n_fused) ISX_CUDA(cudaMemcpyAsync(d_task, ctx->h_task, sizeof(int32_t) * P.n_fused, cudaMemcpyHostToDevice, s));
   ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
   BlockDev* d_blocks = (BlockDev*)(ar + o_blocks);
   int32_t* A = (int32_t*)(ar + o_A);
   int32_t* B = (int32_t*)(ar + o_B);
-  int32_t* coef = (int32_t*)(ar + o_coef);
+  uint8_t* coef = ar + o_coef;
   StageTimer& T = ctx->timer;
   if (T.on && !T.pending.empty()) T.collect();
   T.mark("encode.plan", s);
   int L = launch_plan_blocks(d_tiles, n_tiles, 0, d_blocks, s);
   T.mark("encode.transform", s);
-  L += launch_forward_transform(d_tiles, n_tiles, P.max_levels, P.max_dim, A, B, s);
-  T.mark("encode.pack", s);
-  L += launch_pack_blocks(d_tiles, d_blocks, NB, A, coef, s);
+  L += launch_fused_forward(d_tiles, d_task, P.n_fused, P.max_plane_bytes, d_blocks, coef, s);
+  if (P.n_fused < n_tiles) {
+    T.mark("encode.transform_global", s);
+    L += launch_forward_transform(d_tiles, n_tiles, P.max_levels, P.max_dim, A, B, s);
+    T.mark("encode.pack", s);
+    L += launch_pack_blocks(d_tiles, d_blocks, NB, A, coef, s);
+  }
   EncodeBuffers eb;
   eb.tiles = d_tiles; eb.n_tiles = n_tiles; eb.blocks = d_blocks; eb.n_blocks = NB; eb.coef = coef;
   eb.stats = (BlockStats*)(ar + o_stats);
@@ -398,8 +423,8 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   const int z = level;
   int C = -1, bits = -1;
   int32_t nsel = 0;
-  int64_t n_blocks = 0, plane_total = 0;
-  int max_levels = 0, max_dim = 1;
+  int64_t n_blocks = 0, plane_total = 0, sym_cap = 0, max_items = 0;
+  int max_levels = 0, max_dim = 1, n_fused = 0, max_plane_bytes = 0;
   for (int32_t i = 0; i < n_tiles; ++i) {
     const isx_tile_desc& t = tiles[i];
     std::string why;
@@ -413,12 +438,20 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
       return fail(ctx, ISX_ERR_ARG, "tiles of one region must share channels and sample size");
     int64_t nb, nc;
     tile_counts(t, z, &nb, &nc);
+    // symbols of every kept plane: at most (1 + magnitude bits) planes of p*w*h/8 bytes each, plus padding
+    sym_cap += (int64_t)(t.bits <= 12 ? 16 : kMaxD) * (nc / 8) + 16 * kMaxD * nb;
+    max_items += (int64_t)(t.bits <= 12 ? 16 : kMaxD) * nb;
     TileDev& d = ctx->h_tiles[nsel];
     fill_tiledev(d, t);
     d.nb = (int32_t)nb;
     d.block_base = n_blocks;
     d.plane_base = plane_total;
     d.coef_base = 0;
+    d.fused = fused_tile(zw, zh, t.bits) ? 1 : 0;
+    if (d.fused) {
+      ctx->h_task[n_fused++] = nsel;
+      max_plane_bytes = std::max(max_plane_bytes, zw * zh * 2);
+    }
     ctx->h_index[nsel] = i;
     ++nsel;
     n_blocks += nb;
@@ -432,8 +465,13 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   Carve cv;
   size_t o_tiles = cv.take(sizeof(TileDev) * nsel);
   size_t o_idx = cv.take(8 * (size_t)nsel);
+  size_t o_task = cv.take(4 * (size_t)std::max(n_fused, 1));
   size_t o_blocks = cv.take(sizeof(BlockDev) * n_blocks);
   size_t o_bb = cv.take(8 * n_blocks), o_bl = cv.take(4 * n_blocks);
+  size_t o_info = cv.take(sizeof(DecInfo) * n_blocks), o_sb = cv.take(8 * n_blocks), o_so = cv.take(8 * n_blocks);
+  size_t o_part = cv.take(8 * (n_blocks / 2048 + 2)), o_tot = cv.take(64);
+  size_t o_tab = cv.take(dec_table_bytes() * n_blocks), o_bucket = cv.take(8 * 2 * 512), o_items = cv.take(8 * (size_t)max_items);
+  size_t o_sym = cv.take((size_t)sym_cap + 64);
   size_t o_A = cv.take(4 * (size_t)plane_total), o_B = cv.take(4 * (size_t)plane_total);
   st = ensure_arena(ctx, cv.used);
   if (st != ISX_OK) return st;
@@ -442,6 +480,8 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   int64_t* d_idx = (int64_t*)(ar + o_idx);
   ISX_CUDA(cudaMemcpyAsync(d_tiles, ctx->h_tiles, sizeof(TileDev) * nsel, cudaMemcpyHostToDevice, s));
   ISX_CUDA(cudaMemcpyAsync(d_idx, ctx->h_index, 8 * (size_t)nsel, cudaMemcpyHostToDevice, s));
+  int32_t* d_task = (int32_t*)(ar + o_task);
+  if (n_fused) ISX_CUDA(cudaMemcpyAsync(d_task, ctx->h_task, 4 * (size_t)n_fused, cudaMemcpyHostToDevice, s));
   ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
   DecodeBuffers db;
   db.tiles = d_tiles; db.n_tiles = nsel; db.tile_index = d_idx;
@@ -449,11 +489,19 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   db.blocks = (BlockDev*)(ar + o_blocks); db.block_byte = (int64_t*)(ar + o_bb); db.block_len = (int32_t*)(ar + o_bl);
   db.n_blocks = n_blocks; db.z = z; db.drop = drop_lsb_planes;
   db.planes = (int32_t*)(ar + o_A); db.status = ctx->d_status;
+  db.info = (DecInfo*)(ar + o_info); db.sym_bytes = (int64_t*)(ar + o_sb); db.sym_off = (int64_t*)(ar + o_so);
+  db.scan_part = (int64_t*)(ar + o_part); db.totals = (int64_t*)(ar + o_tot);
+  db.sym = ar + o_sym; db.sym_cap = sym_cap;
+  db.tables = ar + o_tab; db.bucket = (int64_t*)(ar + o_bucket); db.items = (int64_t*)(ar + o_items); db.max_items = max_items;
   StageTimer& T = ctx->timer;
   if (T.on && !T.pending.empty()) T.collect();
   int L = launch_decode_blocks(db, s, &T);
   T.mark("decode.inverse_transform", s);
-  L += launch_inverse_transform(d_tiles, nsel, max_levels, z, max_dim, (int32_t*)(ar + o_A), (int32_t*)(ar + o_B), s);
+  L += launch_fused_inverse(d_tiles, d_task, n_fused, max_plane_bytes, z, (int32_t*)(ar + o_A), s);
+  if (n_fused < nsel) {
+    T.mark("decode.inverse_global", s);
+    L += launch_inverse_transform(d_tiles, nsel, max_levels, z, max_dim, (int32_t*)(ar + o_A), (int32_t*)(ar + o_B), s);
+  }
   T.mark("decode.store", s);
   L += launch_store_region(d_tiles, nsel, z, (int32_t*)(ar + o_A), d_out, out_pitch_bytes, rx, ry, rw, rh, s);
   T.mark(nullptr, s);

@@ -12,8 +12,7 @@
 
 namespace isx {
 
-constexpr int kTabBits = 10;
-constexpr int kSymBytes = 96 * 1024;   // symbol planes per pass, shared memory
+constexpr int kTabBits = 9;
 
 // Index of the ki-th (0-based) set bit of a 3-bit type mask.
 __device__ inline int nth_type(uint32_t km, int ki) {
@@ -88,36 +87,50 @@ __global__ void k_decode_plan(const TileDev* __restrict__ tiles, int n_tiles, co
   if (!ok) set_status(status, kStCorrupt);
 }
 
-// MSB-first bit reader over a block's bytes (reads past the end give 0).
+// MSB-first bit reader over a block's bytes (bytes outside the block read
+// as 0).  It always loads aligned 32-bit words; only a word that crosses
+// the block's first or last byte is assembled byte by byte.
 struct BitIn {
   const uint8_t* p;
   int64_t nbytes;
-  int64_t next;    // next byte to load
+  int64_t wbyte;   // offset of the next word to load, relative to p (aligned in memory)
   uint64_t buf;    // left aligned
   int nbuf;
-  int64_t pos;     // bits consumed from the block start
-  __device__ void seek(int64_t bitpos) {
-    next = bitpos >> 3;
-    buf = 0;
-    nbuf = 0;
-    pos = next * 8;
-    refill();
-    skip((int)(bitpos & 7));
-  }
-  __device__ void refill() {
-    while (nbuf <= 56) {
-      uint64_t b = next < nbytes ? p[next] : 0;
-      ++next;
-      buf |= b << (56 - nbuf);
-      nbuf += 8;
+  int64_t pos;     // bit position of the next unread bit, relative to p
+  __device__ uint32_t load_word() {
+    uint32_t w;
+    if (wbyte >= 0 && wbyte + 4 <= nbytes) {
+      w = __byte_perm(*reinterpret_cast<const uint32_t*>(p + wbyte), 0, 0x0123);
+    } else {
+      w = 0;
+      for (int k = 0; k < 4; ++k) {
+        const int64_t o = wbyte + k;
+        w = (w << 8) | (uint32_t)(o >= 0 && o < nbytes ? p[o] : 0);
+      }
     }
+    wbyte += 4;
+    return w;
+  }
+  __device__ void seek(int64_t bitpos) {
+    const int64_t byte = bitpos >> 3;
+    const int mis = (int)(reinterpret_cast<uintptr_t>(p + byte) & 3);
+    wbyte = byte - mis;
+    buf = (uint64_t)load_word() << 32;
+    buf |= load_word();
+    const int drop = mis * 8 + (int)(bitpos & 7);
+    buf <<= drop;
+    nbuf = 64 - drop;
+    pos = bitpos;
   }
   __device__ uint32_t peek(int n) const { return n ? (uint32_t)(buf >> (64 - n)) : 0u; }
-  __device__ void skip(int n) {
+  __device__ void skip(int n) {   // n <= 32
     buf <<= n;
     nbuf -= n;
     pos += n;
-    if (nbuf < 32) refill();
+    if (nbuf <= 32) {
+      buf |= (uint64_t)load_word() << (32 - nbuf);
+      nbuf += 32;
+    }
   }
   __device__ uint32_t get(int n) {
     uint32_t v = peek(n);
@@ -126,237 +139,357 @@ struct BitIn {
   }
 };
 
-struct DecShared {
-  uint16_t tab[1 << kTabBits];     // (len << 8) | sym, or 0x8000 | node for longer codes
-  uint16_t kid[512][2];
-  int16_t sym[512];                // leaf symbol or -1
-  uint32_t code[512];
-  uint8_t dep[512];
-  uint32_t seglen[32];
-  int64_t segpos[32];
-  uint32_t removed[3];
-  int nnodes, d, czr, wbits, ok, keep;
-};
-
-__device__ bool parse_block_header(DecShared& S, const uint8_t* bp, int blen, int p) {
-  BitIn in{bp, blen, 0, 0, 0, 0};
-  in.seek(0);
-  const int64_t nbits = (int64_t)blen * 8;
-  int d = (int)in.get(5);
-  if (d < 1) return false;
-  S.d = d;
-  bool any = false;
-  for (int t = 0; t < 3; ++t) S.removed[t] = 0;
-  for (int t = 0; t < 3; ++t)
-    for (int pl = 0; pl < d; ++pl) {
-      uint32_t bit = t < p ? in.get(1) : 1u;
-      if (bit) S.removed[t] |= 1u << pl;
-      else any = true;
-    }
-  if (in.pos > nbits) return false;
-  if (!any) {
-    S.nnodes = 0;
-    return true;
-  }
-  S.czr = (int)in.get(8);
-  S.wbits = (int)in.get(5);
-  int t = (int)in.get(5);
-  if (t < 1 || S.wbits < 1) return false;
-  for (int pl = 0; pl < d; ++pl) S.seglen[pl] = in.get(t);
-  // preorder tree: 0 = internal node, 1 + 8 bits = leaf
-  int stack[34];
-  int filled[34];
-  int sp = 0, nn = 0;
-  for (;;) {
-    if (nn >= 511 || in.pos >= nbits) return false;
-    int v = nn++;
-    uint32_t bit = in.get(1);
-    S.kid[v][0] = S.kid[v][1] = 0;
-    if (sp == 0) {
-      S.code[v] = 0;
-      S.dep[v] = 0;
-    } else {
-      int par = stack[sp - 1];
-      int side = filled[sp - 1]++;
-      S.kid[par][side] = (uint16_t)v;
-      S.code[v] = (S.code[par] << 1) | (uint32_t)side;
-      S.dep[v] = (uint8_t)(S.dep[par] + 1);
-    }
-    if (bit) {
-      S.sym[v] = (int16_t)in.get(8);
-      while (sp > 0 && filled[sp - 1] == 2) --sp;
-      if (sp == 0) break;
-    } else {
-      S.sym[v] = -1;
-      if (sp >= 32) return false;   // codes longer than 32 bits
-      stack[sp] = v;
-      filled[sp] = 0;
-      ++sp;
-    }
-  }
-  S.nnodes = nn;
-  int64_t pos = in.pos;
-  for (int pl = 0; pl < d; ++pl) {
-    S.segpos[pl] = pos;
-    pos += S.seglen[pl];
-  }
-  return pos <= nbits;
+__device__ inline uint32_t kept_mask(const uint32_t* removed, int p, int pl) {
+  uint32_t km = 0;
+  for (int t = 0; t < p; ++t)
+    if (!((removed[t] >> pl) & 1u)) km |= 1u << t;
+  return km;
 }
 
-__global__ void __launch_bounds__(kCtaThreads) k_decode_block(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
-                                                             const uint8_t* __restrict__ stream, const int64_t* __restrict__ bbyte,
-                                                             const int32_t* __restrict__ blen, int z, int drop, int32_t* __restrict__ planes,
-                                                             int* __restrict__ status) {
-  extern __shared__ uint8_t s_sym[];
-  __shared__ DecShared S;
+// Symbol buffer layout of one block: for every decoded plane pl in order,
+// its kept types' symbols (n each, types in order HL, LH, HH), the plane's
+// region rounded up to 16 bytes.
+__device__ inline int64_t plane_region(uint32_t km, int n) { return ((int64_t)__popc(km) * n + 15) & ~15LL; }
+
+// Decode table of one block, built once by k_dec_tables and read by every
+// segment decoder of the block: codes up to kTabBits bits resolve with one
+// lookup, longer ones walk the tree from the node reached after kTabBits bits.
+struct DecTab {
+  uint16_t tab[1 << kTabBits];   // (len << 8) | symbol, or 0x8000 | node
+  uint32_t node[512];            // internal: kid0 | kid1 << 16; leaf: 0x80000000 | symbol
+  int64_t segpos[32];            // bit position of plane segment pl from the block start
+  uint32_t seglen[32];
+  int32_t czr, wbits, nnodes, pad;
+};
+
+// Header pass: one thread per block parses the Fig. 3 header (d, removed
+// mask, C_zr, w, t, seektable, preorder tree), builds the block's decode
+// table and sizes its symbol region.
+__global__ void k_dec_tables(const BlockDev* __restrict__ blocks, int64_t nb, const uint8_t* __restrict__ stream,
+                             const int64_t* __restrict__ bbyte, const int32_t* __restrict__ blen, int drop, DecInfo* __restrict__ info,
+                             DecTab* __restrict__ tabs, int64_t* __restrict__ sym_bytes, int* __restrict__ status) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= nb) return;
+  const BlockDev b = blocks[bi];
+  DecInfo di;
+  di.d = 0; di.keep = 0; di.removed[0] = di.removed[1] = di.removed[2] = ~0u;
+  int64_t bytes = 0;
+  DecTab& T = tabs[bi];
+  T.nnodes = 0;
+  if (b.p > 0) {
+    const int nbytes = blen[bi];
+    const int64_t nbits = (int64_t)nbytes * 8;
+    BitIn in{stream + bbyte[bi], nbytes, 0, 0, 0, 0};
+    in.seek(0);
+    int d = (int)in.get(5);
+    bool any = false;
+    for (int t = 0; t < 3; ++t) {
+      uint32_t r = 0;
+      for (int pl = 0; pl < d; ++pl) {
+        if (t >= b.p || in.get(1)) r |= 1u << pl;
+        else any = true;
+      }
+      di.removed[t] = r;
+    }
+    bool ok = d >= 1 && in.pos <= nbits;
+    if (ok && any) {
+      T.czr = (int)in.get(8);
+      T.wbits = (int)in.get(5);
+      const int t = (int)in.get(5);
+      ok = t >= 1 && T.wbits >= 1;
+      for (int pl = 0; ok && pl < d; ++pl) T.seglen[pl] = in.get(t);
+      // preorder tree: 0 = internal node, 1 + 8 bits = leaf; codes grow as we descend
+      int stack[34], filled[34];
+      uint32_t scode[34];
+      int sp = 0, nn = 0;
+      while (ok) {
+        if (nn >= 511 || in.pos >= nbits) { ok = false; break; }
+        const int v = nn++;
+        uint32_t code = 0;
+        int dep = 0;
+        if (sp > 0) {
+          const int side = filled[sp - 1]++;
+          const int par = stack[sp - 1];
+          if (side == 0) T.node[par] = (uint32_t)v;
+          else T.node[par] |= (uint32_t)v << 16;
+          code = (scode[sp - 1] << 1) | (uint32_t)side;
+          dep = sp;
+        }
+        if (in.get(1)) {
+          const uint32_t sym = in.get(8);
+          T.node[v] = 0x80000000u | sym;
+          if (dep <= kTabBits) {
+            const uint32_t lo = code << (kTabBits - dep), cnt = 1u << (kTabBits - dep);
+            for (uint32_t k = 0; k < cnt; ++k) T.tab[lo + k] = (uint16_t)((dep << 8) | sym);
+          }
+          while (sp > 0 && filled[sp - 1] == 2) --sp;
+          if (sp == 0) break;
+        } else {
+          if (sp >= 32) { ok = false; break; }   // codes longer than 32 bits
+          if (dep == kTabBits) T.tab[code] = (uint16_t)(0x8000 | v);
+          stack[sp] = v;
+          filled[sp] = 0;
+          scode[sp] = code;
+          ++sp;
+        }
+      }
+      if (ok) {
+        int64_t pos = in.pos;
+        for (int pl = 0; pl < d; ++pl) {
+          T.segpos[pl] = pos;
+          pos += T.seglen[pl];
+        }
+        ok = pos <= nbits;
+        T.nnodes = nn;
+      }
+    }
+    if (!ok) {
+      set_status(status, kStCorrupt);
+      d = 0;
+      T.nnodes = 0;
+    }
+    di.d = d;
+    di.keep = d ? max(1, d - drop) : 0;
+    const int n = b.w * b.h / 8;
+    for (int pl = 0; pl < di.keep; ++pl) bytes += plane_region(kept_mask(di.removed, b.p, pl), n);
+  }
+  info[bi] = di;
+  sym_bytes[bi] = bytes;
+}
+
+// Segment items are bucketed by (level, plane) so that a warp decodes 32
+// segments of similar length.
+constexpr int kBuckets = 16 * 32;
+
+__global__ void k_dec_item_count(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
+                                 const DecTab* __restrict__ tabs, int64_t* __restrict__ bucket) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= nb) return;
+  const BlockDev b = blocks[bi];
+  const DecInfo di = info[bi];
+  if (b.p == 0 || di.d == 0 || tabs[bi].nnodes == 0) return;
+  for (int pl = 0; pl < di.keep; ++pl)
+    if (kept_mask(di.removed, b.p, pl)) atomicAdd(reinterpret_cast<unsigned long long*>(&bucket[b.level * 32 + pl]), 1ull);
+}
+
+__global__ void k_dec_item_fill(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
+                                const DecTab* __restrict__ tabs, const int64_t* __restrict__ bucket_off, int64_t* __restrict__ fill,
+                                int64_t* __restrict__ items) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= nb) return;
+  const BlockDev b = blocks[bi];
+  const DecInfo di = info[bi];
+  if (b.p == 0 || di.d == 0 || tabs[bi].nnodes == 0) return;
+  for (int pl = 0; pl < di.keep; ++pl) {
+    if (!kept_mask(di.removed, b.p, pl)) continue;
+    const int k = b.level * 32 + pl;
+    const int64_t pos = bucket_off[k] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&fill[k]), 1ull);
+    items[pos] = (bi << 5) | pl;
+  }
+}
+
+// 16-byte symbol writer of one thread.
+struct SymOut {
+  uint4* dst;          // 16-byte chunks of the plane region
+  uint64_t lo, hi;
+  int c;               // bytes in the pending chunk
+  __device__ void flush() {
+    *dst++ = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+    lo = hi = 0;
+    c = 0;
+  }
+  __device__ void put(uint32_t s) {
+    if (c < 8) lo |= (uint64_t)s << (8 * c);
+    else hi |= (uint64_t)s << (8 * (c - 8));
+    if (++c == 16) flush();
+  }
+  __device__ void zeros(uint32_t cnt) {
+    while (cnt > 0) {
+      if (c == 0 && cnt >= 16) {
+        *dst++ = make_uint4(0, 0, 0, 0);
+        cnt -= 16;
+      } else {
+        uint32_t take = min(cnt, (uint32_t)(16 - c));
+        c += take;
+        cnt -= take;
+        if (c == 16) flush();
+      }
+    }
+  }
+};
+
+// Segment pass: one thread per (block, plane) item decodes that plane
+// segment on its own from its seektable start, expanding zero runs, into
+// the block's symbol region.
+__global__ void __launch_bounds__(256) k_dec_segments(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ items,
+                                                     const int64_t* __restrict__ n_items_p, const uint8_t* __restrict__ stream,
+                                                     const int64_t* __restrict__ bbyte, const int32_t* __restrict__ blen,
+                                                     const DecInfo* __restrict__ info, const DecTab* __restrict__ tabs,
+                                                     const int64_t* __restrict__ sym_off, uint8_t* __restrict__ sym,
+                                                     const int64_t* __restrict__ sym_total, int64_t sym_cap, int* __restrict__ status) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= *n_items_p) return;
+  if (*sym_total > sym_cap) {   // a stream claiming more planes than its bit depth allows
+    if (it == 0) set_status(status, kStCorrupt);
+    return;
+  }
+  const int64_t item = items[it];
+  const int64_t bi = item >> 5;
+  const int pl = (int)(item & 31);
+  const BlockDev b = blocks[bi];
+  const DecInfo di = info[bi];
+  const DecTab* T = tabs + bi;
+  const int n = b.w * b.h / 8;
+  const uint32_t km = kept_mask(di.removed, b.p, pl);
+  int64_t off = sym_off[bi];
+  for (int q = 0; q < pl; ++q) off += plane_region(kept_mask(di.removed, b.p, q), n);
+  const int need = __popc(km) * n;
+  const int nbytes = blen[bi];
+  BitIn in{stream + bbyte[bi], nbytes, 0, 0, 0, 0};
+  const int64_t start = T->segpos[pl];
+  const int64_t limit = start + T->seglen[pl];
+  in.seek(start);
+  SymOut out{reinterpret_cast<uint4*>(sym + off), 0, 0, 0};
+  const int czr = T->czr, wb = T->wbits;
+  int pos = 0;
+  bool bad = false;
+  while (pos < need) {
+    const uint32_t e = __ldg(&T->tab[in.peek(kTabBits)]);
+    int s;
+    if (e & 0x8000u) {
+      uint32_t nd = __ldg(&T->node[e & 0x1ff]);
+      in.skip(kTabBits);
+      int guard = 0;
+      while (!(nd & 0x80000000u)) {
+        const uint32_t kid = in.get(1) ? (nd >> 16) : (nd & 0xffffu);
+        nd = __ldg(&T->node[kid & 0x1ff]);
+        if (++guard > 32) { bad = true; break; }
+      }
+      if (bad) break;
+      s = (int)(nd & 0xff);
+    } else {
+      s = (int)(e & 0xff);
+      in.skip((int)(e >> 8));
+    }
+    if (s == czr) {
+      const uint32_t cnt = in.get(wb);
+      if (cnt == 0) {
+        out.put((uint32_t)s);
+        ++pos;
+      } else {
+        if (pos + (int)cnt > need) { bad = true; break; }
+        out.zeros(cnt);
+        pos += (int)cnt;
+      }
+    } else {
+      out.put((uint32_t)s);
+      ++pos;
+    }
+    if (in.pos > limit) { bad = true; break; }
+  }
+  if (out.c) out.flush();
+  if (bad || in.pos != limit) set_status(status, kStCorrupt);
+}
+
+// Rebuild pass: per block, every area's 8 coefficients from the decoded
+// planes (sign plane, then magnitude bits d-2 .. 0), dequantised at the bin
+// midpoint, stored into the level-z Mallat plane (padding cropped).
+__global__ void __launch_bounds__(256) k_dec_rebuild(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
+                                                    const DecInfo* __restrict__ info, const int64_t* __restrict__ sym_off,
+                                                    const uint8_t* __restrict__ sym, const int64_t* __restrict__ sym_total,
+                                                    int64_t sym_cap, int z, int32_t* __restrict__ planes) {
+  __shared__ int64_t s_poff[32];
+  if (*sym_total > sym_cap) return;
+  __shared__ uint32_t s_km[32];
   const BlockDev b = blocks[blockIdx.x];
-  if (b.p == 0) return;   // unreadable tile (status already set)
+  const DecInfo di = info[blockIdx.x];
+  if (b.p == 0 || di.d == 0) return;
   const TileDev& t = tiles[b.tile];
-  const int tid = threadIdx.x;
-  const uint8_t* bp = stream + bbyte[blockIdx.x];
-  const int nbytes = blen[blockIdx.x];
   const int n = b.w * b.h / 8, na = b.p * n;
-  if (tid == 0) {
-    S.ok = parse_block_header(S, bp, nbytes, b.p) ? 1 : 0;
-    if (!S.ok) set_status(status, kStCorrupt);
-    S.keep = S.ok ? max(1, S.d - drop) : 0;
+  if (threadIdx.x == 0) {
+    int64_t off = sym_off[blockIdx.x];
+    for (int pl = 0; pl < di.keep; ++pl) {
+      s_km[pl] = kept_mask(di.removed, b.p, pl);
+      s_poff[pl] = off;
+      off += plane_region(s_km[pl], n);
+    }
   }
   __syncthreads();
-  if (!S.ok) return;
-  const int d = S.d;
-  const int keep = S.keep;
-  // plane geometry of the destination
   const int zw = level_dim(t.w, z), zh = level_dim(t.h, z);
   int32_t* plane = planes + t.plane_base + (int64_t)b.c * zw * zh;
   const int q = qlog2_of(t, b.level);
   const int32_t delta = 1 << q;
-  if (S.nnodes > 0) {
-    // decode table: codes up to kTabBits bits resolve in one lookup
-    for (int v = tid; v < S.nnodes; v += blockDim.x) {
-      int dep = S.dep[v];
-      if (S.sym[v] >= 0 && dep <= kTabBits) {
-        uint32_t lo = S.code[v] << (kTabBits - dep), cnt = 1u << (kTabBits - dep);
-        for (uint32_t k = 0; k < cnt; ++k) S.tab[lo + k] = (uint16_t)((dep << 8) | S.sym[v]);
-      } else if (S.sym[v] < 0 && dep == kTabBits) {
-        S.tab[S.code[v]] = (uint16_t)(0x8000 | v);
+  const int d = di.d;
+  for (int a = threadIdx.x; a < na; a += blockDim.x) {
+    const int type = a / n, k = a - type * n;
+    uint32_t mag[8], neg = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) mag[e] = 0;
+    for (int pl = 0; pl < di.keep; ++pl) {
+      const uint32_t km = s_km[pl];
+      if (!((km >> type) & 1u)) continue;
+      const int ki = __popc(km & ((1u << type) - 1u));
+      const uint32_t s = sym[s_poff[pl] + (int64_t)ki * n + k];
+      if (!s) continue;
+      if (pl == 0) {
+        neg = s;
+      } else {
+        const int sh = d - 1 - pl;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) mag[e] |= ((s >> e) & 1u) << sh;
       }
     }
-  }
-  const int planes_per_pass = max(1, kSymBytes / na);
-  const bool single = planes_per_pass >= keep;
-  for (int pb = 0; pb < keep; pb += planes_per_pass) {
-    const int pe = min(keep, pb + planes_per_pass);
-    for (int k = tid; k < (pe - pb) * na; k += blockDim.x) s_sym[k] = 0;
-    __syncthreads();
-    // one thread per plane segment
-    if (tid < pe - pb && S.nnodes > 0) {
-      const int pl = pb + tid;
-      uint32_t km = 0;
-      for (int ty = 0; ty < b.p; ++ty)
-        if (!((S.removed[ty] >> pl) & 1u)) km |= 1u << ty;
-      if (km) {
-        const int need = __popc(km) * n;
-        BitIn in{bp, nbytes, 0, 0, 0, 0};
-        in.seek(S.segpos[pl]);
-        const int64_t limit = S.segpos[pl] + S.seglen[pl];
-        uint8_t* dst = s_sym + (int64_t)(pl - pb) * na;
-        int pos = 0;
-        bool bad = false;
-        while (pos < need) {
-          uint32_t e = S.tab[in.peek(kTabBits)];
-          int sym;
-          if (e & 0x8000u) {
-            int v = e & 0x1ff;
-            in.skip(kTabBits);
-            int guard = 0;
-            while (S.sym[v] < 0) {
-              v = S.kid[v][in.get(1)];
-              if (++guard > 32) { bad = true; break; }
-            }
-            if (bad) break;
-            sym = S.sym[v];
-          } else {
-            sym = e & 0xff;
-            in.skip((int)(e >> 8));
-          }
-          if (sym == S.czr) {
-            uint32_t cnt = in.get(S.wbits);
-            if (cnt == 0) {
-              int ki = pos / n;
-              int ty = nth_type(km, ki);
-              dst[ty * n + pos - ki * n] = (uint8_t)sym;
-              ++pos;
-            } else {
-              pos += (int)cnt;   // zeros: the buffer is already clear
-              if (pos > need) { bad = true; break; }
-            }
-          } else {
-            int ki = pos / n;
-            int ty = nth_type(km, ki);
-            dst[ty * n + pos - ki * n] = (uint8_t)sym;
-            ++pos;
-          }
-          if (in.pos > limit) { bad = true; break; }
-        }
-        if (bad || in.pos != limit) set_status(status, kStCorrupt);
-      }
+    int i, j;
+    area_ij(k, b.w, &i, &j);
+    int sx, sy, sw, sh;
+    subband_rect(t.w, t.h, t.L, b.level, type, &sx, &sy, &sw, &sh);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int yy = kCell * b.by + i + (e >> 2), xx = kCell * b.bx + j + (e & 3);
+      if (yy >= sh || xx >= sw) continue;
+      const int32_t m = (int32_t)mag[e];
+      const int32_t v = m == 0 ? 0 : m * delta + (delta >> 1);
+      plane[(int64_t)(sy + yy) * zw + sx + xx] = ((neg >> e) & 1u) ? -v : v;
     }
-    __syncthreads();
-    // rebuild the coefficients of each area
-    for (int a = tid; a < na; a += blockDim.x) {
-      const int type = a / n, k = a - type * n;
-      int i, j;
-      area_ij(k, b.w, &i, &j);
-      int sx, sy, sw, sh;
-      subband_rect(t.w, t.h, t.L, b.level, type, &sx, &sy, &sw, &sh);
-      uint32_t mag[8], neg[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) { mag[e] = 0; neg[e] = 0; }
-      for (int pl = pb; pl < pe; ++pl) {
-        uint32_t s = s_sym[(int64_t)(pl - pb) * na + a];
-        if (!s) continue;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          uint32_t bit = (s >> e) & 1u;
-          if (pl == 0) neg[e] = bit;
-          else mag[e] |= bit << (d - 1 - pl);
-        }
-      }
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        int yy = kCell * b.by + i + (e >> 2), xx = kCell * b.bx + j + (e & 3);
-        if (yy >= sh || xx >= sw) continue;
-        int32_t* dst = plane + (int64_t)(sy + yy) * zw + sx + xx;
-        if (!single) {
-          // several passes: accumulate sign (bit 31) and magnitude, convert at the end
-          uint32_t acc = (pb == 0) ? 0u : (uint32_t)*dst;
-          acc |= (neg[e] << 31) | mag[e];
-          if (pe < keep) { *dst = (int32_t)acc; continue; }
-          neg[e] = acc >> 31;
-          mag[e] = acc & 0x7fffffffu;
-        }
-        int32_t m = (int32_t)mag[e];
-        int32_t v = m == 0 ? 0 : m * delta + (delta >> 1);
-        *dst = neg[e] ? -v : v;
-      }
-    }
-    __syncthreads();
   }
 }
 
 int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T) {
+  int L = 0;
   T->mark("decode.plan", s);
   k_decode_plan<<<ceil_div(db.n_tiles, 128), 128, 0, s>>>(db.tiles, db.n_tiles, db.tile_index, db.stream, db.stream_offsets, db.z,
                                                          db.blocks, db.block_byte, db.block_len, db.status);
-  T->mark("decode.blocks", s);
-  if (db.n_blocks > 0)
-    k_decode_block<<<(unsigned)db.n_blocks, kCtaThreads, kSymBytes, s>>>(db.tiles, db.blocks, db.stream, db.block_byte, db.block_len,
-                                                                          db.z, db.drop, db.planes, db.status);
-  return 2;
+  ++L;
+  if (db.n_blocks == 0) return L;
+  const unsigned g = (unsigned)((db.n_blocks + 127) / 128);
+  T->mark("decode.tables", s);
+  k_dec_tables<<<g, 128, 0, s>>>(db.blocks, db.n_blocks, db.stream, db.block_byte, db.block_len, db.drop, db.info,
+                                 reinterpret_cast<DecTab*>(db.tables), db.sym_bytes, db.status);
+  ++L;
+  T->mark("decode.items", s);
+  L += launch_exclusive_scan(db.sym_bytes, db.n_blocks, db.sym_off, db.scan_part, db.totals, s);
+  cudaMemsetAsync(db.bucket, 0, 2 * sizeof(int64_t) * kBuckets, s);
+  k_dec_item_count<<<g, 128, 0, s>>>(db.blocks, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.bucket);
+  L += 1 + launch_exclusive_scan(db.bucket, kBuckets, db.bucket + kBuckets, db.scan_part, db.totals + 1, s);
+  cudaMemsetAsync(db.bucket, 0, sizeof(int64_t) * kBuckets, s);
+  k_dec_item_fill<<<g, 128, 0, s>>>(db.blocks, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.bucket + kBuckets,
+                                    db.bucket, db.items);
+  ++L;
+  T->mark("decode.segments", s);
+  // one thread per item; the item count is read on the device (grid sized by its upper bound)
+  k_dec_segments<<<(unsigned)((db.max_items + 255) / 256), 256, 0, s>>>(
+      db.blocks, db.items, db.totals + 1, db.stream, db.block_byte, db.block_len, db.info, reinterpret_cast<const DecTab*>(db.tables),
+      db.sym_off, db.sym, db.totals, db.sym_cap, db.status);
+  ++L;
+  T->mark("decode.rebuild", s);
+  k_dec_rebuild<<<(unsigned)db.n_blocks, 256, 0, s>>>(db.tiles, db.blocks, db.info, db.sym_off, db.sym, db.totals, db.sym_cap, db.z,
+                                                      db.planes);
+  ++L;
+  return L;
 }
 
-void decode_set_attributes() {
-  cudaFuncSetAttribute(k_decode_block, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymBytes);
-}
+size_t dec_table_bytes() { return sizeof(DecTab); }
+
+void decode_set_attributes() {}
 
 }  // namespace isx

@@ -20,10 +20,30 @@ namespace isx {
 constexpr uint32_t kAllZero = 0x80000000u;
 constexpr int kStageWords = 12288;   // 48 KB output window per CTA
 
-__device__ inline uint32_t area_symbol(const int32_t* __restrict__ cf, int a, int pl, int d) {
-  const int4* p4 = reinterpret_cast<const int4*>(cf + (int64_t)a * 8);
-  const int4 u = p4[0], v = p4[1];
-  const int32_t c[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+// The coefficients of one block: 8 per area in Eq. 2 bit order, int16 or int32.
+struct CoefRef {
+  const uint8_t* base;
+  int is16;
+  __device__ void load(int a, int32_t* c) const {
+    if (is16) {
+      const uint4 u = reinterpret_cast<const uint4*>(base)[a];
+      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        c[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu);
+        c[2 * k + 1] = (int32_t)(int16_t)(w[k] >> 16);
+      }
+    } else {
+      const int4* p4 = reinterpret_cast<const int4*>(base) + 2 * (int64_t)a;
+      const int4 u = p4[0], v = p4[1];
+      c[0] = u.x; c[1] = u.y; c[2] = u.z; c[3] = u.w; c[4] = v.x; c[5] = v.y; c[6] = v.z; c[7] = v.w;
+    }
+  }
+};
+
+__device__ inline uint32_t area_symbol(const CoefRef& cf, int a, int pl, int d) {
+  int32_t c[8];
+  cf.load(a, c);
   uint32_t s = 0;
   if (pl == 0) {
 #pragma unroll
@@ -69,7 +89,7 @@ __device__ inline void record_run(uint32_t L, uint32_t* s_hist, uint32_t* s_runs
   }
 }
 
-__global__ void __launch_bounds__(kCtaThreads) k_block_stats(const BlockDev* __restrict__ blocks, const int32_t* __restrict__ coef,
+__global__ void __launch_bounds__(kCtaThreads) k_block_stats(const BlockDev* __restrict__ blocks, const uint8_t* __restrict__ coef,
                                                             BlockStats* __restrict__ stats) {
   __shared__ uint32_t s_hist[256];
   __shared__ uint32_t s_extra[kMaxW + 1];
@@ -78,7 +98,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_block_stats(const BlockDev* __r
   __shared__ uint32_t s_tmp[33];
   const BlockDev b = blocks[blockIdx.x];
   const int n = b.w * b.h / 8, na = b.p * n;
-  const int32_t* cf = coef + b.coef;
+  const CoefRef cf{coef + b.coef, b.coef16};
   const int tid = threadIdx.x;
   for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
   if (tid <= kMaxW) s_extra[tid] = 0;
@@ -87,11 +107,15 @@ __global__ void __launch_bounds__(kCtaThreads) k_block_stats(const BlockDev* __r
   __syncthreads();
   {
     uint32_t o[3] = {0, 0, 0}, ng[3] = {0, 0, 0};
-    for (int e = tid; e < na * 8; e += blockDim.x) {
-      int t = e / (n * 8);
-      int32_t v = cf[e];
-      o[t] |= (uint32_t)abs(v);
-      ng[t] |= (uint32_t)(v < 0);
+    for (int a = tid; a < na; a += blockDim.x) {
+      const int t = a / n;
+      int32_t c[8];
+      cf.load(a, c);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        o[t] |= (uint32_t)abs(c[e]);
+        ng[t] |= (uint32_t)(c[e] < 0);
+      }
     }
     for (int t = 0; t < 3; ++t) {
       uint32_t ro = __reduce_or_sync(0xffffffffu, o[t]);
@@ -380,7 +404,7 @@ __device__ inline int64_t put_literal(const CodeTab& ct, const Window& win, int6
 
 // One pass over all planes: writes the tokens that fall in the window and
 // records the segment lengths.  All threads of the CTA call it.
-__device__ void emit_planes(const int32_t* __restrict__ cf, int n, int p, int d, const uint32_t* removed, const CodeTab& ct,
+__device__ void emit_planes(const CoefRef& cf, int n, int p, int d, const uint32_t* removed, const CodeTab& ct,
                             const Window& win, int64_t seg_start, uint32_t* s_seglen, uint32_t* s_tmp32, uint64_t* s_tmp64) {
   const int na = p * n;
   const int m = (na + blockDim.x - 1) / blockDim.x;
@@ -445,7 +469,7 @@ __device__ void emit_planes(const int32_t* __restrict__ cf, int n, int p, int d,
 }
 
 __global__ void __launch_bounds__(kCtaThreads) k_block_emit(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
-                                                           const int32_t* __restrict__ coef, const BlockCode* __restrict__ codes,
+                                                           const uint8_t* __restrict__ coef, const BlockCode* __restrict__ codes,
                                                            const int64_t* __restrict__ slot_off, const int64_t* __restrict__ slot_size,
                                                            uint8_t* __restrict__ slots, int64_t slot_cap, const int64_t* __restrict__ totals,
                                                            int64_t* __restrict__ item_size, int* __restrict__ status) {
@@ -495,7 +519,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_block_emit(const TileDev* __res
       for (int k = tid; k < kStageWords; k += blockDim.x) stage[k] = 0;
       __syncthreads();
       const int64_t hdr = hm + 18 + (int64_t)d * t + tree_bits;
-      emit_planes(coef + b.coef, n, p, d, removed, ct, win, hdr, s_seglen, s_tmp32, s_tmp64);
+      emit_planes(CoefRef{coef + b.coef, b.coef16}, n, p, d, removed, ct, win, hdr, s_seglen, s_tmp32, s_tmp64);
       if (wlo > 0) break;
       // first window: fix t (raised only when a segment length needs more bits)
       uint32_t mx = 0;
@@ -601,7 +625,7 @@ int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T)
   int launches = 0;
   const unsigned nb = (unsigned)eb.n_blocks;
   T->mark("encode.stats", s);
-  k_block_stats<<<nb, kCtaThreads, 0, s>>>(eb.blocks, eb.coef, eb.stats);
+  k_block_stats<<<nb, kCtaThreads, 0, s>>>(eb.blocks, (const uint8_t*)eb.coef, eb.stats);
   T->mark("encode.huffman", s);
   k_block_huffman<<<(unsigned)((eb.n_blocks + 63) / 64), 64, 0, s>>>(eb.blocks, eb.stats, eb.codes, eb.slot_size, eb.n_blocks);
   launches += 2;
@@ -609,7 +633,7 @@ int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T)
   launches += launch_exclusive_scan(eb.slot_size, eb.n_blocks, eb.slot_off, eb.scan_part, eb.totals + 0, s);
   const size_t smem = (size_t)kStageWords * 4;
   T->mark("encode.emit", s);
-  k_block_emit<<<nb, kCtaThreads, smem, s>>>(eb.tiles, eb.blocks, eb.coef, eb.codes, eb.slot_off, eb.slot_size, eb.slots,
+  k_block_emit<<<nb, kCtaThreads, smem, s>>>(eb.tiles, eb.blocks, (const uint8_t*)eb.coef, eb.codes, eb.slot_off, eb.slot_size, eb.slots,
                                              eb.slot_capacity, eb.totals, eb.exact_size, eb.status);
   ++launches;
   T->mark("encode.scan", s);

@@ -21,6 +21,7 @@ struct TileDev {
   int32_t w, h, C, bits, L, x0, y0;
   uint8_t q[16];
   int32_t nb;               // number of coefficient blocks
+  int32_t fused;            // 1: transformed by the fused shared-memory kernels
   int64_t block_base;       // index of its first block
   int64_t plane_base;       // element offset of its first Mallat plane
   int64_t coef_base;        // element offset of its first area-ordered block
@@ -31,6 +32,7 @@ struct BlockDev {
   int32_t tile, c, level;   // level 0 = the LL band of the tile
   int32_t by, bx;           // cell position within the subband grid
   int32_t p, w, h;          // types and padded size (multiples of 4)
+  int32_t coef16;           // coefficients stored as int16 (bits <= 12) or int32
   int64_t coef;             // element offset of its coefficients: [type][area][8]
 };
 
@@ -57,13 +59,18 @@ struct BlockCode {
   uint64_t slot_bytes;      // upper bound of the block size (t at its largest)
 };
 
+// Per-block decode information found by the header pass.
+struct DecInfo {
+  int32_t d, keep;           // bit depth, planes decoded (d minus dropped LSB planes, at least 1)
+  uint32_t removed[3];
+};
+
 __host__ __device__ inline int level_dim(int n, int l) {
   for (int i = 0; i < l; ++i) n = (n + 1) >> 1;
   return n;
 }
 __host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
-__host__ __device__ inline int bitlen32(uint32_t v) { return v ? 32 - __builtin_clz(v) : 0; }
 __device__ inline int bitlen_u32(uint32_t v) { return 32 - __clz(v); }
 __device__ inline int bitlen_u64(uint64_t v) { return 64 - __clzll(v); }
 

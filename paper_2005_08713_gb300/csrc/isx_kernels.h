@@ -11,8 +11,14 @@ int launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* p
 int launch_plan_blocks(const TileDev* d_tiles, int n_tiles, int min_level, BlockDev* d_blocks, cudaStream_t s);
 int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B,
                              cudaStream_t s);
-int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t n_blocks, const int32_t* planes, int32_t* coef,
+int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t n_blocks, const int32_t* planes, void* coef,
                        cudaStream_t s);
+int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const BlockDev* d_blocks,
+                         void* coef, cudaStream_t s);
+int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, int z, int32_t* planes,
+                         cudaStream_t s);
+bool fused_tile(int w, int h, int bits);
+void transform_set_attributes();
 int launch_quantise_planes(const TileDev* d_tiles, int n_tiles, const int32_t* planes, int32_t* out, cudaStream_t s);
 int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int32_t* A, int32_t* B,
                              cudaStream_t s);
@@ -25,7 +31,7 @@ struct EncodeBuffers {
   int n_tiles;
   const BlockDev* blocks;
   int64_t n_blocks;
-  const int32_t* coef;
+  const void* coef;          // int16 or int32 per block (BlockDev::coef16)
   BlockStats* stats;
   BlockCode* codes;
   int64_t* slot_size;     // [n_blocks]
@@ -62,8 +68,20 @@ struct DecodeBuffers {
   int64_t n_blocks;
   int z, drop;
   int32_t* planes;
+  DecInfo* info;             // [n_blocks]
+  int64_t* sym_bytes;        // [n_blocks]
+  int64_t* sym_off;          // [n_blocks]
+  int64_t* scan_part;
+  int64_t* totals;           // [2]: symbol buffer bytes, segment items
+  void* tables;              // [n_blocks] decode tables (dec_table_bytes() each)
+  int64_t* bucket;           // [2 * 512] item counts / offsets by (level, plane)
+  int64_t* items;            // [max_items] (block << 5 | plane)
+  int64_t max_items;
+  uint8_t* sym;              // symbol buffer
+  int64_t sym_cap;           // its size: an upper bound from the tiles' bit depths
   int* status;
 };
 int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T);
+size_t dec_table_bytes();
 
 }  // namespace isx

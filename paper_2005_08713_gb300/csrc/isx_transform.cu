@@ -38,7 +38,8 @@ __global__ void k_plan_blocks(const TileDev* __restrict__ tiles, int n_tiles, in
           b.w = pad4(min(kCell, gw - kCell * bx));
           b.h = pad4(min(kCell, gh - kCell * by));
           b.coef = coef;
-          coef += (int64_t)p * b.w * b.h;
+          b.coef16 = t.bits <= 12 ? 1 : 0;
+          coef += (int64_t)p * b.w * b.h * (b.coef16 ? 2 : 4);
           out[idx++] = b;
         }
     }
@@ -111,6 +112,7 @@ int launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* p
 // JPEG 2000 for 3 channels: Y = floor((R+2G+B)/4), Cb = B-G, Cr = R-G.
 __global__ void k_load_pixels(const TileDev* __restrict__ tiles, int32_t* __restrict__ planes) {
   const TileDev& t = tiles[blockIdx.x];
+  if (t.fused) return;
   const int64_t np = (int64_t)t.w * t.h;
   int32_t* out = planes + t.plane_base;
   for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < np; e += (int64_t)gridDim.y * blockDim.x) {
@@ -188,7 +190,7 @@ struct PassGeom {
 };
 
 __device__ inline bool pass_geom(const TileDev& t, int c, int lvl, bool decode_plane, int z, PassGeom* g) {
-  if (c >= t.C || lvl >= t.L || lvl < z) return false;
+  if (c >= t.C || lvl >= t.L || lvl < z || t.fused) return false;
   int pw = decode_plane ? level_dim(t.w, z) : t.w;
   int ph = decode_plane ? level_dim(t.h, z) : t.h;
   g->cw = level_dim(t.w, lvl);
@@ -242,13 +244,13 @@ __global__ void k_inv_vpass(const TileDev* __restrict__ tiles, int lvl, int z, c
 // int32 in Eq. 2 bit order (upper row then lower row, left to right).
 // Positions outside the subband are the zero padding.
 __global__ void __launch_bounds__(256) k_pack_blocks(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
-                                                     const int32_t* __restrict__ planes, int32_t* __restrict__ coef) {
+                                                     const int32_t* __restrict__ planes, void* __restrict__ coef_buf) {
   const BlockDev b = blocks[blockIdx.x];
   const TileDev& t = tiles[b.tile];
+  if (t.fused) return;   // packed by the fused kernel
   const int n = b.w * b.h / 8, na = b.p * n;
   const int q = qlog2_of(t, b.level);
   const int32_t* plane = planes + t.plane_base + (int64_t)b.c * t.w * t.h;
-  int32_t* out = coef + b.coef;
   for (int a = threadIdx.x; a < na; a += blockDim.x) {
     int type = a / n, k = a - type * n;
     int i, j;
@@ -265,9 +267,18 @@ __global__ void __launch_bounds__(256) k_pack_blocks(const TileDev* __restrict__
       m >>= q;
       v[e] = c < 0 ? -m : m;
     }
-    int4* o = reinterpret_cast<int4*>(out + (int64_t)a * 8);
-    o[0] = make_int4(v[0], v[1], v[2], v[3]);
-    o[1] = make_int4(v[4], v[5], v[6], v[7]);
+    if (b.coef16) {
+      uint4 u;
+      u.x = (uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+      u.y = (uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+      u.z = (uint16_t)v[4] | ((uint32_t)(uint16_t)v[5] << 16);
+      u.w = (uint16_t)v[6] | ((uint32_t)(uint16_t)v[7] << 16);
+      reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(coef_buf) + b.coef)[a] = u;
+    } else {
+      int4* o = reinterpret_cast<int4*>(reinterpret_cast<uint8_t*>(coef_buf) + b.coef) + 2 * (int64_t)a;
+      o[0] = make_int4(v[0], v[1], v[2], v[3]);
+      o[1] = make_int4(v[4], v[5], v[6], v[7]);
+    }
   }
 }
 
@@ -326,6 +337,186 @@ __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const i
   }
 }
 
+// ------------------------------------------------- fused shared-memory path
+// Tiles whose channel plane fits in shared memory as int16 (bits <= 12: the
+// worst-case gain of the iterated 5/3 filters keeps every coefficient below
+// 2^15) are transformed by one CTA per (tile, channel), in place on the
+// interleaved layout: after level l the LL samples sit at multiples of 2^l,
+// and the high-pass samples of level l at odd multiples of 2^(l-1).
+constexpr int kSmemPlaneBytes = 160 * 1024;
+constexpr int kFusedThreads = 1024;
+
+__host__ __device__ inline bool tile_uses_smem(int w, int h, int bits) {
+  return bits <= 12 && (int64_t)w * h * 2 <= kSmemPlaneBytes;
+}
+
+// Interleaved position of subband sample (y, x) of `type` at `level`
+// (level 0 = LL_L) relative to a grid whose LL is level `z`.
+__device__ inline void ilv_pos(int L, int level, int type, int y, int x, int z, int* py, int* px) {
+  if (level == 0) {
+    *py = y << (L - z);
+    *px = x << (L - z);
+    return;
+  }
+  const int s = 1 << (level - 1 - z), s2 = s << 1;
+  *py = y * s2 + (type >= 1 ? s : 0);
+  *px = x * s2 + (type != 1 ? s : 0);
+}
+
+// One in-place lifting step along one axis of the grid at stride s:
+// n samples per line, `lines` lines; odd = predict (odd positions) or update
+// (even positions); inverse undoes the step.  Mirror at both ends.
+__device__ inline void lift_step(int16_t* P, int pitch, int n, int lines, int s, bool vertical, bool odd, bool inverse) {
+  const int nt = odd ? n / 2 : (n + 1) / 2;
+  const int total = nt * lines;
+  for (int it = threadIdx.x; it < total; it += blockDim.x) {
+    // consecutive threads walk along a row: across columns (vertical) or along the line (horizontal)
+    const int line = vertical ? it % lines : it / nt;
+    const int k = vertical ? it / lines : it % nt;
+    const int r = odd ? 2 * k + 1 : 2 * k;
+    const int rm = r - 1 >= 0 ? r - 1 : r + 1;
+    const int rp = r + 1 < n ? r + 1 : r - 1;
+    int16_t *c, *a, *b;
+    if (vertical) {
+      c = P + (r * s) * pitch + line * s;
+      a = P + (rm * s) * pitch + line * s;
+      b = P + (rp * s) * pitch + line * s;
+    } else {
+      c = P + (line * s) * pitch + r * s;
+      a = P + (line * s) * pitch + rm * s;
+      b = P + (line * s) * pitch + rp * s;
+    }
+    const int32_t va = *a, vb = *b;
+    int32_t v = *c;
+    if (odd) v = inverse ? v + ((va + vb) >> 1) : v - ((va + vb) >> 1);
+    else v = inverse ? v - ((va + vb + 2) >> 2) : v + ((va + vb + 2) >> 2);
+    *c = (int16_t)v;
+  }
+}
+
+__global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
+                                                                 const BlockDev* __restrict__ blocks, uint8_t* __restrict__ coef) {
+  extern __shared__ int16_t P[];
+  const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
+  const TileDev& t = tiles[tt];
+  if (c >= t.C) return;
+  const int w = t.w, h = t.h, pitch = w;
+  // load + colour transform of channel c
+  for (int e = threadIdx.x; e < w * h; e += blockDim.x) {
+    const int y = e / w, x = e - y * w;
+    const uint8_t* row = t.pixels + (int64_t)y * t.pitch;
+    int32_t v;
+    if (t.C == 3) {
+      const int32_t R = row[3 * x], G = row[3 * x + 1], B = row[3 * x + 2];
+      v = c == 0 ? (R + 2 * G + B) >> 2 : c == 1 ? B - G : R - G;
+    } else {
+      v = t.bits <= 8 ? (int32_t)row[x] : (int32_t)reinterpret_cast<const uint16_t*>(row)[x];
+    }
+    P[y * pitch + x] = (int16_t)v;
+  }
+  __syncthreads();
+  for (int l = 0; l < t.L; ++l) {
+    const int s = 1 << l, cw = level_dim(w, l), ch = level_dim(h, l);
+    if (ch >= 2) {
+      lift_step(P, pitch, ch, cw, s, true, true, false);
+      __syncthreads();
+      lift_step(P, pitch, ch, cw, s, true, false, false);
+      __syncthreads();
+    }
+    if (cw >= 2) {
+      lift_step(P, pitch, cw, ch, s, false, true, false);
+      __syncthreads();
+      lift_step(P, pitch, cw, ch, s, false, false, false);
+      __syncthreads();
+    }
+  }
+  // quantise + area-ordered pack of this channel's blocks
+  const int64_t b0 = t.block_base + (int64_t)c * (t.nb / t.C), b1 = b0 + t.nb / t.C;
+  for (int64_t bi = b0; bi < b1; ++bi) {
+    const BlockDev b = blocks[bi];
+    const int n = b.w * b.h / 8, na = b.p * n;
+    const int q = qlog2_of(t, b.level);
+    uint4* out = reinterpret_cast<uint4*>(coef + b.coef);
+    for (int a = threadIdx.x; a < na; a += blockDim.x) {
+      const int type = a / n, k = a - type * n;
+      int i, j;
+      area_ij(k, b.w, &i, &j);
+      int sx, sy, sw, sh;
+      subband_rect(w, h, t.L, b.level, type, &sx, &sy, &sw, &sh);
+      int16_t v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int yy = kCell * b.by + i + (e >> 2), xx = kCell * b.bx + j + (e & 3);
+        int32_t cval = 0;
+        if (yy < sh && xx < sw) {
+          int py, px;
+          ilv_pos(t.L, b.level, type, yy, xx, 0, &py, &px);
+          cval = P[py * pitch + px];
+        }
+        int32_t m = cval < 0 ? -cval : cval;
+        m >>= q;
+        v[e] = (int16_t)(cval < 0 ? -m : m);
+      }
+      uint4 u;
+      u.x = (uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+      u.y = (uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+      u.z = (uint16_t)v[4] | ((uint32_t)(uint16_t)v[5] << 16);
+      u.w = (uint16_t)v[6] | ((uint32_t)(uint16_t)v[7] << 16);
+      out[a] = u;
+    }
+  }
+}
+
+// Decode side: the level-z Mallat plane (int32, written by the block
+// rebuild) is loaded into the interleaved int16 layout, lifted back from
+// level L to level z and written back row-major as the LL_z image.
+__global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
+                                                                 int z, int32_t* __restrict__ planes) {
+  extern __shared__ int16_t P[];
+  const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
+  const TileDev& t = tiles[tt];
+  if (c >= t.C || t.L <= z) return;
+  const int zw = level_dim(t.w, z), zh = level_dim(t.h, z), pitch = zw;
+  int32_t* g = planes + t.plane_base + (int64_t)c * zw * zh;
+  // Mallat -> interleaved: walk the subbands of levels L .. z+1 and the LL
+  for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
+    const int y = e / zw, x = e - y * zw;
+    // which subband holds Mallat position (x, y) of the level-z region
+    int level = 0, type = 0, sy = y, sx = x;
+    for (int l = z + 1; l <= t.L; ++l) {
+      const int pw = level_dim(t.w, l - 1), ph = level_dim(t.h, l - 1);
+      const int lw = (pw + 1) >> 1, lh = (ph + 1) >> 1;
+      if (x >= lw || y >= lh) {
+        level = l;
+        type = (y < lh) ? 0 : (x < lw ? 1 : 2);
+        sx = x >= lw ? x - lw : x;
+        sy = y >= lh ? y - lh : y;
+        break;
+      }
+    }
+    int py, px;
+    ilv_pos(t.L, level, type, sy, sx, z, &py, &px);
+    P[py * pitch + px] = (int16_t)g[e];
+  }
+  __syncthreads();
+  for (int l = t.L - 1; l >= z; --l) {
+    const int s = 1 << (l - z), cw = level_dim(t.w, l), ch = level_dim(t.h, l);
+    if (cw >= 2) {
+      lift_step(P, pitch, cw, ch, s, false, false, true);
+      __syncthreads();
+      lift_step(P, pitch, cw, ch, s, false, true, true);
+      __syncthreads();
+    }
+    if (ch >= 2) {
+      lift_step(P, pitch, ch, cw, s, true, false, true);
+      __syncthreads();
+      lift_step(P, pitch, ch, cw, s, true, true, true);
+      __syncthreads();
+    }
+  }
+  for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) g[e] = P[e];
+}
+
 // --------------------------------------------------------------- launches
 int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B,
                              cudaStream_t s) {
@@ -344,10 +535,31 @@ int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels
   return launches;
 }
 
-int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t n_blocks, const int32_t* planes, int32_t* coef,
+int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t n_blocks, const int32_t* planes, void* coef,
                        cudaStream_t s) {
   k_pack_blocks<<<(unsigned)n_blocks, 256, 0, s>>>(d_tiles, d_blocks, planes, coef);
   return 1;
+}
+
+int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const BlockDev* d_blocks,
+                         void* coef, cudaStream_t s) {
+  if (n_fused == 0) return 0;
+  k_fwd_tile_smem<<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, d_blocks, (uint8_t*)coef);
+  return 1;
+}
+
+int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, int z, int32_t* planes,
+                         cudaStream_t s) {
+  if (n_fused == 0) return 0;
+  k_inv_tile_smem<<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, z, planes);
+  return 1;
+}
+
+bool fused_tile(int w, int h, int bits) { return tile_uses_smem(w, h, bits); }
+
+void transform_set_attributes() {
+  cudaFuncSetAttribute(k_fwd_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
+  cudaFuncSetAttribute(k_inv_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
 }
 
 int launch_plan_blocks(const TileDev* d_tiles, int n_tiles, int min_level, BlockDev* d_blocks, cudaStream_t s) {
