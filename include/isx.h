@@ -75,13 +75,15 @@ void isx_destroy(isx_ctx* ctx);
 /* Encode n_tiles tiles into one contiguous stream (Fig. 1 left to right,
  * Fig. 2 a-e, Fig. 3).
  *   tiles          HOST array of n_tiles descriptors (pixels on the device).
- *   d_out          DEVICE buffer of out_capacity bytes receiving the tile
- *                  streams back to back, tile i at d_tile_offsets[i].
+ *   d_out          DEVICE buffer of out_capacity bytes, 4-byte aligned,
+ *                  receiving the tile streams back to back, tile i at
+ *                  d_tile_offsets[i].  The stream is written in whole
+ *                  32-bit words: it needs its size rounded up to a
+ *                  multiple of 4 bytes of capacity.
  *   d_tile_offsets DEVICE array of n_tiles + 1 uint64; [n_tiles] is the
- *                  total size.  If the total exceeds out_capacity nothing
- *                  is written to d_out, [n_tiles] still receives the
- *                  required size and isx_sync_status returns
- *                  ISX_ERR_CAPACITY.
+ *                  total size.  If the stream does not fit, nothing is
+ *                  written to d_out, [n_tiles] receives the capacity it
+ *                  needs and isx_sync_status returns ISX_ERR_CAPACITY.
  * Tile stream layout (little endian): "ISX1", u16 width, u16 height,
  * u8 channels, u8 bits, u8 levels, u8 colour transform (1 = RCT),
  * u32 n_blocks, u8 qstep_log2[16], u32 block_end[n_blocks], block data.

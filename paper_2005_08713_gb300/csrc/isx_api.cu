@@ -12,7 +12,6 @@
 #include "isx_kernels.h"
 
 namespace isx {
-int launch_encode_finalize(const EncodeBuffers& eb, int64_t header_total, cudaStream_t s);
 void encode_set_attributes();
 void decode_set_attributes();
 }  // namespace isx
@@ -188,7 +187,7 @@ void fill_tiledev(TileDev& d, const isx_tile_desc& t) {
 }
 
 struct EncodePlan {
-  int64_t n_blocks = 0, coef_bytes = 0, plane_total = 0, header_total = 0;
+  int64_t n_blocks = 0, coef_bytes = 0, plane_total = 0, header_total = 0, sym_bytes = 0;
   int max_levels = 0, max_dim = 1;
   int n_fused = 0, max_plane_bytes = 0;
 };
@@ -217,8 +216,11 @@ isx_status plan_encode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n, bool
     } else {
       P.plane_total += (int64_t)t.channels * t.width * t.height;
     }
+    d.sym_base = P.sym_bytes;
     P.n_blocks += nb;
     P.coef_bytes += nc * (t.bits <= 12 ? 2 : 4);
+    // symbol regions: dmax planes of p*w*h/8 bytes per block, each rounded up to 16
+    P.sym_bytes += ((int64_t)dmax_of_bits(t.bits) * (nc / 8 + 16 * nb) + 15) & ~15LL;   // 16-byte aligned regions
     P.header_total += 32 + 4 * nb;
     P.max_levels = std::max(P.max_levels, t.levels);
     P.max_dim = std::max(P.max_dim, std::max(t.width, t.height));
@@ -346,6 +348,7 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   if (!ctx) return ISX_ERR_ARG;
   if (!tiles || n_tiles < 1 || !d_tile_offsets || (!d_out && out_capacity))
     return fail(ctx, ISX_ERR_ARG, "bad arguments");
+  if (reinterpret_cast<uintptr_t>(d_out) & 3) return fail(ctx, ISX_ERR_ARG, "d_out must be 4-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   ISX_CUDA(cudaSetDevice(ctx->device));
   EncodePlan P;
@@ -353,7 +356,6 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   if (st != ISX_OK) return st;
   const int64_t NB = P.n_blocks;
   const int64_t n_part = NB / 2048 + 2;
-  const int64_t slot_cap = (int64_t)out_capacity + 32 * NB + 4096;
   Carve cv;
   size_t o_tiles = cv.take(sizeof(TileDev) * n_tiles);
   size_t o_task = cv.take(sizeof(int32_t) * (size_t)std::max(P.n_fused, 1));
@@ -361,11 +363,12 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   size_t o_A = cv.take(4 * (size_t)P.plane_total);
   size_t o_B = cv.take(4 * (size_t)P.plane_total);
   size_t o_coef = cv.take((size_t)P.coef_bytes);
+  size_t o_sym = cv.take((size_t)P.sym_bytes);
   size_t o_stats = cv.take(sizeof(BlockStats) * NB);
   size_t o_codes = cv.take(sizeof(BlockCode) * NB);
-  size_t o_ss = cv.take(8 * NB), o_so = cv.take(8 * NB), o_es = cv.take(8 * NB), o_fp = cv.take(8 * NB);
+  size_t o_hdrs = cv.take(enc_hdr_bytes() * NB);
+  size_t o_is = cv.take(8 * NB), o_fp = cv.take(8 * NB);
   size_t o_part = cv.take(8 * n_part), o_tot = cv.take(64);
-  size_t o_slots = cv.take((size_t)slot_cap);
   st = ensure_arena(ctx, cv.used);
   if (st != ISX_OK) return st;
   uint8_t* ar = ctx->arena;
@@ -392,17 +395,15 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   }
   EncodeBuffers eb;
   eb.tiles = d_tiles; eb.n_tiles = n_tiles; eb.blocks = d_blocks; eb.n_blocks = NB; eb.coef = coef;
+  eb.sym = ar + o_sym;
   eb.stats = (BlockStats*)(ar + o_stats);
   eb.codes = (BlockCode*)(ar + o_codes);
-  eb.slot_size = (int64_t*)(ar + o_ss); eb.slot_off = (int64_t*)(ar + o_so);
-  eb.exact_size = (int64_t*)(ar + o_es); eb.final_pos = (int64_t*)(ar + o_fp);
+  eb.hdrs = ar + o_hdrs;
+  eb.item_size = (int64_t*)(ar + o_is); eb.final_pos = (int64_t*)(ar + o_fp);
   eb.scan_part = (int64_t*)(ar + o_part); eb.totals = (int64_t*)(ar + o_tot);
-  eb.slots = ar + o_slots; eb.slot_capacity = slot_cap;
   eb.out = (uint8_t*)d_out; eb.out_capacity = (int64_t)out_capacity;
   eb.tile_offsets = d_tile_offsets; eb.status = ctx->d_status;
   L += launch_encode_coding(eb, s, &T);
-  T.mark("encode.finalize", s);
-  L += launch_encode_finalize(eb, P.header_total, s);
   T.mark(nullptr, s);
   ctx->launches = L;
   ISX_CUDA(cudaGetLastError());

@@ -1,24 +1,29 @@
 // isx_encode.cu — the block coder (Sec. 4, Fig. 2 c-e, Fig. 3):
-//   pass 1  k_block_stats    per block: bit depth d, removed planes, symbol
-//                            histogram, zero runs (one CTA per block);
+//   pass 1  k_enc_symbols    per block: bit depth d, removed planes, the kept
+//                            symbols written once to a flat symbol buffer,
+//                            then histogram and zero runs from that buffer;
 //   pass 2  k_block_huffman  per block: zero-run symbol C_zr, counter width
 //                            w (Eq. 3), provisional and final Huffman codes,
-//                            tree bits, exact token bits (one thread per block:
-//                            32 blocks' trees are built side by side in a warp);
-//   pass 3  k_block_emit     per block: header, seektable, tree and plane
-//                            segments written bit-exactly into a slot;
-//   pass 4  k_finalize_tiles / k_copy_blocks: tile headers and a compacted,
-//                            contiguous stream.
+//                            tree bits (one thread per block: the trees of 32
+//                            blocks are built side by side in a warp);
+//   pass 3  k_enc_size       per block (one warp): exact plane segment
+//                            lengths, seektable width t, block size;
+//   pass 4  k_enc_emit       per block (one warp): header, seektable, tree
+//                            and segments written bit-exactly into their
+//                            final place in the contiguous stream;
+//           k_tile_headers   tile headers.
 // Symbols: every 4x2 area (8 coefficients stored consecutively in Eq. 2
 // bit order) gives one byte per bitplane; plane 0 is the sign plane, plane
 // pl >= 1 magnitude bit d-1-pl (signed-magnitude representation, Sec. 4).
+// A block's symbol region holds, for every plane with a kept type, the kept
+// types' symbols (n = w*h/8 each, types in order HL, LH, HH) padded to 16
+// bytes: the plane segments of Fig. 3 before zero-run and Huffman coding.
 #include "isx_internal.cuh"
 #include "isx_kernels.h"
 
 namespace isx {
 
 constexpr uint32_t kAllZero = 0x80000000u;
-constexpr int kStageWords = 12288;   // 48 KB output window per CTA
 
 // The coefficients of one block: 8 per area in Eq. 2 bit order, int16 or int32.
 struct CoefRef {
@@ -41,38 +46,51 @@ struct CoefRef {
   }
 };
 
-__device__ inline uint32_t area_symbol(const CoefRef& cf, int a, int pl, int d) {
-  int32_t c[8];
-  cf.load(a, c);
-  uint32_t s = 0;
-  if (pl == 0) {
-#pragma unroll
-    for (int e = 0; e < 8; ++e) s |= (uint32_t)(c[e] < 0) << e;
-  } else {
-    const int sh = d - 1 - pl;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) s |= ((uint32_t)(abs(c[e]) >> sh) & 1u) << e;
-  }
-  return s;
-}
-
-// Removed-plane masks and depth from the OR of the magnitudes of each type.
-__device__ inline void block_masks(const uint32_t* s_or, const uint32_t* s_neg, int p, int d, uint32_t* removed) {
-  for (int t = 0; t < 3; ++t) {
-    uint32_t r = 0;
-    for (int pl = 0; pl < d; ++pl) {
-      bool empty = t >= p || (pl == 0 ? s_neg[t] == 0 : ((s_or[t] >> (d - 1 - pl)) & 1u) == 0);
-      if (empty) r |= 1u << pl;
-    }
-    removed[t] = r;
-  }
-}
-
 __device__ inline uint32_t kept_types(const uint32_t* removed, int p, int pl) {
   uint32_t km = 0;
   for (int t = 0; t < p; ++t)
     if (!((removed[t] >> pl) & 1u)) km |= 1u << t;
   return km;
+}
+
+__device__ inline int64_t region16(uint32_t km, int n) { return ((int64_t)__popc(km) * n + 15) & ~15LL; }
+
+// ------------------------------------------------------------ warp runs
+// A zero-run carry element: bit 31 = every symbol covered is zero, low bits
+// = zeros at the end of the covered range.  Lanes cover 16 symbols each.
+__device__ inline uint32_t warp_carry_exclusive(uint32_t v, uint32_t* inclusive_of_lane, uint32_t* total) {
+  const int lane = threadIdx.x & 31;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = carry_combine(y, x);
+  }
+  uint32_t ex = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) ex = kAllZero;
+  *inclusive_of_lane = x;
+  *total = __shfl_sync(0xffffffffu, x, 31);
+  return ex;
+}
+
+// Summary of a lane's symbols: leading zeros, trailing zeros, any nonzero.
+struct LaneSyms {
+  uint32_t w[4];
+  int cnt;
+  __device__ uint32_t at(int k) const { return (w[k >> 2] >> (8 * (k & 3))) & 0xffu; }
+};
+
+__device__ inline LaneSyms load_lane(const uint8_t* seg, int len, int base) {
+  const int lane = threadIdx.x & 31;
+  LaneSyms L;
+  const int my0 = base + lane * 16;
+  L.cnt = max(0, min(16, len - my0));
+  L.w[0] = L.w[1] = L.w[2] = L.w[3] = 0;
+  if (L.cnt > 0) {
+    const uint4 u = *reinterpret_cast<const uint4*>(seg + my0);
+    L.w[0] = u.x; L.w[1] = u.y; L.w[2] = u.z; L.w[3] = u.w;
+  }
+  return L;
 }
 
 // ------------------------------------------------------------- pass 1
@@ -83,23 +101,24 @@ __device__ inline void record_run(uint32_t L, uint32_t* s_hist, uint32_t* s_runs
   }
   atomicAdd(s_runs, 1u);
   for (int w = 2; w <= kMaxW; ++w) {
-    uint32_t M = (1u << w) - 1u;
+    const uint32_t M = (1u << w) - 1u;
     if (M >= L) break;
     atomicAdd(&s_extra[w], (L + M - 1) / M - 1);
   }
 }
 
-__global__ void __launch_bounds__(kCtaThreads) k_block_stats(const BlockDev* __restrict__ blocks, const uint8_t* __restrict__ coef,
-                                                            BlockStats* __restrict__ stats) {
+__global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict__ blocks, const uint8_t* __restrict__ coef,
+                                                    uint8_t* __restrict__ sym, BlockStats* __restrict__ stats, int* __restrict__ status) {
   __shared__ uint32_t s_hist[256];
   __shared__ uint32_t s_extra[kMaxW + 1];
   __shared__ uint32_t s_runs;
   __shared__ uint32_t s_or[3], s_neg[3];
-  __shared__ uint32_t s_tmp[33];
+  __shared__ uint32_t s_km[32];
+  __shared__ int64_t s_poff[32];
   const BlockDev b = blocks[blockIdx.x];
   const int n = b.w * b.h / 8, na = b.p * n;
   const CoefRef cf{coef + b.coef, b.coef16};
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
   if (tid <= kMaxW) s_extra[tid] = 0;
   if (tid < 3) { s_or[tid] = 0; s_neg[tid] = 0; }
@@ -118,9 +137,9 @@ __global__ void __launch_bounds__(kCtaThreads) k_block_stats(const BlockDev* __r
       }
     }
     for (int t = 0; t < 3; ++t) {
-      uint32_t ro = __reduce_or_sync(0xffffffffu, o[t]);
-      uint32_t rn = __reduce_or_sync(0xffffffffu, ng[t]);
-      if ((tid & 31) == 0) {
+      const uint32_t ro = __reduce_or_sync(0xffffffffu, o[t]);
+      const uint32_t rn = __reduce_or_sync(0xffffffffu, ng[t]);
+      if (lane == 0) {
         if (ro) atomicOr(&s_or[t], ro);
         if (rn) atomicOr(&s_neg[t], rn);
       }
@@ -130,38 +149,98 @@ __global__ void __launch_bounds__(kCtaThreads) k_block_stats(const BlockDev* __r
   const uint32_t all_or = s_or[0] | s_or[1] | s_or[2];
   const int d = 1 + (all_or ? bitlen_u32(all_or) : 0);
   uint32_t removed[3];
-  block_masks(s_or, s_neg, b.p, d, removed);
-  const int m = (na + blockDim.x - 1) / blockDim.x;
-  const int a0 = tid * m, a1 = min(a0 + m, na);
+  for (int t = 0; t < 3; ++t) {
+    uint32_t r = 0;
+    for (int pl = 0; pl < d; ++pl) {
+      const bool empty = t >= b.p || (pl == 0 ? s_neg[t] == 0 : ((s_or[t] >> (d - 1 - pl)) & 1u) == 0);
+      if (empty) r |= 1u << pl;
+    }
+    removed[t] = r;
+  }
+  if (d > b.dmax) {   // cannot happen for inputs within the stated bit depth
+    if (tid == 0) set_status(status, 7);
+    return;
+  }
   uint32_t n_sym = 0;
-  for (int pl = 0; pl < d; ++pl) {
-    const uint32_t km = kept_types(removed, b.p, pl);
-    if (!km) continue;
-    n_sym += (uint32_t)__popc(km) * n;
-    const int t_last = 31 - __clz(km);
-    const int end_owner = (t_last * n + n - 1) / m;
-    uint32_t cnt = 0, zeros = 0, lz = 0;
-    bool seen = false;
-    for (int a = a0; a < a1; ++a) {
-      if (!((km >> (a / n)) & 1u)) continue;
-      uint32_t s = area_symbol(cf, a, pl, d);
-      ++cnt;
-      if (s == 0) {
-        ++zeros;
+  {
+    int64_t off = 0;
+    for (int pl = 0; pl < d; ++pl) {
+      const uint32_t km = kept_types(removed, b.p, pl);
+      if (tid == 0) { s_km[pl] = km; s_poff[pl] = off; }
+      off += km ? region16(km, n) : 0;
+      n_sym += (uint32_t)__popc(km) * n;
+    }
+  }
+  __syncthreads();
+  // symbols of every kept (plane, type), written once
+  uint8_t* S = sym + b.sym;
+  for (int a = tid; a < na; a += blockDim.x) {
+    const int t = a / n, k = a - t * n;
+    int32_t c[8];
+    cf.load(a, c);
+    uint32_t negm = 0, m01 = 0, m23 = 0, m45 = 0, m67 = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) negm |= (uint32_t)(c[e] < 0) << e;
+    // magnitudes packed in pairs (e, e + 4) so one shift serves both rows of the area
+    m01 = (uint32_t)abs(c[0]) | ((uint32_t)abs(c[4]) << 16);
+    m23 = (uint32_t)abs(c[1]) | ((uint32_t)abs(c[5]) << 16);
+    m45 = (uint32_t)abs(c[2]) | ((uint32_t)abs(c[6]) << 16);
+    m67 = (uint32_t)abs(c[3]) | ((uint32_t)abs(c[7]) << 16);
+    const bool wide = !b.coef16;
+    for (int pl = 0; pl < d; ++pl) {
+      const uint32_t km = s_km[pl];
+      if (!((km >> t) & 1u)) continue;
+      uint32_t s;
+      if (pl == 0) {
+        s = negm;
       } else {
-        atomicAdd(&s_hist[s], 1u);
-        if (!seen) { lz = zeros; seen = true; }
-        else if (zeros) record_run(zeros, s_hist, &s_runs, s_extra);
-        zeros = 0;
+        const int sh = d - 1 - pl;
+        if (!wide) {
+          const uint32_t x = ((m01 >> sh) & 0x10001u) | (((m23 >> sh) & 0x10001u) << 1) | (((m45 >> sh) & 0x10001u) << 2) |
+                             (((m67 >> sh) & 0x10001u) << 3);
+          s = (x & 0xfu) | ((x >> 12) & 0xf0u);
+        } else {
+          s = 0;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) s |= (((uint32_t)abs(c[e]) >> sh) & 1u) << e;
+        }
       }
+      const int ki = __popc(km & ((1u << t) - 1u));
+      S[s_poff[pl] + (int64_t)ki * n + k] = (uint8_t)s;
     }
-    const uint32_t elem = seen ? zeros : (kAllZero | cnt);
-    const uint32_t cin = cta_exclusive_carry(elem, s_tmp) & ~kAllZero;
-    if (seen && cin + lz > 0) record_run(cin + lz, s_hist, &s_runs, s_extra);
-    if (tid == end_owner) {
-      uint32_t Lf = seen ? zeros : cin + cnt;
-      if (Lf) record_run(Lf, s_hist, &s_runs, s_extra);
+  }
+  __syncthreads();
+  // histogram and zero runs, one warp per plane segment
+  for (int pl = wid; pl < d; pl += nw) {
+    const uint32_t km = s_km[pl];
+    if (!km) continue;
+    const int len = __popc(km) * n;
+    const uint8_t* seg = S + s_poff[pl];
+    uint32_t carry = kAllZero;
+    for (int base = 0; base < len; base += 512) {
+      const LaneSyms L = load_lane(seg, len, base);
+      uint32_t zeros = 0, lz = 0;
+      bool seen = false;
+      for (int k = 0; k < L.cnt; ++k) {
+        const uint32_t s = L.at(k);
+        if (s == 0) {
+          ++zeros;
+        } else {
+          atomicAdd(&s_hist[s], 1u);
+          if (!seen) { lz = zeros; seen = true; }
+          else if (zeros) record_run(zeros, s_hist, &s_runs, s_extra);
+          zeros = 0;
+        }
+      }
+      const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
+      uint32_t incl, tot;
+      const uint32_t ex = warp_carry_exclusive(elem, &incl, &tot);
+      const uint32_t cin = carry_combine(carry, ex) & ~kAllZero;
+      if (seen && cin + lz > 0) record_run(cin + lz, s_hist, &s_runs, s_extra);
+      carry = carry_combine(carry, tot);
     }
+    const uint32_t fin = carry & ~kAllZero;
+    if (lane == 0 && fin) record_run(fin, s_hist, &s_runs, s_extra);
   }
   __syncthreads();
   BlockStats* st = stats + blockIdx.x;
@@ -247,7 +326,7 @@ __device__ inline void put_bits_local(uint32_t* words, int pos, uint32_t v, int 
 }
 
 __global__ void __launch_bounds__(64) k_block_huffman(const BlockDev* __restrict__ blocks, const BlockStats* __restrict__ stats,
-                                                      BlockCode* __restrict__ codes, int64_t* __restrict__ slot_size, int64_t nb) {
+                                                      BlockCode* __restrict__ codes, int64_t nb) {
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (bi >= nb) return;
   const BlockStats& st = stats[bi];
@@ -265,8 +344,6 @@ __global__ void __launch_bounds__(64) k_block_huffman(const BlockDev* __restrict
     bc.token_bits = 0;
     bc.tree_bits = 0;
     bc.czr = 0; bc.wbits = 0;
-    int64_t bytes = (5 + p * d + 7) / 8;
-    slot_size[bi] = (bytes + 15) & ~15LL;
     return;
   }
   bc.any_kept = 1;
@@ -335,33 +412,10 @@ __global__ void __launch_bounds__(64) k_block_huffman(const BlockDev* __restrict
   bc.czr = czr;
   bc.wbits = wbest;
   bc.token_bits = token_bits;
-  const int tmax = max(t0, bitlen_u64(token_bits));
-  const uint64_t hdr = 5 + (uint64_t)p * d + 18 + (uint64_t)d * tmax + tree_bits;
-  const int64_t bytes = (int64_t)((hdr + token_bits + 7) / 8);
-  slot_size[bi] = (bytes + 15) & ~15LL;
 }
 
-// ------------------------------------------------------------- pass 3
-// MSB-first bit writer into a shared-memory window of the block's output
-// (words hold the stream big-endian: stream bit q is bit 31 - q%32).
-struct Window {
-  uint32_t* w;
-  int64_t lo;   // first bit of the window (multiple of 32)
-  int64_t hi;   // one past its last bit
-};
 
-__device__ inline void put_bits(const Window& win, int64_t pos, uint32_t v, int nb) {
-  if (nb <= 0 || pos + nb <= win.lo || pos >= win.hi) return;
-  const int64_t rel = pos - win.lo;
-  const int64_t wi = rel >= 0 ? rel >> 5 : -((-rel + 31) >> 5);
-  const int off = (int)(rel - wi * 32);
-  const uint64_t vv = (uint64_t)(v & (nb == 32 ? 0xffffffffu : ((1u << nb) - 1u))) << (64 - off - nb);
-  const int64_t nw = (win.hi - win.lo) >> 5;
-  const uint32_t hi = (uint32_t)(vv >> 32), lo = (uint32_t)vv;
-  if (hi && wi >= 0 && wi < nw) atomicOr(&win.w[wi], hi);
-  if (lo && wi + 1 >= 0 && wi + 1 < nw) atomicOr(&win.w[wi + 1], lo);
-}
-
+// ------------------------------------------------------------- pass 3/4
 struct CodeTab {
   const uint32_t* code;
   const uint8_t* len;
@@ -369,233 +423,297 @@ struct CodeTab {
   uint32_t M;
 };
 
-__device__ inline uint64_t run_bits(const CodeTab& ct, uint32_t L) {
+__device__ inline uint32_t run_bits(const CodeTab& ct, uint32_t L) {
   if (L == 1) return ct.len[0];
   if (ct.M == 0) return 0;
-  uint32_t pairs = (L + ct.M - 1) / ct.M;
-  return (uint64_t)pairs * (ct.len[ct.czr] + ct.wbits);
+  return ((L + ct.M - 1) / ct.M) * (uint32_t)(ct.len[ct.czr] + ct.wbits);
+}
+__device__ inline uint32_t lit_bits(const CodeTab& ct, uint32_t s) {
+  return ct.len[s] + ((int)s == ct.czr ? ct.wbits : 0);
 }
 
-__device__ inline int64_t put_run(const CodeTab& ct, const Window& win, int64_t pos, uint32_t L) {
-  if (L == 1) {
-    put_bits(win, pos, ct.code[0], ct.len[0]);
-    return pos + ct.len[0];
+// MSB-first writer of one lane's contiguous bit range straight into the
+// stream (32-bit words, big endian).  Words strictly inside the range are
+// stored; the first and last (shared with neighbouring ranges) are OR-ed
+// into the zero-initialised stream.
+struct LaneWriter {
+  uint32_t* out;
+  int64_t w0, wcur;
+  uint64_t acc;
+  int nacc;
+  __device__ void begin(uint32_t* o, int64_t bitpos) {
+    out = o;
+    wcur = w0 = bitpos >> 5;
+    acc = 0;
+    nacc = (int)(bitpos & 31);
   }
+  __device__ void word(uint32_t x) {
+    const uint32_t be = __byte_perm(x, 0, 0x0123);
+    if (wcur == w0) atomicOr(&out[wcur], be);
+    else out[wcur] = be;
+    ++wcur;
+  }
+  __device__ void put(uint32_t v, int nb) {   // nb <= 32
+    if (nb <= 0) return;
+    const uint64_t x = (uint64_t)(nb == 32 ? v : (v & ((1u << nb) - 1u)));
+    acc |= x << (64 - nacc - nb);
+    nacc += nb;
+    if (nacc >= 32) {
+      word((uint32_t)(acc >> 32));
+      acc <<= 32;
+      nacc -= 32;
+    }
+  }
+  __device__ void end() {
+    if (nacc > 0) atomicOr(&out[wcur], __byte_perm((uint32_t)(acc >> 32), 0, 0x0123));
+  }
+};
+
+__device__ inline void put_run(const CodeTab& ct, LaneWriter& W, uint32_t L) {
+  if (L == 1) {
+    W.put(ct.code[0], ct.len[0]);
+    return;
+  }
+  if (ct.M == 0) return;   // counter width is always >= 2
   const int lc = ct.len[ct.czr];
   const uint32_t cz = ct.code[ct.czr];
-  if (ct.M == 0) return pos;   // counter width is always >= 2; never loop on a bad table
   while (L > 0) {
-    uint32_t k = L >= ct.M ? ct.M : L;
-    put_bits(win, pos, cz, lc);
-    pos += lc;
-    put_bits(win, pos, k, ct.wbits);
-    pos += ct.wbits;
+    const uint32_t k = L >= ct.M ? ct.M : L;
+    W.put(cz, lc);
+    W.put(k, ct.wbits);
     L -= k;
   }
-  return pos;
 }
 
-__device__ inline int64_t put_literal(const CodeTab& ct, const Window& win, int64_t pos, uint32_t s) {
-  put_bits(win, pos, ct.code[s], ct.len[s]);
-  pos += ct.len[s];
-  if ((int)s == ct.czr) pos += ct.wbits;   // counter 0: a literal C_zr
-  return pos;
+__device__ inline void put_literal(const CodeTab& ct, LaneWriter& W, uint32_t s) {
+  W.put(ct.code[s], ct.len[s]);
+  if ((int)s == ct.czr) W.put(0, ct.wbits);   // counter 0: a literal C_zr
 }
 
-// One pass over all planes: writes the tokens that fall in the window and
-// records the segment lengths.  All threads of the CTA call it.
-__device__ void emit_planes(const CoefRef& cf, int n, int p, int d, const uint32_t* removed, const CodeTab& ct,
-                            const Window& win, int64_t seg_start, uint32_t* s_seglen, uint32_t* s_tmp32, uint64_t* s_tmp64) {
-  const int na = p * n;
-  const int m = (na + blockDim.x - 1) / blockDim.x;
-  const int a0 = threadIdx.x * m, a1 = min(a0 + m, na);
-  for (int pl = 0; pl < d; ++pl) {
-    const uint32_t km = kept_types(removed, p, pl);
-    if (!km) {
-      if (threadIdx.x == 0) s_seglen[pl] = 0;
-      continue;
-    }
-    const int t_last = 31 - __clz(km);
-    const bool is_end = (int)threadIdx.x == (t_last * n + n - 1) / m;
-    // count
-    uint32_t cnt = 0, zeros = 0, lz = 0;
+// Per-block layout found by the size pass.
+struct BlockHdr {
+  int32_t t, pad;
+  int64_t hdr_bits;
+  uint32_t seglen[32];
+};
+
+// One warp walks plane segment `seg` (len symbols) in chunks of 512:
+// WRITE = false returns the segment's bit length; WRITE = true writes its
+// tokens from absolute bit position `pos`.
+template <bool WRITE>
+__device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct, uint32_t* out, int64_t pos) {
+  const int lane = threadIdx.x & 31;
+  uint32_t carry = kAllZero;
+  uint64_t total = 0;
+  for (int base = 0; base < len; base += 512) {
+    const LaneSyms L = load_lane(seg, len, base);
+    uint32_t zeros = 0, lz = 0;
     bool seen = false;
-    uint64_t bits = 0;
-    for (int a = a0; a < a1; ++a) {
-      if (!((km >> (a / n)) & 1u)) continue;
-      uint32_t s = area_symbol(cf, a, pl, d);
-      ++cnt;
+    uint32_t bits = 0;
+    for (int k = 0; k < L.cnt; ++k) {
+      const uint32_t s = L.at(k);
       if (s == 0) {
         ++zeros;
       } else {
         if (!seen) { lz = zeros; seen = true; }
         else if (zeros) bits += run_bits(ct, zeros);
-        bits += ct.len[s] + ((int)s == ct.czr ? ct.wbits : 0);
+        bits += lit_bits(ct, s);
         zeros = 0;
       }
     }
-    const uint32_t elem = seen ? zeros : (kAllZero | cnt);
-    const uint32_t cin = cta_exclusive_carry(elem, s_tmp32) & ~kAllZero;
+    const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
+    uint32_t incl, tot;
+    const uint32_t ex = warp_carry_exclusive(elem, &incl, &tot);
+    const uint32_t cin = carry_combine(carry, ex) & ~kAllZero;
     const uint32_t lead = seen ? cin + lz : 0;
     if (lead) bits += run_bits(ct, lead);
-    uint32_t fin = 0;
-    if (is_end) fin = seen ? zeros : cin + cnt;
+    // the lane holding the segment's last symbol closes the final run
+    const bool last_lane = base + 512 >= len && lane == (len - 1 - base) / 16;
+    const uint32_t fin = last_lane ? (carry_combine(carry, incl) & ~kAllZero) : 0;
     if (fin) bits += run_bits(ct, fin);
-    uint64_t seg_total;
-    const uint64_t myoff = cta_exclusive_sum<uint64_t>(bits, s_tmp64, &seg_total);
-    // write
-    int64_t pos = seg_start + (int64_t)myoff;
-    if (lead) pos = put_run(ct, win, pos, lead);
-    zeros = 0;
-    bool first = true;
-    for (int a = a0; a < a1; ++a) {
-      if (!((km >> (a / n)) & 1u)) continue;
-      uint32_t s = area_symbol(cf, a, pl, d);
-      if (s == 0) {
-        ++zeros;
-      } else {
-        if (!first && zeros) pos = put_run(ct, win, pos, zeros);
-        first = false;
-        pos = put_literal(ct, win, pos, s);
-        zeros = 0;
-      }
+    // bit offsets of the lanes within the chunk
+    uint32_t x = bits;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    if (fin) pos = put_run(ct, win, pos, fin);
-    if (threadIdx.x == 0) s_seglen[pl] = (uint32_t)seg_total;
-    seg_start += (int64_t)seg_total;
-    __syncthreads();
+    const uint32_t chunk_bits = __shfl_sync(0xffffffffu, x, 31);
+    if (WRITE && bits) {
+      LaneWriter W;
+      W.begin(out, pos + (int64_t)total + (x - bits));
+      if (lead) put_run(ct, W, lead);
+      uint32_t z = 0;
+      bool first = true;
+      for (int k = 0; k < L.cnt; ++k) {
+        const uint32_t s = L.at(k);
+        if (s == 0) {
+          ++z;
+        } else {
+          if (!first && z) put_run(ct, W, z);
+          first = false;
+          put_literal(ct, W, s);
+          z = 0;
+        }
+      }
+      if (fin) put_run(ct, W, fin);
+      W.end();
+    }
+    total += chunk_bits;
+    carry = carry_combine(carry, tot);
   }
-  __syncthreads();
+  return total;
 }
 
-__global__ void __launch_bounds__(kCtaThreads) k_block_emit(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
-                                                           const uint8_t* __restrict__ coef, const BlockCode* __restrict__ codes,
-                                                           const int64_t* __restrict__ slot_off, const int64_t* __restrict__ slot_size,
-                                                           uint8_t* __restrict__ slots, int64_t slot_cap, const int64_t* __restrict__ totals,
-                                                           int64_t* __restrict__ item_size, int* __restrict__ status) {
-  extern __shared__ uint32_t stage[];
-  __shared__ uint32_t s_code[256];
-  __shared__ uint8_t s_len[256];
-  __shared__ uint32_t s_seglen[32];
-  __shared__ uint32_t s_tmp32[33];
-  __shared__ uint64_t s_tmp64[33];
-  __shared__ int s_t;
-  const int64_t bi = blockIdx.x;
-  if (totals[0] > slot_cap) return;   // not enough scratch: reported by k_finalize_tiles
+constexpr int kEmitWarps = 8;
+
+__device__ inline int64_t block_bit_start(const TileDev& t, const int64_t* final_pos, int64_t bi) {
+  return 8 * (final_pos[bi] + (bi == t.block_base ? 32 + 4 * (int64_t)t.nb : 0));
+}
+
+// Size pass: exact segment lengths, t, header and block size.
+__global__ void __launch_bounds__(32 * kEmitWarps) k_enc_size(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
+                                                             int64_t nb, const uint8_t* sym, const BlockCode* __restrict__ codes,
+                                                             BlockHdr* __restrict__ hdrs, int64_t* __restrict__ item_size,
+                                                             int* __restrict__ status) {
+  __shared__ uint32_t s_code[kEmitWarps][256];
+  __shared__ uint8_t s_len[kEmitWarps][256];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t bi = (int64_t)blockIdx.x * kEmitWarps + wid;
+  if (bi >= nb) return;
   const BlockDev b = blocks[bi];
   const BlockCode& bc = codes[bi];
   const TileDev& tile = tiles[b.tile];
-  const int n = b.w * b.h / 8, p = b.p, d = bc.d;
-  const int tid = threadIdx.x;
-  uint32_t removed[3] = {bc.removed[0], bc.removed[1], bc.removed[2]};
-  uint8_t* out = slots + slot_off[bi];
-  const int64_t cap_bytes = slot_size[bi];
-  const int64_t stage_bits = (int64_t)kStageWords * 32;
-  const int64_t first_item_extra = (bi == tile.block_base) ? 32 + 4 * (int64_t)tile.nb : 0;
+  const int64_t extra = bi == tile.block_base ? 32 + 4 * (int64_t)tile.nb : 0;
+  const int d = bc.d, p = b.p, n = b.w * b.h / 8;
   if (!bc.any_kept) {
-    // d and the all-ones removed mask only
-    if (tid == 0) {
-      uint32_t w[5] = {0, 0, 0, 0, 0};
-      put_bits_local(w, 0, (uint32_t)d, 5);
-      for (int t = 0; t < p; ++t)
-        for (int pl = 0; pl < d; ++pl) put_bits_local(w, 5 + t * d + pl, 1u, 1);
-      int bytes = (5 + p * d + 7) / 8;
-      for (int k = 0; k < bytes; ++k) out[k] = (uint8_t)(w[k >> 2] >> (24 - 8 * (k & 3)));
-      item_size[bi] = bytes + first_item_extra;
+    if (lane == 0) {
+      hdrs[bi].t = 0;
+      hdrs[bi].hdr_bits = 5 + (int64_t)p * d;
+      item_size[bi] = (5 + (int64_t)p * d + 7) / 8 + extra;
     }
     return;
   }
-  for (int s = tid; s < 256; s += blockDim.x) { s_code[s] = bc.code[s]; s_len[s] = bc.len[s]; }
-  if (tid == 0) s_t = bc.t0;
-  __syncthreads();
-  CodeTab ct{s_code, s_len, bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
-  const int tree_bits = bc.tree_bits;
-  const int64_t hm = 5 + (int64_t)p * d;
-  int t = s_t;
-  int64_t total_bits = 0;
-  for (int64_t wlo = 0;; wlo += stage_bits) {
-    Window win{stage, wlo, wlo + stage_bits};
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      for (int k = tid; k < kStageWords; k += blockDim.x) stage[k] = 0;
-      __syncthreads();
-      const int64_t hdr = hm + 18 + (int64_t)d * t + tree_bits;
-      emit_planes(CoefRef{coef + b.coef, b.coef16}, n, p, d, removed, ct, win, hdr, s_seglen, s_tmp32, s_tmp64);
-      if (wlo > 0) break;
-      // first window: fix t (raised only when a segment length needs more bits)
-      uint32_t mx = 0;
-      uint64_t sum = 0;
-      for (int pl = 0; pl < d; ++pl) { mx = max(mx, s_seglen[pl]); sum += s_seglen[pl]; }
-      if (sum != bc.token_bits) {
-        if (tid == 0) set_status(status, 7);
-        return;
-      }
-      const int need = mx ? bitlen_u32(mx) : 0;
-      if (need <= t) break;
-      t = need;
-      __syncthreads();
+  for (int s = lane; s < 256; s += 32) { s_code[wid][s] = bc.code[s]; s_len[wid][s] = bc.len[s]; }
+  __syncwarp();
+  const CodeTab ct{s_code[wid], s_len[wid], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
+  const uint32_t removed[3] = {bc.removed[0], bc.removed[1], bc.removed[2]};
+  const uint8_t* S = sym + b.sym;
+  int64_t off = 0;
+  uint64_t sum = 0;
+  uint32_t mx = 0;
+  for (int pl = 0; pl < d; ++pl) {
+    const uint32_t km = kept_types(removed, p, pl);
+    uint32_t len_bits = 0;
+    if (km) {
+      len_bits = (uint32_t)warp_segment<false>(S + off, __popc(km) * n, ct, nullptr, 0);
+      off += region16(km, n);
     }
-    const int64_t hdr = hm + 18 + (int64_t)d * t + tree_bits;
-    total_bits = hdr + (int64_t)bc.token_bits;
-    if (wlo == 0) {
-      // header: d, removed mask, C_zr, w, t, seektable, tree
-      if (tid == 0) {
-        put_bits(win, 0, (uint32_t)d, 5);
-        for (int ty = 0; ty < p; ++ty)
-          for (int pl = 0; pl < d; ++pl)
-            if ((removed[ty] >> pl) & 1u) put_bits(win, 5 + ty * d + pl, 1u, 1);
-        put_bits(win, hm, (uint32_t)bc.czr, 8);
-        put_bits(win, hm + 8, (uint32_t)bc.wbits, 5);
-        put_bits(win, hm + 13, (uint32_t)t, 5);
-      }
-      if (tid < d) put_bits(win, hm + 18 + (int64_t)tid * t, s_seglen[tid], t);
-      const int64_t tree_pos = hm + 18 + (int64_t)d * t;
-      for (int k = tid; k * 32 < tree_bits; k += blockDim.x) {
-        int nbk = min(32, tree_bits - 32 * k);
-        put_bits(win, tree_pos + 32 * k, bc.tree[k] >> (32 - nbk), nbk);
-      }
-      if (tid == 0) {
-        int64_t bytes = (total_bits + 7) / 8;
-        if (bytes > cap_bytes) set_status(status, 7);
-        item_size[bi] = bytes + first_item_extra;
-      }
-    }
-    __syncthreads();
-    // flush the window (bytes beyond the block end are zero padding inside the slot)
-    const int64_t total_bytes = (total_bits + 7) / 8;
-    const int64_t wbyte = wlo / 8;
-    const int64_t nbytes = min((int64_t)kStageWords * 4, total_bytes - wbyte);
-    const int64_t nwords = (nbytes + 3) / 4;
-    if (wbyte + nwords * 4 <= cap_bytes) {
-      uint32_t* o32 = reinterpret_cast<uint32_t*>(out + wbyte);
-      for (int64_t k = tid; k < nwords; k += blockDim.x) o32[k] = __byte_perm(stage[k], 0, 0x0123);
-    } else if (tid == 0) {
-      set_status(status, 7);
-    }
-    __syncthreads();
-    if (wlo + stage_bits >= total_bits) break;
+    if (lane == 0) hdrs[bi].seglen[pl] = len_bits;
+    sum += len_bits;
+    mx = max(mx, len_bits);
+  }
+  if (lane == 0) {
+    const int t = max(bc.t0, mx ? bitlen_u32(mx) : 0);
+    const int64_t hdr = 5 + (int64_t)p * d + 18 + (int64_t)d * t + bc.tree_bits;
+    hdrs[bi].t = t;
+    hdrs[bi].hdr_bits = hdr;
+    if (sum != bc.token_bits) set_status(status, 7);
+    item_size[bi] = (hdr + (int64_t)sum + 7) / 8 + extra;
   }
 }
 
-// ------------------------------------------------------------- pass 4
-// One CTA per tile: its stream offset, its header (little endian) and its
-// blocks copied from their slots into the contiguous output.  Every output
-// byte of a tile is written by that tile's CTA only.
-__global__ void __launch_bounds__(256) k_assemble_tiles(const TileDev* tiles, int n_tiles, const int64_t* final_pos,
-                                                       const int64_t* item_size, const int64_t* slot_off, const int64_t* totals,
-                                                       int64_t slot_cap, int64_t header_total, const uint8_t* slots, uint8_t* out,
-                                                       int64_t out_cap, uint64_t* tile_offsets, int* status) {
+// Zero the stream (its shared boundary words are OR-ed).
+// The stream is written in whole 32-bit words: it needs its size rounded
+// up to a multiple of 4 bytes of capacity.
+__device__ inline int64_t needed_capacity(int64_t total) { return (total + 3) & ~3LL; }
+
+__global__ void k_zero_stream(uint32_t* __restrict__ out, const int64_t* __restrict__ totals, int64_t out_cap) {
+  const int64_t total = totals[0];
+  if (needed_capacity(total) > out_cap) return;
+  const int64_t nw = (total + 3) / 4;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (int64_t)gridDim.x * blockDim.x) out[k] = 0;
+}
+
+// Emit pass: one warp per block writes header and segments in place.
+__global__ void __launch_bounds__(32 * kEmitWarps) k_enc_emit(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
+                                                             int64_t nb, const uint8_t* sym, const BlockCode* __restrict__ codes,
+                                                             const BlockHdr* __restrict__ hdrs, const int64_t* __restrict__ final_pos,
+                                                             const int64_t* __restrict__ totals, int64_t out_cap, uint32_t* __restrict__ out) {
+  __shared__ uint32_t s_code[kEmitWarps][256];
+  __shared__ uint8_t s_len[kEmitWarps][256];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t bi = (int64_t)blockIdx.x * kEmitWarps + wid;
+  if (bi >= nb || needed_capacity(totals[0]) > out_cap) return;
+  const BlockDev b = blocks[bi];
+  const BlockCode& bc = codes[bi];
+  const BlockHdr& H = hdrs[bi];
+  const TileDev& tile = tiles[b.tile];
+  const int d = bc.d, p = b.p, n = b.w * b.h / 8;
+  const uint32_t removed[3] = {bc.removed[0], bc.removed[1], bc.removed[2]};
+  const int64_t B0 = block_bit_start(tile, final_pos, bi);
+  // header: d and the removed mask (type-major, plane order)
+  if (lane == 0) {
+    LaneWriter W;
+    W.begin(out, B0);
+    W.put((uint32_t)d, 5);
+    for (int ty = 0; ty < p; ++ty)
+      for (int pl = 0; pl < d; ++pl) W.put((removed[ty] >> pl) & 1u, 1);
+    if (bc.any_kept) {
+      W.put((uint32_t)bc.czr, 8);
+      W.put((uint32_t)bc.wbits, 5);
+      W.put((uint32_t)H.t, 5);
+    }
+    W.end();
+  }
+  if (!bc.any_kept) return;
+  const int t = H.t;
+  const int64_t seek = B0 + 5 + (int64_t)p * d + 18;
+  if (lane < d) {
+    LaneWriter W;
+    W.begin(out, seek + (int64_t)lane * t);
+    W.put(H.seglen[lane], t);
+    W.end();
+  }
+  const int64_t tree_pos = seek + (int64_t)d * t;
+  for (int k = lane; k * 32 < bc.tree_bits; k += 32) {
+    const int nbk = min(32, bc.tree_bits - 32 * k);
+    LaneWriter W;
+    W.begin(out, tree_pos + 32 * k);
+    W.put(bc.tree[k] >> (32 - nbk), nbk);
+    W.end();
+  }
+  for (int s = lane; s < 256; s += 32) { s_code[wid][s] = bc.code[s]; s_len[wid][s] = bc.len[s]; }
+  __syncwarp();
+  const CodeTab ct{s_code[wid], s_len[wid], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
+  const uint8_t* S = sym + b.sym;
+  int64_t off = 0;
+  int64_t pos = B0 + H.hdr_bits;
+  for (int pl = 0; pl < d; ++pl) {
+    const uint32_t km = kept_types(removed, p, pl);
+    if (!km) continue;
+    warp_segment<true>(S + off, __popc(km) * n, ct, out, pos);
+    off += region16(km, n);
+    pos += H.seglen[pl];
+  }
+}
+
+// Tile headers (little endian) and the stream offsets; capacity check.
+__global__ void k_tile_headers(const TileDev* __restrict__ tiles, int n_tiles, const int64_t* __restrict__ final_pos,
+                               const int64_t* __restrict__ item_size, const int64_t* __restrict__ totals, uint8_t* __restrict__ out,
+                               int64_t out_cap, uint64_t* __restrict__ tile_offsets, int* __restrict__ status) {
   const int ti = blockIdx.x;
   const TileDev& t = tiles[ti];
-  const int64_t tot_slots = totals[0], tot_stream = totals[1];
-  const bool scratch_ok = tot_slots <= slot_cap;
-  const int64_t total = scratch_ok ? tot_stream : tot_slots + header_total;
+  const int64_t total = totals[0];
+  const bool fits = needed_capacity(total) <= out_cap;
   if (ti == n_tiles - 1 && threadIdx.x == 0) {
-    tile_offsets[n_tiles] = (uint64_t)total;
-    if (!scratch_ok || total > out_cap) set_status(status, kStCapacity);
+    // the stream size, or the capacity it needs when it does not fit
+    tile_offsets[n_tiles] = (uint64_t)(fits ? total : needed_capacity(total));
+    if (!fits) set_status(status, kStCapacity);
   }
   const int64_t toff = final_pos[t.block_base];
   if (threadIdx.x == 0) tile_offsets[ti] = (uint64_t)toff;
-  if (!scratch_ok || total > out_cap) return;
+  if (!fits) return;
   uint8_t* o = out + toff;
   const int64_t hdr = 32 + 4 * (int64_t)t.nb;
   if (threadIdx.x == 0) {
@@ -611,44 +729,35 @@ __global__ void __launch_bounds__(256) k_assemble_tiles(const TileDev* tiles, in
     const int64_t end = final_pos[bi] + item_size[bi] - (toff + hdr);   // the first item includes the header
     for (int k = 0; k < 4; ++k) o[32 + 4 * j + k] = (uint8_t)((uint64_t)end >> (8 * k));
   }
-  for (int j = 0; j < t.nb; ++j) {
-    const int64_t bi = t.block_base + j;
-    const int64_t extra = j == 0 ? hdr : 0;
-    const int64_t size = item_size[bi] - extra;
-    const uint8_t* src = slots + slot_off[bi];
-    uint8_t* dst = out + final_pos[bi] + extra;
-    for (int64_t k = threadIdx.x; k < size; k += blockDim.x) dst[k] = src[k];
-  }
 }
 
 int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T) {
-  int launches = 0;
+  int L = 0;
   const unsigned nb = (unsigned)eb.n_blocks;
-  T->mark("encode.stats", s);
-  k_block_stats<<<nb, kCtaThreads, 0, s>>>(eb.blocks, (const uint8_t*)eb.coef, eb.stats);
+  T->mark("encode.symbols", s);
+  k_enc_symbols<<<nb, 256, 0, s>>>(eb.blocks, (const uint8_t*)eb.coef, eb.sym, eb.stats, eb.status);
   T->mark("encode.huffman", s);
-  k_block_huffman<<<(unsigned)((eb.n_blocks + 63) / 64), 64, 0, s>>>(eb.blocks, eb.stats, eb.codes, eb.slot_size, eb.n_blocks);
-  launches += 2;
+  k_block_huffman<<<(unsigned)((eb.n_blocks + 63) / 64), 64, 0, s>>>(eb.blocks, eb.stats, eb.codes, eb.n_blocks);
+  T->mark("encode.size", s);
+  const unsigned gw = (unsigned)((eb.n_blocks + kEmitWarps - 1) / kEmitWarps);
+  k_enc_size<<<gw, 32 * kEmitWarps, 0, s>>>(eb.tiles, eb.blocks, eb.n_blocks, eb.sym, eb.codes, reinterpret_cast<BlockHdr*>(eb.hdrs), eb.item_size, eb.status);
+  L += 3;
   T->mark("encode.scan", s);
-  launches += launch_exclusive_scan(eb.slot_size, eb.n_blocks, eb.slot_off, eb.scan_part, eb.totals + 0, s);
-  const size_t smem = (size_t)kStageWords * 4;
+  L += launch_exclusive_scan(eb.item_size, eb.n_blocks, eb.final_pos, eb.scan_part, eb.totals, s);
+  T->mark("encode.zero", s);
+  k_zero_stream<<<152 * 8, 256, 0, s>>>(reinterpret_cast<uint32_t*>(eb.out), eb.totals, eb.out_capacity);
   T->mark("encode.emit", s);
-  k_block_emit<<<nb, kCtaThreads, smem, s>>>(eb.tiles, eb.blocks, (const uint8_t*)eb.coef, eb.codes, eb.slot_off, eb.slot_size, eb.slots,
-                                             eb.slot_capacity, eb.totals, eb.exact_size, eb.status);
-  ++launches;
-  T->mark("encode.scan", s);
-  launches += launch_exclusive_scan(eb.exact_size, eb.n_blocks, eb.final_pos, eb.scan_part, eb.totals + 1, s);
-  return launches;
+  k_enc_emit<<<gw, 32 * kEmitWarps, 0, s>>>(eb.tiles, eb.blocks, eb.n_blocks, eb.sym, eb.codes, reinterpret_cast<const BlockHdr*>(eb.hdrs), eb.final_pos, eb.totals,
+                                           eb.out_capacity, reinterpret_cast<uint32_t*>(eb.out));
+  T->mark("encode.tile_headers", s);
+  k_tile_headers<<<eb.n_tiles, 128, 0, s>>>(eb.tiles, eb.n_tiles, eb.final_pos, eb.item_size, eb.totals, eb.out, eb.out_capacity,
+                                            eb.tile_offsets, eb.status);
+  L += 3;
+  return L;
 }
 
-int launch_encode_finalize(const EncodeBuffers& eb, int64_t header_total, cudaStream_t s) {
-  k_assemble_tiles<<<eb.n_tiles, 256, 0, s>>>(eb.tiles, eb.n_tiles, eb.final_pos, eb.exact_size, eb.slot_off, eb.totals, eb.slot_capacity,
-                                              header_total, eb.slots, eb.out, eb.out_capacity, eb.tile_offsets, eb.status);
-  return 1;
-}
+size_t enc_hdr_bytes() { return sizeof(BlockHdr); }
 
-void encode_set_attributes() {
-  cudaFuncSetAttribute(k_block_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageWords * 4);
-}
+void encode_set_attributes() {}
 
 }  // namespace isx

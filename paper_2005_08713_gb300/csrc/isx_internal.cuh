@@ -11,6 +11,7 @@ constexpr int kMaxLevels = 15;
 constexpr int kMaxD = 31;           // block bit depth field is 5 bits
 constexpr int kMaxW = 18;           // largest zero-run counter width considered (w in [2, b], b <= 18)
 constexpr int kCtaThreads = 256;    // CTA size of the per-block coding kernels
+constexpr int kMaxDConst = 31;
 
 enum DevStatus : int { kStOk = 0, kStCapacity = 2, kStCorrupt = 3, kStTimeout = 6 };
 
@@ -24,7 +25,8 @@ struct TileDev {
   int32_t fused;            // 1: transformed by the fused shared-memory kernels
   int64_t block_base;       // index of its first block
   int64_t plane_base;       // element offset of its first Mallat plane
-  int64_t coef_base;        // element offset of its first area-ordered block
+  int64_t coef_base;        // byte offset of its first area-ordered coefficient block
+  int64_t sym_base;         // byte offset of its first block's symbol region (encode)
 };
 
 // One coefficient block (Fig. 3): LL (p = 1) or HL, LH, HH (p = 3).
@@ -33,8 +35,12 @@ struct BlockDev {
   int32_t by, bx;           // cell position within the subband grid
   int32_t p, w, h;          // types and padded size (multiples of 4)
   int32_t coef16;           // coefficients stored as int16 (bits <= 12) or int32
-  int64_t coef;             // element offset of its coefficients: [type][area][8]
+  int32_t dmax;             // largest bit depth its coefficients can reach (bits + 6, at most 31)
+  int64_t coef;             // byte offset of its coefficients: [type][area][8]
+  int64_t sym;              // byte offset of its symbol region (encode)
 };
+
+__host__ __device__ inline int dmax_of_bits(int bits) { return bits + 6 < kMaxD ? bits + 6 : kMaxD; }
 
 // Per-block statistics gathered from the symbol stream (encode, pass 1).
 struct BlockStats {

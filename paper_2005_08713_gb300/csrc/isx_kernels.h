@@ -31,22 +31,22 @@ struct EncodeBuffers {
   int n_tiles;
   const BlockDev* blocks;
   int64_t n_blocks;
-  const void* coef;          // int16 or int32 per block (BlockDev::coef16)
+  const void* coef;          // int16 or int32 per block (BlockDev::coef16), byte offsets
+  uint8_t* sym;              // symbol regions (BlockDev::sym)
   BlockStats* stats;
   BlockCode* codes;
-  int64_t* slot_size;     // [n_blocks]
-  int64_t* slot_off;      // [n_blocks]
-  int64_t* exact_size;    // [n_blocks]  (item sizes for the final scan: block + its tile header when first)
-  int64_t* final_pos;     // [n_blocks]
-  int64_t* scan_part;     // scan partials
-  int64_t* totals;        // [4]: slot total, stream total
-  uint8_t* slots;
-  int64_t slot_capacity;
-  uint8_t* out;
+  void* hdrs;                // [n_blocks] enc_hdr_bytes() each
+  int64_t* item_size;        // [n_blocks] block bytes, plus its tile header for a tile's first block
+  int64_t* final_pos;        // [n_blocks]
+  int64_t* scan_part;
+  int64_t* totals;           // [1]: stream size
+  uint8_t* out;              // 4-byte aligned
   int64_t out_capacity;
-  uint64_t* tile_offsets; // [n_tiles + 1]
+  uint64_t* tile_offsets;    // [n_tiles + 1]
   int* status;
 };
+size_t enc_hdr_bytes();
+
 // Records an event between kernel groups: closes the open stage and opens
 // `name` (nullptr: none).  A no-op unless timing is enabled.
 struct StageMarks {

@@ -25,6 +25,8 @@ __global__ void k_plan_blocks(const TileDev* __restrict__ tiles, int n_tiles, in
   const TileDev t = tiles[ti];
   int64_t idx = t.block_base;
   int64_t coef = t.coef_base;
+  int64_t sym = t.sym_base;
+  const int dmax = dmax_of_bits(t.bits);
   for (int c = 0; c < t.C; ++c) {
     for (int lv = 0; lv <= t.L; ++lv) {
       int level = lv == 0 ? 0 : t.L + 1 - lv;   // 0 (LL), then L, L-1, ..., 1
@@ -39,7 +41,10 @@ __global__ void k_plan_blocks(const TileDev* __restrict__ tiles, int n_tiles, in
           b.h = pad4(min(kCell, gh - kCell * by));
           b.coef = coef;
           b.coef16 = t.bits <= 12 ? 1 : 0;
+          b.dmax = dmax;
+          b.sym = sym;
           coef += (int64_t)p * b.w * b.h * (b.coef16 ? 2 : 4);
+          sym += (int64_t)dmax * (((int64_t)p * b.w * b.h / 8 + 15) & ~15LL);
           out[idx++] = b;
         }
     }
