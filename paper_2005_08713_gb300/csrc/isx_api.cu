@@ -498,7 +498,7 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   if (T.on && !T.pending.empty()) T.collect();
   int L = launch_decode_blocks(db, s, &T);
   T.mark("decode.inverse_transform", s);
-  L += launch_fused_inverse(d_tiles, d_task, n_fused, max_plane_bytes, z, (int32_t*)(ar + o_A), s);
+  L += launch_fused_inverse(d_tiles, d_task, n_fused, max_plane_bytes, db, s);
   if (n_fused < nsel) {
     T.mark("decode.inverse_global", s);
     L += launch_inverse_transform(d_tiles, nsel, max_levels, z, max_dim, (int32_t*)(ar + o_A), (int32_t*)(ar + o_B), s);

@@ -405,6 +405,7 @@ __global__ void __launch_bounds__(256) k_dec_rebuild(const TileDev* __restrict__
   const DecInfo di = info[blockIdx.x];
   if (b.p == 0 || di.d == 0) return;
   const TileDev& t = tiles[b.tile];
+  if (t.fused) return;   // rebuilt inside the fused inverse transform
   const int n = b.w * b.h / 8, na = b.p * n;
   if (threadIdx.x == 0) {
     int64_t off = sym_off[blockIdx.x];

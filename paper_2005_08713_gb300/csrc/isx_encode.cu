@@ -255,165 +255,240 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
 }
 
 // ------------------------------------------------------------- pass 2
-// Two-queue Huffman construction: leaves with f > 0 sorted ascending by
-// (f, symbol); each merge takes the lighter queue front twice, the leaf
-// queue first on equal weight; first taken = left child (bit 0).
-struct Huff {
-  uint32_t key[256];     // sorted leaves: (f << 8) | symbol
-  uint32_t wgt[511];
-  uint16_t kid[255][2];
-  uint16_t parent[511];
-  int nl, root;
+// Two-queue Huffman construction (one warp per block): leaves with f > 0
+// sorted ascending by (f, symbol) (warp bitonic sort in registers); each
+// merge takes the lighter queue front twice, the leaf queue first on equal
+// weight; the first taken becomes the left child (bit 0).
+constexpr int kHuffWarps = 8;
+constexpr uint32_t kInf = 0xffffffffu;
+
+struct HuffWarp {
+  uint32_t f[256];        // frequencies
+  uint32_t leaf[256];     // sorted leaves: (f << 8) | symbol
+  uint32_t iw[256];       // internal node weights in creation order
+  uint16_t kid[256][2];   // children of internal node i (leaves 0..nl-1, internal nl + i)
+  uint16_t parent[512];   // parent node id | 0x8000 for a right child
+  uint32_t tree[81];
+  int nl;
 };
 
-__device__ void sort_keys(uint32_t* a, uint32_t* tmp, int n) {
-  // bottom-up merge sort, ascending
-  uint32_t* src = a;
-  uint32_t* dst = tmp;
-  for (int width = 1; width < n; width <<= 1) {
-    for (int lo = 0; lo < n; lo += 2 * width) {
-      int mid = min(lo + width, n), hi = min(lo + 2 * width, n);
-      int i = lo, j = mid, k = lo;
-      while (i < mid && j < hi) dst[k++] = src[i] <= src[j] ? src[i++] : src[j++];
-      while (i < mid) dst[k++] = src[i++];
-      while (j < hi) dst[k++] = src[j++];
+// Sorts 8 keys per lane (element lane*8 + r) ascending across the warp.
+__device__ inline void warp_bitonic_256(uint32_t (&k)[8]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 256; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= 8) {
+        const int lstride = stride >> 3;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int i = lane * 8 + r;
+          const bool up = (i & size) == 0;
+          const uint32_t other = __shfl_xor_sync(0xffffffffu, k[r], lstride);
+          const bool lower = (lane & lstride) == 0;
+          const uint32_t mn = min(k[r], other), mx = max(k[r], other);
+          k[r] = (lower == up) ? mn : mx;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int pr = r ^ stride;
+          if (pr > r) {
+            const int i = lane * 8 + r;
+            const bool up = (i & size) == 0;
+            const uint32_t a = k[r], b = k[pr];
+            k[r] = up ? min(a, b) : max(a, b);
+            k[pr] = up ? max(a, b) : min(a, b);
+          }
+        }
+      }
     }
-    uint32_t* t = src; src = dst; dst = t;
   }
-  if (src != a)
-    for (int i = 0; i < n; ++i) a[i] = src[i];
 }
 
-__device__ void huff_merge(Huff& H, const uint32_t* f) {
-  int nl = 0;
-  for (int s = 0; s < 256; ++s)
-    if (f[s]) H.key[nl++] = (f[s] << 8) | (uint32_t)s;
-  sort_keys(H.key, H.wgt, nl);
-  for (int i = 0; i < nl; ++i) H.wgt[i] = H.key[i] >> 8;
-  int qa = 0, qb = nl, nxt = nl;
-  for (int st = 0; st < nl - 1; ++st) {
-    int a, b;
-    if (qa < nl && (qb >= nxt || H.wgt[qa] <= H.wgt[qb])) a = qa++; else a = qb++;
-    if (qa < nl && (qb >= nxt || H.wgt[qa] <= H.wgt[qb])) b = qa++; else b = qb++;
-    H.wgt[nxt] = H.wgt[a] + H.wgt[b];
-    H.kid[nxt - nl][0] = (uint16_t)a;
-    H.kid[nxt - nl][1] = (uint16_t)b;
-    H.parent[a] = (uint16_t)nxt;
-    H.parent[b] = (uint16_t)nxt;
-    ++nxt;
+// Builds the code of the frequencies in H.f; returns the root id.
+__device__ int huff_build_warp(HuffWarp& H) {
+  const int lane = threadIdx.x & 31;
+  uint32_t k[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int sym = lane * 8 + r;
+    const uint32_t fr = H.f[sym];
+    k[r] = fr ? ((fr << 8) | (uint32_t)sym) : kInf;
   }
-  H.nl = nl;
-  H.root = nl <= 1 ? 0 : nxt - 1;
+  warp_bitonic_256(k);
+  int cnt = 0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    H.leaf[lane * 8 + r] = k[r];
+    cnt += k[r] != kInf;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  const int nl = cnt;
+  __syncwarp();
+  if (lane == 0) {
+    H.nl = nl;
+    int qa = 0, qb = 0, ni = 0;
+    uint32_t wl = nl > 0 ? H.leaf[0] >> 8 : kInf, wi = kInf;
+    for (int st = 0; st < nl - 1; ++st) {
+      int a, b;
+      uint32_t wa, wb;
+      if (wl <= wi) { a = qa; wa = wl; ++qa; wl = qa < nl ? H.leaf[qa] >> 8 : kInf; }
+      else { a = nl + qb; wa = wi; ++qb; wi = qb < ni ? H.iw[qb] : kInf; }
+      if (wl <= wi) { b = qa; wb = wl; ++qa; wl = qa < nl ? H.leaf[qa] >> 8 : kInf; }
+      else { b = nl + qb; wb = wi; ++qb; wi = qb < ni ? H.iw[qb] : kInf; }
+      const uint32_t wn = wa + wb;
+      H.iw[ni] = wn;
+      H.kid[ni][0] = (uint16_t)a;
+      H.kid[ni][1] = (uint16_t)b;
+      H.parent[a] = (uint16_t)(nl + ni);
+      H.parent[b] = (uint16_t)((nl + ni) | 0x8000);
+      if (qb == ni) wi = wn;   // the internal queue was empty: the new node is its front
+      ++ni;
+    }
+  }
+  __syncwarp();
+  return nl <= 1 ? 0 : 2 * nl - 2;
 }
 
-__device__ int huff_depth_of(const Huff& H, int sym) {
-  if (H.nl <= 1) return 0;
-  int leaf = -1;
-  for (int i = 0; i < H.nl; ++i)
-    if ((int)(H.key[i] & 255u) == sym) { leaf = i; break; }
-  if (leaf < 0) return 0;
-  int dep = 0;
-  for (int v = leaf; v != H.root; v = H.parent[v]) ++dep;
-  return dep;
+__device__ inline void leaf_code(const HuffWarp& H, int leaf, int root, uint32_t* code, int* len) {
+  uint32_t c = 0;
+  int l = 0;
+  for (int v = leaf; v != root && l < 40; ++l) {
+    const uint32_t p = H.parent[v];
+    c |= (p >> 15) << l;
+    v = p & 0x7fff;
+  }
+  *code = c;
+  *len = l;
 }
 
-__device__ inline void put_bits_local(uint32_t* words, int pos, uint32_t v, int nb) {
-  if (nb <= 0) return;
-  int wi = pos >> 5, off = pos & 31;
-  uint64_t vv = (uint64_t)(v & (nb == 32 ? 0xffffffffu : ((1u << nb) - 1u))) << (64 - off - nb);
-  words[wi] |= (uint32_t)(vv >> 32);
-  if ((uint32_t)vv) words[wi + 1] |= (uint32_t)vv;
-}
-
-__global__ void __launch_bounds__(64) k_block_huffman(const BlockDev* __restrict__ blocks, const BlockStats* __restrict__ stats,
-                                                      BlockCode* __restrict__ codes, int64_t nb) {
-  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * kHuffWarps) k_block_huffman(const BlockDev* __restrict__ blocks, const BlockStats* __restrict__ stats,
+                                                                  BlockCode* __restrict__ codes, int64_t nb) {
+  __shared__ HuffWarp hw[kHuffWarps];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t bi = (int64_t)blockIdx.x * kHuffWarps + wid;
   if (bi >= nb) return;
+  HuffWarp& H = hw[wid];
   const BlockStats& st = stats[bi];
   const BlockDev b = blocks[bi];
   BlockCode& bc = codes[bi];
   const int d = st.d, p = b.p;
   const uint32_t n_sym = st.n_sym;
-  bc.d = d;
-  bc.p = p;
-  for (int t = 0; t < 3; ++t) bc.removed[t] = st.removed[t];
   const int t0 = bitlen_u32((uint32_t)(p * b.w * b.h / 8)) - 1 + 5;
-  bc.t0 = t0;
+  if (lane == 0) {
+    bc.d = d;
+    bc.p = p;
+    for (int t = 0; t < 3; ++t) bc.removed[t] = st.removed[t];
+    bc.t0 = t0;
+  }
   if (n_sym == 0) {
-    bc.any_kept = 0;
-    bc.token_bits = 0;
-    bc.tree_bits = 0;
-    bc.czr = 0; bc.wbits = 0;
+    if (lane == 0) {
+      bc.any_kept = 0;
+      bc.token_bits = 0;
+      bc.tree_bits = 0;
+      bc.czr = 0;
+      bc.wbits = 0;
+    }
     return;
   }
-  bc.any_kept = 1;
-  uint32_t f[256];
-  for (int s = 0; s < 256; ++s) f[s] = st.hist[s];
-  int czr = 1;
-  for (int s = 2; s < 256; ++s)
-    if (f[s] < f[czr]) czr = s;
-  const uint32_t lit_czr = f[czr];
-  // provisional code: every run counts once for C_zr
-  f[czr] = lit_czr + st.n_runs;
-  Huff H;
-  huff_merge(H, f);
-  const int l = f[czr] > 0 ? huff_depth_of(H, czr) : 0;
+  // C_zr: least frequent of 1..255, smallest on ties
+  uint32_t best = kInf;
+  for (int s = lane; s < 256; s += 32) {
+    const uint32_t fr = st.hist[s];
+    H.f[s] = fr;
+    if (s >= 1) best = min(best, (fr << 8) | (uint32_t)s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+  const int czr = (int)(best & 0xffu);
+  const uint32_t lit_czr = best >> 8;
+  __syncwarp();
+  // provisional code: every run counts once for C_zr; l = C_zr's code length
+  if (lane == 0) H.f[czr] = lit_czr + st.n_runs;
+  __syncwarp();
+  int l = 0;
+  {
+    const int root = huff_build_warp(H);
+    if (H.f[czr] > 0 && H.nl > 1) {
+      for (int i = lane; i < H.nl; i += 32)
+        if ((int)(H.leaf[i] & 0xffu) == czr) {
+          uint32_t c;
+          int len;
+          leaf_code(H, i, root, &c, &len);
+          l = len;
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) l = max(l, __shfl_xor_sync(0xffffffffu, l, o));
+    }
+  }
   // Eq. 3 (reading): w minimises (w + l) * (#C_zr tokens at width w) over [2, b]
   int bmax = n_sym > 1 ? bitlen_u32(n_sym - 1) : 0;
   if (bmax < 2) bmax = 2;
   int wbest = 2;
-  uint64_t best = ~0ull;
+  uint64_t bestc = ~0ull;
   for (int w = 2; w <= bmax; ++w) {
-    uint64_t pairs = (uint64_t)lit_czr + st.n_runs + st.extra[w];
-    uint64_t cost = (uint64_t)(w + l) * pairs;
-    if (cost < best) { best = cost; wbest = w; }
+    const uint64_t pairs = (uint64_t)lit_czr + st.n_runs + st.extra[w];
+    const uint64_t cost = (uint64_t)(w + l) * pairs;
+    if (cost < bestc) { bestc = cost; wbest = w; }
   }
-  f[czr] = lit_czr + st.n_runs + st.extra[wbest];
-  huff_merge(H, f);
-  // codes, top down (children were created before their parents)
-  uint32_t ncode[511];
-  uint8_t ndep[511];
-  const int nl = H.nl, nn = nl > 1 ? 2 * nl - 1 : 1;
-  ncode[H.root] = 0;
-  ndep[H.root] = 0;
-  for (int i = nn - 1; i >= nl; --i) {
-    for (int side = 0; side < 2; ++side) {
-      int c = H.kid[i - nl][side];
-      ncode[c] = (ncode[i] << 1) | (uint32_t)side;
-      ndep[c] = (uint8_t)(ndep[i] + 1);
+  __syncwarp();
+  if (lane == 0) H.f[czr] = lit_czr + st.n_runs + st.extra[wbest];
+  __syncwarp();
+  const int root = huff_build_warp(H);
+  const int nl = H.nl;
+  // codes: every leaf walks up to the root
+  for (int s = lane; s < 256; s += 32) { bc.code[s] = 0; bc.len[s] = 0; }
+  __syncwarp();
+  uint64_t tb = 0;
+  for (int i = lane; i < nl; i += 32) {
+    uint32_t c;
+    int len;
+    leaf_code(H, i, root, &c, &len);
+    const int sym = (int)(H.leaf[i] & 0xffu);
+    bc.code[sym] = c;
+    bc.len[sym] = (uint8_t)len;
+    tb += (uint64_t)H.f[sym] * len;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tb += __shfl_xor_sync(0xffffffffu, tb, o);
+  // preorder tree (Fig. 3): 0 = internal node, 1 + 8-bit symbol = leaf
+  if (lane == 0) {
+    for (int k = 0; k < 81; ++k) H.tree[k] = 0;
+    int stack[40];
+    int sp = 0, pos = 0;
+    stack[sp++] = root;
+    while (sp > 0) {
+      const int v = stack[--sp];
+      if (v < nl) {
+        const uint32_t val = 0x100u | (H.leaf[v] & 0xffu);
+        const int wi = pos >> 5, off = pos & 31;
+        const uint64_t vv = (uint64_t)val << (64 - off - 9);
+        H.tree[wi] |= (uint32_t)(vv >> 32);
+        H.tree[wi + 1] |= (uint32_t)vv;
+        pos += 9;
+      } else {
+        ++pos;   // a 0 bit
+        const int i = v - nl;
+        if (sp < 38) {
+          stack[sp++] = H.kid[i][1];
+          stack[sp++] = H.kid[i][0];
+        }
+      }
     }
+    bc.tree_bits = pos;
   }
-  for (int s = 0; s < 256; ++s) { bc.code[s] = 0; bc.len[s] = 0; }
-  uint64_t token_bits = 0;
-  for (int i = 0; i < nl; ++i) {
-    int s = H.key[i] & 255u;
-    bc.code[s] = ncode[i];
-    bc.len[s] = ndep[i];
-    token_bits += (uint64_t)f[s] * ndep[i];
+  __syncwarp();
+  for (int k = lane; k < 80; k += 32) bc.tree[k] = H.tree[k];
+  if (lane == 0) {
+    bc.any_kept = 1;
+    bc.czr = czr;
+    bc.wbits = wbest;
+    bc.token_bits = tb + (uint64_t)wbest * H.f[czr];
   }
-  token_bits += (uint64_t)wbest * f[czr];
-  // preorder tree (Fig. 3): subtree sizes bottom up, offsets top down
-  uint16_t* sz = H.parent;            // reuse: parents are no longer needed
-  uint16_t off[511];
-  for (int i = 0; i < nl; ++i) sz[i] = 9;
-  for (int i = nl; i < nn; ++i) sz[i] = (uint16_t)(1 + sz[H.kid[i - nl][0]] + sz[H.kid[i - nl][1]]);
-  off[H.root] = 0;
-  for (int i = nn - 1; i >= nl; --i) {
-    int a = H.kid[i - nl][0], c = H.kid[i - nl][1];
-    off[a] = (uint16_t)(off[i] + 1);
-    off[c] = (uint16_t)(off[i] + 1 + sz[a]);
-  }
-  uint32_t tw[81];
-  for (int k = 0; k < 81; ++k) tw[k] = 0;
-  for (int i = 0; i < nl; ++i) put_bits_local(tw, off[i], 0x100u | (H.key[i] & 255u), 9);
-  for (int k = 0; k < 80; ++k) bc.tree[k] = tw[k];
-  const int tree_bits = sz[H.root];
-  bc.tree_bits = tree_bits;
-  bc.czr = czr;
-  bc.wbits = wbest;
-  bc.token_bits = token_bits;
 }
-
 
 // ------------------------------------------------------------- pass 3/4
 struct CodeTab {
@@ -737,7 +812,8 @@ int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T)
   T->mark("encode.symbols", s);
   k_enc_symbols<<<nb, 256, 0, s>>>(eb.blocks, (const uint8_t*)eb.coef, eb.sym, eb.stats, eb.status);
   T->mark("encode.huffman", s);
-  k_block_huffman<<<(unsigned)((eb.n_blocks + 63) / 64), 64, 0, s>>>(eb.blocks, eb.stats, eb.codes, eb.n_blocks);
+  k_block_huffman<<<(unsigned)((eb.n_blocks + kHuffWarps - 1) / kHuffWarps), 32 * kHuffWarps, 0, s>>>(eb.blocks, eb.stats, eb.codes,
+                                                                                                    eb.n_blocks);
   T->mark("encode.size", s);
   const unsigned gw = (unsigned)((eb.n_blocks + kEmitWarps - 1) / kEmitWarps);
   k_enc_size<<<gw, 32 * kEmitWarps, 0, s>>>(eb.tiles, eb.blocks, eb.n_blocks, eb.sym, eb.codes, reinterpret_cast<BlockHdr*>(eb.hdrs), eb.item_size, eb.status);

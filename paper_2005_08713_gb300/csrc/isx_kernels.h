@@ -15,8 +15,6 @@ int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t
                        cudaStream_t s);
 int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const BlockDev* d_blocks,
                          void* coef, cudaStream_t s);
-int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, int z, int32_t* planes,
-                         cudaStream_t s);
 bool fused_tile(int w, int h, int bits);
 void transform_set_attributes();
 int launch_quantise_planes(const TileDev* d_tiles, int n_tiles, const int32_t* planes, int32_t* out, cudaStream_t s);
@@ -82,6 +80,8 @@ struct DecodeBuffers {
   int* status;
 };
 int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T);
+int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const DecodeBuffers& db,
+                         cudaStream_t s);
 size_t dec_table_bytes();
 
 }  // namespace isx

@@ -371,13 +371,19 @@ __device__ inline void ilv_pos(int L, int level, int type, int y, int x, int z, 
 // One in-place lifting step along one axis of the grid at stride s:
 // n samples per line, `lines` lines; odd = predict (odd positions) or update
 // (even positions); inverse undoes the step.  Mirror at both ends.
+// Work items are split over a power-of-two fast dimension (no divisions):
+// across columns for vertical steps, along the line for horizontal ones.
 __device__ inline void lift_step(int16_t* P, int pitch, int n, int lines, int s, bool vertical, bool odd, bool inverse) {
   const int nt = odd ? n / 2 : (n + 1) / 2;
-  const int total = nt * lines;
+  const int fast = vertical ? lines : nt, slow = vertical ? nt : lines;
+  const int fbits = 32 - __clz(fast - 1 > 0 ? fast - 1 : 0);   // ceil(log2(fast))
+  const int fmask = (1 << fbits) - 1;
+  const int total = slow << fbits;
   for (int it = threadIdx.x; it < total; it += blockDim.x) {
-    // consecutive threads walk along a row: across columns (vertical) or along the line (horizontal)
-    const int line = vertical ? it % lines : it / nt;
-    const int k = vertical ? it / lines : it % nt;
+    const int fi = it & fmask, si = it >> fbits;
+    if (fi >= fast) continue;
+    const int line = vertical ? fi : si;
+    const int k = vertical ? si : fi;
     const int r = odd ? 2 * k + 1 : 2 * k;
     const int rm = r - 1 >= 0 ? r - 1 : r + 1;
     const int rp = r + 1 < n ? r + 1 : r - 1;
@@ -401,12 +407,32 @@ __device__ inline void lift_step(int16_t* P, int pitch, int n, int lines, int s,
 
 __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
                                                                  const BlockDev* __restrict__ blocks, uint8_t* __restrict__ coef) {
-  extern __shared__ int16_t P[];
+  extern __shared__ __align__(16) int16_t P[];
   const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
   const TileDev& t = tiles[tt];
   if (c >= t.C) return;
   const int w = t.w, h = t.h, pitch = w;
   // load + colour transform of channel c
+  const bool quad = t.C == 3 && t.bits <= 8 && (w & 3) == 0 && (t.pitch & 3) == 0 && ((reinterpret_cast<uintptr_t>(t.pixels) & 3) == 0);
+  if (quad) {
+    // four pixels (12 bytes, three aligned words) per thread
+    const int qw = w >> 2;
+    for (int e = threadIdx.x; e < qw * h; e += blockDim.x) {
+      const int y = e / qw, x4 = (e - y * qw) << 2;
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(t.pixels + (int64_t)y * t.pitch + 3 * x4);
+      const uint32_t w0 = src[0], w1 = src[1], w2 = src[2];
+      const int32_t R[4] = {(int32_t)(w0 & 255), (int32_t)((w0 >> 24) & 255), (int32_t)((w1 >> 16) & 255), (int32_t)((w2 >> 8) & 255)};
+      const int32_t G[4] = {(int32_t)((w0 >> 8) & 255), (int32_t)(w1 & 255), (int32_t)((w1 >> 24) & 255), (int32_t)((w2 >> 16) & 255)};
+      const int32_t B[4] = {(int32_t)((w0 >> 16) & 255), (int32_t)((w1 >> 8) & 255), (int32_t)(w2 & 255), (int32_t)((w2 >> 24) & 255)};
+      int32_t v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = c == 0 ? (R[q] + 2 * G[q] + B[q]) >> 2 : c == 1 ? B[q] - G[q] : R[q] - G[q];
+      uint2 pk;
+      pk.x = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+      pk.y = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+      *reinterpret_cast<uint2*>(P + y * pitch + x4) = pk;
+    }
+  } else
   for (int e = threadIdx.x; e < w * h; e += blockDim.x) {
     const int y = e / w, x = e - y * w;
     const uint8_t* row = t.pixels + (int64_t)y * t.pitch;
@@ -472,36 +498,80 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   }
 }
 
-// Decode side: the level-z Mallat plane (int32, written by the block
-// rebuild) is loaded into the interleaved int16 layout, lifted back from
-// level L to level z and written back row-major as the LL_z image.
+// Decode side, fused with the coefficient rebuild: every block of the tile
+// channel needed at level z (the LL and the levels above z) is rebuilt from
+// its decoded symbol planes (sign plane, magnitude bits d-2 .. 0),
+// dequantised at the bin midpoint and placed into the interleaved int16
+// layout; the CTA then lifts back from level L to level z and writes the
+// LL_z image row-major (int32) for the colour store.
 __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
-                                                                 int z, int32_t* __restrict__ planes) {
-  extern __shared__ int16_t P[];
+                                                                 const BlockDev* __restrict__ blocks, const DecInfo* __restrict__ info,
+                                                                 const int64_t* __restrict__ sym_off, const uint8_t* __restrict__ sym,
+                                                                 const int64_t* __restrict__ sym_total, int64_t sym_cap, int z,
+                                                                 int32_t* __restrict__ planes) {
+  extern __shared__ __align__(16) int16_t P[];
+  __shared__ int64_t s_poff[32];
+  __shared__ uint32_t s_km[32];
   const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
   const TileDev& t = tiles[tt];
-  if (c >= t.C || t.L <= z) return;
+  if (c >= t.C || *sym_total > sym_cap) return;
   const int zw = level_dim(t.w, z), zh = level_dim(t.h, z), pitch = zw;
-  int32_t* g = planes + t.plane_base + (int64_t)c * zw * zh;
-  // Mallat -> interleaved: walk the subbands of levels L .. z+1 and the LL
-  for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
-    const int y = e / zw, x = e - y * zw;
-    // which subband holds Mallat position (x, y) of the level-z region
-    int level = 0, type = 0, sy = y, sx = x;
-    for (int l = z + 1; l <= t.L; ++l) {
-      const int pw = level_dim(t.w, l - 1), ph = level_dim(t.h, l - 1);
-      const int lw = (pw + 1) >> 1, lh = (ph + 1) >> 1;
-      if (x >= lw || y >= lh) {
-        level = l;
-        type = (y < lh) ? 0 : (x < lw ? 1 : 2);
-        sx = x >= lw ? x - lw : x;
-        sy = y >= lh ? y - lh : y;
-        break;
+  const int64_t b0 = t.block_base + (int64_t)c * (t.nb / t.C), b1 = b0 + t.nb / t.C;
+  for (int64_t bi = b0; bi < b1; ++bi) {
+    const BlockDev b = blocks[bi];
+    const DecInfo di = info[bi];
+    if (b.p == 0 || di.d == 0) continue;   // unreadable block: status already set
+    const int n = b.w * b.h / 8, na = b.p * n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t off = sym_off[bi];
+      for (int pl = 0; pl < di.keep; ++pl) {
+        uint32_t km = 0;
+        for (int ty = 0; ty < b.p; ++ty)
+          if (!((di.removed[ty] >> pl) & 1u)) km |= 1u << ty;
+        s_km[pl] = km;
+        s_poff[pl] = off;
+        off += ((int64_t)__popc(km) * n + 15) & ~15LL;
       }
     }
-    int py, px;
-    ilv_pos(t.L, level, type, sy, sx, z, &py, &px);
-    P[py * pitch + px] = (int16_t)g[e];
+    __syncthreads();
+    const int q = qlog2_of(t, b.level);
+    const int32_t delta = 1 << q;
+    const int d = di.d;
+    for (int a = threadIdx.x; a < na; a += blockDim.x) {
+      const int type = a / n, k = a - type * n;
+      uint32_t mag[8], neg = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) mag[e] = 0;
+      for (int pl = 0; pl < di.keep; ++pl) {
+        const uint32_t km = s_km[pl];
+        if (!((km >> type) & 1u)) continue;
+        const int ki = __popc(km & ((1u << type) - 1u));
+        const uint32_t sv = sym[s_poff[pl] + (int64_t)ki * n + k];
+        if (!sv) continue;
+        if (pl == 0) {
+          neg = sv;
+        } else {
+          const int sh = d - 1 - pl;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) mag[e] |= ((sv >> e) & 1u) << sh;
+        }
+      }
+      int i, j;
+      area_ij(k, b.w, &i, &j);
+      int sx, sy, sw, sh;
+      subband_rect(t.w, t.h, t.L, b.level, type, &sx, &sy, &sw, &sh);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int yy = kCell * b.by + i + (e >> 2), xx = kCell * b.bx + j + (e & 3);
+        if (yy >= sh || xx >= sw) continue;
+        const int32_t m = (int32_t)mag[e];
+        const int32_t v = m == 0 ? 0 : m * delta + (delta >> 1);
+        int py, px;
+        ilv_pos(t.L, b.level, type, yy, xx, z, &py, &px);
+        P[py * pitch + px] = (int16_t)(((neg >> e) & 1u) ? -v : v);
+      }
+    }
   }
   __syncthreads();
   for (int l = t.L - 1; l >= z; --l) {
@@ -519,6 +589,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
       __syncthreads();
     }
   }
+  int32_t* g = planes + t.plane_base + (int64_t)c * zw * zh;
   for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) g[e] = P[e];
 }
 
@@ -553,10 +624,11 @@ int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int
   return 1;
 }
 
-int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, int z, int32_t* planes,
+int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const DecodeBuffers& db,
                          cudaStream_t s) {
   if (n_fused == 0) return 0;
-  k_inv_tile_smem<<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, z, planes);
+  k_inv_tile_smem<<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, db.blocks, db.info, db.sym_off, db.sym,
+                                                                      db.totals, db.sym_cap, db.z, db.planes);
   return 1;
 }
 
