@@ -212,7 +212,7 @@ isx_status plan_encode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n, bool
     d.plane_base = d.fused ? 0 : P.plane_total;
     if (d.fused) {
       ctx->h_task[P.n_fused++] = i;
-      P.max_plane_bytes = std::max(P.max_plane_bytes, t.width * t.height * 2);
+      P.max_plane_bytes = std::max(P.max_plane_bytes, fused_plane_bytes(t.width, t.height));
     } else {
       P.plane_total += (int64_t)t.channels * t.width * t.height;
     }
@@ -367,7 +367,7 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   size_t o_stats = cv.take(sizeof(BlockStats) * NB);
   size_t o_codes = cv.take(sizeof(BlockCode) * NB);
   size_t o_hdrs = cv.take(enc_hdr_bytes() * NB);
-  size_t o_is = cv.take(8 * NB), o_fp = cv.take(8 * NB);
+  size_t o_is = cv.take(8 * NB), o_fp = cv.take(8 * NB), o_perm = cv.take(8 * NB), o_bucket = cv.take(8 * 64);
   size_t o_part = cv.take(8 * n_part), o_tot = cv.take(64);
   st = ensure_arena(ctx, cv.used);
   if (st != ISX_OK) return st;
@@ -401,6 +401,7 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   eb.hdrs = ar + o_hdrs;
   eb.item_size = (int64_t*)(ar + o_is); eb.final_pos = (int64_t*)(ar + o_fp);
   eb.scan_part = (int64_t*)(ar + o_part); eb.totals = (int64_t*)(ar + o_tot);
+  eb.bucket = (int64_t*)(ar + o_bucket); eb.perm = (int64_t*)(ar + o_perm);
   eb.out = (uint8_t*)d_out; eb.out_capacity = (int64_t)out_capacity;
   eb.tile_offsets = d_tile_offsets; eb.status = ctx->d_status;
   L += launch_encode_coding(eb, s, &T);
@@ -451,7 +452,7 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
     d.fused = fused_tile(zw, zh, t.bits) ? 1 : 0;
     if (d.fused) {
       ctx->h_task[n_fused++] = nsel;
-      max_plane_bytes = std::max(max_plane_bytes, zw * zh * 2);
+      max_plane_bytes = std::max(max_plane_bytes, fused_plane_bytes(zw, zh));
     }
     ctx->h_index[nsel] = i;
     ++nsel;

@@ -257,36 +257,102 @@ __global__ void k_dec_tables(const BlockDev* __restrict__ blocks, int64_t nb, co
   sym_bytes[bi] = bytes;
 }
 
-// Segment items are bucketed by (level, plane) so that a warp decodes 32
-// segments of similar length.
-constexpr int kBuckets = 16 * 32;
+// Blocks are processed in groups of kGroup of one level (counting sort by
+// level), so that the segments a CTA decodes have similar lengths.
+constexpr int kLevels = 16;
+constexpr int kGroup = 32;
 
-__global__ void k_dec_item_count(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
-                                 const DecTab* __restrict__ tabs, int64_t* __restrict__ bucket) {
+__global__ void k_dec_level_count(const BlockDev* __restrict__ blocks, int64_t nb, int64_t* __restrict__ cnt) {
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (bi >= nb) return;
-  const BlockDev b = blocks[bi];
-  const DecInfo di = info[bi];
-  if (b.p == 0 || di.d == 0 || tabs[bi].nnodes == 0) return;
-  for (int pl = 0; pl < di.keep; ++pl)
-    if (kept_mask(di.removed, b.p, pl)) atomicAdd(reinterpret_cast<unsigned long long*>(&bucket[b.level * 32 + pl]), 1ull);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[blocks[bi].level]), 1ull);
 }
 
-__global__ void k_dec_item_fill(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
-                                const DecTab* __restrict__ tabs, const int64_t* __restrict__ bucket_off, int64_t* __restrict__ fill,
-                                int64_t* __restrict__ items) {
+__global__ void k_dec_level_fill(const BlockDev* __restrict__ blocks, int64_t nb, const int64_t* __restrict__ off, int64_t* __restrict__ fill,
+                                 int64_t* __restrict__ perm) {
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (bi >= nb) return;
-  const BlockDev b = blocks[bi];
-  const DecInfo di = info[bi];
-  if (b.p == 0 || di.d == 0 || tabs[bi].nnodes == 0) return;
-  for (int pl = 0; pl < di.keep; ++pl) {
-    if (!kept_mask(di.removed, b.p, pl)) continue;
-    const int k = b.level * 32 + pl;
-    const int64_t pos = bucket_off[k] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&fill[k]), 1ull);
-    items[pos] = (bi << 5) | pl;
+  const int l = blocks[bi].level;
+  perm[off[l] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&fill[l]), 1ull)] = bi;
+}
+
+// Double-buffered MSB-first reader: 16-byte chunks are requested one chunk
+// ahead of use; bytes outside the block read as 0.
+struct BitPf {
+  const uint8_t* p;
+  int64_t nbytes;
+  int64_t cbyte;       // block offset of the next chunk to request (16-byte aligned in memory)
+  uint4 nxt;
+  uint32_t a0, a1, a2, a3;
+  int avail;
+  uint64_t buf;
+  int nbuf;
+  int64_t pos;
+  __device__ uint4 chunk(int64_t off) const {
+    if (off >= 0 && off + 16 <= nbytes) return __ldg(reinterpret_cast<const uint4*>(p + off));
+    uint32_t w[4];
+    for (int q = 0; q < 4; ++q) {
+      uint32_t v = 0;
+      for (int k = 0; k < 4; ++k) {
+        const int64_t o = off + 4 * q + k;
+        v |= (uint32_t)(o >= 0 && o < nbytes ? p[o] : 0) << (8 * k);
+      }
+      w[q] = v;
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
   }
-}
+  __device__ uint32_t next_word() {
+    if (avail == 0) {
+      a0 = __byte_perm(nxt.x, 0, 0x0123);
+      a1 = __byte_perm(nxt.y, 0, 0x0123);
+      a2 = __byte_perm(nxt.z, 0, 0x0123);
+      a3 = __byte_perm(nxt.w, 0, 0x0123);
+      avail = 4;
+      nxt = chunk(cbyte);
+      cbyte += 16;
+    }
+    const uint32_t w = a0;
+    a0 = a1; a1 = a2; a2 = a3;
+    --avail;
+    return w;
+  }
+  __device__ void seek(const uint8_t* base, int64_t n, int64_t bitpos) {
+    p = base;
+    nbytes = n;
+    const int64_t byte = bitpos >> 3;
+    const int mis = (int)(reinterpret_cast<uintptr_t>(p + byte) & 15);
+    cbyte = byte - mis;
+    nxt = chunk(cbyte);
+    cbyte += 16;
+    avail = 0;
+    buf = (uint64_t)next_word() << 32;
+    buf |= next_word();
+    nbuf = 64;
+    int drop = mis * 8 + (int)(bitpos & 7);
+    while (drop >= 32) {   // skip whole words of the first chunk
+      buf = (buf << 32) | next_word();
+      drop -= 32;
+    }
+    buf <<= drop;
+    nbuf = 64 - drop;
+    pos = bitpos;
+  }
+  __device__ uint32_t peek(int n) const { return n ? (uint32_t)(buf >> (64 - n)) : 0u; }
+  __device__ void skip(int n) {   // n <= 32
+    buf <<= n;
+    nbuf -= n;
+    pos += n;
+    if (nbuf <= 32) {
+      buf |= (uint64_t)next_word() << (32 - nbuf);
+      nbuf += 32;
+    }
+  }
+  __device__ uint32_t get(int n) {
+    const uint32_t v = peek(n);
+    skip(n);
+    return v;
+  }
+};
 
 // 16-byte symbol writer of one thread.
 struct SymOut {
@@ -318,6 +384,41 @@ struct SymOut {
   }
 };
 
+// Segment items (block << 5 | plane) are bucketed by the bit length of the
+// segment (its seektable entry), longest first, so that the 32 segments of
+// a warp take similar time and the longest start first.
+constexpr int kLenBuckets = 33;
+
+__device__ inline int len_bucket(uint32_t seglen) { return 32 - (seglen ? (32 - __clz(seglen)) : 0); }   // longest -> 0
+
+__global__ void k_dec_item_count(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
+                                 const DecTab* __restrict__ tabs, int64_t* __restrict__ bucket) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= nb) return;
+  const BlockDev b = blocks[bi];
+  const DecInfo di = info[bi];
+  if (b.p == 0 || di.d == 0 || tabs[bi].nnodes == 0) return;
+  for (int pl = 0; pl < di.keep; ++pl)
+    if (kept_mask(di.removed, b.p, pl))
+      atomicAdd(reinterpret_cast<unsigned long long*>(&bucket[len_bucket(tabs[bi].seglen[pl])]), 1ull);
+}
+
+__global__ void k_dec_item_fill(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
+                                const DecTab* __restrict__ tabs, const int64_t* __restrict__ bucket_off, int64_t* __restrict__ fill,
+                                int64_t* __restrict__ items) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= nb) return;
+  const BlockDev b = blocks[bi];
+  const DecInfo di = info[bi];
+  if (b.p == 0 || di.d == 0 || tabs[bi].nnodes == 0) return;
+  for (int pl = 0; pl < di.keep; ++pl) {
+    if (!kept_mask(di.removed, b.p, pl)) continue;
+    const int k = len_bucket(tabs[bi].seglen[pl]);
+    const int64_t pos = bucket_off[k] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&fill[k]), 1ull);
+    items[pos] = (bi << 5) | pl;
+  }
+}
+
 // Segment pass: one thread per (block, plane) item decodes that plane
 // segment on its own from its seektable start, expanding zero runs, into
 // the block's symbol region.
@@ -344,25 +445,26 @@ __global__ void __launch_bounds__(256) k_dec_segments(const BlockDev* __restrict
   int64_t off = sym_off[bi];
   for (int q = 0; q < pl; ++q) off += plane_region(kept_mask(di.removed, b.p, q), n);
   const int need = __popc(km) * n;
-  const int nbytes = blen[bi];
-  BitIn in{stream + bbyte[bi], nbytes, 0, 0, 0, 0};
   const int64_t start = T->segpos[pl];
   const int64_t limit = start + T->seglen[pl];
-  in.seek(start);
-  SymOut out{reinterpret_cast<uint4*>(sym + off), 0, 0, 0};
   const int czr = T->czr, wb = T->wbits;
+  const uint16_t* tab = T->tab;
+  const uint32_t* node = T->node;
+  BitPf in;
+  in.seek(stream + bbyte[bi], blen[bi], start);
+  SymOut out{reinterpret_cast<uint4*>(sym + off), 0, 0, 0};
   int pos = 0;
   bool bad = false;
   while (pos < need) {
-    const uint32_t e = __ldg(&T->tab[in.peek(kTabBits)]);
+    const uint32_t e = __ldg(&tab[in.peek(kTabBits)]);
     int s;
     if (e & 0x8000u) {
-      uint32_t nd = __ldg(&T->node[e & 0x1ff]);
+      uint32_t nd = __ldg(&node[e & 0x1ff]);
       in.skip(kTabBits);
       int guard = 0;
       while (!(nd & 0x80000000u)) {
         const uint32_t kid = in.get(1) ? (nd >> 16) : (nd & 0xffffu);
-        nd = __ldg(&T->node[kid & 0x1ff]);
+        nd = __ldg(&node[kid & 0x1ff]);
         if (++guard > 32) { bad = true; break; }
       }
       if (bad) break;
@@ -467,17 +569,16 @@ int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T)
   k_dec_tables<<<g, 128, 0, s>>>(db.blocks, db.n_blocks, db.stream, db.block_byte, db.block_len, db.drop, db.info,
                                  reinterpret_cast<DecTab*>(db.tables), db.sym_bytes, db.status);
   ++L;
-  T->mark("decode.items", s);
+  T->mark("decode.order", s);
   L += launch_exclusive_scan(db.sym_bytes, db.n_blocks, db.sym_off, db.scan_part, db.totals, s);
-  cudaMemsetAsync(db.bucket, 0, 2 * sizeof(int64_t) * kBuckets, s);
+  cudaMemsetAsync(db.bucket, 0, 2 * sizeof(int64_t) * kLenBuckets, s);
   k_dec_item_count<<<g, 128, 0, s>>>(db.blocks, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.bucket);
-  L += 1 + launch_exclusive_scan(db.bucket, kBuckets, db.bucket + kBuckets, db.scan_part, db.totals + 1, s);
-  cudaMemsetAsync(db.bucket, 0, sizeof(int64_t) * kBuckets, s);
-  k_dec_item_fill<<<g, 128, 0, s>>>(db.blocks, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.bucket + kBuckets,
+  L += 1 + launch_exclusive_scan(db.bucket, kLenBuckets, db.bucket + kLenBuckets, db.scan_part, db.totals + 1, s);
+  cudaMemsetAsync(db.bucket, 0, sizeof(int64_t) * kLenBuckets, s);
+  k_dec_item_fill<<<g, 128, 0, s>>>(db.blocks, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.bucket + kLenBuckets,
                                     db.bucket, db.items);
   ++L;
   T->mark("decode.segments", s);
-  // one thread per item; the item count is read on the device (grid sized by its upper bound)
   k_dec_segments<<<(unsigned)((db.max_items + 255) / 256), 256, 0, s>>>(
       db.blocks, db.items, db.totals + 1, db.stream, db.block_byte, db.block_len, db.info, reinterpret_cast<const DecTab*>(db.tables),
       db.sym_off, db.sym, db.totals, db.sym_cap, db.status);
@@ -490,6 +591,18 @@ int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T)
 }
 
 size_t dec_table_bytes() { return sizeof(DecTab); }
+
+// Blocks ordered by level (counting sort; order inside a level arbitrary).
+int launch_level_sort(const BlockDev* blocks, int64_t nb, int64_t* bucket /* 2 * kLevels */, int64_t* perm, int64_t* scan_part,
+                      int64_t* total, cudaStream_t s) {
+  const unsigned g = (unsigned)((nb + 127) / 128);
+  cudaMemsetAsync(bucket, 0, 2 * sizeof(int64_t) * kLevels, s);
+  k_dec_level_count<<<g, 128, 0, s>>>(blocks, nb, bucket);
+  int L = 1 + launch_exclusive_scan(bucket, kLevels, bucket + kLevels, scan_part, total, s);
+  cudaMemsetAsync(bucket, 0, sizeof(int64_t) * kLevels, s);
+  k_dec_level_fill<<<g, 128, 0, s>>>(blocks, nb, bucket + kLevels, bucket, perm);
+  return L + 1;
+}
 
 void decode_set_attributes() {}
 

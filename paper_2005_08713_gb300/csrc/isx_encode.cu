@@ -641,64 +641,128 @@ __device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct,
 }
 
 constexpr int kEmitWarps = 8;
+constexpr int kEncGroup = 32;
+constexpr int kEncSmem = kEncGroup * (256 * 4 + 256) + kEncGroup * 32 * 2;
 
 __device__ inline int64_t block_bit_start(const TileDev& t, const int64_t* final_pos, int64_t bi) {
   return 8 * (final_pos[bi] + (bi == t.block_base ? 32 + 4 * (int64_t)t.nb : 0));
 }
 
-// Size pass: exact segment lengths, t, header and block size.
-__global__ void __launch_bounds__(32 * kEmitWarps) k_enc_size(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
+// Group of kEncGroup level-sorted blocks: their code tables in shared
+// memory and their (block, plane) segments listed plane-major.
+struct EncGroup {
+  uint32_t (*code)[256];
+  uint8_t (*len)[256];
+  uint16_t* item;
+  int nitem;
+};
+
+__device__ int load_group(const int64_t* perm, int64_t nb, const BlockDev* blocks, const BlockCode* codes, uint8_t* dyn, EncGroup& G,
+                          int* s_nitem) {
+  const int64_t g0 = (int64_t)blockIdx.x * kEncGroup;
+  const int ng = (int)min((int64_t)kEncGroup, nb - g0);
+  G.code = reinterpret_cast<uint32_t (*)[256]>(dyn);
+  G.len = reinterpret_cast<uint8_t (*)[256]>(dyn + kEncGroup * 256 * 4);
+  G.item = reinterpret_cast<uint16_t*>(dyn + kEncGroup * (256 * 4 + 256));
+  for (int j = 0; j < ng; ++j) {
+    const BlockCode& bc = codes[perm[g0 + j]];
+    if (!bc.any_kept) continue;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+      G.code[j][k] = bc.code[k];
+      G.len[j][k] = bc.len[k];
+    }
+  }
+  if (threadIdx.x < 32) {
+    const int j = threadIdx.x;
+    uint32_t planes = 0;
+    if (j < ng) {
+      const BlockCode& bc = codes[perm[g0 + j]];
+      if (bc.any_kept)
+        for (int pl = 0; pl < bc.d; ++pl)
+          if (kept_types(bc.removed, bc.p, pl)) planes |= 1u << pl;
+    }
+    int base = 0;
+    for (int pl = 0; pl < 32; ++pl) {
+      const uint32_t m = __ballot_sync(0xffffffffu, (planes >> pl) & 1u);
+      if ((planes >> pl) & 1u) G.item[base + __popc(m & ((1u << j) - 1u))] = (uint16_t)((j << 5) | pl);
+      base += __popc(m);
+    }
+    if (j == 0) *s_nitem = base;
+  }
+  __syncthreads();
+  G.nitem = *s_nitem;
+  return ng;
+}
+
+// Symbol offset of plane pl inside a block's region.
+__device__ inline int64_t plane_offset(const uint32_t* removed, int p, int n, int pl) {
+  int64_t off = 0;
+  for (int q = 0; q < pl; ++q) {
+    const uint32_t km = kept_types(removed, p, q);
+    if (km) off += region16(km, n);
+  }
+  return off;
+}
+
+// Size pass: one warp per (block, plane) segment gives its exact bit length.
+__global__ void __launch_bounds__(32 * kEmitWarps) k_enc_size(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm,
                                                              int64_t nb, const uint8_t* sym, const BlockCode* __restrict__ codes,
-                                                             BlockHdr* __restrict__ hdrs, int64_t* __restrict__ item_size,
-                                                             int* __restrict__ status) {
-  __shared__ uint32_t s_code[kEmitWarps][256];
-  __shared__ uint8_t s_len[kEmitWarps][256];
+                                                             BlockHdr* __restrict__ hdrs) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  __shared__ int s_nitem;
+  EncGroup G;
+  load_group(perm, nb, blocks, codes, dyn, G, &s_nitem);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t bi = (int64_t)blockIdx.x * kEmitWarps + wid;
+  const int64_t g0 = (int64_t)blockIdx.x * kEncGroup;
+  for (int it = wid; it < G.nitem; it += kEmitWarps) {
+    const int j = G.item[it] >> 5, pl = G.item[it] & 31;
+    const int64_t bi = perm[g0 + j];
+    const BlockDev b = blocks[bi];
+    const BlockCode& bc = codes[bi];
+    const int n = b.w * b.h / 8;
+    const CodeTab ct{G.code[j], G.len[j], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
+    const uint32_t km = kept_types(bc.removed, b.p, pl);
+    const uint64_t bits = warp_segment<false>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, nullptr, 0);
+    if (lane == 0) hdrs[bi].seglen[pl] = (uint32_t)bits;
+  }
+}
+
+// Per block: seektable width t (raised only when a segment length needs
+// more bits), header bits and the block's size in the stream.
+__global__ void k_enc_blocksize(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks, int64_t nb,
+                                const BlockCode* __restrict__ codes, BlockHdr* __restrict__ hdrs, int64_t* __restrict__ item_size,
+                                int* __restrict__ status) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (bi >= nb) return;
   const BlockDev b = blocks[bi];
   const BlockCode& bc = codes[bi];
   const TileDev& tile = tiles[b.tile];
   const int64_t extra = bi == tile.block_base ? 32 + 4 * (int64_t)tile.nb : 0;
-  const int d = bc.d, p = b.p, n = b.w * b.h / 8;
+  const int d = bc.d, p = b.p;
+  BlockHdr& H = hdrs[bi];
   if (!bc.any_kept) {
-    if (lane == 0) {
-      hdrs[bi].t = 0;
-      hdrs[bi].hdr_bits = 5 + (int64_t)p * d;
-      item_size[bi] = (5 + (int64_t)p * d + 7) / 8 + extra;
-    }
+    H.t = 0;
+    H.hdr_bits = 5 + (int64_t)p * d;
+    item_size[bi] = (5 + (int64_t)p * d + 7) / 8 + extra;
     return;
   }
-  for (int s = lane; s < 256; s += 32) { s_code[wid][s] = bc.code[s]; s_len[wid][s] = bc.len[s]; }
-  __syncwarp();
-  const CodeTab ct{s_code[wid], s_len[wid], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
-  const uint32_t removed[3] = {bc.removed[0], bc.removed[1], bc.removed[2]};
-  const uint8_t* S = sym + b.sym;
-  int64_t off = 0;
   uint64_t sum = 0;
   uint32_t mx = 0;
   for (int pl = 0; pl < d; ++pl) {
-    const uint32_t km = kept_types(removed, p, pl);
-    uint32_t len_bits = 0;
-    if (km) {
-      len_bits = (uint32_t)warp_segment<false>(S + off, __popc(km) * n, ct, nullptr, 0);
-      off += region16(km, n);
-    }
-    if (lane == 0) hdrs[bi].seglen[pl] = len_bits;
-    sum += len_bits;
-    mx = max(mx, len_bits);
+    uint32_t v = 0;
+    if (kept_types(bc.removed, p, pl)) v = H.seglen[pl];
+    else H.seglen[pl] = 0;
+    sum += v;
+    mx = max(mx, v);
   }
-  if (lane == 0) {
-    const int t = max(bc.t0, mx ? bitlen_u32(mx) : 0);
-    const int64_t hdr = 5 + (int64_t)p * d + 18 + (int64_t)d * t + bc.tree_bits;
-    hdrs[bi].t = t;
-    hdrs[bi].hdr_bits = hdr;
-    if (sum != bc.token_bits) set_status(status, 7);
-    item_size[bi] = (hdr + (int64_t)sum + 7) / 8 + extra;
-  }
+  const int t = max(bc.t0, mx ? bitlen_u32(mx) : 0);
+  const int64_t hdr = 5 + (int64_t)p * d + 18 + (int64_t)d * t + bc.tree_bits;
+  H.t = t;
+  H.hdr_bits = hdr;
+  if (sum != bc.token_bits) set_status(status, 7);
+  item_size[bi] = (hdr + (int64_t)sum + 7) / 8 + extra;
 }
 
-// Zero the stream (its shared boundary words are OR-ed).
 // The stream is written in whole 32-bit words: it needs its size rounded
 // up to a multiple of 4 bytes of capacity.
 __device__ inline int64_t needed_capacity(int64_t total) { return (total + 3) & ~3LL; }
@@ -710,66 +774,70 @@ __global__ void k_zero_stream(uint32_t* __restrict__ out, const int64_t* __restr
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (int64_t)gridDim.x * blockDim.x) out[k] = 0;
 }
 
-// Emit pass: one warp per block writes header and segments in place.
+// Emit pass: warps write the group's block headers (d, removed mask, C_zr,
+// w, t, seektable, tree), then one warp per segment writes its tokens.
 __global__ void __launch_bounds__(32 * kEmitWarps) k_enc_emit(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
-                                                             int64_t nb, const uint8_t* sym, const BlockCode* __restrict__ codes,
-                                                             const BlockHdr* __restrict__ hdrs, const int64_t* __restrict__ final_pos,
-                                                             const int64_t* __restrict__ totals, int64_t out_cap, uint32_t* __restrict__ out) {
-  __shared__ uint32_t s_code[kEmitWarps][256];
-  __shared__ uint8_t s_len[kEmitWarps][256];
+                                                             const int64_t* __restrict__ perm, int64_t nb, const uint8_t* sym,
+                                                             const BlockCode* __restrict__ codes, const BlockHdr* __restrict__ hdrs,
+                                                             const int64_t* __restrict__ final_pos, const int64_t* __restrict__ totals,
+                                                             int64_t out_cap, uint32_t* __restrict__ out) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  __shared__ int s_nitem;
+  if (needed_capacity(totals[0]) > out_cap) return;
+  EncGroup G;
+  const int ng = load_group(perm, nb, blocks, codes, dyn, G, &s_nitem);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t bi = (int64_t)blockIdx.x * kEmitWarps + wid;
-  if (bi >= nb || needed_capacity(totals[0]) > out_cap) return;
-  const BlockDev b = blocks[bi];
-  const BlockCode& bc = codes[bi];
-  const BlockHdr& H = hdrs[bi];
-  const TileDev& tile = tiles[b.tile];
-  const int d = bc.d, p = b.p, n = b.w * b.h / 8;
-  const uint32_t removed[3] = {bc.removed[0], bc.removed[1], bc.removed[2]};
-  const int64_t B0 = block_bit_start(tile, final_pos, bi);
-  // header: d and the removed mask (type-major, plane order)
-  if (lane == 0) {
-    LaneWriter W;
-    W.begin(out, B0);
-    W.put((uint32_t)d, 5);
-    for (int ty = 0; ty < p; ++ty)
-      for (int pl = 0; pl < d; ++pl) W.put((removed[ty] >> pl) & 1u, 1);
-    if (bc.any_kept) {
-      W.put((uint32_t)bc.czr, 8);
-      W.put((uint32_t)bc.wbits, 5);
-      W.put((uint32_t)H.t, 5);
+  const int64_t g0 = (int64_t)blockIdx.x * kEncGroup;
+  for (int j = wid; j < ng; j += kEmitWarps) {
+    const int64_t bi = perm[g0 + j];
+    const BlockDev b = blocks[bi];
+    const BlockCode& bc = codes[bi];
+    const BlockHdr& H = hdrs[bi];
+    const int d = bc.d, p = b.p;
+    const int64_t B0 = block_bit_start(tiles[b.tile], final_pos, bi);
+    if (lane == 0) {
+      LaneWriter W;
+      W.begin(out, B0);
+      W.put((uint32_t)d, 5);
+      for (int ty = 0; ty < p; ++ty)
+        for (int pl = 0; pl < d; ++pl) W.put((bc.removed[ty] >> pl) & 1u, 1);
+      if (bc.any_kept) {
+        W.put((uint32_t)bc.czr, 8);
+        W.put((uint32_t)bc.wbits, 5);
+        W.put((uint32_t)H.t, 5);
+      }
+      W.end();
     }
-    W.end();
+    if (!bc.any_kept) continue;
+    const int t = H.t;
+    const int64_t seek = B0 + 5 + (int64_t)p * d + 18;
+    if (lane < d) {
+      LaneWriter W;
+      W.begin(out, seek + (int64_t)lane * t);
+      W.put(H.seglen[lane], t);
+      W.end();
+    }
+    const int64_t tree_pos = seek + (int64_t)d * t;
+    for (int k = lane; k * 32 < bc.tree_bits; k += 32) {
+      const int nbk = min(32, bc.tree_bits - 32 * k);
+      LaneWriter W;
+      W.begin(out, tree_pos + 32 * k);
+      W.put(bc.tree[k] >> (32 - nbk), nbk);
+      W.end();
+    }
   }
-  if (!bc.any_kept) return;
-  const int t = H.t;
-  const int64_t seek = B0 + 5 + (int64_t)p * d + 18;
-  if (lane < d) {
-    LaneWriter W;
-    W.begin(out, seek + (int64_t)lane * t);
-    W.put(H.seglen[lane], t);
-    W.end();
-  }
-  const int64_t tree_pos = seek + (int64_t)d * t;
-  for (int k = lane; k * 32 < bc.tree_bits; k += 32) {
-    const int nbk = min(32, bc.tree_bits - 32 * k);
-    LaneWriter W;
-    W.begin(out, tree_pos + 32 * k);
-    W.put(bc.tree[k] >> (32 - nbk), nbk);
-    W.end();
-  }
-  for (int s = lane; s < 256; s += 32) { s_code[wid][s] = bc.code[s]; s_len[wid][s] = bc.len[s]; }
-  __syncwarp();
-  const CodeTab ct{s_code[wid], s_len[wid], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
-  const uint8_t* S = sym + b.sym;
-  int64_t off = 0;
-  int64_t pos = B0 + H.hdr_bits;
-  for (int pl = 0; pl < d; ++pl) {
-    const uint32_t km = kept_types(removed, p, pl);
-    if (!km) continue;
-    warp_segment<true>(S + off, __popc(km) * n, ct, out, pos);
-    off += region16(km, n);
-    pos += H.seglen[pl];
+  for (int it = wid; it < G.nitem; it += kEmitWarps) {
+    const int j = G.item[it] >> 5, pl = G.item[it] & 31;
+    const int64_t bi = perm[g0 + j];
+    const BlockDev b = blocks[bi];
+    const BlockCode& bc = codes[bi];
+    const BlockHdr& H = hdrs[bi];
+    const int n = b.w * b.h / 8;
+    const CodeTab ct{G.code[j], G.len[j], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
+    int64_t pos = block_bit_start(tiles[b.tile], final_pos, bi) + H.hdr_bits;
+    for (int q = 0; q < pl; ++q) pos += H.seglen[q];
+    const uint32_t km = kept_types(bc.removed, b.p, pl);
+    warp_segment<true>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, out, pos);
   }
 }
 
@@ -814,17 +882,23 @@ int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T)
   T->mark("encode.huffman", s);
   k_block_huffman<<<(unsigned)((eb.n_blocks + kHuffWarps - 1) / kHuffWarps), 32 * kHuffWarps, 0, s>>>(eb.blocks, eb.stats, eb.codes,
                                                                                                     eb.n_blocks);
+  L += 2;
+  T->mark("encode.order", s);
+  L += launch_level_sort(eb.blocks, eb.n_blocks, eb.bucket, eb.perm, eb.scan_part, eb.totals + 1, s);
   T->mark("encode.size", s);
-  const unsigned gw = (unsigned)((eb.n_blocks + kEmitWarps - 1) / kEmitWarps);
-  k_enc_size<<<gw, 32 * kEmitWarps, 0, s>>>(eb.tiles, eb.blocks, eb.n_blocks, eb.sym, eb.codes, reinterpret_cast<BlockHdr*>(eb.hdrs), eb.item_size, eb.status);
-  L += 3;
+  const unsigned gg = (unsigned)((eb.n_blocks + kEncGroup - 1) / kEncGroup);
+  BlockHdr* hdrs = reinterpret_cast<BlockHdr*>(eb.hdrs);
+  k_enc_size<<<gg, 32 * kEmitWarps, kEncSmem, s>>>(eb.blocks, eb.perm, eb.n_blocks, eb.sym, eb.codes, hdrs);
+  k_enc_blocksize<<<(unsigned)((eb.n_blocks + 127) / 128), 128, 0, s>>>(eb.tiles, eb.blocks, eb.n_blocks, eb.codes, hdrs, eb.item_size,
+                                                                      eb.status);
+  L += 2;
   T->mark("encode.scan", s);
   L += launch_exclusive_scan(eb.item_size, eb.n_blocks, eb.final_pos, eb.scan_part, eb.totals, s);
   T->mark("encode.zero", s);
   k_zero_stream<<<152 * 8, 256, 0, s>>>(reinterpret_cast<uint32_t*>(eb.out), eb.totals, eb.out_capacity);
   T->mark("encode.emit", s);
-  k_enc_emit<<<gw, 32 * kEmitWarps, 0, s>>>(eb.tiles, eb.blocks, eb.n_blocks, eb.sym, eb.codes, reinterpret_cast<const BlockHdr*>(eb.hdrs), eb.final_pos, eb.totals,
-                                           eb.out_capacity, reinterpret_cast<uint32_t*>(eb.out));
+  k_enc_emit<<<gg, 32 * kEmitWarps, kEncSmem, s>>>(eb.tiles, eb.blocks, eb.perm, eb.n_blocks, eb.sym, eb.codes, hdrs, eb.final_pos,
+                                                   eb.totals, eb.out_capacity, reinterpret_cast<uint32_t*>(eb.out));
   T->mark("encode.tile_headers", s);
   k_tile_headers<<<eb.n_tiles, 128, 0, s>>>(eb.tiles, eb.n_tiles, eb.final_pos, eb.item_size, eb.totals, eb.out, eb.out_capacity,
                                             eb.tile_offsets, eb.status);
@@ -834,6 +908,9 @@ int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T)
 
 size_t enc_hdr_bytes() { return sizeof(BlockHdr); }
 
-void encode_set_attributes() {}
+void encode_set_attributes() {
+  cudaFuncSetAttribute(k_enc_size, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
+  cudaFuncSetAttribute(k_enc_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
+}
 
 }  // namespace isx

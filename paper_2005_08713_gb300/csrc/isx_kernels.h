@@ -16,6 +16,7 @@ int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t
 int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const BlockDev* d_blocks,
                          void* coef, cudaStream_t s);
 bool fused_tile(int w, int h, int bits);
+int fused_plane_bytes(int w, int h);
 void transform_set_attributes();
 int launch_quantise_planes(const TileDev* d_tiles, int n_tiles, const int32_t* planes, int32_t* out, cudaStream_t s);
 int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int32_t* A, int32_t* B,
@@ -37,7 +38,9 @@ struct EncodeBuffers {
   int64_t* item_size;        // [n_blocks] block bytes, plus its tile header for a tile's first block
   int64_t* final_pos;        // [n_blocks]
   int64_t* scan_part;
-  int64_t* totals;           // [1]: stream size
+  int64_t* totals;           // [2]: stream size, scratch
+  int64_t* bucket;           // [2 * 16]
+  int64_t* perm;             // [n_blocks] blocks ordered by level
   uint8_t* out;              // 4-byte aligned
   int64_t out_capacity;
   uint64_t* tile_offsets;    // [n_tiles + 1]
@@ -72,8 +75,8 @@ struct DecodeBuffers {
   int64_t* scan_part;
   int64_t* totals;           // [2]: symbol buffer bytes, segment items
   void* tables;              // [n_blocks] decode tables (dec_table_bytes() each)
-  int64_t* bucket;           // [2 * 512] item counts / offsets by (level, plane)
-  int64_t* items;            // [max_items] (block << 5 | plane)
+  int64_t* bucket;           // [2 * 64] counts / offsets of the sort buckets
+  int64_t* items;            // [max_items] (block << 5 | plane), longest segments first
   int64_t max_items;
   uint8_t* sym;              // symbol buffer
   int64_t sym_cap;           // its size: an upper bound from the tiles' bit depths
@@ -83,5 +86,7 @@ int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T)
 int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const DecodeBuffers& db,
                          cudaStream_t s);
 size_t dec_table_bytes();
+int launch_level_sort(const BlockDev* blocks, int64_t nb, int64_t* bucket /* 2 * 16 */, int64_t* perm, int64_t* scan_part,
+                      int64_t* total, cudaStream_t s);
 
 }  // namespace isx

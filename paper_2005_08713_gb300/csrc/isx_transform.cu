@@ -351,8 +351,9 @@ __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const i
 constexpr int kSmemPlaneBytes = 160 * 1024;
 constexpr int kFusedThreads = 1024;
 
+__host__ __device__ inline int smem_pitch(int w);
 __host__ __device__ inline bool tile_uses_smem(int w, int h, int bits) {
-  return bits <= 12 && (int64_t)w * h * 2 <= kSmemPlaneBytes;
+  return bits <= 12 && (int64_t)smem_pitch(w) * h * 2 <= kSmemPlaneBytes;
 }
 
 // Interleaved position of subband sample (y, x) of `type` at `level`
@@ -368,41 +369,69 @@ __device__ inline void ilv_pos(int L, int level, int type, int y, int x, int z, 
   *px = x * s2 + (type != 1 ? s : 0);
 }
 
-// One in-place lifting step along one axis of the grid at stride s:
-// n samples per line, `lines` lines; odd = predict (odd positions) or update
-// (even positions); inverse undoes the step.  Mirror at both ends.
-// Work items are split over a power-of-two fast dimension (no divisions):
-// across columns for vertical steps, along the line for horizontal ones.
-__device__ inline void lift_step(int16_t* P, int pitch, int n, int lines, int s, bool vertical, bool odd, bool inverse) {
-  const int nt = odd ? n / 2 : (n + 1) / 2;
-  const int fast = vertical ? lines : nt, slow = vertical ? nt : lines;
-  const int fbits = 32 - __clz(fast - 1 > 0 ? fast - 1 : 0);   // ceil(log2(fast))
-  const int fmask = (1 << fbits) - 1;
-  const int total = slow << fbits;
-  for (int it = threadIdx.x; it < total; it += blockDim.x) {
-    const int fi = it & fmask, si = it >> fbits;
-    if (fi >= fast) continue;
-    const int line = vertical ? fi : si;
-    const int k = vertical ? si : fi;
-    const int r = odd ? 2 * k + 1 : 2 * k;
-    const int rm = r - 1 >= 0 ? r - 1 : r + 1;
-    const int rp = r + 1 < n ? r + 1 : r - 1;
-    int16_t *c, *a, *b;
-    if (vertical) {
-      c = P + (r * s) * pitch + line * s;
-      a = P + (rm * s) * pitch + line * s;
-      b = P + (rp * s) * pitch + line * s;
+// Shared-memory row pitch (int16 elements): an odd number of 32-bit words,
+// so that threads sweeping different rows hit different banks.
+__host__ __device__ inline int smem_pitch(int w) { return ((w + 1) & ~1) | 2; }
+
+// In-place forward 5/3 lifting of one line of n samples `st` elements apart:
+// afterwards the low-pass samples sit at even and the high-pass samples at
+// odd positions.  Predict and update run in one sweep with a small register
+// window (x[2k+2] is read before position 2k+2 is overwritten).
+__device__ inline void sweep_fwd(int16_t* x, int n, int st) {
+  if (n < 2) return;
+  int32_t xe = x[0], dprev = 0;
+  for (int k = 0; 2 * k < n; ++k) {
+    int32_t d, xe2;
+    if (2 * k + 1 < n) {
+      xe2 = (2 * k + 2 < n) ? x[(2 * k + 2) * st] : xe;   // x[n] mirrors to x[n-2]
+      d = x[(2 * k + 1) * st] - ((xe + xe2) >> 1);
+      x[(2 * k + 1) * st] = (int16_t)d;
     } else {
-      c = P + (line * s) * pitch + r * s;
-      a = P + (line * s) * pitch + rm * s;
-      b = P + (line * s) * pitch + rp * s;
+      d = dprev;   // odd n: d[nh] mirrors to d[nh-1]
+      xe2 = xe;
     }
-    const int32_t va = *a, vb = *b;
-    int32_t v = *c;
-    if (odd) v = inverse ? v + ((va + vb) >> 1) : v - ((va + vb) >> 1);
-    else v = inverse ? v - ((va + vb + 2) >> 2) : v + ((va + vb + 2) >> 2);
-    *c = (int16_t)v;
+    const int32_t dm1 = k == 0 ? d : dprev;   // d[-1] mirrors to d[0]
+    x[(2 * k) * st] = (int16_t)(xe + ((dm1 + d + 2) >> 2));
+    dprev = d;
+    xe = xe2;
   }
+}
+
+// In-place inverse of sweep_fwd.
+__device__ inline void sweep_inv(int16_t* x, int n, int st) {
+  if (n < 2) return;
+  const int nl = (n + 1) >> 1, nh = n >> 1;
+  int32_t dk = x[st];
+  int32_t e = x[0] - ((dk + dk + 2) >> 2);
+  for (int k = 0; k < nh; ++k) {
+    const int32_t dk1 = (k + 1 < nh) ? x[(2 * k + 3) * st] : dk;
+    const int32_t en = (k + 1 < nl) ? x[(2 * k + 2) * st] - ((dk + dk1 + 2) >> 2) : e;
+    x[(2 * k) * st] = (int16_t)e;
+    x[(2 * k + 1) * st] = (int16_t)(dk + ((e + en) >> 1));
+    e = en;
+    dk = dk1;
+  }
+  if (n & 1) x[(n - 1) * st] = (int16_t)e;
+}
+
+// One level of the in-place 2-D transform on the grid at stride s
+// (cw x ch samples): columns then rows (forward), rows then columns (inverse).
+__device__ inline void level_fwd(int16_t* P, int pitch, int cw, int ch, int s) {
+  if (ch >= 2)
+    for (int c = threadIdx.x; c < cw; c += blockDim.x) sweep_fwd(P + c * s, ch, s * pitch);
+  __syncthreads();
+  if (cw >= 2)
+    for (int r = threadIdx.x; r < ch; r += blockDim.x) sweep_fwd(P + (r * s) * pitch, cw, s);
+  __syncthreads();
+}
+
+__device__ inline void level_inv(int16_t* P, int pitch, int cw, int ch, int s) {
+  if (cw >= 2)
+    for (int r = threadIdx.x; r < ch; r += blockDim.x) sweep_inv(P + (r * s) * pitch, cw, s);
+  __syncthreads();
+  if (ch >= 2)
+    for (int c = threadIdx.x; c < cw; c += blockDim.x) sweep_inv(P + c * s, ch, s * pitch);
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
@@ -411,12 +440,13 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
   const TileDev& t = tiles[tt];
   if (c >= t.C) return;
-  const int w = t.w, h = t.h, pitch = w;
+  const int w = t.w, h = t.h, pitch = smem_pitch(w);
   // load + colour transform of channel c
   const bool quad = t.C == 3 && t.bits <= 8 && (w & 3) == 0 && (t.pitch & 3) == 0 && ((reinterpret_cast<uintptr_t>(t.pixels) & 3) == 0);
   if (quad) {
     // four pixels (12 bytes, three aligned words) per thread
     const int qw = w >> 2;
+#pragma unroll 4
     for (int e = threadIdx.x; e < qw * h; e += blockDim.x) {
       const int y = e / qw, x4 = (e - y * qw) << 2;
       const uint32_t* src = reinterpret_cast<const uint32_t*>(t.pixels + (int64_t)y * t.pitch + 3 * x4);
@@ -427,10 +457,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
       int32_t v[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) v[q] = c == 0 ? (R[q] + 2 * G[q] + B[q]) >> 2 : c == 1 ? B[q] - G[q] : R[q] - G[q];
-      uint2 pk;
-      pk.x = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
-      pk.y = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
-      *reinterpret_cast<uint2*>(P + y * pitch + x4) = pk;
+      uint32_t* dst = reinterpret_cast<uint32_t*>(P + y * pitch + x4);   // 4-byte aligned: pitch and x4 are even
+      dst[0] = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+      dst[1] = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
     }
   } else
   for (int e = threadIdx.x; e < w * h; e += blockDim.x) {
@@ -446,21 +475,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
     P[y * pitch + x] = (int16_t)v;
   }
   __syncthreads();
-  for (int l = 0; l < t.L; ++l) {
-    const int s = 1 << l, cw = level_dim(w, l), ch = level_dim(h, l);
-    if (ch >= 2) {
-      lift_step(P, pitch, ch, cw, s, true, true, false);
-      __syncthreads();
-      lift_step(P, pitch, ch, cw, s, true, false, false);
-      __syncthreads();
-    }
-    if (cw >= 2) {
-      lift_step(P, pitch, cw, ch, s, false, true, false);
-      __syncthreads();
-      lift_step(P, pitch, cw, ch, s, false, false, false);
-      __syncthreads();
-    }
-  }
+  for (int l = 0; l < t.L; ++l) level_fwd(P, pitch, level_dim(w, l), level_dim(h, l), 1 << l);
   // quantise + area-ordered pack of this channel's blocks
   const int64_t b0 = t.block_base + (int64_t)c * (t.nb / t.C), b1 = b0 + t.nb / t.C;
   for (int64_t bi = b0; bi < b1; ++bi) {
@@ -515,7 +530,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
   const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
   const TileDev& t = tiles[tt];
   if (c >= t.C || *sym_total > sym_cap) return;
-  const int zw = level_dim(t.w, z), zh = level_dim(t.h, z), pitch = zw;
+  const int zw = level_dim(t.w, z), zh = level_dim(t.h, z), pitch = smem_pitch(zw);
   const int64_t b0 = t.block_base + (int64_t)c * (t.nb / t.C), b1 = b0 + t.nb / t.C;
   for (int64_t bi = b0; bi < b1; ++bi) {
     const BlockDev b = blocks[bi];
@@ -543,18 +558,29 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
       uint32_t mag[8], neg = 0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) mag[e] = 0;
-      for (int pl = 0; pl < di.keep; ++pl) {
-        const uint32_t km = s_km[pl];
-        if (!((km >> type) & 1u)) continue;
-        const int ki = __popc(km & ((1u << type) - 1u));
-        const uint32_t sv = sym[s_poff[pl] + (int64_t)ki * n + k];
-        if (!sv) continue;
-        if (pl == 0) {
-          neg = sv;
-        } else {
-          const int sh = d - 1 - pl;
+      // issue the loads of all planes (at most 16 for int16 data) before using them
+      for (int p0 = 0; p0 < di.keep; p0 += 16) {
+        uint32_t sv[16];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) mag[e] |= ((sv >> e) & 1u) << sh;
+        for (int u = 0; u < 16; ++u) {
+          const int pl = p0 + u;
+          sv[u] = 0;
+          if (pl < di.keep) {
+            const uint32_t km = s_km[pl];
+            if ((km >> type) & 1u) sv[u] = sym[s_poff[pl] + (int64_t)__popc(km & ((1u << type) - 1u)) * n + k];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int pl = p0 + u;
+          if (pl >= di.keep || !sv[u]) continue;
+          if (pl == 0) {
+            neg = sv[u];
+          } else {
+            const int sh = d - 1 - pl;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) mag[e] |= ((sv[u] >> e) & 1u) << sh;
+          }
         }
       }
       int i, j;
@@ -574,23 +600,12 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
     }
   }
   __syncthreads();
-  for (int l = t.L - 1; l >= z; --l) {
-    const int s = 1 << (l - z), cw = level_dim(t.w, l), ch = level_dim(t.h, l);
-    if (cw >= 2) {
-      lift_step(P, pitch, cw, ch, s, false, false, true);
-      __syncthreads();
-      lift_step(P, pitch, cw, ch, s, false, true, true);
-      __syncthreads();
-    }
-    if (ch >= 2) {
-      lift_step(P, pitch, ch, cw, s, true, false, true);
-      __syncthreads();
-      lift_step(P, pitch, ch, cw, s, true, true, true);
-      __syncthreads();
-    }
-  }
+  for (int l = t.L - 1; l >= z; --l) level_inv(P, pitch, level_dim(t.w, l), level_dim(t.h, l), 1 << (l - z));
   int32_t* g = planes + t.plane_base + (int64_t)c * zw * zh;
-  for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) g[e] = P[e];
+  for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
+    const int y = e / zw, x = e - y * zw;
+    g[e] = P[y * pitch + x];
+  }
 }
 
 // --------------------------------------------------------------- launches
@@ -633,6 +648,7 @@ int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int
 }
 
 bool fused_tile(int w, int h, int bits) { return tile_uses_smem(w, h, bits); }
+int fused_plane_bytes(int w, int h) { return smem_pitch(w) * h * 2; }
 
 void transform_set_attributes() {
   cudaFuncSetAttribute(k_fwd_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
