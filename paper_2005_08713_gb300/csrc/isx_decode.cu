@@ -391,32 +391,52 @@ constexpr int kLenBuckets = 33;
 
 __device__ inline int len_bucket(uint32_t seglen) { return 32 - (seglen ? (32 - __clz(seglen)) : 0); }   // longest -> 0
 
-__global__ void k_dec_item_count(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
-                                 const DecTab* __restrict__ tabs, int64_t* __restrict__ bucket) {
+__global__ void __launch_bounds__(128) k_dec_item_count(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
+                                                       const DecTab* __restrict__ tabs, int64_t* __restrict__ bucket) {
+  __shared__ unsigned long long h[kLenBuckets];
+  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x) h[k] = 0;
+  __syncthreads();
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (bi >= nb) return;
-  const BlockDev b = blocks[bi];
-  const DecInfo di = info[bi];
-  if (b.p == 0 || di.d == 0 || tabs[bi].nnodes == 0) return;
-  for (int pl = 0; pl < di.keep; ++pl)
-    if (kept_mask(di.removed, b.p, pl))
-      atomicAdd(reinterpret_cast<unsigned long long*>(&bucket[len_bucket(tabs[bi].seglen[pl])]), 1ull);
+  if (bi < nb) {
+    const BlockDev b = blocks[bi];
+    const DecInfo di = info[bi];
+    if (b.p > 0 && di.d > 0 && tabs[bi].nnodes > 0)
+      for (int pl = 0; pl < di.keep; ++pl)
+        if (kept_mask(di.removed, b.p, pl)) atomicAdd(&h[len_bucket(tabs[bi].seglen[pl])], 1ull);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x)
+    if (h[k]) atomicAdd(reinterpret_cast<unsigned long long*>(&bucket[k]), h[k]);
 }
 
-__global__ void k_dec_item_fill(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
-                                const DecTab* __restrict__ tabs, const int64_t* __restrict__ bucket_off, int64_t* __restrict__ fill,
-                                int64_t* __restrict__ items) {
+__global__ void __launch_bounds__(128) k_dec_item_fill(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
+                                                      const DecTab* __restrict__ tabs, const int64_t* __restrict__ bucket_off,
+                                                      int64_t* __restrict__ fill, int64_t* __restrict__ items) {
+  __shared__ unsigned long long h[kLenBuckets];
+  __shared__ unsigned long long base[kLenBuckets];
+  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x) h[k] = 0;
+  __syncthreads();
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (bi >= nb) return;
-  const BlockDev b = blocks[bi];
-  const DecInfo di = info[bi];
-  if (b.p == 0 || di.d == 0 || tabs[bi].nnodes == 0) return;
-  for (int pl = 0; pl < di.keep; ++pl) {
-    if (!kept_mask(di.removed, b.p, pl)) continue;
-    const int k = len_bucket(tabs[bi].seglen[pl]);
-    const int64_t pos = bucket_off[k] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&fill[k]), 1ull);
-    items[pos] = (bi << 5) | pl;
+  uint32_t planes = 0;
+  BlockDev b;
+  DecInfo di;
+  if (bi < nb) {
+    b = blocks[bi];
+    di = info[bi];
+    if (b.p > 0 && di.d > 0 && tabs[bi].nnodes > 0)
+      for (int pl = 0; pl < di.keep; ++pl)
+        if (kept_mask(di.removed, b.p, pl)) planes |= 1u << pl;
   }
+  // local slots first, then one global reservation per bucket
+  unsigned long long local[32];
+  for (int pl = 0; pl < 32; ++pl)
+    if ((planes >> pl) & 1u) local[pl] = atomicAdd(&h[len_bucket(tabs[bi].seglen[pl])], 1ull);
+  __syncthreads();
+  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x)
+    base[k] = h[k] ? (unsigned long long)bucket_off[k] + atomicAdd(reinterpret_cast<unsigned long long*>(&fill[k]), h[k]) : 0ull;
+  __syncthreads();
+  for (int pl = 0; pl < 32; ++pl)
+    if ((planes >> pl) & 1u) items[base[len_bucket(tabs[bi].seglen[pl])] + local[pl]] = (bi << 5) | pl;
 }
 
 // Segment pass: one thread per (block, plane) item decodes that plane

@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
   __shared__ int64_t s_poff[32];
   const BlockDev b = blocks[blockIdx.x];
   const int n = b.w * b.h / 8, na = b.p * n;
+  AreaMap am;
+  am.init(b.w, b.h);
   const CoefRef cf{coef + b.coef, b.coef16};
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
@@ -127,7 +129,8 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
   {
     uint32_t o[3] = {0, 0, 0}, ng[3] = {0, 0, 0};
     for (int a = tid; a < na; a += blockDim.x) {
-      const int t = a / n;
+      int t, kk;
+      am.split(a, &t, &kk);
       int32_t c[8];
       cf.load(a, c);
 #pragma unroll
@@ -175,7 +178,8 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
   // symbols of every kept (plane, type), written once
   uint8_t* S = sym + b.sym;
   for (int a = tid; a < na; a += blockDim.x) {
-    const int t = a / n, k = a - t * n;
+    int t, k;
+    am.split(a, &t, &k);
     int32_t c[8];
     cf.load(a, c);
     uint32_t negm = 0, m01 = 0, m23 = 0, m45 = 0, m67 = 0;

@@ -87,6 +87,30 @@ __device__ inline void area_ij(int k, int w, int* i, int* j) {
   *j = 4 * ((k >> 1) % (w >> 2));
 }
 
+// Area index -> (type, k') and k' -> (i, j) for one block, with shifts when
+// the block's sizes are powers of two (the common case) instead of divisions.
+struct AreaMap {
+  int n, w, nlog, wlog;
+  __device__ void init(int bw, int bh) {
+    w = bw;
+    n = bw * bh / 8;
+    nlog = (n & (n - 1)) == 0 ? 31 - __clz(n) : -1;
+    wlog = (w & (w - 1)) == 0 ? 31 - __clz(w) : -1;
+  }
+  __device__ void split(int a, int* type, int* k) const {
+    if (nlog >= 0) { *type = a >> nlog; *k = a & (n - 1); }
+    else { *type = a / n; *k = a - *type * n; }
+  }
+  __device__ void ij(int k, int* i, int* j) const {
+    if (wlog >= 0) {
+      *i = 4 * ((2 * k) >> wlog) + 2 * (k & 1);
+      *j = 4 * ((k >> 1) & ((w >> 2) - 1));
+    } else {
+      area_ij(k, w, i, j);
+    }
+  }
+};
+
 // Subband rectangle of a block's type within the tile's Mallat plane.
 __device__ inline void subband_rect(int tw, int th, int L, int level, int type, int* x, int* y, int* sw, int* sh) {
   if (level == 0) {

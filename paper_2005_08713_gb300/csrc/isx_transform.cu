@@ -380,6 +380,7 @@ __host__ __device__ inline int smem_pitch(int w) { return ((w + 1) & ~1) | 2; }
 __device__ inline void sweep_fwd(int16_t* x, int n, int st) {
   if (n < 2) return;
   int32_t xe = x[0], dprev = 0;
+#pragma unroll 4
   for (int k = 0; 2 * k < n; ++k) {
     int32_t d, xe2;
     if (2 * k + 1 < n) {
@@ -403,6 +404,7 @@ __device__ inline void sweep_inv(int16_t* x, int n, int st) {
   const int nl = (n + 1) >> 1, nh = n >> 1;
   int32_t dk = x[st];
   int32_t e = x[0] - ((dk + dk + 2) >> 2);
+#pragma unroll 4
   for (int k = 0; k < nh; ++k) {
     const int32_t dk1 = (k + 1 < nh) ? x[(2 * k + 3) * st] : dk;
     const int32_t en = (k + 1 < nl) ? x[(2 * k + 2) * st] - ((dk + dk1 + 2) >> 2) : e;
@@ -415,7 +417,8 @@ __device__ inline void sweep_inv(int16_t* x, int n, int st) {
 }
 
 // One level of the in-place 2-D transform on the grid at stride s
-// (cw x ch samples): columns then rows (forward), rows then columns (inverse).
+// (cw x ch samples): columns then rows (forward), rows then columns (inverse);
+// one thread sweeps one line.
 __device__ inline void level_fwd(int16_t* P, int pitch, int cw, int ch, int s) {
   if (ch >= 2)
     for (int c = threadIdx.x; c < cw; c += blockDim.x) sweep_fwd(P + c * s, ch, s * pitch);
@@ -483,10 +486,12 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
     const int n = b.w * b.h / 8, na = b.p * n;
     const int q = qlog2_of(t, b.level);
     uint4* out = reinterpret_cast<uint4*>(coef + b.coef);
+    AreaMap am;
+    am.init(b.w, b.h);
     for (int a = threadIdx.x; a < na; a += blockDim.x) {
-      const int type = a / n, k = a - type * n;
-      int i, j;
-      area_ij(k, b.w, &i, &j);
+      int type, k, i, j;
+      am.split(a, &type, &k);
+      am.ij(k, &i, &j);
       int sx, sy, sw, sh;
       subband_rect(w, h, t.L, b.level, type, &sx, &sy, &sw, &sh);
       int16_t v[8];
@@ -553,8 +558,11 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
     const int q = qlog2_of(t, b.level);
     const int32_t delta = 1 << q;
     const int d = di.d;
+    AreaMap am;
+    am.init(b.w, b.h);
     for (int a = threadIdx.x; a < na; a += blockDim.x) {
-      const int type = a / n, k = a - type * n;
+      int type, k;
+      am.split(a, &type, &k);
       uint32_t mag[8], neg = 0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) mag[e] = 0;
@@ -584,7 +592,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
         }
       }
       int i, j;
-      area_ij(k, b.w, &i, &j);
+      am.ij(k, &i, &j);
       int sx, sy, sw, sh;
       subband_rect(t.w, t.h, t.L, b.level, type, &sx, &sy, &sw, &sh);
 #pragma unroll
