@@ -94,9 +94,9 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
                             size_t out_capacity, uint64_t* d_tile_offsets, void* stream);
 
 /* Decode the rectangle (rx, ry, rw, rh), given in pixels of resolution level
- * `level` (0 = full size; level z halves the size z times, Sec. 4
- * "reconstruct the image at any resolution level ... by simply discarding
- * the high-pass coefficients"), from tiles encoded by isx_encode_tiles.
+ * `level` (0 = full size; level z halves the size z times: the decoder
+ * skips the high-pass blocks of the z finest levels and inverts the rest,
+ * Sec. 4), from tiles encoded by isx_encode_tiles.
  *   d_stream, d_tile_offsets  DEVICE stream and its n_tiles + 1 offsets.
  *   tiles           HOST array describing the same tiles (pixels ignored).
  *   drop_lsb_planes discards that many least significant magnitude planes
@@ -157,6 +157,46 @@ int32_t isx_last_launch_count(isx_ctx* ctx);
 
 /* Message for the last error on this context (static storage). */
 const char* isx_last_error(isx_ctx* ctx);
+
+/* Size of the library's static device scratch array (16 MiB), the whole
+ * working memory of isx_encode_tile_static. */
+#define ISX_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* Encodes ONE tile without allocating anything: no cudaMalloc, no
+ * cudaFree, no pinned host buffer, no context.  The paper has no
+ * counterpart; this is a service entry point for callers that may not
+ * allocate device memory while they encode (a server whose HBM is all
+ * handed out to its own pools; code that cannot afford the device-wide
+ * synchronisation an allocation or a free may cause).  Its bytes are
+ * identical to those of isx_encode_tiles for the same tile.
+ *   tile      HOST pointer to one descriptor (pixels on the device).
+ *   d_out     DEVICE buffer of out_capacity bytes, 4-byte aligned, as for
+ *             isx_encode_tiles (capacity >= size rounded up to 4).
+ *   h_size    HOST; receives the stream size, or on ISX_ERR_CAPACITY the
+ *             capacity the stream needs (nothing is written to d_out).
+ *   stream    cudaStream_t the work is enqueued on (NULL = legacy stream).
+ *   h_err     optional HOST buffer of err_len bytes for an error message.
+ * Runs on the calling thread's current CUDA device and is SYNCHRONOUS: it
+ * returns after `stream` has finished the work.  All working memory (tile
+ * descriptor, blocks, planes, coefficients, symbols, codes, offsets and the
+ * status word) is carved from one file-scope __device__ array of
+ * ISX_STATIC_SCRATCH_BYTES per device, reserved when the library's device
+ * code is loaded.  A tile whose working set exceeds it is rejected before
+ * anything is enqueued with ISX_ERR_OOM and a message giving both sizes;
+ * every tile of at most 512 x 512 pixels fits, at any channel count, bit
+ * depth and level count.
+ * The first call on each device does the set-up: it looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and sets
+ * the kernels' shared-memory attributes; make that first call before any
+ * stream capture begins.
+ * All calls on one device share the one array.  Each call zeroes what must
+ * start at zero (the status word; d_out is cleared by the encoder itself)
+ * and writes every other scratch byte before reading it, so calls made one
+ * after another need nothing in between; calls that overlap in time (from
+ * several host threads on the same device) race on the array and corrupt
+ * each other: the caller must serialise them. */
+isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_out, size_t out_capacity, size_t* h_size,
+                                  void* stream, char* h_err, size_t err_len);
 
 #ifdef __cplusplus
 }

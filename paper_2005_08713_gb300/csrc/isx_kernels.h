@@ -47,6 +47,7 @@ struct EncodeBuffers {
   int* status;
 };
 size_t enc_hdr_bytes();
+void encode_set_attributes();   // dynamic shared memory limits of the coding kernels (current device)
 
 // Records an event between kernel groups: closes the open stage and opens
 // `name` (nullptr: none).  A no-op unless timing is enabled.

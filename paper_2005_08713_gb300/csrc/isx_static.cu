@@ -1,0 +1,203 @@
+// isx_static.cu — isx_encode_tile_static: the encoder of one tile, working
+// entirely in one statically sized device array of this file.
+//
+// Who needs it: callers that must not allocate device memory at the moment
+// they encode.  A serving process that has handed every byte of HBM to its
+// own pools cannot let a library grow a scratch arena behind its back, and
+// cudaMalloc / cudaFree may synchronise the whole device, stalling every
+// other stream of the process.  The context entry points (isx_encode_tiles)
+// grow their arena on demand; this one never allocates: its working set is
+// the array below, reserved once when the library's module is loaded.
+#include <mutex>
+#include <string>
+#include <cstring>
+#include <algorithm>
+
+#include "isx.h"
+#include "isx_kernels.h"
+
+namespace isx {
+namespace {
+
+constexpr size_t kStaticBytes = ISX_STATIC_SCRATCH_BYTES;
+__device__ __align__(256) uint8_t g_static_scratch[kStaticBytes];
+
+// Per-device set-up: the array's device address and the kernels' shared
+// memory attributes, done once with that device current.
+constexpr int kMaxDevices = 64;
+struct StaticSetup {
+  std::once_flag once;
+  cudaError_t err = cudaSuccess;
+  uint8_t* base = nullptr;
+};
+StaticSetup g_setup[kMaxDevices];
+
+void setup_device(StaticSetup& S) {
+  void* p = nullptr;
+  S.err = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (S.err != cudaSuccess) return;
+  S.base = static_cast<uint8_t*>(p);
+  encode_set_attributes();
+  transform_set_attributes();
+  S.err = cudaGetLastError();
+}
+
+// Writes the tile descriptor, the fused-task list and a zero status word into
+// the scratch (kernel parameters instead of a host copy).
+__global__ void k_static_begin(TileDev t, TileDev* d_tile, int32_t* d_task, int* d_status) {
+  *d_tile = t;
+  d_task[0] = 0;
+  *d_status = 0;
+}
+
+isx_status fail(char* err, size_t err_len, isx_status st, const std::string& msg) {
+  if (err && err_len) {
+    size_t k = std::min(msg.size(), err_len - 1);
+    std::memcpy(err, msg.data(), k);
+    err[k] = 0;
+  }
+  return st;
+}
+
+size_t take(size_t* used, size_t bytes) {
+  size_t off = *used;
+  *used += (bytes + 255) & ~(size_t)255;
+  return off;
+}
+
+}  // namespace
+}  // namespace isx
+
+using namespace isx;
+
+extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_out, size_t out_capacity, size_t* h_size,
+                                             void* stream, char* h_err, size_t err_len) {
+  if (h_err && err_len) h_err[0] = 0;
+  if (!tile || !h_size || (!d_out && out_capacity)) return fail(h_err, err_len, ISX_ERR_ARG, "bad arguments");
+  if (reinterpret_cast<uintptr_t>(d_out) & 3) return fail(h_err, err_len, ISX_ERR_ARG, "d_out must be 4-byte aligned");
+  const isx_tile_desc& t = *tile;
+  if (t.width < 1 || t.width > 65535 || t.height < 1 || t.height > 65535)
+    return fail(h_err, err_len, ISX_ERR_ARG, "width/height out of 1..65535");
+  if (t.channels != 1 && t.channels != 3) return fail(h_err, err_len, ISX_ERR_ARG, "channels must be 1 or 3");
+  if (t.bits < 1 || t.bits > 16) return fail(h_err, err_len, ISX_ERR_ARG, "bits out of 1..16");
+  if (t.levels < 0 || t.levels > kMaxLevels) return fail(h_err, err_len, ISX_ERR_ARG, "levels out of 0..15");
+  if (t.x0 < 0 || t.y0 < 0) return fail(h_err, err_len, ISX_ERR_ARG, "negative tile origin");
+  for (int l = 0; l <= t.levels; ++l)
+    if (t.qstep_log2[l] > 15) return fail(h_err, err_len, ISX_ERR_ARG, "qstep_log2 out of 0..15");
+  if (!t.pixels || t.row_pitch_bytes < (int64_t)t.width * t.channels * (t.bits <= 8 ? 1 : 2))
+    return fail(h_err, err_len, ISX_ERR_ARG, "missing pixels or row pitch too small");
+
+  // Blocks and padded coefficients of the tile: the LL band, then three
+  // subbands per level, each cut into 128 x 128 cells (Fig. 3).
+  int64_t nb = 0, nc = 0;
+  {
+    const int lw = level_dim(t.width, t.levels), lh = level_dim(t.height, t.levels);
+    nb += (int64_t)ceil_div(lw, kCell) * ceil_div(lh, kCell);
+    nc += (int64_t)pad4(lw) * pad4(lh);
+    for (int l = t.levels; l >= 1; --l) {
+      const int gw = level_dim(t.width, l), gh = level_dim(t.height, l);
+      nb += (int64_t)ceil_div(gw, kCell) * ceil_div(gh, kCell);
+      nc += 3LL * pad4(gw) * pad4(gh);
+    }
+    nb *= t.channels;
+    nc *= t.channels;
+  }
+  const bool fused = fused_tile(t.width, t.height, t.bits);
+  const int64_t plane_total = fused ? 0 : (int64_t)t.channels * t.width * t.height;
+  const int64_t coef_bytes = nc * (t.bits <= 12 ? 2 : 4);
+  const int64_t sym_bytes = ((int64_t)dmax_of_bits(t.bits) * (nc / 8 + 16 * nb) + 15) & ~15LL;
+  const int64_t n_part = nb / 2048 + 2;
+
+  size_t used = 0;
+  const size_t o_tile = take(&used, sizeof(TileDev));
+  const size_t o_task = take(&used, sizeof(int32_t));
+  const size_t o_status = take(&used, sizeof(int));
+  const size_t o_offsets = take(&used, 2 * sizeof(uint64_t));
+  const size_t o_blocks = take(&used, sizeof(BlockDev) * nb);
+  const size_t o_A = take(&used, 4 * (size_t)plane_total);
+  const size_t o_B = take(&used, 4 * (size_t)plane_total);
+  const size_t o_coef = take(&used, (size_t)coef_bytes);
+  const size_t o_sym = take(&used, (size_t)sym_bytes);
+  const size_t o_stats = take(&used, sizeof(BlockStats) * nb);
+  const size_t o_codes = take(&used, sizeof(BlockCode) * nb);
+  const size_t o_hdrs = take(&used, enc_hdr_bytes() * nb);
+  const size_t o_is = take(&used, 8 * nb), o_fp = take(&used, 8 * nb), o_perm = take(&used, 8 * nb);
+  const size_t o_bucket = take(&used, 8 * 64), o_part = take(&used, 8 * n_part), o_tot = take(&used, 64);
+  if (used > kStaticBytes)
+    return fail(h_err, err_len, ISX_ERR_OOM,
+                "tile needs " + std::to_string(used) + " bytes of working memory; the static scratch holds " +
+                    std::to_string(kStaticBytes));
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(h_err, err_len, ISX_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(h_err, err_len, ISX_ERR_ARG, "device ordinal beyond 63");
+  StaticSetup& S = g_setup[dev];
+  std::call_once(S.once, setup_device, std::ref(S));
+  if (S.err != cudaSuccess)
+    return fail(h_err, err_len, ISX_ERR_CUDA, std::string("static scratch set-up: ") + cudaGetErrorString(S.err));
+
+  uint8_t* ar = S.base;
+  cudaStream_t s = (cudaStream_t)stream;
+  TileDev td;
+  std::memset(&td, 0, sizeof(td));
+  td.pixels = (const uint8_t*)t.pixels;
+  td.pitch = t.row_pitch_bytes;
+  td.w = t.width; td.h = t.height; td.C = t.channels; td.bits = t.bits; td.L = t.levels;
+  td.x0 = t.x0; td.y0 = t.y0;
+  for (int k = 0; k < 16; ++k) td.q[k] = k <= t.levels ? t.qstep_log2[k] : 0;
+  td.nb = (int32_t)nb;
+  td.fused = fused ? 1 : 0;
+  td.block_base = 0; td.plane_base = 0; td.coef_base = 0; td.sym_base = 0;
+
+  TileDev* d_tile = (TileDev*)(ar + o_tile);
+  int32_t* d_task = (int32_t*)(ar + o_task);
+  int* d_status = (int*)(ar + o_status);
+  uint64_t* d_offsets = (uint64_t*)(ar + o_offsets);
+  BlockDev* d_blocks = (BlockDev*)(ar + o_blocks);
+  uint8_t* coef = ar + o_coef;
+
+  k_static_begin<<<1, 1, 0, s>>>(td, d_tile, d_task, d_status);
+  launch_plan_blocks(d_tile, 1, 0, d_blocks, s);
+  if (fused) {
+    launch_fused_forward(d_tile, d_task, 1, fused_plane_bytes(t.width, t.height), d_blocks, coef, s);
+  } else {
+    launch_forward_transform(d_tile, 1, t.levels, std::max(t.width, t.height), (int32_t*)(ar + o_A), (int32_t*)(ar + o_B), s);
+    launch_pack_blocks(d_tile, d_blocks, nb, (int32_t*)(ar + o_A), coef, s);
+  }
+  EncodeBuffers eb;
+  eb.tiles = d_tile; eb.n_tiles = 1; eb.blocks = d_blocks; eb.n_blocks = nb; eb.coef = coef;
+  eb.sym = ar + o_sym;
+  eb.stats = (BlockStats*)(ar + o_stats);
+  eb.codes = (BlockCode*)(ar + o_codes);
+  eb.hdrs = ar + o_hdrs;
+  eb.item_size = (int64_t*)(ar + o_is); eb.final_pos = (int64_t*)(ar + o_fp);
+  eb.scan_part = (int64_t*)(ar + o_part); eb.totals = (int64_t*)(ar + o_tot);
+  eb.bucket = (int64_t*)(ar + o_bucket); eb.perm = (int64_t*)(ar + o_perm);
+  eb.out = (uint8_t*)d_out; eb.out_capacity = (int64_t)out_capacity;
+  eb.tile_offsets = d_offsets; eb.status = d_status;
+  struct NoMarks : StageMarks {
+    void mark(const char*, cudaStream_t) override {}
+  } marks;
+  launch_encode_coding(eb, s, &marks);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h_err, err_len, ISX_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+
+  // offsets [0, size] and the status word sit next to each other in the scratch
+  uint8_t res[32];
+  e = cudaMemcpyAsync(res, ar + o_offsets, 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res + 16, ar + o_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(h_err, err_len, ISX_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  uint64_t size = 0;
+  int status = 0;
+  std::memcpy(&size, res + 8, 8);
+  std::memcpy(&status, res + 16, sizeof(int));
+  *h_size = (size_t)size;
+  if (status == kStCapacity)
+    return fail(h_err, err_len, ISX_ERR_CAPACITY,
+                "output buffer too small: the stream needs " + std::to_string(size) + " bytes of capacity");
+  if (status != 0)
+    return fail(h_err, err_len, ISX_ERR_CUDA, "internal consistency check failed on the device (code " + std::to_string(status) + ")");
+  return ISX_OK;
+}

@@ -25,7 +25,10 @@ STATUS_NAMES = {0: "ISX_OK", 1: "ISX_ERR_ARG", 2: "ISX_ERR_CAPACITY", 3: "ISX_ER
 # every entry point declared in include/isx.h
 EXPORTS = ["isx_create", "isx_destroy", "isx_encode_tiles", "isx_decode_region", "isx_encode_tiles_host",
            "isx_decode_region_host", "isx_forward_coefficients", "isx_sync_status", "isx_last_launch_count",
-           "isx_last_error", "isx_set_timing", "isx_stage_times"]
+           "isx_last_error", "isx_set_timing", "isx_stage_times", "isx_encode_tile_static"]
+
+# size of the library's static device scratch (ISX_STATIC_SCRATCH_BYTES)
+STATIC_SCRATCH_BYTES = 16 << 20
 
 
 class IsxError(RuntimeError):
@@ -107,8 +110,29 @@ def load(build_if_missing: bool = True):
         lib.isx_stage_times.restype = i32
         lib.isx_last_error.argtypes = [vp]
         lib.isx_last_error.restype = ctypes.c_char_p
+        lib.isx_encode_tile_static.argtypes = [vp, vp, sz, ctypes.POINTER(sz), vp, ctypes.c_char_p, sz]
+        lib.isx_encode_tile_static.restype = st
         _lib = lib
         return lib
+
+
+def encode_tile_static(tile: Tile, out, stream=None) -> int:
+    """Encode one tile with the no-allocation entry point (isx_encode_tile_static).
+
+    out: uint8 CUDA tensor (its size is the capacity).  Synchronous; returns
+    the stream size.  On ISX_ERR_CAPACITY the raised error's ``needed``
+    attribute holds the capacity the stream needs."""
+    lib = load()
+    desc = tile.to_c()
+    size = ctypes.c_size_t(0)
+    err = ctypes.create_string_buffer(512)
+    rc = lib.isx_encode_tile_static(ctypes.byref(desc), out.data_ptr(), out.numel() * out.element_size(),
+                                    ctypes.byref(size), _stream_ptr(stream), err, 512)
+    if rc != ISX_OK:
+        e = IsxError(rc, err.value.decode())
+        e.needed = int(size.value)
+        raise e
+    return int(size.value)
 
 
 class TileArray:
