@@ -100,6 +100,80 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per pixel of each stage's kernel, from one
+# ncu --set full capture of the 8192 x 8192 case of this workload (profiles/kernels_slide_8192x8192_lossy.md),
+# scaled to a full launch by pixels.  Valid only while the kernel's source file is the one captured
+# (first 16 hex digits of its sha256); otherwise the bench reports traffic as null.
+NCU_TRAFFIC = {
+    "encode.transform": ("k_fwd_tile_smem", "isx_transform.cu", "414dc082d1cdeba3", 8.197),
+    "encode.symbols": ("k_enc_symbols", "isx_encode.cu", "63ed4df3ed2c7365", 8.139),
+    "encode.huffman": ("k_block_huffman", "isx_encode.cu", "63ed4df3ed2c7365", 0.545),
+    "encode.emit": ("k_enc_emit", "isx_encode.cu", "63ed4df3ed2c7365", 3.805),
+    "decode.tables": ("k_dec_tables", "isx_decode.cu", "5b1305e839dcd65d", 0.530),
+    "decode.segments": ("k_dec_segments", "isx_decode.cu", "5b1305e839dcd65d", 2.652),
+    "decode.inverse_transform": ("k_inv_tile_smem", "isx_transform.cu", "414dc082d1cdeba3", 12.807),
+}
+
+
+def traffic_bytes(stage, px):
+    import hashlib
+    ent = NCU_TRAFFIC.get(stage)
+    if not ent:
+        return None
+    path = os.path.join(ROOT, "paper_2005_08713_gb300", "csrc", ent[1])
+    try:
+        with open(path, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return int(ent[3] * px) if digest == ent[2] else None
+
+
+def block_geometry(w, h, levels, channels):
+    """(p, padded width, padded height) of every block of a tile, in stream order (Fig. 3)."""
+    def ld(n, l):
+        for _ in range(l):
+            n = (n + 1) >> 1
+        return n
+    out = []
+    for _c in range(channels):
+        for lv in range(levels + 1):
+            level = 0 if lv == 0 else levels + 1 - lv
+            gw, gh = ld(w, levels if level == 0 else level), ld(h, levels if level == 0 else level)
+            p = 1 if level == 0 else 3
+            for by in range(-(-gh // 128)):
+                for bx in range(-(-gw // 128)):
+                    out.append((p, (min(128, gw - 128 * bx) + 3) // 4 * 4, (min(128, gh - 128 * by) + 3) // 4 * 4))
+    return out
+
+
+def kept_symbol_bytes(raw, offs, grid, levels, channels):
+    """Number of blocks and total symbol bytes of their kept (plane, type) pairs, read from the block
+    headers of an encoded stream: each block opens with d (5 bits) and p*d removed-plane flags."""
+    starts, geo = [], []
+    cache = {}
+    for i, (x, y, w, h) in enumerate(grid):
+        t0 = int(offs[i])
+        nb = int(np.frombuffer(raw[t0 + 12:t0 + 16].tobytes(), "<u4")[0])
+        ends = np.frombuffer(raw[t0 + 32:t0 + 32 + 4 * nb].tobytes(), "<u4").astype(np.int64)
+        data = t0 + 32 + 4 * nb
+        starts.append(data + np.concatenate(([0], ends[:-1])))
+        key = (w, h)
+        if key not in cache:
+            cache[key] = np.array(block_geometry(w, h, levels, channels), np.int64)
+        geo.append(cache[key])
+    starts = np.concatenate(starts)
+    geo = np.concatenate(geo)
+    padded = np.concatenate([raw, np.zeros(16, np.uint8)])
+    bits = np.unpackbits(padded[starts[:, None] + np.arange(16)[None, :]], axis=1).astype(np.int32)
+    d = bits[:, :5] @ np.array([16, 8, 4, 2, 1])
+    p, bw, bh = geo[:, 0], geo[:, 1], geo[:, 2]
+    cs = np.cumsum(bits, axis=1)
+    removed = cs[np.arange(len(d)), 4 + p * d] - cs[:, 4]
+    kept = p * d - removed
+    return len(d), int((kept * (bw * bh // 8)).sum())
+
+
 def make_slide(seed):
     import torch
     from paper_2005_08713_gb300 import synth
@@ -226,16 +300,21 @@ def run_gpu(args):
             cnt += 3 * ((lw + 3) // 4 * 4) * ((lh + 3) // 4 * 4)
         cnt += ((lw + 3) // 4 * 4) * ((lh + 3) // 4 * 4)
         coef_elems += 3 * cnt
-    n_blocks = 0
-    for (x, y, w, h) in grid:
-        n_blocks += 3 * (LEVELS + 1)
-    algo = {   # bytes each stage must move in this design, per call
-        "encode.stats": 4 * coef_elems + 1200 * n_blocks,
-        "encode.emit": 4 * coef_elems + 1700 * n_blocks + total_bytes,
-        "encode.huffman": (1200 + 1700) * n_blocks,
-        "decode.blocks": total_bytes + 4 * IMG_W * IMG_H * 3,
-        "decode.inverse_transform": 2 * 2 * 4 * IMG_W * IMG_H * 3,
-        "encode.transform": 2 * 2 * 4 * IMG_W * IMG_H * 3 + 3 * IMG_W * IMG_H,
+    raw = d_out[:total_bytes].cpu().numpy()
+    n_blocks, sym_bytes = kept_symbol_bytes(raw, d_offs.cpu().numpy(), grid, LEVELS, 3)
+    px = IMG_W * IMG_H
+    # bytes each kernel must read and write in this design, per call (units: one call over the whole image);
+    # sym_bytes = symbols of every kept (plane, type) of every block, one byte each
+    algo = {
+        "encode.transform": 3 * px + 2 * coef_elems,                    # RGB8 in, int16 area-ordered blocks out
+        "encode.symbols": 2 * coef_elems + sym_bytes + 1200 * n_blocks,  # blocks in, kept symbols + statistics out
+        "encode.huffman": (1200 + 1700) * n_blocks,                      # statistics in, code tables out
+        "encode.size": sym_bytes + 1700 * n_blocks,
+        "encode.emit": sym_bytes + 1700 * n_blocks + total_bytes,        # symbols + codes in, stream out
+        "decode.tables": 600 * n_blocks,                                 # block headers in (<= 600 B), tables out
+        "decode.segments": total_bytes + sym_bytes,                      # stream in, kept symbols out
+        "decode.inverse_transform": sym_bytes + 4 * 3 * px,              # symbols in, int32 planes out
+        "decode.store": 4 * 3 * px + 3 * px,                             # int32 planes in, RGB8 out
     }
     single = {k: v for k, v in stages.items() if k in algo}
     dom = max(single, key=lambda k: single[k][0]) if single else None
@@ -244,7 +323,10 @@ def run_gpu(args):
         avg_ms = single[dom][0] / max(1, single[dom][1])
         ach = algo[dom] / (avg_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
-                "traffic": None, "peak_kind": peak_kind, "avg_launch_ms": round(avg_ms, 3)}
+                "traffic": traffic_bytes(dom, px), "algorithmic_bytes": int(algo[dom]), "peak_kind": peak_kind,
+                "avg_launch_ms": round(avg_ms, 3), "stage_rooflines": {
+                    k: {"GBps": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9, 1),
+                        "frac": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9 / hbm, 4)} for k, v in single.items()}}
     path_bytes = 3 * IMG_W * IMG_H + total_bytes
     path = {"encode_GBps": round(path_bytes / (statistics.median(enc_ms) / 1e3) / 1e9, 1),
             "decode_GBps": round(path_bytes / (statistics.median(dec_ms) / 1e3) / 1e9, 1),
