@@ -427,6 +427,9 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   int32_t nsel = 0;
   int64_t n_blocks = 0, plane_total = 0, sym_cap = 0, max_items = 0;
   int max_levels = 0, max_dim = 1, n_fused = 0, max_plane_bytes = 0;
+  // fused tiles write their pixels themselves; three-channel ones pass int16 planes between their CTAs
+  const bool fstore = true;
+  int64_t fplane_total = 0;
   for (int32_t i = 0; i < n_tiles; ++i) {
     const isx_tile_desc& t = tiles[i];
     std::string why;
@@ -447,9 +450,9 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
     fill_tiledev(d, t);
     d.nb = (int32_t)nb;
     d.block_base = n_blocks;
-    d.plane_base = plane_total;
     d.coef_base = 0;
     d.fused = fused_tile(zw, zh, t.bits) ? 1 : 0;
+    d.plane_base = d.fused && fstore ? fplane_total : plane_total;
     if (d.fused) {
       ctx->h_task[n_fused++] = nsel;
       max_plane_bytes = std::max(max_plane_bytes, fused_plane_bytes(zw, zh));
@@ -457,7 +460,8 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
     ctx->h_index[nsel] = i;
     ++nsel;
     n_blocks += nb;
-    plane_total += (int64_t)t.channels * zw * zh;
+    if (d.fused && fstore) fplane_total += t.channels == 3 ? 3LL * zw * zh : 0;
+    else plane_total += (int64_t)t.channels * zw * zh;
     max_levels = std::max(max_levels, t.levels);
     max_dim = std::max(max_dim, std::max(t.width, t.height));
   }
@@ -475,6 +479,7 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   size_t o_tab = cv.take(dec_table_bytes() * n_blocks), o_bucket = cv.take(8 * 2 * 512), o_items = cv.take(8 * (size_t)max_items);
   size_t o_sym = cv.take((size_t)sym_cap + 64);
   size_t o_A = cv.take(4 * (size_t)plane_total), o_B = cv.take(4 * (size_t)plane_total);
+  size_t o_fp = cv.take(2 * (size_t)fplane_total), o_tk = cv.take(4 * (size_t)std::max(n_fused, 1));
   st = ensure_arena(ctx, cv.used);
   if (st != ISX_OK) return st;
   uint8_t* ar = ctx->arena;
@@ -499,13 +504,16 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   if (T.on && !T.pending.empty()) T.collect();
   int L = launch_decode_blocks(db, s, &T);
   T.mark("decode.inverse_transform", s);
-  L += launch_fused_inverse(d_tiles, d_task, n_fused, max_plane_bytes, db, s);
+  FusedStore fs{d_out, out_pitch_bytes, rx, ry, rw, rh, (int16_t*)(ar + o_fp), (uint32_t*)(ar + o_tk)};
+  L += launch_fused_inverse(d_tiles, d_task, n_fused, max_plane_bytes, db, fstore ? &fs : nullptr, s);
   if (n_fused < nsel) {
     T.mark("decode.inverse_global", s);
     L += launch_inverse_transform(d_tiles, nsel, max_levels, z, max_dim, (int32_t*)(ar + o_A), (int32_t*)(ar + o_B), s);
   }
-  T.mark("decode.store", s);
-  L += launch_store_region(d_tiles, nsel, z, (int32_t*)(ar + o_A), d_out, out_pitch_bytes, rx, ry, rw, rh, s);
+  if (!fstore || n_fused < nsel) {
+    T.mark("decode.store", s);
+    L += launch_store_region(d_tiles, nsel, z, (int32_t*)(ar + o_A), d_out, out_pitch_bytes, rx, ry, rw, rh, fstore, s);
+  }
   T.mark(nullptr, s);
   ctx->launches = L;
   ISX_CUDA(cudaGetLastError());

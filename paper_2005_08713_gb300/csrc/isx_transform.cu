@@ -314,8 +314,9 @@ __global__ void k_quantise_planes(const TileDev* __restrict__ tiles, const int32
 // [0, 2^bits - 1] and write the part of the tile's level-z image that
 // falls inside the requested rectangle.
 __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const int32_t* __restrict__ planes, uint8_t* __restrict__ out,
-                               int64_t pitch, int rx, int ry, int rw, int rh) {
+                               int64_t pitch, int rx, int ry, int rw, int rh, int skip_fused) {
   const TileDev& t = tiles[blockIdx.x];
+  if (skip_fused && t.fused) return;   // written by the fused inverse kernel
   const int zw = level_dim(t.w, z), zh = level_dim(t.h, z);
   const int tx = t.x0 >> z, ty = t.y0 >> z;
   const int64_t np = (int64_t)zw * zh;
@@ -353,7 +354,9 @@ constexpr int kFusedThreads = 1024;
 
 __host__ __device__ inline int smem_pitch(int w);
 __host__ __device__ inline bool tile_uses_smem(int w, int h, int bits) {
-  return bits <= 12 && (int64_t)smem_pitch(w) * h * 2 <= kSmemPlaneBytes;
+  // up to 1024 x 1024 a channel has at most 20 coefficient blocks (LL and
+  // every level) within this plane budget: the block table below holds 32
+  return bits <= 12 && w <= 1024 && h <= 1024 && (int64_t)smem_pitch(w) * h * 2 <= kSmemPlaneBytes;
 }
 
 // Interleaved position of subband sample (y, x) of `type` at `level`
@@ -376,12 +379,35 @@ __host__ __device__ inline int smem_pitch(int w) { return ((w + 1) & ~1) | 2; }
 // In-place forward 5/3 lifting of one line of n samples `st` elements apart:
 // afterwards the low-pass samples sit at even and the high-pass samples at
 // odd positions.  Predict and update run in one sweep with a small register
-// window (x[2k+2] is read before position 2k+2 is overwritten).
+// window (x[2k+2] is read before position 2k+2 is overwritten).  The body
+// runs in chunks of kSweepChunk sample pairs whose reads all lie inside the
+// line: the chunk's loads are issued together, the lifting runs in
+// registers, then the chunk is stored (a chunk reads x[2k+1 .. 2k+2K] and
+// writes x[2k .. 2k+2K-1], so no read of a later chunk is overwritten).
+constexpr int kSweepChunk = 8;
+
 __device__ inline void sweep_fwd(int16_t* x, int n, int st) {
   if (n < 2) return;
   int32_t xe = x[0], dprev = 0;
-#pragma unroll 4
-  for (int k = 0; 2 * k < n; ++k) {
+  int k = 0;
+  for (; 2 * (k + kSweepChunk) < n; k += kSweepChunk) {
+    int32_t v[2 * kSweepChunk], o[2 * kSweepChunk];
+#pragma unroll
+    for (int i = 0; i < 2 * kSweepChunk; ++i) v[i] = x[(2 * k + 1 + i) * st];
+#pragma unroll
+    for (int i = 0; i < kSweepChunk; ++i) {
+      const int32_t xe2 = v[2 * i + 1];
+      const int32_t d = v[2 * i] - ((xe + xe2) >> 1);
+      const int32_t dm1 = (k + i == 0) ? d : dprev;   // d[-1] mirrors to d[0]
+      o[2 * i] = xe + ((dm1 + d + 2) >> 2);
+      o[2 * i + 1] = d;
+      dprev = d;
+      xe = xe2;
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * kSweepChunk; ++i) x[(2 * k + i) * st] = (int16_t)o[i];
+  }
+  for (; 2 * k < n; ++k) {
     int32_t d, xe2;
     if (2 * k + 1 < n) {
       xe2 = (2 * k + 2 < n) ? x[(2 * k + 2) * st] : xe;   // x[n] mirrors to x[n-2]
@@ -398,14 +424,31 @@ __device__ inline void sweep_fwd(int16_t* x, int n, int st) {
   }
 }
 
-// In-place inverse of sweep_fwd.
+// In-place inverse of sweep_fwd, chunked the same way (a chunk reads
+// x[2k+2 .. 2k+2K+1] and writes x[2k .. 2k+2K-1]).
 __device__ inline void sweep_inv(int16_t* x, int n, int st) {
   if (n < 2) return;
   const int nl = (n + 1) >> 1, nh = n >> 1;
   int32_t dk = x[st];
   int32_t e = x[0] - ((dk + dk + 2) >> 2);
-#pragma unroll 4
-  for (int k = 0; k < nh; ++k) {
+  int k = 0;
+  for (; k + kSweepChunk < nh; k += kSweepChunk) {
+    int32_t v[2 * kSweepChunk], o[2 * kSweepChunk];
+#pragma unroll
+    for (int i = 0; i < 2 * kSweepChunk; ++i) v[i] = x[(2 * k + 2 + i) * st];
+#pragma unroll
+    for (int i = 0; i < kSweepChunk; ++i) {
+      const int32_t dk1 = v[2 * i + 1];
+      const int32_t en = v[2 * i] - ((dk + dk1 + 2) >> 2);
+      o[2 * i] = e;
+      o[2 * i + 1] = dk + ((e + en) >> 1);
+      e = en;
+      dk = dk1;
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * kSweepChunk; ++i) x[(2 * k + i) * st] = (int16_t)o[i];
+  }
+  for (; k < nh; ++k) {
     const int32_t dk1 = (k + 1 < nh) ? x[(2 * k + 3) * st] : dk;
     const int32_t en = (k + 1 < nl) ? x[(2 * k + 2) * st] - ((dk + dk1 + 2) >> 2) : e;
     x[(2 * k) * st] = (int16_t)e;
@@ -437,9 +480,81 @@ __device__ inline void level_inv(int16_t* P, int pitch, int cw, int ch, int s) {
   __syncthreads();
 }
 
+// The coefficient blocks of the CTA's tile channel, as its single area loop
+// sees them: area index g of the channel lies in the first block whose
+// `end` exceeds it.
+constexpr int kMaxFusedBlocks = 32;
+constexpr int kMaxFusedPlanes = 20;   // planes of a fused block: at most 12 + 6
+
+struct FusedBlock {
+  int32_t end;                 // inclusive prefix sum of the blocks' areas (p * w * h / 8)
+  int32_t n, w, nlog, wlog;    // AreaMap of the block
+  int32_t q, step;             // quantiser step (log2); distance of neighbouring subband samples
+  int32_t d, keep;             // decode: bit depth and planes kept
+  int64_t base;                // byte offset of its coefficients (encode) or symbols (decode)
+  int4 geo[3];                 // per type: valid width, valid height, interleaved row and column of sample (0, 0)
+};
+
+// Warp 0 fills fb[0 .. nbc) from blocks[b0 ..] for a plane whose LL is level
+// z0; decode passes its DecInfo (else nullptr).  Blocks a decode could not
+// read (p = 0 or d = 0; status already set) get no areas.  The caller
+// synchronises the CTA before use.
+__device__ inline void fused_block_table(const TileDev& t, const BlockDev* __restrict__ blocks, const DecInfo* __restrict__ info,
+                                         const int64_t* __restrict__ sym_off, int64_t b0, int nbc, int z0, FusedBlock* fb,
+                                         int32_t (*po)[kMaxFusedPlanes][3]) {
+  const int lane = threadIdx.x & 31;
+  FusedBlock f;
+  int na = 0;
+  if (lane < nbc) {
+    const BlockDev b = blocks[b0 + lane];
+    f.n = b.w * b.h / 8;
+    f.w = b.w;
+    f.nlog = (f.n & (f.n - 1)) == 0 ? 31 - __clz(f.n) : -1;
+    f.wlog = (f.w & (f.w - 1)) == 0 ? 31 - __clz(f.w) : -1;
+    f.q = qlog2_of(t, b.level);
+    f.step = b.level == 0 ? 1 << (t.L - z0) : 2 << (b.level - 1 - z0);
+    f.d = f.keep = 0;
+    f.base = b.coef;
+    for (int ty = 0; ty < 3; ++ty) {
+      int sx, sy, sw, sh, py, px;
+      subband_rect(t.w, t.h, t.L, b.level, ty < b.p ? ty : 0, &sx, &sy, &sw, &sh);
+      ilv_pos(t.L, b.level, ty < b.p ? ty : 0, kCell * b.by, kCell * b.bx, z0, &py, &px);
+      f.geo[ty] = make_int4(min(sw - kCell * b.bx, b.w), min(sh - kCell * b.by, b.h), py, px);
+    }
+    na = b.p * f.n;
+    if (info) {
+      const DecInfo di = info[b0 + lane];
+      f.d = di.d;
+      f.keep = min(di.keep, kMaxFusedPlanes);
+      f.base = sym_off[b0 + lane];
+      if (b.p == 0 || di.d == 0) na = 0;
+      // kept types of each plane are stored back to back, planes 16-byte aligned
+      int32_t off = 0;
+      for (int pl = 0; pl < f.keep; ++pl) {
+        int32_t o = off;
+        for (int ty = 0; ty < 3; ++ty) {
+          const bool kept = ty < b.p && !((di.removed[ty] >> pl) & 1u);
+          po[lane][pl][ty] = kept ? o : -1;
+          if (kept) o += f.n;
+        }
+        off += (o - off + 15) & ~15;
+      }
+    }
+  }
+  int incl = na;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  f.end = incl;
+  if (lane < nbc) fb[lane] = f;
+}
+
 __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
                                                                  const BlockDev* __restrict__ blocks, uint8_t* __restrict__ coef) {
   extern __shared__ __align__(16) int16_t P[];
+  __shared__ FusedBlock s_fb[kMaxFusedBlocks];
   const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
   const TileDev& t = tiles[tt];
   if (c >= t.C) return;
@@ -447,22 +562,42 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   // load + colour transform of channel c
   const bool quad = t.C == 3 && t.bits <= 8 && (w & 3) == 0 && (t.pitch & 3) == 0 && ((reinterpret_cast<uintptr_t>(t.pixels) & 3) == 0);
   if (quad) {
-    // four pixels (12 bytes, three aligned words) per thread
+    // four pixels (12 bytes, three aligned words) per thread and row; a
+    // thread keeps its column quad and steps over rows, loading four rows'
+    // words before converting them
     const int qw = w >> 2;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < qw * h; e += blockDim.x) {
-      const int y = e / qw, x4 = (e - y * qw) << 2;
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(t.pixels + (int64_t)y * t.pitch + 3 * x4);
-      const uint32_t w0 = src[0], w1 = src[1], w2 = src[2];
-      const int32_t R[4] = {(int32_t)(w0 & 255), (int32_t)((w0 >> 24) & 255), (int32_t)((w1 >> 16) & 255), (int32_t)((w2 >> 8) & 255)};
-      const int32_t G[4] = {(int32_t)((w0 >> 8) & 255), (int32_t)(w1 & 255), (int32_t)((w1 >> 24) & 255), (int32_t)((w2 >> 16) & 255)};
-      const int32_t B[4] = {(int32_t)((w0 >> 16) & 255), (int32_t)((w1 >> 8) & 255), (int32_t)(w2 & 255), (int32_t)((w2 >> 24) & 255)};
-      int32_t v[4];
+    const int dy = blockDim.x / qw;
+    const int y0 = threadIdx.x / qw, x4 = (threadIdx.x - y0 * qw) << 2;
+    if (y0 < dy) {
+      const uint8_t* base = t.pixels + 3 * x4;
+      for (int yb = y0; yb < h; yb += 4 * dy) {
+        uint32_t wv[4][3];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = c == 0 ? (R[q] + 2 * G[q] + B[q]) >> 2 : c == 1 ? B[q] - G[q] : R[q] - G[q];
-      uint32_t* dst = reinterpret_cast<uint32_t*>(P + y * pitch + x4);   // 4-byte aligned: pitch and x4 are even
-      dst[0] = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
-      dst[1] = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+        for (int u = 0; u < 4; ++u) {
+          const int y = yb + u * dy;
+          if (y < h) {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(base + (int64_t)y * t.pitch);
+            wv[u][0] = __ldg(src);
+            wv[u][1] = __ldg(src + 1);
+            wv[u][2] = __ldg(src + 2);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int y = yb + u * dy;
+          if (y >= h) continue;
+          const uint32_t w0 = wv[u][0], w1 = wv[u][1], w2 = wv[u][2];
+          const int32_t R[4] = {(int32_t)(w0 & 255), (int32_t)((w0 >> 24) & 255), (int32_t)((w1 >> 16) & 255), (int32_t)((w2 >> 8) & 255)};
+          const int32_t G[4] = {(int32_t)((w0 >> 8) & 255), (int32_t)(w1 & 255), (int32_t)((w1 >> 24) & 255), (int32_t)((w2 >> 16) & 255)};
+          const int32_t B[4] = {(int32_t)((w0 >> 16) & 255), (int32_t)((w1 >> 8) & 255), (int32_t)(w2 & 255), (int32_t)((w2 >> 24) & 255)};
+          int32_t v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = c == 0 ? (R[q] + 2 * G[q] + B[q]) >> 2 : c == 1 ? B[q] - G[q] : R[q] - G[q];
+          uint32_t* dst = reinterpret_cast<uint32_t*>(P + y * pitch + x4);   // 4-byte aligned: pitch and x4 are even
+          dst[0] = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+          dst[1] = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+        }
+      }
     }
   } else
   for (int e = threadIdx.x; e < w * h; e += blockDim.x) {
@@ -479,43 +614,127 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   }
   __syncthreads();
   for (int l = 0; l < t.L; ++l) level_fwd(P, pitch, level_dim(w, l), level_dim(h, l), 1 << l);
-  // quantise + area-ordered pack of this channel's blocks
-  const int64_t b0 = t.block_base + (int64_t)c * (t.nb / t.C), b1 = b0 + t.nb / t.C;
-  for (int64_t bi = b0; bi < b1; ++bi) {
-    const BlockDev b = blocks[bi];
-    const int n = b.w * b.h / 8, na = b.p * n;
-    const int q = qlog2_of(t, b.level);
-    uint4* out = reinterpret_cast<uint4*>(coef + b.coef);
+  // quantise + area-ordered pack of this channel's blocks, one loop over all their areas
+  const int nbc = t.nb / t.C;
+  if (threadIdx.x < 32) fused_block_table(t, blocks, nullptr, nullptr, t.block_base + (int64_t)c * nbc, nbc, 0, s_fb, nullptr);
+  __syncthreads();
+  const int total = s_fb[nbc - 1].end;
+  int blk = 0;
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+    while (g >= s_fb[blk].end) ++blk;
+    const FusedBlock& f = s_fb[blk];
+    const int a = g - (blk ? s_fb[blk - 1].end : 0);
     AreaMap am;
-    am.init(b.w, b.h);
-    for (int a = threadIdx.x; a < na; a += blockDim.x) {
-      int type, k, i, j;
-      am.split(a, &type, &k);
-      am.ij(k, &i, &j);
-      int sx, sy, sw, sh;
-      subband_rect(w, h, t.L, b.level, type, &sx, &sy, &sw, &sh);
-      int16_t v[8];
+    am.n = f.n; am.w = f.w; am.nlog = f.nlog; am.wlog = f.wlog;
+    int type, k, i, j;
+    am.split(a, &type, &k);
+    am.ij(k, &i, &j);
+    const int4 gm = f.geo[type];
+    const int step = f.step, q = f.q;
+    const int16_t* src = P + (gm.z + i * step) * pitch + gm.w + j * step;
+    int16_t v[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int yy = kCell * b.by + i + (e >> 2), xx = kCell * b.bx + j + (e & 3);
-        int32_t cval = 0;
-        if (yy < sh && xx < sw) {
-          int py, px;
-          ilv_pos(t.L, b.level, type, yy, xx, 0, &py, &px);
-          cval = P[py * pitch + px];
-        }
-        int32_t m = cval < 0 ? -cval : cval;
-        m >>= q;
-        v[e] = (int16_t)(cval < 0 ? -m : m);
+    for (int e = 0; e < 8; ++e) {
+      const int r = e >> 2, cc = e & 3;
+      int32_t cval = 0;
+      if (i + r < gm.y && j + cc < gm.x) cval = src[(r * step) * pitch + cc * step];
+      int32_t m = cval < 0 ? -cval : cval;
+      m >>= q;
+      v[e] = (int16_t)(cval < 0 ? -m : m);
+    }
+    uint4 u;
+    u.x = (uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+    u.y = (uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+    u.z = (uint16_t)v[4] | ((uint32_t)(uint16_t)v[5] << 16);
+    u.w = (uint16_t)v[6] | ((uint32_t)(uint16_t)v[7] << 16);
+    reinterpret_cast<uint4*>(coef + f.base)[a] = u;
+  }
+}
+
+// Decoded RGB8 pixels of one tile at level z into the region output, by the
+// last of the tile's three CTAs: channel `c` is its own shared-memory plane
+// (P, `pitch` elements a row), the other two come from the int16 planes the
+// other CTAs left in global memory (gp: three row-major zw x zh planes, read
+// through L2).  Each thread converts four pixels of a row (inverse RCT,
+// clamp to [0, 2^bits - 1]).
+__device__ inline void store_tile_rgb(const TileDev& t, int z, int zw, int zh, int c, const int16_t* P, int pitch,
+                                      const int16_t* __restrict__ gp, uint8_t* __restrict__ out, int64_t opitch, int rx, int ry, int rw,
+                                      int rh) {
+  const int tx = (t.x0 >> z) - rx, ty = (t.y0 >> z) - ry;   // tile origin in the output
+  const int32_t maxv = (1 << t.bits) - 1;
+  const int qw = (zw + 3) >> 2;
+  const int rows_per_pass = blockDim.x / qw;
+  const int r0 = threadIdx.x / qw, x4 = (threadIdx.x - r0 * qw) << 2;
+  if (r0 >= rows_per_pass) return;
+  const int64_t np = (int64_t)zw * zh;
+  // whole quads inside the region with 4-byte aligned destinations take three word stores
+  const bool words = ((reinterpret_cast<uintptr_t>(out) | (uintptr_t)opitch) & 3) == 0 && ((tx + x4) & 3) == 0 && x4 + 3 < zw &&
+                     tx + x4 >= 0 && tx + x4 + 3 < rw;
+  for (int y = r0; y < zh; y += rows_per_pass) {
+    const int oy = ty + y;
+    if (oy < 0 || oy >= rh) continue;
+    int32_t ch[3][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int x = min(x4 + u, zw - 1);
+        ch[k][u] = k == c ? (int32_t)P[y * pitch + x] : (int32_t)__ldcg(gp + k * np + (int64_t)y * zw + x);
       }
-      uint4 u;
-      u.x = (uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
-      u.y = (uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
-      u.z = (uint16_t)v[4] | ((uint32_t)(uint16_t)v[5] << 16);
-      u.w = (uint16_t)v[6] | ((uint32_t)(uint16_t)v[7] << 16);
-      out[a] = u;
+    int32_t R[4], G[4], B[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int32_t g = ch[0][u] - ((ch[1][u] + ch[2][u]) >> 2);
+      R[u] = min(max(ch[2][u] + g, 0), maxv);
+      G[u] = min(max(g, 0), maxv);
+      B[u] = min(max(ch[1][u] + g, 0), maxv);
+    }
+    uint8_t* row = out + (int64_t)oy * opitch;
+    if (words) {
+      uint32_t* d = reinterpret_cast<uint32_t*>(row + 3 * (tx + x4));
+      d[0] = (uint32_t)R[0] | ((uint32_t)G[0] << 8) | ((uint32_t)B[0] << 16) | ((uint32_t)R[1] << 24);
+      d[1] = (uint32_t)G[1] | ((uint32_t)B[1] << 8) | ((uint32_t)R[2] << 16) | ((uint32_t)G[2] << 24);
+      d[2] = (uint32_t)B[2] | ((uint32_t)R[3] << 8) | ((uint32_t)G[3] << 16) | ((uint32_t)B[3] << 24);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int ox = tx + x4 + u;
+        if (x4 + u >= zw || ox < 0 || ox >= rw) continue;
+        row[3 * ox] = (uint8_t)R[u];
+        row[3 * ox + 1] = (uint8_t)G[u];
+        row[3 * ox + 2] = (uint8_t)B[u];
+      }
     }
   }
+}
+
+// One-channel tile: samples clamped to [0, 2^bits - 1], uint8 (bits <= 8)
+// or uint16 output.
+__device__ inline void store_tile_mono(const TileDev& t, int z, int zw, int zh, const int16_t* P, int pitch, uint8_t* __restrict__ out,
+                                       int64_t opitch, int rx, int ry, int rw, int rh) {
+  const int tx = (t.x0 >> z) - rx, ty = (t.y0 >> z) - ry;
+  const int32_t maxv = (1 << t.bits) - 1;
+  for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
+    const int y = e / zw, x = e - y * zw;
+    const int ox = tx + x, oy = ty + y;
+    if (ox < 0 || oy < 0 || ox >= rw || oy >= rh) continue;
+    const int32_t v = min(max((int32_t)P[y * pitch + x], 0), maxv);
+    uint8_t* row = out + (int64_t)oy * opitch;
+    if (t.bits <= 8) row[ox] = (uint8_t)v;
+    else reinterpret_cast<uint16_t*>(row)[ox] = (uint16_t)v;
+  }
+}
+
+// 8 x 8 bit-matrix transpose of the bytes of (lo, hi): bit e of byte j moves
+// to bit j of byte e (bytes 0-3 in lo, 4-7 in hi).  Three rounds swap the
+// off-diagonal 1 x 1, 2 x 2 and 4 x 4 sub-blocks.
+__device__ __forceinline__ void transpose8x8(uint32_t& lo, uint32_t& hi) {
+  uint32_t t;
+  t = (lo ^ (lo >> 7)) & 0x00AA00AAu; lo ^= t ^ (t << 7);
+  t = (hi ^ (hi >> 7)) & 0x00AA00AAu; hi ^= t ^ (t << 7);
+  t = (lo ^ (lo >> 14)) & 0x0000CCCCu; lo ^= t ^ (t << 14);
+  t = (hi ^ (hi >> 14)) & 0x0000CCCCu; hi ^= t ^ (t << 14);
+  t = ((lo >> 4) ^ hi) & 0x0F0F0F0Fu; hi ^= t; lo ^= t << 4;
 }
 
 // Decode side, fused with the coefficient rebuild: every block of the tile
@@ -524,95 +743,118 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
 // dequantised at the bin midpoint and placed into the interleaved int16
 // layout; the CTA then lifts back from level L to level z and writes the
 // LL_z image row-major (int32) for the colour store.
+template <bool kStore>
 __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
                                                                  const BlockDev* __restrict__ blocks, const DecInfo* __restrict__ info,
                                                                  const int64_t* __restrict__ sym_off, const uint8_t* __restrict__ sym,
                                                                  const int64_t* __restrict__ sym_total, int64_t sym_cap, int z,
-                                                                 int32_t* __restrict__ planes) {
+                                                                 int32_t* __restrict__ planes, int16_t* __restrict__ fplanes,
+                                                                 uint32_t* __restrict__ tickets, uint8_t* __restrict__ out, int64_t out_pitch,
+                                                                 int rx, int ry, int rw, int rh) {
   extern __shared__ __align__(16) int16_t P[];
-  __shared__ int64_t s_poff[32];
-  __shared__ uint32_t s_km[32];
+  __shared__ FusedBlock s_fb[kMaxFusedBlocks];
+  __shared__ int32_t s_po[kMaxFusedBlocks][kMaxFusedPlanes][3];   // (plane, type) symbols from the block's first; -1: not kept
+  __shared__ bool s_last;
   const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
   const TileDev& t = tiles[tt];
   if (c >= t.C || *sym_total > sym_cap) return;
   const int zw = level_dim(t.w, z), zh = level_dim(t.h, z), pitch = smem_pitch(zw);
-  const int64_t b0 = t.block_base + (int64_t)c * (t.nb / t.C), b1 = b0 + t.nb / t.C;
-  for (int64_t bi = b0; bi < b1; ++bi) {
-    const BlockDev b = blocks[bi];
-    const DecInfo di = info[bi];
-    if (b.p == 0 || di.d == 0) continue;   // unreadable block: status already set
-    const int n = b.w * b.h / 8, na = b.p * n;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int64_t off = sym_off[bi];
-      for (int pl = 0; pl < di.keep; ++pl) {
-        uint32_t km = 0;
-        for (int ty = 0; ty < b.p; ++ty)
-          if (!((di.removed[ty] >> pl) & 1u)) km |= 1u << ty;
-        s_km[pl] = km;
-        s_poff[pl] = off;
-        off += ((int64_t)__popc(km) * n + 15) & ~15LL;
+  // rebuild of every block of the channel needed at level z, one loop over all their areas
+  const int nbc = t.nb / t.C;
+  if (threadIdx.x < 32) fused_block_table(t, blocks, info, sym_off, t.block_base + (int64_t)c * nbc, nbc, z, s_fb, s_po);
+  __syncthreads();
+  const int total = s_fb[nbc - 1].end;
+  int blk = 0;
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+    while (g >= s_fb[blk].end) ++blk;
+    const FusedBlock& f = s_fb[blk];
+    const int a = g - (blk ? s_fb[blk - 1].end : 0);
+    AreaMap am;
+    am.n = f.n; am.w = f.w; am.nlog = f.nlog; am.wlog = f.wlog;
+    int type, k;
+    am.split(a, &type, &k);
+    const int d = f.d, keep = f.keep;
+    // symbols of the sign plane and of magnitude planes 1..16 (plane j+1 in byte j of w[]),
+    // loaded together before use; planes not kept (removed or dropped) read as 0
+    const uint8_t* sk = sym + f.base + k;
+    uint32_t sv[17];
+#pragma unroll
+    for (int pl = 0; pl < 17; ++pl) {
+      sv[pl] = 0;
+      if (pl < keep) {
+        const int32_t o = s_po[blk][pl][type];
+        if (o >= 0) sv[pl] = __ldg(sk + o);
       }
     }
-    __syncthreads();
-    const int q = qlog2_of(t, b.level);
-    const int32_t delta = 1 << q;
-    const int d = di.d;
-    AreaMap am;
-    am.init(b.w, b.h);
-    for (int a = threadIdx.x; a < na; a += blockDim.x) {
-      int type, k;
-      am.split(a, &type, &k);
-      uint32_t mag[8], neg = 0;
+    const uint32_t neg = sv[0];
+    uint32_t w[6];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) mag[e] = 0;
-      // issue the loads of all planes (at most 16 for int16 data) before using them
-      for (int p0 = 0; p0 < di.keep; p0 += 16) {
-        uint32_t sv[16];
+    for (int u = 0; u < 4; ++u)
+      w[u] = __byte_perm(__byte_perm(sv[4 * u + 1], sv[4 * u + 2], 0x0040), __byte_perm(sv[4 * u + 3], sv[4 * u + 4], 0x0040), 0x5410);
+    w[4] = w[5] = 0;
+    if (keep > 17) {   // magnitude planes 17..19 (data of more than 10 bits only)
+      uint32_t e4[3];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int pl = p0 + u;
-          sv[u] = 0;
-          if (pl < di.keep) {
-            const uint32_t km = s_km[pl];
-            if ((km >> type) & 1u) sv[u] = sym[s_poff[pl] + (int64_t)__popc(km & ((1u << type) - 1u)) * n + k];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int pl = p0 + u;
-          if (pl >= di.keep || !sv[u]) continue;
-          if (pl == 0) {
-            neg = sv[u];
-          } else {
-            const int sh = d - 1 - pl;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) mag[e] |= ((sv[u] >> e) & 1u) << sh;
-          }
+      for (int u = 0; u < 3; ++u) {
+        const int pl = 17 + u;
+        e4[u] = 0;
+        if (pl < keep) {
+          const int32_t o = s_po[blk][pl][type];
+          if (o >= 0) e4[u] = __ldg(sk + o);
         }
       }
-      int i, j;
-      am.ij(k, &i, &j);
-      int sx, sy, sw, sh;
-      subband_rect(t.w, t.h, t.L, b.level, type, &sx, &sy, &sw, &sh);
+      w[4] = __byte_perm(__byte_perm(e4[0], e4[1], 0x0040), e4[2], 0x0410) & 0x00FFFFFFu;
+    }
+    // bit transposes: afterwards byte e of each pair holds, in bit j, bit e of plane j+1
+    transpose8x8(w[0], w[1]);
+    transpose8x8(w[2], w[3]);
+    if (keep > 17) transpose8x8(w[4], w[5]);
+    int i, j;
+    am.ij(k, &i, &j);
+    const int4 gm = f.geo[type];
+    const int step = f.step, q = f.q;
+    const int32_t half = (1 << q) >> 1;
+    int16_t* dst = P + (gm.z + i * step) * pitch + gm.w + j * step;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int yy = kCell * b.by + i + (e >> 2), xx = kCell * b.bx + j + (e & 3);
-        if (yy >= sh || xx >= sw) continue;
-        const int32_t m = (int32_t)mag[e];
-        const int32_t v = m == 0 ? 0 : m * delta + (delta >> 1);
-        int py, px;
-        ilv_pos(t.L, b.level, type, yy, xx, z, &py, &px);
-        P[py * pitch + px] = (int16_t)(((neg >> e) & 1u) ? -v : v);
-      }
+    for (int e = 0; e < 8; ++e) {
+      const int r = e >> 2, cc = e & 3;
+      if (i + r >= gm.y || j + cc >= gm.x) continue;
+      const uint32_t lo = e < 4 ? w[0] : w[1], mid = e < 4 ? w[2] : w[3], hi = e < 4 ? w[4] : w[5];
+      const int sel = e & 3;
+      // magnitude bits, most significant plane first: reverse the d-1 plane bits
+      const uint32_t rbits = (__byte_perm(lo, mid, sel | ((4 + sel) << 4)) & 0xFFFFu) | (((hi >> (8 * sel)) & 255u) << 16);
+      const int32_t m = d >= 2 ? (int32_t)(__brev(rbits) >> (33 - d)) : 0;
+      const int32_t v = m == 0 ? 0 : (m << q) + half;
+      dst[(r * step) * pitch + cc * step] = (int16_t)(((neg >> e) & 1u) ? -v : v);
     }
   }
   __syncthreads();
   for (int l = t.L - 1; l >= z; --l) level_inv(P, pitch, level_dim(t.w, l), level_dim(t.h, l), 1 << (l - z));
-  int32_t* g = planes + t.plane_base + (int64_t)c * zw * zh;
-  for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
-    const int y = e / zw, x = e - y * zw;
-    g[e] = P[y * pitch + x];
+  if constexpr (!kStore) {
+    int32_t* g = planes + t.plane_base + (int64_t)c * zw * zh;
+    for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
+      const int y = e / zw, x = e - y * zw;
+      g[e] = P[y * pitch + x];
+    }
+  } else if (t.C == 3) {
+    // Every CTA leaves its channel plane (int16) in global memory and takes
+    // a ticket; the tile's third CTA to finish inverts the colour transform
+    // from its own plane and the other two (no CTA waits for another).
+    int16_t* gp = fplanes + t.plane_base;
+    int16_t* mine = gp + (int64_t)c * zw * zh;
+    for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
+      const int y = e / zw, x = e - y * zw;
+      mine[e] = P[y * pitch + x];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&tickets[blockIdx.x / 3], 1u) % 3u) == 2u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    store_tile_rgb(t, z, zw, zh, c, P, pitch, gp, out, out_pitch, rx, ry, rw, rh);
+  } else {
+    store_tile_mono(t, z, zw, zh, P, pitch, out, out_pitch, rx, ry, rw, rh);
   }
 }
 
@@ -648,10 +890,19 @@ int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int
 }
 
 int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const DecodeBuffers& db,
-                         cudaStream_t s) {
+                         const FusedStore* fs, cudaStream_t s) {
   if (n_fused == 0) return 0;
-  k_inv_tile_smem<<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, db.blocks, db.info, db.sym_off, db.sym,
-                                                                      db.totals, db.sym_cap, db.z, db.planes);
+  if (!fs) {
+    k_inv_tile_smem<false><<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, db.blocks, db.info, db.sym_off,
+                                                                             db.sym, db.totals, db.sym_cap, db.z, db.planes, nullptr,
+                                                                             nullptr, nullptr, 0, 0, 0, 0, 0);
+    return 1;
+  }
+  cudaMemsetAsync(fs->tickets, 0, sizeof(uint32_t) * (size_t)n_fused, s);
+  k_inv_tile_smem<true><<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, db.blocks, db.info, db.sym_off, db.sym,
+                                                                          db.totals, db.sym_cap, db.z, db.planes, fs->planes16,
+                                                                          fs->tickets, (uint8_t*)fs->out, fs->pitch, fs->rx, fs->ry,
+                                                                          fs->rw, fs->rh);
   return 1;
 }
 
@@ -660,7 +911,8 @@ int fused_plane_bytes(int w, int h) { return smem_pitch(w) * h * 2; }
 
 void transform_set_attributes() {
   cudaFuncSetAttribute(k_fwd_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
-  cudaFuncSetAttribute(k_inv_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
+  cudaFuncSetAttribute(k_inv_tile_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
+  cudaFuncSetAttribute(k_inv_tile_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
 }
 
 int launch_plan_blocks(const TileDev* d_tiles, int n_tiles, int min_level, BlockDev* d_blocks, cudaStream_t s) {
@@ -688,8 +940,8 @@ int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels
 }
 
 int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, void* out, int64_t pitch, int rx, int ry,
-                        int rw, int rh, cudaStream_t s) {
-  k_store_region<<<dim3(n_tiles, 32), 256, 0, s>>>(d_tiles, z, planes, (uint8_t*)out, pitch, rx, ry, rw, rh);
+                        int rw, int rh, bool skip_fused, cudaStream_t s) {
+  k_store_region<<<dim3(n_tiles, 32), 256, 0, s>>>(d_tiles, z, planes, (uint8_t*)out, pitch, rx, ry, rw, rh, skip_fused ? 1 : 0);
   return 1;
 }
 
