@@ -314,6 +314,7 @@ isx_status isx_sync_status(isx_ctx* ctx, void* stream) {
     case kStCapacity: return fail(ctx, ISX_ERR_CAPACITY, "output buffer too small; required size in tile_offsets[n_tiles]");
     case kStCorrupt: return fail(ctx, ISX_ERR_CORRUPT, "malformed compressed stream");
     case kStTimeout: return fail(ctx, ISX_ERR_TIMEOUT, "device wait gave up");
+    case kStRange: return fail(ctx, ISX_ERR_ARG, "a sample exceeds its tile's bit depth (values must be below 2^bits)");
     default: return fail(ctx, ISX_ERR_CUDA, "internal consistency check failed on the device (code " + std::to_string(st) + ")");
   }
 }
@@ -336,7 +337,7 @@ isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, in
   int32_t* B = (int32_t*)(ctx->arena + o_B);
   ISX_CUDA(cudaMemcpyAsync(d_tiles, ctx->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
   ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
-  int L = launch_forward_transform(d_tiles, n_tiles, P.max_levels, P.max_dim, A, B, s);
+  int L = launch_forward_transform(d_tiles, n_tiles, P.max_levels, P.max_dim, A, B, ctx->d_status, s);
   L += launch_quantise_planes(d_tiles, n_tiles, A, d_coef, s);
   ctx->launches = L;
   ISX_CUDA(cudaGetLastError());
@@ -386,10 +387,10 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   T.mark("encode.plan", s);
   int L = launch_plan_blocks(d_tiles, n_tiles, 0, d_blocks, s);
   T.mark("encode.transform", s);
-  L += launch_fused_forward(d_tiles, d_task, P.n_fused, P.max_plane_bytes, d_blocks, coef, s);
+  L += launch_fused_forward(d_tiles, d_task, P.n_fused, P.max_plane_bytes, d_blocks, coef, ctx->d_status, s);
   if (P.n_fused < n_tiles) {
     T.mark("encode.transform_global", s);
-    L += launch_forward_transform(d_tiles, n_tiles, P.max_levels, P.max_dim, A, B, s);
+    L += launch_forward_transform(d_tiles, n_tiles, P.max_levels, P.max_dim, A, B, ctx->d_status, s);
     T.mark("encode.pack", s);
     L += launch_pack_blocks(d_tiles, d_blocks, NB, A, coef, s);
   }
@@ -460,7 +461,7 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
     ctx->h_index[nsel] = i;
     ++nsel;
     n_blocks += nb;
-    if (d.fused && fstore) fplane_total += t.channels == 3 ? 3LL * zw * zh : 0;
+    if (d.fused && fstore) fplane_total += t.channels == 3 ? (3LL * zw * zh + 7) & ~7LL : 0;   // 16-byte aligned planes
     else plane_total += (int64_t)t.channels * zw * zh;
     max_levels = std::max(max_levels, t.levels);
     max_dim = std::max(max_dim, std::max(t.width, t.height));

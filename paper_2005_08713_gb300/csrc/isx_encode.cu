@@ -160,8 +160,20 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
     }
     removed[t] = r;
   }
-  if (d > b.dmax) {   // cannot happen for inputs within the stated bit depth
-    if (tid == 0) set_status(status, 7);
+  if (d > b.dmax) {
+    // only samples above the stated bit depth get here: record an empty block
+    // (every plane removed, no symbols) so that the later passes stay within
+    // the block's buffers, and report the input error
+    BlockStats* st = stats + blockIdx.x;
+    for (int i = tid; i < 256; i += blockDim.x) st->hist[i] = 0;
+    if (tid <= kMaxW) st->extra[tid] = 0;
+    if (tid == 0) {
+      st->n_runs = 0;
+      st->n_sym = 0;
+      st->removed[0] = st->removed[1] = st->removed[2] = 1u;
+      st->d = 1;
+      set_status(status, kStRange);
+    }
     return;
   }
   uint32_t n_sym = 0;

@@ -13,7 +13,7 @@ constexpr int kMaxW = 18;           // largest zero-run counter width considered
 constexpr int kCtaThreads = 256;    // CTA size of the per-block coding kernels
 constexpr int kMaxDConst = 31;
 
-enum DevStatus : int { kStOk = 0, kStCapacity = 2, kStCorrupt = 3, kStTimeout = 6 };
+enum DevStatus : int { kStOk = 0, kStCapacity = 2, kStCorrupt = 3, kStTimeout = 6, kStRange = 8 };
 
 // One tile as the kernels see it (copied from isx_tile_desc plus its plan).
 struct TileDev {

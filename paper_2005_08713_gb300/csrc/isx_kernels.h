@@ -9,12 +9,13 @@ namespace isx {
 
 int launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* part, int64_t* total, cudaStream_t s);
 int launch_plan_blocks(const TileDev* d_tiles, int n_tiles, int min_level, BlockDev* d_blocks, cudaStream_t s);
-int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B,
+// status: kStRange when a sample exceeds its tile's bit depth
+int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B, int* status,
                              cudaStream_t s);
 int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t n_blocks, const int32_t* planes, void* coef,
                        cudaStream_t s);
 int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const BlockDev* d_blocks,
-                         void* coef, cudaStream_t s);
+                         void* coef, int* status, cudaStream_t s);
 bool fused_tile(int w, int h, int bits);
 int fused_plane_bytes(int w, int h);
 void transform_set_attributes();

@@ -115,17 +115,20 @@ int launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* p
 // --------------------------------------------------- colour transform
 // Pixels -> C int32 planes (Mallat plane 0 .. C-1 of the tile).  RCT of
 // JPEG 2000 for 3 channels: Y = floor((R+2G+B)/4), Cb = B-G, Cr = R-G.
-__global__ void k_load_pixels(const TileDev* __restrict__ tiles, int32_t* __restrict__ planes) {
+__global__ void k_load_pixels(const TileDev* __restrict__ tiles, int32_t* __restrict__ planes, int* __restrict__ status) {
   const TileDev& t = tiles[blockIdx.x];
   if (t.fused) return;
   const int64_t np = (int64_t)t.w * t.h;
   int32_t* out = planes + t.plane_base;
+  uint32_t over = 0;   // bits of samples above the tile's bit depth
   for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < np; e += (int64_t)gridDim.y * blockDim.x) {
     int y = (int)(e / t.w), x = (int)(e - (int64_t)y * t.w);
     const uint8_t* row = t.pixels + (int64_t)y * t.pitch;
     int32_t v[3];
-    for (int c = 0; c < t.C; ++c)
+    for (int c = 0; c < t.C; ++c) {
       v[c] = t.bits <= 8 ? (int32_t)row[x * t.C + c] : (int32_t)((const uint16_t*)row)[x * t.C + c];
+      over |= (uint32_t)v[c] >> t.bits;
+    }
     if (t.C == 3) {
       int32_t R = v[0], G = v[1], B = v[2];
       out[e] = (R + 2 * G + B) >> 2;
@@ -135,6 +138,7 @@ __global__ void k_load_pixels(const TileDev* __restrict__ tiles, int32_t* __rest
       out[e] = v[0];
     }
   }
+  if (over) set_status(status, kStRange);
 }
 
 // -------------------------------------------------------------- lifting
@@ -552,7 +556,8 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
 }
 
 __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
-                                                                 const BlockDev* __restrict__ blocks, uint8_t* __restrict__ coef) {
+                                                                 const BlockDev* __restrict__ blocks, uint8_t* __restrict__ coef,
+                                                                 int* __restrict__ status) {
   extern __shared__ __align__(16) int16_t P[];
   __shared__ FusedBlock s_fb[kMaxFusedBlocks];
   const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
@@ -560,6 +565,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   if (c >= t.C) return;
   const int w = t.w, h = t.h, pitch = smem_pitch(w);
   // load + colour transform of channel c
+  uint32_t over = 0;   // bits of samples above the tile's bit depth
   const bool quad = t.C == 3 && t.bits <= 8 && (w & 3) == 0 && (t.pitch & 3) == 0 && ((reinterpret_cast<uintptr_t>(t.pixels) & 3) == 0);
   if (quad) {
     // four pixels (12 bytes, three aligned words) per thread and row; a
@@ -592,7 +598,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
           const int32_t B[4] = {(int32_t)((w0 >> 16) & 255), (int32_t)((w1 >> 8) & 255), (int32_t)(w2 & 255), (int32_t)((w2 >> 24) & 255)};
           int32_t v[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) v[q] = c == 0 ? (R[q] + 2 * G[q] + B[q]) >> 2 : c == 1 ? B[q] - G[q] : R[q] - G[q];
+          for (int q = 0; q < 4; ++q) {
+            over |= (uint32_t)(R[q] | G[q] | B[q]) >> t.bits;
+            v[q] = c == 0 ? (R[q] + 2 * G[q] + B[q]) >> 2 : c == 1 ? B[q] - G[q] : R[q] - G[q];
+          }
           uint32_t* dst = reinterpret_cast<uint32_t*>(P + y * pitch + x4);   // 4-byte aligned: pitch and x4 are even
           dst[0] = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
           dst[1] = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
@@ -606,12 +615,16 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
     int32_t v;
     if (t.C == 3) {
       const int32_t R = row[3 * x], G = row[3 * x + 1], B = row[3 * x + 2];
+      over |= (uint32_t)(R | G | B) >> t.bits;
       v = c == 0 ? (R + 2 * G + B) >> 2 : c == 1 ? B - G : R - G;
     } else {
       v = t.bits <= 8 ? (int32_t)row[x] : (int32_t)reinterpret_cast<const uint16_t*>(row)[x];
+      over |= (uint32_t)v >> t.bits;
     }
     P[y * pitch + x] = (int16_t)v;
   }
+  // samples above the tile's bit depth void the int16 range bound of the transform
+  if (__any_sync(0xffffffffu, over != 0) && (threadIdx.x & 31) == 0 && c == 0) set_status(status, kStRange);
   __syncthreads();
   for (int l = 0; l < t.L; ++l) level_fwd(P, pitch, level_dim(w, l), level_dim(h, l), 1 << l);
   // quantise + area-ordered pack of this channel's blocks, one loop over all their areas
@@ -667,6 +680,8 @@ __device__ inline void store_tile_rgb(const TileDev& t, int z, int zw, int zh, i
   const int r0 = threadIdx.x / qw, x4 = (threadIdx.x - r0 * qw) << 2;
   if (r0 >= rows_per_pass) return;
   const int64_t np = (int64_t)zw * zh;
+  // whole quads of a plane with rows of a multiple of 4 samples load 8-byte aligned
+  const bool vec = (zw & 3) == 0 && (reinterpret_cast<uintptr_t>(gp) & 7) == 0;
   // whole quads inside the region with 4-byte aligned destinations take three word stores
   const bool words = ((reinterpret_cast<uintptr_t>(out) | (uintptr_t)opitch) & 3) == 0 && ((tx + x4) & 3) == 0 && x4 + 3 < zw &&
                      tx + x4 >= 0 && tx + x4 + 3 < rw;
@@ -674,13 +689,30 @@ __device__ inline void store_tile_rgb(const TileDev& t, int z, int zw, int zh, i
     const int oy = ty + y;
     if (oy < 0 || oy >= rh) continue;
     int32_t ch[3][4];
+    if (vec) {
+      // whole quad: one 8-byte load per global plane, two word loads from shared memory
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int x = min(x4 + u, zw - 1);
-        ch[k][u] = k == c ? (int32_t)P[y * pitch + x] : (int32_t)__ldcg(gp + k * np + (int64_t)y * zw + x);
+      for (int k = 0; k < 3; ++k) {
+        uint32_t lo, hi;
+        if (k == c) {
+          const uint32_t* sp = reinterpret_cast<const uint32_t*>(P + y * pitch + x4);
+          lo = sp[0]; hi = sp[1];
+        } else {
+          const uint2 g2 = __ldcg(reinterpret_cast<const uint2*>(gp + k * np + (int64_t)y * zw + x4));
+          lo = g2.x; hi = g2.y;
+        }
+        ch[k][0] = (int32_t)(int16_t)(lo & 0xFFFFu); ch[k][1] = (int32_t)lo >> 16;
+        ch[k][2] = (int32_t)(int16_t)(hi & 0xFFFFu); ch[k][3] = (int32_t)hi >> 16;
       }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int x = min(x4 + u, zw - 1);
+          ch[k][u] = k == c ? (int32_t)P[y * pitch + x] : (int32_t)__ldcg(gp + k * np + (int64_t)y * zw + x);
+        }
+    }
     int32_t R[4], G[4], B[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -842,9 +874,21 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
     // from its own plane and the other two (no CTA waits for another).
     int16_t* gp = fplanes + t.plane_base;
     int16_t* mine = gp + (int64_t)c * zw * zh;
-    for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
-      const int y = e / zw, x = e - y * zw;
-      mine[e] = P[y * pitch + x];
+    if ((zw & 7) == 0 && ((reinterpret_cast<uintptr_t>(mine) & 15) == 0)) {
+      // rows of eight-sample chunks: four word loads from shared memory, one 16-byte store
+      const int cw = zw >> 3;
+      for (int e = threadIdx.x; e < cw * zh; e += blockDim.x) {
+        const int y = e / cw, x8 = (e - y * cw) << 3;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(P + y * pitch + x8);   // pitch and x8 even: 4-byte aligned
+        uint4 v;
+        v.x = src[0]; v.y = src[1]; v.z = src[2]; v.w = src[3];
+        reinterpret_cast<uint4*>(mine + (int64_t)y * zw)[x8 >> 3] = v;
+      }
+    } else {
+      for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
+        const int y = e / zw, x = e - y * zw;
+        mine[e] = P[y * pitch + x];
+      }
     }
     __threadfence();
     __syncthreads();
@@ -859,11 +903,11 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
 }
 
 // --------------------------------------------------------------- launches
-int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B,
+int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B, int* status,
                              cudaStream_t s) {
   int launches = 0;
   dim3 g0(n_tiles, 64);
-  k_load_pixels<<<g0, 256, 0, s>>>(d_tiles, A);
+  k_load_pixels<<<g0, 256, 0, s>>>(d_tiles, A, status);
   ++launches;
   const int T = 128;
   for (int l = 0; l < max_levels; ++l) {
@@ -883,9 +927,9 @@ int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t
 }
 
 int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const BlockDev* d_blocks,
-                         void* coef, cudaStream_t s) {
+                         void* coef, int* status, cudaStream_t s) {
   if (n_fused == 0) return 0;
-  k_fwd_tile_smem<<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, d_blocks, (uint8_t*)coef);
+  k_fwd_tile_smem<<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, d_blocks, (uint8_t*)coef, status);
   return 1;
 }
 

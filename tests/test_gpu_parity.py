@@ -220,6 +220,29 @@ def test_capacity_error_reports_required_size(codec, orc, synth):
     assert out2[: int(offs[1].item())].cpu().numpy().tobytes() == orc.encode_tile(img, 3, 8)
 
 
+@pytest.mark.parametrize("shape,bits,dtype", [((96, 80, 3), 4, np.uint8), ((64, 64), 6, np.uint8),
+                                               ((128, 96), 12, np.uint16), ((1100, 40), 10, np.uint16)])
+def test_samples_above_bit_depth_are_reported(codec, orc, synth, shape, bits, dtype):
+    """Samples at or above 2^bits are an input error: the encode reports it (and stays within its
+    buffers) on the fused shared-memory path and on the global path (the 1100-wide tile)."""
+    torch = torch_cuda()
+    from paper_2005_08713_gb300 import isx
+    rng = np.random.default_rng(5)
+    img = rng.integers(0, np.iinfo(dtype).max, size=shape, endpoint=True).astype(dtype)
+    d = to_device(img)
+    tiles = [isx.tile_from_tensor(d, 3, bits)]
+    out = torch.zeros(img.nbytes * 4 + 4096, dtype=torch.uint8, device="cuda")
+    offs = torch.zeros(2, dtype=torch.int64, device="cuda")
+    codec.encode_tiles(tiles, out, offs)
+    assert codec.sync_status() == isx.ISX_ERR_ARG
+    # the same tile within range encodes exactly afterwards
+    ok = (img >> (img.dtype.itemsize * 8 - bits)).astype(dtype)
+    d2 = to_device(ok)
+    codec.encode_tiles([isx.tile_from_tensor(d2, 3, bits)], out, offs)
+    assert codec.sync_status() == 0
+    assert out[: int(offs[1].item())].cpu().numpy().tobytes() == orc.encode_tile(ok, 3, bits)
+
+
 def test_corrupt_stream_is_reported(codec, synth):
     torch = torch_cuda()
     from paper_2005_08713_gb300 import isx

@@ -106,3 +106,18 @@ def test_static_encode_capacity_and_size_errors(synth):
     assert bool((out == 0x5A).all())
     # the scratch is usable again right after both errors
     assert _static(t, img.nbytes * 3 + 4096)[0] == ref
+
+
+def test_static_encode_reports_samples_above_bit_depth(synth):
+    from paper_2005_08713_gb300 import isx
+    torch = torch_cuda()
+    img = synth.slide(synth.config_seed(3), 4096, 2048, 128, 128)
+    out = torch.zeros(img.nbytes * 3 + 4096, dtype=torch.uint8, device="cuda")
+    with pytest.raises(isx.IsxError) as ei:
+        isx.encode_tile_static(_tile(img, 4, 5), out)   # 8-bit samples declared as 5-bit
+    assert ei.value.status == isx.ISX_ERR_ARG
+    assert "bit depth" in str(ei.value)
+    # the status word starts at zero again on the next call
+    ok = (img >> 3).astype(np.uint8)
+    n = isx.encode_tile_static(_tile(ok, 4, 5), out)
+    assert n > 0
