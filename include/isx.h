@@ -158,6 +158,89 @@ int32_t isx_last_launch_count(isx_ctx* ctx);
 /* Message for the last error on this context (static storage). */
 const char* isx_last_error(isx_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Batching and serving.  These entry points have no counterpart in the
+ * paper; they organise many tiles and many requests around the same coding
+ * kernels.
+ * ---------------------------------------------------------------------- */
+
+/* One decode job: the part of tile `tile` (index into tiles[] and into the
+ * stream's offset table) that lies inside the rectangle (rx, ry, rw, rh) of
+ * level-`level` pixels is written to d_out, a DEVICE pointer to the
+ * rectangle's pixel (rx, ry), rows out_pitch_bytes apart, in the tile's own
+ * sample format (channels interleaved; uint8 for bits <= 8, else uint16).
+ * Pixels of the rectangle outside the tile are left unchanged. */
+typedef struct {
+  int32_t tile;
+  int32_t rx, ry, rw, rh;
+  void* d_out;
+  int64_t out_pitch_bytes;
+} isx_decode_job;
+
+/* Decode any number of jobs in one call (every job at the same level and
+ * LSB drop): a region decode is the set of jobs of the tiles meeting the
+ * region, all pointing into one image; a batch of tiles can be decoded each
+ * into its own buffer; jobs of several requests can share the call.  Tiles
+ * of different channel counts and bit depths may be mixed.  Asynchronous,
+ * errors as isx_decode_region. */
+isx_status isx_decode_jobs(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets,
+                           const isx_tile_desc* tiles, int32_t n_tiles, const isx_decode_job* jobs,
+                           int32_t n_jobs, int32_t level, int32_t drop_lsb_planes, void* stream);
+
+/* Fused transform schedule.  Tiles whose int16 channel plane fits in shared
+ * memory (width and height <= 1024, bits <= 12, plane <= 160 KB) are
+ * transformed by one CTA per tile and channel; they are grouped in
+ * ISX_SIZE_CLASSES classes by plane size (<= 4 KB, 16 KB, 48 KB, 96 KB,
+ * 160 KB) and each class launches with its own threads per CTA (256, 512
+ * or 1024) for the forward and the inverse transform. */
+#define ISX_SIZE_CLASSES 5
+typedef struct {
+  int32_t forward_threads[ISX_SIZE_CLASSES];
+  int32_t inverse_threads[ISX_SIZE_CLASSES];
+} isx_schedule;
+
+isx_status isx_get_schedule(isx_ctx* ctx, isx_schedule* out);
+/* Every entry must be 256, 512 or 1024 (ISX_ERR_ARG otherwise). */
+isx_status isx_set_schedule(isx_ctx* ctx, const isx_schedule* schedule);
+
+/* Autotuner: encodes and decodes `tiles` (device pixels) once, then times
+ * the fused forward and inverse launches of every size class present with
+ * each thread count, `reps` launches each (CUDA events on `stream`), and
+ * keeps the fastest per class in the context's schedule, which later calls
+ * and plans use.  Synchronous; allocates temporary device buffers. */
+isx_status isx_autotune(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, int32_t reps, void* stream);
+
+/* Plans: an encode of a fixed set of tiles, or a decode of a fixed set of
+ * jobs, prepared once (host planning, device memory of its own, descriptors
+ * uploaded; uses the context's schedule at creation).  Launching a plan
+ * enqueues only kernels and memsets on `stream`, with no host
+ * synchronisation and no allocation, so a launch can be captured into a
+ * CUDA graph and replayed.  A plan is used from one host thread at a time
+ * and by one launch in flight at a time (its scratch is reused).  Data
+ * errors go to the plan's own device status word (isx_plan_sync_status). */
+typedef struct isx_plan isx_plan;
+isx_status isx_plan_encode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, isx_plan** out);
+isx_status isx_plan_decode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles,
+                           const isx_decode_job* jobs, int32_t n_jobs, int32_t level,
+                           int32_t drop_lsb_planes, isx_plan** out);
+/* Same output contract as isx_encode_tiles (the tiles' pixels are read at
+ * launch time from the pointers given at creation). */
+isx_status isx_plan_launch_encode(isx_plan* plan, void* d_out, size_t out_capacity,
+                                  uint64_t* d_tile_offsets, void* stream);
+/* Decodes the plan's jobs from d_stream / d_tile_offsets (same tiles). */
+isx_status isx_plan_launch_decode(isx_plan* plan, const void* d_stream, const uint64_t* d_tile_offsets,
+                                  void* stream);
+/* Synchronises `stream`, returns and clears the first data error of the
+ * plan's launches since the last call. */
+isx_status isx_plan_sync_status(isx_plan* plan, void* stream);
+/* Device memory the plan holds (bytes), for admission by memory budget. */
+size_t isx_plan_device_bytes(const isx_plan* plan);
+/* Kernels the last launch enqueued. */
+int32_t isx_plan_launch_count(const isx_plan* plan);
+const char* isx_plan_last_error(const isx_plan* plan);
+/* Synchronises the device and frees the plan. */
+void isx_plan_destroy(isx_plan* plan);
+
 /* Size of the library's static device scratch array (16 MiB), the whole
  * working memory of isx_encode_tile_static. */
 #define ISX_STATIC_SCRATCH_BYTES ((size_t)16 << 20)

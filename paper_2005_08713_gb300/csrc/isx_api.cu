@@ -60,6 +60,14 @@ struct StageTimer : StageMarks {
   }
 };
 
+// Threads per CTA of the fused transforms for each tile size class (bytes
+// of the tile's int16 channel plane); set by isx_set_schedule or tuned by
+// isx_autotune.
+struct Schedule {
+  int fwd[ISX_SIZE_CLASSES];
+  int inv[ISX_SIZE_CLASSES];
+};
+
 struct isx_ctx {
   StageTimer timer;
   int device = 0;
@@ -76,11 +84,30 @@ struct isx_ctx {
   int* d_status = nullptr;
   uint8_t* d_io = nullptr;         // device staging of the host-buffer calls
   size_t d_io_cap = 0;
+  Schedule sched;
   std::string err;
   int launches = 0;
 };
 
 namespace {
+
+// upper bounds (plane bytes) of the fused size classes
+constexpr int kClassBytes[ISX_SIZE_CLASSES] = {4096, 16384, 49152, 98304, kSmemPlaneBytes};
+
+int class_of(int plane_bytes) {
+  for (int k = 0; k < ISX_SIZE_CLASSES; ++k)
+    if (plane_bytes <= kClassBytes[k]) return k;
+  return ISX_SIZE_CLASSES - 1;
+}
+
+Schedule default_schedule() {
+  Schedule S;
+  const int t[ISX_SIZE_CLASSES] = {256, 256, 512, 1024, 1024};
+  for (int k = 0; k < ISX_SIZE_CLASSES; ++k) S.fwd[k] = S.inv[k] = t[k];
+  return S;
+}
+
+bool valid_threads(int t) { return t == 256 || t == 512 || t == 1024; }
 
 isx_status fail(isx_ctx* c, isx_status st, const std::string& msg) {
   if (c) c->err = msg;
@@ -97,7 +124,7 @@ isx_status cuda_fail(isx_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
-// Bump allocator over the context's arena; sizes are aligned to 256 bytes.
+// Bump allocator over a device region; sizes are aligned to 256 bytes.
 struct Carve {
   size_t used = 0;
   size_t take(size_t bytes) {
@@ -126,26 +153,26 @@ isx_status ensure_arena(isx_ctx* ctx, size_t need) {
   return ISX_OK;
 }
 
-isx_status ensure_staging(isx_ctx* ctx, size_t n_tiles) {
+isx_status ensure_staging(isx_ctx* ctx, size_t n) {
   ISX_CUDA(cudaEventSynchronize(ctx->staging_free));
-  if (n_tiles > ctx->h_tiles_cap) {
+  if (n > ctx->h_tiles_cap) {
     if (ctx->h_tiles) cudaFreeHost(ctx->h_tiles);
     ctx->h_tiles = nullptr;
-    size_t cap = std::max<size_t>(n_tiles, 1024);
+    size_t cap = std::max<size_t>(n, 1024);
     ISX_CUDA(cudaMallocHost(&ctx->h_tiles, cap * sizeof(TileDev)));
     ctx->h_tiles_cap = cap;
   }
-  if (n_tiles > ctx->h_task_cap) {
+  if (n > ctx->h_task_cap) {
     if (ctx->h_task) cudaFreeHost(ctx->h_task);
     ctx->h_task = nullptr;
-    size_t cap = std::max<size_t>(n_tiles, 1024);
+    size_t cap = std::max<size_t>(n, 1024);
     ISX_CUDA(cudaMallocHost(&ctx->h_task, cap * sizeof(int32_t)));
     ctx->h_task_cap = cap;
   }
-  if (n_tiles > ctx->h_index_cap) {
+  if (n > ctx->h_index_cap) {
     if (ctx->h_index) cudaFreeHost(ctx->h_index);
     ctx->h_index = nullptr;
-    size_t cap = std::max<size_t>(n_tiles, 1024);
+    size_t cap = std::max<size_t>(n, 1024);
     ISX_CUDA(cudaMallocHost(&ctx->h_index, cap * sizeof(int64_t)));
     ctx->h_index_cap = cap;
   }
@@ -179,6 +206,7 @@ void tile_counts(const isx_tile_desc& t, int zmin, int64_t* nb, int64_t* ncoef) 
 }
 
 void fill_tiledev(TileDev& d, const isx_tile_desc& t) {
+  std::memset(&d, 0, sizeof(d));
   d.pixels = (const uint8_t*)t.pixels;
   d.pitch = t.row_pitch_bytes;
   d.w = t.width; d.h = t.height; d.C = t.channels; d.bits = t.bits; d.L = t.levels;
@@ -186,49 +214,309 @@ void fill_tiledev(TileDev& d, const isx_tile_desc& t) {
   for (int k = 0; k < 16; ++k) d.q[k] = k <= t.levels ? t.qstep_log2[k] : 0;
 }
 
-struct EncodePlan {
-  int64_t n_blocks = 0, coef_bytes = 0, plane_total = 0, header_total = 0, sym_bytes = 0;
-  int max_levels = 0, max_dim = 1;
-  int n_fused = 0, max_plane_bytes = 0;
+// Tiles of the fused path grouped by size class: task[] lists them class by
+// class; each class launches with its own plane size and thread count.
+struct FusedClass {
+  int begin = 0, count = 0, smem = 0, threads = 256;
 };
 
-isx_status plan_encode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n, bool need_pixels, bool allow_fused, EncodePlan& P) {
-  isx_status st = ensure_staging(ctx, (size_t)n);
-  if (st != ISX_OK) return st;
+void group_fused(const std::vector<std::pair<int32_t, int>>& fused /* (task, plane bytes) */, const int* threads, int32_t* task,
+                 FusedClass* cls) {
+  int pos = 0;
+  for (int k = 0; k < ISX_SIZE_CLASSES; ++k) {
+    cls[k] = FusedClass();
+    cls[k].begin = pos;
+    cls[k].threads = threads[k];
+    for (const auto& f : fused) {
+      if (class_of(f.second) != k) continue;
+      task[pos++] = f.first;
+      cls[k].smem = std::max(cls[k].smem, f.second);
+    }
+    cls[k].count = pos - cls[k].begin;
+  }
+}
+
+// ------------------------------------------------------------ encode
+struct EncodeLayout {
+  int32_t n_tiles = 0;
+  int64_t n_blocks = 0, coef_bytes = 0, plane_total = 0, sym_bytes = 0;
+  int max_levels = 0, max_dim = 1, n_fused = 0;
+  FusedClass cls[ISX_SIZE_CLASSES];
+  size_t o_tiles = 0, o_task = 0, o_blocks = 0, o_A = 0, o_B = 0, o_coef = 0, o_sym = 0, o_stats = 0, o_codes = 0, o_hdrs = 0;
+  size_t o_is = 0, o_fp = 0, o_perm = 0, o_bucket = 0, o_part = 0, o_tot = 0, total = 0;
+};
+
+// Host planning of an encode: descriptors into h_tiles[n], fused tasks into
+// h_task[n], sizes and the device layout into E.
+isx_status plan_encode(const isx_tile_desc* tiles, int32_t n, bool allow_fused, const Schedule& S, TileDev* h_tiles, int32_t* h_task,
+                       EncodeLayout& E, std::string* err) {
+  E = EncodeLayout();
+  E.n_tiles = n;
+  std::vector<std::pair<int32_t, int>> fused;
   for (int32_t i = 0; i < n; ++i) {
     const isx_tile_desc& t = tiles[i];
     std::string why;
-    if (!tile_ok(t, &why)) return fail(ctx, ISX_ERR_ARG, "tile " + std::to_string(i) + ": " + why);
-    if (need_pixels && (!t.pixels || t.row_pitch_bytes < (int64_t)t.width * t.channels * (t.bits <= 8 ? 1 : 2)))
-      return fail(ctx, ISX_ERR_ARG, "tile " + std::to_string(i) + ": missing pixels or row pitch too small");
+    if (!tile_ok(t, &why)) { *err = "tile " + std::to_string(i) + ": " + why; return ISX_ERR_ARG; }
+    if (!t.pixels || t.row_pitch_bytes < (int64_t)t.width * t.channels * (t.bits <= 8 ? 1 : 2)) {
+      *err = "tile " + std::to_string(i) + ": missing pixels or row pitch too small";
+      return ISX_ERR_ARG;
+    }
     int64_t nb, nc;
     tile_counts(t, 0, &nb, &nc);
-    TileDev& d = ctx->h_tiles[i];
+    TileDev& d = h_tiles[i];
     fill_tiledev(d, t);
     d.nb = (int32_t)nb;
-    d.block_base = P.n_blocks;
-    d.coef_base = P.coef_bytes;
+    d.block_base = E.n_blocks;
+    d.coef_base = E.coef_bytes;
     d.fused = allow_fused && fused_tile(t.width, t.height, t.bits) ? 1 : 0;
-    d.plane_base = d.fused ? 0 : P.plane_total;
-    if (d.fused) {
-      ctx->h_task[P.n_fused++] = i;
-      P.max_plane_bytes = std::max(P.max_plane_bytes, fused_plane_bytes(t.width, t.height));
-    } else {
-      P.plane_total += (int64_t)t.channels * t.width * t.height;
-    }
-    d.sym_base = P.sym_bytes;
-    P.n_blocks += nb;
-    P.coef_bytes += nc * (t.bits <= 12 ? 2 : 4);
+    d.plane_base = d.fused ? 0 : E.plane_total;
+    if (d.fused) fused.push_back({i, fused_plane_bytes(t.width, t.height)});
+    else E.plane_total += (int64_t)t.channels * t.width * t.height;
+    d.sym_base = E.sym_bytes;
+    E.n_blocks += nb;
+    E.coef_bytes += nc * (t.bits <= 12 ? 2 : 4);
     // symbol regions: dmax planes of p*w*h/8 bytes per block, each rounded up to 16
-    P.sym_bytes += ((int64_t)dmax_of_bits(t.bits) * (nc / 8 + 16 * nb) + 15) & ~15LL;   // 16-byte aligned regions
-    P.header_total += 32 + 4 * nb;
-    P.max_levels = std::max(P.max_levels, t.levels);
-    P.max_dim = std::max(P.max_dim, std::max(t.width, t.height));
+    E.sym_bytes += ((int64_t)dmax_of_bits(t.bits) * (nc / 8 + 16 * nb) + 15) & ~15LL;
+    E.max_levels = std::max(E.max_levels, t.levels);
+    E.max_dim = std::max(E.max_dim, std::max(t.width, t.height));
   }
+  E.n_fused = (int)fused.size();
+  group_fused(fused, S.fwd, h_task, E.cls);
+  const int64_t NB = E.n_blocks;
+  Carve cv;
+  E.o_tiles = cv.take(sizeof(TileDev) * n);
+  E.o_task = cv.take(sizeof(int32_t) * (size_t)std::max(E.n_fused, 1));
+  E.o_blocks = cv.take(sizeof(BlockDev) * NB);
+  E.o_A = cv.take(4 * (size_t)E.plane_total);
+  E.o_B = cv.take(4 * (size_t)E.plane_total);
+  E.o_coef = cv.take((size_t)E.coef_bytes);
+  E.o_sym = cv.take((size_t)E.sym_bytes);
+  E.o_stats = cv.take(sizeof(BlockStats) * NB);
+  E.o_codes = cv.take(sizeof(BlockCode) * NB);
+  E.o_hdrs = cv.take(enc_hdr_bytes() * NB);
+  E.o_is = cv.take(8 * NB);
+  E.o_fp = cv.take(8 * NB);
+  E.o_perm = cv.take(8 * NB);
+  E.o_bucket = cv.take(8 * 64);
+  E.o_part = cv.take(8 * (NB / 2048 + 2));
+  E.o_tot = cv.take(64);
+  E.total = cv.used;
+  return ISX_OK;
+}
+
+// The kernels of an encode, on descriptors already in the region at `base`.
+// Enqueues kernels (and nothing else) on s.
+int launch_encode(const EncodeLayout& E, uint8_t* base, void* d_out, size_t out_capacity, uint64_t* d_tile_offsets, int* d_status,
+                  StageMarks* T, cudaStream_t s) {
+  TileDev* d_tiles = (TileDev*)(base + E.o_tiles);
+  int32_t* d_task = (int32_t*)(base + E.o_task);
+  BlockDev* d_blocks = (BlockDev*)(base + E.o_blocks);
+  int32_t* A = (int32_t*)(base + E.o_A);
+  int32_t* B = (int32_t*)(base + E.o_B);
+  uint8_t* coef = base + E.o_coef;
+  T->mark("encode.plan", s);
+  int L = launch_plan_blocks(d_tiles, E.n_tiles, 0, d_blocks, s);
+  T->mark("encode.transform", s);
+  for (const FusedClass& c : E.cls)
+    L += launch_fused_forward(d_tiles, d_task + c.begin, c.count, c.smem, c.threads, d_blocks, coef, d_status, s);
+  if (E.n_fused < E.n_tiles) {
+    T->mark("encode.transform_global", s);
+    L += launch_forward_transform(d_tiles, E.n_tiles, E.max_levels, E.max_dim, A, B, d_status, s);
+    T->mark("encode.pack", s);
+    L += launch_pack_blocks(d_tiles, d_blocks, E.n_blocks, A, coef, s);
+  }
+  EncodeBuffers eb;
+  eb.tiles = d_tiles; eb.n_tiles = E.n_tiles; eb.blocks = d_blocks; eb.n_blocks = E.n_blocks; eb.coef = coef;
+  eb.sym = base + E.o_sym;
+  eb.stats = (BlockStats*)(base + E.o_stats);
+  eb.codes = (BlockCode*)(base + E.o_codes);
+  eb.hdrs = base + E.o_hdrs;
+  eb.item_size = (int64_t*)(base + E.o_is); eb.final_pos = (int64_t*)(base + E.o_fp);
+  eb.scan_part = (int64_t*)(base + E.o_part); eb.totals = (int64_t*)(base + E.o_tot);
+  eb.bucket = (int64_t*)(base + E.o_bucket); eb.perm = (int64_t*)(base + E.o_perm);
+  eb.out = (uint8_t*)d_out; eb.out_capacity = (int64_t)out_capacity;
+  eb.tile_offsets = d_tile_offsets; eb.status = d_status;
+  L += launch_encode_coding(eb, s, T);
+  T->mark(nullptr, s);
+  return L;
+}
+
+// ------------------------------------------------------------ decode
+// One decode job: the part of tile `tile` inside (rx, ry, rw, rh) (level-z
+// pixels) into out, whose first byte is pixel (rx, ry).
+struct Job {
+  int32_t tile, rx, ry, rw, rh;
+  void* out;
+  int64_t pitch;
+};
+
+struct DecodeLayout {
+  int32_t nsel = 0;
+  int z = 0, drop = 0;
+  int64_t n_blocks = 0, plane_total = 0, fplane_total = 0, sym_cap = 0, max_items = 0;
+  int max_levels = 0, max_dim = 1, n_fused = 0;
+  FusedClass cls[ISX_SIZE_CLASSES];
+  size_t o_tiles = 0, o_idx = 0, o_task = 0, o_blocks = 0, o_bb = 0, o_bl = 0, o_info = 0, o_sb = 0, o_so = 0, o_part = 0, o_tot = 0;
+  size_t o_tab = 0, o_bucket = 0, o_items = 0, o_sym = 0, o_A = 0, o_B = 0, o_fp = 0, o_tk = 0, total = 0;
+};
+
+// Host planning of a decode: one descriptor per job whose tile meets its
+// rectangle (h_tiles, h_index, h_task hold n_jobs entries).
+isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* jobs, int32_t n_jobs, int z, int drop, const Schedule& S,
+                       TileDev* h_tiles, int64_t* h_index, int32_t* h_task, DecodeLayout& D, std::string* err) {
+  D = DecodeLayout();
+  D.z = z;
+  D.drop = drop;
+  std::vector<std::pair<int32_t, int>> fused;
+  for (int32_t j = 0; j < n_jobs; ++j) {
+    const Job& jb = jobs[j];
+    if (jb.tile < 0 || jb.tile >= n_tiles) { *err = "job " + std::to_string(j) + ": tile index out of range"; return ISX_ERR_ARG; }
+    if (!jb.out || jb.rw < 1 || jb.rh < 1) { *err = "job " + std::to_string(j) + ": bad output rectangle"; return ISX_ERR_ARG; }
+    const isx_tile_desc& t = tiles[jb.tile];
+    std::string why;
+    if (!tile_ok(t, &why)) { *err = "tile " + std::to_string(jb.tile) + ": " + why; return ISX_ERR_ARG; }
+    const int zw = level_dim(t.width, z), zh = level_dim(t.height, z);
+    const int tx = t.x0 >> z, ty = t.y0 >> z;
+    if (tx >= jb.rx + jb.rw || ty >= jb.ry + jb.rh || tx + zw <= jb.rx || ty + zh <= jb.ry) continue;
+    if (z > t.levels) { *err = "level exceeds the levels of tile " + std::to_string(jb.tile); return ISX_ERR_ARG; }
+    if (jb.pitch < (int64_t)jb.rw * t.channels * (t.bits <= 8 ? 1 : 2)) {
+      *err = "job " + std::to_string(j) + ": output pitch too small";
+      return ISX_ERR_ARG;
+    }
+    int64_t nb, nc;
+    tile_counts(t, z, &nb, &nc);
+    // symbols of every kept plane: at most (1 + magnitude bits) planes of p*w*h/8 bytes each, plus padding
+    D.sym_cap += (int64_t)(t.bits <= 12 ? 16 : kMaxD) * (nc / 8) + 16 * kMaxD * nb;
+    D.max_items += (int64_t)(t.bits <= 12 ? 16 : kMaxD) * nb;
+    TileDev& d = h_tiles[D.nsel];
+    fill_tiledev(d, t);
+    d.nb = (int32_t)nb;
+    d.block_base = D.n_blocks;
+    d.coef_base = 0;
+    d.fused = fused_tile(zw, zh, t.bits) ? 1 : 0;
+    d.dst = (uint8_t*)jb.out;
+    d.dpitch = jb.pitch;
+    d.rx = jb.rx; d.ry = jb.ry; d.rw = jb.rw; d.rh = jb.rh;
+    if (d.fused) {
+      // three-channel tiles hand their int16 planes between CTAs: 16-byte aligned
+      d.plane_base = D.fplane_total;
+      if (t.channels == 3) D.fplane_total += (3LL * zw * zh + 7) & ~7LL;
+      fused.push_back({D.nsel, fused_plane_bytes(zw, zh)});
+    } else {
+      d.plane_base = D.plane_total;
+      D.plane_total += (int64_t)t.channels * zw * zh;
+    }
+    h_index[D.nsel] = jb.tile;
+    ++D.nsel;
+    D.n_blocks += nb;
+    D.max_levels = std::max(D.max_levels, t.levels);
+    D.max_dim = std::max(D.max_dim, std::max(t.width, t.height));
+  }
+  D.n_fused = (int)fused.size();
+  group_fused(fused, S.inv, h_task, D.cls);
+  const int64_t nb = D.n_blocks;
+  Carve cv;
+  D.o_tiles = cv.take(sizeof(TileDev) * (size_t)std::max(D.nsel, 1));
+  D.o_idx = cv.take(8 * (size_t)std::max(D.nsel, 1));
+  D.o_task = cv.take(4 * (size_t)std::max(D.n_fused, 1));
+  D.o_blocks = cv.take(sizeof(BlockDev) * nb);
+  D.o_bb = cv.take(8 * nb);
+  D.o_bl = cv.take(4 * nb);
+  D.o_info = cv.take(sizeof(DecInfo) * nb);
+  D.o_sb = cv.take(8 * nb);
+  D.o_so = cv.take(8 * nb);
+  D.o_part = cv.take(8 * (nb / 2048 + 2));
+  D.o_tot = cv.take(64);
+  D.o_tab = cv.take(dec_table_bytes() * nb);
+  D.o_bucket = cv.take(8 * 2 * 512);
+  D.o_items = cv.take(8 * (size_t)D.max_items);
+  D.o_sym = cv.take((size_t)D.sym_cap + 64);
+  D.o_A = cv.take(4 * (size_t)D.plane_total);
+  D.o_B = cv.take(4 * (size_t)D.plane_total);
+  D.o_fp = cv.take(2 * (size_t)D.fplane_total);
+  D.o_tk = cv.take(4 * (size_t)std::max(D.n_fused, 1));
+  D.total = cv.used;
+  return ISX_OK;
+}
+
+// The kernels (and ticket clears) of a decode on descriptors already at base.
+int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, const uint64_t* d_tile_offsets, int* d_status,
+                  StageMarks* T, cudaStream_t s) {
+  if (D.nsel == 0) return 0;
+  TileDev* d_tiles = (TileDev*)(base + D.o_tiles);
+  int32_t* d_task = (int32_t*)(base + D.o_task);
+  DecodeBuffers db;
+  db.tiles = d_tiles; db.n_tiles = D.nsel; db.tile_index = (int64_t*)(base + D.o_idx);
+  db.stream = (const uint8_t*)d_stream; db.stream_offsets = d_tile_offsets;
+  db.blocks = (BlockDev*)(base + D.o_blocks); db.block_byte = (int64_t*)(base + D.o_bb); db.block_len = (int32_t*)(base + D.o_bl);
+  db.n_blocks = D.n_blocks; db.z = D.z; db.drop = D.drop;
+  db.planes = (int32_t*)(base + D.o_A); db.status = d_status;
+  db.info = (DecInfo*)(base + D.o_info); db.sym_bytes = (int64_t*)(base + D.o_sb); db.sym_off = (int64_t*)(base + D.o_so);
+  db.scan_part = (int64_t*)(base + D.o_part); db.totals = (int64_t*)(base + D.o_tot);
+  db.sym = base + D.o_sym; db.sym_cap = D.sym_cap;
+  db.tables = base + D.o_tab; db.bucket = (int64_t*)(base + D.o_bucket); db.items = (int64_t*)(base + D.o_items);
+  db.max_items = D.max_items;
+  int L = launch_decode_blocks(db, s, T);
+  T->mark("decode.inverse_transform", s);
+  uint32_t* tickets = (uint32_t*)(base + D.o_tk);
+  if (D.n_fused) cudaMemsetAsync(tickets, 0, 4 * (size_t)D.n_fused, s);
+  for (const FusedClass& c : D.cls)
+    L += launch_fused_inverse(d_tiles, d_task + c.begin, c.count, c.smem, c.threads, db, (int16_t*)(base + D.o_fp), tickets + c.begin, s);
+  if (D.n_fused < D.nsel) {
+    T->mark("decode.inverse_global", s);
+    L += launch_inverse_transform(d_tiles, D.nsel, D.max_levels, D.z, D.max_dim, (int32_t*)(base + D.o_A), (int32_t*)(base + D.o_B), s);
+    T->mark("decode.store", s);
+    L += launch_store_region(d_tiles, D.nsel, D.z, (int32_t*)(base + D.o_A), s);
+  }
+  T->mark(nullptr, s);
+  return L;
+}
+
+struct NoMarks : StageMarks {
+  void mark(const char*, cudaStream_t) override {}
+};
+
+// Decode of jobs through the context: plan, arena, descriptor upload, kernels.
+isx_status decode_jobs_ctx(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets, const isx_tile_desc* tiles,
+                           int32_t n_tiles, const Job* jobs, int32_t n_jobs, int z, int drop, cudaStream_t s) {
+  ISX_CUDA(cudaSetDevice(ctx->device));
+  isx_status st = ensure_staging(ctx, (size_t)std::max(n_jobs, 1));
+  if (st != ISX_OK) return st;
+  DecodeLayout D;
+  std::string err;
+  st = plan_decode(tiles, n_tiles, jobs, n_jobs, z, drop, ctx->sched, ctx->h_tiles, ctx->h_index, ctx->h_task, D, &err);
+  if (st != ISX_OK) return fail(ctx, st, err);
+  ctx->launches = 0;
+  if (D.nsel == 0) return ISX_OK;
+  st = ensure_arena(ctx, D.total);
+  if (st != ISX_OK) return st;
+  uint8_t* ar = ctx->arena;
+  ISX_CUDA(cudaMemcpyAsync(ar + D.o_tiles, ctx->h_tiles, sizeof(TileDev) * D.nsel, cudaMemcpyHostToDevice, s));
+  ISX_CUDA(cudaMemcpyAsync(ar + D.o_idx, ctx->h_index, 8 * (size_t)D.nsel, cudaMemcpyHostToDevice, s));
+  if (D.n_fused) ISX_CUDA(cudaMemcpyAsync(ar + D.o_task, ctx->h_task, 4 * (size_t)D.n_fused, cudaMemcpyHostToDevice, s));
+  ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
+  StageTimer& T = ctx->timer;
+  if (T.on && !T.pending.empty()) T.collect();
+  ctx->launches = launch_decode(D, ar, d_stream, d_tile_offsets, ctx->d_status, &T, s);
+  ISX_CUDA(cudaGetLastError());
   return ISX_OK;
 }
 
 }  // namespace
+
+// A prepared encode or decode with its own device memory: launching it only
+// enqueues kernels (and ticket clears), so it can be captured in a CUDA graph.
+struct isx_plan {
+  int kind = 0;   // 1 encode, 2 decode
+  int device = 0;
+  EncodeLayout E;
+  DecodeLayout D;
+  uint8_t* mem = nullptr;
+  size_t mem_bytes = 0;
+  int* d_status = nullptr;
+  int launches = 0;
+  std::string err;
+};
 
 extern "C" {
 
@@ -238,6 +526,7 @@ isx_status isx_create(isx_ctx** out, int device, size_t hbm_budget_bytes) {
   isx_ctx* ctx = new isx_ctx();
   ctx->device = device;
   ctx->budget = hbm_budget_bytes;
+  ctx->sched = default_schedule();
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
@@ -302,6 +591,24 @@ const char* isx_last_error(isx_ctx* ctx) { return ctx ? ctx->err.c_str() : "null
 
 int32_t isx_last_launch_count(isx_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+}  // extern "C"
+
+namespace {
+isx_status status_of(isx_ctx* ctx, std::string* err, int st) {
+  switch (st) {
+    case 0: return ISX_OK;
+    case kStCapacity: *err = "output buffer too small; required size in tile_offsets[n_tiles]"; return ISX_ERR_CAPACITY;
+    case kStCorrupt: *err = "malformed compressed stream"; return ISX_ERR_CORRUPT;
+    case kStTimeout: *err = "device wait gave up"; return ISX_ERR_TIMEOUT;
+    case kStRange: *err = "a sample exceeds its tile's bit depth (values must be below 2^bits)"; return ISX_ERR_ARG;
+    default: *err = "internal consistency check failed on the device (code " + std::to_string(st) + ")"; return ISX_ERR_CUDA;
+  }
+  (void)ctx;
+}
+}  // namespace
+
+extern "C" {
+
 isx_status isx_sync_status(isx_ctx* ctx, void* stream) {
   if (!ctx) return ISX_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -309,27 +616,26 @@ isx_status isx_sync_status(isx_ctx* ctx, void* stream) {
   int st = 0;
   ISX_CUDA(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   ISX_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
-  switch (st) {
-    case 0: return ISX_OK;
-    case kStCapacity: return fail(ctx, ISX_ERR_CAPACITY, "output buffer too small; required size in tile_offsets[n_tiles]");
-    case kStCorrupt: return fail(ctx, ISX_ERR_CORRUPT, "malformed compressed stream");
-    case kStTimeout: return fail(ctx, ISX_ERR_TIMEOUT, "device wait gave up");
-    case kStRange: return fail(ctx, ISX_ERR_ARG, "a sample exceeds its tile's bit depth (values must be below 2^bits)");
-    default: return fail(ctx, ISX_ERR_CUDA, "internal consistency check failed on the device (code " + std::to_string(st) + ")");
-  }
+  std::string msg;
+  isx_status r = status_of(ctx, &msg, st);
+  if (r != ISX_OK) ctx->err = msg;
+  return r;
 }
 
 isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, int32_t* d_coef, void* stream) {
   if (!ctx || !tiles || n_tiles < 1 || !d_coef) return fail(ctx, ISX_ERR_ARG, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   ISX_CUDA(cudaSetDevice(ctx->device));
-  EncodePlan P;
-  isx_status st = plan_encode(ctx, tiles, n_tiles, true, false, P);
+  isx_status st = ensure_staging(ctx, (size_t)n_tiles);
   if (st != ISX_OK) return st;
+  EncodeLayout E;
+  std::string err;
+  st = plan_encode(tiles, n_tiles, false, ctx->sched, ctx->h_tiles, ctx->h_task, E, &err);
+  if (st != ISX_OK) return fail(ctx, st, err);
   Carve cv;
   size_t o_tiles = cv.take(sizeof(TileDev) * n_tiles);
-  size_t o_A = cv.take(4 * (size_t)P.plane_total);
-  size_t o_B = cv.take(4 * (size_t)P.plane_total);
+  size_t o_A = cv.take(4 * (size_t)E.plane_total);
+  size_t o_B = cv.take(4 * (size_t)E.plane_total);
   st = ensure_arena(ctx, cv.used);
   if (st != ISX_OK) return st;
   TileDev* d_tiles = (TileDev*)(ctx->arena + o_tiles);
@@ -337,7 +643,7 @@ isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, in
   int32_t* B = (int32_t*)(ctx->arena + o_B);
   ISX_CUDA(cudaMemcpyAsync(d_tiles, ctx->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
   ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
-  int L = launch_forward_transform(d_tiles, n_tiles, P.max_levels, P.max_dim, A, B, ctx->d_status, s);
+  int L = launch_forward_transform(d_tiles, n_tiles, E.max_levels, E.max_dim, A, B, ctx->d_status, s);
   L += launch_quantise_planes(d_tiles, n_tiles, A, d_coef, s);
   ctx->launches = L;
   ISX_CUDA(cudaGetLastError());
@@ -352,62 +658,21 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   if (reinterpret_cast<uintptr_t>(d_out) & 3) return fail(ctx, ISX_ERR_ARG, "d_out must be 4-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   ISX_CUDA(cudaSetDevice(ctx->device));
-  EncodePlan P;
-  isx_status st = plan_encode(ctx, tiles, n_tiles, true, true, P);
+  isx_status st = ensure_staging(ctx, (size_t)n_tiles);
   if (st != ISX_OK) return st;
-  const int64_t NB = P.n_blocks;
-  const int64_t n_part = NB / 2048 + 2;
-  Carve cv;
-  size_t o_tiles = cv.take(sizeof(TileDev) * n_tiles);
-  size_t o_task = cv.take(sizeof(int32_t) * (size_t)std::max(P.n_fused, 1));
-  size_t o_blocks = cv.take(sizeof(BlockDev) * NB);
-  size_t o_A = cv.take(4 * (size_t)P.plane_total);
-  size_t o_B = cv.take(4 * (size_t)P.plane_total);
-  size_t o_coef = cv.take((size_t)P.coef_bytes);
-  size_t o_sym = cv.take((size_t)P.sym_bytes);
-  size_t o_stats = cv.take(sizeof(BlockStats) * NB);
-  size_t o_codes = cv.take(sizeof(BlockCode) * NB);
-  size_t o_hdrs = cv.take(enc_hdr_bytes() * NB);
-  size_t o_is = cv.take(8 * NB), o_fp = cv.take(8 * NB), o_perm = cv.take(8 * NB), o_bucket = cv.take(8 * 64);
-  size_t o_part = cv.take(8 * n_part), o_tot = cv.take(64);
-  st = ensure_arena(ctx, cv.used);
+  EncodeLayout E;
+  std::string err;
+  st = plan_encode(tiles, n_tiles, true, ctx->sched, ctx->h_tiles, ctx->h_task, E, &err);
+  if (st != ISX_OK) return fail(ctx, st, err);
+  st = ensure_arena(ctx, E.total);
   if (st != ISX_OK) return st;
   uint8_t* ar = ctx->arena;
-  TileDev* d_tiles = (TileDev*)(ar + o_tiles);
-  int32_t* d_task = (int32_t*)(ar + o_task);
-  ISX_CUDA(cudaMemcpyAsync(d_tiles, ctx->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
-  if (P.n_fused) ISX_CUDA(cudaMemcpyAsync(d_task, ctx->h_task, sizeof(int32_t) * P.n_fused, cudaMemcpyHostToDevice, s));
+  ISX_CUDA(cudaMemcpyAsync(ar + E.o_tiles, ctx->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
+  if (E.n_fused) ISX_CUDA(cudaMemcpyAsync(ar + E.o_task, ctx->h_task, sizeof(int32_t) * E.n_fused, cudaMemcpyHostToDevice, s));
   ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
-  BlockDev* d_blocks = (BlockDev*)(ar + o_blocks);
-  int32_t* A = (int32_t*)(ar + o_A);
-  int32_t* B = (int32_t*)(ar + o_B);
-  uint8_t* coef = ar + o_coef;
   StageTimer& T = ctx->timer;
   if (T.on && !T.pending.empty()) T.collect();
-  T.mark("encode.plan", s);
-  int L = launch_plan_blocks(d_tiles, n_tiles, 0, d_blocks, s);
-  T.mark("encode.transform", s);
-  L += launch_fused_forward(d_tiles, d_task, P.n_fused, P.max_plane_bytes, d_blocks, coef, ctx->d_status, s);
-  if (P.n_fused < n_tiles) {
-    T.mark("encode.transform_global", s);
-    L += launch_forward_transform(d_tiles, n_tiles, P.max_levels, P.max_dim, A, B, ctx->d_status, s);
-    T.mark("encode.pack", s);
-    L += launch_pack_blocks(d_tiles, d_blocks, NB, A, coef, s);
-  }
-  EncodeBuffers eb;
-  eb.tiles = d_tiles; eb.n_tiles = n_tiles; eb.blocks = d_blocks; eb.n_blocks = NB; eb.coef = coef;
-  eb.sym = ar + o_sym;
-  eb.stats = (BlockStats*)(ar + o_stats);
-  eb.codes = (BlockCode*)(ar + o_codes);
-  eb.hdrs = ar + o_hdrs;
-  eb.item_size = (int64_t*)(ar + o_is); eb.final_pos = (int64_t*)(ar + o_fp);
-  eb.scan_part = (int64_t*)(ar + o_part); eb.totals = (int64_t*)(ar + o_tot);
-  eb.bucket = (int64_t*)(ar + o_bucket); eb.perm = (int64_t*)(ar + o_perm);
-  eb.out = (uint8_t*)d_out; eb.out_capacity = (int64_t)out_capacity;
-  eb.tile_offsets = d_tile_offsets; eb.status = ctx->d_status;
-  L += launch_encode_coding(eb, s, &T);
-  T.mark(nullptr, s);
-  ctx->launches = L;
+  ctx->launches = launch_encode(E, ar, d_out, out_capacity, d_tile_offsets, ctx->d_status, &T, s);
   ISX_CUDA(cudaGetLastError());
   return ISX_OK;
 }
@@ -419,106 +684,41 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   if (!d_stream || !d_tile_offsets || !tiles || n_tiles < 1 || !d_out || rw < 1 || rh < 1 || level < 0 || level > kMaxLevels ||
       drop_lsb_planes < 0 || drop_lsb_planes > kMaxD)
     return fail(ctx, ISX_ERR_ARG, "bad arguments");
-  cudaStream_t s = (cudaStream_t)stream;
-  ISX_CUDA(cudaSetDevice(ctx->device));
-  isx_status st = ensure_staging(ctx, (size_t)n_tiles);
-  if (st != ISX_OK) return st;
-  const int z = level;
+  // one job per tile meeting the rectangle; all write into the one output
+  std::vector<Job> jobs;
   int C = -1, bits = -1;
-  int32_t nsel = 0;
-  int64_t n_blocks = 0, plane_total = 0, sym_cap = 0, max_items = 0;
-  int max_levels = 0, max_dim = 1, n_fused = 0, max_plane_bytes = 0;
-  // fused tiles write their pixels themselves; three-channel ones pass int16 planes between their CTAs
-  const bool fstore = true;
-  int64_t fplane_total = 0;
   for (int32_t i = 0; i < n_tiles; ++i) {
     const isx_tile_desc& t = tiles[i];
     std::string why;
     if (!tile_ok(t, &why)) return fail(ctx, ISX_ERR_ARG, "tile " + std::to_string(i) + ": " + why);
-    const int zw = level_dim(t.width, z), zh = level_dim(t.height, z);
-    const int tx = t.x0 >> z, ty = t.y0 >> z;
+    const int zw = level_dim(t.width, level), zh = level_dim(t.height, level);
+    const int tx = t.x0 >> level, ty = t.y0 >> level;
     if (tx >= rx + rw || ty >= ry + rh || tx + zw <= rx || ty + zh <= ry) continue;
-    if (z > t.levels) return fail(ctx, ISX_ERR_ARG, "level exceeds the levels of tile " + std::to_string(i));
     if (C < 0) { C = t.channels; bits = t.bits; }
     if (t.channels != C || (t.bits <= 8) != (bits <= 8))
       return fail(ctx, ISX_ERR_ARG, "tiles of one region must share channels and sample size");
-    int64_t nb, nc;
-    tile_counts(t, z, &nb, &nc);
-    // symbols of every kept plane: at most (1 + magnitude bits) planes of p*w*h/8 bytes each, plus padding
-    sym_cap += (int64_t)(t.bits <= 12 ? 16 : kMaxD) * (nc / 8) + 16 * kMaxD * nb;
-    max_items += (int64_t)(t.bits <= 12 ? 16 : kMaxD) * nb;
-    TileDev& d = ctx->h_tiles[nsel];
-    fill_tiledev(d, t);
-    d.nb = (int32_t)nb;
-    d.block_base = n_blocks;
-    d.coef_base = 0;
-    d.fused = fused_tile(zw, zh, t.bits) ? 1 : 0;
-    d.plane_base = d.fused && fstore ? fplane_total : plane_total;
-    if (d.fused) {
-      ctx->h_task[n_fused++] = nsel;
-      max_plane_bytes = std::max(max_plane_bytes, fused_plane_bytes(zw, zh));
-    }
-    ctx->h_index[nsel] = i;
-    ++nsel;
-    n_blocks += nb;
-    if (d.fused && fstore) fplane_total += t.channels == 3 ? (3LL * zw * zh + 7) & ~7LL : 0;   // 16-byte aligned planes
-    else plane_total += (int64_t)t.channels * zw * zh;
-    max_levels = std::max(max_levels, t.levels);
-    max_dim = std::max(max_dim, std::max(t.width, t.height));
+    jobs.push_back(Job{i, rx, ry, rw, rh, d_out, out_pitch_bytes});
   }
   if (out_pitch_bytes < (int64_t)rw * std::max(C, 1) * (bits > 8 ? 2 : 1)) return fail(ctx, ISX_ERR_ARG, "output pitch too small");
   ctx->launches = 0;
-  if (nsel == 0) return ISX_OK;
-  Carve cv;
-  size_t o_tiles = cv.take(sizeof(TileDev) * nsel);
-  size_t o_idx = cv.take(8 * (size_t)nsel);
-  size_t o_task = cv.take(4 * (size_t)std::max(n_fused, 1));
-  size_t o_blocks = cv.take(sizeof(BlockDev) * n_blocks);
-  size_t o_bb = cv.take(8 * n_blocks), o_bl = cv.take(4 * n_blocks);
-  size_t o_info = cv.take(sizeof(DecInfo) * n_blocks), o_sb = cv.take(8 * n_blocks), o_so = cv.take(8 * n_blocks);
-  size_t o_part = cv.take(8 * (n_blocks / 2048 + 2)), o_tot = cv.take(64);
-  size_t o_tab = cv.take(dec_table_bytes() * n_blocks), o_bucket = cv.take(8 * 2 * 512), o_items = cv.take(8 * (size_t)max_items);
-  size_t o_sym = cv.take((size_t)sym_cap + 64);
-  size_t o_A = cv.take(4 * (size_t)plane_total), o_B = cv.take(4 * (size_t)plane_total);
-  size_t o_fp = cv.take(2 * (size_t)fplane_total), o_tk = cv.take(4 * (size_t)std::max(n_fused, 1));
-  st = ensure_arena(ctx, cv.used);
-  if (st != ISX_OK) return st;
-  uint8_t* ar = ctx->arena;
-  TileDev* d_tiles = (TileDev*)(ar + o_tiles);
-  int64_t* d_idx = (int64_t*)(ar + o_idx);
-  ISX_CUDA(cudaMemcpyAsync(d_tiles, ctx->h_tiles, sizeof(TileDev) * nsel, cudaMemcpyHostToDevice, s));
-  ISX_CUDA(cudaMemcpyAsync(d_idx, ctx->h_index, 8 * (size_t)nsel, cudaMemcpyHostToDevice, s));
-  int32_t* d_task = (int32_t*)(ar + o_task);
-  if (n_fused) ISX_CUDA(cudaMemcpyAsync(d_task, ctx->h_task, 4 * (size_t)n_fused, cudaMemcpyHostToDevice, s));
-  ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
-  DecodeBuffers db;
-  db.tiles = d_tiles; db.n_tiles = nsel; db.tile_index = d_idx;
-  db.stream = (const uint8_t*)d_stream; db.stream_offsets = d_tile_offsets;
-  db.blocks = (BlockDev*)(ar + o_blocks); db.block_byte = (int64_t*)(ar + o_bb); db.block_len = (int32_t*)(ar + o_bl);
-  db.n_blocks = n_blocks; db.z = z; db.drop = drop_lsb_planes;
-  db.planes = (int32_t*)(ar + o_A); db.status = ctx->d_status;
-  db.info = (DecInfo*)(ar + o_info); db.sym_bytes = (int64_t*)(ar + o_sb); db.sym_off = (int64_t*)(ar + o_so);
-  db.scan_part = (int64_t*)(ar + o_part); db.totals = (int64_t*)(ar + o_tot);
-  db.sym = ar + o_sym; db.sym_cap = sym_cap;
-  db.tables = ar + o_tab; db.bucket = (int64_t*)(ar + o_bucket); db.items = (int64_t*)(ar + o_items); db.max_items = max_items;
-  StageTimer& T = ctx->timer;
-  if (T.on && !T.pending.empty()) T.collect();
-  int L = launch_decode_blocks(db, s, &T);
-  T.mark("decode.inverse_transform", s);
-  FusedStore fs{d_out, out_pitch_bytes, rx, ry, rw, rh, (int16_t*)(ar + o_fp), (uint32_t*)(ar + o_tk)};
-  L += launch_fused_inverse(d_tiles, d_task, n_fused, max_plane_bytes, db, fstore ? &fs : nullptr, s);
-  if (n_fused < nsel) {
-    T.mark("decode.inverse_global", s);
-    L += launch_inverse_transform(d_tiles, nsel, max_levels, z, max_dim, (int32_t*)(ar + o_A), (int32_t*)(ar + o_B), s);
-  }
-  if (!fstore || n_fused < nsel) {
-    T.mark("decode.store", s);
-    L += launch_store_region(d_tiles, nsel, z, (int32_t*)(ar + o_A), d_out, out_pitch_bytes, rx, ry, rw, rh, fstore, s);
-  }
-  T.mark(nullptr, s);
-  ctx->launches = L;
-  ISX_CUDA(cudaGetLastError());
-  return ISX_OK;
+  if (jobs.empty()) return ISX_OK;
+  return decode_jobs_ctx(ctx, d_stream, d_tile_offsets, tiles, n_tiles, jobs.data(), (int32_t)jobs.size(), level, drop_lsb_planes,
+                         (cudaStream_t)stream);
+}
+
+isx_status isx_decode_jobs(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets, const isx_tile_desc* tiles,
+                           int32_t n_tiles, const isx_decode_job* jobs, int32_t n_jobs, int32_t level, int32_t drop_lsb_planes,
+                           void* stream) {
+  if (!ctx) return ISX_ERR_ARG;
+  if (!d_stream || !d_tile_offsets || !tiles || n_tiles < 1 || !jobs || n_jobs < 0 || level < 0 || level > kMaxLevels ||
+      drop_lsb_planes < 0 || drop_lsb_planes > kMaxD)
+    return fail(ctx, ISX_ERR_ARG, "bad arguments");
+  std::vector<Job> J((size_t)n_jobs);
+  for (int32_t j = 0; j < n_jobs; ++j)
+    J[j] = Job{jobs[j].tile, jobs[j].rx, jobs[j].ry, jobs[j].rw, jobs[j].rh, jobs[j].d_out, jobs[j].out_pitch_bytes};
+  ctx->launches = 0;
+  if (n_jobs == 0) return ISX_OK;
+  return decode_jobs_ctx(ctx, d_stream, d_tile_offsets, tiles, n_tiles, J.data(), n_jobs, level, drop_lsb_planes, (cudaStream_t)stream);
 }
 
 isx_status isx_encode_tiles_host(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, void* h_out, size_t out_capacity,
@@ -630,6 +830,258 @@ isx_status isx_decode_region_host(isx_ctx* ctx, const void* h_stream, const uint
   st = isx_sync_status(ctx, stream);
   ctx->launches = L;
   return st;
+}
+
+
+// ---------------------------------------------------------------- schedule
+isx_status isx_get_schedule(isx_ctx* ctx, isx_schedule* out) {
+  if (!ctx || !out) return ISX_ERR_ARG;
+  for (int k = 0; k < ISX_SIZE_CLASSES; ++k) {
+    out->forward_threads[k] = ctx->sched.fwd[k];
+    out->inverse_threads[k] = ctx->sched.inv[k];
+  }
+  return ISX_OK;
+}
+
+isx_status isx_set_schedule(isx_ctx* ctx, const isx_schedule* sch) {
+  if (!ctx || !sch) return ISX_ERR_ARG;
+  for (int k = 0; k < ISX_SIZE_CLASSES; ++k)
+    if (!valid_threads(sch->forward_threads[k]) || !valid_threads(sch->inverse_threads[k]))
+      return fail(ctx, ISX_ERR_ARG, "threads per CTA must be 256, 512 or 1024");
+  for (int k = 0; k < ISX_SIZE_CLASSES; ++k) {
+    ctx->sched.fwd[k] = sch->forward_threads[k];
+    ctx->sched.inv[k] = sch->inverse_threads[k];
+  }
+  return ISX_OK;
+}
+
+isx_status isx_autotune(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, int32_t reps, void* stream) {
+  if (!ctx) return ISX_ERR_ARG;
+  if (!tiles || n_tiles < 1 || reps < 1) return fail(ctx, ISX_ERR_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  ISX_CUDA(cudaSetDevice(ctx->device));
+  static const int kCand[3] = {256, 512, 1024};
+  // encode once into a scratch stream, growing it if the estimate is short
+  std::vector<TileDev> ht(n_tiles);
+  std::vector<int32_t> htask(n_tiles);
+  EncodeLayout E;
+  std::string err;
+  isx_status st = plan_encode(tiles, n_tiles, true, ctx->sched, ht.data(), htask.data(), E, &err);
+  if (st != ISX_OK) return fail(ctx, st, err);
+  size_t cap = 4096;
+  for (int32_t i = 0; i < n_tiles; ++i)
+    cap += (size_t)tiles[i].width * tiles[i].height * tiles[i].channels * 4 + 4096;
+  uint8_t* d_mem = nullptr;
+  const size_t stream_off = (E.total + 255) & ~(size_t)255;
+  const size_t offs_off = stream_off + ((cap + 255) & ~(size_t)255);
+  ISX_CUDA(cudaMalloc(&d_mem, offs_off + 8 * (size_t)(n_tiles + 1)));
+  struct Free { uint8_t* p; ~Free() { if (p) cudaFree(p); } } guard{d_mem};
+  ISX_CUDA(cudaMemcpy(d_mem + E.o_tiles, ht.data(), sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice));
+  if (E.n_fused) ISX_CUDA(cudaMemcpy(d_mem + E.o_task, htask.data(), 4 * (size_t)E.n_fused, cudaMemcpyHostToDevice));
+  NoMarks nm;
+  uint64_t* d_offs = (uint64_t*)(d_mem + offs_off);
+  launch_encode(E, d_mem, d_mem + stream_off, cap, d_offs, ctx->d_status, &nm, s);
+  st = isx_sync_status(ctx, stream);
+  if (st != ISX_OK) return st;
+  cudaEvent_t e0, e1;
+  ISX_CUDA(cudaEventCreate(&e0));
+  ISX_CUDA(cudaEventCreate(&e1));
+  auto time_ms = [&](auto&& launch) {
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  Schedule best = ctx->sched;
+  for (int k = 0; k < ISX_SIZE_CLASSES; ++k) {
+    const FusedClass& c = E.cls[k];
+    if (!c.count) continue;
+    float best_ms = 1e30f;
+    for (int t : kCand) {
+      const float ms = time_ms([&] {
+        launch_fused_forward((TileDev*)(d_mem + E.o_tiles), (int32_t*)(d_mem + E.o_task) + c.begin, c.count, c.smem, t,
+                             (BlockDev*)(d_mem + E.o_blocks), d_mem + E.o_coef, ctx->d_status, s);
+      });
+      if (ms < best_ms) { best_ms = ms; best.fwd[k] = t; }
+    }
+  }
+  // decode every tile whole into its own output
+  std::vector<Job> jobs(n_tiles);
+  size_t out_bytes = 0;
+  for (int32_t i = 0; i < n_tiles; ++i) {
+    const isx_tile_desc& t = tiles[i];
+    const int64_t pitch = (int64_t)t.width * t.channels * (t.bits <= 8 ? 1 : 2);
+    jobs[i] = Job{i, t.x0, t.y0, t.width, t.height, (void*)(uintptr_t)out_bytes, pitch};
+    out_bytes += ((size_t)pitch * t.height + 15) & ~(size_t)15;
+  }
+  std::vector<TileDev> dt(n_tiles);
+  std::vector<int64_t> didx(n_tiles);
+  std::vector<int32_t> dtask(n_tiles);
+  DecodeLayout D;
+  uint8_t* d_dec = nullptr;
+  ISX_CUDA(cudaMalloc(&d_dec, out_bytes));
+  struct Free2 { uint8_t* p; ~Free2() { if (p) cudaFree(p); } } guard2{d_dec};
+  for (auto& j : jobs) j.out = d_dec + (uintptr_t)j.out;
+  st = plan_decode(tiles, n_tiles, jobs.data(), n_tiles, 0, 0, ctx->sched, dt.data(), didx.data(), dtask.data(), D, &err);
+  if (st != ISX_OK) return fail(ctx, st, err);
+  st = ensure_arena(ctx, D.total);
+  if (st != ISX_OK) return st;
+  uint8_t* ar = ctx->arena;
+  ISX_CUDA(cudaMemcpy(ar + D.o_tiles, dt.data(), sizeof(TileDev) * D.nsel, cudaMemcpyHostToDevice));
+  ISX_CUDA(cudaMemcpy(ar + D.o_idx, didx.data(), 8 * (size_t)D.nsel, cudaMemcpyHostToDevice));
+  if (D.n_fused) ISX_CUDA(cudaMemcpy(ar + D.o_task, dtask.data(), 4 * (size_t)D.n_fused, cudaMemcpyHostToDevice));
+  launch_decode(D, ar, d_mem + stream_off, d_offs, ctx->d_status, &nm, s);
+  st = isx_sync_status(ctx, stream);
+  if (st != ISX_OK) return st;
+  DecodeBuffers db;   // the fused inverse reads only these fields
+  db.blocks = (BlockDev*)(ar + D.o_blocks); db.info = (DecInfo*)(ar + D.o_info); db.sym_off = (int64_t*)(ar + D.o_so);
+  db.sym = ar + D.o_sym; db.totals = (int64_t*)(ar + D.o_tot); db.sym_cap = D.sym_cap; db.z = 0;
+  uint32_t* tickets = (uint32_t*)(ar + D.o_tk);
+  for (int k = 0; k < ISX_SIZE_CLASSES; ++k) {
+    const FusedClass& c = D.cls[k];
+    if (!c.count) continue;
+    float best_ms = 1e30f;
+    for (int t : kCand) {
+      const float ms = time_ms([&] {
+        cudaMemsetAsync(tickets + c.begin, 0, 4 * (size_t)c.count, s);
+        launch_fused_inverse((TileDev*)(ar + D.o_tiles), (int32_t*)(ar + D.o_task) + c.begin, c.count, c.smem, t, db,
+                             (int16_t*)(ar + D.o_fp), tickets + c.begin, s);
+      });
+      if (ms < best_ms) { best_ms = ms; best.inv[k] = t; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ISX_CUDA(cudaGetLastError());
+  st = isx_sync_status(ctx, stream);
+  if (st != ISX_OK) return st;
+  ctx->sched = best;
+  return ISX_OK;
+}
+
+// ---------------------------------------------------------------- plans
+isx_status isx_plan_encode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, isx_plan** out) {
+  if (!ctx) return ISX_ERR_ARG;
+  if (!out || !tiles || n_tiles < 1) return fail(ctx, ISX_ERR_ARG, "bad arguments");
+  *out = nullptr;
+  ISX_CUDA(cudaSetDevice(ctx->device));
+  isx_plan* P = new isx_plan();
+  P->kind = 1;
+  P->device = ctx->device;
+  std::vector<TileDev> ht(n_tiles);
+  std::vector<int32_t> htask(n_tiles);
+  std::string err;
+  isx_status st = plan_encode(tiles, n_tiles, true, ctx->sched, ht.data(), htask.data(), P->E, &err);
+  cudaError_t e = cudaSuccess;
+  if (st == ISX_OK) {
+    P->mem_bytes = P->E.total;
+    e = cudaMalloc(&P->mem, P->mem_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(P->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(P->mem + P->E.o_tiles, ht.data(), sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && P->E.n_fused)
+      e = cudaMemcpy(P->mem + P->E.o_task, htask.data(), 4 * (size_t)P->E.n_fused, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaGetLastError(); st = ISX_ERR_OOM; err = std::string("plan memory: ") + cudaGetErrorString(e); }
+  }
+  if (st != ISX_OK) {
+    isx_plan_destroy(P);
+    return fail(ctx, st, err);
+  }
+  *out = P;
+  return ISX_OK;
+}
+
+isx_status isx_plan_decode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, const isx_decode_job* jobs, int32_t n_jobs,
+                           int32_t level, int32_t drop_lsb_planes, isx_plan** out) {
+  if (!ctx) return ISX_ERR_ARG;
+  if (!out || !tiles || n_tiles < 1 || !jobs || n_jobs < 1 || level < 0 || level > kMaxLevels || drop_lsb_planes < 0 ||
+      drop_lsb_planes > kMaxD)
+    return fail(ctx, ISX_ERR_ARG, "bad arguments");
+  *out = nullptr;
+  ISX_CUDA(cudaSetDevice(ctx->device));
+  isx_plan* P = new isx_plan();
+  P->kind = 2;
+  P->device = ctx->device;
+  std::vector<Job> J((size_t)n_jobs);
+  for (int32_t j = 0; j < n_jobs; ++j)
+    J[j] = Job{jobs[j].tile, jobs[j].rx, jobs[j].ry, jobs[j].rw, jobs[j].rh, jobs[j].d_out, jobs[j].out_pitch_bytes};
+  std::vector<TileDev> ht(n_jobs);
+  std::vector<int64_t> hidx(n_jobs);
+  std::vector<int32_t> htask(n_jobs);
+  std::string err;
+  isx_status st = plan_decode(tiles, n_tiles, J.data(), n_jobs, level, drop_lsb_planes, ctx->sched, ht.data(), hidx.data(), htask.data(),
+                              P->D, &err);
+  cudaError_t e = cudaSuccess;
+  if (st == ISX_OK) {
+    P->mem_bytes = P->D.total;
+    e = cudaMalloc(&P->mem, P->mem_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(P->d_status, 0, sizeof(int));
+    if (e == cudaSuccess && P->D.nsel) {
+      e = cudaMemcpy(P->mem + P->D.o_tiles, ht.data(), sizeof(TileDev) * P->D.nsel, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(P->mem + P->D.o_idx, hidx.data(), 8 * (size_t)P->D.nsel, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && P->D.n_fused)
+        e = cudaMemcpy(P->mem + P->D.o_task, htask.data(), 4 * (size_t)P->D.n_fused, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) { cudaGetLastError(); st = ISX_ERR_OOM; err = std::string("plan memory: ") + cudaGetErrorString(e); }
+  }
+  if (st != ISX_OK) {
+    isx_plan_destroy(P);
+    return fail(ctx, st, err);
+  }
+  *out = P;
+  return ISX_OK;
+}
+
+isx_status isx_plan_launch_encode(isx_plan* plan, void* d_out, size_t out_capacity, uint64_t* d_tile_offsets, void* stream) {
+  if (!plan || plan->kind != 1) return ISX_ERR_ARG;
+  if (!d_tile_offsets || (!d_out && out_capacity) || (reinterpret_cast<uintptr_t>(d_out) & 3)) {
+    plan->err = "bad arguments (d_out must be 4-byte aligned)";
+    return ISX_ERR_ARG;
+  }
+  NoMarks nm;
+  plan->launches = launch_encode(plan->E, plan->mem, d_out, out_capacity, d_tile_offsets, plan->d_status, &nm, (cudaStream_t)stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { plan->err = cudaGetErrorString(e); return ISX_ERR_CUDA; }
+  return ISX_OK;
+}
+
+isx_status isx_plan_launch_decode(isx_plan* plan, const void* d_stream, const uint64_t* d_tile_offsets, void* stream) {
+  if (!plan || plan->kind != 2) return ISX_ERR_ARG;
+  if (!d_stream || !d_tile_offsets) { plan->err = "bad arguments"; return ISX_ERR_ARG; }
+  NoMarks nm;
+  plan->launches = launch_decode(plan->D, plan->mem, d_stream, d_tile_offsets, plan->d_status, &nm, (cudaStream_t)stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { plan->err = cudaGetErrorString(e); return ISX_ERR_CUDA; }
+  return ISX_OK;
+}
+
+isx_status isx_plan_sync_status(isx_plan* plan, void* stream) {
+  if (!plan) return ISX_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(plan->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) { plan->err = cudaGetErrorString(e); return ISX_ERR_CUDA; }
+  return status_of(nullptr, &plan->err, st);
+}
+
+size_t isx_plan_device_bytes(const isx_plan* plan) { return plan ? plan->mem_bytes + sizeof(int) : 0; }
+
+int32_t isx_plan_launch_count(const isx_plan* plan) { return plan ? plan->launches : 0; }
+
+const char* isx_plan_last_error(const isx_plan* plan) { return plan ? plan->err.c_str() : "null plan"; }
+
+void isx_plan_destroy(isx_plan* plan) {
+  if (!plan) return;
+  cudaSetDevice(plan->device);
+  if (plan->mem || plan->d_status) cudaDeviceSynchronize();
+  if (plan->mem) cudaFree(plan->mem);
+  if (plan->d_status) cudaFree(plan->d_status);
+  delete plan;
 }
 
 }  // extern "C"

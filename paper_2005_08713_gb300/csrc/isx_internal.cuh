@@ -12,6 +12,7 @@ constexpr int kMaxD = 31;           // block bit depth field is 5 bits
 constexpr int kMaxW = 18;           // largest zero-run counter width considered (w in [2, b], b <= 18)
 constexpr int kCtaThreads = 256;    // CTA size of the per-block coding kernels
 constexpr int kMaxDConst = 31;
+constexpr int kSmemPlaneBytes = 160 * 1024;   // largest int16 channel plane of a tile on the fused shared-memory path
 
 enum DevStatus : int { kStOk = 0, kStCapacity = 2, kStCorrupt = 3, kStTimeout = 6, kStRange = 8 };
 
@@ -27,6 +28,12 @@ struct TileDev {
   int64_t plane_base;       // element offset of its first Mallat plane
   int64_t coef_base;        // byte offset of its first area-ordered coefficient block
   int64_t sym_base;         // byte offset of its first block's symbol region (encode)
+  // decode destination: the part of the tile inside the rectangle (rx, ry,
+  // rw, rh) of level-z pixels goes to dst, whose first byte is pixel
+  // (rx, ry); rows dpitch bytes apart, the tile's own sample format
+  uint8_t* dst;
+  int64_t dpitch;
+  int32_t rx, ry, rw, rh;
 };
 
 // One coefficient block (Fig. 3): LL (p = 1) or HL, LH, HH (p = 3).

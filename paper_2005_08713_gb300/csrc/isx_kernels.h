@@ -14,17 +14,17 @@ int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels
                              cudaStream_t s);
 int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t n_blocks, const int32_t* planes, void* coef,
                        cudaStream_t s);
-int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const BlockDev* d_blocks,
-                         void* coef, int* status, cudaStream_t s);
+// Fused forward transform of n_fused tiles of one size class (as above).
+int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int smem_bytes, int threads,
+                         const BlockDev* d_blocks, void* coef, int* status, cudaStream_t s);
 bool fused_tile(int w, int h, int bits);
 int fused_plane_bytes(int w, int h);
 void transform_set_attributes();
 int launch_quantise_planes(const TileDev* d_tiles, int n_tiles, const int32_t* planes, int32_t* out, cudaStream_t s);
 int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int32_t* A, int32_t* B,
                              cudaStream_t s);
-// skip_fused: tiles with TileDev::fused set were written by the fused inverse kernel
-int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, void* out, int64_t pitch, int rx, int ry,
-                        int rw, int rh, bool skip_fused, cudaStream_t s);
+// Pixels of the tiles not taken by the fused kernels (TileDev::fused = 0) into their destinations.
+int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, cudaStream_t s);
 
 // encode coding stages
 struct EncodeBuffers {
@@ -86,19 +86,14 @@ struct DecodeBuffers {
   int* status;
 };
 int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T);
-// Region output of the fused inverse: when given, the fused kernel writes
-// the tiles' pixels itself; three-channel tiles leave their int16 channel
-// planes in planes16 (TileDev::plane_base, channels x zw x zh each) and the
-// last CTA of each tile (one ticket per fused tile) converts them.
-struct FusedStore {
-  void* out;
-  int64_t pitch;
-  int rx, ry, rw, rh;
-  int16_t* planes16;
-  uint32_t* tickets;   // [n_fused], cleared by the launch
-};
-int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const DecodeBuffers& db,
-                         const FusedStore* fs, cudaStream_t s);
+// Fused inverse (decode) of n_fused tiles of one size class, CTAs of
+// `threads` threads (256, 512 or 1024) with smem_bytes of plane: each tile's
+// pixels go to its destination (TileDev::dst); three-channel tiles pass
+// their int16 channel planes through planes16 (TileDev::plane_base) and the
+// last CTA of each tile, found with tickets[n_fused] (zeroed beforehand),
+// inverts the colour transform.
+int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int smem_bytes, int threads,
+                         const DecodeBuffers& db, int16_t* planes16, uint32_t* tickets, cudaStream_t s);
 size_t dec_table_bytes();
 int launch_level_sort(const BlockDev* blocks, int64_t nb, int64_t* bucket /* 2 * 16 */, int64_t* perm, int64_t* scan_part,
                       int64_t* total, cudaStream_t s);

@@ -160,7 +160,7 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   k_static_begin<<<1, 1, 0, s>>>(td, d_tile, d_task, d_status);
   launch_plan_blocks(d_tile, 1, 0, d_blocks, s);
   if (fused) {
-    launch_fused_forward(d_tile, d_task, 1, fused_plane_bytes(t.width, t.height), d_blocks, coef, d_status, s);
+    launch_fused_forward(d_tile, d_task, 1, fused_plane_bytes(t.width, t.height), 1024, d_blocks, coef, d_status, s);
   } else {
     launch_forward_transform(d_tile, 1, t.levels, std::max(t.width, t.height), (int32_t*)(ar + o_A), (int32_t*)(ar + o_B), d_status, s);
     launch_pack_blocks(d_tile, d_blocks, nb, (int32_t*)(ar + o_A), coef, s);

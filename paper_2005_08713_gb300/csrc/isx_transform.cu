@@ -317,10 +317,12 @@ __global__ void k_quantise_planes(const TileDev* __restrict__ tiles, const int32
 // Inverse RCT (G = Y - floor((Cb+Cr)/4), R = Cr + G, B = Cb + G), clamp to
 // [0, 2^bits - 1] and write the part of the tile's level-z image that
 // falls inside the requested rectangle.
-__global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const int32_t* __restrict__ planes, uint8_t* __restrict__ out,
-                               int64_t pitch, int rx, int ry, int rw, int rh, int skip_fused) {
+__global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const int32_t* __restrict__ planes) {
   const TileDev& t = tiles[blockIdx.x];
-  if (skip_fused && t.fused) return;   // written by the fused inverse kernel
+  if (t.fused) return;   // written by the fused inverse kernel
+  uint8_t* __restrict__ out = t.dst;
+  const int64_t pitch = t.dpitch;
+  const int rx = t.rx, ry = t.ry, rw = t.rw, rh = t.rh;
   const int zw = level_dim(t.w, z), zh = level_dim(t.h, z);
   const int tx = t.x0 >> z, ty = t.y0 >> z;
   const int64_t np = (int64_t)zw * zh;
@@ -353,8 +355,7 @@ __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const i
 // 2^15) are transformed by one CTA per (tile, channel), in place on the
 // interleaved layout: after level l the LL samples sit at multiples of 2^l,
 // and the high-pass samples of level l at odd multiples of 2^(l-1).
-constexpr int kSmemPlaneBytes = 160 * 1024;
-constexpr int kFusedThreads = 1024;
+constexpr int kFusedThreads = 1024;   // most threads of a fused CTA (launches use 256, 512 or 1024)
 
 __host__ __device__ inline int smem_pitch(int w);
 __host__ __device__ inline bool tile_uses_smem(int w, int h, int bits) {
@@ -671,8 +672,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
 // through L2).  Each thread converts four pixels of a row (inverse RCT,
 // clamp to [0, 2^bits - 1]).
 __device__ inline void store_tile_rgb(const TileDev& t, int z, int zw, int zh, int c, const int16_t* P, int pitch,
-                                      const int16_t* __restrict__ gp, uint8_t* __restrict__ out, int64_t opitch, int rx, int ry, int rw,
-                                      int rh) {
+                                      const int16_t* __restrict__ gp) {
+  uint8_t* __restrict__ out = t.dst;
+  const int64_t opitch = t.dpitch;
+  const int rx = t.rx, ry = t.ry, rw = t.rw, rh = t.rh;
   const int tx = (t.x0 >> z) - rx, ty = (t.y0 >> z) - ry;   // tile origin in the output
   const int32_t maxv = (1 << t.bits) - 1;
   const int qw = (zw + 3) >> 2;
@@ -742,8 +745,10 @@ __device__ inline void store_tile_rgb(const TileDev& t, int z, int zw, int zh, i
 
 // One-channel tile: samples clamped to [0, 2^bits - 1], uint8 (bits <= 8)
 // or uint16 output.
-__device__ inline void store_tile_mono(const TileDev& t, int z, int zw, int zh, const int16_t* P, int pitch, uint8_t* __restrict__ out,
-                                       int64_t opitch, int rx, int ry, int rw, int rh) {
+__device__ inline void store_tile_mono(const TileDev& t, int z, int zw, int zh, const int16_t* P, int pitch) {
+  uint8_t* __restrict__ out = t.dst;
+  const int64_t opitch = t.dpitch;
+  const int rx = t.rx, ry = t.ry, rw = t.rw, rh = t.rh;
   const int tx = (t.x0 >> z) - rx, ty = (t.y0 >> z) - ry;
   const int32_t maxv = (1 << t.bits) - 1;
   for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
@@ -775,14 +780,11 @@ __device__ __forceinline__ void transpose8x8(uint32_t& lo, uint32_t& hi) {
 // dequantised at the bin midpoint and placed into the interleaved int16
 // layout; the CTA then lifts back from level L to level z and writes the
 // LL_z image row-major (int32) for the colour store.
-template <bool kStore>
 __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
                                                                  const BlockDev* __restrict__ blocks, const DecInfo* __restrict__ info,
                                                                  const int64_t* __restrict__ sym_off, const uint8_t* __restrict__ sym,
                                                                  const int64_t* __restrict__ sym_total, int64_t sym_cap, int z,
-                                                                 int32_t* __restrict__ planes, int16_t* __restrict__ fplanes,
-                                                                 uint32_t* __restrict__ tickets, uint8_t* __restrict__ out, int64_t out_pitch,
-                                                                 int rx, int ry, int rw, int rh) {
+                                                                 int16_t* __restrict__ fplanes, uint32_t* __restrict__ tickets) {
   extern __shared__ __align__(16) int16_t P[];
   __shared__ FusedBlock s_fb[kMaxFusedBlocks];
   __shared__ int32_t s_po[kMaxFusedBlocks][kMaxFusedPlanes][3];   // (plane, type) symbols from the block's first; -1: not kept
@@ -862,13 +864,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
   }
   __syncthreads();
   for (int l = t.L - 1; l >= z; --l) level_inv(P, pitch, level_dim(t.w, l), level_dim(t.h, l), 1 << (l - z));
-  if constexpr (!kStore) {
-    int32_t* g = planes + t.plane_base + (int64_t)c * zw * zh;
-    for (int e = threadIdx.x; e < zw * zh; e += blockDim.x) {
-      const int y = e / zw, x = e - y * zw;
-      g[e] = P[y * pitch + x];
-    }
-  } else if (t.C == 3) {
+  if (t.C == 3) {
     // Every CTA leaves its channel plane (int16) in global memory and takes
     // a ticket; the tile's third CTA to finish inverts the colour transform
     // from its own plane and the other two (no CTA waits for another).
@@ -896,9 +892,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    store_tile_rgb(t, z, zw, zh, c, P, pitch, gp, out, out_pitch, rx, ry, rw, rh);
+    store_tile_rgb(t, z, zw, zh, c, P, pitch, gp);
   } else {
-    store_tile_mono(t, z, zw, zh, P, pitch, out, out_pitch, rx, ry, rw, rh);
+    store_tile_mono(t, z, zw, zh, P, pitch);
   }
 }
 
@@ -926,27 +922,18 @@ int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t
   return 1;
 }
 
-int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const BlockDev* d_blocks,
-                         void* coef, int* status, cudaStream_t s) {
+int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int smem_bytes, int threads,
+                         const BlockDev* d_blocks, void* coef, int* status, cudaStream_t s) {
   if (n_fused == 0) return 0;
-  k_fwd_tile_smem<<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, d_blocks, (uint8_t*)coef, status);
+  k_fwd_tile_smem<<<3 * n_fused, threads, smem_bytes, s>>>(d_tiles, d_task_tile, d_blocks, (uint8_t*)coef, status);
   return 1;
 }
 
-int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int max_plane_bytes, const DecodeBuffers& db,
-                         const FusedStore* fs, cudaStream_t s) {
+int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int smem_bytes, int threads,
+                         const DecodeBuffers& db, int16_t* planes16, uint32_t* tickets, cudaStream_t s) {
   if (n_fused == 0) return 0;
-  if (!fs) {
-    k_inv_tile_smem<false><<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, db.blocks, db.info, db.sym_off,
-                                                                             db.sym, db.totals, db.sym_cap, db.z, db.planes, nullptr,
-                                                                             nullptr, nullptr, 0, 0, 0, 0, 0);
-    return 1;
-  }
-  cudaMemsetAsync(fs->tickets, 0, sizeof(uint32_t) * (size_t)n_fused, s);
-  k_inv_tile_smem<true><<<3 * n_fused, kFusedThreads, max_plane_bytes, s>>>(d_tiles, d_task_tile, db.blocks, db.info, db.sym_off, db.sym,
-                                                                          db.totals, db.sym_cap, db.z, db.planes, fs->planes16,
-                                                                          fs->tickets, (uint8_t*)fs->out, fs->pitch, fs->rx, fs->ry,
-                                                                          fs->rw, fs->rh);
+  k_inv_tile_smem<<<3 * n_fused, threads, smem_bytes, s>>>(d_tiles, d_task_tile, db.blocks, db.info, db.sym_off, db.sym, db.totals,
+                                                           db.sym_cap, db.z, planes16, tickets);
   return 1;
 }
 
@@ -955,8 +942,7 @@ int fused_plane_bytes(int w, int h) { return smem_pitch(w) * h * 2; }
 
 void transform_set_attributes() {
   cudaFuncSetAttribute(k_fwd_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
-  cudaFuncSetAttribute(k_inv_tile_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
-  cudaFuncSetAttribute(k_inv_tile_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
+  cudaFuncSetAttribute(k_inv_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
 }
 
 int launch_plan_blocks(const TileDev* d_tiles, int n_tiles, int min_level, BlockDev* d_blocks, cudaStream_t s) {
@@ -983,9 +969,8 @@ int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels
   return launches;
 }
 
-int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, void* out, int64_t pitch, int rx, int ry,
-                        int rw, int rh, bool skip_fused, cudaStream_t s) {
-  k_store_region<<<dim3(n_tiles, 32), 256, 0, s>>>(d_tiles, z, planes, (uint8_t*)out, pitch, rx, ry, rw, rh, skip_fused ? 1 : 0);
+int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, cudaStream_t s) {
+  k_store_region<<<dim3(n_tiles, 32), 256, 0, s>>>(d_tiles, z, planes);
   return 1;
 }
 

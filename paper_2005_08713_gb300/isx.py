@@ -25,7 +25,12 @@ STATUS_NAMES = {0: "ISX_OK", 1: "ISX_ERR_ARG", 2: "ISX_ERR_CAPACITY", 3: "ISX_ER
 # every entry point declared in include/isx.h
 EXPORTS = ["isx_create", "isx_destroy", "isx_encode_tiles", "isx_decode_region", "isx_encode_tiles_host",
            "isx_decode_region_host", "isx_forward_coefficients", "isx_sync_status", "isx_last_launch_count",
-           "isx_last_error", "isx_set_timing", "isx_stage_times", "isx_encode_tile_static"]
+           "isx_last_error", "isx_set_timing", "isx_stage_times", "isx_encode_tile_static", "isx_decode_jobs",
+           "isx_get_schedule", "isx_set_schedule", "isx_autotune", "isx_plan_encode", "isx_plan_decode",
+           "isx_plan_launch_encode", "isx_plan_launch_decode", "isx_plan_sync_status", "isx_plan_device_bytes",
+           "isx_plan_launch_count", "isx_plan_last_error", "isx_plan_destroy"]
+
+SIZE_CLASSES = 5
 
 # size of the library's static device scratch (ISX_STATIC_SCRATCH_BYTES)
 STATIC_SCRATCH_BYTES = 16 << 20
@@ -41,6 +46,15 @@ class TileDescC(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("bits", ctypes.c_int32), ("levels", ctypes.c_int32), ("x0", ctypes.c_int32), ("y0", ctypes.c_int32),
                 ("qstep_log2", ctypes.c_uint8 * 16), ("pixels", ctypes.c_void_p), ("row_pitch_bytes", ctypes.c_int64)]
+
+
+class DecodeJobC(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("rx", ctypes.c_int32), ("ry", ctypes.c_int32), ("rw", ctypes.c_int32),
+                ("rh", ctypes.c_int32), ("d_out", ctypes.c_void_p), ("out_pitch_bytes", ctypes.c_int64)]
+
+
+class ScheduleC(ctypes.Structure):
+    _fields_ = [("forward_threads", ctypes.c_int32 * 5), ("inverse_threads", ctypes.c_int32 * 5)]
 
 
 @dataclass
@@ -112,6 +126,32 @@ def load(build_if_missing: bool = True):
         lib.isx_last_error.restype = ctypes.c_char_p
         lib.isx_encode_tile_static.argtypes = [vp, vp, sz, ctypes.POINTER(sz), vp, ctypes.c_char_p, sz]
         lib.isx_encode_tile_static.restype = st
+        lib.isx_decode_jobs.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, i32, vp]
+        lib.isx_decode_jobs.restype = st
+        lib.isx_get_schedule.argtypes = [vp, vp]
+        lib.isx_get_schedule.restype = st
+        lib.isx_set_schedule.argtypes = [vp, vp]
+        lib.isx_set_schedule.restype = st
+        lib.isx_autotune.argtypes = [vp, vp, i32, i32, vp]
+        lib.isx_autotune.restype = st
+        lib.isx_plan_encode.argtypes = [vp, vp, i32, ctypes.POINTER(vp)]
+        lib.isx_plan_encode.restype = st
+        lib.isx_plan_decode.argtypes = [vp, vp, i32, vp, i32, i32, i32, ctypes.POINTER(vp)]
+        lib.isx_plan_decode.restype = st
+        lib.isx_plan_launch_encode.argtypes = [vp, vp, sz, vp, vp]
+        lib.isx_plan_launch_encode.restype = st
+        lib.isx_plan_launch_decode.argtypes = [vp, vp, vp, vp]
+        lib.isx_plan_launch_decode.restype = st
+        lib.isx_plan_sync_status.argtypes = [vp, vp]
+        lib.isx_plan_sync_status.restype = st
+        lib.isx_plan_device_bytes.argtypes = [vp]
+        lib.isx_plan_device_bytes.restype = sz
+        lib.isx_plan_launch_count.argtypes = [vp]
+        lib.isx_plan_launch_count.restype = i32
+        lib.isx_plan_last_error.argtypes = [vp]
+        lib.isx_plan_last_error.restype = ctypes.c_char_p
+        lib.isx_plan_destroy.argtypes = [vp]
+        lib.isx_plan_destroy.restype = None
         _lib = lib
         return lib
 
@@ -229,6 +269,43 @@ class Codec:
         self._check(self.lib.isx_decode_region(self.ctx, stream_buf.data_ptr(), offsets.data_ptr(), arr, len(tiles), level, rx, ry,
                                                rw, rh, drop_lsb_planes, out.data_ptr(), pitch, _stream_ptr(stream)))
 
+    def decode_jobs(self, stream_buf, offsets, tiles: Sequence[Tile], jobs, level=0, drop_lsb_planes=0, stream=None):
+        """jobs: sequence of (tile index, (rx, ry, rw, rh), out tensor whose [0, 0] is pixel (rx, ry))."""
+        arr = _tiles_c(tiles)
+        jc = _jobs_c(jobs)
+        self._check(self.lib.isx_decode_jobs(self.ctx, stream_buf.data_ptr(), offsets.data_ptr(), arr, len(tiles), jc, len(jobs),
+                                             level, drop_lsb_planes, _stream_ptr(stream)))
+
+    def get_schedule(self) -> dict:
+        sc = ScheduleC()
+        self._check(self.lib.isx_get_schedule(self.ctx, ctypes.byref(sc)))
+        return {"forward_threads": list(sc.forward_threads), "inverse_threads": list(sc.inverse_threads)}
+
+    def set_schedule(self, forward_threads, inverse_threads):
+        sc = ScheduleC()
+        for k in range(SIZE_CLASSES):
+            sc.forward_threads[k] = forward_threads[k]
+            sc.inverse_threads[k] = inverse_threads[k]
+        self._check(self.lib.isx_set_schedule(self.ctx, ctypes.byref(sc)))
+
+    def autotune(self, tiles: Sequence[Tile], reps: int = 3, stream=None) -> dict:
+        arr = _tiles_c(tiles)
+        self._check(self.lib.isx_autotune(self.ctx, arr, len(tiles), reps, _stream_ptr(stream)))
+        return self.get_schedule()
+
+    def plan_encode(self, tiles: Sequence[Tile]) -> "Plan":
+        arr = _tiles_c(tiles)
+        h = ctypes.c_void_p()
+        self._check(self.lib.isx_plan_encode(self.ctx, arr, len(tiles), ctypes.byref(h)))
+        return Plan(self.lib, h, "encode", keep=(tiles,))
+
+    def plan_decode(self, tiles: Sequence[Tile], jobs, level=0, drop_lsb_planes=0) -> "Plan":
+        arr = _tiles_c(tiles)
+        jc = _jobs_c(jobs)
+        h = ctypes.c_void_p()
+        self._check(self.lib.isx_plan_decode(self.ctx, arr, len(tiles), jc, len(jobs), level, drop_lsb_planes, ctypes.byref(h)))
+        return Plan(self.lib, h, "decode", keep=(tiles, jobs))
+
     def forward_coefficients(self, tiles: Sequence[Tile], out, stream=None):
         arr = _tiles_c(tiles)
         self._check(self.lib.isx_forward_coefficients(self.ctx, arr, len(tiles), out.data_ptr(), _stream_ptr(stream)))
@@ -247,6 +324,56 @@ class Codec:
         self._check(self.lib.isx_decode_region_host(self.ctx, stream_buf.ctypes.data, offsets.ctypes.data, arr, len(tiles), level,
                                                     rx, ry, rw, rh, drop_lsb_planes, out.ctypes.data, out.strides[0],
                                                     _stream_ptr(stream)))
+
+
+def _jobs_c(jobs):
+    arr = (DecodeJobC * max(1, len(jobs)))()
+    for k, (ti, rect, out) in enumerate(jobs):
+        rx, ry, rw, rh = rect
+        arr[k].tile, arr[k].rx, arr[k].ry, arr[k].rw, arr[k].rh = ti, rx, ry, rw, rh
+        arr[k].d_out = out.data_ptr()
+        arr[k].out_pitch_bytes = out.stride(0) * out.element_size()
+    return arr
+
+
+class Plan:
+    """A prepared encode or decode (isx_plan_*): launches enqueue kernels only, so they can be graph-captured."""
+
+    def __init__(self, lib, handle, kind, keep=()):
+        self.lib, self.h, self.kind, self.keep = lib, handle, kind, keep
+
+    def _check(self, rc):
+        if rc != ISX_OK:
+            raise IsxError(rc, self.lib.isx_plan_last_error(self.h).decode())
+
+    def launch_encode(self, out, offsets, stream=None):
+        self._check(self.lib.isx_plan_launch_encode(self.h, out.data_ptr(), out.numel() * out.element_size(), offsets.data_ptr(),
+                                                    _stream_ptr(stream)))
+
+    def launch_decode(self, stream_buf, offsets, stream=None):
+        self._check(self.lib.isx_plan_launch_decode(self.h, stream_buf.data_ptr(), offsets.data_ptr(), _stream_ptr(stream)))
+
+    def sync_status(self, stream=None) -> int:
+        return int(self.lib.isx_plan_sync_status(self.h, _stream_ptr(stream)))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self.lib.isx_plan_device_bytes(self.h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.isx_plan_launch_count(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.isx_plan_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ helpers

@@ -92,3 +92,32 @@ def phantom(seed: int, W: int, H: int, x0: int = 0, y0: int = 0, w: int | None =
     out = np.empty((h, w), np.uint16)
     _get().isx_gen_phantom(seed, W, H, x0, y0, w, h, out.ctypes.data, out.strides[0], _threads(threads))
     return out
+
+
+def batch_specs(seed: int, n: int):
+    """Tile recipe of the mixed batch workload: per tile, width and height
+    uniform in 17..256, RGB8 (a crop of the slide generator) or 12-bit mono
+    (a crop of the phantom generator) with equal odds, 2..6 wavelet levels,
+    lossless or lossy (steps 8/4/2 on levels 1-3) with equal odds, and the
+    crop position.  numpy's seeded generator draws the choices."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for _ in range(n):
+        w, h = int(rng.integers(17, 257)), int(rng.integers(17, 257))
+        levels = int(rng.integers(2, 7))
+        rgb = bool(rng.random() < 0.5)
+        if rgb:
+            x0, y0 = int(rng.integers(0, 40000 - w)), int(rng.integers(0, 30000 - h))
+        else:
+            x0, y0 = int(rng.integers(0, 2048 - w)), int(rng.integers(0, 2048 - h))
+        lossy = bool(rng.random() < 0.5)
+        q = ([3, 2, 1] + [0] * 13)[:levels + 1] if lossy else [0] * (levels + 1)
+        specs.append({"w": w, "h": h, "levels": levels, "rgb": rgb, "bits": 8 if rgb else 12, "x0": x0, "y0": y0, "q": q})
+    return specs
+
+
+def batch_image(spec, threads: int = 1) -> np.ndarray:
+    """Pixels of one tile of batch_specs()."""
+    if spec["rgb"]:
+        return slide(config_seed(3), spec["x0"], spec["y0"], spec["w"], spec["h"], threads=threads)
+    return phantom(config_seed(2), 2048, 2048, spec["x0"], spec["y0"], spec["w"], spec["h"], threads=threads)
