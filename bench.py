@@ -387,10 +387,186 @@ def run_gpu(args):
            "tile_decode_latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[int(0.99 * (len(lat) - 1))], 3)},
            "stages_ms": {k: round(v[0] / max(1, v[1]), 3) for k, v in stages.items()},
            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+    if rank == 0 and not args.no_serve:
+        # the slide's lossy pyramid is the stream above; encode the lossless one beside it
+        from paper_2005_08713_gb300 import serve
+        tiles_ll = tiles_for(d_img, [0] * 9)
+        d_out2 = torch.empty(cap, dtype=torch.uint8, device=dev)
+        d_offs2 = torch.empty(len(grid) + 1, dtype=torch.int64, device=dev)
+        codec.encode_tiles(tiles_ll, d_out2, d_offs2, stream)
+        if codec.sync_status(stream) != 0:
+            raise RuntimeError("lossless encode failed")
+        pyramids = [serve.Pyramid(IMG_W, IMG_H, TILE, LEVELS, 3, 8, d_out, d_offs, tiles),
+                    serve.Pyramid(IMG_W, IMG_H, TILE, LEVELS, 3, 8, d_out2, d_offs2, tiles_ll)]
+        res["serve"] = run_serve(args, dev, pyramids)
+        del d_out2, d_offs2
     codec.close()
+    if rank == 0 and not args.no_batch:
+        res["batch"] = run_batch(args, dev, args.batch_tiles)
     if world > 1:
         dist.destroy_process_group()
     return res if rank == 0 else None
+
+
+def run_batch(args, dev, n_tiles=4096):
+    """Mixed batch: n_tiles tiles of 17-256 px per side, RGB8 and 12-bit mono, 2-6 levels, lossless and lossy,
+    encoded and decoded (each tile into its own buffer) as one plan pair replayed from a CUDA graph,
+    against the same work issued one tile per call."""
+    import torch
+    from paper_2005_08713_gb300 import isx, synth
+    specs = synth.batch_specs(synth.config_seed(4), n_tiles)
+    imgs = [synth.batch_image(sp) for sp in specs]
+    # pixels packed into one device buffer, 16-byte aligned per tile
+    offs, pos = [], 0
+    for a in imgs:
+        offs.append(pos)
+        pos += (a.nbytes + 15) & ~15
+    h_pix = torch.empty(pos, dtype=torch.uint8, pin_memory=True)
+    hp = h_pix.numpy()
+    for a, o in zip(imgs, offs):
+        hp[o:o + a.nbytes] = a.reshape(-1).view(np.uint8)
+    d_pix = h_pix.to(dev)
+    base = d_pix.data_ptr()
+    tiles = []
+    for i, (a, sp, o) in enumerate(zip(imgs, specs, offs)):
+        bpp = 3 if sp["rgb"] else 2
+        tiles.append(isx.Tile(width=sp["w"], height=sp["h"], channels=3 if sp["rgb"] else 1, bits=sp["bits"], levels=sp["levels"],
+                              qstep_log2=tuple(sp["q"]), x0=0, y0=0, pixels=base + o, row_pitch_bytes=sp["w"] * bpp, keep=d_pix))
+    tarr = isx.TileArray(tiles)
+    mp = sum(sp["w"] * sp["h"] for sp in specs) / 1e6
+    cap = pos * 2 + 4096 * n_tiles
+    d_out = torch.zeros(cap, dtype=torch.uint8, device=dev)
+    d_offs = torch.zeros(n_tiles + 1, dtype=torch.int64, device=dev)
+    d_dec = torch.zeros(pos, dtype=torch.uint8, device=dev)
+    jobs = []
+    for i, (sp, o) in enumerate(zip(specs, offs)):
+        bpp = 3 if sp["rgb"] else 2
+        view = d_dec[o:o + sp["w"] * sp["h"] * bpp].view(sp["h"], sp["w"] * bpp)
+        jobs.append((i, (0, 0, sp["w"], sp["h"]), view))
+    codec = isx.Codec(dev.index or 0)
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.perf_counter()
+    sched = codec.autotune(tarr, reps=3, stream=stream)
+    tune_s = time.perf_counter() - t0
+    penc = codec.plan_encode(tarr)
+    pdec = codec.plan_decode(tarr, jobs)
+    with torch.cuda.stream(stream):
+        penc.launch_encode(d_out, d_offs, stream)
+        pdec.launch_decode(d_out, d_offs, stream)
+    assert penc.sync_status(stream) == 0 and pdec.sync_status(stream) == 0
+    launches = penc.launch_count + pdec.launch_count
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        penc.launch_encode(d_out, d_offs, stream)
+        pdec.launch_decode(d_out, d_offs, stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            fn()
+        ev[1].record(stream)
+        ev[1].synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    with torch.cuda.stream(stream):   # replays run on the current stream, the one the events are recorded on
+        for _ in range(args.warmup):
+            g.replay()
+        graph_ms = timed(g.replay, max(3, args.steps))
+
+    def eager():
+        penc.launch_encode(d_out, d_offs, stream)
+        pdec.launch_decode(d_out, d_offs, stream)
+
+    with torch.cuda.stream(stream):
+        eager_ms = timed(eager, max(3, args.steps))
+    assert penc.sync_status(stream) == 0 and pdec.sync_status(stream) == 0
+    # exactness on sampled tiles of the graph's output
+    import oracle
+    rng = np.random.default_rng(4)
+    o_h = d_offs.cpu().numpy()
+    ok = True
+    sample = rng.choice(n_tiles, 16, replace=False).tolist()
+    dec_h = d_dec.cpu().numpy()
+    for i in sample:
+        sp = specs[i]
+        ref = oracle.encode_tile(imgs[i], sp["levels"], sp["bits"], sp["q"])
+        got = d_out[int(o_h[i]):int(o_h[i + 1])].cpu().numpy().tobytes()
+        bpp = 3 if sp["rgb"] else 2
+        dec = dec_h[offs[i]:offs[i] + sp["w"] * sp["h"] * bpp]
+        dec = dec.view(np.uint16).reshape(sp["h"], sp["w"]) if not sp["rgb"] else dec.reshape(sp["h"], sp["w"], 3)
+        ok = ok and got == ref and np.array_equal(dec, oracle.decode_tile(ref, 0))
+    # the same work one tile per call (each call plans, uploads and launches its own kernels)
+    per_tile = None
+    if not args.no_per_tile:
+        one = [isx.TileArray([t]) for t in tiles]
+
+        def per_tile_pass():
+            for i in range(n_tiles):
+                codec.encode_tiles(one[i], d_out, d_offs, stream)
+                codec.decode_jobs(d_out, d_offs, one[i], [(0, jobs[i][1], jobs[i][2])], 0, 0, stream)
+
+        per_tile_pass()
+        codec.sync_status(stream)
+        t0 = time.perf_counter()
+        pt_ms = timed(per_tile_pass, 1)
+        pt_wall = time.perf_counter() - t0
+        assert codec.sync_status(stream) == 0
+        per_tile = {"ms": round(pt_ms, 2), "MP_per_s": round(mp / (pt_ms / 1e3), 1), "wall_s": round(pt_wall, 2),
+                    "calls": 2 * n_tiles}
+    out = {"workload": f"batch_{n_tiles}_mixed_17to256px_rgb8_mono12_L2to6_lossless_lossy", "tiles": n_tiles,
+           "megapixels": round(mp, 2), "unit": "MP/s (encode + decode round trip)",
+           "graph": {"ms": round(graph_ms, 3), "MP_per_s": round(mp / (graph_ms / 1e3), 1), "kernels": launches},
+           "eager_plans": {"ms": round(eager_ms, 3), "MP_per_s": round(mp / (eager_ms / 1e3), 1)},
+           "per_tile_calls": per_tile, "schedule": sched, "autotune_s": round(tune_s, 2),
+           "exact": {"sampled_tiles": len(sample), "bit_exact": bool(ok)}}
+    if per_tile:
+        out["speedup_vs_per_tile"] = round(per_tile["ms"] / graph_ms, 1)
+    del g
+    penc.close()
+    pdec.close()
+    codec.close()
+    return out
+
+
+def run_serve(args, dev, pyramids):
+    """Viewport serving: Poisson arrivals of 1920x1080 viewport requests at random zoom levels 0-7 and pan
+    positions over the slide's lossy and lossless pyramids (device resident), continuous batching over
+    several streams, scratch admitted by a per-slot HBM budget."""
+    from paper_2005_08713_gb300 import serve
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    out = {"workload": "serve_viewport_1920x1080_z0to7_slide_lossy_lossless", "unit": "MP/s delivered", "rates": []}
+    t0 = time.perf_counter()
+    srv = serve.Server(pyramids, device=dev.index or 0, slots=args.serve_slots, max_batch=args.serve_batch,
+                       scratch_budget=args.serve_budget_mb << 20,
+                       resident_from=None if args.serve_resident_from < 0 else args.serve_resident_from)
+    out["resident_levels_from"] = args.serve_resident_from
+    out["startup_s"] = round(time.perf_counter() - t0, 2)
+    srv.run(serve.poisson_requests(1000.0, 64, pyramids, seed=1))   # warm-up
+    for k, rate in enumerate(rates):
+        n = int(min(rate * args.serve_seconds, args.serve_cap))
+        reqs = serve.poisson_requests(rate, n, pyramids, seed=100 + k)
+        done = srv.run(reqs)
+        px = sum(r.rect[2] * r.rect[3] for r in done)
+        row = {"rate_per_s": rate, "requests": len(done), "elapsed_s": round(srv.elapsed, 3),
+               "achieved_per_s": round(len(done) / srv.elapsed, 1), "MP_per_s": round(px / 1e6 / srv.elapsed, 1),
+               "batches": srv.n_batches, "mean_batch": round(float(np.mean(srv.batch_sizes)), 2)}
+        row.update(serve.latency_stats(done))
+        out["rates"].append(row)
+    srv.close()
+    # the same kind of load served one request per launch on one stream
+    one = serve.Server(pyramids, device=dev.index or 0, slots=1, max_batch=1, scratch_budget=args.serve_budget_mb << 20,
+                       resident_from=None if args.serve_resident_from < 0 else args.serve_resident_from)
+    n = int(min(rates[-1] * args.serve_seconds, args.serve_cap, 4000))
+    reqs = serve.poisson_requests(rates[-1], n, pyramids, seed=999)
+    done = one.run(reqs)
+    px = sum(r.rect[2] * r.rect[3] for r in done)
+    out["one_request_per_launch"] = {"rate_per_s": rates[-1], "requests": len(done), "elapsed_s": round(one.elapsed, 3),
+                                     "MP_per_s": round(px / 1e6 / one.elapsed, 1), **serve.latency_stats(done)}
+    one.close()
+    out["slots"], out["max_batch"], out["scratch_budget_mb_per_slot"] = args.serve_slots, args.serve_batch, args.serve_budget_mb
+    return out
 
 
 def cpu_baseline(img, grid, q, n_tiles):
@@ -466,6 +642,17 @@ def main():
     ap.add_argument("--cpu-tiles", type=int, default=256)
     ap.add_argument("--size", default=None, help="WxH of the slide instead of 40000x30000 (small cases for profiling)")
     ap.add_argument("--no-latency", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-batch measurement")
+    ap.add_argument("--no-per-tile", action="store_true", help="skip the one-tile-per-call comparison of the batch")
+    ap.add_argument("--batch-tiles", type=int, default=4096)
+    ap.add_argument("--no-serve", action="store_true", help="skip the viewport-serving measurement")
+    ap.add_argument("--serve-rates", default="1000,5000,10000,20000,50000")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrivals per rate: seconds of Poisson arrivals ...")
+    ap.add_argument("--serve-cap", type=int, default=10000, help="... but at most this many requests")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-batch", type=int, default=32)
+    ap.add_argument("--serve-budget-mb", type=int, default=1024)
+    ap.add_argument("--serve-resident-from", type=int, default=3, help="keep levels >= this decoded on the device (-1: none)")
     args = ap.parse_args()
     if args.size:
         global IMG_W, IMG_H

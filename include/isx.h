@@ -187,6 +187,20 @@ isx_status isx_decode_jobs(isx_ctx* ctx, const void* d_stream, const uint64_t* d
                            const isx_tile_desc* tiles, int32_t n_tiles, const isx_decode_job* jobs,
                            int32_t n_jobs, int32_t level, int32_t drop_lsb_planes, void* stream);
 
+/* Device scratch (bytes) that isx_decode_jobs would need for these jobs
+ * (host computation only; d_out pointers are not read). */
+isx_status isx_decode_jobs_scratch(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles,
+                                   const isx_decode_job* jobs, int32_t n_jobs, int32_t level,
+                                   int32_t drop_lsb_planes, size_t* bytes);
+
+/* Grows the context's scratch to at least `bytes` now (synchronises the
+ * device when it grows), so that later calls up to that size allocate
+ * nothing; ISX_ERR_OOM beyond the context's HBM budget. */
+isx_status isx_reserve_scratch(isx_ctx* ctx, size_t bytes);
+
+/* Bytes of device scratch the context holds. */
+size_t isx_scratch_bytes(isx_ctx* ctx);
+
 /* Fused transform schedule.  Tiles whose int16 channel plane fits in shared
  * memory (width and height <= 1024, bits <= 12, plane <= 160 KB) are
  * transformed by one CTA per tile and channel; they are grouped in

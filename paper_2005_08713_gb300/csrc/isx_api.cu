@@ -833,6 +833,33 @@ isx_status isx_decode_region_host(isx_ctx* ctx, const void* h_stream, const uint
 }
 
 
+isx_status isx_decode_jobs_scratch(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, const isx_decode_job* jobs,
+                                   int32_t n_jobs, int32_t level, int32_t drop_lsb_planes, size_t* bytes) {
+  if (!ctx) return ISX_ERR_ARG;
+  if (!tiles || n_tiles < 1 || !jobs || n_jobs < 0 || !bytes || level < 0 || level > kMaxLevels) return fail(ctx, ISX_ERR_ARG, "bad arguments");
+  std::vector<Job> J((size_t)n_jobs);
+  for (int32_t j = 0; j < n_jobs; ++j)
+    J[j] = Job{jobs[j].tile, jobs[j].rx, jobs[j].ry, jobs[j].rw, jobs[j].rh, jobs[j].d_out, jobs[j].out_pitch_bytes};
+  std::vector<TileDev> ht((size_t)std::max(n_jobs, 1));
+  std::vector<int64_t> hidx((size_t)std::max(n_jobs, 1));
+  std::vector<int32_t> htask((size_t)std::max(n_jobs, 1));
+  DecodeLayout D;
+  std::string err;
+  isx_status st = plan_decode(tiles, n_tiles, J.data(), n_jobs, level, drop_lsb_planes, ctx->sched, ht.data(), hidx.data(), htask.data(),
+                              D, &err);
+  if (st != ISX_OK) return fail(ctx, st, err);
+  *bytes = D.nsel ? D.total : 0;
+  return ISX_OK;
+}
+
+isx_status isx_reserve_scratch(isx_ctx* ctx, size_t bytes) {
+  if (!ctx) return ISX_ERR_ARG;
+  ISX_CUDA(cudaSetDevice(ctx->device));
+  return ensure_arena(ctx, bytes);
+}
+
+size_t isx_scratch_bytes(isx_ctx* ctx) { return ctx ? ctx->arena_size : 0; }
+
 // ---------------------------------------------------------------- schedule
 isx_status isx_get_schedule(isx_ctx* ctx, isx_schedule* out) {
   if (!ctx || !out) return ISX_ERR_ARG;

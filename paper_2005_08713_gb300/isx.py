@@ -28,7 +28,8 @@ EXPORTS = ["isx_create", "isx_destroy", "isx_encode_tiles", "isx_decode_region",
            "isx_last_error", "isx_set_timing", "isx_stage_times", "isx_encode_tile_static", "isx_decode_jobs",
            "isx_get_schedule", "isx_set_schedule", "isx_autotune", "isx_plan_encode", "isx_plan_decode",
            "isx_plan_launch_encode", "isx_plan_launch_decode", "isx_plan_sync_status", "isx_plan_device_bytes",
-           "isx_plan_launch_count", "isx_plan_last_error", "isx_plan_destroy"]
+           "isx_plan_launch_count", "isx_plan_last_error", "isx_plan_destroy", "isx_decode_jobs_scratch",
+           "isx_reserve_scratch", "isx_scratch_bytes"]
 
 SIZE_CLASSES = 5
 
@@ -51,6 +52,11 @@ class TileDescC(ctypes.Structure):
 class DecodeJobC(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("rx", ctypes.c_int32), ("ry", ctypes.c_int32), ("rw", ctypes.c_int32),
                 ("rh", ctypes.c_int32), ("d_out", ctypes.c_void_p), ("out_pitch_bytes", ctypes.c_int64)]
+
+
+# numpy layout of isx_decode_job (for building many jobs without Python loops)
+JOB_DTYPE = np.dtype([("tile", "<i4"), ("rx", "<i4"), ("ry", "<i4"), ("rw", "<i4"), ("rh", "<i4"), ("_pad", "<i4"),
+                      ("d_out", "<u8"), ("out_pitch_bytes", "<i8")])
 
 
 class ScheduleC(ctypes.Structure):
@@ -152,6 +158,12 @@ def load(build_if_missing: bool = True):
         lib.isx_plan_last_error.restype = ctypes.c_char_p
         lib.isx_plan_destroy.argtypes = [vp]
         lib.isx_plan_destroy.restype = None
+        lib.isx_decode_jobs_scratch.argtypes = [vp, vp, i32, vp, i32, i32, i32, ctypes.POINTER(sz)]
+        lib.isx_decode_jobs_scratch.restype = st
+        lib.isx_reserve_scratch.argtypes = [vp, sz]
+        lib.isx_reserve_scratch.restype = st
+        lib.isx_scratch_bytes.argtypes = [vp]
+        lib.isx_scratch_bytes.restype = sz
         _lib = lib
         return lib
 
@@ -275,6 +287,26 @@ class Codec:
         jc = _jobs_c(jobs)
         self._check(self.lib.isx_decode_jobs(self.ctx, stream_buf.data_ptr(), offsets.data_ptr(), arr, len(tiles), jc, len(jobs),
                                              level, drop_lsb_planes, _stream_ptr(stream)))
+
+    def decode_jobs_array(self, stream_buf, offsets, tiles, jobs: np.ndarray, level=0, drop_lsb_planes=0, stream=None):
+        """jobs: contiguous numpy array of JOB_DTYPE (the C struct layout)."""
+        assert jobs.dtype == JOB_DTYPE and jobs.flags["C_CONTIGUOUS"]
+        self._check(self.lib.isx_decode_jobs(self.ctx, stream_buf.data_ptr(), offsets.data_ptr(), _tiles_c(tiles), len(tiles),
+                                             jobs.ctypes.data, len(jobs), level, drop_lsb_planes, _stream_ptr(stream)))
+
+    def decode_jobs_scratch(self, tiles, jobs: np.ndarray, level=0, drop_lsb_planes=0) -> int:
+        assert jobs.dtype == JOB_DTYPE and jobs.flags["C_CONTIGUOUS"]
+        n = ctypes.c_size_t(0)
+        self._check(self.lib.isx_decode_jobs_scratch(self.ctx, _tiles_c(tiles), len(tiles), jobs.ctypes.data, len(jobs), level,
+                                                     drop_lsb_planes, ctypes.byref(n)))
+        return int(n.value)
+
+    def reserve_scratch(self, nbytes: int):
+        self._check(self.lib.isx_reserve_scratch(self.ctx, nbytes))
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(self.lib.isx_scratch_bytes(self.ctx))
 
     def get_schedule(self) -> dict:
         sc = ScheduleC()

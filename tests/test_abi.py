@@ -32,3 +32,10 @@ def test_tile_descriptor_layout_matches_header():
     # int32 x 7, uint8[16], pointer, int64  ->  64 bytes with natural alignment
     assert ctypes.sizeof(isx.TileDescC) == 64
     assert isx.TileDescC.pixels.offset == 48 and isx.TileDescC.row_pitch_bytes.offset == 56
+
+
+def test_decode_job_array_layout_matches_header():
+    from paper_2005_08713_gb300 import isx
+    assert ctypes.sizeof(isx.DecodeJobC) == isx.JOB_DTYPE.itemsize == 40
+    for name in ("tile", "rx", "ry", "rw", "rh", "d_out", "out_pitch_bytes"):
+        assert getattr(isx.DecodeJobC, name).offset == isx.JOB_DTYPE.fields[name][1], name

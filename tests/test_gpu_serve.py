@@ -1,0 +1,79 @@
+"""The viewport server: requests served in the mix (continuous batching over
+several streams) give exactly what each gives decoded alone, and what the
+oracle gives."""
+import numpy as np
+import pytest
+
+from gpu_helpers import gpu_encode, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _pyramid(codec, synth, lossy, W=3000, H=2000, T=256, L=8):
+    from paper_2005_08713_gb300 import isx, serve
+    img = synth.slide(synth.config_seed(3), 9000, 6000, W, H)
+    grid = [(x, y, min(T, W - x), min(T, H - y)) for y in range(0, H, T) for x in range(0, W, T)]
+    imgs = [np.ascontiguousarray(img[y:y + h, x:x + w]) for (x, y, w, h) in grid]
+    q = [3, 2, 1] + [0] * (L - 2) if lossy else [0] * (L + 1)
+    streams, tiles, out, offs = gpu_encode(codec, imgs, L, 8, [q] * len(imgs), origins=[(x, y) for (x, y, _, _) in grid])
+    return serve.Pyramid(W, H, T, L, 3, 8, out, offs, isx.TileArray(tiles)), streams, grid
+
+
+def test_served_mix_equals_each_request_alone_and_the_oracle(orc, synth):
+    from paper_2005_08713_gb300 import isx, serve
+    torch = torch_cuda()
+    codec = isx.Codec(0)
+    pyrs, meta = [], []
+    for lossy in (True, False):
+        p, streams, grid = _pyramid(codec, synth, lossy)
+        pyrs.append(p)
+        meta.append((streams, grid))
+    reqs = serve.poisson_requests(20000.0, 160, pyrs, seed=5, view=(640, 360), zmax=7)
+    srv = serve.Server(pyrs, slots=3, max_batch=8, scratch_budget=64 << 20, out_shape=(360, 640), keep_outputs=True)
+    done = srv.run(reqs)
+    srv.close()
+    # the same requests again with levels 3.. kept decoded on the device
+    reqs2 = serve.poisson_requests(20000.0, 160, pyrs, seed=5, view=(640, 360), zmax=7)
+    srv2 = serve.Server(pyrs, slots=2, max_batch=16, scratch_budget=64 << 20, out_shape=(360, 640), keep_outputs=True,
+                        resident_from=3)
+    done2 = srv2.run(reqs2)
+    srv2.close()
+    by_id = {r.rid: r.result for r in done}
+    for r in done2:
+        assert np.array_equal(r.result, by_id[r.rid]), r.rid
+    assert len(done) == len(reqs)
+    assert max(srv.batch_sizes) > 1, "requests arriving together should share batches"
+    for r in done:
+        p = pyrs[r.pyramid]
+        rx, ry, rw, rh = r.rect
+        alone = torch.zeros((rh, rw, 3), dtype=torch.uint8, device="cuda")
+        codec.decode_region(p.stream, p.offsets, p.tiles, r.z, r.rect, alone)
+        assert codec.sync_status() == 0
+        assert np.array_equal(r.result, alone.cpu().numpy()), r.rid
+    # a few against the oracle's decode of the tiles
+    for r in done[:12]:
+        streams, grid = meta[r.pyramid]
+        rx, ry, rw, rh = r.rect
+        z = r.z
+        ref = np.zeros((rh, rw, 3), np.uint8)
+        for (x, y, w, h), s in zip(grid, streams):
+            tx, ty = x >> z, y >> z
+            d = orc.decode_tile(s, z)
+            x0, y0 = max(tx, rx), max(ty, ry)
+            x1, y1 = min(tx + d.shape[1], rx + rw), min(ty + d.shape[0], ry + rh)
+            if x0 < x1 and y0 < y1:
+                ref[y0 - ry:y1 - ry, x0 - rx:x1 - rx] = d[y0 - ty:y1 - ty, x0 - tx:x1 - tx]
+        assert np.array_equal(r.result, ref), r.rid
+    codec.close()
+
+
+def test_server_admission_refuses_a_request_beyond_the_slot_budget(synth):
+    from paper_2005_08713_gb300 import isx, serve
+    codec = isx.Codec(0)
+    p, _, _ = _pyramid(codec, synth, True, W=1024, H=768)
+    reqs = [serve.Request(0, 0.0, 0, 0, (0, 0, 640, 360))]
+    srv = serve.Server([p], slots=1, max_batch=4, scratch_budget=1 << 16, out_shape=(360, 640))
+    with pytest.raises(RuntimeError, match="slot budget"):
+        srv.run(reqs)
+    srv.close()
+    codec.close()
