@@ -107,15 +107,17 @@ __device__ inline void record_run(uint32_t L, uint32_t* s_hist, uint32_t* s_runs
   }
 }
 
-__global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict__ blocks, const uint8_t* __restrict__ coef,
-                                                    uint8_t* __restrict__ sym, BlockStats* __restrict__ stats, int* __restrict__ status) {
+__global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm,
+                                                    const uint8_t* __restrict__ coef, uint8_t* __restrict__ sym,
+                                                    BlockStats* __restrict__ stats, int* __restrict__ status) {
   __shared__ uint32_t s_hist[256];
   __shared__ uint32_t s_extra[kMaxW + 1];
   __shared__ uint32_t s_runs;
   __shared__ uint32_t s_or[3], s_neg[3];
   __shared__ uint32_t s_km[32];
   __shared__ int64_t s_poff[32];
-  const BlockDev b = blocks[blockIdx.x];
+  const int64_t bi = perm[blockIdx.x];   // blocks by level: neighbouring CTAs do similar work
+  const BlockDev b = blocks[bi];
   const int n = b.w * b.h / 8, na = b.p * n;
   AreaMap am;
   am.init(b.w, b.h);
@@ -126,17 +128,46 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
   if (tid < 3) { s_or[tid] = 0; s_neg[tid] = 0; }
   if (tid == 0) s_runs = 0;
   __syncthreads();
+  // int16 blocks whose type rows hold a multiple of 4 areas go 4 consecutive areas (64 bytes) per thread
+  const bool quads = b.coef16 && (n & 3) == 0;
   {
     uint32_t o[3] = {0, 0, 0}, ng[3] = {0, 0, 0};
-    for (int a = tid; a < na; a += blockDim.x) {
-      int t, kk;
-      am.split(a, &t, &kk);
-      int32_t c[8];
-      cf.load(a, c);
+    if (quads) {
+      const uint4* q4 = reinterpret_cast<const uint4*>(coef + b.coef);
+      for (int u = tid; u < (na >> 2); u += blockDim.x) {
+        uint4 v[4];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        o[t] |= (uint32_t)abs(c[e]);
-        ng[t] |= (uint32_t)(c[e] < 0);
+        for (int i = 0; i < 4; ++i) v[i] = q4[4 * u + i];
+        uint32_t x = 0, g = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int32_t lo = (int32_t)(int16_t)(w[k] & 0xffffu), hi = (int32_t)w[k] >> 16;
+            x |= (uint32_t)abs(lo) | (uint32_t)abs(hi);
+            g |= w[k] & 0x80008000u;
+          }
+        }
+        const int t = (4 * u) / n;
+        o[0] |= t == 0 ? x : 0u; o[1] |= t == 1 ? x : 0u; o[2] |= t == 2 ? x : 0u;
+        const uint32_t gn = g ? 1u : 0u;
+        ng[0] |= t == 0 ? gn : 0u; ng[1] |= t == 1 ? gn : 0u; ng[2] |= t == 2 ? gn : 0u;
+      }
+    } else {
+      for (int a = tid; a < na; a += blockDim.x) {
+        int t, kk;
+        am.split(a, &t, &kk);
+        int32_t c[8];
+        cf.load(a, c);
+        uint32_t x = 0, g = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          x |= (uint32_t)abs(c[e]);
+          g |= (uint32_t)(c[e] < 0);
+        }
+        o[0] |= t == 0 ? x : 0u; o[1] |= t == 1 ? x : 0u; o[2] |= t == 2 ? x : 0u;
+        ng[0] |= t == 0 ? g : 0u; ng[1] |= t == 1 ? g : 0u; ng[2] |= t == 2 ? g : 0u;
       }
     }
     for (int t = 0; t < 3; ++t) {
@@ -164,7 +195,7 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
     // only samples above the stated bit depth get here: record an empty block
     // (every plane removed, no symbols) so that the later passes stay within
     // the block's buffers, and report the input error
-    BlockStats* st = stats + blockIdx.x;
+    BlockStats* st = stats + bi;
     for (int i = tid; i < 256; i += blockDim.x) st->hist[i] = 0;
     if (tid <= kMaxW) st->extra[tid] = 0;
     if (tid == 0) {
@@ -189,6 +220,56 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
   __syncthreads();
   // symbols of every kept (plane, type), written once
   uint8_t* S = sym + b.sym;
+  if (quads) {
+    // four areas per thread: one word of four symbols per kept plane
+    const uint4* q4 = reinterpret_cast<const uint4*>(coef + b.coef);
+    for (int u = tid; u < (na >> 2); u += blockDim.x) {
+      const int t = (4 * u) / n, k0 = 4 * u - t * n;
+      uint4 v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = q4[4 * u + i];
+      uint32_t negw = 0, mp[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+        int32_t c[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          c[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu);
+          c[2 * k + 1] = (int32_t)w[k] >> 16;
+        }
+        uint32_t negm = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) negm |= (uint32_t)(c[e] < 0) << e;
+        negw |= negm << (8 * i);
+        // magnitudes packed in pairs (e, e + 4) so one shift serves both rows of the area
+        mp[i][0] = (uint32_t)abs(c[0]) | ((uint32_t)abs(c[4]) << 16);
+        mp[i][1] = (uint32_t)abs(c[1]) | ((uint32_t)abs(c[5]) << 16);
+        mp[i][2] = (uint32_t)abs(c[2]) | ((uint32_t)abs(c[6]) << 16);
+        mp[i][3] = (uint32_t)abs(c[3]) | ((uint32_t)abs(c[7]) << 16);
+      }
+      for (int pl = 0; pl < d; ++pl) {
+        const uint32_t km = s_km[pl];
+        if (!((km >> t) & 1u)) continue;
+        uint32_t sw;
+        if (pl == 0) {
+          sw = negw;
+        } else {
+          const int sh = d - 1 - pl;
+          sw = 0;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint32_t x = ((mp[i][0] >> sh) & 0x10001u) | (((mp[i][1] >> sh) & 0x10001u) << 1) |
+                               (((mp[i][2] >> sh) & 0x10001u) << 2) | (((mp[i][3] >> sh) & 0x10001u) << 3);
+            sw |= ((x & 0xfu) | ((x >> 12) & 0xf0u)) << (8 * i);
+          }
+        }
+        const int ki = __popc(km & ((1u << t) - 1u));
+        // plane rows start 16-byte aligned and n, k0 are multiples of 4: an aligned word
+        *reinterpret_cast<uint32_t*>(S + s_poff[pl] + (int64_t)ki * n + k0) = sw;
+      }
+    }
+  } else
   for (int a = tid; a < na; a += blockDim.x) {
     int t, k;
     am.split(a, &t, &k);
@@ -259,7 +340,7 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
     if (lane == 0 && fin) record_run(fin, s_hist, &s_runs, s_extra);
   }
   __syncthreads();
-  BlockStats* st = stats + blockIdx.x;
+  BlockStats* st = stats + bi;
   for (int i = tid; i < 256; i += blockDim.x) st->hist[i] = s_hist[i];
   if (tid <= kMaxW) st->extra[tid] = s_extra[tid];
   if (tid == 0) {
@@ -381,12 +462,15 @@ __device__ inline void leaf_code(const HuffWarp& H, int leaf, int root, uint32_t
   *len = l;
 }
 
-__global__ void __launch_bounds__(32 * kHuffWarps) k_block_huffman(const BlockDev* __restrict__ blocks, const BlockStats* __restrict__ stats,
-                                                                  BlockCode* __restrict__ codes, int64_t nb) {
+__global__ void __launch_bounds__(32 * kHuffWarps) k_block_huffman(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm,
+                                                                  const BlockStats* __restrict__ stats, BlockCode* __restrict__ codes,
+                                                                  int64_t nb) {
   __shared__ HuffWarp hw[kHuffWarps];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t bi = (int64_t)blockIdx.x * kHuffWarps + wid;
-  if (bi >= nb) return;
+  const int64_t gi = (int64_t)blockIdx.x * kHuffWarps + wid;
+  if (gi >= nb) return;
+  // blocks by level: the warps of a CTA get blocks of similar size and finish together
+  const int64_t bi = perm[gi];
   HuffWarp& H = hw[wid];
   const BlockStats& st = stats[bi];
   const BlockDev b = blocks[bi];
@@ -893,14 +977,14 @@ __global__ void k_tile_headers(const TileDev* __restrict__ tiles, int n_tiles, c
 int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T) {
   int L = 0;
   const unsigned nb = (unsigned)eb.n_blocks;
-  T->mark("encode.symbols", s);
-  k_enc_symbols<<<nb, 256, 0, s>>>(eb.blocks, (const uint8_t*)eb.coef, eb.sym, eb.stats, eb.status);
-  T->mark("encode.huffman", s);
-  k_block_huffman<<<(unsigned)((eb.n_blocks + kHuffWarps - 1) / kHuffWarps), 32 * kHuffWarps, 0, s>>>(eb.blocks, eb.stats, eb.codes,
-                                                                                                    eb.n_blocks);
-  L += 2;
   T->mark("encode.order", s);
   L += launch_level_sort(eb.blocks, eb.n_blocks, eb.bucket, eb.perm, eb.scan_part, eb.totals + 1, s);
+  T->mark("encode.symbols", s);
+  k_enc_symbols<<<nb, 256, 0, s>>>(eb.blocks, eb.perm, (const uint8_t*)eb.coef, eb.sym, eb.stats, eb.status);
+  T->mark("encode.huffman", s);
+  k_block_huffman<<<(unsigned)((eb.n_blocks + kHuffWarps - 1) / kHuffWarps), 32 * kHuffWarps, 0, s>>>(eb.blocks, eb.perm, eb.stats,
+                                                                                                    eb.codes, eb.n_blocks);
+  L += 2;
   T->mark("encode.size", s);
   const unsigned gg = (unsigned)((eb.n_blocks + kEncGroup - 1) / kEncGroup);
   BlockHdr* hdrs = reinterpret_cast<BlockHdr*>(eb.hdrs);

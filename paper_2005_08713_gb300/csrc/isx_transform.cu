@@ -485,6 +485,59 @@ __device__ inline void level_inv(int16_t* P, int pitch, int cw, int ch, int s) {
   __syncthreads();
 }
 
+// The same levels done by one warp with warp barriers: once a level's grid
+// is at most 32 x 32 samples there are too few lines to occupy the CTA, and
+// the CTA-wide barriers would cost more than the sweeps.
+__device__ inline void level_fwd_warp(int16_t* P, int pitch, int cw, int ch, int s) {
+  const int lane = threadIdx.x & 31;
+  if (ch >= 2)
+    for (int c = lane; c < cw; c += 32) sweep_fwd(P + c * s, ch, s * pitch);
+  __syncwarp();
+  if (cw >= 2)
+    for (int r = lane; r < ch; r += 32) sweep_fwd(P + (r * s) * pitch, cw, s);
+  __syncwarp();
+}
+
+__device__ inline void level_inv_warp(int16_t* P, int pitch, int cw, int ch, int s) {
+  const int lane = threadIdx.x & 31;
+  if (cw >= 2)
+    for (int r = lane; r < ch; r += 32) sweep_inv(P + (r * s) * pitch, cw, s);
+  __syncwarp();
+  if (ch >= 2)
+    for (int c = lane; c < cw; c += 32) sweep_inv(P + c * s, ch, s * pitch);
+  __syncwarp();
+}
+
+constexpr int kWarpGrid = 32;   // grids up to 32 x 32 samples take the one-warp path
+
+// Levels 0 .. L-1 of the forward transform of a w x h plane.
+__device__ inline void transform_fwd_levels(int16_t* P, int pitch, int w, int h, int L) {
+  int l = 0;
+  for (; l < L; ++l) {
+    const int cw = level_dim(w, l), ch = level_dim(h, l);
+    if (cw <= kWarpGrid && ch <= kWarpGrid) break;
+    level_fwd(P, pitch, cw, ch, 1 << l);
+  }
+  if (l < L) {
+    if (threadIdx.x < 32)
+      for (int m = l; m < L; ++m) level_fwd_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << m);
+    __syncthreads();
+  }
+}
+
+// Inverse levels L-1 .. z, the plane's LL being level z.
+__device__ inline void transform_inv_levels(int16_t* P, int pitch, int w, int h, int L, int z) {
+  int l = L - 1;
+  if (l >= z && level_dim(w, l) <= kWarpGrid && level_dim(h, l) <= kWarpGrid) {
+    if (threadIdx.x < 32)
+      for (int m = l; m >= z && level_dim(w, m) <= kWarpGrid && level_dim(h, m) <= kWarpGrid; --m)
+        level_inv_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << (m - z));
+    __syncthreads();
+    while (l >= z && level_dim(w, l) <= kWarpGrid && level_dim(h, l) <= kWarpGrid) --l;
+  }
+  for (; l >= z; --l) level_inv(P, pitch, level_dim(w, l), level_dim(h, l), 1 << (l - z));
+}
+
 // The coefficient blocks of the CTA's tile channel, as its single area loop
 // sees them: area index g of the channel lies in the first block whose
 // `end` exceeds it.
@@ -492,10 +545,11 @@ constexpr int kMaxFusedBlocks = 32;
 constexpr int kMaxFusedPlanes = 20;   // planes of a fused block: at most 12 + 6
 
 struct FusedBlock {
-  int32_t end;                 // inclusive prefix sum of the blocks' areas (p * w * h / 8)
+  int32_t end;                 // inclusive prefix sum of the blocks' loop units (areas, or area quads)
   int32_t n, w, nlog, wlog;    // AreaMap of the block
   int32_t q, step;             // quantiser step (log2); distance of neighbouring subband samples
   int32_t d, keep;             // decode: bit depth and planes kept
+  int32_t quad;                // decode: the loop's units are 4 consecutive areas of a type (n % 4 == 0)
   int64_t base;                // byte offset of its coefficients (encode) or symbols (decode)
   int4 geo[3];                 // per type: valid width, valid height, interleaved row and column of sample (0, 0)
 };
@@ -519,6 +573,7 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
     f.q = qlog2_of(t, b.level);
     f.step = b.level == 0 ? 1 << (t.L - z0) : 2 << (b.level - 1 - z0);
     f.d = f.keep = 0;
+    f.quad = 0;
     f.base = b.coef;
     for (int ty = 0; ty < 3; ++ty) {
       int sx, sy, sw, sh, py, px;
@@ -533,6 +588,8 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
       f.keep = min(di.keep, kMaxFusedPlanes);
       f.base = sym_off[b0 + lane];
       if (b.p == 0 || di.d == 0) na = 0;
+      f.quad = (f.n & 3) == 0;
+      if (f.quad) na >>= 2;
       // kept types of each plane are stored back to back, planes 16-byte aligned
       int32_t off = 0;
       for (int pl = 0; pl < f.keep; ++pl) {
@@ -627,7 +684,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   // samples above the tile's bit depth void the int16 range bound of the transform
   if (__any_sync(0xffffffffu, over != 0) && (threadIdx.x & 31) == 0 && c == 0) set_status(status, kStRange);
   __syncthreads();
-  for (int l = 0; l < t.L; ++l) level_fwd(P, pitch, level_dim(w, l), level_dim(h, l), 1 << l);
+  transform_fwd_levels(P, pitch, w, h, t.L);
   // quantise + area-ordered pack of this channel's blocks, one loop over all their areas
   const int nbc = t.nb / t.C;
   if (threadIdx.x < 32) fused_block_table(t, blocks, nullptr, nullptr, t.block_base + (int64_t)c * nbc, nbc, 0, s_fb, nullptr);
@@ -780,6 +837,67 @@ __device__ __forceinline__ void transpose8x8(uint32_t& lo, uint32_t& hi) {
 // dequantised at the bin midpoint and placed into the interleaved int16
 // layout; the CTA then lifts back from level L to level z and writes the
 // LL_z image row-major (int32) for the colour store.
+// Rebuild of four consecutive areas (k0 .. k0+3, one type) of a block whose
+// plane rows are multiples of 4 bytes: one word load per plane for the four
+// areas, a 4 x 4 byte transpose per four planes, then per area the 8 x 8
+// bit transposes of the single-area path.  Planes 0 .. 15 (sign and 15
+// magnitude planes: every plane of int16 coefficients).
+__device__ inline void rebuild_quad(const FusedBlock& f, const AreaMap& am, const int32_t (*po)[3], const uint8_t* __restrict__ sym,
+                                    int a0, int16_t* P, int pitch) {
+  int type, k0;
+  am.split(a0, &type, &k0);
+  const int d = f.d, keep = f.keep;
+  const uint32_t* sk = reinterpret_cast<const uint32_t*>(sym + f.base + k0);   // 4-byte aligned: planes 16, n and k0 multiples of 4
+  uint32_t pw[16];
+#pragma unroll
+  for (int pl = 0; pl < 16; ++pl) {
+    pw[pl] = 0;
+    if (pl < keep) {
+      const int32_t o = po[pl][type];
+      if (o >= 0) pw[pl] = __ldg(sk + (o >> 2));
+    }
+  }
+  // aw[G][a]: bytes = planes 4G+1 .. 4G+4 of area a (plane 16 reads as 0)
+  uint32_t aw[4][4];
+#pragma unroll
+  for (int G = 0; G < 4; ++G) {
+    const uint32_t A = pw[4 * G + 1], B = pw[4 * G + 2], C = pw[4 * G + 3], D = G < 3 ? pw[4 * G + 4] : 0u;
+    const uint32_t t0 = __byte_perm(A, B, 0x5140), t1 = __byte_perm(C, D, 0x5140);
+    const uint32_t t2 = __byte_perm(A, B, 0x7362), t3 = __byte_perm(C, D, 0x7362);
+    aw[G][0] = __byte_perm(t0, t1, 0x5410);
+    aw[G][1] = __byte_perm(t0, t1, 0x7632);
+    aw[G][2] = __byte_perm(t2, t3, 0x5410);
+    aw[G][3] = __byte_perm(t2, t3, 0x7632);
+  }
+  const int4 gm = f.geo[type];
+  const int step = f.step, q = f.q;
+  const int32_t half = (1 << q) >> 1;
+  const int rowstep = step * pitch;
+  const int shift = 33 - d;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    uint32_t w0 = aw[0][a], w1 = aw[1][a], w2 = aw[2][a], w3 = aw[3][a];
+    transpose8x8(w0, w1);
+    transpose8x8(w2, w3);
+    const uint32_t neg = (pw[0] >> (8 * a)) & 255u;
+    int i, j;
+    am.ij(k0 + a, &i, &j);
+    int16_t* dst = P + (gm.z + i * step) * pitch + gm.w + j * step;
+    const bool inside = i + 1 < gm.y && j + 3 < gm.x;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int r = e >> 2, cc = e & 3;
+      if (!inside && (i + r >= gm.y || j + cc >= gm.x)) continue;
+      // magnitude bits, most significant plane first (bit j of the pair = plane j + 1); with d <= 16
+      // the two unrelated upper bytes of the permute end below bit 33 - d and are shifted out
+      const uint32_t rb = __byte_perm(e < 4 ? w0 : w1, e < 4 ? w2 : w3, cc | ((4 + cc) << 4));
+      const int32_t m = d >= 2 ? (int32_t)(__brev(rb) >> shift) : 0;
+      const int32_t v = m == 0 ? 0 : (m << q) + half;
+      dst[r * rowstep + cc * step] = (int16_t)(((neg >> e) & 1u) ? -v : v);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
                                                                  const BlockDev* __restrict__ blocks, const DecInfo* __restrict__ info,
                                                                  const int64_t* __restrict__ sym_off, const uint8_t* __restrict__ sym,
@@ -802,9 +920,14 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
   for (int g = threadIdx.x; g < total; g += blockDim.x) {
     while (g >= s_fb[blk].end) ++blk;
     const FusedBlock& f = s_fb[blk];
-    const int a = g - (blk ? s_fb[blk - 1].end : 0);
+    const int u = g - (blk ? s_fb[blk - 1].end : 0);
     AreaMap am;
     am.n = f.n; am.w = f.w; am.nlog = f.nlog; am.wlog = f.wlog;
+    if (f.quad) {
+      rebuild_quad(f, am, s_po[blk], sym, 4 * u, P, pitch);
+      continue;
+    }
+    const int a = u;
     int type, k;
     am.split(a, &type, &k);
     const int d = f.d, keep = f.keep;
@@ -863,7 +986,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
     }
   }
   __syncthreads();
-  for (int l = t.L - 1; l >= z; --l) level_inv(P, pitch, level_dim(t.w, l), level_dim(t.h, l), 1 << (l - z));
+  transform_inv_levels(P, pitch, t.w, t.h, t.L, z);
   if (t.C == 3) {
     // Every CTA leaves its channel plane (int16) in global memory and takes
     // a ticket; the tile's third CTA to finish inverts the colour transform
