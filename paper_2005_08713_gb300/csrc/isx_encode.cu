@@ -359,11 +359,10 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
 constexpr int kHuffWarps = 8;
 constexpr uint32_t kInf = 0xffffffffu;
 
-struct HuffWarp {
+struct __align__(16) HuffWarp {
   uint32_t f[256];        // frequencies
   uint32_t leaf[256];     // sorted leaves: (f << 8) | symbol
   uint32_t iw[256];       // internal node weights in creation order
-  uint16_t kid[256][2];   // children of internal node i (leaves 0..nl-1, internal nl + i)
   uint16_t parent[512];   // parent node id | 0x8000 for a right child
   uint32_t tree[81];
   int nl;
@@ -404,8 +403,11 @@ __device__ inline void warp_bitonic_256(uint32_t (&k)[8]) {
   }
 }
 
-// Builds the code of the frequencies in H.f; returns the root id.
-__device__ int huff_build_warp(HuffWarp& H) {
+// Builds the code of the frequencies in H.f; returns the root id.  With
+// kTree the parent links are stored (H.parent); otherwise only the depth of
+// the leaf holding symbol `track` (-1: none) is returned in *depth.
+template <bool kTree>
+__device__ int huff_build_warp(HuffWarp& H, int track, int* depth) {
   const int lane = threadIdx.x & 31;
   uint32_t k[8];
 #pragma unroll
@@ -415,54 +417,50 @@ __device__ int huff_build_warp(HuffWarp& H) {
     k[r] = fr ? ((fr << 8) | (uint32_t)sym) : kInf;
   }
   warp_bitonic_256(k);
-  int cnt = 0;
+  int cnt = 0, where = -1;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     H.leaf[lane * 8 + r] = k[r];
     cnt += k[r] != kInf;
+    if (k[r] != kInf && (int)(k[r] & 0xffu) == track) where = lane * 8 + r;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    where = max(where, __shfl_xor_sync(0xffffffffu, where, o));
+  }
   const int nl = cnt;
   __syncwarp();
   if (lane == 0) {
     H.nl = nl;
-    int qa = 0, qb = 0, ni = 0;
+    int qa = 0, qb = 0, ni = 0, cur = where, dep = 0;
     uint32_t wl = nl > 0 ? H.leaf[0] >> 8 : kInf, wi = kInf;
     for (int st = 0; st < nl - 1; ++st) {
       int a, b;
       uint32_t wa, wb;
-      if (wl <= wi) { a = qa; wa = wl; ++qa; wl = qa < nl ? H.leaf[qa] >> 8 : kInf; }
+      if (wl <= wi) { a = qa; wa = wl; ++qa; wl = qa < nl ? H.leaf[qa] >> 8 : kInf; }   // the leaf queue wins ties
       else { a = nl + qb; wa = wi; ++qb; wi = qb < ni ? H.iw[qb] : kInf; }
       if (wl <= wi) { b = qa; wb = wl; ++qa; wl = qa < nl ? H.leaf[qa] >> 8 : kInf; }
       else { b = nl + qb; wb = wi; ++qb; wi = qb < ni ? H.iw[qb] : kInf; }
       const uint32_t wn = wa + wb;
       H.iw[ni] = wn;
-      H.kid[ni][0] = (uint16_t)a;
-      H.kid[ni][1] = (uint16_t)b;
-      H.parent[a] = (uint16_t)(nl + ni);
-      H.parent[b] = (uint16_t)((nl + ni) | 0x8000);
+      if (kTree) {
+        H.parent[a] = (uint16_t)(nl + ni);
+        H.parent[b] = (uint16_t)((nl + ni) | 0x8000);
+      } else if (a == cur || b == cur) {
+        ++dep;
+        cur = nl + ni;
+      }
       if (qb == ni) wi = wn;   // the internal queue was empty: the new node is its front
       ++ni;
     }
+    if (depth) *depth = dep;
   }
   __syncwarp();
   return nl <= 1 ? 0 : 2 * nl - 2;
 }
 
-__device__ inline void leaf_code(const HuffWarp& H, int leaf, int root, uint32_t* code, int* len) {
-  uint32_t c = 0;
-  int l = 0;
-  for (int v = leaf; v != root && l < 40; ++l) {
-    const uint32_t p = H.parent[v];
-    c |= (p >> 15) << l;
-    v = p & 0x7fff;
-  }
-  *code = c;
-  *len = l;
-}
-
-__global__ void __launch_bounds__(32 * kHuffWarps) k_block_huffman(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm,
+__global__ void __launch_bounds__(32 * kHuffWarps, 4) k_block_huffman(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm,
                                                                   const BlockStats* __restrict__ stats, BlockCode* __restrict__ codes,
                                                                   int64_t nb) {
   __shared__ HuffWarp hw[kHuffWarps];
@@ -511,18 +509,10 @@ __global__ void __launch_bounds__(32 * kHuffWarps) k_block_huffman(const BlockDe
   __syncwarp();
   int l = 0;
   {
-    const int root = huff_build_warp(H);
-    if (H.f[czr] > 0 && H.nl > 1) {
-      for (int i = lane; i < H.nl; i += 32)
-        if ((int)(H.leaf[i] & 0xffu) == czr) {
-          uint32_t c;
-          int len;
-          leaf_code(H, i, root, &c, &len);
-          l = len;
-        }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) l = max(l, __shfl_xor_sync(0xffffffffu, l, o));
-    }
+    __shared__ int s_depth[kHuffWarps];
+    huff_build_warp<false>(H, czr, &s_depth[wid]);
+    __syncwarp();
+    l = H.f[czr] > 0 && H.nl > 1 ? s_depth[wid] : 0;
   }
   // Eq. 3 (reading): w minimises (w + l) * (#C_zr tokens at width w) over [2, b]
   int bmax = n_sym > 1 ? bitlen_u32(n_sym - 1) : 0;
@@ -537,49 +527,81 @@ __global__ void __launch_bounds__(32 * kHuffWarps) k_block_huffman(const BlockDe
   __syncwarp();
   if (lane == 0) H.f[czr] = lit_czr + st.n_runs + st.extra[wbest];
   __syncwarp();
-  const int root = huff_build_warp(H);
+  const int root = huff_build_warp<true>(H, -1, nullptr);
   const int nl = H.nl;
-  // codes: every leaf walks up to the root
-  for (int s = lane; s < 256; s += 32) { bc.code[s] = 0; bc.len[s] = 0; }
-  __syncwarp();
+  // codes: every leaf walks up to the root; a lane walks its (up to) 8 leaves together
+  for (int s2 = lane; s2 < 256; s2 += 32) { bc.code[s2] = 0; bc.len[s2] = 0; }
+  for (int k = lane; k < 81; k += 32) H.tree[k] = 0;
+  int v[8], len[8];
+  uint32_t code[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    v[m] = lane + 32 * m;
+    code[m] = 0;
+    len[m] = 0;
+  }
+  for (int depth = 0; depth < 40; ++depth) {
+    bool more = false;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      if (lane + 32 * m < nl && v[m] != root) {
+        const uint32_t p = H.parent[v[m]];
+        code[m] |= (p >> 15) << len[m];
+        ++len[m];
+        v[m] = p & 0x7fff;
+        more = true;
+      }
+    }
+    if (!__any_sync(0xffffffffu, more)) break;
+  }
+  // Preorder tree (Fig. 3: 0 = internal node, 1 + 8-bit symbol = leaf).  Leaves
+  // appear in preorder in the lexicographic order of their codes, and the
+  // record of a leaf with code c of length l and rank r in that order starts
+  // at bit l + 10 r - popcount(c): its l ancestors' 0 bits, plus, for each
+  // right turn on its path, the left sibling subtree (10 bits per leaf less
+  // one).  Ranks by counting smaller left-aligned codes.
+  uint32_t* K = H.iw;   // the merge's weights are no longer needed
   uint64_t tb = 0;
-  for (int i = lane; i < nl; i += 32) {
-    uint32_t c;
-    int len;
-    leaf_code(H, i, root, &c, &len);
-    const int sym = (int)(H.leaf[i] & 0xffu);
-    bc.code[sym] = c;
-    bc.len[sym] = (uint8_t)len;
-    tb += (uint64_t)H.f[sym] * len;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int i = lane + 32 * m;
+    if (i < nl) {
+      K[i] = len[m] ? code[m] << (31 - len[m]) : 0u;   // codes are at most 31 bits (Fibonacci bound)
+      const int sym = (int)(H.leaf[i] & 0xffu);
+      bc.code[sym] = code[m];
+      bc.len[sym] = (uint8_t)len[m];
+      tb += (uint64_t)H.f[sym] * len[m];
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tb += __shfl_xor_sync(0xffffffffu, tb, o);
-  // preorder tree (Fig. 3): 0 = internal node, 1 + 8-bit symbol = leaf
-  if (lane == 0) {
-    for (int k = 0; k < 81; ++k) H.tree[k] = 0;
-    int stack[40];
-    int sp = 0, pos = 0;
-    stack[sp++] = root;
-    while (sp > 0) {
-      const int v = stack[--sp];
-      if (v < nl) {
-        const uint32_t val = 0x100u | (H.leaf[v] & 0xffu);
-        const int wi = pos >> 5, off = pos & 31;
-        const uint64_t vv = (uint64_t)val << (64 - off - 9);
-        H.tree[wi] |= (uint32_t)(vv >> 32);
-        H.tree[wi + 1] |= (uint32_t)vv;
-        pos += 9;
-      } else {
-        ++pos;   // a 0 bit
-        const int i = v - nl;
-        if (sp < 38) {
-          stack[sp++] = H.kid[i][1];
-          stack[sp++] = H.kid[i][0];
-        }
-      }
-    }
-    bc.tree_bits = pos;
+  __syncwarp();
+  int rank[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) rank[m] = 0;
+  uint32_t key[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) key[m] = lane + 32 * m < nl ? K[lane + 32 * m] : 0u;
+  if (lane < 3 && nl + lane < ((nl + 3) & ~3)) K[nl + lane] = kInf;   // pad to whole words of four: never smaller
+  __syncwarp();
+  for (int j = 0; j < nl; j += 4) {
+    const uint4 kq = *reinterpret_cast<const uint4*>(K + j);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) rank[m] += (kq.x < key[m]) + (kq.y < key[m]) + (kq.z < key[m]) + (kq.w < key[m]);
   }
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int i = lane + 32 * m;
+    if (i < nl) {
+      const int pos = len[m] + 10 * rank[m] - __popc(code[m]);
+      const uint32_t val = 0x100u | (H.leaf[i] & 0xffu);
+      const int wi = pos >> 5, off = pos & 31;
+      const uint64_t vv = (uint64_t)val << (64 - off - 9);
+      atomicOr(&H.tree[wi], (uint32_t)(vv >> 32));
+      if ((uint32_t)vv) atomicOr(&H.tree[wi + 1], (uint32_t)vv);
+    }
+  }
+  if (lane == 0) bc.tree_bits = 10 * nl - 1;
   __syncwarp();
   for (int k = lane; k < 80; k += 32) bc.tree[k] = H.tree[k];
   if (lane == 0) {
