@@ -391,7 +391,8 @@ __host__ __device__ inline int smem_pitch(int w) { return ((w + 1) & ~1) | 2; }
 // writes x[2k .. 2k+2K-1], so no read of a later chunk is overwritten).
 constexpr int kSweepChunk = 8;
 
-__device__ inline void sweep_fwd(int16_t* x, int n, int st) {
+template <typename T>
+__device__ inline void sweep_fwd(T* x, int n, int st) {
   if (n < 2) return;
   int32_t xe = x[0], dprev = 0;
   int k = 0;
@@ -410,20 +411,20 @@ __device__ inline void sweep_fwd(int16_t* x, int n, int st) {
       xe = xe2;
     }
 #pragma unroll
-    for (int i = 0; i < 2 * kSweepChunk; ++i) x[(2 * k + i) * st] = (int16_t)o[i];
+    for (int i = 0; i < 2 * kSweepChunk; ++i) x[(2 * k + i) * st] = (T)o[i];
   }
   for (; 2 * k < n; ++k) {
     int32_t d, xe2;
     if (2 * k + 1 < n) {
       xe2 = (2 * k + 2 < n) ? x[(2 * k + 2) * st] : xe;   // x[n] mirrors to x[n-2]
       d = x[(2 * k + 1) * st] - ((xe + xe2) >> 1);
-      x[(2 * k + 1) * st] = (int16_t)d;
+      x[(2 * k + 1) * st] = (T)d;
     } else {
       d = dprev;   // odd n: d[nh] mirrors to d[nh-1]
       xe2 = xe;
     }
     const int32_t dm1 = k == 0 ? d : dprev;   // d[-1] mirrors to d[0]
-    x[(2 * k) * st] = (int16_t)(xe + ((dm1 + d + 2) >> 2));
+    x[(2 * k) * st] = (T)(xe + ((dm1 + d + 2) >> 2));
     dprev = d;
     xe = xe2;
   }
@@ -431,7 +432,8 @@ __device__ inline void sweep_fwd(int16_t* x, int n, int st) {
 
 // In-place inverse of sweep_fwd, chunked the same way (a chunk reads
 // x[2k+2 .. 2k+2K+1] and writes x[2k .. 2k+2K-1]).
-__device__ inline void sweep_inv(int16_t* x, int n, int st) {
+template <typename T>
+__device__ inline void sweep_inv(T* x, int n, int st) {
   if (n < 2) return;
   const int nl = (n + 1) >> 1, nh = n >> 1;
   int32_t dk = x[st];
@@ -451,17 +453,17 @@ __device__ inline void sweep_inv(int16_t* x, int n, int st) {
       dk = dk1;
     }
 #pragma unroll
-    for (int i = 0; i < 2 * kSweepChunk; ++i) x[(2 * k + i) * st] = (int16_t)o[i];
+    for (int i = 0; i < 2 * kSweepChunk; ++i) x[(2 * k + i) * st] = (T)o[i];
   }
   for (; k < nh; ++k) {
     const int32_t dk1 = (k + 1 < nh) ? x[(2 * k + 3) * st] : dk;
     const int32_t en = (k + 1 < nl) ? x[(2 * k + 2) * st] - ((dk + dk1 + 2) >> 2) : e;
-    x[(2 * k) * st] = (int16_t)e;
-    x[(2 * k + 1) * st] = (int16_t)(dk + ((e + en) >> 1));
+    x[(2 * k) * st] = (T)e;
+    x[(2 * k + 1) * st] = (T)(dk + ((e + en) >> 1));
     e = en;
     dk = dk1;
   }
-  if (n & 1) x[(n - 1) * st] = (int16_t)e;
+  if (n & 1) x[(n - 1) * st] = (T)e;
 }
 
 // One level of the in-place 2-D transform on the grid at stride s
@@ -538,6 +540,53 @@ __device__ inline void transform_inv_levels(int16_t* P, int pitch, int w, int h,
   for (; l >= z; --l) level_inv(P, pitch, level_dim(w, l), level_dim(h, l), 1 << (l - z));
 }
 
+// Named barrier over the first n threads of the CTA (warps 0 .. n/32-1),
+// id 1 or 2 (0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+// Forward levels lmin .. L-1 done by the first n threads only (barrier 1):
+// after level 0 at most half the lines remain, and the rest of the CTA can
+// pack the finished level-1 blocks meanwhile.
+__device__ inline void transform_fwd_levels_group(int16_t* P, int pitch, int w, int h, int lmin, int L, int n) {
+  int l = lmin;
+  for (; l < L; ++l) {
+    const int cw = level_dim(w, l), ch = level_dim(h, l), s = 1 << l;
+    if (cw <= kWarpGrid && ch <= kWarpGrid) break;
+    if (ch >= 2)
+      for (int c = threadIdx.x; c < cw; c += n) sweep_fwd(P + c * s, ch, s * pitch);
+    group_sync(1, n);
+    if (cw >= 2)
+      for (int r = threadIdx.x; r < ch; r += n) sweep_fwd(P + (r * s) * pitch, cw, s);
+    group_sync(1, n);
+  }
+  if (l < L) {
+    if (threadIdx.x < 32)
+      for (int m = l; m < L; ++m) level_fwd_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << m);
+    group_sync(1, n);
+  }
+}
+
+// Inverse levels L-1 .. lmin (the plane's LL being level z) by the first n threads (barrier 1).
+__device__ inline void transform_inv_levels_group(int16_t* P, int pitch, int w, int h, int L, int lmin, int z, int n) {
+  int l = L - 1;
+  if (l >= lmin && level_dim(w, l) <= kWarpGrid && level_dim(h, l) <= kWarpGrid) {
+    if (threadIdx.x < 32)
+      for (int m = l; m >= lmin && level_dim(w, m) <= kWarpGrid && level_dim(h, m) <= kWarpGrid; --m)
+        level_inv_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << (m - z));
+    group_sync(1, n);
+    while (l >= lmin && level_dim(w, l) <= kWarpGrid && level_dim(h, l) <= kWarpGrid) --l;
+  }
+  for (; l >= lmin; --l) {
+    const int cw = level_dim(w, l), ch = level_dim(h, l), s = 1 << (l - z);
+    if (cw >= 2)
+      for (int r = threadIdx.x; r < ch; r += n) sweep_inv(P + (r * s) * pitch, cw, s);
+    group_sync(1, n);
+    if (ch >= 2)
+      for (int c = threadIdx.x; c < cw; c += n) sweep_inv(P + c * s, ch, s * pitch);
+    group_sync(1, n);
+  }
+}
+
 // The coefficient blocks of the CTA's tile channel, as its single area loop
 // sees them: area index g of the channel lies in the first block whose
 // `end` exceeds it.
@@ -550,6 +599,7 @@ struct FusedBlock {
   int32_t q, step;             // quantiser step (log2); distance of neighbouring subband samples
   int32_t d, keep;             // decode: bit depth and planes kept
   int32_t quad;                // decode: the loop's units are 4 consecutive areas of a type (n % 4 == 0)
+  int32_t level;               // 0 = LL
   int64_t base;                // byte offset of its coefficients (encode) or symbols (decode)
   int4 geo[3];                 // per type: valid width, valid height, interleaved row and column of sample (0, 0)
 };
@@ -574,6 +624,7 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
     f.step = b.level == 0 ? 1 << (t.L - z0) : 2 << (b.level - 1 - z0);
     f.d = f.keep = 0;
     f.quad = 0;
+    f.level = b.level;
     f.base = b.coef;
     for (int ty = 0; ty < 3; ++ty) {
       int sx, sy, sw, sh, py, px;
@@ -611,6 +662,42 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
   }
   f.end = incl;
   if (lane < nbc) fb[lane] = f;
+}
+
+// Quantise + area-ordered pack of the loop units [u0, u1) of the block table
+// (one area each), by threads tid = first .. of n.
+__device__ inline void pack_units(const FusedBlock* s_fb, int u0, int u1, int tid, int n, const int16_t* P, int pitch,
+                                  uint8_t* __restrict__ coef) {
+  int blk = 0;
+  for (int g = u0 + tid; g < u1; g += n) {
+    while (g >= s_fb[blk].end) ++blk;
+    const FusedBlock& f = s_fb[blk];
+    const int a = g - (blk ? s_fb[blk - 1].end : 0);
+    AreaMap am;
+    am.n = f.n; am.w = f.w; am.nlog = f.nlog; am.wlog = f.wlog;
+    int type, k, i, j;
+    am.split(a, &type, &k);
+    am.ij(k, &i, &j);
+    const int4 gm = f.geo[type];
+    const int step = f.step, q = f.q;
+    const int16_t* src = P + (gm.z + i * step) * pitch + gm.w + j * step;
+    int16_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int r = e >> 2, cc = e & 3;
+      int32_t cval = 0;
+      if (i + r < gm.y && j + cc < gm.x) cval = src[(r * step) * pitch + cc * step];
+      int32_t m = cval < 0 ? -cval : cval;
+      m >>= q;
+      v[e] = (int16_t)(cval < 0 ? -m : m);
+    }
+    uint4 u;
+    u.x = (uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+    u.y = (uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+    u.z = (uint16_t)v[4] | ((uint32_t)(uint16_t)v[5] << 16);
+    u.w = (uint16_t)v[6] | ((uint32_t)(uint16_t)v[7] << 16);
+    reinterpret_cast<uint4*>(coef + f.base)[a] = u;
+  }
 }
 
 __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
@@ -684,42 +771,40 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   // samples above the tile's bit depth void the int16 range bound of the transform
   if (__any_sync(0xffffffffu, over != 0) && (threadIdx.x & 31) == 0 && c == 0) set_status(status, kStRange);
   __syncthreads();
-  transform_fwd_levels(P, pitch, w, h, t.L);
-  // quantise + area-ordered pack of this channel's blocks, one loop over all their areas
+  // quantise + area-ordered pack of this channel's blocks (one loop over the areas of a range of blocks)
   const int nbc = t.nb / t.C;
-  if (threadIdx.x < 32) fused_block_table(t, blocks, nullptr, nullptr, t.block_base + (int64_t)c * nbc, nbc, 0, s_fb, nullptr);
-  __syncthreads();
-  const int total = s_fb[nbc - 1].end;
-  int blk = 0;
-  for (int g = threadIdx.x; g < total; g += blockDim.x) {
-    while (g >= s_fb[blk].end) ++blk;
-    const FusedBlock& f = s_fb[blk];
-    const int a = g - (blk ? s_fb[blk - 1].end : 0);
-    AreaMap am;
-    am.n = f.n; am.w = f.w; am.nlog = f.nlog; am.wlog = f.wlog;
-    int type, k, i, j;
-    am.split(a, &type, &k);
-    am.ij(k, &i, &j);
-    const int4 gm = f.geo[type];
-    const int step = f.step, q = f.q;
-    const int16_t* src = P + (gm.z + i * step) * pitch + gm.w + j * step;
-    int16_t v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int r = e >> 2, cc = e & 3;
-      int32_t cval = 0;
-      if (i + r < gm.y && j + cc < gm.x) cval = src[(r * step) * pitch + cc * step];
-      int32_t m = cval < 0 ? -cval : cval;
-      m >>= q;
-      v[e] = (int16_t)(cval < 0 ? -m : m);
-    }
-    uint4 u;
-    u.x = (uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
-    u.y = (uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
-    u.z = (uint16_t)v[4] | ((uint32_t)(uint16_t)v[5] << 16);
-    u.w = (uint16_t)v[6] | ((uint32_t)(uint16_t)v[7] << 16);
-    reinterpret_cast<uint4*>(coef + f.base)[a] = u;
+  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  // After level 0 the level-1 blocks (3/4 of the coefficients) are final and
+  // at most half of the lines are left to lift: the first W warps lift levels
+  // 1.. while the others build the block table and pack the level-1 blocks.
+  int W = 0;
+  if (t.L >= 2 && level_dim(w, 0) > kWarpGrid) {
+    W = (max(level_dim(w, 1), level_dim(h, 1)) + 31) >> 5;
+    if (W >= nwarps) W = 0;
   }
+  if (W == 0) {
+    transform_fwd_levels(P, pitch, w, h, t.L);
+    if (threadIdx.x < 32) fused_block_table(t, blocks, nullptr, nullptr, t.block_base + (int64_t)c * nbc, nbc, 0, s_fb, nullptr);
+    __syncthreads();
+    pack_units(s_fb, 0, s_fb[nbc - 1].end, threadIdx.x, blockDim.x, P, pitch, coef);
+    return;
+  }
+  level_fwd(P, pitch, level_dim(w, 0), level_dim(h, 0), 1);
+  // table order: LL, levels L .. 1 (stream order), so the level-1 blocks come last
+  if (warp < W) {
+    transform_fwd_levels_group(P, pitch, w, h, 1, t.L, W * 32);
+  } else {
+    const int gt = threadIdx.x - W * 32, gn = blockDim.x - W * 32;
+    if (gt < 32) fused_block_table(t, blocks, nullptr, nullptr, t.block_base + (int64_t)c * nbc, nbc, 0, s_fb, nullptr);
+    group_sync(2, gn);
+    int k1 = nbc;
+    while (k1 > 0 && s_fb[k1 - 1].level == 1) --k1;
+    pack_units(s_fb, k1 ? s_fb[k1 - 1].end : 0, s_fb[nbc - 1].end, gt, gn, P, pitch, coef);
+  }
+  __syncthreads();
+  int k1 = nbc;
+  while (k1 > 0 && s_fb[k1 - 1].level == 1) --k1;
+  pack_units(s_fb, 0, k1 ? s_fb[k1 - 1].end : 0, threadIdx.x, blockDim.x, P, pitch, coef);
 }
 
 // Decoded RGB8 pixels of one tile at level z into the region output, by the
@@ -898,26 +983,12 @@ __device__ inline void rebuild_quad(const FusedBlock& f, const AreaMap& am, cons
   }
 }
 
-__global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
-                                                                 const BlockDev* __restrict__ blocks, const DecInfo* __restrict__ info,
-                                                                 const int64_t* __restrict__ sym_off, const uint8_t* __restrict__ sym,
-                                                                 const int64_t* __restrict__ sym_total, int64_t sym_cap, int z,
-                                                                 int16_t* __restrict__ fplanes, uint32_t* __restrict__ tickets) {
-  extern __shared__ __align__(16) int16_t P[];
-  __shared__ FusedBlock s_fb[kMaxFusedBlocks];
-  __shared__ int32_t s_po[kMaxFusedBlocks][kMaxFusedPlanes][3];   // (plane, type) symbols from the block's first; -1: not kept
-  __shared__ bool s_last;
-  const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
-  const TileDev& t = tiles[tt];
-  if (c >= t.C || *sym_total > sym_cap) return;
-  const int zw = level_dim(t.w, z), zh = level_dim(t.h, z), pitch = smem_pitch(zw);
-  // rebuild of every block of the channel needed at level z, one loop over all their areas
-  const int nbc = t.nb / t.C;
-  if (threadIdx.x < 32) fused_block_table(t, blocks, info, sym_off, t.block_base + (int64_t)c * nbc, nbc, z, s_fb, s_po);
-  __syncthreads();
-  const int total = s_fb[nbc - 1].end;
+// Rebuild of the loop units [u0, u1) of the block table (areas or area
+// quads) into the interleaved plane, by threads tid = first .. of n.
+__device__ inline void rebuild_units(const FusedBlock* s_fb, const int32_t (*s_po)[kMaxFusedPlanes][3], const uint8_t* __restrict__ sym,
+                                     int u0, int u1, int tid, int n, int16_t* P, int pitch) {
   int blk = 0;
-  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+  for (int g = u0 + tid; g < u1; g += n) {
     while (g >= s_fb[blk].end) ++blk;
     const FusedBlock& f = s_fb[blk];
     const int u = g - (blk ? s_fb[blk - 1].end : 0);
@@ -985,8 +1056,52 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
       dst[(r * step) * pitch + cc * step] = (int16_t)(((neg >> e) & 1u) ? -v : v);
     }
   }
+}
+
+__global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
+                                                                 const BlockDev* __restrict__ blocks, const DecInfo* __restrict__ info,
+                                                                 const int64_t* __restrict__ sym_off, const uint8_t* __restrict__ sym,
+                                                                 const int64_t* __restrict__ sym_total, int64_t sym_cap, int z,
+                                                                 int16_t* __restrict__ fplanes, uint32_t* __restrict__ tickets) {
+  extern __shared__ __align__(16) int16_t P[];
+  __shared__ FusedBlock s_fb[kMaxFusedBlocks];
+  __shared__ int32_t s_po[kMaxFusedBlocks][kMaxFusedPlanes][3];   // (plane, type) symbols from the block's first; -1: not kept
+  __shared__ bool s_last;
+  const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
+  const TileDev& t = tiles[tt];
+  if (c >= t.C || *sym_total > sym_cap) return;
+  const int zw = level_dim(t.w, z), zh = level_dim(t.h, z), pitch = smem_pitch(zw);
+  // rebuild of every block of the channel needed at level z, one loop over all their areas
+  const int nbc = t.nb / t.C;
+  if (threadIdx.x < 32) fused_block_table(t, blocks, info, sym_off, t.block_base + (int64_t)c * nbc, nbc, z, s_fb, s_po);
   __syncthreads();
-  transform_inv_levels(P, pitch, t.w, t.h, t.L, z);
+  const int total = s_fb[nbc - 1].end;
+  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  // The blocks of the finest level decoded (z + 1) come last in the table and
+  // hold 3/4 of the coefficients; the inverse levels above it touch only the
+  // coarser grid.  So: rebuild the coarser blocks, then the first W warps
+  // invert levels L-1 .. z+1 while the others rebuild the finest blocks,
+  // then the CTA inverts level z+1 into the level-z image.
+  int kf = nbc;
+  while (kf > 0 && s_fb[kf - 1].level == z + 1) --kf;
+  const int uF = kf ? s_fb[kf - 1].end : 0;
+  int W = 0;
+  if (t.L - 1 >= z + 1 && kf < nbc && level_dim(t.w, z) > kWarpGrid) {
+    W = (max(level_dim(t.w, z + 1), level_dim(t.h, z + 1)) + 31) >> 5;
+    if (W >= nwarps) W = 0;
+  }
+  if (W == 0) {
+    rebuild_units(s_fb, s_po, sym, 0, total, threadIdx.x, blockDim.x, P, pitch);
+    __syncthreads();
+    transform_inv_levels(P, pitch, t.w, t.h, t.L, z);
+  } else {
+    rebuild_units(s_fb, s_po, sym, 0, uF, threadIdx.x, blockDim.x, P, pitch);
+    __syncthreads();
+    if (warp < W) transform_inv_levels_group(P, pitch, t.w, t.h, t.L, z + 1, z, W * 32);
+    else rebuild_units(s_fb, s_po, sym, uF, total, threadIdx.x - W * 32, blockDim.x - W * 32, P, pitch);
+    __syncthreads();
+    level_inv(P, pitch, level_dim(t.w, z), level_dim(t.h, z), 1);
+  }
   if (t.C == 3) {
     // Every CTA leaves its channel plane (int16) in global memory and takes
     // a ticket; the tile's third CTA to finish inverts the colour transform
