@@ -316,17 +316,28 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
     uint32_t carry = kAllZero;
     for (int base = 0; base < len; base += 512) {
       const LaneSyms L = load_lane(seg, len, base);
-      uint32_t zeros = 0, lz = 0;
-      bool seen = false;
-      for (int k = 0; k < L.cnt; ++k) {
-        const uint32_t s = L.at(k);
-        if (s == 0) {
-          ++zeros;
-        } else {
-          atomicAdd(&s_hist[s], 1u);
-          if (!seen) { lz = zeros; seen = true; }
-          else if (zeros) record_run(zeros, s_hist, &s_runs, s_extra);
-          zeros = 0;
+      // bit k of Z: symbol k of the lane is zero (4 bytes at a time)
+      uint32_t Z = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t t = __vcmpeq4(L.w[q], 0u) & 0x01010101u;
+        Z |= ((t * 0x01020408u) >> 24) << (4 * q);   // the four byte flags land in bits 24..27 without carries
+      }
+      const uint32_t valid = L.cnt >= 32 ? 0xffffffffu : (1u << L.cnt) - 1u;
+      Z &= valid;
+      const uint32_t NZ = ~Z & valid;
+      const bool seen = NZ != 0;
+      uint32_t lz = 0, zeros = 0;
+      if (seen) {
+        for (uint32_t m = NZ; m; m &= m - 1u) atomicAdd(&s_hist[L.at(__ffs(m) - 1)], 1u);
+        const int first = __ffs(NZ) - 1, last = 31 - __clz(NZ);
+        lz = (uint32_t)first;
+        zeros = (uint32_t)(L.cnt - 1 - last);
+        // zero runs between the lane's first and last nonzero symbols
+        const uint32_t Zi = Z & ((last >= 31 ? 0xffffffffu : (2u << last) - 1u) & ~((2u << first) - 1u));
+        for (uint32_t st = Zi & ~(Zi << 1); st; st &= st - 1u) {
+          const int s0 = __ffs(st) - 1;
+          record_run((uint32_t)(__ffs(~(Zi >> s0)) - 1), s_hist, &s_runs, s_extra);
         }
       }
       const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
