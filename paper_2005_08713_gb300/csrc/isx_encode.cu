@@ -93,6 +93,20 @@ __device__ inline LaneSyms load_lane(const uint8_t* seg, int len, int base) {
   return L;
 }
 
+// Bit k set: symbol k of the lane is nonzero (k < cnt).  Four byte
+// compares per word; the multiply gathers the four flags into bits 24..27
+// (the partial products never overlap, so there are no carries).
+__device__ inline uint32_t nonzero_mask(const LaneSyms& L) {
+  uint32_t Z = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t t = __vcmpeq4(L.w[q], 0u) & 0x01010101u;
+    Z |= ((t * 0x01020408u) >> 24) << (4 * q);
+  }
+  const uint32_t valid = (1u << L.cnt) - 1u;   // cnt <= 16
+  return ~Z & valid;
+}
+
 // ------------------------------------------------------------- pass 1
 __device__ inline void record_run(uint32_t L, uint32_t* s_hist, uint32_t* s_runs, uint32_t* s_extra) {
   if (L == 1) {
@@ -316,16 +330,8 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
     uint32_t carry = kAllZero;
     for (int base = 0; base < len; base += 512) {
       const LaneSyms L = load_lane(seg, len, base);
-      // bit k of Z: symbol k of the lane is zero (4 bytes at a time)
-      uint32_t Z = 0;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t t = __vcmpeq4(L.w[q], 0u) & 0x01010101u;
-        Z |= ((t * 0x01020408u) >> 24) << (4 * q);   // the four byte flags land in bits 24..27 without carries
-      }
-      const uint32_t valid = L.cnt >= 32 ? 0xffffffffu : (1u << L.cnt) - 1u;
-      Z &= valid;
-      const uint32_t NZ = ~Z & valid;
+      const uint32_t NZ = nonzero_mask(L);
+      const uint32_t Z = ~NZ & ((1u << L.cnt) - 1u);   // the lane's zero symbols
       const bool seen = NZ != 0;
       uint32_t lz = 0, zeros = 0;
       if (seen) {
@@ -715,18 +721,21 @@ __device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct,
   uint64_t total = 0;
   for (int base = 0; base < len; base += 512) {
     const LaneSyms L = load_lane(seg, len, base);
-    uint32_t zeros = 0, lz = 0;
-    bool seen = false;
-    uint32_t bits = 0;
-    for (int k = 0; k < L.cnt; ++k) {
-      const uint32_t s = L.at(k);
-      if (s == 0) {
-        ++zeros;
-      } else {
-        if (!seen) { lz = zeros; seen = true; }
-        else if (zeros) bits += run_bits(ct, zeros);
-        bits += lit_bits(ct, s);
-        zeros = 0;
+    // nonzero symbols of the lane as a bit mask: the loops visit only those;
+    // the zeros between two of them form one run
+    const uint32_t NZ = nonzero_mask(L);
+    const bool seen = NZ != 0;
+    uint32_t zeros = 0, lz = 0, bits = 0;
+    if (seen) {
+      const int first = __ffs(NZ) - 1, last = 31 - __clz(NZ);
+      lz = (uint32_t)first;
+      zeros = (uint32_t)(L.cnt - 1 - last);
+      int prev = first;
+      for (uint32_t m = NZ; m; m &= m - 1u) {
+        const int k = __ffs(m) - 1;
+        if (k - prev > 1) bits += run_bits(ct, (uint32_t)(k - prev - 1));
+        bits += lit_bits(ct, L.at(k));
+        prev = k;
       }
     }
     const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
@@ -751,18 +760,12 @@ __device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct,
       LaneWriter W;
       W.begin(out, pos + (int64_t)total + (x - bits));
       if (lead) put_run(ct, W, lead);
-      uint32_t z = 0;
-      bool first = true;
-      for (int k = 0; k < L.cnt; ++k) {
-        const uint32_t s = L.at(k);
-        if (s == 0) {
-          ++z;
-        } else {
-          if (!first && z) put_run(ct, W, z);
-          first = false;
-          put_literal(ct, W, s);
-          z = 0;
-        }
+      int prev = __ffs(NZ) - 1;
+      for (uint32_t m = NZ; m; m &= m - 1u) {
+        const int k = __ffs(m) - 1;
+        if (k - prev > 1) put_run(ct, W, (uint32_t)(k - prev - 1));
+        put_literal(ct, W, L.at(k));
+        prev = k;
       }
       if (fin) put_run(ct, W, fin);
       W.end();
