@@ -358,6 +358,7 @@ struct DecodeLayout {
   FusedClass cls[ISX_SIZE_CLASSES];
   size_t o_tiles = 0, o_idx = 0, o_task = 0, o_blocks = 0, o_bb = 0, o_bl = 0, o_info = 0, o_sb = 0, o_so = 0, o_part = 0, o_tot = 0;
   size_t o_tab = 0, o_bucket = 0, o_items = 0, o_sym = 0, o_A = 0, o_B = 0, o_fp = 0, o_tk = 0, total = 0;
+  size_t o_perm = 0, o_icnt = 0, o_ibase = 0;
 };
 
 // Host planning of a decode: one descriptor per job whose tile meets its
@@ -430,6 +431,9 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
   D.o_tab = cv.take(dec_table_bytes() * nb);
   D.o_bucket = cv.take(8 * 2 * 512);
   D.o_items = cv.take(8 * (size_t)D.max_items);
+  D.o_perm = cv.take(8 * nb);
+  D.o_icnt = cv.take(8 * nb);
+  D.o_ibase = cv.take(8 * nb);
   D.o_sym = cv.take((size_t)D.sym_cap + 64);
   D.o_A = cv.take(4 * (size_t)D.plane_total);
   D.o_B = cv.take(4 * (size_t)D.plane_total);
@@ -456,6 +460,7 @@ int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, co
   db.sym = base + D.o_sym; db.sym_cap = D.sym_cap;
   db.tables = base + D.o_tab; db.bucket = (int64_t*)(base + D.o_bucket); db.items = (int64_t*)(base + D.o_items);
   db.max_items = D.max_items;
+  db.perm = (int64_t*)(base + D.o_perm); db.item_cnt = (int64_t*)(base + D.o_icnt); db.item_base = (int64_t*)(base + D.o_ibase);
   int L = launch_decode_blocks(db, s, T);
   T->mark("decode.inverse_transform", s);
   uint32_t* tickets = (uint32_t*)(base + D.o_tk);

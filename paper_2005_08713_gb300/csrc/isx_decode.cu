@@ -257,10 +257,9 @@ __global__ void k_dec_tables(const BlockDev* __restrict__ blocks, int64_t nb, co
   sym_bytes[bi] = bytes;
 }
 
-// Blocks are processed in groups of kGroup of one level (counting sort by
-// level), so that the segments a CTA decodes have similar lengths.
+// Blocks ordered by level (counting sort): neighbouring blocks in the order
+// have the same size.
 constexpr int kLevels = 16;
-constexpr int kGroup = 32;
 
 __global__ void k_dec_level_count(const BlockDev* __restrict__ blocks, int64_t nb, int64_t* __restrict__ cnt) {
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -356,107 +355,121 @@ struct BitPf {
 
 // 16-byte symbol writer of one thread.
 struct SymOut {
-  uint4* dst;          // 16-byte chunks of the plane region
+  uint4* dst;          // the 16-byte chunk being filled
   uint64_t lo, hi;
-  int c;               // bytes in the pending chunk
+  int c;               // position of the next symbol in the chunk
+  bool dirty;          // the chunk holds a nonzero symbol
   __device__ void flush() {
-    *dst++ = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+    if (dirty) *dst = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+    ++dst;
     lo = hi = 0;
     c = 0;
+    dirty = false;
   }
   __device__ void put(uint32_t s) {
-    if (c < 8) lo |= (uint64_t)s << (8 * c);
-    else hi |= (uint64_t)s << (8 * (c - 8));
+    const uint64_t v = (uint64_t)s << (8 * (c & 7));
+    if (c < 8) lo |= v;
+    else hi |= v;
+    dirty = true;
     if (++c == 16) flush();
   }
+  // The region was cleared beforehand: a run of zeros only moves the position.
   __device__ void zeros(uint32_t cnt) {
-    while (cnt > 0) {
-      if (c == 0 && cnt >= 16) {
-        *dst++ = make_uint4(0, 0, 0, 0);
-        cnt -= 16;
-      } else {
-        uint32_t take = min(cnt, (uint32_t)(16 - c));
-        c += take;
-        cnt -= take;
-        if (c == 16) flush();
-      }
+    const uint32_t p = (uint32_t)c + cnt;
+    if (p < 16) {
+      c = (int)p;
+      return;
     }
+    flush();
+    dst += (p >> 4) - 1;
+    c = (int)(p & 15);
   }
 };
-
-// Segment items (block << 5 | plane) are bucketed by the bit length of the
-// segment (its seektable entry), longest first, so that the 32 segments of
-// a warp take similar time and the longest start first.
-constexpr int kLenBuckets = 33;
-
-__device__ inline int len_bucket(uint32_t seglen) { return 32 - (seglen ? (32 - __clz(seglen)) : 0); }   // longest -> 0
-
-__global__ void __launch_bounds__(128) k_dec_item_count(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
-                                                       const DecTab* __restrict__ tabs, int64_t* __restrict__ bucket) {
-  __shared__ unsigned long long h[kLenBuckets];
-  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x) h[k] = 0;
-  __syncthreads();
-  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (bi < nb) {
-    const BlockDev b = blocks[bi];
-    const DecInfo di = info[bi];
-    if (b.p > 0 && di.d > 0 && tabs[bi].nnodes > 0)
-      for (int pl = 0; pl < di.keep; ++pl)
-        if (kept_mask(di.removed, b.p, pl)) atomicAdd(&h[len_bucket(tabs[bi].seglen[pl])], 1ull);
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x)
-    if (h[k]) atomicAdd(reinterpret_cast<unsigned long long*>(&bucket[k]), h[k]);
-}
-
-__global__ void __launch_bounds__(128) k_dec_item_fill(const BlockDev* __restrict__ blocks, int64_t nb, const DecInfo* __restrict__ info,
-                                                      const DecTab* __restrict__ tabs, const int64_t* __restrict__ bucket_off,
-                                                      int64_t* __restrict__ fill, int64_t* __restrict__ items) {
-  __shared__ unsigned long long h[kLenBuckets];
-  __shared__ unsigned long long base[kLenBuckets];
-  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x) h[k] = 0;
-  __syncthreads();
-  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Segment items (block << 5 | plane) in block-major order: blocks by level
+// (neighbouring blocks have the same size), each block's kept planes in
+// order, so that the 32 lanes of a warp decode the planes of a few blocks
+// whose lookup tables the warp keeps in shared memory.
+__device__ inline uint32_t block_item_planes(const BlockDev& b, const DecInfo& di, const DecTab& T) {
   uint32_t planes = 0;
-  BlockDev b;
-  DecInfo di;
-  if (bi < nb) {
-    b = blocks[bi];
-    di = info[bi];
-    if (b.p > 0 && di.d > 0 && tabs[bi].nnodes > 0)
-      for (int pl = 0; pl < di.keep; ++pl)
-        if (kept_mask(di.removed, b.p, pl)) planes |= 1u << pl;
-  }
-  // local slots first, then one global reservation per bucket
-  unsigned long long local[32];
-  for (int pl = 0; pl < 32; ++pl)
-    if ((planes >> pl) & 1u) local[pl] = atomicAdd(&h[len_bucket(tabs[bi].seglen[pl])], 1ull);
-  __syncthreads();
-  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x)
-    base[k] = h[k] ? (unsigned long long)bucket_off[k] + atomicAdd(reinterpret_cast<unsigned long long*>(&fill[k]), h[k]) : 0ull;
-  __syncthreads();
-  for (int pl = 0; pl < 32; ++pl)
-    if ((planes >> pl) & 1u) items[base[len_bucket(tabs[bi].seglen[pl])] + local[pl]] = (bi << 5) | pl;
+  if (b.p > 0 && di.d > 0 && T.nnodes > 0)
+    for (int pl = 0; pl < di.keep; ++pl)
+      if (kept_mask(di.removed, b.p, pl)) planes |= 1u << pl;
+  return planes;
 }
 
-// Segment pass: one thread per (block, plane) item decodes that plane
-// segment on its own from its seektable start, expanding zero runs, into
-// the block's symbol region.
-__global__ void __launch_bounds__(256) k_dec_segments(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ items,
+__global__ void __launch_bounds__(128) k_dec_item_count(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm, int64_t nb,
+                                                       const DecInfo* __restrict__ info, const DecTab* __restrict__ tabs,
+                                                       int64_t* __restrict__ cnt) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const int64_t bi = perm[j];
+  cnt[j] = __popc(block_item_planes(blocks[bi], info[bi], tabs[bi]));
+}
+
+__global__ void __launch_bounds__(128) k_dec_item_fill(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm, int64_t nb,
+                                                      const DecInfo* __restrict__ info, const DecTab* __restrict__ tabs,
+                                                      const int64_t* __restrict__ base, int64_t* __restrict__ items) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const int64_t bi = perm[j];
+  uint32_t planes = block_item_planes(blocks[bi], info[bi], tabs[bi]);
+  int64_t o = base[j];
+  while (planes) {
+    const int pl = __ffs(planes) - 1;
+    planes &= planes - 1u;
+    items[o++] = (bi << 5) | pl;
+  }
+}
+
+// Clears the decode's symbol buffer (totals[0] bytes): zero runs are then
+// skipped instead of written.
+__global__ void k_dec_zero_sym(uint4* __restrict__ sym, const int64_t* __restrict__ total, int64_t cap) {
+  const int64_t n = min(*total, cap) / 16;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    sym[k] = make_uint4(0, 0, 0, 0);
+}
+
+constexpr int kSegWarps = 8, kSegSlots = 4;   // 256 threads; lookup tables in shared memory per warp
+
+__global__ void __launch_bounds__(32 * kSegWarps) k_dec_segments(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ items,
                                                      const int64_t* __restrict__ n_items_p, const uint8_t* __restrict__ stream,
                                                      const int64_t* __restrict__ bbyte, const int32_t* __restrict__ blen,
                                                      const DecInfo* __restrict__ info, const DecTab* __restrict__ tabs,
                                                      const int64_t* __restrict__ sym_off, uint8_t* __restrict__ sym,
                                                      const int64_t* __restrict__ sym_total, int64_t sym_cap, int* __restrict__ status) {
+  __shared__ __align__(16) uint16_t s_tab[kSegWarps][kSegSlots][1 << kTabBits];
   const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (it >= *n_items_p) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (*sym_total > sym_cap) {   // a stream claiming more planes than its bit depth allows
     if (it == 0) set_status(status, kStCorrupt);
     return;
   }
-  const int64_t item = items[it];
-  const int64_t bi = item >> 5;
-  const int pl = (int)(item & 31);
+  const bool active = it < *n_items_p;
+  int64_t bi = -1;
+  int pl = 0;
+  if (active) {
+    const int64_t item = items[it];
+    bi = item >> 5;
+    pl = (int)(item & 31);
+  }
+  // The items are block-major: the lanes of one block are neighbours.  The
+  // first kSegSlots blocks of the warp get their 9-bit lookup table copied to
+  // shared memory (the lookups are on every symbol's critical path); any
+  // further block reads its table from global memory.
+  const int64_t prev = __shfl_up_sync(0xffffffffu, bi, 1);
+  const uint32_t heads = __ballot_sync(0xffffffffu, active && (lane == 0 || prev != bi));
+  const int slot = __popc(heads & ((2u << lane) - 1u)) - 1;
+  const int nslots = min(__popc(heads), kSegSlots);
+  uint32_t h = heads;
+  for (int sidx = 0; sidx < nslots; ++sidx) {
+    const int64_t b = __shfl_sync(0xffffffffu, bi, __ffs(h) - 1);
+    h &= h - 1u;
+    const uint4* src = reinterpret_cast<const uint4*>(tabs[b].tab);
+    uint4* dst = reinterpret_cast<uint4*>(s_tab[wid][sidx]);
+    for (int k = lane; k < (1 << kTabBits) / 8; k += 32) dst[k] = __ldg(src + k);
+  }
+  __syncwarp();
+  if (!active) return;
   const BlockDev b = blocks[bi];
   const DecInfo di = info[bi];
   const DecTab* T = tabs + bi;
@@ -468,15 +481,15 @@ __global__ void __launch_bounds__(256) k_dec_segments(const BlockDev* __restrict
   const int64_t start = T->segpos[pl];
   const int64_t limit = start + T->seglen[pl];
   const int czr = T->czr, wb = T->wbits;
-  const uint16_t* tab = T->tab;
+  const uint16_t* tab = slot < kSegSlots ? s_tab[wid][slot] : T->tab;
   const uint32_t* node = T->node;
   BitPf in;
   in.seek(stream + bbyte[bi], blen[bi], start);
-  SymOut out{reinterpret_cast<uint4*>(sym + off), 0, 0, 0};
+  SymOut out{reinterpret_cast<uint4*>(sym + off), 0, 0, 0, false};
   int pos = 0;
   bool bad = false;
   while (pos < need) {
-    const uint32_t e = __ldg(&tab[in.peek(kTabBits)]);
+    const uint32_t e = tab[in.peek(kTabBits)];
     int s;
     if (e & 0x8000u) {
       uint32_t nd = __ldg(&node[e & 0x1ff]);
@@ -591,14 +604,15 @@ int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T)
   ++L;
   T->mark("decode.order", s);
   L += launch_exclusive_scan(db.sym_bytes, db.n_blocks, db.sym_off, db.scan_part, db.totals, s);
-  cudaMemsetAsync(db.bucket, 0, 2 * sizeof(int64_t) * kLenBuckets, s);
-  k_dec_item_count<<<g, 128, 0, s>>>(db.blocks, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.bucket);
-  L += 1 + launch_exclusive_scan(db.bucket, kLenBuckets, db.bucket + kLenBuckets, db.scan_part, db.totals + 1, s);
-  cudaMemsetAsync(db.bucket, 0, sizeof(int64_t) * kLenBuckets, s);
-  k_dec_item_fill<<<g, 128, 0, s>>>(db.blocks, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.bucket + kLenBuckets,
-                                    db.bucket, db.items);
+  L += launch_level_sort(db.blocks, db.n_blocks, db.bucket, db.perm, db.scan_part, db.totals + 2, s);
+  k_dec_item_count<<<g, 128, 0, s>>>(db.blocks, db.perm, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.item_cnt);
+  L += 1 + launch_exclusive_scan(db.item_cnt, db.n_blocks, db.item_base, db.scan_part, db.totals + 1, s);
+  k_dec_item_fill<<<g, 128, 0, s>>>(db.blocks, db.perm, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.item_base,
+                                    db.items);
   ++L;
   T->mark("decode.segments", s);
+  k_dec_zero_sym<<<152 * 8, 256, 0, s>>>(reinterpret_cast<uint4*>(db.sym), db.totals, db.sym_cap);
+  ++L;
   k_dec_segments<<<(unsigned)((db.max_items + 255) / 256), 256, 0, s>>>(
       db.blocks, db.items, db.totals + 1, db.stream, db.block_byte, db.block_len, db.info, reinterpret_cast<const DecTab*>(db.tables),
       db.sym_off, db.sym, db.totals, db.sym_cap, db.status);

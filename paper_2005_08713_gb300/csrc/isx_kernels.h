@@ -79,8 +79,11 @@ struct DecodeBuffers {
   int64_t* totals;           // [2]: symbol buffer bytes, segment items
   void* tables;              // [n_blocks] decode tables (dec_table_bytes() each)
   int64_t* bucket;           // [2 * 64] counts / offsets of the sort buckets
-  int64_t* items;            // [max_items] (block << 5 | plane), longest segments first
+  int64_t* items;            // [max_items] (block << 5 | plane), blocks by level, planes in order
   int64_t max_items;
+  int64_t* perm;             // [n_blocks] blocks by level
+  int64_t* item_cnt;         // [n_blocks] kept plane segments of block perm[j]
+  int64_t* item_base;        // [n_blocks] first item of block perm[j]
   uint8_t* sym;              // symbol buffer
   int64_t sym_cap;           // its size: an upper bound from the tiles' bit depths
   int* status;
