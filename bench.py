@@ -105,13 +105,14 @@ class ClockSampler:
 # scaled to a full launch by pixels.  Valid only while the kernel's source file is the one captured
 # (first 16 hex digits of its sha256); otherwise the bench reports traffic as null.
 NCU_TRAFFIC = {
-    "encode.transform": ("k_fwd_tile_smem", "isx_transform.cu", "414dc082d1cdeba3", 8.197),
-    "encode.symbols": ("k_enc_symbols", "isx_encode.cu", "63ed4df3ed2c7365", 8.139),
-    "encode.huffman": ("k_block_huffman", "isx_encode.cu", "63ed4df3ed2c7365", 0.545),
-    "encode.emit": ("k_enc_emit", "isx_encode.cu", "63ed4df3ed2c7365", 3.805),
-    "decode.tables": ("k_dec_tables", "isx_decode.cu", "5b1305e839dcd65d", 0.530),
-    "decode.segments": ("k_dec_segments", "isx_decode.cu", "5b1305e839dcd65d", 2.652),
-    "decode.inverse_transform": ("k_inv_tile_smem", "isx_transform.cu", "414dc082d1cdeba3", 12.807),
+    "encode.transform": ("k_fwd_tile_smem", "isx_transform.cu", "1b6053f34866cd3a", 8.194),
+    "encode.symbols": ("k_enc_symbols", "isx_encode.cu", "5bfb56406164d0c9", 8.111),
+    "encode.huffman": ("k_block_huffman", "isx_encode.cu", "5bfb56406164d0c9", 0.504),
+    "encode.size": ("k_enc_size", "isx_encode.cu", "5bfb56406164d0c9", 2.376),
+    "encode.emit": ("k_enc_emit", "isx_encode.cu", "5bfb56406164d0c9", 3.808),
+    "decode.tables": ("k_dec_tables", "isx_decode.cu", "84710de25853770e", 0.530),
+    "decode.segments": ("k_dec_segments", "isx_decode.cu", "84710de25853770e", 2.486),
+    "decode.inverse_transform": ("k_inv_tile_smem", "isx_transform.cu", "1b6053f34866cd3a", 9.812),
 }
 
 
@@ -313,8 +314,7 @@ def run_gpu(args):
         "encode.emit": sym_bytes + 1700 * n_blocks + total_bytes,        # symbols + codes in, stream out
         "decode.tables": 600 * n_blocks,                                 # block headers in (<= 600 B), tables out
         "decode.segments": total_bytes + sym_bytes,                      # stream in, kept symbols out
-        "decode.inverse_transform": sym_bytes + 4 * 3 * px,              # symbols in, int32 planes out
-        "decode.store": 4 * 3 * px + 3 * px,                             # int32 planes in, RGB8 out
+        "decode.inverse_transform": sym_bytes + 3 * px,                  # symbols in, RGB8 pixels out (fused store)
     }
     single = {k: v for k, v in stages.items() if k in algo}
     dom = max(single, key=lambda k: single[k][0]) if single else None
