@@ -116,6 +116,26 @@ NCU_TRAFFIC = {
 }
 
 
+# Warp instructions per pixel of each stage's kernel (smsp__inst_executed.sum of the same capture),
+# for the issue-rate co-roofline: the codec is integer work, and its kernels are bound by latency and
+# instruction issue long before DRAM bandwidth.
+NCU_WARP_INST_PER_PX = {
+    "encode.transform": 6.531, "encode.symbols": 6.858, "encode.huffman": 6.394, "encode.size": 3.505,
+    "encode.emit": 7.874, "decode.tables": 1.438, "decode.segments": 9.170, "decode.inverse_transform": 7.492,
+}
+
+
+def issue_roofline(stage, px, ms):
+    """Achieved warp instructions per second (ncu count per pixel x pixels / event time) against the issue
+    peak: SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock seen during the run."""
+    import torch
+    per_px = NCU_WARP_INST_PER_PX.get(stage)
+    if per_px is None or traffic_bytes(stage, px) is None:   # same validity rule as the traffic figures
+        return None
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return per_px, sms
+
+
 def traffic_bytes(stage, px):
     import hashlib
     ent = NCU_TRAFFIC.get(stage)
@@ -322,7 +342,17 @@ def run_gpu(args):
     if dom:
         avg_ms = single[dom][0] / max(1, single[dom][1])
         ach = algo[dom] / (avg_ms / 1e3) / 1e9
+        iss = issue_roofline(dom, px, avg_ms)
+        alu = None
+        if iss and clk.get("sm_mhz"):
+            per_px, sms = iss
+            peak_wi = sms * 4 * clk["sm_mhz"] * 1e6
+            got = per_px * px / (avg_ms / 1e3)
+            alu = {"bound": "issue", "achieved": round(got / 1e9, 1), "peak": round(peak_wi / 1e9, 1), "unit": "G warp-inst/s",
+                   "frac": round(got / peak_wi, 4), "warp_inst_per_px": per_px,
+                   "peak_basis": f"{sms} SMs x 4 schedulers x 1 warp-inst/cycle x {clk['sm_mhz']:.0f} MHz (median under load)"}
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+                "issue_coroofline": alu,
                 "traffic": traffic_bytes(dom, px), "algorithmic_bytes": int(algo[dom]), "peak_kind": peak_kind,
                 "avg_launch_ms": round(avg_ms, 3), "stage_rooflines": {
                     k: {"GBps": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9, 1),
