@@ -381,27 +381,38 @@ __device__ inline void ilv_pos(int L, int level, int type, int y, int x, int z, 
 // so that threads sweeping different rows hit different banks.
 __host__ __device__ inline int smem_pitch(int w) { return ((w + 1) & ~1) | 2; }
 
-// In-place forward 5/3 lifting of one line of n samples `st` elements apart:
-// afterwards the low-pass samples sit at even and the high-pass samples at
-// odd positions.  Predict and update run in one sweep with a small register
-// window (x[2k+2] is read before position 2k+2 is overwritten).  The body
-// runs in chunks of kSweepChunk sample pairs whose reads all lie inside the
-// line: the chunk's loads are issued together, the lifting runs in
-// registers, then the chunk is stored (a chunk reads x[2k+1 .. 2k+2K] and
-// writes x[2k .. 2k+2K-1], so no read of a later chunk is overwritten).
-constexpr int kSweepChunk = 8;
+// In-place forward 5/3 lifting of the sample pairs k0 .. k1-1 of a line of
+// n samples `st` elements apart (pair k: x[2k], x[2k+1]; the last pair of an
+// odd line has only its even sample): afterwards the low-pass samples sit at
+// even and the high-pass samples at odd positions.  Predict and update run
+// in one sweep with a small register window (x[2k+2] is read before
+// position 2k+2 is overwritten).  The body runs in chunks of kSweepChunk
+// pairs whose reads all lie inside the run: the chunk's loads are issued
+// together, the lifting runs in registers, then the chunk is stored (a chunk
+// reads x[2k+1 .. 2k+2K] and writes x[2k .. 2k+2K-1]).  The run's last
+// pairs (at most kSweepChunk) take the same straight-line code in chunks of
+// kTailChunk pairs: loads past the run are clamped to the run's last sample
+// and the stores past it are predicated off, so no load waits behind a
+// branch (a scalar tail loop cost a shared-memory round trip per pair, which
+// dominated the short lines of the coarse levels).
+// A run that does not start the line takes the two samples before it
+// (pe = x[2k0-2], pd = x[2k0-1]) and one that does not end it the sample
+// after it (ne = x[2k1]), all as they were before the sweep: the caller
+// reads them before any thread of the line writes.
+constexpr int kSweepChunk = 8, kTailChunk = 2;
 
 template <typename T>
-__device__ inline void sweep_fwd(T* x, int n, int st) {
-  if (n < 2) return;
-  int32_t xe = x[0], dprev = 0;
-  int k = 0;
-  for (; 2 * (k + kSweepChunk) < n; k += kSweepChunk) {
-    int32_t v[2 * kSweepChunk], o[2 * kSweepChunk];
+__device__ inline void sweep_fwd_range(T* x, int n, int st, int k0, int k1, int32_t pe, int32_t pd, int32_t ne) {
+  constexpr int K = kSweepChunk;
+  int32_t xe = x[(2 * k0) * st], dprev = 0;
+  if (k0 > 0) dprev = pd - ((pe + xe) >> 1);   // d[k0-1], from the samples before the run
+  int k = k0;
+  for (; k + K < k1; k += K) {
+    int32_t v[2 * K], o[2 * K];
 #pragma unroll
-    for (int i = 0; i < 2 * kSweepChunk; ++i) v[i] = x[(2 * k + 1 + i) * st];
+    for (int i = 0; i < 2 * K; ++i) v[i] = x[(2 * k + 1 + i) * st];
 #pragma unroll
-    for (int i = 0; i < kSweepChunk; ++i) {
+    for (int i = 0; i < K; ++i) {
       const int32_t xe2 = v[2 * i + 1];
       const int32_t d = v[2 * i] - ((xe + xe2) >> 1);
       const int32_t dm1 = (k + i == 0) ? d : dprev;   // d[-1] mirrors to d[0]
@@ -411,40 +422,57 @@ __device__ inline void sweep_fwd(T* x, int n, int st) {
       xe = xe2;
     }
 #pragma unroll
-    for (int i = 0; i < 2 * kSweepChunk; ++i) x[(2 * k + i) * st] = (T)o[i];
+    for (int i = 0; i < 2 * K; ++i) x[(2 * k + i) * st] = (T)o[i];
   }
-  for (; 2 * k < n; ++k) {
-    int32_t d, xe2;
-    if (2 * k + 1 < n) {
-      xe2 = (2 * k + 2 < n) ? x[(2 * k + 2) * st] : xe;   // x[n] mirrors to x[n-2]
-      d = x[(2 * k + 1) * st] - ((xe + xe2) >> 1);
-      x[(2 * k + 1) * st] = (T)d;
-    } else {
-      d = dprev;   // odd n: d[nh] mirrors to d[nh-1]
-      xe2 = xe;
+  // last pairs k .. k1-1 (at most K), in predicated chunks of kTailChunk
+  // pairs; the sample after the run is ne, or x[n-2] at the end of an even
+  // line (mirror)
+  const int lim = min(2 * k1, n);   // samples of the run: x[2k .. lim-1]
+  for (; k < k1; k += kTailChunk) {
+    constexpr int J = kTailChunk;
+    int32_t v[2 * J], o[2 * J];
+#pragma unroll
+    for (int i = 0; i < 2 * J; ++i) v[i] = x[min(2 * k + 1 + i, lim - 1) * st];
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      // even sample after pair k+i: own, the next run's, or x[n-2] (mirror) at the end of an even line
+      const int32_t xe2 = (2 * (k + i) + 2 < lim) ? v[2 * i + 1] : (2 * k1 < n ? ne : xe);
+      const int32_t d = (2 * (k + i) + 1 < n) ? v[2 * i] - ((xe + xe2) >> 1) : dprev;   // odd n: d[nh] mirrors to d[nh-1]
+      const int32_t dm1 = (k + i == 0) ? d : dprev;
+      o[2 * i] = xe + ((dm1 + d + 2) >> 2);
+      o[2 * i + 1] = d;
+      dprev = d;
+      xe = xe2;
     }
-    const int32_t dm1 = k == 0 ? d : dprev;   // d[-1] mirrors to d[0]
-    x[(2 * k) * st] = (T)(xe + ((dm1 + d + 2) >> 2));
-    dprev = d;
-    xe = xe2;
+#pragma unroll
+    for (int i = 0; i < 2 * J; ++i) {
+      if (2 * k + i < lim) x[(2 * k + i) * st] = (T)o[i];
+    }
   }
 }
 
-// In-place inverse of sweep_fwd, chunked the same way (a chunk reads
-// x[2k+2 .. 2k+2K+1] and writes x[2k .. 2k+2K-1]).
 template <typename T>
-__device__ inline void sweep_inv(T* x, int n, int st) {
-  if (n < 2) return;
+__device__ inline void sweep_fwd(T* x, int n, int st) {
+  if (n >= 2) sweep_fwd_range(x, n, st, 0, (n + 1) >> 1, 0, 0, 0);
+}
+
+// In-place inverse of sweep_fwd_range over pairs k0 .. k1-1, chunked the same
+// way (a chunk reads x[2k+2 .. 2k+2K+1] and writes x[2k .. 2k+2K-1]).  A run
+// that does not start the line takes pd = x[2k0-1], one that does not end it
+// ns = x[2k1] and nd = x[2k1+1], all as they were before the sweep.
+template <typename T>
+__device__ inline void sweep_inv_range(T* x, int n, int st, int k0, int k1, int32_t pd, int32_t ns, int32_t nd) {
+  constexpr int K = kSweepChunk;
   const int nl = (n + 1) >> 1, nh = n >> 1;
-  int32_t dk = x[st];
-  int32_t e = x[0] - ((dk + dk + 2) >> 2);
-  int k = 0;
-  for (; k + kSweepChunk < nh; k += kSweepChunk) {
-    int32_t v[2 * kSweepChunk], o[2 * kSweepChunk];
+  int32_t dk = k0 < nh ? (int32_t)x[(2 * k0 + 1) * st] : pd;   // d[nh] mirrors to d[nh-1]
+  int32_t e = x[(2 * k0) * st] - (((k0 > 0 ? pd : dk) + dk + 2) >> 2);   // d[-1] mirrors to d[0]
+  int k = k0;
+  for (; k + K < k1 && k + K < nh; k += K) {
+    int32_t v[2 * K], o[2 * K];
 #pragma unroll
-    for (int i = 0; i < 2 * kSweepChunk; ++i) v[i] = x[(2 * k + 2 + i) * st];
+    for (int i = 0; i < 2 * K; ++i) v[i] = x[(2 * k + 2 + i) * st];
 #pragma unroll
-    for (int i = 0; i < kSweepChunk; ++i) {
+    for (int i = 0; i < K; ++i) {
       const int32_t dk1 = v[2 * i + 1];
       const int32_t en = v[2 * i] - ((dk + dk1 + 2) >> 2);
       o[2 * i] = e;
@@ -453,38 +481,115 @@ __device__ inline void sweep_inv(T* x, int n, int st) {
       dk = dk1;
     }
 #pragma unroll
-    for (int i = 0; i < 2 * kSweepChunk; ++i) x[(2 * k + i) * st] = (T)o[i];
+    for (int i = 0; i < 2 * K; ++i) x[(2 * k + i) * st] = (T)o[i];
   }
-  for (; k < nh; ++k) {
-    const int32_t dk1 = (k + 1 < nh) ? x[(2 * k + 3) * st] : dk;
-    const int32_t en = (k + 1 < nl) ? x[(2 * k + 2) * st] - ((dk + dk1 + 2) >> 2) : e;
-    x[(2 * k) * st] = (T)e;
-    x[(2 * k + 1) * st] = (T)(dk + ((e + en) >> 1));
-    e = en;
-    dk = dk1;
+  // last pairs k .. k1-1, in predicated chunks of kTailChunk pairs; v holds
+  // s[k+1..], d[k+1..] of the run, then the next run's ns, nd
+  const int lim = min(2 * k1, n);
+  for (; k < k1; k += kTailChunk) {
+    constexpr int J = kTailChunk;
+    int32_t v[2 * J], o[2 * J];
+#pragma unroll
+    for (int i = 0; i < 2 * J; ++i) {
+      const int idx = 2 * k + 2 + i;
+      const int32_t xv = x[min(idx, lim - 1) * st];
+      v[i] = idx < lim ? xv : (idx == 2 * k1 ? ns : nd);
+    }
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      const int kk = k + i;
+      const int32_t dk1 = (kk + 1 < nh) ? v[2 * i + 1] : dk;   // d[nh] mirrors to d[nh-1]
+      const int32_t en = (kk + 1 < nl) ? v[2 * i] - ((dk + dk1 + 2) >> 2) : e;   // x[n] mirrors to x[n-2]
+      o[2 * i] = e;
+      o[2 * i + 1] = dk + ((e + en) >> 1);
+      // pairs past the line's last odd sample leave e (the last even sample of an odd line) alone
+      const bool live = kk < nh;
+      e = live ? en : e;
+      dk = live ? dk1 : dk;
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * J; ++i) {
+      if (2 * k + i < lim && k + i / 2 < nh) x[(2 * k + i) * st] = (T)o[i];
+    }
   }
-  if (n & 1) x[(n - 1) * st] = (T)e;
+  if (k1 == nl && (n & 1)) x[(n - 1) * st] = (T)e;
+}
+
+template <typename T>
+__device__ inline void sweep_inv(T* x, int n, int st) {
+  if (n >= 2) sweep_inv_range(x, n, st, 0, (n + 1) >> 1, 0, 0, 0);
+}
+
+// Named barrier over the first n threads of the CTA (warps 0 .. n/32-1),
+// id 1 or 2 (0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+struct CtaSync {
+  __device__ void operator()() const { __syncthreads(); }
+};
+struct GroupSync {   // the first n threads, barrier 1
+  int n;
+  __device__ void operator()() const { group_sync(1, n); }
+};
+
+// One lifting pass over `nlines` lines of `len` samples (line i starts at
+// P + i * lstep, its samples `st` elements apart) by threads tid < n, ending
+// with sync().  When there are at least twice as many threads as lines
+// (rounded up to whole warps) and the lines are long, each line may be cut
+// into S <= smax runs of pairs, run j lifted by the threads of warp group j
+// (so the warps keep the one-line-per-lane access pattern): every thread
+// first reads the samples next to its run that a neighbouring run
+// overwrites, the group synchronises, then the runs are lifted.  Splitting
+// pays only where a few warps lift while the rest of the CTA does other
+// work: with the whole CTA lifting, shared-memory bandwidth bounds the pass
+// and the extra barrier costs more than the shorter runs save.
+template <bool kFwd, class Sync>
+__device__ inline void lift_pass(int16_t* P, int nlines, int len, int lstep, int st, int tid, int n, int smax, Sync sync) {
+  const int G = (nlines + 31) & ~31;
+  const int npairs = (len + 1) >> 1;
+  const int S = min(min(n / G, smax), npairs >> 4);
+  if (S <= 1) {
+    for (int i = tid; i < nlines; i += n) {
+      if (kFwd) sweep_fwd(P + i * lstep, len, st);
+      else sweep_inv(P + i * lstep, len, st);
+    }
+    sync();
+    return;
+  }
+  const int line = tid % G, run = tid / G;
+  const bool act = run < S && line < nlines;
+  int16_t* x = P + line * lstep;
+  const int k0 = run * npairs / S, k1 = (run + 1) * npairs / S;
+  int32_t h0 = 0, h1 = 0, h2 = 0;
+  if (act) {
+    if (kFwd) {
+      if (k0 > 0) { h0 = x[(2 * k0 - 2) * st]; h1 = x[(2 * k0 - 1) * st]; }
+      if (2 * k1 < len) h2 = x[(2 * k1) * st];
+    } else {
+      if (k0 > 0) h0 = x[(2 * k0 - 1) * st];
+      if (2 * k1 < len) h1 = x[(2 * k1) * st];
+      if (2 * k1 + 1 < len) h2 = x[(2 * k1 + 1) * st];
+    }
+  }
+  sync();
+  if (act) {
+    if (kFwd) sweep_fwd_range(x, len, st, k0, k1, h0, h1, h2);
+    else sweep_inv_range(x, len, st, k0, k1, h0, h1, h2);
+  }
+  sync();
 }
 
 // One level of the in-place 2-D transform on the grid at stride s
 // (cw x ch samples): columns then rows (forward), rows then columns (inverse);
 // one thread sweeps one line.
 __device__ inline void level_fwd(int16_t* P, int pitch, int cw, int ch, int s) {
-  if (ch >= 2)
-    for (int c = threadIdx.x; c < cw; c += blockDim.x) sweep_fwd(P + c * s, ch, s * pitch);
-  __syncthreads();
-  if (cw >= 2)
-    for (int r = threadIdx.x; r < ch; r += blockDim.x) sweep_fwd(P + (r * s) * pitch, cw, s);
-  __syncthreads();
+  lift_pass<true>(P, cw, ch, s, s * pitch, threadIdx.x, blockDim.x, 1, CtaSync());
+  lift_pass<true>(P, ch, cw, s * pitch, s, threadIdx.x, blockDim.x, 1, CtaSync());
 }
 
 __device__ inline void level_inv(int16_t* P, int pitch, int cw, int ch, int s) {
-  if (cw >= 2)
-    for (int r = threadIdx.x; r < ch; r += blockDim.x) sweep_inv(P + (r * s) * pitch, cw, s);
-  __syncthreads();
-  if (ch >= 2)
-    for (int c = threadIdx.x; c < cw; c += blockDim.x) sweep_inv(P + c * s, ch, s * pitch);
-  __syncthreads();
+  lift_pass<false>(P, ch, cw, s * pitch, s, threadIdx.x, blockDim.x, 1, CtaSync());
+  lift_pass<false>(P, cw, ch, s, s * pitch, threadIdx.x, blockDim.x, 1, CtaSync());
 }
 
 // The same levels done by one warp with warp barriers: once a level's grid
@@ -511,6 +616,32 @@ __device__ inline void level_inv_warp(int16_t* P, int pitch, int cw, int ch, int
 }
 
 constexpr int kWarpGrid = 32;   // grids up to 32 x 32 samples take the one-warp path
+
+// Warps that lift the levels coarser than the finest while the rest of the
+// CTA packs (encode) or rebuilds (decode) the finest level's blocks: the
+// lines of the level (cw x ch grid) rounded up to whole warps, times up to
+// `split` runs per line, leaving at least half of the warps to the blocks
+// (0: no overlap).  Measured per phase: two runs per line shorten the
+// encode's lifting; the decode's lifting is fastest on one run per line.
+#ifndef ISX_OVERLAP_SPLIT_FWD
+#define ISX_OVERLAP_SPLIT_FWD 2
+#endif
+#ifndef ISX_OVERLAP_SPLIT_INV
+#define ISX_OVERLAP_SPLIT_INV 1
+#endif
+// Warps that pack (encode) or rebuild (decode) the finest level's blocks
+// meanwhile, at most: the lifting warps are the critical path, and every
+// further block warp takes issue slots and shared-memory bandwidth from
+// them (measured on 256 x 256 tiles with 1024 threads: 8 and 12 balance the
+// two groups).
+constexpr int kOverlapBlockWarpsFwd = 8, kOverlapBlockWarpsInv = 12;
+__device__ inline int overlap_warps(int cw, int ch, int nwarps, int split) {
+  const int base = (max(cw, ch) + 31) >> 5;
+  int sp = split;
+  while (sp > 1 && 2 * base * sp > nwarps) --sp;
+  const int W = base * sp;
+  return W < nwarps ? W : 0;
+}
 
 // Levels 0 .. L-1 of the forward transform of a w x h plane.
 __device__ inline void transform_fwd_levels(int16_t* P, int pitch, int w, int h, int L) {
@@ -540,10 +671,6 @@ __device__ inline void transform_inv_levels(int16_t* P, int pitch, int w, int h,
   for (; l >= z; --l) level_inv(P, pitch, level_dim(w, l), level_dim(h, l), 1 << (l - z));
 }
 
-// Named barrier over the first n threads of the CTA (warps 0 .. n/32-1),
-// id 1 or 2 (0 is __syncthreads).
-__device__ __forceinline__ void group_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
-
 // Forward levels lmin .. L-1 done by the first n threads only (barrier 1):
 // after level 0 at most half the lines remain, and the rest of the CTA can
 // pack the finished level-1 blocks meanwhile.
@@ -552,12 +679,8 @@ __device__ inline void transform_fwd_levels_group(int16_t* P, int pitch, int w, 
   for (; l < L; ++l) {
     const int cw = level_dim(w, l), ch = level_dim(h, l), s = 1 << l;
     if (cw <= kWarpGrid && ch <= kWarpGrid) break;
-    if (ch >= 2)
-      for (int c = threadIdx.x; c < cw; c += n) sweep_fwd(P + c * s, ch, s * pitch);
-    group_sync(1, n);
-    if (cw >= 2)
-      for (int r = threadIdx.x; r < ch; r += n) sweep_fwd(P + (r * s) * pitch, cw, s);
-    group_sync(1, n);
+    lift_pass<true>(P, cw, ch, s, s * pitch, threadIdx.x, n, 4, GroupSync{n});
+    lift_pass<true>(P, ch, cw, s * pitch, s, threadIdx.x, n, 4, GroupSync{n});
   }
   if (l < L) {
     if (threadIdx.x < 32)
@@ -578,12 +701,8 @@ __device__ inline void transform_inv_levels_group(int16_t* P, int pitch, int w, 
   }
   for (; l >= lmin; --l) {
     const int cw = level_dim(w, l), ch = level_dim(h, l), s = 1 << (l - z);
-    if (cw >= 2)
-      for (int r = threadIdx.x; r < ch; r += n) sweep_inv(P + (r * s) * pitch, cw, s);
-    group_sync(1, n);
-    if (ch >= 2)
-      for (int c = threadIdx.x; c < cw; c += n) sweep_inv(P + c * s, ch, s * pitch);
-    group_sync(1, n);
+    lift_pass<false>(P, ch, cw, s * pitch, s, threadIdx.x, n, 4, GroupSync{n});
+    lift_pass<false>(P, cw, ch, s, s * pitch, threadIdx.x, n, 4, GroupSync{n});
   }
 }
 
@@ -777,11 +896,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   // After level 0 the level-1 blocks (3/4 of the coefficients) are final and
   // at most half of the lines are left to lift: the first W warps lift levels
   // 1.. while the others build the block table and pack the level-1 blocks.
-  int W = 0;
-  if (t.L >= 2 && level_dim(w, 0) > kWarpGrid) {
-    W = (max(level_dim(w, 1), level_dim(h, 1)) + 31) >> 5;
-    if (W >= nwarps) W = 0;
-  }
+  const int W = t.L >= 2 && level_dim(w, 0) > kWarpGrid ? overlap_warps(level_dim(w, 1), level_dim(h, 1), nwarps, ISX_OVERLAP_SPLIT_FWD) : 0;
   if (W == 0) {
     transform_fwd_levels(P, pitch, w, h, t.L);
     if (threadIdx.x < 32) fused_block_table(t, blocks, nullptr, nullptr, t.block_base + (int64_t)c * nbc, nbc, 0, s_fb, nullptr);
@@ -799,7 +914,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
     group_sync(2, gn);
     int k1 = nbc;
     while (k1 > 0 && s_fb[k1 - 1].level == 1) --k1;
-    pack_units(s_fb, k1 ? s_fb[k1 - 1].end : 0, s_fb[nbc - 1].end, gt, gn, P, pitch, coef);
+    const int pn = min(gn, kOverlapBlockWarpsFwd * 32);
+    if (gt < pn) pack_units(s_fb, k1 ? s_fb[k1 - 1].end : 0, s_fb[nbc - 1].end, gt, pn, P, pitch, coef);
   }
   __syncthreads();
   int k1 = nbc;
@@ -1085,11 +1201,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
   int kf = nbc;
   while (kf > 0 && s_fb[kf - 1].level == z + 1) --kf;
   const int uF = kf ? s_fb[kf - 1].end : 0;
-  int W = 0;
-  if (t.L - 1 >= z + 1 && kf < nbc && level_dim(t.w, z) > kWarpGrid) {
-    W = (max(level_dim(t.w, z + 1), level_dim(t.h, z + 1)) + 31) >> 5;
-    if (W >= nwarps) W = 0;
-  }
+  const int W = t.L - 1 >= z + 1 && kf < nbc && level_dim(t.w, z) > kWarpGrid
+                    ? overlap_warps(level_dim(t.w, z + 1), level_dim(t.h, z + 1), nwarps, ISX_OVERLAP_SPLIT_INV)
+                    : 0;
   if (W == 0) {
     rebuild_units(s_fb, s_po, sym, 0, total, threadIdx.x, blockDim.x, P, pitch);
     __syncthreads();
@@ -1097,8 +1211,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
   } else {
     rebuild_units(s_fb, s_po, sym, 0, uF, threadIdx.x, blockDim.x, P, pitch);
     __syncthreads();
+    const int rn = min((int)blockDim.x - W * 32, kOverlapBlockWarpsInv * 32);
     if (warp < W) transform_inv_levels_group(P, pitch, t.w, t.h, t.L, z + 1, z, W * 32);
-    else rebuild_units(s_fb, s_po, sym, uF, total, threadIdx.x - W * 32, blockDim.x - W * 32, P, pitch);
+    else if (threadIdx.x - W * 32 < rn) rebuild_units(s_fb, s_po, sym, uF, total, threadIdx.x - W * 32, rn, P, pitch);
     __syncthreads();
     level_inv(P, pitch, level_dim(t.w, z), level_dim(t.h, z), 1);
   }
