@@ -10,6 +10,7 @@
 // (Mallat layout).  Floors are arithmetic right shifts.
 #include "isx_internal.cuh"
 #include "isx_kernels.h"
+#include "isx_warp_levels.cuh"
 
 namespace isx {
 
@@ -592,19 +593,11 @@ __device__ inline void level_inv(int16_t* P, int pitch, int cw, int ch, int s) {
   lift_pass<false>(P, cw, ch, s, s * pitch, threadIdx.x, blockDim.x, 1, CtaSync());
 }
 
-// The same levels done by one warp with warp barriers: once a level's grid
-// is at most 32 x 32 samples there are too few lines to occupy the CTA, and
-// the CTA-wide barriers would cost more than the sweeps.
-__device__ inline void level_fwd_warp(int16_t* P, int pitch, int cw, int ch, int s) {
-  const int lane = threadIdx.x & 31;
-  if (ch >= 2)
-    for (int c = lane; c < cw; c += 32) sweep_fwd(P + c * s, ch, s * pitch);
-  __syncwarp();
-  if (cw >= 2)
-    for (int r = lane; r < ch; r += 32) sweep_fwd(P + (r * s) * pitch, cw, s);
-  __syncwarp();
-}
-
+// The decode's one-warp coarse levels (grids of at most 32 x 32 samples):
+// in-place line sweeps, one lane per line.  The register version
+// (isx_warp_levels.cuh) measured slower here: beside the block rebuild's
+// conflicted shared-memory stores, its transposes and plane reads wait
+// longer in the shared-memory queue than these sweeps.
 __device__ inline void level_inv_warp(int16_t* P, int pitch, int cw, int ch, int s) {
   const int lane = threadIdx.x & 31;
   if (cw >= 2)
@@ -615,7 +608,8 @@ __device__ inline void level_inv_warp(int16_t* P, int pitch, int cw, int ch, int
   __syncwarp();
 }
 
-constexpr int kWarpGrid = 32;   // grids up to 32 x 32 samples take the one-warp path
+// Scratch of the encode's one-warp coarse levels (isx_warp_levels.cuh): 32 x 33 words.
+__shared__ int32_t s_wl_scratch[32 * kWlPitch];
 
 // Warps that lift the levels coarser than the finest while the rest of the
 // CTA packs (encode) or rebuilds (decode) the finest level's blocks: the
@@ -632,9 +626,20 @@ constexpr int kWarpGrid = 32;   // grids up to 32 x 32 samples take the one-warp
 // Warps that pack (encode) or rebuild (decode) the finest level's blocks
 // meanwhile, at most: the lifting warps are the critical path, and every
 // further block warp takes issue slots and shared-memory bandwidth from
-// them (measured on 256 x 256 tiles with 1024 threads: 8 and 12 balance the
-// two groups).
-constexpr int kOverlapBlockWarpsFwd = 8, kOverlapBlockWarpsInv = 12;
+// them.  The block warps are taken among those that share no warp scheduler
+// with warp 0 (warp w issues on scheduler w % 4), which lifts the coarse
+// levels alone.
+constexpr int kOverlapBlockWarpsFwd = 12, kOverlapBlockWarpsInv = 12;
+
+// Rank of warp w among the block warps (w >= W, w % 4 != 0), or -1.
+__device__ inline int block_warp_rank(int w, int W) {
+  if (w < W || (w & 3) == 0) return -1;
+  return (w - W) - (((w - 1) >> 2) - ((W - 1) >> 2));
+}
+// Block warps available in a CTA of nwarps warps after W lifting warps (W >= 1).
+__device__ inline int block_warps(int nwarps, int W, int cap) {
+  return min(cap, (nwarps - W) - (((nwarps - 1) >> 2) - ((W - 1) >> 2)));
+}
 __device__ inline int overlap_warps(int cw, int ch, int nwarps, int split) {
   const int base = (max(cw, ch) + 31) >> 5;
   int sp = split;
@@ -652,8 +657,7 @@ __device__ inline void transform_fwd_levels(int16_t* P, int pitch, int w, int h,
     level_fwd(P, pitch, cw, ch, 1 << l);
   }
   if (l < L) {
-    if (threadIdx.x < 32)
-      for (int m = l; m < L; ++m) level_fwd_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << m);
+    if (threadIdx.x < 32) warp_levels_fwd(P, pitch, w, h, l, L, s_wl_scratch, threadIdx.x);
     __syncthreads();
   }
 }
@@ -662,11 +666,10 @@ __device__ inline void transform_fwd_levels(int16_t* P, int pitch, int w, int h,
 __device__ inline void transform_inv_levels(int16_t* P, int pitch, int w, int h, int L, int z) {
   int l = L - 1;
   if (l >= z && level_dim(w, l) <= kWarpGrid && level_dim(h, l) <= kWarpGrid) {
-    if (threadIdx.x < 32)
-      for (int m = l; m >= z && level_dim(w, m) <= kWarpGrid && level_dim(h, m) <= kWarpGrid; --m)
-        level_inv_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << (m - z));
-    __syncthreads();
     while (l >= z && level_dim(w, l) <= kWarpGrid && level_dim(h, l) <= kWarpGrid) --l;
+    if (threadIdx.x < 32)
+      for (int m = L - 1; m > l; --m) level_inv_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << (m - z));
+    __syncthreads();
   }
   for (; l >= z; --l) level_inv(P, pitch, level_dim(w, l), level_dim(h, l), 1 << (l - z));
 }
@@ -683,8 +686,7 @@ __device__ inline void transform_fwd_levels_group(int16_t* P, int pitch, int w, 
     lift_pass<true>(P, ch, cw, s * pitch, s, threadIdx.x, n, 4, GroupSync{n});
   }
   if (l < L) {
-    if (threadIdx.x < 32)
-      for (int m = l; m < L; ++m) level_fwd_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << m);
+    if (threadIdx.x < 32) warp_levels_fwd(P, pitch, w, h, l, L, s_wl_scratch, threadIdx.x);
     group_sync(1, n);
   }
 }
@@ -693,11 +695,10 @@ __device__ inline void transform_fwd_levels_group(int16_t* P, int pitch, int w, 
 __device__ inline void transform_inv_levels_group(int16_t* P, int pitch, int w, int h, int L, int lmin, int z, int n) {
   int l = L - 1;
   if (l >= lmin && level_dim(w, l) <= kWarpGrid && level_dim(h, l) <= kWarpGrid) {
-    if (threadIdx.x < 32)
-      for (int m = l; m >= lmin && level_dim(w, m) <= kWarpGrid && level_dim(h, m) <= kWarpGrid; --m)
-        level_inv_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << (m - z));
-    group_sync(1, n);
     while (l >= lmin && level_dim(w, l) <= kWarpGrid && level_dim(h, l) <= kWarpGrid) --l;
+    if (threadIdx.x < 32)
+      for (int m = L - 1; m > l; --m) level_inv_warp(P, pitch, level_dim(w, m), level_dim(h, m), 1 << (m - z));
+    group_sync(1, n);
   }
   for (; l >= lmin; --l) {
     const int cw = level_dim(w, l), ch = level_dim(h, l), s = 1 << (l - z);
@@ -914,8 +915,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
     group_sync(2, gn);
     int k1 = nbc;
     while (k1 > 0 && s_fb[k1 - 1].level == 1) --k1;
-    const int pn = min(gn, kOverlapBlockWarpsFwd * 32);
-    if (gt < pn) pack_units(s_fb, k1 ? s_fb[k1 - 1].end : 0, s_fb[nbc - 1].end, gt, pn, P, pitch, coef);
+    const int rank = block_warp_rank(warp, W), K = block_warps(nwarps, W, kOverlapBlockWarpsFwd);
+    if (rank >= 0 && rank < K)
+      pack_units(s_fb, k1 ? s_fb[k1 - 1].end : 0, s_fb[nbc - 1].end, rank * 32 + (threadIdx.x & 31), K * 32, P, pitch, coef);
   }
   __syncthreads();
   int k1 = nbc;
@@ -1211,9 +1213,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
   } else {
     rebuild_units(s_fb, s_po, sym, 0, uF, threadIdx.x, blockDim.x, P, pitch);
     __syncthreads();
-    const int rn = min((int)blockDim.x - W * 32, kOverlapBlockWarpsInv * 32);
+    const int rank = block_warp_rank(warp, W), K = block_warps(nwarps, W, kOverlapBlockWarpsInv);
     if (warp < W) transform_inv_levels_group(P, pitch, t.w, t.h, t.L, z + 1, z, W * 32);
-    else if (threadIdx.x - W * 32 < rn) rebuild_units(s_fb, s_po, sym, uF, total, threadIdx.x - W * 32, rn, P, pitch);
+    else if (rank >= 0 && rank < K) rebuild_units(s_fb, s_po, sym, uF, total, rank * 32 + (threadIdx.x & 31), K * 32, P, pitch);
     __syncthreads();
     level_inv(P, pitch, level_dim(t.w, z), level_dim(t.h, z), 1);
   }
