@@ -1077,26 +1077,72 @@ __device__ inline void rebuild_quad(const FusedBlock& f, const AreaMap& am, cons
   const int32_t half = (1 << q) >> 1;
   const int rowstep = step * pitch;
   const int shift = 33 - d;
+  // With a block width of 8 or more (a power of two) the quad's areas tile a
+  // 4 x 8 region: area a covers rows 2 (a & 1) .., columns 4 (a >> 1) ..
+  // The 32 coefficients are packed in pairs, R[r][k] = columns 2k, 2k+1 of
+  // region row r.
+  uint32_t R[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) R[r][k] = 0;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     uint32_t w0 = aw[0][a], w1 = aw[1][a], w2 = aw[2][a], w3 = aw[3][a];
     transpose8x8(w0, w1);
     transpose8x8(w2, w3);
     const uint32_t neg = (pw[0] >> (8 * a)) & 255u;
-    int i, j;
-    am.ij(k0 + a, &i, &j);
-    int16_t* dst = P + (gm.z + i * step) * pitch + gm.w + j * step;
-    const bool inside = i + 1 < gm.y && j + 3 < gm.x;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const int r = e >> 2, cc = e & 3;
-      if (!inside && (i + r >= gm.y || j + cc >= gm.x)) continue;
+      const int cc = e & 3;
       // magnitude bits, most significant plane first (bit j of the pair = plane j + 1); with d <= 16
       // the two unrelated upper bytes of the permute end below bit 33 - d and are shifted out
       const uint32_t rb = __byte_perm(e < 4 ? w0 : w1, e < 4 ? w2 : w3, cc | ((4 + cc) << 4));
       const int32_t m = d >= 2 ? (int32_t)(__brev(rb) >> shift) : 0;
       const int32_t v = m == 0 ? 0 : (m << q) + half;
-      dst[r * rowstep + cc * step] = (int16_t)(((neg >> e) & 1u) ? -v : v);
+      const uint32_t h16 = (uint32_t)(uint16_t)(((neg >> e) & 1u) ? -v : v);
+      const int r = 2 * (a & 1) + (e >> 2), c = 4 * (a >> 1) + cc;
+      R[r][c >> 1] |= h16 << (16 * (c & 1));
+    }
+  }
+  int i0, j0;
+  am.ij(k0, &i0, &j0);
+  int16_t* base = P + (gm.z + i0 * step) * pitch + gm.w + j0 * step;
+  if (am.wlog >= 3 && i0 + 3 < gm.y && j0 + 7 < gm.x) {
+    // Rotated stores: in store t of a row, lane l writes column (t + rho) & 7
+    // with rho = (l >> 2) & 7.  Neighbouring lanes' regions start 8 columns
+    // apart, so without rotation every store of a warp hits only four banks
+    // (8- to 32-way conflicts at steps 2 .. 8); rotated, the 32 lanes spread
+    // over all banks.
+    const int rho = (threadIdx.x >> 2) & 7, qw = rho >> 1, sh = (rho & 1) << 4;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      uint32_t Y[4], O[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t t0 = (qw & 1) ? R[r][(k + 1) & 3] : R[r][k];
+        const uint32_t t2 = (qw & 1) ? R[r][(k + 3) & 3] : R[r][(k + 2) & 3];
+        Y[k] = (qw & 2) ? t2 : t0;   // Y[k] = R[r][(k + qw) & 3]
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) O[k] = __funnelshift_r(Y[k], Y[(k + 1) & 3], sh);   // slot t = column (t + rho) & 7
+      int16_t* row = base + r * rowstep;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) row[((t + rho) & 7) * step] = (int16_t)(O[t >> 1] >> (16 * (t & 1)));
+    }
+    return;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int i, j;
+    am.ij(k0 + a, &i, &j);
+    int16_t* dst = P + (gm.z + i * step) * pitch + gm.w + j * step;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int rr = e >> 2, cc = e & 3;
+      if (i + rr >= gm.y || j + cc >= gm.x) continue;
+      const int r = 2 * (a & 1) + rr, c = 4 * (a >> 1) + cc;
+      dst[rr * rowstep + cc * step] = (int16_t)(R[r][c >> 1] >> (16 * (c & 1)));
     }
   }
 }
