@@ -718,7 +718,7 @@ struct FusedBlock {
   int32_t n, w, nlog, wlog;    // AreaMap of the block
   int32_t q, step;             // quantiser step (log2); distance of neighbouring subband samples
   int32_t d, keep;             // decode: bit depth and planes kept
-  int32_t quad;                // decode: the loop's units are 4 consecutive areas of a type (n % 4 == 0)
+  int32_t quad;                // the loop's units are 4 consecutive areas of a type (n % 4 == 0)
   int32_t level;               // 0 = LL
   int64_t base;                // byte offset of its coefficients (encode) or symbols (decode)
   int4 geo[3];                 // per type: valid width, valid height, interleaved row and column of sample (0, 0)
@@ -733,6 +733,7 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
                                          int32_t (*po)[kMaxFusedPlanes][3]) {
   const int lane = threadIdx.x & 31;
   FusedBlock f;
+  f.quad = 0;
   int na = 0;
   if (lane < nbc) {
     const BlockDev b = blocks[b0 + lane];
@@ -753,14 +754,13 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
       f.geo[ty] = make_int4(min(sw - kCell * b.bx, b.w), min(sh - kCell * b.by, b.h), py, px);
     }
     na = b.p * f.n;
+    f.quad = (f.n & 3) == 0;   // encode and decode loop over quads of areas where the block allows
     if (info) {
       const DecInfo di = info[b0 + lane];
       f.d = di.d;
       f.keep = min(di.keep, kMaxFusedPlanes);
       f.base = sym_off[b0 + lane];
       if (b.p == 0 || di.d == 0) na = 0;
-      f.quad = (f.n & 3) == 0;
-      if (f.quad) na >>= 2;
       // kept types of each plane are stored back to back, planes 16-byte aligned
       int32_t off = 0;
       for (int pl = 0; pl < f.keep; ++pl) {
@@ -774,6 +774,7 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
       }
     }
   }
+  if (f.quad) na >>= 2;
   int incl = na;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -786,6 +787,78 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
 
 // Quantise + area-ordered pack of the loop units [u0, u1) of the block table
 // (one area each), by threads tid = first .. of n.
+// Rotates eight int16 held in pairs (w[k] = slots 2k, 2k+1) so that slot t
+// takes slot (t + rot) & 7.
+__device__ __forceinline__ void rotate8x16(const uint32_t (&w)[4], int rot, uint32_t (&o)[4]) {
+  const int qw = rot >> 1, sh = (rot & 1) << 4;
+  uint32_t y[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t t0 = (qw & 1) ? w[(k + 1) & 3] : w[k];
+    const uint32_t t2 = (qw & 1) ? w[(k + 3) & 3] : w[(k + 2) & 3];
+    y[k] = (qw & 2) ? t2 : t0;   // y[k] = w[(k + qw) & 3]
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o[k] = __funnelshift_r(y[k], y[(k + 1) & 3], sh);
+}
+
+__device__ __forceinline__ uint32_t quantise16(int32_t c, int q) {
+  int32_t m = (c < 0 ? -c : c) >> q;
+  return (uint32_t)(uint16_t)(c < 0 ? -m : m);
+}
+
+// Quantise + pack of 4 consecutive areas a0 .. a0+3 of one type (the quad
+// of the decode's rebuild_quad): with a block width of 8 or more they tile
+// a 4 x 8 region, read row by row in lane-rotated column order (lane l reads
+// column (t + rho) & 7 in read t, rho = (l >> 2) & 7: neighbouring lanes'
+// regions start 8 columns apart, so unrotated reads hit four banks).
+__device__ inline void pack_quad(const FusedBlock& f, const AreaMap& am, int a0, const int16_t* P, int pitch,
+                                 uint8_t* __restrict__ coef) {
+  int type, k0;
+  am.split(a0, &type, &k0);
+  const int4 gm = f.geo[type];
+  const int step = f.step, q = f.q;
+  uint32_t R[4][4];   // region row r, columns 2k, 2k+1
+  int i0, j0;
+  am.ij(k0, &i0, &j0);
+  if (am.wlog >= 3 && i0 + 3 < gm.y && j0 + 7 < gm.x) {
+    const int rho = (threadIdx.x >> 2) & 7;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int16_t* row = P + (gm.z + (i0 + r) * step) * pitch + gm.w + j0 * step;
+      uint32_t O[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int t = 0; t < 8; ++t) O[t >> 1] |= quantise16(row[((t + rho) & 7) * step], q) << (16 * (t & 1));
+      rotate8x16(O, (8 - rho) & 7, R[r]);   // slot c = column c
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) R[r][k] = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int i, j;
+      am.ij(k0 + a, &i, &j);
+      const int16_t* src = P + (gm.z + i * step) * pitch + gm.w + j * step;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int rr = e >> 2, cc = e & 3;
+        int32_t cval = 0;
+        if (i + rr < gm.y && j + cc < gm.x) cval = src[(rr * step) * pitch + cc * step];
+        const int r = 2 * (a & 1) + rr, c = 4 * (a >> 1) + cc;
+        R[r][c >> 1] |= quantise16(cval, q) << (16 * (c & 1));
+      }
+    }
+  }
+  uint4* dst = reinterpret_cast<uint4*>(coef + f.base) + a0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r0 = 2 * (a & 1), k = 2 * (a >> 1);
+    dst[a] = make_uint4(R[r0][k], R[r0][k + 1], R[r0 + 1][k], R[r0 + 1][k + 1]);
+  }
+}
+
 __device__ inline void pack_units(const FusedBlock* s_fb, int u0, int u1, int tid, int n, const int16_t* P, int pitch,
                                   uint8_t* __restrict__ coef) {
   int blk = 0;
@@ -795,6 +868,10 @@ __device__ inline void pack_units(const FusedBlock* s_fb, int u0, int u1, int ti
     const int a = g - (blk ? s_fb[blk - 1].end : 0);
     AreaMap am;
     am.n = f.n; am.w = f.w; am.nlog = f.nlog; am.wlog = f.wlog;
+    if (f.quad) {
+      pack_quad(f, am, 4 * a, P, pitch, coef);
+      continue;
+    }
     int type, k, i, j;
     am.split(a, &type, &k);
     am.ij(k, &i, &j);
@@ -1114,18 +1191,11 @@ __device__ inline void rebuild_quad(const FusedBlock& f, const AreaMap& am, cons
     // apart, so without rotation every store of a warp hits only four banks
     // (8- to 32-way conflicts at steps 2 .. 8); rotated, the 32 lanes spread
     // over all banks.
-    const int rho = (threadIdx.x >> 2) & 7, qw = rho >> 1, sh = (rho & 1) << 4;
+    const int rho = (threadIdx.x >> 2) & 7;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      uint32_t Y[4], O[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t t0 = (qw & 1) ? R[r][(k + 1) & 3] : R[r][k];
-        const uint32_t t2 = (qw & 1) ? R[r][(k + 3) & 3] : R[r][(k + 2) & 3];
-        Y[k] = (qw & 2) ? t2 : t0;   // Y[k] = R[r][(k + qw) & 3]
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) O[k] = __funnelshift_r(Y[k], Y[(k + 1) & 3], sh);   // slot t = column (t + rho) & 7
+      uint32_t O[4];
+      rotate8x16(R[r], rho, O);   // slot t = column (t + rho) & 7
       int16_t* row = base + r * rowstep;
 #pragma unroll
       for (int t = 0; t < 8; ++t) row[((t + rho) & 7) * step] = (int16_t)(O[t >> 1] >> (16 * (t & 1)));
