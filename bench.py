@@ -102,17 +102,17 @@ class ClockSampler:
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per pixel of each stage's kernel, from one
 # ncu --set full capture of the 8192 x 8192 case of this workload (profiles/kernels_slide_8192x8192_lossy.md),
-# scaled to a full launch by pixels.  Valid only while the kernel's source file is the one captured
-# (first 16 hex digits of its sha256); otherwise the bench reports traffic as null.
+# scaled to a full launch by pixels.  Valid only while the kernel's source files are the ones captured
+# (first 16 hex digits of the sha256 of their contents in order); otherwise the bench reports traffic as null.
 NCU_TRAFFIC = {
-    "encode.transform": ("k_fwd_tile_smem", "isx_transform.cu", "1b6053f34866cd3a", 8.194),
+    "encode.transform": ("k_fwd_tile_smem", ("isx_transform.cu", "isx_warp_levels.cuh"), "f05605e453638b39", 8.187),
     "encode.symbols": ("k_enc_symbols", "isx_encode.cu", "5bfb56406164d0c9", 8.111),
     "encode.huffman": ("k_block_huffman", "isx_encode.cu", "5bfb56406164d0c9", 0.504),
     "encode.size": ("k_enc_size", "isx_encode.cu", "5bfb56406164d0c9", 2.376),
     "encode.emit": ("k_enc_emit", "isx_encode.cu", "5bfb56406164d0c9", 3.808),
     "decode.tables": ("k_dec_tables", "isx_decode.cu", "84710de25853770e", 0.530),
     "decode.segments": ("k_dec_segments", "isx_decode.cu", "84710de25853770e", 2.486),
-    "decode.inverse_transform": ("k_inv_tile_smem", "isx_transform.cu", "1b6053f34866cd3a", 9.812),
+    "decode.inverse_transform": ("k_inv_tile_smem", ("isx_transform.cu", "isx_warp_levels.cuh"), "f05605e453638b39", 9.812),
 }
 
 
@@ -120,8 +120,8 @@ NCU_TRAFFIC = {
 # for the issue-rate co-roofline: the codec is integer work, and its kernels are bound by latency and
 # instruction issue long before DRAM bandwidth.
 NCU_WARP_INST_PER_PX = {
-    "encode.transform": 6.531, "encode.symbols": 6.858, "encode.huffman": 6.394, "encode.size": 3.505,
-    "encode.emit": 7.874, "decode.tables": 1.438, "decode.segments": 9.170, "decode.inverse_transform": 7.492,
+    "encode.transform": 6.207, "encode.symbols": 6.858, "encode.huffman": 6.394, "encode.size": 3.505,
+    "encode.emit": 7.874, "decode.tables": 1.438, "decode.segments": 9.179, "decode.inverse_transform": 7.149,
 }
 
 
@@ -141,12 +141,15 @@ def traffic_bytes(stage, px):
     ent = NCU_TRAFFIC.get(stage)
     if not ent:
         return None
-    path = os.path.join(ROOT, "paper_2005_08713_gb300", "csrc", ent[1])
+    names = ent[1] if isinstance(ent[1], tuple) else (ent[1],)
+    h = hashlib.sha256()
     try:
-        with open(path, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+        for name in names:
+            with open(os.path.join(ROOT, "paper_2005_08713_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
     except OSError:
         return None
+    digest = h.hexdigest()[:16]
     return int(ent[3] * px) if digest == ent[2] else None
 
 
