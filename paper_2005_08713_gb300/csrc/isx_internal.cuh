@@ -78,10 +78,9 @@ struct DecInfo {
   uint32_t removed[3];
 };
 
-__host__ __device__ inline int level_dim(int n, int l) {
-  for (int i = 0; i < l; ++i) n = (n + 1) >> 1;
-  return n;
-}
+// Samples along one axis after l halvings with rounding up: ceil(n / 2^l)
+// (nested ceilings of halves compose); 0 stays 0.
+__host__ __device__ inline int level_dim(int n, int l) { return ((n - 1) >> l) + 1; }
 __host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 __device__ inline int bitlen_u32(uint32_t v) { return 32 - __clz(v); }

@@ -629,7 +629,7 @@ __shared__ int32_t s_wl_scratch[32 * kWlPitch];
 // them.  The block warps are taken among those that share no warp scheduler
 // with warp 0 (warp w issues on scheduler w % 4), which lifts the coarse
 // levels alone.
-constexpr int kOverlapBlockWarpsFwd = 12, kOverlapBlockWarpsInv = 12;
+constexpr int kOverlapBlockWarpsFwd = 8, kOverlapBlockWarpsInv = 12;
 
 // Rank of warp w among the block warps (w >= W, w % 4 != 0), or -1.
 __device__ inline int block_warp_rank(int w, int W) {
@@ -734,7 +734,11 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
   const int lane = threadIdx.x & 31;
   FusedBlock f;
   f.quad = 0;
+  f.keep = 0;
+  f.n = 0;
   int na = 0;
+  uint32_t rem[3] = {~0u, ~0u, ~0u};   // decode: removed planes per type
+  int p_types = 0;
   if (lane < nbc) {
     const BlockDev b = blocks[b0 + lane];
     f.n = b.w * b.h / 8;
@@ -761,17 +765,8 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
       f.keep = min(di.keep, kMaxFusedPlanes);
       f.base = sym_off[b0 + lane];
       if (b.p == 0 || di.d == 0) na = 0;
-      // kept types of each plane are stored back to back, planes 16-byte aligned
-      int32_t off = 0;
-      for (int pl = 0; pl < f.keep; ++pl) {
-        int32_t o = off;
-        for (int ty = 0; ty < 3; ++ty) {
-          const bool kept = ty < b.p && !((di.removed[ty] >> pl) & 1u);
-          po[lane][pl][ty] = kept ? o : -1;
-          if (kept) o += f.n;
-        }
-        off += (o - off + 15) & ~15;
-      }
+      rem[0] = di.removed[0]; rem[1] = di.removed[1]; rem[2] = di.removed[2];
+      p_types = b.p;
     }
   }
   if (f.quad) na >>= 2;
@@ -783,6 +778,38 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
   }
   f.end = incl;
   if (lane < nbc) fb[lane] = f;
+  if (!info) return;
+  // Symbol offsets of each (plane, type) from the block's first symbol: the
+  // kept types of a plane are stored back to back, planes 16-byte aligned.
+  // Per block, lane pl sizes plane pl and a warp scan places the planes.
+  for (int blk = 0; blk < nbc; ++blk) {
+    const int keep = __shfl_sync(0xffffffffu, f.keep, blk), n = __shfl_sync(0xffffffffu, f.n, blk);
+    const int pt = __shfl_sync(0xffffffffu, p_types, blk);
+    uint32_t r[3];
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty) r[ty] = __shfl_sync(0xffffffffu, rem[ty], blk);
+    const int pl = lane;
+    uint32_t km = 0;
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty)
+      if (ty < pt && !((r[ty] >> pl) & 1u)) km |= 1u << ty;
+    const int bytes = pl < keep ? ((__popc(km) * n + 15) & ~15) : 0;
+    int end = bytes;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, end, o);
+      if (lane >= o) end += y;
+    }
+    if (pl < keep) {
+      int32_t o = end - bytes;
+#pragma unroll
+      for (int ty = 0; ty < 3; ++ty) {
+        const bool kept = (km >> ty) & 1u;
+        po[blk][pl][ty] = kept ? o : -1;
+        if (kept) o += n;
+      }
+    }
+  }
 }
 
 // Quantise + area-ordered pack of the loop units [u0, u1) of the block table
