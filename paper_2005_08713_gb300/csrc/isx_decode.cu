@@ -198,39 +198,47 @@ __global__ void k_dec_tables(const BlockDev* __restrict__ blocks, int64_t nb, co
       const int t = (int)in.get(5);
       ok = t >= 1 && T.wbits >= 1;
       for (int pl = 0; ok && pl < d; ++pl) T.seglen[pl] = in.get(t);
-      // preorder tree: 0 = internal node, 1 + 8 bits = leaf; codes grow as we descend
-      int stack[34], filled[34];
-      uint32_t scode[34];
-      int sp = 0, nn = 0;
+      // Preorder tree: 0 = internal node (its left subtree, then its right
+      // subtree, follow), 1 + 8 bits = leaf.  The walk keeps the current
+      // node's code and depth only: a left child is the node read right after
+      // its parent (kid0 = parent + 1); after a leaf the walk climbs while
+      // the node is a right child (odd code) and moves to the sibling.  The
+      // internal node entered at each depth is remembered to receive its
+      // right child's index (kid1).
+      int path[33];
+      uint32_t code = 0;
+      int dep = 0, nn = 0;
       while (ok) {
         if (nn >= 511 || in.pos >= nbits) { ok = false; break; }
         const int v = nn++;
-        uint32_t code = 0;
-        int dep = 0;
-        if (sp > 0) {
-          const int side = filled[sp - 1]++;
-          const int par = stack[sp - 1];
-          if (side == 0) T.node[par] = (uint32_t)v;
-          else T.node[par] |= (uint32_t)v << 16;
-          code = (scode[sp - 1] << 1) | (uint32_t)side;
-          dep = sp;
-        }
+        if (dep > 0 && (code & 1u)) T.node[path[dep - 1]] |= (uint32_t)v << 16;
         if (in.get(1)) {
           const uint32_t sym = in.get(8);
           T.node[v] = 0x80000000u | sym;
           if (dep <= kTabBits) {
             const uint32_t lo = code << (kTabBits - dep), cnt = 1u << (kTabBits - dep);
-            for (uint32_t k = 0; k < cnt; ++k) T.tab[lo + k] = (uint16_t)((dep << 8) | sym);
+            const uint32_t e = ((uint32_t)dep << 8) | sym;
+            if (cnt >= 8) {   // whole 8-entry groups, 16-byte aligned
+              const uint32_t e2 = e | (e << 16);
+              uint4* t4 = reinterpret_cast<uint4*>(T.tab + lo);
+              for (uint32_t k = 0; k < (cnt >> 3); ++k) t4[k] = make_uint4(e2, e2, e2, e2);
+            } else {
+              for (uint32_t k = 0; k < cnt; ++k) T.tab[lo + k] = (uint16_t)e;
+            }
           }
-          while (sp > 0 && filled[sp - 1] == 2) --sp;
-          if (sp == 0) break;
+          while (dep > 0 && (code & 1u)) {
+            code >>= 1;
+            --dep;
+          }
+          if (dep == 0) break;   // back at the root: the tree is complete
+          code |= 1u;            // the right sibling
         } else {
-          if (sp >= 32) { ok = false; break; }   // codes longer than 32 bits
+          if (dep >= 32) { ok = false; break; }   // codes longer than 32 bits
           if (dep == kTabBits) T.tab[code] = (uint16_t)(0x8000 | v);
-          stack[sp] = v;
-          filled[sp] = 0;
-          scode[sp] = code;
-          ++sp;
+          T.node[v] = (uint32_t)(v + 1);   // kid0; kid1 is set when the right child starts
+          path[dep] = v;
+          code <<= 1;
+          ++dep;
         }
       }
       if (ok) {

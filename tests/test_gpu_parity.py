@@ -295,3 +295,46 @@ def test_repeated_encodes_are_identical(codec, orc, synth):
     for rep in range(6):
         streams, _, _, _ = gpu_encode(codec, imgs, 8, 8, CONFIG3_Q, origins=[(i * 256, 0) for i in range(len(imgs))])
         assert_streams_equal(streams, refs, f"repeat {rep}")
+
+
+def _longest_code_bits(stream: bytes, w: int, h: int, channels: int, levels: int) -> int:
+    """Longest Huffman code of any block of a tile stream, read with the independent block parser
+    (block order: per channel the LL band, then levels L .. 1, 128 x 128 cells in raster order)."""
+    from blockparse import parse_block
+    from gpu_helpers import split_blocks
+
+    def ld(n, l):
+        return -(-n // (1 << l))
+
+    _, blocks = split_blocks(stream)
+    geo = []
+    for _c in range(channels):
+        for p, l in [(1, levels)] + [(3, l) for l in range(levels, 0, -1)]:
+            gw, gh = ld(w, l), ld(h, l)
+            for cy in range(0, gh, 128):
+                for cx in range(0, gw, 128):
+                    geo.append((p, -(-min(128, gw - cx) // 4) * 4, -(-min(128, gh - cy) // 4) * 4))
+    assert len(geo) == len(blocks)
+    best = 0
+    for data, (p, bw, bh) in zip(blocks, geo):
+        pb = parse_block(data, p, bw, bh)
+        if pb.get("codes"):
+            best = max(best, max(len(k) for k in pb["codes"]))
+    return best
+
+
+def test_codes_longer_than_the_lookup_table(codec, orc):
+    # 12-bit samples with a geometric value distribution: skewed symbol counts
+    # give some blocks codes of 10-11 bits, which the segment decoder resolves
+    # by walking the tree past its 9-bit lookup table
+    rng = np.random.default_rng(2024)
+    imgs = []
+    for k in range(3):
+        g = rng.geometric(0.35, size=(128, 128)) - 1
+        imgs.append(np.minimum(g * (1 + k), 4095).astype(np.uint16))
+    refs = [orc.encode_tile(a, 1, 12) for a in imgs]
+    assert max(_longest_code_bits(r, 128, 128, 1, 1) for r in refs) > 9, "inputs no longer produce long codes"
+    streams, tiles, out, offs = gpu_encode(codec, imgs, 1, 12)
+    assert_streams_equal(streams, refs, "long-code tiles")
+    for i, a in enumerate(imgs):
+        assert np.array_equal(gpu_decode_tile(codec, out, offs, tiles, i), a), i
