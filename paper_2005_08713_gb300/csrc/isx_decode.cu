@@ -141,8 +141,9 @@ struct BitIn {
 
 __device__ inline uint32_t kept_mask(const uint32_t* removed, int p, int pl) {
   uint32_t km = 0;
-  for (int t = 0; t < p; ++t)
-    if (!((removed[t] >> pl) & 1u)) km |= 1u << t;
+#pragma unroll
+  for (int t = 0; t < 3; ++t)   // fixed trip count: removed[] stays in registers
+    if (t < p && !((removed[t] >> pl) & 1u)) km |= 1u << t;
   return km;
 }
 
@@ -298,8 +299,10 @@ struct BitPf {
   __device__ uint4 chunk(int64_t off) const {
     if (off >= 0 && off + 16 <= nbytes) return __ldg(reinterpret_cast<const uint4*>(p + off));
     uint32_t w[4];
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint32_t v = 0;
+#pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int64_t o = off + 4 * q + k;
         v |= (uint32_t)(o >= 0 && o < nbytes ? p[o] : 0) << (8 * k);

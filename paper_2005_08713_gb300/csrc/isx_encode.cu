@@ -48,8 +48,9 @@ struct CoefRef {
 
 __device__ inline uint32_t kept_types(const uint32_t* removed, int p, int pl) {
   uint32_t km = 0;
-  for (int t = 0; t < p; ++t)
-    if (!((removed[t] >> pl) & 1u)) km |= 1u << t;
+#pragma unroll
+  for (int t = 0; t < 3; ++t)   // fixed trip count: removed[] stays in registers
+    if (t < p && !((removed[t] >> pl) & 1u)) km |= 1u << t;
   return km;
 }
 
@@ -197,6 +198,7 @@ __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict_
   const uint32_t all_or = s_or[0] | s_or[1] | s_or[2];
   const int d = 1 + (all_or ? bitlen_u32(all_or) : 0);
   uint32_t removed[3];
+#pragma unroll
   for (int t = 0; t < 3; ++t) {
     uint32_t r = 0;
     for (int pl = 0; pl < d; ++pl) {
