@@ -461,6 +461,7 @@ int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, co
   db.tables = base + D.o_tab; db.bucket = (int64_t*)(base + D.o_bucket); db.items = (int64_t*)(base + D.o_items);
   db.max_items = D.max_items;
   db.perm = (int64_t*)(base + D.o_perm); db.item_cnt = (int64_t*)(base + D.o_icnt); db.item_base = (int64_t*)(base + D.o_ibase);
+  db.global_rebuild = D.n_fused < D.nsel;
   int L = launch_decode_blocks(db, s, T);
   T->mark("decode.inverse_transform", s);
   uint32_t* tickets = (uint32_t*)(base + D.o_tk);

@@ -633,10 +633,12 @@ int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T)
       db.blocks, db.items, db.totals + 1, db.stream, db.block_byte, db.block_len, db.info, reinterpret_cast<const DecTab*>(db.tables),
       db.sym_off, db.sym, db.totals, db.sym_cap, db.status);
   ++L;
-  T->mark("decode.rebuild", s);
-  k_dec_rebuild<<<(unsigned)db.n_blocks, 256, 0, s>>>(db.tiles, db.blocks, db.info, db.sym_off, db.sym, db.totals, db.sym_cap, db.z,
-                                                      db.planes);
-  ++L;
+  if (db.global_rebuild) {   // fused tiles rebuild their blocks inside the fused inverse
+    T->mark("decode.rebuild", s);
+    k_dec_rebuild<<<(unsigned)db.n_blocks, 256, 0, s>>>(db.tiles, db.blocks, db.info, db.sym_off, db.sym, db.totals, db.sym_cap, db.z,
+                                                        db.planes);
+    ++L;
+  }
   return L;
 }
 

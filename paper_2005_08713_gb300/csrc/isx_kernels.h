@@ -87,6 +87,7 @@ struct DecodeBuffers {
   uint8_t* sym;              // symbol buffer
   int64_t sym_cap;           // its size: an upper bound from the tiles' bit depths
   int* status;
+  bool global_rebuild = true;   // some selected tile takes the global (non-fused) inverse
 };
 int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T);
 // Fused inverse (decode) of n_fused tiles of one size class, CTAs of
