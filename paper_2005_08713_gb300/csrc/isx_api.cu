@@ -205,6 +205,18 @@ void tile_counts(const isx_tile_desc& t, int zmin, int64_t* nb, int64_t* ncoef) 
   *ncoef = c * t.channels;
 }
 
+// Blocks of each level of a tile (level 0 = LL) and the largest block of
+// each level in area quads (4 areas of 8 coefficients), all channels.
+void level_blocks(const isx_tile_desc& t, int64_t* count, int* quads) {
+  for (int l = 0; l <= t.levels; ++l) {
+    const int gw = level_dim(t.width, l == 0 ? t.levels : l), gh = level_dim(t.height, l == 0 ? t.levels : l);
+    count[l] += (int64_t)ceil_div(gw, kCell) * ceil_div(gh, kCell) * t.channels;
+    const int p = l == 0 ? 1 : 3;
+    const int q = p * pad4(std::min(gw, kCell)) * pad4(std::min(gh, kCell)) / 32;
+    quads[l] = std::max(quads[l], q);
+  }
+}
+
 void fill_tiledev(TileDev& d, const isx_tile_desc& t) {
   std::memset(&d, 0, sizeof(d));
   d.pixels = (const uint8_t*)t.pixels;
@@ -242,6 +254,8 @@ struct EncodeLayout {
   int64_t n_blocks = 0, coef_bytes = 0, plane_total = 0, sym_bytes = 0;
   int max_levels = 0, max_dim = 1, n_fused = 0;
   FusedClass cls[ISX_SIZE_CLASSES];
+  int64_t level_blocks[16] = {};
+  int level_quads[16] = {};
   size_t o_tiles = 0, o_task = 0, o_blocks = 0, o_A = 0, o_B = 0, o_coef = 0, o_sym = 0, o_stats = 0, o_codes = 0, o_hdrs = 0;
   size_t o_is = 0, o_fp = 0, o_perm = 0, o_bucket = 0, o_part = 0, o_tot = 0, total = 0;
 };
@@ -263,6 +277,7 @@ isx_status plan_encode(const isx_tile_desc* tiles, int32_t n, bool allow_fused, 
     }
     int64_t nb, nc;
     tile_counts(t, 0, &nb, &nc);
+    level_blocks(t, E.level_blocks, E.level_quads);
     TileDev& d = h_tiles[i];
     fill_tiledev(d, t);
     d.nb = (int32_t)nb;
@@ -336,6 +351,10 @@ int launch_encode(const EncodeLayout& E, uint8_t* base, void* d_out, size_t out_
   eb.bucket = (int64_t*)(base + E.o_bucket); eb.perm = (int64_t*)(base + E.o_perm);
   eb.out = (uint8_t*)d_out; eb.out_capacity = (int64_t)out_capacity;
   eb.tile_offsets = d_tile_offsets; eb.status = d_status;
+  for (int l = 0; l < 16; ++l) {
+    eb.level_blocks[l] = E.level_blocks[l];
+    eb.level_quads[l] = E.level_quads[l];
+  }
   L += launch_encode_coding(eb, s, T);
   T->mark(nullptr, s);
   return L;

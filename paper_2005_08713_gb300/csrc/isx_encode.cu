@@ -1018,11 +1018,30 @@ int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T)
   T->mark("encode.order", s);
   L += launch_level_sort(eb.blocks, eb.n_blocks, eb.bucket, eb.perm, eb.scan_part, eb.totals + 1, s);
   T->mark("encode.symbols", s);
-  k_enc_symbols<<<nb, 256, 0, s>>>(eb.blocks, eb.perm, (const uint8_t*)eb.coef, eb.sym, eb.stats, eb.status);
+  int64_t listed = 0;
+  for (int l = 0; l < 16; ++l) listed += eb.level_blocks[l];
+  if (listed == eb.n_blocks) {
+    // one launch per level (the level sort's order): CTAs no larger than the
+    // level's blocks need (the small blocks of the coarse levels would leave
+    // most of a 256-thread CTA idle through its barriers)
+    int64_t off = 0;
+    for (int l = 0; l < 16; ++l) {
+      if (!eb.level_blocks[l]) continue;
+      int threads = 32;
+      while (threads < 256 && threads < eb.level_quads[l]) threads <<= 1;
+      k_enc_symbols<<<(unsigned)eb.level_blocks[l], threads, 0, s>>>(eb.blocks, eb.perm + off, (const uint8_t*)eb.coef, eb.sym, eb.stats,
+                                                                      eb.status);
+      off += eb.level_blocks[l];
+      ++L;
+    }
+  } else {
+    k_enc_symbols<<<nb, 256, 0, s>>>(eb.blocks, eb.perm, (const uint8_t*)eb.coef, eb.sym, eb.stats, eb.status);
+    ++L;
+  }
   T->mark("encode.huffman", s);
   k_block_huffman<<<(unsigned)((eb.n_blocks + kHuffWarps - 1) / kHuffWarps), 32 * kHuffWarps, 0, s>>>(eb.blocks, eb.perm, eb.stats,
                                                                                                     eb.codes, eb.n_blocks);
-  L += 2;
+  L += 1;
   T->mark("encode.size", s);
   const unsigned gg = (unsigned)((eb.n_blocks + kEncGroup - 1) / kEncGroup);
   BlockHdr* hdrs = reinterpret_cast<BlockHdr*>(eb.hdrs);

@@ -47,6 +47,11 @@ struct EncodeBuffers {
   int64_t out_capacity;
   uint64_t* tile_offsets;    // [n_tiles + 1]
   int* status;
+  // Blocks per level (BlockDev::level; the level sort puts them in this order)
+  // and the largest block of each level in area quads: the symbol pass then
+  // launches per level with CTAs sized to the blocks (all zero: one launch).
+  int64_t level_blocks[16] = {};
+  int level_quads[16] = {};
 };
 size_t enc_hdr_bytes();
 void encode_set_attributes();   // dynamic shared memory limits of the coding kernels (current device)
