@@ -802,13 +802,14 @@ __device__ int load_group(const int64_t* perm, int64_t nb, const BlockDev* block
   G.code = reinterpret_cast<uint32_t (*)[256]>(dyn);
   G.len = reinterpret_cast<uint8_t (*)[256]>(dyn + kEncGroup * 256 * 4);
   G.item = reinterpret_cast<uint16_t*>(dyn + kEncGroup * (256 * 4 + 256));
-  for (int j = 0; j < ng; ++j) {
+  // code and length tables of the group's blocks, all copies in flight at
+  // once: per block 64 16-byte words of codes and 16 of lengths
+  for (int idx = threadIdx.x; idx < ng * 80; idx += blockDim.x) {
+    const int j = idx / 80, q = idx - j * 80;
     const BlockCode& bc = codes[perm[g0 + j]];
     if (!bc.any_kept) continue;
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
-      G.code[j][k] = bc.code[k];
-      G.len[j][k] = bc.len[k];
-    }
+    if (q < 64) reinterpret_cast<uint4*>(G.code[j])[q] = reinterpret_cast<const uint4*>(bc.code)[q];
+    else reinterpret_cast<uint4*>(G.len[j])[q - 64] = reinterpret_cast<const uint4*>(bc.len)[q - 64];
   }
   if (threadIdx.x < 32) {
     const int j = threadIdx.x;

@@ -59,8 +59,9 @@ struct BlockStats {
   int32_t d;
 };
 
-// Per-block code (encode, pass 2).
-struct BlockCode {
+// Per-block code (encode, pass 2); 16-byte aligned so that the code and
+// length arrays copy as 16-byte words.
+struct __align__(16) BlockCode {
   uint32_t code[256];
   uint8_t len[256];
   uint32_t tree[80];        // preorder tree, MSB-first bit string (<= 2559 bits)
