@@ -435,13 +435,51 @@ __device__ int huff_build_warp(HuffWarp& H, int track, int* depth) {
     const uint32_t fr = H.f[sym];
     k[r] = fr ? ((fr << 8) | (uint32_t)sym) : kInf;
   }
-  warp_bitonic_256(k);
-  int cnt = 0, where = -1;
+  // symbols with a nonzero count
+  int present = 0;
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    H.leaf[lane * 8 + r] = k[r];
-    cnt += k[r] != kInf;
-    if (k[r] != kInf && (int)(k[r] & 0xffu) == track) where = lane * 8 + r;
+  for (int r = 0; r < 8; ++r) present += __popc(__ballot_sync(0xffffffffu, k[r] != kInf));
+  if (present <= 32) {
+    // small alphabet (the coarse levels' blocks): gather the keys, one per
+    // lane, and sort 32 instead of 256
+    int base = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint32_t m = __ballot_sync(0xffffffffu, k[r] != kInf);
+      if (k[r] != kInf) H.leaf[base + __popc(m & ((1u << lane) - 1u))] = k[r];
+      base += __popc(m);
+    }
+    __syncwarp();
+    uint32_t x = lane < present ? H.leaf[lane] : kInf;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, x, stride);
+        const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
+        x = (lower == up) ? min(x, other) : max(x, other);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) k[r] = kInf;
+    k[0] = x;   // key of rank `lane` (lanes >= present: none)
+    H.leaf[lane] = x;
+  } else {
+    warp_bitonic_256(k);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) H.leaf[lane * 8 + r] = k[r];
+  }
+  int cnt = 0, where = -1;
+  if (present <= 32) {
+    cnt = lane == 0 ? present : 0;
+    if (k[0] != kInf && (int)(k[0] & 0xffu) == track) where = lane;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      cnt += k[r] != kInf;
+      if (k[r] != kInf && (int)(k[r] & 0xffu) == track) where = lane * 8 + r;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
