@@ -78,7 +78,10 @@ __device__ inline uint32_t warp_carry_exclusive(uint32_t v, uint32_t* inclusive_
 struct LaneSyms {
   uint32_t w[4];
   int cnt;
-  __device__ uint32_t at(int k) const { return (w[k >> 2] >> (8 * (k & 3))) & 0xffu; }
+  __device__ uint32_t at(int k) const {   // selects, not an indexed array: w[] stays in registers
+    const uint32_t lo = (k & 4) ? w[1] : w[0], hi = (k & 4) ? w[3] : w[2];
+    return (((k & 8) ? hi : lo) >> (8 * (k & 3))) & 0xffu;
+  }
 };
 
 __device__ inline LaneSyms load_lane(const uint8_t* seg, int len, int base) {
