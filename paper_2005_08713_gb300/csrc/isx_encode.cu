@@ -820,7 +820,7 @@ __device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct,
 }
 
 constexpr int kEmitWarps = 8;
-constexpr int kEncGroup = 32;
+constexpr int kEncGroup = 16;
 constexpr int kEncSmem = kEncGroup * (256 * 4 + 256) + kEncGroup * 32 * 2;
 
 __device__ inline int64_t block_bit_start(const TileDev& t, const int64_t* final_pos, int64_t bi) {
