@@ -106,10 +106,10 @@ class ClockSampler:
 # (first 16 hex digits of the sha256 of their contents in order); otherwise the bench reports traffic as null.
 NCU_TRAFFIC = {
     "encode.transform": ("k_fwd_tile_smem", ("isx_transform.cu", "isx_warp_levels.cuh", "isx_internal.cuh"), "65d38685fb5e6aa5", 8.179),
-    "encode.symbols": ("k_enc_symbols", ("isx_encode.cu", "isx_internal.cuh"), "2756c98cbde7fb9f", 7.347),
-    "encode.huffman": ("k_block_huffman", ("isx_encode.cu", "isx_internal.cuh"), "2756c98cbde7fb9f", 0.510),
-    "encode.size": ("k_enc_size", ("isx_encode.cu", "isx_internal.cuh"), "2756c98cbde7fb9f", 2.365),
-    "encode.emit": ("k_enc_emit", ("isx_encode.cu", "isx_internal.cuh"), "2756c98cbde7fb9f", 3.807),
+    "encode.symbols": ("k_enc_symbols", ("isx_encode.cu", "isx_internal.cuh"), "1165ba547f3ff870", 7.404),
+    "encode.huffman": ("k_block_huffman", ("isx_encode.cu", "isx_internal.cuh"), "1165ba547f3ff870", 0.513),
+    "encode.size": ("k_enc_size", ("isx_encode.cu", "isx_internal.cuh"), "1165ba547f3ff870", 2.360),
+    "encode.emit": ("k_enc_emit", ("isx_encode.cu", "isx_internal.cuh"), "1165ba547f3ff870", 3.822),
     "decode.tables": ("k_dec_tables", ("isx_decode.cu", "isx_internal.cuh"), "4d283b7b52238491", 0.403),
     "decode.segments": ("k_dec_segments", ("isx_decode.cu", "isx_internal.cuh"), "4d283b7b52238491", 2.433),
     "decode.inverse_transform": ("k_inv_tile_smem", ("isx_transform.cu", "isx_warp_levels.cuh", "isx_internal.cuh"), "65d38685fb5e6aa5", 9.808),
@@ -120,8 +120,8 @@ NCU_TRAFFIC = {
 # for the issue-rate co-roofline: the codec is integer work, and its kernels are bound by latency and
 # instruction issue long before DRAM bandwidth.
 NCU_WARP_INST_PER_PX = {
-    "encode.transform": 6.110, "encode.symbols": 5.264, "encode.huffman": 6.270, "encode.size": 3.162,
-    "encode.emit": 7.544, "decode.tables": 1.164, "decode.segments": 8.980, "decode.inverse_transform": 7.060,
+    "encode.transform": 6.110, "encode.symbols": 4.878, "encode.huffman": 6.270, "encode.size": 2.777,
+    "encode.emit": 7.561, "decode.tables": 1.164, "decode.segments": 8.980, "decode.inverse_transform": 7.060,
 }
 
 
