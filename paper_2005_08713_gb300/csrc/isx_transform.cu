@@ -617,12 +617,7 @@ __shared__ int32_t s_wl_scratch[32 * kWlPitch];
 // `split` runs per line, leaving at least half of the warps to the blocks
 // (0: no overlap).  Measured per phase: two runs per line shorten the
 // encode's lifting; the decode's lifting is fastest on one run per line.
-#ifndef ISX_OVERLAP_SPLIT_FWD
-#define ISX_OVERLAP_SPLIT_FWD 2
-#endif
-#ifndef ISX_OVERLAP_SPLIT_INV
-#define ISX_OVERLAP_SPLIT_INV 1
-#endif
+constexpr int kOverlapSplitFwd = 2, kOverlapSplitInv = 1;
 // Warps that pack (encode) or rebuild (decode) the finest level's blocks
 // meanwhile, at most: the lifting warps are the critical path, and every
 // further block warp takes issue slots and shared-memory bandwidth from
@@ -1001,7 +996,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   // After level 0 the level-1 blocks (3/4 of the coefficients) are final and
   // at most half of the lines are left to lift: the first W warps lift levels
   // 1.. while the others build the block table and pack the level-1 blocks.
-  const int W = t.L >= 2 && level_dim(w, 0) > kWarpGrid ? overlap_warps(level_dim(w, 1), level_dim(h, 1), nwarps, ISX_OVERLAP_SPLIT_FWD) : 0;
+  const int W = t.L >= 2 && level_dim(w, 0) > kWarpGrid ? overlap_warps(level_dim(w, 1), level_dim(h, 1), nwarps, kOverlapSplitFwd) : 0;
   if (W == 0) {
     transform_fwd_levels(P, pitch, w, h, t.L);
     if (threadIdx.x < 32) fused_block_table(t, blocks, nullptr, nullptr, t.block_base + (int64_t)c * nbc, nbc, 0, s_fb, nullptr);
@@ -1347,7 +1342,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
   while (kf > 0 && s_fb[kf - 1].level == z + 1) --kf;
   const int uF = kf ? s_fb[kf - 1].end : 0;
   const int W = t.L - 1 >= z + 1 && kf < nbc && level_dim(t.w, z) > kWarpGrid
-                    ? overlap_warps(level_dim(t.w, z + 1), level_dim(t.h, z + 1), nwarps, ISX_OVERLAP_SPLIT_INV)
+                    ? overlap_warps(level_dim(t.w, z + 1), level_dim(t.h, z + 1), nwarps, kOverlapSplitInv)
                     : 0;
   if (W == 0) {
     rebuild_units(s_fb, s_po, sym, 0, total, threadIdx.x, blockDim.x, P, pitch);

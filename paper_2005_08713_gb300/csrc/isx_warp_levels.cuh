@@ -1,9 +1,9 @@
-// isx_warp_levels.cuh — the coarse levels of the fused 5/3 transforms on one
-// warp, in registers.
+// isx_warp_levels.cuh — the coarse levels of the fused forward 5/3
+// transform on one warp, in registers.
 //
 // Once a level's grid is at most 32 x 32 samples (levels 3 .. L-1 of a
 // 256 x 256 tile) the CTA has too few lines to share out, so the first warp
-// finishes the transform alone while the other warps pack or rebuild blocks.
+// finishes the transform alone while the other warps pack the blocks.
 // Lifting those levels in place in the shared-memory plane costs a
 // shared-memory round trip per sample and pass, at strides of 8 .. 128
 // samples (4- to 16-way bank conflicts), queued behind the other warps'
@@ -13,12 +13,12 @@
 // for the other direction, and writes each level's detail samples (the ones
 // with an odd row or column index, Sec. 3's subbands) to the plane once.
 //
-// Forward level (Eq. of the 5/3 lifting: predict, then update, with the
-// same whole-sample symmetric extension as the line sweeps): columns, then
-// rows; the low band (even row and column) is compacted into the next
-// level's columns through the scratch.  Inverse level: rows, then columns;
-// the result is expanded into the next finer grid together with that
-// level's detail samples read from the plane.
+// A level (the 5/3 lifting: predict, then update, with the same
+// whole-sample symmetric extension as the line sweeps): columns, then rows;
+// the low band (even row and column) is compacted into the next level's
+// columns through the scratch.  (The inverse was built the same way and
+// measured slower inside the decode kernel, whose coarse levels stay
+// in-place line sweeps.)
 //
 // The functions are written for one full warp (all 32 lanes call them);
 // ISX_WL_FN, ISX_WL_SYNC and ISX_WL_MIN let the same source run lane by lane
@@ -53,24 +53,6 @@ ISX_WL_FN void reg_lift_fwd(int32_t (&v)[32], int n) {
     const int32_t dr = (2 * k + 1 < n) ? v[ISX_WL_MIN(2 * k + 1, N - 1)] : dl;
     const int32_t s = v[2 * k] + ((dl + dr + 2) >> 2);
     v[2 * k] = (2 * k < n) ? s : v[2 * k];
-  }
-}
-
-// Inverse of reg_lift_fwd: undo the update, then the prediction.
-template <int N>
-ISX_WL_FN void reg_lift_inv(int32_t (&v)[32], int n) {
-#pragma unroll
-  for (int k = 0; 2 * k < N; ++k) {
-    const int32_t dl = k > 0 ? v[2 * k - 1] : v[1];
-    const int32_t dr = (2 * k + 1 < n) ? v[ISX_WL_MIN(2 * k + 1, N - 1)] : dl;
-    const int32_t e = v[2 * k] - ((dl + dr + 2) >> 2);
-    v[2 * k] = (2 * k < n) ? e : v[2 * k];
-  }
-#pragma unroll
-  for (int k = 0; 2 * k + 1 < N; ++k) {
-    const int32_t right = (2 * k + 2 < n) ? v[ISX_WL_MIN(2 * k + 2, N - 1)] : v[2 * k];
-    const int32_t x = v[2 * k + 1] + ((v[2 * k] + right) >> 1);
-    v[2 * k + 1] = (2 * k + 1 < n) ? x : v[2 * k + 1];
   }
 }
 
@@ -152,77 +134,6 @@ ISX_WL_FN void warp_levels_fwd(int16_t* P, int pitch, int w, int h, int l0, int 
     for (int r = 0; r < 16; ++r)
       if (r < ch) P[(r * s) * pitch + lane * s] = (int16_t)v[r];
   }
-}
-
-// Inverse level m = lw + R (grid cw x ch <= N = 32 >> R a side, samples `s`
-// apart): v holds the rows on entry.  For R > 0 the result is expanded into
-// the level m-1 grid (cw2 x ch2, samples s2 apart), rows again, its odd rows
-// and columns read from the plane; for R = 0 it is stored to the plane.
-template <int R>
-ISX_WL_FN void wl_inv_level(int32_t (&v)[32], int16_t* P, int pitch, int32_t* T, int lane, int s, int cw, int ch, int s2, int cw2,
-                            int ch2) {
-  constexpr int N = 32 >> R;
-  if (cw >= 2) reg_lift_inv<N>(v, cw);   // rows (lane r: row r)
-  reg_transpose<N>(v, T, lane);
-  if (ch >= 2) reg_lift_inv<N>(v, ch);   // columns (lane c: column c)
-  if (R == 0) {
-    if (lane < cw) {
-#pragma unroll
-      for (int r = 0; r < N; ++r)
-        if (r < ch) P[(r * s) * pitch + lane * s] = (int16_t)v[r];
-    }
-    return;
-  }
-  constexpr int N2 = 2 * N <= 32 ? 2 * N : 32;
-  if (lane < N) {
-#pragma unroll
-    for (int r = 0; r < N; ++r) T[lane * kWlPitch + r] = v[r];   // T[c][r] = sample (r, c)
-  }
-  ISX_WL_SYNC();
-  if (lane < N2) {
-    const int rc = ISX_WL_MIN(lane, ch2 - 1);   // rows past the grid read a valid sample, never stored
-    const int16_t* row = P + (rc * s2) * pitch;
-    const bool even_row = !(lane & 1);
-#pragma unroll
-    for (int c = 0; c < N2; ++c) {
-      const int32_t fromP = row[ISX_WL_MIN(c, cw2 - 1) * s2];
-      if (c & 1) {
-        v[c] = fromP;
-      } else {
-        const int32_t fromT = T[(c >> 1) * kWlPitch + (lane >> 1)];
-        v[c] = even_row ? fromT : fromP;
-      }
-    }
-  }
-  ISX_WL_SYNC();
-}
-
-// Inverse levels L-1 .. lw (the plane's LL being level z), level lw's grid
-// being at most 32 x 32: levels above lw + 4 have one-sample grids and are
-// the identity.
-ISX_WL_FN void warp_levels_inv(int16_t* P, int pitch, int w, int h, int lw, int L, int z, int32_t* T, int lane) {
-  const int top = ISX_WL_MIN(L - 1 - lw, 4);   // R of the coarsest level that changes anything
-  if (top < 0) return;
-  int32_t v[32];
-  {
-    const int m = lw + top, s = 1 << (m - z);
-    const int cw = level_dim(w, m), ch = level_dim(h, m);
-    const int16_t* row = P + (ISX_WL_MIN(lane, ch - 1) * s) * pitch;   // rows: lane r holds row r
-#pragma unroll
-    for (int c = 0; c < 32; ++c) v[c] = row[ISX_WL_MIN(c, cw - 1) * s];
-  }
-#define ISX_WL_INV_STEP(R)                                                                                          \
-  if (top >= R) {                                                                                                   \
-    const int m = lw + R;                                                                                           \
-    wl_inv_level<R>(v, P, pitch, T, lane, 1 << (m - z), level_dim(w, m), level_dim(h, m), (1 << (m - z)) >> 1,     \
-                    R > 0 ? level_dim(w, m - 1) : 0, R > 0 ? level_dim(h, m - 1) : 0);                              \
-  }
-  ISX_WL_INV_STEP(4)
-  ISX_WL_INV_STEP(3)
-  ISX_WL_INV_STEP(2)
-  ISX_WL_INV_STEP(1)
-  ISX_WL_INV_STEP(0)
-#undef ISX_WL_INV_STEP
 }
 
 }  // namespace isx
