@@ -567,12 +567,23 @@ __global__ void __launch_bounds__(32 * kHuffWarps, 4) k_block_huffman(const Bloc
   // provisional code: every run counts once for C_zr; l = C_zr's code length
   if (lane == 0) H.f[czr] = lit_czr + st.n_runs;
   __syncwarp();
+  // The provisional tree is built with its parent links: when the chosen
+  // width needs no extra run tokens, the final counts equal these and the
+  // tree is reused as is.
+  int root = huff_build_warp<true>(H, -1, nullptr);
   int l = 0;
-  {
-    __shared__ int s_depth[kHuffWarps];
-    huff_build_warp<false>(H, czr, &s_depth[wid]);
-    __syncwarp();
-    l = H.f[czr] > 0 && H.nl > 1 ? s_depth[wid] : 0;
+  if (H.f[czr] > 0 && H.nl > 1) {
+    int leaf = -1;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int i = lane + 32 * m;
+      if (i < H.nl && (int)(H.leaf[i] & 0xffu) == czr) leaf = i;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) leaf = max(leaf, __shfl_xor_sync(0xffffffffu, leaf, o));
+    int dep = 0;
+    for (int v = leaf; v != root && dep < 64; ++dep) v = H.parent[v] & 0x7fff;   // the leaf's depth
+    l = dep;
   }
   // Eq. 3 (reading): w minimises (w + l) * (#C_zr tokens at width w) over [2, b]
   int bmax = n_sym > 1 ? bitlen_u32(n_sym - 1) : 0;
@@ -584,10 +595,12 @@ __global__ void __launch_bounds__(32 * kHuffWarps, 4) k_block_huffman(const Bloc
     const uint64_t cost = (uint64_t)(w + l) * pairs;
     if (cost < bestc) { bestc = cost; wbest = w; }
   }
-  __syncwarp();
-  if (lane == 0) H.f[czr] = lit_czr + st.n_runs + st.extra[wbest];
-  __syncwarp();
-  const int root = huff_build_warp<true>(H, -1, nullptr);
+  if (st.extra[wbest] != 0) {   // C_zr's count changes: build the final tree
+    __syncwarp();
+    if (lane == 0) H.f[czr] = lit_czr + st.n_runs + st.extra[wbest];
+    __syncwarp();
+    root = huff_build_warp<true>(H, -1, nullptr);
+  }
   const int nl = H.nl;
   // codes: every leaf walks up to the root; a lane walks its (up to) 8 leaves together
   for (int s2 = lane; s2 < 256; s2 += 32) { bc.code[s2] = 0; bc.len[s2] = 0; }
