@@ -719,10 +719,12 @@ struct FusedBlock {
   int4 geo[3];                 // per type: valid width, valid height, interleaved row and column of sample (0, 0)
 };
 
-// Warp 0 fills fb[0 .. nbc) from blocks[b0 ..] for a plane whose LL is level
-// z0; decode passes its DecInfo (else nullptr).  Blocks a decode could not
-// read (p = 0 or d = 0; status already set) get no areas.  The caller
-// synchronises the CTA before use.
+// One warp fills fb[0 .. nbc) from blocks[b0 ..] for a plane whose LL is
+// level z0 (lane i: block i); decode passes its DecInfo (else nullptr) and
+// gets the symbol offset of every kept (plane, type) in po (a warp scan over
+// the planes per block).  Blocks a decode could not read (p = 0 or d = 0;
+// status already set) get no units.  The caller synchronises the CTA
+// before use.
 __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __restrict__ blocks, const DecInfo* __restrict__ info,
                                          const int64_t* __restrict__ sym_off, int64_t b0, int nbc, int z0, FusedBlock* fb,
                                          int32_t (*po)[kMaxFusedPlanes][3]) {
@@ -807,8 +809,6 @@ __device__ inline void fused_block_table(const TileDev& t, const BlockDev* __res
   }
 }
 
-// Quantise + area-ordered pack of the loop units [u0, u1) of the block table
-// (one area each), by threads tid = first .. of n.
 // Rotates eight int16 held in pairs (w[k] = slots 2k, 2k+1) so that slot t
 // takes slot (t + rot) & 7.
 __device__ __forceinline__ void rotate8x16(const uint32_t (&w)[4], int rot, uint32_t (&o)[4]) {
@@ -881,6 +881,9 @@ __device__ inline void pack_quad(const FusedBlock& f, const AreaMap& am, int a0,
   }
 }
 
+// Quantise + area-ordered pack of the loop units [u0, u1) of the block table
+// (an area quad where the block's type rows hold a multiple of 4 areas, else
+// one area), by threads tid = first .. of n.
 __device__ inline void pack_units(const FusedBlock* s_fb, int u0, int u1, int tid, int n, const int16_t* P, int pitch,
                                   uint8_t* __restrict__ coef) {
   int blk = 0;
