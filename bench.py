@@ -102,17 +102,17 @@ class ClockSampler:
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per pixel of each stage's kernel, from one
 # ncu --set full capture of the 8192 x 8192 case of this workload (profiles/kernels_slide_8192x8192_lossy.md),
-# scaled to a full launch by pixels.  Valid only while the kernel's source files are the ones captured
-# (first 16 hex digits of the sha256 of their contents in order); otherwise the bench reports traffic as null.
+# scaled to a full launch by pixels.  Valid only while the code of the kernel's source files is the one
+# captured (source_digest: comments and whitespace aside); otherwise the bench reports traffic as null.
 NCU_TRAFFIC = {
-    "encode.transform": ("k_fwd_tile_smem", ("isx_transform.cu", "isx_warp_levels.cuh", "isx_internal.cuh"), "e0f9edba69ec00f7", 8.179),
+    "encode.transform": ("k_fwd_tile_smem", ("isx_transform.cu", "isx_warp_levels.cuh", "isx_internal.cuh"), "5822ca7b8c98d403", 8.179),
     "encode.symbols": ("k_enc_symbols", ("isx_encode.cu", "isx_internal.cuh"), "1165ba547f3ff870", 7.404),
     "encode.huffman": ("k_block_huffman", ("isx_encode.cu", "isx_internal.cuh"), "1165ba547f3ff870", 0.513),
     "encode.size": ("k_enc_size", ("isx_encode.cu", "isx_internal.cuh"), "1165ba547f3ff870", 2.360),
     "encode.emit": ("k_enc_emit", ("isx_encode.cu", "isx_internal.cuh"), "1165ba547f3ff870", 3.822),
-    "decode.tables": ("k_dec_tables", ("isx_decode.cu", "isx_internal.cuh"), "4d283b7b52238491", 0.403),
-    "decode.segments": ("k_dec_segments", ("isx_decode.cu", "isx_internal.cuh"), "4d283b7b52238491", 2.433),
-    "decode.inverse_transform": ("k_inv_tile_smem", ("isx_transform.cu", "isx_warp_levels.cuh", "isx_internal.cuh"), "e0f9edba69ec00f7", 9.808),
+    "decode.tables": ("k_dec_tables", ("isx_decode.cu", "isx_internal.cuh"), "6bcd2f7f03c53525", 0.403),
+    "decode.segments": ("k_dec_segments", ("isx_decode.cu", "isx_internal.cuh"), "6bcd2f7f03c53525", 2.433),
+    "decode.inverse_transform": ("k_inv_tile_smem", ("isx_transform.cu", "isx_warp_levels.cuh", "isx_internal.cuh"), "5822ca7b8c98d403", 9.808),
 }
 
 
@@ -136,20 +136,30 @@ def issue_roofline(stage, px, ms):
     return per_px, sms
 
 
-def traffic_bytes(stage, px):
+def source_digest(names):
+    """First 16 hex digits of the sha256 of the code of the named csrc files, comments and whitespace removed
+    (an edit of a comment does not change the kernels the counters were taken on)."""
     import hashlib
+    import re
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2005_08713_gb300", "csrc", name)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
+    return h.hexdigest()[:16]
+
+
+def traffic_bytes(stage, px):
     ent = NCU_TRAFFIC.get(stage)
     if not ent:
         return None
     names = ent[1] if isinstance(ent[1], tuple) else (ent[1],)
-    h = hashlib.sha256()
     try:
-        for name in names:
-            with open(os.path.join(ROOT, "paper_2005_08713_gb300", "csrc", name), "rb") as f:
-                h.update(f.read())
+        digest = source_digest(names)
     except OSError:
         return None
-    digest = h.hexdigest()[:16]
     return int(ent[3] * px) if digest == ent[2] else None
 
 
