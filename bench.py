@@ -216,10 +216,34 @@ def make_slide(seed):
     return h_img
 
 
+def replica_seed(rank):
+    """Each replica encodes its own slide: the workload's seed offset by the rank."""
+    from paper_2005_08713_gb300 import synth
+    return synth.config_seed(3) + rank
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest replica's timed region (ms): a MAX reduction over the ranks."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_throughput(ms_total, steps, world, mp_per_replica):
+    """(ms per step, whole-job MP/s): every replica's pixels over the slowest
+    replica's time (weak scaling, one slide per GPU)."""
+    ms_step = ms_total / steps
+    return ms_step, world * mp_per_replica / (ms_step / 1e3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
-    from paper_2005_08713_gb300 import isx, synth
+    from paper_2005_08713_gb300 import isx
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -233,8 +257,7 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    seed = synth.config_seed(3) + rank
-    h_img = make_slide(seed)
+    h_img = make_slide(replica_seed(rank))
     mp = IMG_W * IMG_H / 1e6
     d_img = h_img.to(dev, non_blocking=False)
     grid = tile_grid()
@@ -298,12 +321,8 @@ def run_gpu(args):
     ms = t0.elapsed_time(t1)
     stages = codec.stage_times()
     codec.set_timing(False)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    ms_step = ms / args.steps
-    value = world * mp / (ms_step / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    ms_step, value = replica_throughput(ms, args.steps, world, mp)
 
     # exactness on the bench's own launch: decoded tiles equal the oracle's, sampled
     exact = None
