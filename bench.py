@@ -631,6 +631,52 @@ def run_serve(args, dev, pyramids):
     return out
 
 
+def host_cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or the machine type."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_single_core():
+    """One host core running the oracle on the two single-image workloads:
+    the 512 x 512 RGB8 stain tile (3 levels, lossless) and the 2048 x 2048
+    12-bit phantom (5 levels, lossless); encode and decode ms, best of 3."""
+    import oracle
+    from paper_2005_08713_gb300 import synth
+    cases = {"stain_512x512_rgb8_L3_lossless": (synth.stain(synth.config_seed(1)), 3, 8),
+             "phantom_2048x2048_u12_L5_lossless": (synth.phantom(synth.config_seed(2), 2048, 2048), 5, 12)}
+    out = {}
+    for name, (img, levels, bits) in cases.items():
+        enc, dec = [], []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            s = oracle.encode_tile(img, levels, bits, [0] * (levels + 1))
+            t1 = time.perf_counter()
+            back = oracle.decode_tile(s)
+            t2 = time.perf_counter()
+            enc.append(t1 - t0)
+            dec.append(t2 - t1)
+        if not np.array_equal(back, img):
+            raise RuntimeError(f"oracle round trip of {name} is not lossless")
+        out[name] = {"encode_ms": round(min(enc) * 1e3, 1), "decode_ms": round(min(dec) * 1e3, 1),
+                     "mp": round(img.shape[0] * img.shape[1] / 1e6, 3), "bytes": len(s)}
+    return out
+
+
 def cpu_baseline(img, grid, q, n_tiles):
     """The oracle as it stands, all host cores, on a bounded sample of the workload's tiles."""
     import oracle
@@ -648,7 +694,8 @@ def cpu_baseline(img, grid, q, n_tiles):
     t2 = time.perf_counter()
     return {"value": round(mp / (t2 - t0), 2), "unit": "MP/s", "cores": cores, "kind": "oracle",
             "encode_mps": round(mp / (t1 - t0), 2), "decode_mps": round(mp / (t2 - t1), 2),
-            "sample": f"{len(imgs)} random 256x256 tiles of the same slide ({mp:.1f} MP), encode+decode, thread pool over tiles"}
+            "sample": f"{len(imgs)} random 256x256 tiles of the same slide ({mp:.1f} MP), encode+decode, thread pool over tiles",
+            "cpu_model": host_cpu_model(), "single_core": oracle_single_core()}
 
 
 def run_reference(args):
@@ -687,7 +734,8 @@ def run_reference(args):
             "config": {"workload": f"slide_{IMG_W}x{IMG_H}_rgb8_tile{TILE}_L{LEVELS}_" + ("lossless" if args.lossless else "lossy_q8421"),
                        "sample_tiles": n},
             "cpu_baseline": {"value": round(value, 2), "unit": "MP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{n} random tiles of the slide per step ({mp:.1f} MP), encode+decode"},
+                             "sample": f"{n} random tiles of the slide per step ({mp:.1f} MP), encode+decode",
+                             "cpu_model": host_cpu_model()},
             "e2e": {"value": round(value, 2), "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
