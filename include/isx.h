@@ -53,7 +53,8 @@ typedef enum {
  * colorspace transformation", Fig. 1); channels = 1 codes the samples as is.
  * qstep_log2[l-1] is the quantiser step 2^q of wavelet level l (l = 1 is the
  * finest), qstep_log2[levels] the step of the LL band; all 0 = lossless.
- * x0, y0 place the tile in the image (level-0 pixels) for region decodes. */
+ * x0, y0 place the tile in the image (level-0 pixels) for region decodes.
+ * A field outside its stated range is an argument error (ISX_ERR_ARG). */
 typedef struct {
   int32_t width, height;   /* 1 .. 65535 */
   int32_t channels;        /* 1 or 3 */

@@ -183,6 +183,7 @@ bool tile_ok(const isx_tile_desc& t, std::string* why) {
   if (t.width < 1 || t.width > 65535 || t.height < 1 || t.height > 65535) { *why = "width/height out of 1..65535"; return false; }
   if (t.channels != 1 && t.channels != 3) { *why = "channels must be 1 or 3"; return false; }
   if (t.bits < 1 || t.bits > 16) { *why = "bits out of 1..16"; return false; }
+  if (t.channels == 3 && t.bits > 8) { *why = "3-channel tiles take bits 1..8"; return false; }
   if (t.levels < 0 || t.levels > kMaxLevels) { *why = "levels out of 0..15"; return false; }
   if (t.x0 < 0 || t.y0 < 0) { *why = "negative tile origin"; return false; }
   for (int l = 0; l <= t.levels; ++l)

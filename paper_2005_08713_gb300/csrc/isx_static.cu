@@ -80,6 +80,7 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
     return fail(h_err, err_len, ISX_ERR_ARG, "width/height out of 1..65535");
   if (t.channels != 1 && t.channels != 3) return fail(h_err, err_len, ISX_ERR_ARG, "channels must be 1 or 3");
   if (t.bits < 1 || t.bits > 16) return fail(h_err, err_len, ISX_ERR_ARG, "bits out of 1..16");
+  if (t.channels == 3 && t.bits > 8) return fail(h_err, err_len, ISX_ERR_ARG, "3-channel tiles take bits 1..8");
   if (t.levels < 0 || t.levels > kMaxLevels) return fail(h_err, err_len, ISX_ERR_ARG, "levels out of 0..15");
   if (t.x0 < 0 || t.y0 < 0) return fail(h_err, err_len, ISX_ERR_ARG, "negative tile origin");
   for (int l = 0; l <= t.levels; ++l)
