@@ -43,25 +43,43 @@ def interleaved_to_mallat(I: np.ndarray, levels: int) -> np.ndarray:
     return M
 
 
+SANITIZE = ["-fsanitize=address,undefined", "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer"]
+
+
 @pytest.fixture(scope="module")
 def harness(tmp_path_factory):
+    """The harness, built with the address and undefined-behaviour
+    sanitizers where the compiler has them: then every plane and scratch
+    access of the device code outside its buffer fails the run."""
     cxx = shutil.which("g++")
     if not cxx:
         pytest.skip("no C++ compiler")
     exe = str(tmp_path_factory.mktemp("wl") / "warp_levels_host")
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", os.path.join(HERE, "warp_levels_host.cpp"), "-o", exe],
-                       capture_output=True, text=True)
+    base = [cxx, "-std=c++20", "-O1", "-g", "-pthread", os.path.join(HERE, "warp_levels_host.cpp"), "-o", exe]
+    r = subprocess.run(base[:1] + SANITIZE + base[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        r = subprocess.run(base, capture_output=True, text=True)
     if r.returncode != 0:
         pytest.fail("harness build failed:\n" + r.stderr[-2000:])
     return exe
 
 
+def run_many(exe, cases):
+    """cases: [(plane, levels)] -> the harness's result plane of each."""
+    inp = []
+    for plane, levels in cases:
+        h, w = plane.shape
+        inp.append(f"{w} {h} {levels}\n" + "\n".join(" ".join(str(int(v)) for v in row) for row in plane) + "\n")
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=0")
+    r = subprocess.run([exe], input="".join(inp), capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-3000:]
+    out = r.stdout.split("--\n")
+    assert len(out) == len(cases) + 1 and out[-1] == ""
+    return [np.array([[int(v) for v in line.split()] for line in o.strip().splitlines()], dtype=np.int64) for o in out[:-1]]
+
+
 def run(exe, plane: np.ndarray, levels: int) -> np.ndarray:
-    h, w = plane.shape
-    inp = f"{w} {h} {levels}\n" + "\n".join(" ".join(str(int(v)) for v in row) for row in plane) + "\n"
-    r = subprocess.run([exe], input=inp, capture_output=True, text=True, timeout=60)
-    assert r.returncode == 0, r.stderr
-    return np.array([[int(v) for v in line.split()] for line in r.stdout.strip().splitlines()], dtype=np.int64)
+    return run_many(exe, [(plane, levels)])[0]
 
 
 @pytest.mark.parametrize("h,w,levels", [(32, 32, 5), (32, 32, 8), (1, 32, 5), (32, 1, 4), (25, 18, 3), (17, 31, 6),
@@ -73,3 +91,16 @@ def test_warp_levels_match_oracle(harness, orc, h, w, levels):
     got = interleaved_to_mallat(run(harness, plane, levels), levels)
     ref = orc.dwt2_forward(plane, levels)
     assert np.array_equal(got, ref), f"{h}x{w} L={levels}: {np.argwhere(got != ref)[:5].tolist()}"
+
+
+def test_warp_levels_every_grid_shape(harness, orc):
+    """Every grid of 1..32 x 1..32 samples at a random level count 1..7,
+    in one run of the (sanitized) harness."""
+    rng = np.random.default_rng(2024)
+    cases = []
+    for h in range(1, 33):
+        for w in range(1, 33):
+            cases.append((rng.integers(-255, 256, size=(h, w)).astype(np.int64), int(rng.integers(1, 8))))
+    for (plane, levels), got in zip(cases, run_many(harness, cases)):
+        ref = orc.dwt2_forward(plane, levels)
+        assert np.array_equal(interleaved_to_mallat(got, levels), ref), (plane.shape, levels)
