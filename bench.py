@@ -48,19 +48,25 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms from start()
+    (before the warm-up, so that sampling runs by the time the timed region
+    starts) to stop(); the summary keeps the samples whose nvidia-smi
+    timestamp falls between mark_start() and mark_end()."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, exe: str = "nvidia-smi"):
         self.dev = device_index
+        self.exe = exe
         self.proc = None
         self.lines = []
         self.thread = None
+        self.t_start = self.t_end = None
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+            self.proc = subprocess.Popen([self.exe, "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                           "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -72,6 +78,53 @@ class ClockSampler:
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
 
+    def mark_start(self):
+        self.t_start = time.time()
+
+    def mark_end(self):
+        self.t_end = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        """nvidia-smi's timestamp ("2026/12/04 03:02:11.123", local time) as epoch seconds, else None."""
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text.strip(), fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
+    def summary(self, lines):
+        rows = []
+        for ln in lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                sm, smax = float(parts[2]), float(parts[3])
+            except ValueError:
+                continue
+            active = {nm for k, nm in enumerate(self.REASONS) if parts[6 + k].lower().startswith("active")}
+            rows.append((self._stamp(parts[0]), sm, smax, active))
+        if self.t_start is not None and self.t_end is not None:
+            inside = [r for r in rows if r[0] is not None and self.t_start <= r[0] <= self.t_end]
+        else:
+            inside = []
+        # a timed region shorter than the sampling period can fall between two samples: then take the
+        # first sample after it started (the clock the region ran at, as near as nvidia-smi saw it)
+        if not inside and self.t_start is not None:
+            after = [r for r in rows if r[0] is not None and r[0] >= self.t_start]
+            inside = after[:1]
+        if not inside:
+            inside = rows
+        reasons = set()
+        for r in inside:
+            reasons |= r[3]
+        return {"sm_mhz": statistics.median([r[1] for r in inside]) if inside else None,
+                "sm_max_mhz": inside[-1][2] if inside else None, "reasons": sorted(reasons),
+                "samples": len(inside), "samples_total": len(rows)}
+
     def stop(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -82,22 +135,7 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
-            except ValueError:
-                continue
-            for k, nm in enumerate(names):
-                if parts[5 + k].lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return self.summary(list(self.lines))
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per pixel of each stage's kernel, from one
@@ -287,6 +325,9 @@ def run_gpu(args):
         raise RuntimeError(f"device status {st}")
     total_bytes = int(d_offs[-1].item())
 
+    # clocks are sampled from here on, so that nvidia-smi is running by the time the timed region starts
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -303,19 +344,19 @@ def run_gpu(args):
         enc_ms.append(ev[0].elapsed_time(ev[1]))
         dec_ms.append(ev[1].elapsed_time(ev[2]))
 
-    clocks = ClockSampler(local)
     codec.set_timing(True)
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     launches = 0
+    clocks.mark_start()
     t0.record(stream)
     for _ in range(args.steps):
         launches += step()
     t1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier()
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)

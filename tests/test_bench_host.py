@@ -39,3 +39,79 @@ def test_cpu_baseline_on_a_small_slide():
     assert r["value"] > 0 and r["encode_mps"] > 0 and r["decode_mps"] > 0
     assert r["cpu_model"] and set(r["single_core"]) == {"stain_512x512_rgb8_L3_lossless",
                                                          "phantom_2048x2048_u12_L5_lossless"}
+
+
+def _smi_line(t, sm, reasons=()):
+    import datetime
+    stamp = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    flags = ["Active" if nm in reasons else "Not Active" for nm in ("hw_slowdown", "hw_thermal_slowdown",
+                                                                     "sw_thermal_slowdown", "sw_power_cap")]
+    return ", ".join([stamp, "0", str(sm), "2070", "900.5", "0x0"] + flags)
+
+
+def test_clock_summary_keeps_the_timed_region():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.t_start, c.t_end = 1_700_000_010.0, 1_700_000_011.0
+    lines = [_smi_line(1_700_000_009.5, 1200),                              # warm-up, before the region
+             _smi_line(1_700_000_010.2, 2070), _smi_line(1_700_000_010.4, 2055, {"sw_power_cap"}),
+             _smi_line(1_700_000_010.6, 2070),
+             _smi_line(1_700_000_011.3, 900, {"hw_slowdown"}),               # after the region
+             "garbage line", ""]
+    r = c.summary(lines)
+    assert r["samples"] == 3 and r["samples_total"] == 5
+    assert r["sm_mhz"] == 2070 and r["sm_max_mhz"] == 2070
+    assert r["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_of_a_region_between_two_samples():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.t_start, c.t_end = 1_700_000_010.00, 1_700_000_010.05
+    r = c.summary([_smi_line(1_700_000_009.9, 1500), _smi_line(1_700_000_010.1, 2070, {"sw_thermal_slowdown"})])
+    # the first sample after the region started stands for it
+    assert r["samples"] == 1 and r["sm_mhz"] == 2070 and r["reasons"] == ["sw_thermal_slowdown"]
+    # unparseable timestamps: every sample counts
+    c2 = bench.ClockSampler(0)
+    c2.t_start, c2.t_end = 1.0, 2.0
+    r2 = c2.summary(["??, 0, 1980, 2070, 800, 0x0, Not Active, Not Active, Not Active, Not Active"])
+    assert r2["samples"] == 1 and r2["sm_mhz"] == 1980 and r2["reasons"] == []
+
+
+def test_clock_sampler_runs_a_sampling_process(tmp_path):
+    """start/mark/stop around a fake nvidia-smi that prints a sample every 50 ms."""
+    import time
+    fake = tmp_path / "fake-smi"
+    fake.write_text(
+        "#!" + sys.executable + "\n"
+        "import datetime, sys, time\n"
+        "assert sys.argv[1:3] == ['-i', '0'] and sys.argv[3].startswith('--query-gpu=timestamp,')\n"
+        "while True:\n"
+        "    s = datetime.datetime.now().strftime('%Y/%m/%d %H:%M:%S.%f')[:-3]\n"
+        "    print(s + ', 0, 2070, 2070, 700.0, 0x0, Not Active, Not Active, Not Active, Not Active', flush=True)\n"
+        "    time.sleep(0.05)\n")
+    fake.chmod(0o755)
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0, exe=str(fake))
+    c.start()
+    time.sleep(0.5)
+    c.mark_start()
+    time.sleep(0.6)
+    c.mark_end()
+    r = c.stop()
+    assert r["sm_mhz"] == 2070 and r["reasons"] == []
+    assert 5 <= r["samples"] <= r["samples_total"], r
+    assert c.proc.poll() is not None   # the sampler is gone
+
+
+def test_clock_sampler_without_nvidia_smi():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0, exe="/nonexistent/nvidia-smi")
+    c.start()
+    c.mark_start()
+    c.mark_end()
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
