@@ -115,3 +115,74 @@ def test_clock_sampler_without_nvidia_smi():
     c.mark_start()
     c.mark_end()
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def _blocks_of_tile(w, h, levels, channels):
+    """(p, padded w, padded h) of each block in stream order, from the container's documented order: per
+    channel the LL band, then the high-pass bands of levels L .. 1, each cut into 128 x 128 cells in raster
+    order; a level-l band is ceil(w / 2^l) x ceil(h / 2^l); blocks are padded to multiples of 4."""
+    out = []
+    for _ in range(channels):
+        bands = [(1, levels)] + [(3, l) for l in range(levels, 0, -1)]
+        for p, l in bands:
+            bw, bh = ((w - 1) >> l) + 1, ((h - 1) >> l) + 1
+            for cy in range(0, bh, 128):
+                for cx in range(0, bw, 128):
+                    cw, chh = min(128, bw - cx), min(128, bh - cy)
+                    out.append((p, -(-cw // 4) * 4, -(-chh // 4) * 4))
+    return out
+
+
+def _kept_bytes_by_parsing(streams, geoms):
+    import numpy as np
+    from blockparse import Bits
+    n, total = 0, 0
+    for s, geo in zip(streams, geoms):
+        assert s[:4] == b"ISX1"
+        nb = int(np.frombuffer(s[12:16], "<u4")[0])
+        assert nb == len(geo)
+        ends = np.frombuffer(s[32:32 + 4 * nb], "<u4")
+        data = 32 + 4 * nb
+        begin = 0
+        for (p, bw, bh), end in zip(geo, ends):
+            b = Bits(s, 8 * (data + begin))
+            d = b.get(5)
+            removed = sum(b.get(1) for _ in range(p * d))
+            total += (p * d - removed) * (bw * bh // 8)
+            n += 1
+            begin = int(end)
+    return n, total
+
+
+def _check_kept_symbol_bytes(orc, imgs, grid, levels, channels, bits, q):
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    streams = [orc.encode_tile(a, levels, bits, q) for a in imgs]
+    offs = np.concatenate(([0], np.cumsum([len(s) for s in streams]))).astype(np.int64)
+    raw = np.frombuffer(b"".join(streams), np.uint8)
+    geoms = [_blocks_of_tile(w, h, levels, channels) for (_, _, w, h) in grid]
+    for (_, _, w, h), g in zip(grid, geoms):
+        assert [tuple(int(v) for v in b) for b in bench.block_geometry(w, h, levels, channels)] == g
+    got = bench.kept_symbol_bytes(raw, offs, grid, levels, channels)
+    assert got == _kept_bytes_by_parsing(streams, geoms)
+    return got
+
+
+def test_kept_symbol_bytes_of_slide_tiles(orc, synth):
+    """The benchmark's algorithmic bytes come from the block headers of its own stream; count them again with
+    the independent block reader on oracle streams (edge tiles included, lossy and lossless)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    W, H = 600, 300
+    img = synth.slide(bench.replica_seed(0), 0, 0, W, H)
+    grid = bench.tile_grid(W, H)
+    tiles = [img[y:y + h, x:x + w] for (x, y, w, h) in grid]
+    for q in (bench.LOSSY_Q, [0] * 9):
+        nb, kept = _check_kept_symbol_bytes(orc, tiles, grid, 8, 3, 8, q)
+        assert nb > 0 and kept > 0
+
+
+def test_kept_symbol_bytes_of_a_12_bit_mono_tile(orc, synth):
+    a = synth.phantom(synth.config_seed(2), 2048, 2048, 300, 500, 200, 130)
+    _check_kept_symbol_bytes(orc, [a], [(0, 0, 200, 130)], 5, 1, 12, [0] * 6)
