@@ -186,3 +186,32 @@ def test_kept_symbol_bytes_of_slide_tiles(orc, synth):
 def test_kept_symbol_bytes_of_a_12_bit_mono_tile(orc, synth):
     a = synth.phantom(synth.config_seed(2), 2048, 2048, 300, 500, 200, 130)
     _check_kept_symbol_bytes(orc, [a], [(0, 0, 200, 130)], 5, 1, 12, [0] * 6)
+
+
+def test_traffic_figures_follow_the_source_digest(tmp_path, monkeypatch):
+    """ncu traffic is reported only for the kernel code it was captured on: comments and whitespace may
+    change, code may not."""
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    for stage, ent in bench.NCU_TRAFFIC.items():
+        valid = bench.source_digest(ent[1]) == ent[2]
+        t = bench.traffic_bytes(stage, 1_000_000)
+        assert (t == int(ent[3] * 1_000_000)) if valid else (t is None), stage
+    assert bench.traffic_bytes("no.such.stage", 10) is None
+    # a copy of the sources: comment and whitespace edits keep the digest, a code edit changes it
+    csrc = tmp_path / "paper_2005_08713_gb300" / "csrc"
+    shutil.copytree(os.path.join(ROOT, "paper_2005_08713_gb300", "csrc"), csrc)
+    names = ("isx_decode.cu", "isx_internal.cuh")
+    before = bench.source_digest(names)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.source_digest(names) == before
+    p = csrc / "isx_decode.cu"
+    src = p.read_text()
+    p.write_text("// a new comment\n/* and a\n   block comment */\n" + src.replace("\n", "\n\n", 3) + "   \n")
+    assert bench.source_digest(names) == before
+    p.write_text(src + "\nstatic int isx_extra_symbol = 1;\n")
+    assert bench.source_digest(names) != before
+    # a missing file makes the figure unavailable, not an error
+    p.unlink()
+    assert bench.traffic_bytes("decode.segments", 10) is None
