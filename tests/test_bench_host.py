@@ -215,3 +215,15 @@ def test_traffic_figures_follow_the_source_digest(tmp_path, monkeypatch):
     # a missing file makes the figure unavailable, not an error
     p.unlink()
     assert bench.traffic_bytes("decode.segments", 10) is None
+
+
+def test_optional_measurements_fail_soft():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.soft(lambda a, b=0: a + b, 2, b=3) == 5
+
+    def broken():
+        raise RuntimeError("device status 3")
+    r = bench.soft(broken)
+    assert r == {"error": "RuntimeError: device status 3"}
+    assert len(bench.soft(lambda: (_ for _ in ()).throw(ValueError("x" * 1000)))["error"]) == 400
