@@ -174,11 +174,13 @@ def encode_block(coef: np.ndarray):
     p, h, w = c.shape
     cap = 64 + p * h * w * 8
     out = np.zeros(cap, np.uint8)
-    st = np.zeros(8, np.int64)
+    st = np.zeros(8 + 256, np.int64)
     n = _get().orc_encode_block(p, w, h, _p(c), _p(out), cap, _p(st))
     assert n > 0
     keys = ["d", "czr", "w", "t", "b", "l_prov", "n_sym"]
-    return out[:n].tobytes(), dict(zip(keys, st[:7].tolist()))
+    stats = dict(zip(keys, st[:7].tolist()))
+    stats["prov_len"] = st[8:].tolist()   # provisional code lengths behind l (0 = absent)
+    return out[:n].tobytes(), stats
 
 
 def decode_block(data: bytes, p: int, w: int, h: int, drop: int = 0):

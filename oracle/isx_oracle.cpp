@@ -431,6 +431,7 @@ std::vector<Token> tokens_of(const SegmentRuns& r, int czr, int w) {
 
 struct EncodeStats {  // exposed for the pins (Eq. 3 choice, Huffman)
   int d, czr, w, t, b, l_prov, n_kept_planes;
+  int prov_len[256];    // code lengths of the provisional code of Eq. 3's l (0 = symbol absent)
   int64_t n_sym;
 };
 
@@ -465,7 +466,10 @@ std::vector<uint8_t> encode_block(const Block& blk, EncodeStats* st) {
   bw.put((uint64_t)d, 5);
   for (int t = 0; t < p; ++t)
     for (int pl = 0; pl < d; ++pl) bw.put((uint64_t)removed[t][pl], 1);
-  if (st) { st->d = d; st->n_sym = n_sym; st->czr = -1; st->w = -1; st->t = -1; st->b = -1; st->l_prov = -1; }
+  if (st) {
+    st->d = d; st->n_sym = n_sym; st->czr = -1; st->w = -1; st->t = -1; st->b = -1; st->l_prov = -1;
+    for (int s = 0; s < 256; ++s) st->prov_len[s] = 0;
+  }
   if (n_sym == 0) return bw.bytes;  // nothing kept: mask only
 
   // Zero-run symbol: least frequent of 1..255 among the kept symbols,
@@ -492,6 +496,8 @@ std::vector<uint8_t> encode_block(const Block& blk, EncodeStats* st) {
     }
   HuffCode hprov = huffman_build(prov);
   int l = prov[czr] > 0 ? hprov.len[czr] : 0;
+  if (st)
+    for (int s = 0; s < 256; ++s) st->prov_len[s] = hprov.len[s] > 0 ? hprov.len[s] : 0;
   int b = 0;
   while (((int64_t)1 << b) < n_sym) ++b;  // ceil(log2 n_sym)
   if (b < 2) b = 2;
@@ -934,7 +940,8 @@ int64_t orc_tokens(const int32_t* seg, int64_t n, int czr, int w, int32_t* sym_o
 }
 
 // Block codec on explicit coefficients: coef = p planes of h x w (padded).
-// stats_out (8 x int64): d, czr, w, t, b, l_prov, n_sym, 0.
+// stats_out (8 + 256 int64): d, czr, w, t, b, l_prov, n_sym, 0, then the
+// provisional code's length of each symbol 0..255 (0 = absent).
 int64_t orc_encode_block(int p, int64_t w, int64_t h, const int64_t* coef, uint8_t* out, int64_t cap, int64_t* stats_out) {
   Block b;
   b.p = p; b.w = w; b.h = h;
@@ -944,6 +951,7 @@ int64_t orc_encode_block(int p, int64_t w, int64_t h, const int64_t* coef, uint8
   if (stats_out) {
     stats_out[0] = st.d; stats_out[1] = st.czr; stats_out[2] = st.w; stats_out[3] = st.t;
     stats_out[4] = st.b; stats_out[5] = st.l_prov; stats_out[6] = st.n_sym; stats_out[7] = 0;
+    for (int s = 0; s < 256; ++s) stats_out[8 + s] = st.prov_len[s];
   }
   if ((int64_t)bytes.size() > cap) return -(int64_t)bytes.size();
   std::memcpy(out, bytes.data(), bytes.size());

@@ -190,7 +190,45 @@ def block_cases():
     alt = np.zeros((1, 16, 16), np.int64)
     alt[0, ::2, ::2] = 1
     cases.append(alt)
+    # tiny blocks: N_sym <= 4 symbols, so b = max(2, ceil(log2 N_sym)) = 2
+    one = np.zeros((1, 4, 4), np.int64)
+    one[0, 0, 0] = -1                       # d = 2, both planes kept: 4 symbols
+    cases.append(one)
+    one = np.zeros((1, 4, 4), np.int64)
+    one[0, 2, 1] = 1                        # sign plane removed: 2 symbols
+    cases.append(one)
+    # dense halves beside zero halves: every byte value occurs in the kept planes (so C_zr occurs as
+    # a literal, and Eq. 3's cost counts its literal tokens) next to long zero runs
+    for frac in (0.5, 0.8, 0.95):
+        c = rng.integers(-(1 << 10), 1 << 10, (3, 128, 128)).astype(np.int64)
+        c[:, : int(128 * frac), :] = 0
+        cases.append(c)
+    # uniform symbols (C_zr occurs about 220 times as a literal) and one 4 x 8 hole, i.e. a run of 4
+    # zero areas opening every plane: w = 2 wins only because the literal C_zr tokens are costed too
+    # (without them, 3 counter bits and one pair per run would be cheaper)
+    c = np.random.default_rng(3).integers(-1023, 1024, (3, 128, 128)).astype(np.int64)
+    c[0, 0:4, 0:8] = 0
+    cases.append(c)
     return cases
+
+
+def expected_segments(orc, coef, removed, d):
+    """Plane segment pl = the symbols of plane pl (Eq. 1 order, Eq. 2 values) of each kept type, the types
+    in the block's order (HL, LH, HH), concatenated."""
+    p, h, w = coef.shape
+    n = w * h // 8
+    segs = []
+    for pl in range(d):
+        seg = []
+        for t in range(p):
+            if removed[t][pl]:
+                continue
+            for k in range(pl * n, (pl + 1) * n):
+                i, j, kp = orc.area_T(k, w, h)
+                assert kp == pl
+                seg.append(orc.area_symbol(coef[t], i, j, pl, d))
+        segs.append(seg)
+    return segs
 
 
 def test_block_roundtrip_and_format(orc):
@@ -200,6 +238,10 @@ def test_block_roundtrip_and_format(orc):
         back = orc.decode_block(data, p, w, h)
         assert np.array_equal(back, coef)
         parsed = parse_block(data, p, w, h)
+        if w * h * p <= 64 * 64 * 3 or coef.std() > 100:
+            want = expected_segments(orc, coef, parsed["removed"], parsed["d"])
+            got = [[] if pl is None else pl["symbols"] for pl in parsed["planes"]]
+            assert got == want
         m = int(np.abs(coef).max())
         assert parsed["d"] == st["d"] == 1 + m.bit_length()
         # removed planes are exactly the all-zero (type, plane) symbol sets
@@ -251,6 +293,28 @@ def check_block_properties(parsed, st, p, w, h):
                 i += 1
     b = max(2, (st["n_sym"] - 1).bit_length())
     assert st["b"] == b
+    # l: C_zr's length in the provisional code, where each run counts once for C_zr and every other
+    # symbol (isolated zeros and literal C_zr included) counts as itself.  Its lengths must be those of an
+    # optimal code for exactly these counts (Huffman), and l the entry of C_zr.
+    prov = np.zeros(256, np.int64)
+    for pl in planes:
+        seq, i = pl["symbols"], 0
+        while i < len(seq):
+            j = i
+            while j < len(seq) and seq[j] == 0:
+                j += 1
+            if j - i >= 2:
+                prov[czr] += 1
+                i = j
+            else:
+                prov[seq[i]] += 1
+                i += 1
+    plen = np.array(st["prov_len"], np.int64)
+    if (prov > 0).sum() >= 2:
+        assert set(np.nonzero(plen)[0].tolist()) == set(np.nonzero(prov)[0].tolist())
+        assert sum(2.0 ** -int(v) for v in plen[plen > 0]) == 1.0
+        assert int((prov * plen).sum()) == optimal_cost(prov.tolist())
+    assert st["l_prov"] == (int(plen[czr]) if prov[czr] > 0 else 0)
     costs = {wc: (wc + st["l_prov"]) * (int(count[czr]) + sum(-(-L // (2 ** wc - 1)) for L in runs))
              for wc in range(2, b + 1)}
     assert wb == min(costs, key=lambda k: (costs[k], k))

@@ -118,3 +118,70 @@ def test_corrupt_tile_stream_is_an_error(orc, synth):
     bad[0] = ord("J")
     with pytest.raises(ValueError):
         orc.decode_tile(bytes(bad))
+
+
+def _expected_bands(orc, img, levels, q):
+    """Per channel, the quantised subbands of the tile built from the pinned steps: the colour transform,
+    the 2-D transform in Mallat layout (LL top-left; per level HL top-right = high horizontally, LH
+    bottom-left, HH bottom-right), then each band quantised with its own step: 2^q[l-1] for the bands
+    of level l (l = 1 finest), 2^q[levels] for the LL band."""
+    planes = orc.rct_forward(img.astype(np.int64)) if img.ndim == 3 else img.astype(np.int64)[..., None]
+    h, w = img.shape[:2]
+    quant = np.vectorize(orc.quantise)
+    out = []
+    for c in range(planes.shape[2]):
+        M = orc.dwt2_forward(planes[..., c], levels)
+        bands = {}
+        for l in range(1, levels + 1):
+            pw, ph = _levels_dims(w, l - 1), _levels_dims(h, l - 1)
+            lw, lh = (pw + 1) // 2, (ph + 1) // 2
+            delta = 1 << q[l - 1]
+            bands[(l, 0)] = quant(M[:lh, lw:pw], delta)     # HL
+            bands[(l, 1)] = quant(M[lh:ph, :lw], delta)     # LH
+            bands[(l, 2)] = quant(M[lh:ph, lw:pw], delta)   # HH
+        bands[(0, 0)] = quant(M[:_levels_dims(h, levels), :_levels_dims(w, levels)], 1 << q[levels])
+        out.append(bands)
+    return out
+
+
+@pytest.mark.parametrize("shape,levels,bits,q", [((136, 200, 3), 3, 8, [1, 2, 3, 2]),
+                                                 ((300, 260), 2, 12, [0, 1, 3]),
+                                                 ((70, 45, 3), 4, 8, [0, 0, 0, 0, 0])])
+def test_tile_stream_layout(orc, synth, shape, levels, bits, q):
+    """The tile container as documented: header fields, then per channel the LL blocks and the high-pass
+    blocks of levels L .. 1, each band cut into 128 x 128 cells in raster order; a high-pass block
+    multiplexes HL, LH and HH (Fig. 3) in that order, each band quantised with its own level's step."""
+    if len(shape) == 3:
+        img = synth.slide(synth.config_seed(3), 7000, 9000, shape[1], shape[0])
+    else:
+        img = synth.phantom(synth.config_seed(2), 2048, 2048, 900, 700, shape[1], shape[0])
+    h, w = img.shape[:2]
+    C = 1 if img.ndim == 2 else 3
+    s = orc.encode_tile(img, levels, bits, q)
+    assert s[:4] == b"ISX1"
+    hdr = np.frombuffer(s[4:12], np.uint8)
+    assert int.from_bytes(s[4:6], "little") == w and int.from_bytes(s[6:8], "little") == h
+    assert list(hdr[4:8]) == [C, bits, levels, 1 if C == 3 else 0]
+    nb = int.from_bytes(s[12:16], "little")
+    assert list(s[16:16 + levels + 1]) == list(q)
+    ends = [int.from_bytes(s[32 + 4 * i:36 + 4 * i], "little") for i in range(nb)]
+    data = s[32 + 4 * nb:]
+    assert ends == sorted(ends) and ends[-1] == len(data)
+    bands = _expected_bands(orc, img, levels, q)
+    k = 0
+    for c in range(C):
+        for l in [0] + list(range(levels, 0, -1)):
+            gw, gh = _levels_dims(w, levels if l == 0 else l), _levels_dims(h, levels if l == 0 else l)
+            types = [(0, 0)] if l == 0 else [(l, 0), (l, 1), (l, 2)]
+            for by in range(0, gh, 128):
+                for bx in range(0, gw, 128):
+                    bw, bh = -(-min(128, gw - bx) // 4) * 4, -(-min(128, gh - by) // 4) * 4
+                    want = np.zeros((len(types), bh, bw), np.int64)
+                    for t, key in enumerate(types):
+                        part = bands[c][key][by:by + bh, bx:bx + bw]
+                        want[t, :part.shape[0], :part.shape[1]] = part
+                    blk = data[(ends[k - 1] if k else 0):ends[k]]
+                    got = orc.decode_block(blk, len(types), bw, bh)
+                    assert np.array_equal(got, want), (c, l, by, bx)
+                    k += 1
+    assert k == nb
