@@ -18,8 +18,10 @@
 // All integer arithmetic is int64_t; floor division is written out.
 // "parity unpinned" functions (no paper example exists): the Eq. 1 area
 // order, the block header field order (Fig. 3 is missing), the Huffman
-// tie-break shape and the Eq. 3 cost reading.  Their pins are invariants
-// (bijection, round trip, optimal length), not paper bytes.
+// tie-break shape, the Eq. 3 cost reading and the 2-D lifting order
+// (columns, then rows: integer lifting does not commute, and the paper
+// does not say).  Their pins are invariants (bijection, round trip,
+// optimal length), not paper bytes.
 
 #include <cstdint>
 #include <cstring>
