@@ -130,10 +130,13 @@ isx_status isx_decode_region_host(isx_ctx* ctx, const void* h_stream, const uint
                                   int32_t ry, int32_t rw, int32_t rh, int32_t drop_lsb_planes, void* h_out,
                                   int64_t out_pitch_bytes, void* stream);
 
-/* Forward transform stage alone: colour transform, wavelet and
- * quantisation of each tile, written as int32 Mallat planes (per tile,
- * channels planes of height x width, tiles back to back) to d_coef, which
- * must hold sum(channels * width * height) elements. */
+/* Forward transform stage alone: colour transform (Fig. 1), 5/3 lifting
+ * wavelet (Sec. 4) and quantisation (Sec. 3) of each tile, written as
+ * int32 Mallat planes (per tile, channels planes of height x width, tiles
+ * back to back; per level HL top-right, LH bottom-left, HH bottom-right) to
+ * d_coef, a DEVICE buffer owned by the caller, which must hold
+ * sum(channels * width * height) elements.  Asynchronous; argument errors
+ * as isx_encode_tiles. */
 isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles,
                                     int32_t* d_coef, void* stream);
 
@@ -179,7 +182,8 @@ typedef struct {
 } isx_decode_job;
 
 /* Decode any number of jobs in one call (every job at the same level and
- * LSB drop): a region decode is the set of jobs of the tiles meeting the
+ * LSB drop; level and drop as in isx_decode_region, Sec. 4
+ * "Decompression"): a region decode is the set of jobs of the tiles meeting the
  * region, all pointing into one image; a batch of tiles can be decoded each
  * into its own buffer; jobs of several requests can share the call.  Tiles
  * of different channel counts and bit depths may be mixed.  Asynchronous,
