@@ -227,3 +227,19 @@ def test_optional_measurements_fail_soft():
     r = bench.soft(broken)
     assert r == {"error": "RuntimeError: device status 3"}
     assert len(bench.soft(lambda: (_ for _ in ()).throw(ValueError("x" * 1000)))["error"]) == 400
+
+
+def test_slide_workload_geometry():
+    """40000 x 30000 pixels in 256 x 256 tiles: 157 x 118 = 18 526 tiles, the right column 64 wide, the
+    bottom row 48 tall; the tiles cover the image exactly once."""
+    sys.path.insert(0, ROOT)
+    import bench
+    grid = bench.tile_grid(40000, 30000)
+    assert len(grid) == 157 * 118 == 18526
+    assert {w for (x, _, w, _) in grid if x == 156 * 256} == {64}
+    assert {h for (_, y, _, h) in grid if y == 117 * 256} == {48}
+    assert sum(w * h for (_, _, w, h) in grid) == 40000 * 30000
+    assert grid[0] == (0, 0, 256, 256) and grid[-1] == (156 * 256, 117 * 256, 64, 48)
+    # row-major order: the offsets index of tile (row r, column c) is r * 157 + c
+    assert grid[157] == (0, 256, 256, 256)
+    assert bench.LEVELS == 8 and bench.LOSSY_Q[:4] == [3, 2, 1, 0]
