@@ -42,3 +42,27 @@ def test_slide_background_fraction_and_ranges(synth):
 def test_phantom_is_12_bit(synth):
     ph = synth.phantom(synth.config_seed(2), 2048, 2048, 0, 0, 2048, 256)
     assert ph.dtype == np.uint16 and ph.max() <= 4095 and ph.max() > 1000
+
+
+def test_mixed_batch_recipe(synth):
+    """4096 tiles: sides uniform in 17..256, RGB8 slide crops or 12-bit phantom crops with equal odds,
+    2..6 levels, lossless or lossy with equal odds; every crop inside its generator's image."""
+    import numpy as np
+    specs = synth.batch_specs(synth.config_seed(4), 4096)
+    assert specs == synth.batch_specs(synth.config_seed(4), 4096)           # seeded
+    w = np.array([s["w"] for s in specs]); h = np.array([s["h"] for s in specs])
+    assert w.min() >= 17 and w.max() <= 256 and h.min() >= 17 and h.max() <= 256
+    assert abs(w.mean() - 136.5) < 3 and abs(h.mean() - 136.5) < 3
+    lv = np.array([s["levels"] for s in specs])
+    assert set(lv.tolist()) == {2, 3, 4, 5, 6}
+    rgb = np.array([s["rgb"] for s in specs])
+    assert 0.45 < rgb.mean() < 0.55
+    lossy = np.array([any(s["q"]) for s in specs])
+    assert 0.45 < lossy.mean() < 0.55
+    for s in specs:
+        assert len(s["q"]) == s["levels"] + 1
+        assert s["bits"] == (8 if s["rgb"] else 12)
+        W, H = (40000, 30000) if s["rgb"] else (2048, 2048)
+        assert 0 <= s["x0"] and s["x0"] + s["w"] <= W and 0 <= s["y0"] and s["y0"] + s["h"] <= H
+    img = synth.batch_image(specs[0])
+    assert img.shape[:2] == (specs[0]["h"], specs[0]["w"])
