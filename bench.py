@@ -138,9 +138,9 @@ class ClockSampler:
         return self.summary(list(self.lines))
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per pixel of each stage's kernel, from one
-# ncu --set full capture of the 8192 x 8192 case of this workload (profiles/kernels_slide_8192x8192_lossy.md),
-# scaled to a full launch by pixels.  Valid only while the code of the kernel's source files is the one
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per pixel of each stage's kernel, from the
+# committed ncu captures of the 8192 x 8192 case of this workload (one kernel per capture), scaled to a full
+# launch by pixels.  These are figures copied from those captures, not measured by this run.  Valid only while the code of the kernel's source files is the one
 # captured (source_digest: comments and whitespace aside); otherwise the bench reports traffic as null.
 NCU_TRAFFIC = {
     "encode.transform": ("k_fwd_tile_smem", ("isx_transform.cu", "isx_warp_levels.cuh", "isx_internal.cuh"), "5822ca7b8c98d403", 8.179),
@@ -154,7 +154,7 @@ NCU_TRAFFIC = {
 }
 
 
-# Warp instructions per pixel of each stage's kernel (smsp__inst_executed.sum of the same capture),
+# Warp instructions per pixel of each stage's kernel (smsp__inst_executed.sum of the same captures),
 # for the issue-rate co-roofline: the codec is integer work, and its kernels are bound by latency and
 # instruction issue long before DRAM bandwidth.
 NCU_WARP_INST_PER_PX = {
@@ -421,9 +421,12 @@ def run_gpu(args):
     single = {k: v for k, v in stages.items() if k in algo}
     dom = max(single, key=lambda k: single[k][0]) if single else None
     roof = None
+    # algorithmic bytes of the path (one encode or one decode of the image): 3 B/px of pixels plus the
+    # compressed stream; coefficients and symbols moved between kernels are not algorithmic
+    path_bytes = 3 * px + total_bytes
     if dom:
         avg_ms = single[dom][0] / max(1, single[dom][1])
-        ach = algo[dom] / (avg_ms / 1e3) / 1e9
+        ach = path_bytes / (avg_ms / 1e3) / 1e9
         iss = issue_roofline(dom, px, avg_ms)
         alu = None
         if iss and clk.get("sm_mhz"):
@@ -434,12 +437,23 @@ def run_gpu(args):
                    "frac": round(got / peak_wi, 4), "warp_inst_per_px": per_px,
                    "peak_basis": f"{sms} SMs x 4 schedulers x 1 warp-inst/cycle x {clk['sm_mhz']:.0f} MHz (median under load)"}
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+                "algorithmic_bytes": int(path_bytes),
+                "algorithmic_basis": "3 B/px of pixels + the compressed stream, per launch (the kernel covers the whole image)",
                 "issue_coroofline": alu,
-                "traffic": traffic_bytes(dom, px), "algorithmic_bytes": int(algo[dom]), "peak_kind": peak_kind,
-                "avg_launch_ms": round(avg_ms, 3), "stage_rooflines": {
-                    k: {"GBps": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9, 1),
-                        "frac": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9 / hbm, 4)} for k, v in single.items()}}
-    path_bytes = 3 * IMG_W * IMG_H + total_bytes
+                "traffic": traffic_bytes(dom, px), "peak_kind": peak_kind,
+                "traffic_source": "committed ncu capture of the 8192x8192 case, scaled by pixels; null once the kernel's code "
+                                  "differs from the captured code",
+                "avg_launch_ms": round(avg_ms, 3),
+                "kernel_io_bytes": int(algo[dom]),
+                "stage_rooflines": {
+                    k: {"ms": round(v[0] / max(1, v[1]), 3),
+                        "path_frac": round(path_bytes / (v[0] / max(1, v[1]) / 1e3) / 1e9 / hbm, 4),
+                        "kernel_io_GBps": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9, 1),
+                        "kernel_io_frac": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9 / hbm, 4)} for k, v in single.items()},
+                "stage_rooflines_basis": "path_frac: the path's algorithmic bytes over the stage's time; kernel_io: the bytes this "
+                                         "design's kernel must read and write (intermediates included)"}
+        if alu:
+            alu["source"] = "warp instructions per pixel from the committed ncu capture (not measured by this run)"
     path = {"encode_GBps": round(path_bytes / (statistics.median(enc_ms) / 1e3) / 1e9, 1),
             "decode_GBps": round(path_bytes / (statistics.median(dec_ms) / 1e3) / 1e9, 1),
             "algorithmic_bytes_per_px": round(path_bytes / (IMG_W * IMG_H), 3), "peak_GBps": hbm}
@@ -482,6 +496,44 @@ def run_gpu(args):
                "h2d_bytes_per_step": 3 * IMG_W * IMG_H + nbytes + 8 * (len(grid) + 1),
                "d2h_bytes_per_step": nbytes + 8 * (len(grid) + 1) + 3 * IMG_W * IMG_H}
 
+    # the same slide lossless (BASELINE config 3's second run): encode + full decode, device events
+    ll = {"tiles": None}
+
+    def lossless_run():
+        tiles_ll = tiles_for(d_img, [0] * 9)
+        d_out2 = torch.empty(cap, dtype=torch.uint8, device=dev)
+        d_offs2 = torch.empty(len(grid) + 1, dtype=torch.int64, device=dev)
+        codec.encode_tiles(tiles_ll, d_out2, d_offs2, stream)
+        if codec.sync_status(stream) != 0:
+            raise RuntimeError("lossless encode failed")
+        ll.update(tiles=tiles_ll, out=d_out2, offs=d_offs2)
+        e_ms, d_ms = [], []
+        for _ in range(max(3, min(args.steps, 6))):
+            ev[0].record(stream)
+            codec.encode_tiles(tiles_ll, d_out2, d_offs2, stream)
+            ev[1].record(stream)
+            codec.decode_region(d_out2, d_offs2, tiles_ll, 0, (0, 0, IMG_W, IMG_H), d_dec, 0, stream)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            e_ms.append(ev[0].elapsed_time(ev[1]))
+            d_ms.append(ev[1].elapsed_time(ev[2]))
+        if codec.sync_status(stream) != 0:
+            raise RuntimeError("lossless round trip failed")
+        nb = int(d_offs2[-1].item())
+        pb = 3 * px + nb
+        em, dm = statistics.median(e_ms), statistics.median(d_ms)
+        return {"workload": f"slide_{IMG_W}x{IMG_H}_rgb8_tile{TILE}_L{LEVELS}_lossless",
+                "encode_mps": round(mp / (em / 1e3), 1), "decode_mps": round(mp / (dm / 1e3), 1),
+                "encode_ms": round(em, 3), "decode_ms": round(dm, 3),
+                "compressed_bytes": nb, "bits_per_pixel": round(8 * nb / px, 3),
+                "algorithmic_bytes_per_px": round(pb / px, 3),
+                "encode_frac": round(pb / (em / 1e3) / 1e9 / hbm, 4), "decode_frac": round(pb / (dm / 1e3) / 1e9 / hbm, 4),
+                "lossless_identity": bool(torch.equal(d_dec, d_img))}
+
+    lossless = soft(lossless_run) if rank == 0 and not args.lossless else None
+
+    singles = soft(run_single_configs, dev, stream, max(5, args.steps)) if rank == 0 and not args.no_single else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = soft(cpu_baseline, h_img.numpy(), grid, q, args.cpu_tiles)
@@ -498,16 +550,14 @@ def run_gpu(args):
            "exact": exact, "roofline": roof, "path_roofline": path,
            "tile_decode_latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[int(0.99 * (len(lat) - 1))], 3)},
            "stages_ms": {k: round(v[0] / max(1, v[1]), 3) for k, v in stages.items()},
-           "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+           "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+           "lossless": lossless, "single_image_configs": singles}
     def serving():
         # the slide's lossy pyramid is the stream above; encode the lossless one beside it
         from paper_2005_08713_gb300 import serve
-        tiles_ll = tiles_for(d_img, [0] * 9)
-        d_out2 = torch.empty(cap, dtype=torch.uint8, device=dev)
-        d_offs2 = torch.empty(len(grid) + 1, dtype=torch.int64, device=dev)
-        codec.encode_tiles(tiles_ll, d_out2, d_offs2, stream)
-        if codec.sync_status(stream) != 0:
-            raise RuntimeError("lossless encode failed")
+        if ll["tiles"] is None:
+            lossless_run()
+        tiles_ll, d_out2, d_offs2 = ll["tiles"], ll["out"], ll["offs"]
         pyramids = [serve.Pyramid(IMG_W, IMG_H, TILE, LEVELS, 3, 8, d_out, d_offs, tiles),
                     serve.Pyramid(IMG_W, IMG_H, TILE, LEVELS, 3, 8, d_out2, d_offs2, tiles_ll)]
         return run_serve(args, dev, pyramids)
@@ -520,6 +570,53 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return res if rank == 0 else None
+
+
+def run_single_configs(dev, stream, reps):
+    """The two single-image workloads on the GPU: the 512 x 512 RGB8 stain tile (3 levels) and the
+    2048 x 2048 12-bit phantom (5 levels), lossless; encode and decode MP/s (device events, median of
+    `reps`), streams checked byte for byte and decodes pixel for pixel against the oracle."""
+    import torch
+    import oracle
+    from paper_2005_08713_gb300 import isx, synth
+    cases = {"stain_512x512_rgb8_L3_lossless": (synth.stain(synth.config_seed(1)), 3, 8),
+             "phantom_2048x2048_u12_L5_lossless": (synth.phantom(synth.config_seed(2), 2048, 2048), 5, 12)}
+    out = {}
+    with isx.Codec(dev.index or 0) as codec:
+        for name, (img, L, bits) in cases.items():
+            a = np.ascontiguousarray(img)
+            d = torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).to(dev)
+            tiles = isx.TileArray([isx.tile_from_tensor(d, L, bits)])
+            cap = a.nbytes * 2 + (1 << 16)
+            d_out = torch.empty(cap, dtype=torch.uint8, device=dev)
+            d_offs = torch.empty(2, dtype=torch.int64, device=dev)
+            d_dec = torch.empty_like(d)
+            h, w = a.shape[:2]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e_ms, d_ms = [], []
+            for k in range(reps + 2):
+                ev[0].record(stream)
+                codec.encode_tiles(tiles, d_out, d_offs, stream)
+                ev[1].record(stream)
+                codec.decode_region(d_out, d_offs, tiles, 0, (0, 0, w, h), d_dec, 0, stream)
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+                if k >= 2:
+                    e_ms.append(ev[0].elapsed_time(ev[1]))
+                    d_ms.append(ev[1].elapsed_time(ev[2]))
+            if codec.sync_status(stream) != 0:
+                raise RuntimeError(f"{name}: device status")
+            n = int(d_offs[1].item())
+            got = d_out[:n].cpu().numpy().tobytes()
+            dec = d_dec.cpu().numpy()
+            dec = dec.view(np.uint16) if a.dtype == np.uint16 else dec
+            exact = got == oracle.encode_tile(a, L, bits) and np.array_equal(dec, a)
+            em, dm = statistics.median(e_ms), statistics.median(d_ms)
+            mpx = w * h / 1e6
+            out[name] = {"encode_mps": round(mpx / (em / 1e3), 1), "decode_mps": round(mpx / (dm / 1e3), 1),
+                         "encode_ms": round(em, 3), "decode_ms": round(dm, 3), "compressed_bytes": n,
+                         "bit_exact": bool(exact)}
+    return out
 
 
 def run_batch(args, dev, n_tiles=4096):
@@ -804,6 +901,7 @@ def main():
     ap.add_argument("--cpu-tiles", type=int, default=256)
     ap.add_argument("--size", default=None, help="WxH of the slide instead of 40000x30000 (small cases for profiling)")
     ap.add_argument("--no-latency", action="store_true")
+    ap.add_argument("--no-single", action="store_true", help="skip the single-image workloads (512x512 stain, 2048x2048 phantom)")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-batch measurement")
     ap.add_argument("--no-per-tile", action="store_true", help="skip the one-tile-per-call comparison of the batch")
     ap.add_argument("--batch-tiles", type=int, default=4096)

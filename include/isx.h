@@ -162,6 +162,21 @@ int32_t isx_last_launch_count(isx_ctx* ctx);
 /* Message for the last error on this context (static storage). */
 const char* isx_last_error(isx_ctx* ctx);
 
+/* Which inverse transform a decode of `tile` at `level` with
+ * `drop_lsb_planes` dropped planes (Sec. 4, "Decompression") takes:
+ * 1 = the fused shared-memory inverse, which holds every sample of the
+ * 5/3 synthesis (Sec. 4) in int16; 0 = the global inverse in int32
+ * planes; -1 = an invalid descriptor, level or drop.  Host computation
+ * only (no GPU needed).  h_bound (HOST, optional) receives the proven
+ * bound on the magnitude of every value the inverse holds for streams the
+ * encoder wrote: the forward transform's range for the tile's bit depth
+ * and channel count (5/3 filter gains plus rounding) plus the largest
+ * deviation the tile's quantiser steps and the dropped planes can carry
+ * through the synthesis.  The fused inverse is taken only when the tile
+ * fits its shared-memory plane (width and height at level `level` up to
+ * 1024, bits <= 12, plane <= 160 KB) and the bound is at most 32767. */
+int32_t isx_decode_path(const isx_tile_desc* tile, int32_t level, int32_t drop_lsb_planes, double* h_bound);
+
 /* ------------------------------------------------------------------------
  * Batching and serving.  These entry points have no counterpart in the
  * paper; they organise many tiles and many requests around the same coding
@@ -290,7 +305,11 @@ void isx_plan_destroy(isx_plan* plan);
  * The first call on each device does the set-up: it looks up the array's
  * device address (cudaGetSymbolAddress, with that device current) and sets
  * the kernels' shared-memory attributes; make that first call before any
- * stream capture begins.
+ * stream capture begins.  A set-up that fails returns ISX_ERR_CUDA and is
+ * tried again by the next call.  A CUDA error already pending on the
+ * calling thread (left by earlier work) makes the call return ISX_ERR_CUDA
+ * before anything is enqueued, leaving that error pending.  Every return,
+ * errors included, happens after `stream` has finished the call's work.
  * All calls on one device share the one array.  Each call zeroes what must
  * start at zero (the status word; d_out is cleared by the encoder itself)
  * and writes every other scratch byte before reading it, so calls made one

@@ -1,6 +1,7 @@
 // isx_api.cu — the C ABI of include/isx.h: context, scratch arena,
 // argument checks, tile planning and the kernel sequences of encode and
 // decode.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -10,10 +11,10 @@
 #include "../../include/isx.h"
 #include "isx_internal.cuh"
 #include "isx_kernels.h"
+#include "isx_host_plan.h"
 
 namespace isx {
-void encode_set_attributes();
-void decode_set_attributes();
+cudaError_t decode_set_attributes();
 }  // namespace isx
 
 using namespace isx;
@@ -179,53 +180,46 @@ isx_status ensure_staging(isx_ctx* ctx, size_t n) {
   return ISX_OK;
 }
 
-bool tile_ok(const isx_tile_desc& t, std::string* why) {
-  if (t.width < 1 || t.width > 65535 || t.height < 1 || t.height > 65535) { *why = "width/height out of 1..65535"; return false; }
-  if (t.channels != 1 && t.channels != 3) { *why = "channels must be 1 or 3"; return false; }
-  if (t.bits < 1 || t.bits > 16) { *why = "bits out of 1..16"; return false; }
-  if (t.channels == 3 && t.bits > 8) { *why = "3-channel tiles take bits 1..8"; return false; }
-  if (t.levels < 0 || t.levels > kMaxLevels) { *why = "levels out of 0..15"; return false; }
-  if (t.x0 < 0 || t.y0 < 0) { *why = "negative tile origin"; return false; }
-  for (int l = 0; l <= t.levels; ++l)
-    if (t.qstep_log2[l] > 15) { *why = "qstep_log2 out of 0..15"; return false; }
-  return true;
-}
-
-// blocks of a tile (all levels, or LL + levels > zmin) and padded coefficients
-void tile_counts(const isx_tile_desc& t, int zmin, int64_t* nb, int64_t* ncoef) {
-  int64_t b = 0, c = 0;
-  int lw = level_dim(t.width, t.levels), lh = level_dim(t.height, t.levels);
-  b += (int64_t)ceil_div(lw, kCell) * ceil_div(lh, kCell);
-  c += (int64_t)pad4(lw) * pad4(lh);
-  for (int l = t.levels; l >= 1 && l > zmin; --l) {
-    int gw = level_dim(t.width, l), gh = level_dim(t.height, l);
-    b += (int64_t)ceil_div(gw, kCell) * ceil_div(gh, kCell);
-    c += 3LL * pad4(gw) * pad4(gh);
+// Bound on every value the fused inverse holds in its int16 plane for a tile
+// decoded at level z with `drop` least significant planes discarded (Sec. 4,
+// "Decompression"), for streams written by the encoder.  Each state of the
+// inverse is a state of the lossless inverse (= a state of the forward
+// transform of the original samples, by perfect reconstruction) plus a
+// deviation caused by the dequantised coefficients.
+//  - Forward states: for samples in [0, M] (a mono plane or Y) or [-M, M]
+//    (RCT chroma, counted as a range of 2M), the linear 5/3 lifting reaches
+//    at most kGain2D * range.  kGain2D comes from the L1 norms of the
+//    equivalent filters of up to 15 iterated levels, taken on finite lines
+//    with symmetric extension at both ends (at most 1.720 for the low and
+//    2.873 for the high cascades; the infinite line gives 1.716 and 2.867),
+//    rounded up to 1.73 and 2.885: 2.885^2 / 2 <= 4.17.  The floors of the
+//    integer lifting add at most 2 inside a level and 1.875 to each LL,
+//    carried on by the linear filters with a 2-D gain of at most
+//    2.885^2 <= 8.33: kRoundPerLevel per level.
+//  - Deviation: a band sample of step D = 2^q decoded with k planes dropped
+//    is off by at most 2^k D - 1 (and never by more than F + D/2).  One
+//    inverse level maps deviations (LL, HL, LH, HH) to at most
+//    LL + HL + LH + HH + 6 (the 5/3 synthesis has L-inf gain 1 on each band
+//    pair; three passes, each floor off by less than 1), and a level whose
+//    inputs are all exact adds nothing.
+// Tiles for which F + deviation exceeds int16 take the int32 global inverse.
+constexpr double kGain2D = 4.17;
+constexpr double kRoundPerLevel = 16.0;   // >= 1.875 * 8.33
+double int16_state_bound(const isx_tile_desc& t, int z, int drop) {
+  const double M = (double)((1 << t.bits) - 1) * (t.channels == 3 ? 2.0 : 1.0);
+  const double F = M * kGain2D + 2.0 + kRoundPerLevel * t.levels;
+  auto dev = [&](int q) {
+    const double D = std::ldexp(1.0, q);
+    return std::min(std::ldexp(D, std::min(drop, 40)) - 1.0, F + D / 2);
+  };
+  double E = dev(t.qstep_log2[t.levels]);
+  for (int l = t.levels; l > z; --l) {
+    const double e = dev(t.qstep_log2[l - 1]);
+    if (E > 0 || e > 0) E += 3.0 * e + 6.0;
   }
-  *nb = b * t.channels;
-  *ncoef = c * t.channels;
+  return F + E;
 }
-
-// Blocks of each level of a tile (level 0 = LL) and the largest block of
-// each level in area quads (4 areas of 8 coefficients), all channels.
-void level_blocks(const isx_tile_desc& t, int64_t* count, int* quads) {
-  for (int l = 0; l <= t.levels; ++l) {
-    const int gw = level_dim(t.width, l == 0 ? t.levels : l), gh = level_dim(t.height, l == 0 ? t.levels : l);
-    count[l] += (int64_t)ceil_div(gw, kCell) * ceil_div(gh, kCell) * t.channels;
-    const int p = l == 0 ? 1 : 3;
-    const int q = p * pad4(std::min(gw, kCell)) * pad4(std::min(gh, kCell)) / 32;
-    quads[l] = std::max(quads[l], q);
-  }
-}
-
-void fill_tiledev(TileDev& d, const isx_tile_desc& t) {
-  std::memset(&d, 0, sizeof(d));
-  d.pixels = (const uint8_t*)t.pixels;
-  d.pitch = t.row_pitch_bytes;
-  d.w = t.width; d.h = t.height; d.C = t.channels; d.bits = t.bits; d.L = t.levels;
-  d.x0 = t.x0; d.y0 = t.y0;
-  for (int k = 0; k < 16; ++k) d.q[k] = k <= t.levels ? t.qstep_log2[k] : 0;
-}
+bool fused_inverse_fits_int16(const isx_tile_desc& t, int z, int drop) { return int16_state_bound(t, z, drop) <= 32767.0; }
 
 // Tiles of the fused path grouped by size class: task[] lists them class by
 // class; each class launches with its own plane size and thread count.
@@ -414,7 +408,7 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
     d.nb = (int32_t)nb;
     d.block_base = D.n_blocks;
     d.coef_base = 0;
-    d.fused = fused_tile(zw, zh, t.bits) ? 1 : 0;
+    d.fused = fused_tile(zw, zh, t.bits) && fused_inverse_fits_int16(t, z, drop) ? 1 : 0;
     d.dst = (uint8_t*)jb.out;
     d.dpitch = jb.pitch;
     d.rx = jb.rx; d.ry = jb.ry; d.rw = jb.rw; d.rh = jb.rh;
@@ -562,9 +556,14 @@ isx_status isx_create(isx_ctx** out, int device, size_t hbm_budget_bytes) {
     delete ctx;
     return ISX_ERR_CUDA;
   }
-  encode_set_attributes();
-  decode_set_attributes();
-  transform_set_attributes();
+  if (e == cudaSuccess) e = encode_set_attributes();
+  if (e == cudaSuccess) e = decode_set_attributes();
+  if (e == cudaSuccess) e = transform_set_attributes();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    isx_destroy(ctx);
+    return ISX_ERR_CUDA;
+  }
   *out = ctx;
   return ISX_OK;
 }
@@ -614,6 +613,15 @@ int32_t isx_stage_times(isx_ctx* ctx, char* names, int64_t names_len, double* ms
 }
 
 const char* isx_last_error(isx_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int32_t isx_decode_path(const isx_tile_desc* tile, int32_t level, int32_t drop_lsb_planes, double* h_bound) {
+  std::string why;
+  if (!tile || !tile_ok(*tile, &why) || level < 0 || level > tile->levels || drop_lsb_planes < 0) return -1;
+  const double b = int16_state_bound(*tile, level, drop_lsb_planes);
+  if (h_bound) *h_bound = b;
+  const int zw = level_dim(tile->width, level), zh = level_dim(tile->height, level);
+  return fused_tile(zw, zh, tile->bits) && b <= 32767.0 ? 1 : 0;
+}
 
 int32_t isx_last_launch_count(isx_ctx* ctx) { return ctx ? ctx->launches : 0; }
 

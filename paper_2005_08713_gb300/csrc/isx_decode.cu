@@ -656,6 +656,6 @@ int launch_level_sort(const BlockDev* blocks, int64_t nb, int64_t* bucket /* 2 *
   return L + 1;
 }
 
-void decode_set_attributes() {}
+cudaError_t decode_set_attributes() { return cudaSuccess; }
 
 }  // namespace isx

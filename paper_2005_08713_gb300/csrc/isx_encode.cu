@@ -1120,9 +1120,10 @@ int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T)
 
 size_t enc_hdr_bytes() { return sizeof(BlockHdr); }
 
-void encode_set_attributes() {
-  cudaFuncSetAttribute(k_enc_size, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
-  cudaFuncSetAttribute(k_enc_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
+cudaError_t encode_set_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_enc_size, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_enc_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
+  return e;
 }
 
 }  // namespace isx

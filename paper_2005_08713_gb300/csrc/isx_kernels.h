@@ -19,7 +19,7 @@ int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int
                          const BlockDev* d_blocks, void* coef, int* status, cudaStream_t s);
 bool fused_tile(int w, int h, int bits);
 int fused_plane_bytes(int w, int h);
-void transform_set_attributes();
+cudaError_t transform_set_attributes();   // dynamic shared memory limits of the fused transforms (current device)
 int launch_quantise_planes(const TileDev* d_tiles, int n_tiles, const int32_t* planes, int32_t* out, cudaStream_t s);
 int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int32_t* A, int32_t* B,
                              cudaStream_t s);
@@ -54,7 +54,7 @@ struct EncodeBuffers {
   int level_quads[16] = {};
 };
 size_t enc_hdr_bytes();
-void encode_set_attributes();   // dynamic shared memory limits of the coding kernels (current device)
+cudaError_t encode_set_attributes();   // dynamic shared memory limits of the coding kernels (current device)
 
 // Records an event between kernel groups: closes the open stage and opens
 // `name` (nullptr: none).  A no-op unless timing is enabled.

@@ -15,6 +15,7 @@
 
 #include "isx.h"
 #include "isx_kernels.h"
+#include "isx_host_plan.h"
 
 namespace isx {
 namespace {
@@ -23,23 +24,28 @@ constexpr size_t kStaticBytes = ISX_STATIC_SCRATCH_BYTES;
 __device__ __align__(256) uint8_t g_static_scratch[kStaticBytes];
 
 // Per-device set-up: the array's device address and the kernels' shared
-// memory attributes, done once with that device current.
+// memory attributes, with that device current.  Recorded as done only when
+// every call succeeded, so that a failed set-up is tried again by the next
+// call instead of failing every later call on the device.
 constexpr int kMaxDevices = 64;
 struct StaticSetup {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
+  bool done = false;
   uint8_t* base = nullptr;
 };
 StaticSetup g_setup[kMaxDevices];
+std::mutex g_setup_mutex;
 
-void setup_device(StaticSetup& S) {
+cudaError_t setup_device(StaticSetup& S) {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (S.done) return cudaSuccess;
   void* p = nullptr;
-  S.err = cudaGetSymbolAddress(&p, g_static_scratch);
-  if (S.err != cudaSuccess) return;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e == cudaSuccess) e = encode_set_attributes();
+  if (e == cudaSuccess) e = transform_set_attributes();
+  if (e != cudaSuccess) return e;
   S.base = static_cast<uint8_t*>(p);
-  encode_set_attributes();
-  transform_set_attributes();
-  S.err = cudaGetLastError();
+  S.done = true;
+  return cudaSuccess;
 }
 
 // Writes the tile descriptor, the fused-task list and a zero status word into
@@ -76,33 +82,15 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   if (!tile || !h_size || (!d_out && out_capacity)) return fail(h_err, err_len, ISX_ERR_ARG, "bad arguments");
   if (reinterpret_cast<uintptr_t>(d_out) & 3) return fail(h_err, err_len, ISX_ERR_ARG, "d_out must be 4-byte aligned");
   const isx_tile_desc& t = *tile;
-  if (t.width < 1 || t.width > 65535 || t.height < 1 || t.height > 65535)
-    return fail(h_err, err_len, ISX_ERR_ARG, "width/height out of 1..65535");
-  if (t.channels != 1 && t.channels != 3) return fail(h_err, err_len, ISX_ERR_ARG, "channels must be 1 or 3");
-  if (t.bits < 1 || t.bits > 16) return fail(h_err, err_len, ISX_ERR_ARG, "bits out of 1..16");
-  if (t.channels == 3 && t.bits > 8) return fail(h_err, err_len, ISX_ERR_ARG, "3-channel tiles take bits 1..8");
-  if (t.levels < 0 || t.levels > kMaxLevels) return fail(h_err, err_len, ISX_ERR_ARG, "levels out of 0..15");
-  if (t.x0 < 0 || t.y0 < 0) return fail(h_err, err_len, ISX_ERR_ARG, "negative tile origin");
-  for (int l = 0; l <= t.levels; ++l)
-    if (t.qstep_log2[l] > 15) return fail(h_err, err_len, ISX_ERR_ARG, "qstep_log2 out of 0..15");
+  std::string why;
+  if (!tile_ok(t, &why)) return fail(h_err, err_len, ISX_ERR_ARG, why);
   if (!t.pixels || t.row_pitch_bytes < (int64_t)t.width * t.channels * (t.bits <= 8 ? 1 : 2))
     return fail(h_err, err_len, ISX_ERR_ARG, "missing pixels or row pitch too small");
 
   // Blocks and padded coefficients of the tile: the LL band, then three
   // subbands per level, each cut into 128 x 128 cells (Fig. 3).
   int64_t nb = 0, nc = 0;
-  {
-    const int lw = level_dim(t.width, t.levels), lh = level_dim(t.height, t.levels);
-    nb += (int64_t)ceil_div(lw, kCell) * ceil_div(lh, kCell);
-    nc += (int64_t)pad4(lw) * pad4(lh);
-    for (int l = t.levels; l >= 1; --l) {
-      const int gw = level_dim(t.width, l), gh = level_dim(t.height, l);
-      nb += (int64_t)ceil_div(gw, kCell) * ceil_div(gh, kCell);
-      nc += 3LL * pad4(gw) * pad4(gh);
-    }
-    nb *= t.channels;
-    nc *= t.channels;
-  }
+  tile_counts(t, 0, &nb, &nc);
   const bool fused = fused_tile(t.width, t.height, t.bits);
   const int64_t plane_total = fused ? 0 : (int64_t)t.channels * t.width * t.height;
   const int64_t coef_bytes = nc * (t.bits <= 12 ? 2 : 4);
@@ -134,19 +122,22 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   if (e != cudaSuccess) return fail(h_err, err_len, ISX_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(h_err, err_len, ISX_ERR_ARG, "device ordinal beyond 63");
   StaticSetup& S = g_setup[dev];
-  std::call_once(S.once, setup_device, std::ref(S));
-  if (S.err != cudaSuccess)
-    return fail(h_err, err_len, ISX_ERR_CUDA, std::string("static scratch set-up: ") + cudaGetErrorString(S.err));
+  e = setup_device(S);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h_err, err_len, ISX_ERR_CUDA, std::string("static scratch set-up: ") + cudaGetErrorString(e));
+  }
+  // An error left pending by earlier work of the caller would surface at our
+  // launch check below and be reported as ours: refuse the call instead (the
+  // error stays pending for its owner), before anything is enqueued.
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess)
+    return fail(h_err, err_len, ISX_ERR_CUDA, std::string("a CUDA error was pending before the call: ") + cudaGetErrorString(e));
 
   uint8_t* ar = S.base;
   cudaStream_t s = (cudaStream_t)stream;
   TileDev td;
-  std::memset(&td, 0, sizeof(td));
-  td.pixels = (const uint8_t*)t.pixels;
-  td.pitch = t.row_pitch_bytes;
-  td.w = t.width; td.h = t.height; td.C = t.channels; td.bits = t.bits; td.L = t.levels;
-  td.x0 = t.x0; td.y0 = t.y0;
-  for (int k = 0; k < 16; ++k) td.q[k] = k <= t.levels ? t.qstep_log2[k] : 0;
+  fill_tiledev(td, t);
   td.nb = (int32_t)nb;
   td.fused = fused ? 1 : 0;
   td.block_base = 0; td.plane_base = 0; td.coef_base = 0; td.sym_base = 0;
@@ -177,19 +168,28 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   eb.bucket = (int64_t*)(ar + o_bucket); eb.perm = (int64_t*)(ar + o_perm);
   eb.out = (uint8_t*)d_out; eb.out_capacity = (int64_t)out_capacity;
   eb.tile_offsets = d_offsets; eb.status = d_status;
+  // the symbol pass launches per level with CTAs sized to the level's blocks, as for isx_encode_tiles
+  level_blocks(t, eb.level_blocks, eb.level_quads);
   struct NoMarks : StageMarks {
     void mark(const char*, cudaStream_t) override {}
   } marks;
   launch_encode_coding(eb, s, &marks);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(h_err, err_len, ISX_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    // kernels may already be in flight on the shared scratch and on d_out: the call stays synchronous
+    cudaStreamSynchronize(s);
+    return fail(h_err, err_len, ISX_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  }
 
   // offsets [0, size] and the status word sit next to each other in the scratch
   uint8_t res[32];
   e = cudaMemcpyAsync(res, ar + o_offsets, 16, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(res + 16, ar + o_status, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(h_err, err_len, ISX_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    return fail(h_err, err_len, ISX_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  }
   uint64_t size = 0;
   int status = 0;
   std::memcpy(&size, res + 8, 8);

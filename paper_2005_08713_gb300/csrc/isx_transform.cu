@@ -1436,9 +1436,10 @@ int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int
 bool fused_tile(int w, int h, int bits) { return tile_uses_smem(w, h, bits); }
 int fused_plane_bytes(int w, int h) { return smem_pitch(w) * h * 2; }
 
-void transform_set_attributes() {
-  cudaFuncSetAttribute(k_fwd_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
-  cudaFuncSetAttribute(k_inv_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
+cudaError_t transform_set_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_tile_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPlaneBytes);
+  return e;
 }
 
 int launch_plan_blocks(const TileDev* d_tiles, int n_tiles, int min_level, BlockDev* d_blocks, cudaStream_t s) {

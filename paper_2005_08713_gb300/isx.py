@@ -29,7 +29,7 @@ EXPORTS = ["isx_create", "isx_destroy", "isx_encode_tiles", "isx_decode_region",
            "isx_get_schedule", "isx_set_schedule", "isx_autotune", "isx_plan_encode", "isx_plan_decode",
            "isx_plan_launch_encode", "isx_plan_launch_decode", "isx_plan_sync_status", "isx_plan_device_bytes",
            "isx_plan_launch_count", "isx_plan_last_error", "isx_plan_destroy", "isx_decode_jobs_scratch",
-           "isx_reserve_scratch", "isx_scratch_bytes"]
+           "isx_reserve_scratch", "isx_scratch_bytes", "isx_decode_path"]
 
 SIZE_CLASSES = 5
 
@@ -164,8 +164,20 @@ def load(build_if_missing: bool = True):
         lib.isx_reserve_scratch.restype = st
         lib.isx_scratch_bytes.argtypes = [vp]
         lib.isx_scratch_bytes.restype = sz
+        lib.isx_decode_path.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_double)]
+        lib.isx_decode_path.restype = i32
         _lib = lib
         return lib
+
+
+def decode_path(tile: Tile, level: int = 0, drop_lsb_planes: int = 0):
+    """(path, bound) of isx_decode_path: path 1 = fused int16 inverse, 0 = global int32 inverse,
+    -1 = invalid; bound = proven magnitude bound of the inverse's values (host computation only)."""
+    lib = load()
+    desc = tile.to_c()
+    b = ctypes.c_double(0.0)
+    path = int(lib.isx_decode_path(ctypes.byref(desc), level, drop_lsb_planes, ctypes.byref(b)))
+    return path, float(b.value)
 
 
 def encode_tile_static(tile: Tile, out, stream=None) -> int:

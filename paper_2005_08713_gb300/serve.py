@@ -80,6 +80,7 @@ class Request:
     buf: object = None        # the pooled output buffer `out` views
     jobs: object = None
     result: object = None     # host copy of the output (Server(keep_outputs=True))
+    error: object = None      # status name when the decode of this request reported a data error
 
 
 @dataclass
@@ -207,6 +208,19 @@ class Server:
             batch.append(r)
         return batch
 
+    def _isolate_failures(self, slot: _Slot, batch):
+        """A batch whose decode reported a data error (a corrupt stream, a capacity or consistency
+        status): each of its decoded requests is decoded again alone on the slot, so that only the
+        requests whose own decode fails get `error` set; the others keep a correct result."""
+        for r in batch:
+            if r.jobs is None or not len(r.jobs):
+                continue
+            p = self.pyr[r.pyramid]
+            slot.codec.decode_jobs_array(p.stream, p.offsets, p.tiles, r.jobs, r.z, 0, slot.stream)
+            st = slot.codec.sync_status(slot.stream)
+            if st != 0:
+                r.error = isx.STATUS_NAMES.get(st, st)
+
     # ------------------------------------------------------------ the loop
     def run(self, requests):
         """Serves requests (sorted by arrival, seconds from now); returns them with `done` set."""
@@ -222,6 +236,9 @@ class Server:
             progressed = False
             for s in self.slots:
                 if s.busy and s.event.query():
+                    # the stream is idle: reading the slot's device status word costs no wait
+                    if s.codec.sync_status(s.stream) != 0:
+                        self._isolate_failures(s, s.batch)
                     t = time.perf_counter() - t0
                     for r in s.batch:
                         r.done = t

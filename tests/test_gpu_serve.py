@@ -77,3 +77,34 @@ def test_server_admission_refuses_a_request_beyond_the_slot_budget(synth):
         srv.run(reqs)
     srv.close()
     codec.close()
+
+
+def test_served_request_over_a_corrupt_tile_alone_reports_an_error(synth):
+    """One tile's stream scrambled on the device: the requests that meet it report ISX_ERR_CORRUPT,
+    every other request of the same batches still equals its decode alone."""
+    from paper_2005_08713_gb300 import isx, serve
+    torch = torch_cuda()
+    codec = isx.Codec(0)
+    p, streams, grid = _pyramid(codec, synth, True, W=2048, H=1024)
+    offs = p.offsets.cpu().numpy()
+    bad = 9                                                # grid 8 x 4: pixels (256..511, 256..511) at level 0
+    ref_stream = p.stream.clone()
+    p.stream[int(offs[bad]) + 40:int(offs[bad + 1])] ^= 0x5A
+    rects = [(0, 0, 200, 150), (300, 300, 200, 150), (1200, 700, 200, 150), (600, 40, 200, 150),
+             (250, 250, 20, 20), (1800, 800, 200, 150)]
+    reqs = [serve.Request(i, 0.0, 0, 0, r) for i, r in enumerate(rects)]
+    srv = serve.Server([p], slots=1, max_batch=8, scratch_budget=64 << 20, out_shape=(150, 200), keep_outputs=True)
+    done = srv.run(reqs)
+    srv.close()
+    assert len(srv.batch_sizes) == 1
+    for r in done:
+        meets = bad in set(p.tiles_meeting(0, *r.rect).tolist())
+        assert (r.error == "ISX_ERR_CORRUPT") == meets, (r.rid, r.error)
+        if not meets:
+            rx, ry, rw, rh = r.rect
+            alone = torch.zeros((rh, rw, 3), dtype=torch.uint8, device="cuda")
+            codec.decode_region(ref_stream, p.offsets, p.tiles, 0, r.rect, alone)
+            assert codec.sync_status() == 0
+            assert np.array_equal(r.result, alone.cpu().numpy()), r.rid
+    assert sum(r.error is not None for r in done) == 2
+    codec.close()

@@ -1,0 +1,191 @@
+"""The int16 range bound behind the fused transforms (CPU).
+
+The fused shared-memory kernels hold every sample of the 5/3 lifting
+(Sec. 4) in int16.  The library decides per tile whether a decode may take
+that path (isx_decode_path) from a bound made of
+  - the forward transform's range: 2-D L1 gain of the iterated analysis
+    filters x the sample range, plus the floors' rounding, and
+  - the deviation the quantiser steps (Sec. 3) and dropped planes (Sec. 4,
+    "Decompression") carry through the synthesis.
+These tests recompute the constants of that bound from the filters, check
+that symmetric extension at the ends of finite lines never exceeds them,
+check the library's routing on the workloads' settings, and compare the
+bound with the largest values the oracle's int64 synthesis reaches on
+adversarial tiles."""
+import numpy as np
+import pytest
+
+GAIN_2D = 4.17            # the library's constants (isx_api.cu)
+ROUND_PER_LEVEL = 16.0
+LO_1D, HI_1D = 1.73, 2.885   # bounds of the finite-line 1-D cascade gains behind them
+
+
+def cascade_l1(levels=15):
+    """L1 norms of the equivalent analysis filters of 1..levels iterated 5/3 levels (infinite line):
+    (low cascade, high after the low cascade)."""
+    h = np.array([-1, 2, 6, 2, -1]) / 8.0      # 5/3 analysis low-pass (linear part of predict + update)
+    g = np.array([-1, 2, -1]) / 2.0            # 5/3 analysis high-pass (predict)
+    cur = np.array([1.0])
+    lo_l1, hi_l1 = [1.0], [1.0]
+    for j in range(1, levels + 1):
+        up = np.zeros(2 ** (j - 1) * 4 + 1); up[:: 2 ** (j - 1)] = h
+        upg = np.zeros(2 ** (j - 1) * 2 + 1); upg[:: 2 ** (j - 1)] = g
+        lo, hi = np.convolve(cur, up), np.convolve(cur, upg)
+        lo_l1.append(np.abs(lo).sum())
+        hi_l1.append(np.abs(hi).sum())
+        cur = lo
+    return lo_l1, hi_l1
+
+
+def two_d_worst(lo, hi):
+    """Largest 2-D gain / 2 over every level and pass, from 1-D cascade gains lo[k], hi[k]."""
+    worst = 0.0
+    for k in range(1, len(lo)):
+        a_lo, a_hi = lo[k], hi[k]
+        # the row pass sees the low cascade of this level (after it) or of the previous one (before it)
+        for a, az in ((a_lo, False), (a_hi, True)):
+            for b, bz in ((lo[k - 1], False), (lo[k], False), (a_hi, True)):
+                # zero-sum weights on [0, M] reach M * L1 / 2; a low (x) low pair reaches M * (L1a * L1b + 1) / 2
+                worst = max(worst, a * b / 2 if (az or bz) else (a * b + 1) / 2)
+    return worst
+
+
+def test_gain_constant_covers_every_level_and_pass():
+    lo, hi = cascade_l1()
+    assert 4.11 < two_d_worst(lo, hi) < GAIN_2D          # infinite line
+    assert two_d_worst([1.0] + [LO_1D] * 15, [1.0] + [HI_1D] * 15) <= GAIN_2D
+    assert max(lo) < LO_1D and max(hi) < HI_1D
+
+
+def test_rounding_constant():
+    lo, hi = cascade_l1()
+    # largest 2-D gain from an LL deviation to any later state: a low cascade then one (lo|hi) x (lo|hi) pass
+    g = max(LO_1D, HI_1D) ** 2
+    assert g <= 8.33
+    # per level the floors add at most 1.875 to the LL (predict 1/2, update 3/4; columns then rows)
+    inject = 1.5 * 0.75 + 0.75
+    assert inject == 1.875 and inject * 8.33 <= ROUND_PER_LEVEL
+
+
+def mirror_idx(i, n):
+    """Whole-sample symmetric index into [0, n) (vectorised)."""
+    if n == 1:
+        return np.zeros_like(i)
+    p = 2 * (n - 1)
+    i = np.abs(i) % p
+    return np.where(i >= n, p - i, i)
+
+
+def lifting_level(X):
+    """One level of the linear 5/3 lifting with whole-sample symmetric extension applied to the rows of X
+    (each row a weight vector over the input samples): returns (low rows, high rows)."""
+    m = X.shape[0]
+    nl, nh = (m + 1) // 2, m // 2
+    k = np.arange(nh)
+    d = X[mirror_idx(2 * k + 1, m)] - (X[mirror_idx(2 * k, m)] + X[mirror_idx(2 * k + 2, m)]) / 2
+    j = np.arange(nl)
+    if nh == 0:
+        return X[2 * j], d
+
+    def D(i):  # the high-pass sequence mirrors with the signal: d at odd position q equals d at the mirror of q
+        return d[(mirror_idx(2 * i + 1, m) - 1) // 2]
+    return X[2 * j] + (D(j - 1) + D(j)) / 4, d
+
+
+def finite_gains(n, levels):
+    lo, hi = [], []
+    X = np.eye(n)
+    for _ in range(levels):
+        if X.shape[0] < 2:
+            break
+        X, d = lifting_level(X)
+        hi.append(np.abs(d).sum(1).max())
+        lo.append(np.abs(X).sum(1).max())
+    return lo, hi
+
+
+def test_finite_lines_stay_below_the_1d_constants():
+    """Symmetric extension at the ends of a finite line adds up to ~0.3 % to the infinite-line gains;
+    every length up to 600 at every level, and sampled lengths up to 2100 (the exhaustive run up to
+    2100 at 11 levels peaks at 1.7200 / 2.8721)."""
+    top_lo = top_hi = 0.0
+    for n in list(range(2, 601)) + [1023, 1024, 1025, 1537, 2047, 2100]:
+        lo, hi = finite_gains(n, 11)
+        top_lo, top_hi = max(top_lo, max(lo)), max(top_hi, max(hi))
+    assert top_lo < LO_1D and top_hi < HI_1D
+    assert top_lo > 1.7157      # the boundary effect is real: the infinite-line low gain (1.71557) is exceeded
+
+
+def test_forward_range_fits_int16_at_every_accepted_setting():
+    # 12-bit mono and 8-bit RGB chroma (range 510), up to 15 levels
+    for rng in (4095, 510):
+        assert rng * GAIN_2D + 2 + ROUND_PER_LEVEL * 15 < 32767
+
+
+def test_library_routing_on_the_workloads():
+    from paper_2005_08713_gb300 import isx
+    q3 = (3, 2, 1, 0, 0, 0, 0, 0, 0)
+    # slide tiles (256 x 256 RGB8, 8 levels), lossy and lossless: fused
+    for q in ((), q3):
+        path, bound = isx.decode_path(isx.Tile(256, 256, 3, 8, 8, q), 0, 0)
+        assert path == 1 and bound < 32767
+    # mixed-batch mono12 tiles with the lossy steps, every level
+    for L in range(2, 7):
+        for z in range(L + 1):
+            assert isx.decode_path(isx.Tile(256, 200, 1, 12, L, q3[:L] + (0,)), z, 0)[0] == 1
+    # 12-bit tiles lossless at up to 10 levels (the largest fused planes)
+    assert isx.decode_path(isx.Tile(283, 283, 1, 12, 10), 0, 0)[0] == 1
+    # huge steps on every level: the deviation can leave int16, so the global inverse
+    assert isx.decode_path(isx.Tile(256, 256, 1, 12, 6, (12,) * 7), 0, 0)[0] == 0
+    # planes too large for shared memory: global at level 0, fused at a coarser level
+    assert isx.decode_path(isx.Tile(512, 512, 3, 8, 3), 0, 0)[0] == 0
+    assert isx.decode_path(isx.Tile(512, 512, 3, 8, 3), 1, 0)[0] == 1
+    # more dropped planes: larger deviation, never a smaller bound
+    b = [isx.decode_path(isx.Tile(256, 256, 1, 12, 6, (4,) * 7), 0, k)[1] for k in range(6)]
+    assert all(x <= y for x, y in zip(b, b[1:]))
+    # invalid descriptors and levels
+    assert isx.decode_path(isx.Tile(256, 256, 2, 8, 3), 0, 0)[0] == -1
+    assert isx.decode_path(isx.Tile(256, 256, 1, 8, 3), 4, 0)[0] == -1
+
+
+def _synthesis_max(orc, coef, w, h, L, z):
+    """Largest |value| the int64 inverse reaches after each 1-D pass (rows then columns per level),
+    from the oracle's own 1-D inverse lifting, on one channel plane in Mallat layout."""
+    a = coef.astype(np.int64).copy()
+    top = int(np.abs(a).max())
+    dims = [(w, h)]
+    for _ in range(L):
+        dims.append(((dims[-1][0] + 1) // 2, (dims[-1][1] + 1) // 2))
+    for lv in range(L, z, -1):
+        cw, ch = dims[lv - 1]
+        if cw >= 2:
+            for y in range(ch):
+                nl = (cw + 1) // 2
+                a[y, :cw] = orc.lift53_inverse(a[y, :nl], a[y, nl:cw])
+        top = max(top, int(np.abs(a[:ch, :cw]).max()))
+        if ch >= 2:
+            for x in range(cw):
+                nl = (ch + 1) // 2
+                a[:ch, x] = orc.lift53_inverse(a[:nl, x], a[nl:ch, x])
+        top = max(top, int(np.abs(a[:ch, :cw]).max()))
+    return top
+
+
+@pytest.mark.parametrize("qlog", [0, 4, 8, 9, 12])
+def test_bound_holds_on_adversarial_tiles(orc, qlog):
+    from paper_2005_08713_gb300 import isx
+    w = h = 64
+    L = 6
+    yy, xx = np.indices((h, w))
+    rng = np.random.default_rng(5)
+    pats = [((yy + xx) % 2) * 4095, ((xx % 2) * 4095), ((yy // 3) % 2) * 4095, rng.integers(0, 2, (h, w)) * 4095]
+    q = (qlog,) * (L + 1)
+    delta = 1 << qlog
+    for p in pats:
+        img = p.astype(np.uint16)
+        cq = orc.tile_coefficients(img, L, 12, q)[0]
+        deq = np.sign(cq) * (np.abs(cq) * delta + delta // 2) * (cq != 0)
+        for z in (0, 2):
+            top = _synthesis_max(orc, deq, w, h, L, z)
+            bound = isx.decode_path(isx.Tile(w, h, 1, 12, L, q), z, 0)[1]
+            assert top <= bound, (qlog, z, top, bound)

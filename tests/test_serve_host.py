@@ -92,6 +92,18 @@ class _FakeCodec:
         self.calls += 1
         return self.per_tile * len(jobs)
 
+    # the device status word: a batch containing a job of a tile in `bad` reports ISX_ERR_CORRUPT
+    bad = frozenset()
+    pending = 0
+
+    def decode_jobs_array(self, stream_buf, offsets, tiles, jobs, level=0, drop_lsb_planes=0, stream=None):
+        if any(int(t) in self.bad for t in jobs["tile"]):
+            self.pending = 3
+
+    def sync_status(self, stream=None):
+        st, self.pending = self.pending, 0
+        return st
+
 
 class _FakeEvent:
     def __init__(self, polls):
@@ -117,6 +129,9 @@ def _fake_server(pyrs, slots=2, max_batch=4, budget=10_000, pool=8, per_tile=100
 
     def launch(slot, batch):
         srv.launched.append([r.rid for r in batch])
+        for r in batch:
+            if r.jobs is not None and len(r.jobs):
+                slot.codec.decode_jobs_array(None, None, None, r.jobs, r.z)
         slot.batch, slot.event, slot.busy = batch, _FakeEvent(polls), True
     srv._launch = launch
     return srv
@@ -191,3 +206,18 @@ def test_run_serves_every_request_once(slots, max_batch, pool):
     order = [i for b in srv.launched for i in b]
     arrival = {r.rid: r.arrival for r in reqs}
     assert all(arrival[a] <= arrival[b] for a, b in zip(order, order[1:]))
+
+
+def test_run_isolates_a_failed_request_in_its_batch():
+    """A batch whose device status reports a data error: only the request over the bad tile is marked."""
+    pyrs = [_pyramid(2048, 1024, 256, 3)]
+    srv = _fake_server(pyrs, slots=1, max_batch=8, budget=1 << 40, pool=16)
+    bad_tile = 9            # grid 8 x 4: row 1, column 1 (pixels 256..511 at level 0)
+    for s in srv.slots:
+        s.codec.bad = frozenset([bad_tile])
+    reqs = [_req(0, 0.0, rect=(0, 0, 96, 64)), _req(1, 0.0, rect=(300, 300, 96, 64)),
+            _req(2, 0.0, rect=(1200, 700, 96, 64)), _req(3, 0.0, rect=(600, 40, 96, 64))]
+    done = srv.run(reqs)
+    assert len(srv.launched) == 1 and sorted(srv.launched[0]) == [0, 1, 2, 3]
+    errs = {r.rid: r.error for r in done}
+    assert errs == {0: None, 1: "ISX_ERR_CORRUPT", 2: None, 3: None}
