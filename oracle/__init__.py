@@ -32,7 +32,12 @@ def build(force: bool = False) -> str:
 class OrcTile(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("bits", ctypes.c_int32), ("levels", ctypes.c_int32), ("x0", ctypes.c_int32),
-                ("y0", ctypes.c_int32), ("qstep_log2", ctypes.c_uint8 * 16)]
+                ("y0", ctypes.c_int32), ("qstep_log2", ctypes.c_uint8 * 16), ("transform", ctypes.c_int32)]
+
+
+# colour transform selectors of a tile (orc_tile.transform): DEFAULT = RCT for three channels and none
+# otherwise; RCT and YCOCG_R act on channels 0..2 of a tile of three or more channels
+CT_DEFAULT, CT_NONE, CT_RCT, CT_YCOCG_R = 0, 1, 2, 3
 
 
 def _get():
@@ -44,6 +49,8 @@ def _get():
             sig = {
                 "orc_rct_forward": ([vp, i64, vp], None),
                 "orc_rct_inverse": ([vp, i64, vp], None),
+                "orc_ycocg_forward": ([vp, i64, vp], None),
+                "orc_ycocg_inverse": ([vp, i64, vp], None),
                 "orc_lift53_forward": ([vp, i64, vp, vp], None),
                 "orc_lift53_inverse": ([vp, vp, i64, vp], None),
                 "orc_dwt2_forward": ([vp, i64, i64, i32], None),
@@ -74,9 +81,10 @@ def _p(a: np.ndarray):
     return a.ctypes.data
 
 
-def tile_struct(width, height, channels, bits, levels, qstep_log2=(), x0=0, y0=0) -> OrcTile:
+def tile_struct(width, height, channels, bits, levels, qstep_log2=(), x0=0, y0=0, transform=CT_DEFAULT) -> OrcTile:
     t = OrcTile()
     t.width, t.height, t.channels, t.bits, t.levels, t.x0, t.y0 = width, height, channels, bits, levels, x0, y0
+    t.transform = transform
     q = list(qstep_log2) + [0] * (16 - len(qstep_log2))
     for i in range(16):
         t.qstep_log2[i] = q[i]
@@ -95,6 +103,20 @@ def rct_inverse(ycc: np.ndarray) -> np.ndarray:
     a = np.ascontiguousarray(ycc, dtype=np.int64).reshape(-1, 3)
     out = np.empty_like(a)
     _get().orc_rct_inverse(_p(a), a.shape[0], _p(out))
+    return out.reshape(np.shape(ycc))
+
+
+def ycocg_forward(rgb: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(rgb, dtype=np.int64).reshape(-1, 3)
+    out = np.empty_like(a)
+    _get().orc_ycocg_forward(_p(a), a.shape[0], _p(out))
+    return out.reshape(np.shape(rgb))
+
+
+def ycocg_inverse(ycc: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(ycc, dtype=np.int64).reshape(-1, 3)
+    out = np.empty_like(a)
+    _get().orc_ycocg_inverse(_p(a), a.shape[0], _p(out))
     return out.reshape(np.shape(ycc))
 
 
@@ -198,11 +220,11 @@ def _pixels(img: np.ndarray):
     return a, a.strides[0]
 
 
-def tile_coefficients(img: np.ndarray, levels: int, bits: int, qstep_log2=()) -> np.ndarray:
+def tile_coefficients(img: np.ndarray, levels: int, bits: int, qstep_log2=(), transform=CT_DEFAULT) -> np.ndarray:
     a, pitch = _pixels(img)
     h, w = a.shape[:2]
     C = 1 if a.ndim == 2 else a.shape[2]
-    t = tile_struct(w, h, C, bits, levels, qstep_log2)
+    t = tile_struct(w, h, C, bits, levels, qstep_log2, transform=transform)
     out = np.zeros((C, h, w), np.int64)
     rc = _get().orc_tile_coefficients(ctypes.byref(t), _p(a), pitch, _p(out))
     if rc != 0:
@@ -210,11 +232,11 @@ def tile_coefficients(img: np.ndarray, levels: int, bits: int, qstep_log2=()) ->
     return out
 
 
-def encode_tile(img: np.ndarray, levels: int, bits: int, qstep_log2=()) -> bytes:
+def encode_tile(img: np.ndarray, levels: int, bits: int, qstep_log2=(), transform=CT_DEFAULT) -> bytes:
     a, pitch = _pixels(img)
     h, w = a.shape[:2]
     C = 1 if a.ndim == 2 else a.shape[2]
-    t = tile_struct(w, h, C, bits, levels, qstep_log2)
+    t = tile_struct(w, h, C, bits, levels, qstep_log2, transform=transform)
     cap = 4096 + a.nbytes * 4
     while True:
         out = np.zeros(cap, np.uint8)

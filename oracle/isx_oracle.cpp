@@ -99,6 +99,25 @@ void rct_inverse(int64_t Y, int64_t Cb, int64_t Cr, int64_t* R, int64_t* G, int6
   *B = Cb + *G;
 }
 
+// The alternative reversible colour transform the build also offers:
+// YCoCg-R (Malvar and Sullivan, "YCoCg-R: A Color Space with RGB
+// Reversibility and Low Dynamic Range", JVT-I014, 2003), two lifting steps
+// per chroma pair:
+//   Co = R - B,  t = B + floor(Co / 2),  Cg = G - t,  Y = t + floor(Cg / 2)
+void ycocg_forward(int64_t R, int64_t G, int64_t B, int64_t* Y, int64_t* Co, int64_t* Cg) {
+  *Co = R - B;
+  const int64_t t = B + floordiv(*Co, 2);
+  *Cg = G - t;
+  *Y = t + floordiv(*Cg, 2);
+}
+//   t = Y - floor(Cg / 2),  G = Cg + t,  B = t - floor(Co / 2),  R = B + Co
+void ycocg_inverse(int64_t Y, int64_t Co, int64_t Cg, int64_t* R, int64_t* G, int64_t* B) {
+  const int64_t t = Y - floordiv(Cg, 2);
+  *G = Cg + t;
+  *B = t - floordiv(Co, 2);
+  *R = *B + Co;
+}
+
 // ------------------------------------------- 5/3 Le Gall integer lifting (Sec. 4)
 // Reading: the reversible 5/3 of ISO/IEC 15444-1 Annex F with whole-sample
 // symmetric extension, even-indexed samples low-pass:
@@ -645,7 +664,8 @@ int decode_block(const uint8_t* data, int64_t size, Block& blk, int drop) {
 // Byte layout of a tile stream (the paper defines only the block, Fig. 3):
 //   0  'I' 'S' 'X' '1'
 //   4  u16 width        6  u16 height
-//   8  u8 channels      9  u8 bits     10 u8 levels   11 u8 colour transform (1 = RCT)
+//   8  u8 channels      9  u8 bits     10 u8 levels
+//  11  u8 colour transform of channels 0..2 (0 none, 1 RCT, 2 YCoCg-R)
 //  12  u32 n_blocks
 //  16  u8 qstep_log2[16]   (index l-1 for level l, index `levels` for the LL)
 //  32  u32 block_end[n_blocks]  (cumulative byte ends, relative to the block data)
@@ -743,18 +763,21 @@ void put_u32(uint8_t* p, uint32_t v) { for (int i = 0; i < 4; ++i) p[i] = (uint8
 uint32_t get_u16(const uint8_t* p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
 uint32_t get_u32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i); return v; }
 
-// Forward transform + quantisation of one tile into C Mallat planes.
+// Forward transform + quantisation of one tile into C Mallat planes.  The
+// colour transform (Fig. 1, "optional") acts on channels 0..2; any further
+// channels (and every channel of a tile without one) are coded as they are
+// (Sec. 3: "an arbitrary number of channels").
 std::vector<std::vector<int64_t>> tile_coefficients(const TileInfo& ti, const void* px, int64_t pitch) {
   std::vector<std::vector<int64_t>> planes(ti.C, std::vector<int64_t>((size_t)ti.w * ti.h));
   for (int64_t y = 0; y < ti.h; ++y)
     for (int64_t x = 0; x < ti.w; ++x) {
-      if (ti.ct == 1) {
-        int64_t Y, Cb, Cr;
-        rct_forward(pixel_at(px, pitch, ti.bits, 3, x, y, 0), pixel_at(px, pitch, ti.bits, 3, x, y, 1),
-                    pixel_at(px, pitch, ti.bits, 3, x, y, 2), &Y, &Cb, &Cr);
-        planes[0][y * ti.w + x] = Y; planes[1][y * ti.w + x] = Cb; planes[2][y * ti.w + x] = Cr;
-      } else {
-        for (int c = 0; c < ti.C; ++c) planes[c][y * ti.w + x] = pixel_at(px, pitch, ti.bits, ti.C, x, y, c);
+      for (int c = 0; c < ti.C; ++c) planes[c][y * ti.w + x] = pixel_at(px, pitch, ti.bits, ti.C, x, y, c);
+      if (ti.ct != 0) {
+        const int64_t R = planes[0][y * ti.w + x], G = planes[1][y * ti.w + x], B = planes[2][y * ti.w + x];
+        int64_t a, b, c;
+        if (ti.ct == 1) rct_forward(R, G, B, &a, &b, &c);
+        else ycocg_forward(R, G, B, &a, &b, &c);
+        planes[0][y * ti.w + x] = a; planes[1][y * ti.w + x] = b; planes[2][y * ti.w + x] = c;
       }
     }
   for (int c = 0; c < ti.C; ++c) {
@@ -779,7 +802,8 @@ std::vector<std::vector<int64_t>> tile_coefficients(const TileInfo& ti, const vo
 
 bool tile_info_valid(const TileInfo& ti) {
   if (ti.w < 1 || ti.w > 65535 || ti.h < 1 || ti.h > 65535) return false;
-  if (!(ti.C == 1 || ti.C == 3)) return false;
+  if (ti.C < 1 || ti.C > 16) return false;
+  if (ti.ct < 0 || ti.ct > 2 || (ti.ct != 0 && ti.C < 3)) return false;
   if (ti.bits < 1 || ti.bits > 16) return false;
   if (ti.L < 0 || ti.L > 15) return false;
   for (int l = 0; l <= ti.L; ++l) if (ti.q[l] > 15) return false;
@@ -870,12 +894,10 @@ int decode_tile(const uint8_t* s, int64_t size, int z, int drop, void* out, int6
   int64_t maxv = ((int64_t)1 << ti.bits) - 1;
   for (int64_t y = 0; y < zh; ++y)
     for (int64_t x = 0; x < zw; ++x) {
-      int64_t v[3];
-      if (ti.ct == 1) {
-        rct_inverse(planes[0][y * ti.w + x], planes[1][y * ti.w + x], planes[2][y * ti.w + x], &v[0], &v[1], &v[2]);
-      } else {
-        for (int c = 0; c < ti.C; ++c) v[c] = planes[c][y * ti.w + x];
-      }
+      int64_t v[16];
+      for (int c = 0; c < ti.C; ++c) v[c] = planes[c][y * ti.w + x];
+      if (ti.ct == 1) rct_inverse(v[0], v[1], v[2], &v[0], &v[1], &v[2]);
+      else if (ti.ct == 2) ycocg_inverse(v[0], v[1], v[2], &v[0], &v[1], &v[2]);
       for (int c = 0; c < ti.C; ++c) {
         int64_t q = std::min(std::max(v[c], (int64_t)0), maxv);
         uint8_t* row = (uint8_t*)out + y * pitch;
@@ -892,15 +914,18 @@ int decode_tile(const uint8_t* s, int64_t size, int z, int drop, void* out, int6
 // Used through ctypes by the tests and the benchmark's CPU-baseline leg.
 extern "C" {
 
+// transform: 0 = RCT for three channels and none otherwise, 1 = none,
+// 2 = RCT, 3 = YCoCg-R (2 and 3 on channels 0..2 of a tile of 3 or more).
 typedef struct {
   int32_t width, height, channels, bits, levels, x0, y0;
   uint8_t qstep_log2[16];
+  int32_t transform;
 } orc_tile;
 
 static TileInfo to_info(const orc_tile* t) {
   TileInfo ti;
   ti.w = t->width; ti.h = t->height; ti.C = t->channels; ti.bits = t->bits; ti.L = t->levels;
-  ti.ct = t->channels == 3 ? 1 : 0;
+  ti.ct = t->transform == 0 ? (t->channels == 3 ? 1 : 0) : t->transform == 1 ? 0 : t->transform == 2 ? 1 : t->transform == 3 ? 2 : -1;
   for (int i = 0; i < 16; ++i) ti.q[i] = i <= t->levels ? t->qstep_log2[i] : 0;
   return ti;
 }
@@ -911,6 +936,12 @@ void orc_rct_forward(const int64_t* rgb, int64_t n, int64_t* ycc) {
 }
 void orc_rct_inverse(const int64_t* ycc, int64_t n, int64_t* rgb) {
   for (int64_t i = 0; i < n; ++i) rct_inverse(ycc[3 * i], ycc[3 * i + 1], ycc[3 * i + 2], &rgb[3 * i], &rgb[3 * i + 1], &rgb[3 * i + 2]);
+}
+void orc_ycocg_forward(const int64_t* rgb, int64_t n, int64_t* ycc) {
+  for (int64_t i = 0; i < n; ++i) ycocg_forward(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], &ycc[3 * i], &ycc[3 * i + 1], &ycc[3 * i + 2]);
+}
+void orc_ycocg_inverse(const int64_t* ycc, int64_t n, int64_t* rgb) {
+  for (int64_t i = 0; i < n; ++i) ycocg_inverse(ycc[3 * i], ycc[3 * i + 1], ycc[3 * i + 2], &rgb[3 * i], &rgb[3 * i + 1], &rgb[3 * i + 2]);
 }
 void orc_lift53_forward(const int64_t* x, int64_t n, int64_t* low, int64_t* high) { lift53_forward(x, n, low, high); }
 void orc_lift53_inverse(const int64_t* low, const int64_t* high, int64_t n, int64_t* x) { lift53_inverse(low, high, n, x); }
