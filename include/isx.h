@@ -46,24 +46,36 @@ typedef enum {
   ISX_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up */
 } isx_status;
 
+/* Colour transform of a tile (the paper's "optional colorspace
+ * transformation", Fig. 1; Sec. 3 allows any number of channels):
+ * ISX_CT_DEFAULT applies the JPEG 2000 RCT to three-channel tiles and no
+ * transform otherwise; ISX_CT_RCT and ISX_CT_YCOCG_R (Malvar and Sullivan's
+ * reversible YCoCg-R) transform channels 0..2 of a tile of 3 or more
+ * channels, the other channels are coded as they are. */
+#define ISX_CT_DEFAULT 0
+#define ISX_CT_NONE 1
+#define ISX_CT_RCT 2
+#define ISX_CT_YCOCG_R 3
+
 /* One tile: an independent rectangle of an image, transformed on its own.
  * pixels: DEVICE pointer, interleaved HWC samples, uint8 when bits <= 8 and
- * uint16 otherwise, rows `row_pitch_bytes` apart.  channels = 3 applies the
- * reversible colour transform (JPEG 2000 RCT; the paper's "optional
- * colorspace transformation", Fig. 1); channels = 1 codes the samples as is.
- * qstep_log2[l-1] is the quantiser step 2^q of wavelet level l (l = 1 is the
- * finest), qstep_log2[levels] the step of the LL band; all 0 = lossless.
- * x0, y0 place the tile in the image (level-0 pixels) for region decodes.
- * A field outside its stated range is an argument error (ISX_ERR_ARG). */
+ * uint16 otherwise, rows `row_pitch_bytes` apart.  `transform` selects the
+ * colour transform (ISX_CT_*).  qstep_log2[l-1] is the quantiser step 2^q
+ * of wavelet level l (l = 1 is the finest), qstep_log2[levels] the step of
+ * the LL band; all 0 = lossless.  x0, y0 place the tile in the image
+ * (level-0 pixels) for region decodes.  A field outside its stated range is
+ * an argument error (ISX_ERR_ARG). */
 typedef struct {
   int32_t width, height;   /* 1 .. 65535 */
-  int32_t channels;        /* 1 or 3 */
-  int32_t bits;            /* significant bits per sample, 1 .. 16 (3 channels: 1 .. 8) */
+  int32_t channels;        /* 1 .. 16 */
+  int32_t bits;            /* significant bits per sample, 1 .. 16 */
   int32_t levels;          /* wavelet levels, 0 .. 15 */
   int32_t x0, y0;          /* tile origin in the image, >= 0 */
   uint8_t qstep_log2[16];  /* 0 .. 15 each */
   const void* pixels;      /* device pointer (ignored by decode calls) */
   int64_t row_pitch_bytes;
+  int32_t transform;       /* ISX_CT_DEFAULT .. ISX_CT_YCOCG_R; RCT and YCoCg-R need channels >= 3 */
+  int32_t reserved;        /* 0 */
 } isx_tile_desc;
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the
@@ -86,7 +98,8 @@ void isx_destroy(isx_ctx* ctx);
  *                  written to d_out, [n_tiles] receives the capacity it
  *                  needs and isx_sync_status returns ISX_ERR_CAPACITY.
  * Tile stream layout (little endian): "ISX1", u16 width, u16 height,
- * u8 channels, u8 bits, u8 levels, u8 colour transform (1 = RCT),
+ * u8 channels, u8 bits, u8 levels, u8 colour transform of channels 0..2
+ * (0 none, 1 RCT, 2 YCoCg-R),
  * u32 n_blocks, u8 qstep_log2[16], u32 block_end[n_blocks], block data.
  * Blocks: per channel the LL blocks, then the high-pass blocks of levels
  * L .. 1, each subband cut into 128 x 128 cells in raster order.  The bytes
@@ -174,7 +187,7 @@ const char* isx_last_error(isx_ctx* ctx);
  * deviation the tile's quantiser steps and the dropped planes can carry
  * through the synthesis.  The fused inverse is taken only when the tile
  * fits its shared-memory plane (width and height at level `level` up to
- * 1024, bits <= 12, plane <= 160 KB) and the bound is at most 32767. */
+ * 1024, plane <= 160 KB) and the bound is at most 32767. */
 int32_t isx_decode_path(const isx_tile_desc* tile, int32_t level, int32_t drop_lsb_planes, double* h_bound);
 
 /* ------------------------------------------------------------------------
@@ -222,8 +235,9 @@ isx_status isx_reserve_scratch(isx_ctx* ctx, size_t bytes);
 size_t isx_scratch_bytes(isx_ctx* ctx);
 
 /* Fused transform schedule.  Tiles whose int16 channel plane fits in shared
- * memory (width and height <= 1024, bits <= 12, plane <= 160 KB) are
- * transformed by one CTA per tile and channel; they are grouped in
+ * memory (width and height <= 1024, plane <= 160 KB) and whose samples keep
+ * every coefficient inside int16 (see isx_decode_path) are transformed by
+ * one CTA per tile and channel; they are grouped in
  * ISX_SIZE_CLASSES classes by plane size (<= 4 KB, 16 KB, 48 KB, 96 KB,
  * 160 KB) and each class launches with its own threads per CTA (256, 512
  * or 1024) for the forward and the inverse transform. */
@@ -300,8 +314,8 @@ void isx_plan_destroy(isx_plan* plan);
  * ISX_STATIC_SCRATCH_BYTES per device, reserved when the library's device
  * code is loaded.  A tile whose working set exceeds it is rejected before
  * anything is enqueued with ISX_ERR_OOM and a message giving both sizes;
- * every tile of at most 512 x 512 pixels fits, at any channel count, bit
- * depth and level count.
+ * every tile of at most 512 x 512 pixels and 4 channels fits, at any bit
+ * depth, colour transform and level count.
  * The first call on each device does the set-up: it looks up the array's
  * device address (cudaGetSymbolAddress, with that device current) and sets
  * the kernels' shared-memory attributes; make that first call before any

@@ -180,64 +180,30 @@ isx_status ensure_staging(isx_ctx* ctx, size_t n) {
   return ISX_OK;
 }
 
-// Bound on every value the fused inverse holds in its int16 plane for a tile
-// decoded at level z with `drop` least significant planes discarded (Sec. 4,
-// "Decompression"), for streams written by the encoder.  Each state of the
-// inverse is a state of the lossless inverse (= a state of the forward
-// transform of the original samples, by perfect reconstruction) plus a
-// deviation caused by the dequantised coefficients.
-//  - Forward states: for samples in [0, M] (a mono plane or Y) or [-M, M]
-//    (RCT chroma, counted as a range of 2M), the linear 5/3 lifting reaches
-//    at most kGain2D * range.  kGain2D comes from the L1 norms of the
-//    equivalent filters of up to 15 iterated levels, taken on finite lines
-//    with symmetric extension at both ends (at most 1.720 for the low and
-//    2.873 for the high cascades; the infinite line gives 1.716 and 2.867),
-//    rounded up to 1.73 and 2.885: 2.885^2 / 2 <= 4.17.  The floors of the
-//    integer lifting add at most 2 inside a level and 1.875 to each LL,
-//    carried on by the linear filters with a 2-D gain of at most
-//    2.885^2 <= 8.33: kRoundPerLevel per level.
-//  - Deviation: a band sample of step D = 2^q decoded with k planes dropped
-//    is off by at most 2^k D - 1 (and never by more than F + D/2).  One
-//    inverse level maps deviations (LL, HL, LH, HH) to at most
-//    LL + HL + LH + HH + 6 (the 5/3 synthesis has L-inf gain 1 on each band
-//    pair; three passes, each floor off by less than 1), and a level whose
-//    inputs are all exact adds nothing.
-// Tiles for which F + deviation exceeds int16 take the int32 global inverse.
-constexpr double kGain2D = 4.17;
-constexpr double kRoundPerLevel = 16.0;   // >= 1.875 * 8.33
-double int16_state_bound(const isx_tile_desc& t, int z, int drop) {
-  const double M = (double)((1 << t.bits) - 1) * (t.channels == 3 ? 2.0 : 1.0);
-  const double F = M * kGain2D + 2.0 + kRoundPerLevel * t.levels;
-  auto dev = [&](int q) {
-    const double D = std::ldexp(1.0, q);
-    return std::min(std::ldexp(D, std::min(drop, 40)) - 1.0, F + D / 2);
-  };
-  double E = dev(t.qstep_log2[t.levels]);
-  for (int l = t.levels; l > z; --l) {
-    const double e = dev(t.qstep_log2[l - 1]);
-    if (E > 0 || e > 0) E += 3.0 * e + 6.0;
-  }
-  return F + E;
-}
-bool fused_inverse_fits_int16(const isx_tile_desc& t, int z, int drop) { return int16_state_bound(t, z, drop) <= 32767.0; }
+bool fused_inverse_fits_int16(const isx_tile_desc& t, int z, int drop) { return inverse_state_bound(t, z, drop) <= 32767.0; }
 
 // Tiles of the fused path grouped by size class: task[] lists them class by
 // class; each class launches with its own plane size and thread count.
 struct FusedClass {
-  int begin = 0, count = 0, smem = 0, threads = 256;
+  int begin = 0, count = 0, smem = 0, threads = 256, slots = 1;   // slots: CTAs per tile, the class's most channels
 };
 
-void group_fused(const std::vector<std::pair<int32_t, int>>& fused /* (task, plane bytes) */, const int* threads, int32_t* task,
-                 FusedClass* cls) {
+struct FusedTask {
+  int32_t task;
+  int plane_bytes, channels;
+};
+
+void group_fused(const std::vector<FusedTask>& fused, const int* threads, int32_t* task, FusedClass* cls) {
   int pos = 0;
   for (int k = 0; k < ISX_SIZE_CLASSES; ++k) {
     cls[k] = FusedClass();
     cls[k].begin = pos;
     cls[k].threads = threads[k];
     for (const auto& f : fused) {
-      if (class_of(f.second) != k) continue;
-      task[pos++] = f.first;
-      cls[k].smem = std::max(cls[k].smem, f.second);
+      if (class_of(f.plane_bytes) != k) continue;
+      task[pos++] = f.task;
+      cls[k].smem = std::max(cls[k].smem, f.plane_bytes);
+      cls[k].slots = std::max(cls[k].slots, f.channels);
     }
     cls[k].count = pos - cls[k].begin;
   }
@@ -247,7 +213,7 @@ void group_fused(const std::vector<std::pair<int32_t, int>>& fused /* (task, pla
 struct EncodeLayout {
   int32_t n_tiles = 0;
   int64_t n_blocks = 0, coef_bytes = 0, plane_total = 0, sym_bytes = 0;
-  int max_levels = 0, max_dim = 1, n_fused = 0;
+  int max_levels = 0, max_dim = 1, max_c = 1, n_fused = 0;
   FusedClass cls[ISX_SIZE_CLASSES];
   int64_t level_blocks[16] = {};
   int level_quads[16] = {};
@@ -261,7 +227,7 @@ isx_status plan_encode(const isx_tile_desc* tiles, int32_t n, bool allow_fused, 
                        EncodeLayout& E, std::string* err) {
   E = EncodeLayout();
   E.n_tiles = n;
-  std::vector<std::pair<int32_t, int>> fused;
+  std::vector<FusedTask> fused;
   for (int32_t i = 0; i < n; ++i) {
     const isx_tile_desc& t = tiles[i];
     std::string why;
@@ -278,13 +244,15 @@ isx_status plan_encode(const isx_tile_desc* tiles, int32_t n, bool allow_fused, 
     d.nb = (int32_t)nb;
     d.block_base = E.n_blocks;
     d.coef_base = E.coef_bytes;
-    d.fused = allow_fused && fused_tile(t.width, t.height, t.bits) ? 1 : 0;
+    // the fused kernels hold the plane in int16: only when every state of the forward transform fits
+    d.fused = allow_fused && fused_tile(t.width, t.height) && d.coef16 ? 1 : 0;
     d.plane_base = d.fused ? 0 : E.plane_total;
-    if (d.fused) fused.push_back({i, fused_plane_bytes(t.width, t.height)});
+    if (d.fused) fused.push_back({i, fused_plane_bytes(t.width, t.height), t.channels});
     else E.plane_total += (int64_t)t.channels * t.width * t.height;
     d.sym_base = E.sym_bytes;
     E.n_blocks += nb;
-    E.coef_bytes += nc * (t.bits <= 12 ? 2 : 4);
+    E.coef_bytes += nc * (d.coef16 ? 2 : 4);
+    E.max_c = std::max(E.max_c, t.channels);
     // symbol regions: dmax planes of p*w*h/8 bytes per block, each rounded up to 16
     E.sym_bytes += ((int64_t)dmax_of_bits(t.bits) * (nc / 8 + 16 * nb) + 15) & ~15LL;
     E.max_levels = std::max(E.max_levels, t.levels);
@@ -328,10 +296,10 @@ int launch_encode(const EncodeLayout& E, uint8_t* base, void* d_out, size_t out_
   int L = launch_plan_blocks(d_tiles, E.n_tiles, 0, d_blocks, s);
   T->mark("encode.transform", s);
   for (const FusedClass& c : E.cls)
-    L += launch_fused_forward(d_tiles, d_task + c.begin, c.count, c.smem, c.threads, d_blocks, coef, d_status, s);
+    L += launch_fused_forward(d_tiles, d_task + c.begin, c.count, c.slots, c.smem, c.threads, d_blocks, coef, d_status, s);
   if (E.n_fused < E.n_tiles) {
     T->mark("encode.transform_global", s);
-    L += launch_forward_transform(d_tiles, E.n_tiles, E.max_levels, E.max_dim, A, B, d_status, s);
+    L += launch_forward_transform(d_tiles, E.n_tiles, E.max_levels, E.max_dim, E.max_c, A, B, d_status, s);
     T->mark("encode.pack", s);
     L += launch_pack_blocks(d_tiles, d_blocks, E.n_blocks, A, coef, s);
   }
@@ -368,7 +336,7 @@ struct DecodeLayout {
   int32_t nsel = 0;
   int z = 0, drop = 0;
   int64_t n_blocks = 0, plane_total = 0, fplane_total = 0, sym_cap = 0, max_items = 0;
-  int max_levels = 0, max_dim = 1, n_fused = 0;
+  int max_levels = 0, max_dim = 1, max_c = 1, n_fused = 0;
   FusedClass cls[ISX_SIZE_CLASSES];
   size_t o_tiles = 0, o_idx = 0, o_task = 0, o_blocks = 0, o_bb = 0, o_bl = 0, o_info = 0, o_sb = 0, o_so = 0, o_part = 0, o_tot = 0;
   size_t o_tab = 0, o_bucket = 0, o_items = 0, o_sym = 0, o_A = 0, o_B = 0, o_fp = 0, o_tk = 0, total = 0;
@@ -382,7 +350,7 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
   D = DecodeLayout();
   D.z = z;
   D.drop = drop;
-  std::vector<std::pair<int32_t, int>> fused;
+  std::vector<FusedTask> fused;
   for (int32_t j = 0; j < n_jobs; ++j) {
     const Job& jb = jobs[j];
     if (jb.tile < 0 || jb.tile >= n_tiles) { *err = "job " + std::to_string(j) + ": tile index out of range"; return ISX_ERR_ARG; }
@@ -400,23 +368,27 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
     }
     int64_t nb, nc;
     tile_counts(t, z, &nb, &nc);
-    // symbols of every kept plane: at most (1 + magnitude bits) planes of p*w*h/8 bytes each, plus padding
-    D.sym_cap += (int64_t)(t.bits <= 12 ? 16 : kMaxD) * (nc / 8) + 16 * kMaxD * nb;
-    D.max_items += (int64_t)(t.bits <= 12 ? 16 : kMaxD) * nb;
+    // symbols of every kept plane: at most 1 + bitlen(F) planes (sign and magnitude; F bounds every
+    // coefficient the encoder writes) of p*w*h/8 bytes each, plus padding
+    const double F = forward_state_bound(t);
+    int64_t planes = 1;
+    while (planes < kMaxD && std::ldexp(1.0, (int)planes - 1) <= F) ++planes;
+    D.sym_cap += planes * (nc / 8) + 16 * kMaxD * nb;
+    D.max_items += planes * nb;
     TileDev& d = h_tiles[D.nsel];
     fill_tiledev(d, t);
     d.nb = (int32_t)nb;
     d.block_base = D.n_blocks;
     d.coef_base = 0;
-    d.fused = fused_tile(zw, zh, t.bits) && fused_inverse_fits_int16(t, z, drop) ? 1 : 0;
+    d.fused = fused_tile(zw, zh) && fused_inverse_fits_int16(t, z, drop) ? 1 : 0;
     d.dst = (uint8_t*)jb.out;
     d.dpitch = jb.pitch;
     d.rx = jb.rx; d.ry = jb.ry; d.rw = jb.rw; d.rh = jb.rh;
     if (d.fused) {
-      // three-channel tiles hand their int16 planes between CTAs: 16-byte aligned
+      // tiles with a colour transform hand the int16 planes of channels 0..2 between CTAs: 16-byte aligned
       d.plane_base = D.fplane_total;
-      if (t.channels == 3) D.fplane_total += (3LL * zw * zh + 7) & ~7LL;
-      fused.push_back({D.nsel, fused_plane_bytes(zw, zh)});
+      if (d.ct) D.fplane_total += (3LL * zw * zh + 7) & ~7LL;
+      fused.push_back({D.nsel, fused_plane_bytes(zw, zh), t.channels});
     } else {
       d.plane_base = D.plane_total;
       D.plane_total += (int64_t)t.channels * zw * zh;
@@ -426,6 +398,7 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
     D.n_blocks += nb;
     D.max_levels = std::max(D.max_levels, t.levels);
     D.max_dim = std::max(D.max_dim, std::max(t.width, t.height));
+    D.max_c = std::max(D.max_c, t.channels);
   }
   D.n_fused = (int)fused.size();
   group_fused(fused, S.inv, h_task, D.cls);
@@ -481,10 +454,12 @@ int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, co
   uint32_t* tickets = (uint32_t*)(base + D.o_tk);
   if (D.n_fused) cudaMemsetAsync(tickets, 0, 4 * (size_t)D.n_fused, s);
   for (const FusedClass& c : D.cls)
-    L += launch_fused_inverse(d_tiles, d_task + c.begin, c.count, c.smem, c.threads, db, (int16_t*)(base + D.o_fp), tickets + c.begin, s);
+    L += launch_fused_inverse(d_tiles, d_task + c.begin, c.count, c.slots, c.smem, c.threads, db, (int16_t*)(base + D.o_fp),
+                              tickets + c.begin, s);
   if (D.n_fused < D.nsel) {
     T->mark("decode.inverse_global", s);
-    L += launch_inverse_transform(d_tiles, D.nsel, D.max_levels, D.z, D.max_dim, (int32_t*)(base + D.o_A), (int32_t*)(base + D.o_B), s);
+    L += launch_inverse_transform(d_tiles, D.nsel, D.max_levels, D.z, D.max_dim, D.max_c, (int32_t*)(base + D.o_A),
+                                  (int32_t*)(base + D.o_B), s);
     T->mark("decode.store", s);
     L += launch_store_region(d_tiles, D.nsel, D.z, (int32_t*)(base + D.o_A), s);
   }
@@ -617,10 +592,10 @@ const char* isx_last_error(isx_ctx* ctx) { return ctx ? ctx->err.c_str() : "null
 int32_t isx_decode_path(const isx_tile_desc* tile, int32_t level, int32_t drop_lsb_planes, double* h_bound) {
   std::string why;
   if (!tile || !tile_ok(*tile, &why) || level < 0 || level > tile->levels || drop_lsb_planes < 0) return -1;
-  const double b = int16_state_bound(*tile, level, drop_lsb_planes);
+  const double b = inverse_state_bound(*tile, level, drop_lsb_planes);
   if (h_bound) *h_bound = b;
   const int zw = level_dim(tile->width, level), zh = level_dim(tile->height, level);
-  return fused_tile(zw, zh, tile->bits) && b <= 32767.0 ? 1 : 0;
+  return fused_tile(zw, zh) && b <= 32767.0 ? 1 : 0;
 }
 
 int32_t isx_last_launch_count(isx_ctx* ctx) { return ctx ? ctx->launches : 0; }
@@ -677,7 +652,7 @@ isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, in
   int32_t* B = (int32_t*)(ctx->arena + o_B);
   ISX_CUDA(cudaMemcpyAsync(d_tiles, ctx->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
   ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
-  int L = launch_forward_transform(d_tiles, n_tiles, E.max_levels, E.max_dim, A, B, ctx->d_status, s);
+  int L = launch_forward_transform(d_tiles, n_tiles, E.max_levels, E.max_dim, E.max_c, A, B, ctx->d_status, s);
   L += launch_quantise_planes(d_tiles, n_tiles, A, d_coef, s);
   ctx->launches = L;
   ISX_CUDA(cudaGetLastError());
@@ -963,7 +938,7 @@ isx_status isx_autotune(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tile
     float best_ms = 1e30f;
     for (int t : kCand) {
       const float ms = time_ms([&] {
-        launch_fused_forward((TileDev*)(d_mem + E.o_tiles), (int32_t*)(d_mem + E.o_task) + c.begin, c.count, c.smem, t,
+        launch_fused_forward((TileDev*)(d_mem + E.o_tiles), (int32_t*)(d_mem + E.o_task) + c.begin, c.count, c.slots, c.smem, t,
                              (BlockDev*)(d_mem + E.o_blocks), d_mem + E.o_coef, ctx->d_status, s);
       });
       if (ms < best_ms) { best_ms = ms; best.fwd[k] = t; }
@@ -1008,7 +983,7 @@ isx_status isx_autotune(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tile
     for (int t : kCand) {
       const float ms = time_ms([&] {
         cudaMemsetAsync(tickets + c.begin, 0, 4 * (size_t)c.count, s);
-        launch_fused_inverse((TileDev*)(ar + D.o_tiles), (int32_t*)(ar + D.o_task) + c.begin, c.count, c.smem, t, db,
+        launch_fused_inverse((TileDev*)(ar + D.o_tiles), (int32_t*)(ar + D.o_task) + c.begin, c.count, c.slots, c.smem, t, db,
                              (int16_t*)(ar + D.o_fp), tickets + c.begin, s);
       });
       if (ms < best_ms) { best_ms = ms; best.inv[k] = t; }

@@ -51,7 +51,7 @@ __global__ void k_decode_plan(const TileDev* __restrict__ tiles, int n_tiles, co
   bool ok = tend - toff >= 32 && s[0] == 'I' && s[1] == 'S' && s[2] == 'X' && s[3] == '1';
   if (ok) {
     ok = (int)(s[4] | (s[5] << 8)) == t.w && (int)(s[6] | (s[7] << 8)) == t.h && s[8] == t.C && s[9] == t.bits &&
-         s[10] == t.L && (int)rd_u32le(s + 12) == nb_all && tend - toff >= 32 + 4 * (int64_t)nb_all;
+         s[10] == t.L && s[11] == t.ct && (int)rd_u32le(s + 12) == nb_all && tend - toff >= 32 + 4 * (int64_t)nb_all;
     for (int k = 0; ok && k <= t.L; ++k) ok = s[16 + k] == t.q[k];
   }
   int64_t idx = t.block_base;

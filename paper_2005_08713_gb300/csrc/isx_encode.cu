@@ -1056,7 +1056,7 @@ __global__ void k_tile_headers(const TileDev* __restrict__ tiles, int n_tiles, c
     o[0] = 'I'; o[1] = 'S'; o[2] = 'X'; o[3] = '1';
     o[4] = (uint8_t)t.w; o[5] = (uint8_t)(t.w >> 8);
     o[6] = (uint8_t)t.h; o[7] = (uint8_t)(t.h >> 8);
-    o[8] = (uint8_t)t.C; o[9] = (uint8_t)t.bits; o[10] = (uint8_t)t.L; o[11] = t.C == 3 ? 1 : 0;
+    o[8] = (uint8_t)t.C; o[9] = (uint8_t)t.bits; o[10] = (uint8_t)t.L; o[11] = (uint8_t)t.ct;
     for (int k = 0; k < 4; ++k) o[12 + k] = (uint8_t)((uint32_t)t.nb >> (8 * k));
     for (int k = 0; k < 16; ++k) o[16 + k] = k <= t.L ? t.q[k] : 0;
   }

@@ -21,6 +21,8 @@ struct TileDev {
   const uint8_t* pixels;    // device, HWC
   int64_t pitch;            // bytes
   int32_t w, h, C, bits, L, x0, y0;
+  int32_t ct;               // colour transform of channels 0..2: 0 none, 1 RCT, 2 YCoCg-R (the stored id)
+  int32_t coef16;           // every coefficient (and every state of the transforms) fits int16
   uint8_t q[16];
   int32_t nb;               // number of coefficient blocks
   int32_t fused;            // 1: transformed by the fused shared-memory kernels
@@ -41,7 +43,7 @@ struct BlockDev {
   int32_t tile, c, level;   // level 0 = the LL band of the tile
   int32_t by, bx;           // cell position within the subband grid
   int32_t p, w, h;          // types and padded size (multiples of 4)
-  int32_t coef16;           // coefficients stored as int16 (bits <= 12) or int32
+  int32_t coef16;           // coefficients stored as int16 (TileDev::coef16) or int32
   int32_t dmax;             // largest bit depth its coefficients can reach (bits + 6, at most 31)
   int64_t coef;             // byte offset of its coefficients: [type][area][8]
   int64_t sym;              // byte offset of its symbol region (encode)

@@ -10,19 +10,22 @@ namespace isx {
 int launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* part, int64_t* total, cudaStream_t s);
 int launch_plan_blocks(const TileDev* d_tiles, int n_tiles, int min_level, BlockDev* d_blocks, cudaStream_t s);
 // status: kStRange when a sample exceeds its tile's bit depth
-int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B, int* status,
-                             cudaStream_t s);
+// Global (int32, HBM) path of the tiles with TileDev::fused = 0; max_c = the largest channel count.
+int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int max_c, int32_t* A, int32_t* B,
+                             int* status, cudaStream_t s);
 int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t n_blocks, const int32_t* planes, void* coef,
                        cudaStream_t s);
-// Fused forward transform of n_fused tiles of one size class (as above).
-int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int smem_bytes, int threads,
+// Fused forward transform of n_fused tiles of one size class (as above):
+// `slots` CTAs per tile (the class's largest channel count; CTA c takes
+// channel c).
+int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int slots, int smem_bytes, int threads,
                          const BlockDev* d_blocks, void* coef, int* status, cudaStream_t s);
-bool fused_tile(int w, int h, int bits);
+bool fused_tile(int w, int h);   // geometry: the int16 channel plane fits in shared memory
 int fused_plane_bytes(int w, int h);
 cudaError_t transform_set_attributes();   // dynamic shared memory limits of the fused transforms (current device)
 int launch_quantise_planes(const TileDev* d_tiles, int n_tiles, const int32_t* planes, int32_t* out, cudaStream_t s);
-int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int32_t* A, int32_t* B,
-                             cudaStream_t s);
+int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int max_c, int32_t* A,
+                             int32_t* B, cudaStream_t s);
 // Pixels of the tiles not taken by the fused kernels (TileDev::fused = 0) into their destinations.
 int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, cudaStream_t s);
 
@@ -95,13 +98,14 @@ struct DecodeBuffers {
   bool global_rebuild = true;   // some selected tile takes the global (non-fused) inverse
 };
 int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T);
-// Fused inverse (decode) of n_fused tiles of one size class, CTAs of
-// `threads` threads (256, 512 or 1024) with smem_bytes of plane: each tile's
-// pixels go to its destination (TileDev::dst); three-channel tiles pass
-// their int16 channel planes through planes16 (TileDev::plane_base) and the
-// last CTA of each tile, found with tickets[n_fused] (zeroed beforehand),
-// inverts the colour transform.
-int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int smem_bytes, int threads,
+// Fused inverse (decode) of n_fused tiles of one size class, `slots` CTAs
+// per tile of `threads` threads (256, 512 or 1024) with smem_bytes of
+// plane: each tile's pixels go to its destination (TileDev::dst); tiles
+// with a colour transform pass the int16 planes of channels 0..2 through
+// planes16 (TileDev::plane_base) and the last of those three CTAs, found
+// with tickets[n_fused] (zeroed beforehand), inverts the transform; other
+// channels are written by their own CTA.
+int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int slots, int smem_bytes, int threads,
                          const DecodeBuffers& db, int16_t* planes16, uint32_t* tickets, cudaStream_t s);
 size_t dec_table_bytes();
 int launch_level_sort(const BlockDev* blocks, int64_t nb, int64_t* bucket /* 2 * 16 */, int64_t* perm, int64_t* scan_part,

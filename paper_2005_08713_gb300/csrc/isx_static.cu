@@ -91,9 +91,11 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   // subbands per level, each cut into 128 x 128 cells (Fig. 3).
   int64_t nb = 0, nc = 0;
   tile_counts(t, 0, &nb, &nc);
-  const bool fused = fused_tile(t.width, t.height, t.bits);
+  TileDev td;
+  fill_tiledev(td, t);
+  const bool fused = fused_tile(t.width, t.height) && td.coef16;
   const int64_t plane_total = fused ? 0 : (int64_t)t.channels * t.width * t.height;
-  const int64_t coef_bytes = nc * (t.bits <= 12 ? 2 : 4);
+  const int64_t coef_bytes = nc * (td.coef16 ? 2 : 4);
   const int64_t sym_bytes = ((int64_t)dmax_of_bits(t.bits) * (nc / 8 + 16 * nb) + 15) & ~15LL;
   const int64_t n_part = nb / 2048 + 2;
 
@@ -136,8 +138,6 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
 
   uint8_t* ar = S.base;
   cudaStream_t s = (cudaStream_t)stream;
-  TileDev td;
-  fill_tiledev(td, t);
   td.nb = (int32_t)nb;
   td.fused = fused ? 1 : 0;
   td.block_base = 0; td.plane_base = 0; td.coef_base = 0; td.sym_base = 0;
@@ -152,9 +152,10 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   k_static_begin<<<1, 1, 0, s>>>(td, d_tile, d_task, d_status);
   launch_plan_blocks(d_tile, 1, 0, d_blocks, s);
   if (fused) {
-    launch_fused_forward(d_tile, d_task, 1, fused_plane_bytes(t.width, t.height), 1024, d_blocks, coef, d_status, s);
+    launch_fused_forward(d_tile, d_task, 1, t.channels, fused_plane_bytes(t.width, t.height), 1024, d_blocks, coef, d_status, s);
   } else {
-    launch_forward_transform(d_tile, 1, t.levels, std::max(t.width, t.height), (int32_t*)(ar + o_A), (int32_t*)(ar + o_B), d_status, s);
+    launch_forward_transform(d_tile, 1, t.levels, std::max(t.width, t.height), t.channels, (int32_t*)(ar + o_A), (int32_t*)(ar + o_B),
+                             d_status, s);
     launch_pack_blocks(d_tile, d_blocks, nb, (int32_t*)(ar + o_A), coef, s);
   }
   EncodeBuffers eb;

@@ -41,7 +41,7 @@ __global__ void k_plan_blocks(const TileDev* __restrict__ tiles, int n_tiles, in
           b.w = pad4(min(kCell, gw - kCell * bx));
           b.h = pad4(min(kCell, gh - kCell * by));
           b.coef = coef;
-          b.coef16 = t.bits <= 12 ? 1 : 0;
+          b.coef16 = t.coef16;
           b.dmax = dmax;
           b.sym = sym;
           coef += (int64_t)p * b.w * b.h * (b.coef16 ? 2 : 4);
@@ -114,8 +114,35 @@ int launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* p
 }
 
 // --------------------------------------------------- colour transform
-// Pixels -> C int32 planes (Mallat plane 0 .. C-1 of the tile).  RCT of
-// JPEG 2000 for 3 channels: Y = floor((R+2G+B)/4), Cb = B-G, Cr = R-G.
+// Colour transforms of channels 0..2 (Fig. 1, "optional colorspace
+// transformation"), component c of (R, G, B):
+//  ct 1, the RCT of JPEG 2000: Y = floor((R+2G+B)/4), Cb = B-G, Cr = R-G;
+//  ct 2, YCoCg-R: Co = R-B, t = B + floor(Co/2), Cg = G-t, Y = t + floor(Cg/2).
+__device__ __forceinline__ int32_t ct_forward(int ct, int c, int32_t R, int32_t G, int32_t B) {
+  if (ct == 1) return c == 0 ? (R + 2 * G + B) >> 2 : c == 1 ? B - G : R - G;
+  const int32_t Co = R - B, t = B + (Co >> 1), Cg = G - t;
+  return c == 0 ? t + (Cg >> 1) : c == 1 ? Co : Cg;
+}
+// Inverse of ct_forward: (Y, Cb, Cr) or (Y, Co, Cg) -> (R, G, B).
+__device__ __forceinline__ void ct_inverse(int ct, int32_t a, int32_t b, int32_t c, int32_t* R, int32_t* G, int32_t* B) {
+  if (ct == 1) {
+    *G = a - ((b + c) >> 2);
+    *R = c + *G;
+    *B = b + *G;
+  } else {
+    const int32_t t = a - (c >> 1);
+    *G = c + t;
+    *B = t - (b >> 1);
+    *R = *B + b;
+  }
+}
+// Sample x of channel c of an interleaved row (uint8 when bits <= 8, else uint16).
+__device__ __forceinline__ int32_t sample_at(const uint8_t* row, int x, int C, int c, int bits) {
+  return bits <= 8 ? (int32_t)row[x * C + c] : (int32_t)reinterpret_cast<const uint16_t*>(row)[x * C + c];
+}
+
+// Pixels -> C int32 planes (Mallat plane 0 .. C-1 of the tile), channels
+// 0..2 through the tile's colour transform, the others as they are.
 __global__ void k_load_pixels(const TileDev* __restrict__ tiles, int32_t* __restrict__ planes, int* __restrict__ status) {
   const TileDev& t = tiles[blockIdx.x];
   if (t.fused) return;
@@ -125,19 +152,15 @@ __global__ void k_load_pixels(const TileDev* __restrict__ tiles, int32_t* __rest
   for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < np; e += (int64_t)gridDim.y * blockDim.x) {
     int y = (int)(e / t.w), x = (int)(e - (int64_t)y * t.w);
     const uint8_t* row = t.pixels + (int64_t)y * t.pitch;
-    int32_t v[3];
+    int32_t v[3] = {0, 0, 0};
     for (int c = 0; c < t.C; ++c) {
-      v[c] = t.bits <= 8 ? (int32_t)row[x * t.C + c] : (int32_t)((const uint16_t*)row)[x * t.C + c];
-      over |= (uint32_t)v[c] >> t.bits;
+      const int32_t s = sample_at(row, x, t.C, c, t.bits);
+      over |= (uint32_t)s >> t.bits;
+      if (t.ct && c < 3) v[c] = s;
+      else out[c * np + e] = s;
     }
-    if (t.C == 3) {
-      int32_t R = v[0], G = v[1], B = v[2];
-      out[e] = (R + 2 * G + B) >> 2;
-      out[np + e] = B - G;
-      out[2 * np + e] = R - G;
-    } else {
-      out[e] = v[0];
-    }
+    if (t.ct)
+      for (int c = 0; c < 3; ++c) out[c * np + e] = ct_forward(t.ct, c, v[0], v[1], v[2]);
   }
   if (over) set_status(status, kStRange);
 }
@@ -190,8 +213,8 @@ __device__ void lift_inv(const int32_t* in, int32_t* x, int n, int64_t stride) {
   if (n & 1) x[(int64_t)(n - 1) * stride] = e;
 }
 
-// Task = (tile, channel) in blockIdx.x (3 slots per tile); blockIdx.y
-// chunks the columns (vertical) or rows (horizontal) of the LL region.
+// Task = tile in blockIdx.x, channel in blockIdx.z; blockIdx.y chunks the
+// columns (vertical) or rows (horizontal) of the LL region.
 // Plane geometry: stride = plane_w (the tile width for encode, the level-z
 // width for decode); region cw x ch at level `lvl` of each tile.
 struct PassGeom {
@@ -211,18 +234,18 @@ __device__ inline bool pass_geom(const TileDev& t, int c, int lvl, bool decode_p
 }
 
 __global__ void k_fwd_vpass(const TileDev* __restrict__ tiles, int lvl, const int32_t* __restrict__ A, int32_t* __restrict__ B) {
-  const TileDev& t = tiles[blockIdx.x / 3];
+  const TileDev& t = tiles[blockIdx.x];
   PassGeom g;
-  if (!pass_geom(t, blockIdx.x % 3, lvl, false, 0, &g)) return;
+  if (!pass_geom(t, blockIdx.z, lvl, false, 0, &g)) return;
   int col = blockIdx.y * blockDim.x + threadIdx.x;
   if (col >= g.cw) return;
   lift_fwd(A + g.base + col, B + g.base + col, g.ch, g.stride);
 }
 
 __global__ void k_fwd_hpass(const TileDev* __restrict__ tiles, int lvl, const int32_t* __restrict__ B, int32_t* __restrict__ A) {
-  const TileDev& t = tiles[blockIdx.x / 3];
+  const TileDev& t = tiles[blockIdx.x];
   PassGeom g;
-  if (!pass_geom(t, blockIdx.x % 3, lvl, false, 0, &g)) return;
+  if (!pass_geom(t, blockIdx.z, lvl, false, 0, &g)) return;
   int row = blockIdx.y * blockDim.x + threadIdx.x;
   if (row >= g.ch) return;
   lift_fwd(B + g.base + (int64_t)row * g.stride, A + g.base + (int64_t)row * g.stride, g.cw, 1);
@@ -231,18 +254,18 @@ __global__ void k_fwd_hpass(const TileDev* __restrict__ tiles, int lvl, const in
 // Inverse level lvl (0-based: undoes the transform of LL_lvl) on decode
 // planes of size level_dim(w, z) x level_dim(h, z).
 __global__ void k_inv_hpass(const TileDev* __restrict__ tiles, int lvl, int z, const int32_t* __restrict__ A, int32_t* __restrict__ B) {
-  const TileDev& t = tiles[blockIdx.x / 3];
+  const TileDev& t = tiles[blockIdx.x];
   PassGeom g;
-  if (!pass_geom(t, blockIdx.x % 3, lvl, true, z, &g)) return;
+  if (!pass_geom(t, blockIdx.z, lvl, true, z, &g)) return;
   int row = blockIdx.y * blockDim.x + threadIdx.x;
   if (row >= g.ch) return;
   lift_inv(A + g.base + (int64_t)row * g.stride, B + g.base + (int64_t)row * g.stride, g.cw, 1);
 }
 
 __global__ void k_inv_vpass(const TileDev* __restrict__ tiles, int lvl, int z, const int32_t* __restrict__ B, int32_t* __restrict__ A) {
-  const TileDev& t = tiles[blockIdx.x / 3];
+  const TileDev& t = tiles[blockIdx.x];
   PassGeom g;
-  if (!pass_geom(t, blockIdx.x % 3, lvl, true, z, &g)) return;
+  if (!pass_geom(t, blockIdx.z, lvl, true, z, &g)) return;
   int col = blockIdx.y * blockDim.x + threadIdx.x;
   if (col >= g.cw) return;
   lift_inv(B + g.base + col, A + g.base + col, g.ch, g.stride);
@@ -315,9 +338,9 @@ __global__ void k_quantise_planes(const TileDev* __restrict__ tiles, const int32
 }
 
 // ---------------------------------------------------------- decode output
-// Inverse RCT (G = Y - floor((Cb+Cr)/4), R = Cr + G, B = Cb + G), clamp to
-// [0, 2^bits - 1] and write the part of the tile's level-z image that
-// falls inside the requested rectangle.
+// Inverse colour transform of channels 0..2 (ct_inverse), clamp to
+// [0, 2^bits - 1] and write the part of the tile's level-z image that falls
+// inside the requested rectangle.
 __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const int32_t* __restrict__ planes) {
   const TileDev& t = tiles[blockIdx.x];
   if (t.fused) return;   // written by the fused inverse kernel
@@ -333,17 +356,12 @@ __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const i
     int y = (int)(e / zw), x = (int)(e - (int64_t)y * zw);
     int ox = tx + x - rx, oy = ty + y - ry;
     if (ox < 0 || oy < 0 || ox >= rw || oy >= rh) continue;
-    int32_t v[3];
-    if (t.C == 3) {
-      int32_t Y = pl[e], Cb = pl[np + e], Cr = pl[2 * np + e];
-      int32_t G = Y - ((Cb + Cr) >> 2);
-      v[0] = Cr + G; v[1] = G; v[2] = Cb + G;
-    } else {
-      v[0] = pl[e];
-    }
+    int32_t v[3] = {0, 0, 0};
+    if (t.ct) ct_inverse(t.ct, pl[e], pl[np + e], pl[2 * np + e], &v[0], &v[1], &v[2]);
     uint8_t* row = out + (int64_t)oy * pitch;
     for (int c = 0; c < t.C; ++c) {
-      int32_t q = min(max(v[c], 0), maxv);
+      const int32_t s = t.ct && c < 3 ? v[c] : pl[c * np + e];
+      int32_t q = min(max(s, 0), maxv);
       if (t.bits <= 8) row[ox * t.C + c] = (uint8_t)q;
       else reinterpret_cast<uint16_t*>(row)[ox * t.C + c] = (uint16_t)q;
     }
@@ -351,18 +369,20 @@ __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const i
 }
 
 // ------------------------------------------------- fused shared-memory path
-// Tiles whose channel plane fits in shared memory as int16 (bits <= 12: the
-// worst-case gain of the iterated 5/3 filters keeps every coefficient below
-// 2^15) are transformed by one CTA per (tile, channel), in place on the
+// Tiles whose channel plane fits in shared memory as int16 (the host checks
+// that the worst-case gain of the iterated 5/3 filters keeps every state of
+// the tile's transform below 2^15: TileDev::coef16 for the forward, the
+// deviation bound of the decode for the inverse) are transformed by one CTA
+// per (tile, channel), in place on the
 // interleaved layout: after level l the LL samples sit at multiples of 2^l,
 // and the high-pass samples of level l at odd multiples of 2^(l-1).
 constexpr int kFusedThreads = 1024;   // most threads of a fused CTA (launches use 256, 512 or 1024)
 
 __host__ __device__ inline int smem_pitch(int w);
-__host__ __device__ inline bool tile_uses_smem(int w, int h, int bits) {
+__host__ __device__ inline bool tile_uses_smem(int w, int h) {
   // up to 1024 x 1024 a channel has at most 20 coefficient blocks (LL and
   // every level) within this plane budget: the block table below holds 32
-  return bits <= 12 && w <= 1024 && h <= 1024 && (int64_t)smem_pitch(w) * h * 2 <= kSmemPlaneBytes;
+  return w <= 1024 && h <= 1024 && (int64_t)smem_pitch(w) * h * 2 <= kSmemPlaneBytes;
 }
 
 // Interleaved position of subband sample (y, x) of `type` at `level`
@@ -923,17 +943,18 @@ __device__ inline void pack_units(const FusedBlock* s_fb, int u0, int u1, int ti
 }
 
 __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
-                                                                 const BlockDev* __restrict__ blocks, uint8_t* __restrict__ coef,
+                                                                 int slots, const BlockDev* __restrict__ blocks, uint8_t* __restrict__ coef,
                                                                  int* __restrict__ status) {
   extern __shared__ __align__(16) int16_t P[];
   __shared__ FusedBlock s_fb[kMaxFusedBlocks];
-  const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
+  const int tt = task_tile[blockIdx.x / slots], c = blockIdx.x % slots;
   const TileDev& t = tiles[tt];
   if (c >= t.C) return;
   const int w = t.w, h = t.h, pitch = smem_pitch(w);
   // load + colour transform of channel c
   uint32_t over = 0;   // bits of samples above the tile's bit depth
-  const bool quad = t.C == 3 && t.bits <= 8 && (w & 3) == 0 && (t.pitch & 3) == 0 && ((reinterpret_cast<uintptr_t>(t.pixels) & 3) == 0);
+  const bool quad = t.C == 3 && t.ct == 1 && t.bits <= 8 && (w & 3) == 0 && (t.pitch & 3) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(t.pixels) & 3) == 0);
   if (quad) {
     // four pixels (12 bytes, three aligned words) per thread and row; a
     // thread keeps its column quad and steps over rows, loading four rows'
@@ -980,18 +1001,18 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
     const int y = e / w, x = e - y * w;
     const uint8_t* row = t.pixels + (int64_t)y * t.pitch;
     int32_t v;
-    if (t.C == 3) {
-      const int32_t R = row[3 * x], G = row[3 * x + 1], B = row[3 * x + 2];
+    if (t.ct && c < 3) {
+      const int32_t R = sample_at(row, x, t.C, 0, t.bits), G = sample_at(row, x, t.C, 1, t.bits), B = sample_at(row, x, t.C, 2, t.bits);
       over |= (uint32_t)(R | G | B) >> t.bits;
-      v = c == 0 ? (R + 2 * G + B) >> 2 : c == 1 ? B - G : R - G;
+      v = ct_forward(t.ct, c, R, G, B);
     } else {
-      v = t.bits <= 8 ? (int32_t)row[x] : (int32_t)reinterpret_cast<const uint16_t*>(row)[x];
+      v = sample_at(row, x, t.C, c, t.bits);
       over |= (uint32_t)v >> t.bits;
     }
     P[y * pitch + x] = (int16_t)v;
   }
   // samples above the tile's bit depth void the int16 range bound of the transform
-  if (__any_sync(0xffffffffu, over != 0) && (threadIdx.x & 31) == 0 && c == 0) set_status(status, kStRange);
+  if (__any_sync(0xffffffffu, over != 0) && (threadIdx.x & 31) == 0) set_status(status, kStRange);
   __syncthreads();
   // quantise + area-ordered pack of this channel's blocks (one loop over the areas of a range of blocks)
   const int nbc = t.nb / t.C;
@@ -1027,14 +1048,15 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   pack_units(s_fb, 0, k1 ? s_fb[k1 - 1].end : 0, threadIdx.x, blockDim.x, P, pitch, coef);
 }
 
-// Decoded RGB8 pixels of one tile at level z into the region output, by the
-// last of the tile's three CTAs: channel `c` is its own shared-memory plane
-// (P, `pitch` elements a row), the other two come from the int16 planes the
-// other CTAs left in global memory (gp: three row-major zw x zh planes, read
-// through L2).  Each thread converts four pixels of a row (inverse RCT,
-// clamp to [0, 2^bits - 1]).
-__device__ inline void store_tile_rgb(const TileDev& t, int z, int zw, int zh, int c, const int16_t* P, int pitch,
-                                      const int16_t* __restrict__ gp) {
+// Decoded channels 0..2 of one tile with a colour transform at level z into
+// the region output, by the last of the tile's CTAs of those channels:
+// channel `c` is its own shared-memory plane (P, `pitch` elements a row),
+// the other two come from the int16 planes the other CTAs left in global
+// memory (gp: three row-major zw x zh planes, read through L2).  Each thread
+// converts four pixels of a row (inverse colour transform, clamp to
+// [0, 2^bits - 1]); samples are uint8 (bits <= 8) or uint16, C to a pixel.
+__device__ inline void store_tile_ct(const TileDev& t, int z, int zw, int zh, int c, const int16_t* P, int pitch,
+                                     const int16_t* __restrict__ gp) {
   uint8_t* __restrict__ out = t.dst;
   const int64_t opitch = t.dpitch;
   const int rx = t.rx, ry = t.ry, rw = t.rw, rh = t.rh;
@@ -1047,9 +1069,10 @@ __device__ inline void store_tile_rgb(const TileDev& t, int z, int zw, int zh, i
   const int64_t np = (int64_t)zw * zh;
   // whole quads of a plane with rows of a multiple of 4 samples load 8-byte aligned
   const bool vec = (zw & 3) == 0 && (reinterpret_cast<uintptr_t>(gp) & 7) == 0;
-  // whole quads inside the region with 4-byte aligned destinations take three word stores
-  const bool words = ((reinterpret_cast<uintptr_t>(out) | (uintptr_t)opitch) & 3) == 0 && ((tx + x4) & 3) == 0 && x4 + 3 < zw &&
-                     tx + x4 >= 0 && tx + x4 + 3 < rw;
+  // whole quads of RGB8 inside the region with 4-byte aligned destinations take three word stores
+  const bool words = t.C == 3 && t.bits <= 8 && ((reinterpret_cast<uintptr_t>(out) | (uintptr_t)opitch) & 3) == 0 &&
+                     ((tx + x4) & 3) == 0 && x4 + 3 < zw && tx + x4 >= 0 && tx + x4 + 3 < rw;
+  const int C = t.C;
   for (int y = r0; y < zh; y += rows_per_pass) {
     const int oy = ty + y;
     if (oy < 0 || oy >= rh) continue;
@@ -1081,10 +1104,11 @@ __device__ inline void store_tile_rgb(const TileDev& t, int z, int zw, int zh, i
     int32_t R[4], G[4], B[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int32_t g = ch[0][u] - ((ch[1][u] + ch[2][u]) >> 2);
-      R[u] = min(max(ch[2][u] + g, 0), maxv);
+      int32_t r, g, b;
+      ct_inverse(t.ct, ch[0][u], ch[1][u], ch[2][u], &r, &g, &b);
+      R[u] = min(max(r, 0), maxv);
       G[u] = min(max(g, 0), maxv);
-      B[u] = min(max(ch[1][u] + g, 0), maxv);
+      B[u] = min(max(b, 0), maxv);
     }
     uint8_t* row = out + (int64_t)oy * opitch;
     if (words) {
@@ -1097,17 +1121,24 @@ __device__ inline void store_tile_rgb(const TileDev& t, int z, int zw, int zh, i
       for (int u = 0; u < 4; ++u) {
         const int ox = tx + x4 + u;
         if (x4 + u >= zw || ox < 0 || ox >= rw) continue;
-        row[3 * ox] = (uint8_t)R[u];
-        row[3 * ox + 1] = (uint8_t)G[u];
-        row[3 * ox + 2] = (uint8_t)B[u];
+        if (t.bits <= 8) {
+          row[C * ox] = (uint8_t)R[u];
+          row[C * ox + 1] = (uint8_t)G[u];
+          row[C * ox + 2] = (uint8_t)B[u];
+        } else {
+          uint16_t* r16 = reinterpret_cast<uint16_t*>(row);
+          r16[C * ox] = (uint16_t)R[u];
+          r16[C * ox + 1] = (uint16_t)G[u];
+          r16[C * ox + 2] = (uint16_t)B[u];
+        }
       }
     }
   }
 }
 
-// One-channel tile: samples clamped to [0, 2^bits - 1], uint8 (bits <= 8)
-// or uint16 output.
-__device__ inline void store_tile_mono(const TileDev& t, int z, int zw, int zh, const int16_t* P, int pitch) {
+// Channel c of a tile coded without a colour transform on it: samples
+// clamped to [0, 2^bits - 1], uint8 (bits <= 8) or uint16, C to a pixel.
+__device__ inline void store_tile_channel(const TileDev& t, int z, int zw, int zh, int c, const int16_t* P, int pitch) {
   uint8_t* __restrict__ out = t.dst;
   const int64_t opitch = t.dpitch;
   const int rx = t.rx, ry = t.ry, rw = t.rw, rh = t.rh;
@@ -1119,8 +1150,8 @@ __device__ inline void store_tile_mono(const TileDev& t, int z, int zw, int zh, 
     if (ox < 0 || oy < 0 || ox >= rw || oy >= rh) continue;
     const int32_t v = min(max((int32_t)P[y * pitch + x], 0), maxv);
     uint8_t* row = out + (int64_t)oy * opitch;
-    if (t.bits <= 8) row[ox] = (uint8_t)v;
-    else reinterpret_cast<uint16_t*>(row)[ox] = (uint16_t)v;
+    if (t.bits <= 8) row[ox * t.C + c] = (uint8_t)v;
+    else reinterpret_cast<uint16_t*>(row)[ox * t.C + c] = (uint16_t)v;
   }
 }
 
@@ -1320,13 +1351,13 @@ __device__ inline void rebuild_units(const FusedBlock* s_fb, const int32_t (*s_p
 __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* __restrict__ tiles, const int32_t* __restrict__ task_tile,
                                                                  const BlockDev* __restrict__ blocks, const DecInfo* __restrict__ info,
                                                                  const int64_t* __restrict__ sym_off, const uint8_t* __restrict__ sym,
-                                                                 const int64_t* __restrict__ sym_total, int64_t sym_cap, int z,
+                                                                 const int64_t* __restrict__ sym_total, int64_t sym_cap, int z, int slots,
                                                                  int16_t* __restrict__ fplanes, uint32_t* __restrict__ tickets) {
   extern __shared__ __align__(16) int16_t P[];
   __shared__ FusedBlock s_fb[kMaxFusedBlocks];
   __shared__ int32_t s_po[kMaxFusedBlocks][kMaxFusedPlanes][3];   // (plane, type) symbols from the block's first; -1: not kept
   __shared__ bool s_last;
-  const int tt = task_tile[blockIdx.x / 3], c = blockIdx.x % 3;
+  const int tt = task_tile[blockIdx.x / slots], c = blockIdx.x % slots;
   const TileDev& t = tiles[tt];
   if (c >= t.C || *sym_total > sym_cap) return;
   const int zw = level_dim(t.w, z), zh = level_dim(t.h, z), pitch = smem_pitch(zw);
@@ -1360,10 +1391,11 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
     __syncthreads();
     level_inv(P, pitch, level_dim(t.w, z), level_dim(t.h, z), 1);
   }
-  if (t.C == 3) {
-    // Every CTA leaves its channel plane (int16) in global memory and takes
-    // a ticket; the tile's third CTA to finish inverts the colour transform
-    // from its own plane and the other two (no CTA waits for another).
+  if (t.ct && c < 3) {
+    // Every CTA of channels 0..2 leaves its channel plane (int16) in global
+    // memory and takes a ticket; the tile's third CTA to finish inverts the
+    // colour transform from its own plane and the other two (no CTA waits
+    // for another).
     int16_t* gp = fplanes + t.plane_base;
     int16_t* mine = gp + (int64_t)c * zw * zh;
     if ((zw & 7) == 0 && ((reinterpret_cast<uintptr_t>(mine) & 15) == 0)) {
@@ -1384,19 +1416,19 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&tickets[blockIdx.x / 3], 1u) % 3u) == 2u;
+    if (threadIdx.x == 0) s_last = (atomicAdd(&tickets[blockIdx.x / slots], 1u) % 3u) == 2u;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    store_tile_rgb(t, z, zw, zh, c, P, pitch, gp);
+    store_tile_ct(t, z, zw, zh, c, P, pitch, gp);
   } else {
-    store_tile_mono(t, z, zw, zh, P, pitch);
+    store_tile_channel(t, z, zw, zh, c, P, pitch);
   }
 }
 
 // --------------------------------------------------------------- launches
-int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int32_t* A, int32_t* B, int* status,
-                             cudaStream_t s) {
+int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int max_dim, int max_c, int32_t* A, int32_t* B,
+                             int* status, cudaStream_t s) {
   int launches = 0;
   dim3 g0(n_tiles, 64);
   k_load_pixels<<<g0, 256, 0, s>>>(d_tiles, A, status);
@@ -1404,7 +1436,7 @@ int launch_forward_transform(const TileDev* d_tiles, int n_tiles, int max_levels
   const int T = 128;
   for (int l = 0; l < max_levels; ++l) {
     int md = level_dim(max_dim, l);
-    dim3 g(3 * n_tiles, ceil_div(md, T));
+    dim3 g(n_tiles, ceil_div(md, T), max_c);
     k_fwd_vpass<<<g, T, 0, s>>>(d_tiles, l, A, B);
     k_fwd_hpass<<<g, T, 0, s>>>(d_tiles, l, B, A);
     launches += 2;
@@ -1418,22 +1450,22 @@ int launch_pack_blocks(const TileDev* d_tiles, const BlockDev* d_blocks, int64_t
   return 1;
 }
 
-int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int smem_bytes, int threads,
+int launch_fused_forward(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int slots, int smem_bytes, int threads,
                          const BlockDev* d_blocks, void* coef, int* status, cudaStream_t s) {
   if (n_fused == 0) return 0;
-  k_fwd_tile_smem<<<3 * n_fused, threads, smem_bytes, s>>>(d_tiles, d_task_tile, d_blocks, (uint8_t*)coef, status);
+  k_fwd_tile_smem<<<slots * n_fused, threads, smem_bytes, s>>>(d_tiles, d_task_tile, slots, d_blocks, (uint8_t*)coef, status);
   return 1;
 }
 
-int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int smem_bytes, int threads,
+int launch_fused_inverse(const TileDev* d_tiles, const int32_t* d_task_tile, int n_fused, int slots, int smem_bytes, int threads,
                          const DecodeBuffers& db, int16_t* planes16, uint32_t* tickets, cudaStream_t s) {
   if (n_fused == 0) return 0;
-  k_inv_tile_smem<<<3 * n_fused, threads, smem_bytes, s>>>(d_tiles, d_task_tile, db.blocks, db.info, db.sym_off, db.sym, db.totals,
-                                                           db.sym_cap, db.z, planes16, tickets);
+  k_inv_tile_smem<<<slots * n_fused, threads, smem_bytes, s>>>(d_tiles, d_task_tile, db.blocks, db.info, db.sym_off, db.sym, db.totals,
+                                                               db.sym_cap, db.z, slots, planes16, tickets);
   return 1;
 }
 
-bool fused_tile(int w, int h, int bits) { return tile_uses_smem(w, h, bits); }
+bool fused_tile(int w, int h) { return tile_uses_smem(w, h); }
 int fused_plane_bytes(int w, int h) { return smem_pitch(w) * h * 2; }
 
 cudaError_t transform_set_attributes() {
@@ -1452,13 +1484,13 @@ int launch_quantise_planes(const TileDev* d_tiles, int n_tiles, const int32_t* p
   return 1;
 }
 
-int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int32_t* A, int32_t* B,
-                             cudaStream_t s) {
+int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_dim, int max_c, int32_t* A,
+                             int32_t* B, cudaStream_t s) {
   int launches = 0;
   const int T = 128;
   for (int l = max_levels - 1; l >= z; --l) {
     int md = level_dim(max_dim, l);
-    dim3 g(3 * n_tiles, ceil_div(md, T));
+    dim3 g(n_tiles, ceil_div(md, T), max_c);
     k_inv_hpass<<<g, T, 0, s>>>(d_tiles, l, z, A, B);
     k_inv_vpass<<<g, T, 0, s>>>(d_tiles, l, z, B, A);
     launches += 2;

@@ -33,6 +33,9 @@ EXPORTS = ["isx_create", "isx_destroy", "isx_encode_tiles", "isx_decode_region",
 
 SIZE_CLASSES = 5
 
+# colour transform selectors (isx_tile_desc.transform, ISX_CT_*)
+CT_DEFAULT, CT_NONE, CT_RCT, CT_YCOCG_R = 0, 1, 2, 3
+
 # size of the library's static device scratch (ISX_STATIC_SCRATCH_BYTES)
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -46,7 +49,8 @@ class IsxError(RuntimeError):
 class TileDescC(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("bits", ctypes.c_int32), ("levels", ctypes.c_int32), ("x0", ctypes.c_int32), ("y0", ctypes.c_int32),
-                ("qstep_log2", ctypes.c_uint8 * 16), ("pixels", ctypes.c_void_p), ("row_pitch_bytes", ctypes.c_int64)]
+                ("qstep_log2", ctypes.c_uint8 * 16), ("pixels", ctypes.c_void_p), ("row_pitch_bytes", ctypes.c_int64),
+                ("transform", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class DecodeJobC(ctypes.Structure):
@@ -77,6 +81,7 @@ class Tile:
     pixels: int = 0            # device (or, for the *_host calls, host) address
     row_pitch_bytes: int = 0
     keep: object = field(default=None, repr=False)   # keeps the pixel buffer alive
+    transform: int = CT_DEFAULT
 
     def to_c(self) -> TileDescC:
         t = TileDescC()
@@ -87,6 +92,7 @@ class Tile:
             t.qstep_log2[i] = q[i]
         t.pixels = self.pixels
         t.row_pitch_bytes = self.row_pitch_bytes
+        t.transform = self.transform
         return t
 
 
@@ -427,17 +433,18 @@ def level_dim(n: int, z: int) -> int:
     return n
 
 
-def tile_from_tensor(t, levels: int, bits: int, qstep_log2=(), x0: int = 0, y0: int = 0) -> Tile:
+def tile_from_tensor(t, levels: int, bits: int, qstep_log2=(), x0: int = 0, y0: int = 0, transform: int = CT_DEFAULT) -> Tile:
     """Tile over an HWC (or HW) CUDA tensor view (uint8, or int16/uint16 storage for bits > 8)."""
     h, w = int(t.shape[0]), int(t.shape[1])
     c = 1 if t.dim() == 2 else int(t.shape[2])
     return Tile(width=w, height=h, channels=c, bits=bits, levels=levels, qstep_log2=tuple(qstep_log2), x0=x0, y0=y0,
-                pixels=t.data_ptr(), row_pitch_bytes=t.stride(0) * t.element_size(), keep=t)
+                pixels=t.data_ptr(), row_pitch_bytes=t.stride(0) * t.element_size(), keep=t, transform=transform)
 
 
-def tile_from_array(a: np.ndarray, levels: int, bits: int, qstep_log2=(), x0: int = 0, y0: int = 0) -> Tile:
+def tile_from_array(a: np.ndarray, levels: int, bits: int, qstep_log2=(), x0: int = 0, y0: int = 0,
+                    transform: int = CT_DEFAULT) -> Tile:
     """Tile over a host numpy view (for the *_host calls)."""
     h, w = a.shape[:2]
     c = 1 if a.ndim == 2 else a.shape[2]
     return Tile(width=w, height=h, channels=c, bits=bits, levels=levels, qstep_log2=tuple(qstep_log2), x0=x0, y0=y0,
-                pixels=a.ctypes.data, row_pitch_bytes=a.strides[0], keep=a)
+                pixels=a.ctypes.data, row_pitch_bytes=a.strides[0], keep=a, transform=transform)

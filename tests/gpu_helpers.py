@@ -22,7 +22,7 @@ def to_device(img: np.ndarray):
     return torch.from_numpy(a).cuda()
 
 
-def gpu_encode(codec, imgs, levels, bits, qsteps=None, origins=None, capacity=None):
+def gpu_encode(codec, imgs, levels, bits, qsteps=None, origins=None, capacity=None, transforms=None):
     """Encode a list of images as one batch of tiles; returns (list of tile stream bytes, raw stream, offsets)."""
     torch = torch_cuda()
     from paper_2005_08713_gb300 import isx
@@ -42,7 +42,8 @@ def gpu_encode(codec, imgs, levels, bits, qsteps=None, origins=None, capacity=No
         B = bits[i] if isinstance(bits, (list, tuple)) else bits
         q = qsteps[i] if qsteps and isinstance(qsteps[0], (list, tuple)) else tuple(qsteps or ())
         x0, y0 = origins[i]
-        tiles.append(isx.tile_from_tensor(dt, L, B, q, x0, y0))
+        ct = transforms[i] if isinstance(transforms, (list, tuple)) else (transforms or 0)
+        tiles.append(isx.tile_from_tensor(dt, L, B, q, x0, y0, transform=ct))
     if capacity is None:
         capacity = sum(a.nbytes for a in imgs) * 3 + 4096 * len(imgs)
     out = torch.zeros(capacity, dtype=torch.uint8, device="cuda")

@@ -29,9 +29,15 @@ def test_library_builds_and_exports_every_symbol():
 
 def test_tile_descriptor_layout_matches_header():
     from paper_2005_08713_gb300 import isx
-    # int32 x 7, uint8[16], pointer, int64  ->  64 bytes with natural alignment
-    assert ctypes.sizeof(isx.TileDescC) == 64
+    # int32 x 7, uint8[16], pointer, int64, int32 x 2  ->  72 bytes with natural alignment
+    assert ctypes.sizeof(isx.TileDescC) == 72
     assert isx.TileDescC.pixels.offset == 48 and isx.TileDescC.row_pitch_bytes.offset == 56
+    assert isx.TileDescC.transform.offset == 64 and isx.TileDescC.reserved.offset == 68
+    with open(os.path.join(ROOT, "include", "isx.h")) as f:
+        src = f.read()
+    for name, value in (("ISX_CT_DEFAULT", 0), ("ISX_CT_NONE", 1), ("ISX_CT_RCT", 2), ("ISX_CT_YCOCG_R", 3)):
+        assert re.search(rf"#define {name} {value}\b", src), name
+    assert (isx.CT_DEFAULT, isx.CT_NONE, isx.CT_RCT, isx.CT_YCOCG_R) == (0, 1, 2, 3)
 
 
 def test_decode_job_array_layout_matches_header():

@@ -243,22 +243,23 @@ def test_samples_above_bit_depth_are_reported(codec, orc, synth, shape, bits, dt
     assert out[: int(offs[1].item())].cpu().numpy().tobytes() == orc.encode_tile(ok, 3, bits)
 
 
-def test_rgb_tiles_above_8_bits_are_argument_errors(codec):
-    """3-channel tiles take 1..8 bits (above that the colour-transformed coefficients of the int16 path
-    could overflow): encode and decode descriptors beyond it are refused before anything is enqueued."""
+def test_channel_and_transform_argument_errors(codec):
+    """Descriptors outside the documented ranges (more than 16 channels, a colour transform on fewer
+    than 3 channels, an unknown transform) are refused before anything is enqueued, by encode and decode."""
     torch = torch_cuda()
     from paper_2005_08713_gb300 import isx
-    d = torch.zeros((16, 24, 3), dtype=torch.int16, device="cuda")
     out = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
     offs = torch.zeros(2, dtype=torch.int64, device="cuda")
-    for bits in (9, 12, 16):
-        t = isx.tile_from_tensor(d, 2, bits)
+    for C, ct, msg in ((17, isx.CT_DEFAULT, "channels"), (2, isx.CT_RCT, "3 or more"), (1, isx.CT_YCOCG_R, "3 or more"),
+                       (3, 4, "transform")):
+        d = torch.zeros((16, 24, C), dtype=torch.uint8, device="cuda")
+        t = isx.tile_from_tensor(d, 2, 8, transform=ct)
         with pytest.raises(isx.IsxError) as ei:
             codec.encode_tiles([t], out, offs)
-        assert ei.value.status == isx.ISX_ERR_ARG and "3-channel" in str(ei.value)
+        assert ei.value.status == isx.ISX_ERR_ARG and msg in str(ei.value)
         with pytest.raises(isx.IsxError) as ei:
             codec.decode_region(out, offs, [t], 0, (0, 0, 24, 16), d)
-        assert ei.value.status == isx.ISX_ERR_ARG and "3-channel" in str(ei.value)
+        assert ei.value.status == isx.ISX_ERR_ARG and msg in str(ei.value)
     assert codec.sync_status() == 0
 
 

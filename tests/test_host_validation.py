@@ -48,14 +48,21 @@ def _static(t, d_out=None, cap=0):
 
 @pytest.mark.parametrize("field,value,msg", [
     ("width", 0, "width/height"), ("width", 65536, "width/height"), ("height", -3, "width/height"),
-    ("channels", 2, "channels"), ("channels", 4, "channels"), ("bits", 0, "bits"), ("bits", 17, "bits"),
-    ("bits", 9, "3-channel"), ("bits", 12, "3-channel"), ("bits", 16, "3-channel"),
+    ("channels", 0, "channels"), ("channels", 17, "channels"), ("bits", 0, "bits"), ("bits", 17, "bits"),
+    ("transform", 4, "transform"), ("transform", -1, "transform"), ("reserved", 1, "reserved"),
     ("levels", -1, "levels"), ("levels", 16, "levels"), ("x0", -1, "origin"), ("y0", -256, "origin"),
     ("pixels", 0, "pixels"), ("row_pitch_bytes", 64 * 3 - 1, "row pitch"),
 ])
 def test_static_encode_rejects_bad_descriptors(field, value, msg):
     rc, err, _ = _static(_desc(**{field: value}))
     assert rc == isx.ISX_ERR_ARG and msg in err, (rc, err)
+
+
+@pytest.mark.parametrize("channels", [1, 2])
+@pytest.mark.parametrize("transform", [2, 3])
+def test_colour_transform_needs_three_channels(channels, transform):
+    rc, err, _ = _static(_desc(channels=channels, transform=transform, row_pitch_bytes=64 * channels))
+    assert rc == isx.ISX_ERR_ARG and "3 or more channels" in err, (rc, err)
 
 
 def test_static_encode_rejects_bad_quantiser_steps_and_buffers():
@@ -78,15 +85,16 @@ def test_static_encode_reads_no_step_past_the_ll_band():
 
 @pytest.mark.parametrize("w,h", [(512, 512), (511, 509), (1, 512), (512, 1), (257, 300)])
 def test_static_scratch_holds_every_tile_up_to_512(w, h):
-    """The documented bound: a tile of at most 512 x 512 pixels fits the
-    16 MiB static scratch at any channel count, bit depth and level count,
-    so the sizing passes and the call proceeds to the device (which this
-    machine lacks: a CUDA error, not ISX_ERR_OOM)."""
+    """The documented bound: a tile of at most 512 x 512 pixels and 4
+    channels fits the 16 MiB static scratch at any bit depth, colour
+    transform and level count, so the sizing passes and the call proceeds to
+    the device (which this machine lacks: a CUDA error, not ISX_ERR_OOM)."""
     _no_gpu()
-    for c in (1, 3):
-        for bits in ((1, 8, 12, 13, 16) if c == 1 else (1, 8)):
+    for c in (1, 2, 3, 4):
+        for bits in (1, 8, 11, 12, 13, 16):
             for levels in range(16):
                 t = _desc(width=w, height=h, channels=c, bits=bits, levels=levels,
+                          transform=3 if c >= 3 and levels % 2 else 0,
                           row_pitch_bytes=w * c * (1 if bits <= 8 else 2))
                 rc, err, _ = _static(t)
                 assert rc == isx.ISX_ERR_CUDA, (w, h, c, bits, levels, rc, err)

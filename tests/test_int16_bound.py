@@ -143,8 +143,17 @@ def test_library_routing_on_the_workloads():
     # more dropped planes: larger deviation, never a smaller bound
     b = [isx.decode_path(isx.Tile(256, 256, 1, 12, 6, (4,) * 7), 0, k)[1] for k in range(6)]
     assert all(x <= y for x, y in zip(b, b[1:]))
+    # RGB above 8 bits: the colour transform doubles the chroma range, int16 holds it up to 11 bits
+    for ct in (isx.CT_DEFAULT, isx.CT_RCT, isx.CT_YCOCG_R):
+        assert isx.decode_path(isx.Tile(256, 256, 3, 11, 8, transform=ct), 0, 0)[0] == 1
+        assert isx.decode_path(isx.Tile(256, 256, 3, 12, 8, transform=ct), 0, 0)[0] == 0
+    # channels coded as they are keep the mono range: 12 bits fit, 13 do not
+    assert isx.decode_path(isx.Tile(256, 256, 4, 12, 8, transform=isx.CT_NONE), 0, 0)[0] == 1
+    assert isx.decode_path(isx.Tile(256, 256, 3, 12, 8, transform=isx.CT_NONE), 0, 0)[0] == 1
+    assert isx.decode_path(isx.Tile(256, 256, 2, 13, 8), 0, 0)[0] == 0
     # invalid descriptors and levels
-    assert isx.decode_path(isx.Tile(256, 256, 2, 8, 3), 0, 0)[0] == -1
+    assert isx.decode_path(isx.Tile(256, 256, 17, 8, 3), 0, 0)[0] == -1
+    assert isx.decode_path(isx.Tile(256, 256, 2, 8, 3, transform=isx.CT_RCT), 0, 0)[0] == -1
     assert isx.decode_path(isx.Tile(256, 256, 1, 8, 3), 4, 0)[0] == -1
 
 
