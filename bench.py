@@ -246,6 +246,24 @@ def kept_symbol_bytes(raw, offs, grid, levels, channels):
     return len(d), int((kept * (bw * bh // 8)).sum())
 
 
+def stamp_latency(st, n):
+    """p50 / p99 / max of the per-tile encode and decode latencies (ms) from isx_set_tile_stamps arrays:
+    end - start of each tile that both stamps saw."""
+    out = {}
+    for name, k in (("encode", 0), ("decode", 2)):
+        s0, s1 = st[k * n:(k + 1) * n], st[(k + 1) * n:(k + 2) * n]
+        ok = (s0 != np.iinfo(np.uint64).max) & (s1 != 0) & (s1 >= s0)
+        d = np.sort((s1[ok] - s0[ok]).astype(np.float64) / 1e6)
+        if not len(d):
+            out[name] = None
+            continue
+        out[name] = {"p50": round(float(d[len(d) // 2]), 3), "p99": round(float(d[int(0.99 * (len(d) - 1))]), 3),
+                     "max": round(float(d[-1]), 3), "tiles": int(len(d))}
+    out["what"] = ("per tile, %globaltimer from its first kernel to its last step (tile header written / pixels stored), "
+                   "every tile of one call")
+    return out
+
+
 def make_slide(seed):
     import torch
     from paper_2005_08713_gb300 import synth
@@ -460,8 +478,18 @@ def run_gpu(args):
     path["encode_frac"] = round(path["encode_GBps"] / hbm, 4)
     path["decode_frac"] = round(path["decode_GBps"] / hbm, 4)
 
-    # per-tile decode latency (single-tile region requests), device time
+    # per-tile latency inside the full-image encode and decode: %globaltimer stamps of every tile's first
+    # kernel and of its last step (its tile header, its stored pixels), one stamped step after the timed region
+    stamps = torch.zeros(4 * len(grid), dtype=torch.int64, device=dev)
+    codec.set_tile_stamps(stamps)
+    step()
+    torch.cuda.synchronize()
+    codec.set_tile_stamps(None)
+    tile_lat = stamp_latency(stamps.cpu().numpy().view(np.uint64), len(grid))
+
+    # per-tile decode latency (single-tile region requests): device events, and the host time of the call
     lat = [float("nan")]
+    host_ms = []
     rng = np.random.default_rng(3)
     tile_out = torch.empty((TILE, TILE, 3), dtype=torch.uint8, device=dev)
     for i in ([] if args.no_latency else rng.choice(n_tiles, min(64, n_tiles), replace=False).tolist()):
@@ -469,11 +497,14 @@ def run_gpu(args):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
+        h0 = time.perf_counter()
         codec.decode_region(d_out, d_offs, tiles, 0, (x, y, w, h), tile_out, 0, stream)
+        host_ms.append((time.perf_counter() - h0) * 1e3)
         b.record(stream)
         b.synchronize()
         lat.append(a.elapsed_time(b))
     lat = sorted(v for v in lat if v == v) or [float("nan")]
+    host_ms = sorted(host_ms) or [float("nan")]
 
     # end to end through the host-buffer entry points (pinned host memory)
     h_np = h_img.numpy()
@@ -548,7 +579,11 @@ def run_gpu(args):
            "decode_mps": round(mp / (statistics.median(dec_ms) / 1e3), 1),
            "compressed_bytes": total_bytes, "bits_per_pixel": round(8 * total_bytes / (IMG_W * IMG_H), 3),
            "exact": exact, "roofline": roof, "path_roofline": path,
-           "tile_decode_latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[int(0.99 * (len(lat) - 1))], 3)},
+           "tile_decode_latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[int(0.99 * (len(lat) - 1))], 3),
+                                      "host_call_p50": round(host_ms[len(host_ms) // 2], 3),
+                                      "what": "one 256x256 tile decoded alone by isx_decode_region (device events around "
+                                              "the call, host planning included)"},
+           "tile_latency_in_step_ms": tile_lat,
            "stages_ms": {k: round(v[0] / max(1, v[1]), 3) for k, v in stages.items()},
            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
            "lossless": lossless, "single_image_configs": singles}
@@ -659,8 +694,11 @@ def run_batch(args, dev, n_tiles=4096):
     t0 = time.perf_counter()
     sched = codec.autotune(tarr, reps=3, stream=stream)
     tune_s = time.perf_counter() - t0
+    stamps = torch.zeros(4 * n_tiles, dtype=torch.int64, device=dev)
+    codec.set_tile_stamps(stamps)   # the plans record per-tile stamps on every launch
     penc = codec.plan_encode(tarr)
     pdec = codec.plan_decode(tarr, jobs)
+    codec.set_tile_stamps(None)
     with torch.cuda.stream(stream):
         penc.launch_encode(d_out, d_offs, stream)
         pdec.launch_decode(d_out, d_offs, stream)
@@ -685,6 +723,7 @@ def run_batch(args, dev, n_tiles=4096):
         for _ in range(args.warmup):
             g.replay()
         graph_ms = timed(g.replay, max(3, args.steps))
+    tile_lat = stamp_latency(stamps.cpu().numpy().view(np.uint64), n_tiles)
 
     def eager():
         penc.launch_encode(d_out, d_offs, stream)
@@ -729,6 +768,7 @@ def run_batch(args, dev, n_tiles=4096):
     out = {"workload": f"batch_{n_tiles}_mixed_17to256px_rgb8_mono12_L2to6_lossless_lossy", "tiles": n_tiles,
            "megapixels": round(mp, 2), "unit": "MP/s (encode + decode round trip)",
            "graph": {"ms": round(graph_ms, 3), "MP_per_s": round(mp / (graph_ms / 1e3), 1), "kernels": launches},
+           "tile_latency_ms": tile_lat,
            "eager_plans": {"ms": round(eager_ms, 3), "MP_per_s": round(mp / (eager_ms / 1e3), 1)},
            "per_tile_calls": per_tile, "schedule": sched, "autotune_s": round(tune_s, 2),
            "exact": {"sampled_tiles": len(sample), "bit_exact": bool(ok)}}

@@ -190,6 +190,22 @@ const char* isx_last_error(isx_ctx* ctx);
  * 1024, plane <= 160 KB) and the bound is at most 32767. */
 int32_t isx_decode_path(const isx_tile_desc* tile, int32_t level, int32_t drop_lsb_planes, double* h_bound);
 
+/* Per-tile latency stamps: d_stamps is a DEVICE array of 4 * n_tiles uint64
+ * (nanoseconds of the GPU's global timer, %globaltimer) owned by the
+ * caller, or NULL to stop.  Later calls on the context (and plans created
+ * while it is set) record, for tile i (its index in tiles[] for an encode,
+ * its index in the stream's offset table for a decode):
+ *   [i]            encode start: the earliest start of its first kernel,
+ *   [n_tiles + i]  encode end: its tile header written, the last step of
+ *                  its stream,
+ *   [2 n_tiles + i] decode start: its stream header parsed,
+ *   [3 n_tiles + i] decode end: its pixels stored.
+ * Each encode (decode) clears its two arrays on its stream before its
+ * kernels (start to ~0, end to 0), so tiles a call does not touch keep
+ * those values.  A call with more tiles than n_tiles is an argument error.
+ * No counterpart in the paper: this measures tile latency inside batches. */
+isx_status isx_set_tile_stamps(isx_ctx* ctx, uint64_t* d_stamps, int32_t n_tiles);
+
 /* ------------------------------------------------------------------------
  * Batching and serving.  These entry points have no counterpart in the
  * paper; they organise many tiles and many requests around the same coding

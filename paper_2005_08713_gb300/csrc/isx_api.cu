@@ -88,6 +88,8 @@ struct isx_ctx {
   Schedule sched;
   std::string err;
   int launches = 0;
+  uint64_t* stamps = nullptr;      // per-tile timestamps (isx_set_tile_stamps), 4 x stamp_n
+  int32_t stamp_n = 0;
 };
 
 namespace {
@@ -217,6 +219,8 @@ struct EncodeLayout {
   FusedClass cls[ISX_SIZE_CLASSES];
   int64_t level_blocks[16] = {};
   int level_quads[16] = {};
+  uint64_t* stamps = nullptr;
+  int32_t stamp_n = 0;
   size_t o_tiles = 0, o_task = 0, o_blocks = 0, o_A = 0, o_B = 0, o_coef = 0, o_sym = 0, o_stats = 0, o_codes = 0, o_hdrs = 0;
   size_t o_is = 0, o_fp = 0, o_perm = 0, o_bucket = 0, o_part = 0, o_tot = 0, total = 0;
 };
@@ -224,9 +228,15 @@ struct EncodeLayout {
 // Host planning of an encode: descriptors into h_tiles[n], fused tasks into
 // h_task[n], sizes and the device layout into E.
 isx_status plan_encode(const isx_tile_desc* tiles, int32_t n, bool allow_fused, const Schedule& S, TileDev* h_tiles, int32_t* h_task,
-                       EncodeLayout& E, std::string* err) {
+                       EncodeLayout& E, std::string* err, uint64_t* stamps = nullptr, int32_t stamp_n = 0) {
   E = EncodeLayout();
   E.n_tiles = n;
+  if (stamps && stamp_n < n) {
+    *err = "the tile stamp array holds fewer entries than the call's tiles";
+    return ISX_ERR_ARG;
+  }
+  E.stamps = stamps;
+  E.stamp_n = stamp_n;
   std::vector<FusedTask> fused;
   for (int32_t i = 0; i < n; ++i) {
     const isx_tile_desc& t = tiles[i];
@@ -241,6 +251,9 @@ isx_status plan_encode(const isx_tile_desc* tiles, int32_t n, bool allow_fused, 
     level_blocks(t, E.level_blocks, E.level_quads);
     TileDev& d = h_tiles[i];
     fill_tiledev(d, t);
+    d.stamps = stamps;
+    d.stamp_n = stamp_n;
+    d.stamp_i = i;
     d.nb = (int32_t)nb;
     d.block_base = E.n_blocks;
     d.coef_base = E.coef_bytes;
@@ -293,6 +306,10 @@ int launch_encode(const EncodeLayout& E, uint8_t* base, void* d_out, size_t out_
   int32_t* B = (int32_t*)(base + E.o_B);
   uint8_t* coef = base + E.o_coef;
   T->mark("encode.plan", s);
+  if (E.stamps) {   // start: the earliest kernel of a tile (a minimum), end: its tile header (a maximum)
+    cudaMemsetAsync(E.stamps, 0xff, 8 * (size_t)E.stamp_n, s);
+    cudaMemsetAsync(E.stamps + E.stamp_n, 0, 8 * (size_t)E.stamp_n, s);
+  }
   int L = launch_plan_blocks(d_tiles, E.n_tiles, 0, d_blocks, s);
   T->mark("encode.transform", s);
   for (const FusedClass& c : E.cls)
@@ -338,18 +355,27 @@ struct DecodeLayout {
   int64_t n_blocks = 0, plane_total = 0, fplane_total = 0, sym_cap = 0, max_items = 0;
   int max_levels = 0, max_dim = 1, max_c = 1, n_fused = 0;
   FusedClass cls[ISX_SIZE_CLASSES];
+  uint64_t* stamps = nullptr;
+  int32_t stamp_n = 0;
   size_t o_tiles = 0, o_idx = 0, o_task = 0, o_blocks = 0, o_bb = 0, o_bl = 0, o_info = 0, o_sb = 0, o_so = 0, o_part = 0, o_tot = 0;
   size_t o_tab = 0, o_bucket = 0, o_items = 0, o_sym = 0, o_A = 0, o_B = 0, o_fp = 0, o_tk = 0, total = 0;
-  size_t o_perm = 0, o_icnt = 0, o_ibase = 0;
+  size_t o_perm = 0, o_icnt = 0, o_ibase = 0, o_big = 0;
 };
 
 // Host planning of a decode: one descriptor per job whose tile meets its
 // rectangle (h_tiles, h_index, h_task hold n_jobs entries).
 isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* jobs, int32_t n_jobs, int z, int drop, const Schedule& S,
-                       TileDev* h_tiles, int64_t* h_index, int32_t* h_task, DecodeLayout& D, std::string* err) {
+                       TileDev* h_tiles, int64_t* h_index, int32_t* h_task, DecodeLayout& D, std::string* err,
+                       uint64_t* stamps = nullptr, int32_t stamp_n = 0) {
   D = DecodeLayout();
   D.z = z;
   D.drop = drop;
+  if (stamps && stamp_n < n_tiles) {
+    *err = "the tile stamp array holds fewer entries than the stream's tiles";
+    return ISX_ERR_ARG;
+  }
+  D.stamps = stamps;
+  D.stamp_n = stamp_n;
   std::vector<FusedTask> fused;
   for (int32_t j = 0; j < n_jobs; ++j) {
     const Job& jb = jobs[j];
@@ -377,6 +403,9 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
     D.max_items += planes * nb;
     TileDev& d = h_tiles[D.nsel];
     fill_tiledev(d, t);
+    d.stamps = stamps;
+    d.stamp_n = stamp_n;
+    d.stamp_i = jb.tile;
     d.nb = (int32_t)nb;
     d.block_base = D.n_blocks;
     d.coef_base = 0;
@@ -421,6 +450,7 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
   D.o_perm = cv.take(8 * nb);
   D.o_icnt = cv.take(8 * nb);
   D.o_ibase = cv.take(8 * nb);
+  D.o_big = cv.take(8 * (size_t)D.max_items);
   D.o_sym = cv.take((size_t)D.sym_cap + 64);
   D.o_A = cv.take(4 * (size_t)D.plane_total);
   D.o_B = cv.take(4 * (size_t)D.plane_total);
@@ -429,6 +459,10 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
   D.total = cv.used;
   return ISX_OK;
 }
+
+// Decodes of at most this many blocks (about 300 tiles of 256 x 256) run in
+// latency mode (DecodeBuffers::latency_mode).
+constexpr int64_t kLatencyBlocks = 8192;
 
 // The kernels (and ticket clears) of a decode on descriptors already at base.
 int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, const uint64_t* d_tile_offsets, int* d_status,
@@ -448,7 +482,14 @@ int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, co
   db.tables = base + D.o_tab; db.bucket = (int64_t*)(base + D.o_bucket); db.items = (int64_t*)(base + D.o_items);
   db.max_items = D.max_items;
   db.perm = (int64_t*)(base + D.o_perm); db.item_cnt = (int64_t*)(base + D.o_icnt); db.item_base = (int64_t*)(base + D.o_ibase);
+  db.big = (int64_t*)(base + D.o_big);
+  // a decode of few blocks leaves most of the GPU idle: its long segments are decoded one warp each
+  db.latency_mode = D.n_blocks <= kLatencyBlocks;
   db.global_rebuild = D.n_fused < D.nsel;
+  if (D.stamps) {   // start: its stream header parsed (a minimum), end: its pixels stored (a maximum)
+    cudaMemsetAsync(D.stamps + 2 * (size_t)D.stamp_n, 0xff, 8 * (size_t)D.stamp_n, s);
+    cudaMemsetAsync(D.stamps + 3 * (size_t)D.stamp_n, 0, 8 * (size_t)D.stamp_n, s);
+  }
   int L = launch_decode_blocks(db, s, T);
   T->mark("decode.inverse_transform", s);
   uint32_t* tickets = (uint32_t*)(base + D.o_tk);
@@ -479,7 +520,8 @@ isx_status decode_jobs_ctx(isx_ctx* ctx, const void* d_stream, const uint64_t* d
   if (st != ISX_OK) return st;
   DecodeLayout D;
   std::string err;
-  st = plan_decode(tiles, n_tiles, jobs, n_jobs, z, drop, ctx->sched, ctx->h_tiles, ctx->h_index, ctx->h_task, D, &err);
+  st = plan_decode(tiles, n_tiles, jobs, n_jobs, z, drop, ctx->sched, ctx->h_tiles, ctx->h_index, ctx->h_task, D, &err, ctx->stamps,
+                   ctx->stamp_n);
   if (st != ISX_OK) return fail(ctx, st, err);
   ctx->launches = 0;
   if (D.nsel == 0) return ISX_OK;
@@ -589,6 +631,14 @@ int32_t isx_stage_times(isx_ctx* ctx, char* names, int64_t names_len, double* ms
 
 const char* isx_last_error(isx_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+isx_status isx_set_tile_stamps(isx_ctx* ctx, uint64_t* d_stamps, int32_t n_tiles) {
+  if (!ctx) return ISX_ERR_ARG;
+  if (d_stamps && n_tiles < 1) return fail(ctx, ISX_ERR_ARG, "stamps need n_tiles >= 1");
+  ctx->stamps = d_stamps;
+  ctx->stamp_n = d_stamps ? n_tiles : 0;
+  return ISX_OK;
+}
+
 int32_t isx_decode_path(const isx_tile_desc* tile, int32_t level, int32_t drop_lsb_planes, double* h_bound) {
   std::string why;
   if (!tile || !tile_ok(*tile, &why) || level < 0 || level > tile->levels || drop_lsb_planes < 0) return -1;
@@ -671,7 +721,7 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   if (st != ISX_OK) return st;
   EncodeLayout E;
   std::string err;
-  st = plan_encode(tiles, n_tiles, true, ctx->sched, ctx->h_tiles, ctx->h_task, E, &err);
+  st = plan_encode(tiles, n_tiles, true, ctx->sched, ctx->h_tiles, ctx->h_task, E, &err, ctx->stamps, ctx->stamp_n);
   if (st != ISX_OK) return fail(ctx, st, err);
   st = ensure_arena(ctx, E.total);
   if (st != ISX_OK) return st;
@@ -698,11 +748,13 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   int C = -1, bits = -1;
   for (int32_t i = 0; i < n_tiles; ++i) {
     const isx_tile_desc& t = tiles[i];
-    std::string why;
-    if (!tile_ok(t, &why)) return fail(ctx, ISX_ERR_ARG, "tile " + std::to_string(i) + ": " + why);
+    // tiles outside the rectangle are not read: only the ones it meets are checked
+    if (t.width < 1 || t.height < 1 || t.x0 < 0 || t.y0 < 0) return fail(ctx, ISX_ERR_ARG, "tile " + std::to_string(i) + ": bad geometry");
     const int zw = level_dim(t.width, level), zh = level_dim(t.height, level);
     const int tx = t.x0 >> level, ty = t.y0 >> level;
     if (tx >= rx + rw || ty >= ry + rh || tx + zw <= rx || ty + zh <= ry) continue;
+    std::string why;
+    if (!tile_ok(t, &why)) return fail(ctx, ISX_ERR_ARG, "tile " + std::to_string(i) + ": " + why);
     if (C < 0) { C = t.channels; bits = t.bits; }
     if (t.channels != C || (t.bits <= 8) != (bits <= 8))
       return fail(ctx, ISX_ERR_ARG, "tiles of one region must share channels and sample size");
@@ -1010,7 +1062,7 @@ isx_status isx_plan_encode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_t
   std::vector<TileDev> ht(n_tiles);
   std::vector<int32_t> htask(n_tiles);
   std::string err;
-  isx_status st = plan_encode(tiles, n_tiles, true, ctx->sched, ht.data(), htask.data(), P->E, &err);
+  isx_status st = plan_encode(tiles, n_tiles, true, ctx->sched, ht.data(), htask.data(), P->E, &err, ctx->stamps, ctx->stamp_n);
   cudaError_t e = cudaSuccess;
   if (st == ISX_OK) {
     P->mem_bytes = P->E.total;
@@ -1049,7 +1101,7 @@ isx_status isx_plan_decode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_t
   std::vector<int32_t> htask(n_jobs);
   std::string err;
   isx_status st = plan_decode(tiles, n_tiles, J.data(), n_jobs, level, drop_lsb_planes, ctx->sched, ht.data(), hidx.data(), htask.data(),
-                              P->D, &err);
+                              P->D, &err, ctx->stamps, ctx->stamp_n);
   cudaError_t e = cudaSuccess;
   if (st == ISX_OK) {
     P->mem_bytes = P->D.total;

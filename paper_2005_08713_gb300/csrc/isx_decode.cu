@@ -37,6 +37,7 @@ __global__ void k_decode_plan(const TileDev* __restrict__ tiles, int n_tiles, co
   const int ti = blockIdx.x * blockDim.x + threadIdx.x;
   if (ti >= n_tiles) return;
   const TileDev t = tiles[ti];
+  stamp_tile(t, kStampDecStart);
   const int64_t src = tile_index[ti];
   const int64_t toff = (int64_t)offs[src], tend = (int64_t)offs[src + 1];
   const uint8_t* s = stream + toff;
@@ -87,58 +88,6 @@ __global__ void k_decode_plan(const TileDev* __restrict__ tiles, int n_tiles, co
   if (!ok) set_status(status, kStCorrupt);
 }
 
-// MSB-first bit reader over a block's bytes (bytes outside the block read
-// as 0).  It always loads aligned 32-bit words; only a word that crosses
-// the block's first or last byte is assembled byte by byte.
-struct BitIn {
-  const uint8_t* p;
-  int64_t nbytes;
-  int64_t wbyte;   // offset of the next word to load, relative to p (aligned in memory)
-  uint64_t buf;    // left aligned
-  int nbuf;
-  int64_t pos;     // bit position of the next unread bit, relative to p
-  __device__ uint32_t load_word() {
-    uint32_t w;
-    if (wbyte >= 0 && wbyte + 4 <= nbytes) {
-      w = __byte_perm(*reinterpret_cast<const uint32_t*>(p + wbyte), 0, 0x0123);
-    } else {
-      w = 0;
-      for (int k = 0; k < 4; ++k) {
-        const int64_t o = wbyte + k;
-        w = (w << 8) | (uint32_t)(o >= 0 && o < nbytes ? p[o] : 0);
-      }
-    }
-    wbyte += 4;
-    return w;
-  }
-  __device__ void seek(int64_t bitpos) {
-    const int64_t byte = bitpos >> 3;
-    const int mis = (int)(reinterpret_cast<uintptr_t>(p + byte) & 3);
-    wbyte = byte - mis;
-    buf = (uint64_t)load_word() << 32;
-    buf |= load_word();
-    const int drop = mis * 8 + (int)(bitpos & 7);
-    buf <<= drop;
-    nbuf = 64 - drop;
-    pos = bitpos;
-  }
-  __device__ uint32_t peek(int n) const { return n ? (uint32_t)(buf >> (64 - n)) : 0u; }
-  __device__ void skip(int n) {   // n <= 32
-    buf <<= n;
-    nbuf -= n;
-    pos += n;
-    if (nbuf <= 32) {
-      buf |= (uint64_t)load_word() << (32 - nbuf);
-      nbuf += 32;
-    }
-  }
-  __device__ uint32_t get(int n) {
-    uint32_t v = peek(n);
-    skip(n);
-    return v;
-  }
-};
-
 __device__ inline uint32_t kept_mask(const uint32_t* removed, int p, int pl) {
   uint32_t km = 0;
 #pragma unroll
@@ -162,127 +111,6 @@ struct DecTab {
   uint32_t seglen[32];
   int32_t czr, wbits, nnodes, pad;
 };
-
-// Header pass: one thread per block parses the Fig. 3 header (d, removed
-// mask, C_zr, w, t, seektable, preorder tree), builds the block's decode
-// table and sizes its symbol region.
-__global__ void k_dec_tables(const BlockDev* __restrict__ blocks, int64_t nb, const uint8_t* __restrict__ stream,
-                             const int64_t* __restrict__ bbyte, const int32_t* __restrict__ blen, int drop, DecInfo* __restrict__ info,
-                             DecTab* __restrict__ tabs, int64_t* __restrict__ sym_bytes, int* __restrict__ status) {
-  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (bi >= nb) return;
-  const BlockDev b = blocks[bi];
-  DecInfo di;
-  di.d = 0; di.keep = 0; di.removed[0] = di.removed[1] = di.removed[2] = ~0u;
-  int64_t bytes = 0;
-  DecTab& T = tabs[bi];
-  T.nnodes = 0;
-  if (b.p > 0) {
-    const int nbytes = blen[bi];
-    const int64_t nbits = (int64_t)nbytes * 8;
-    BitIn in{stream + bbyte[bi], nbytes, 0, 0, 0, 0};
-    in.seek(0);
-    int d = (int)in.get(5);
-    bool any = false;
-    for (int t = 0; t < 3; ++t) {
-      uint32_t r = 0;
-      for (int pl = 0; pl < d; ++pl) {
-        if (t >= b.p || in.get(1)) r |= 1u << pl;
-        else any = true;
-      }
-      di.removed[t] = r;
-    }
-    bool ok = d >= 1 && in.pos <= nbits;
-    if (ok && any) {
-      T.czr = (int)in.get(8);
-      T.wbits = (int)in.get(5);
-      const int t = (int)in.get(5);
-      ok = t >= 1 && T.wbits >= 1;
-      for (int pl = 0; ok && pl < d; ++pl) T.seglen[pl] = in.get(t);
-      // Preorder tree: 0 = internal node (its left subtree, then its right
-      // subtree, follow), 1 + 8 bits = leaf.  The walk keeps the current
-      // node's code and depth only: a left child is the node read right after
-      // its parent (kid0 = parent + 1); after a leaf the walk climbs while
-      // the node is a right child (odd code) and moves to the sibling.  The
-      // internal node entered at each depth is remembered to receive its
-      // right child's index (kid1).
-      int path[33];
-      uint32_t code = 0;
-      int dep = 0, nn = 0;
-      while (ok) {
-        if (nn >= 511 || in.pos >= nbits) { ok = false; break; }
-        const int v = nn++;
-        if (dep > 0 && (code & 1u)) T.node[path[dep - 1]] |= (uint32_t)v << 16;
-        if (in.get(1)) {
-          const uint32_t sym = in.get(8);
-          T.node[v] = 0x80000000u | sym;
-          if (dep <= kTabBits) {
-            const uint32_t lo = code << (kTabBits - dep), cnt = 1u << (kTabBits - dep);
-            const uint32_t e = ((uint32_t)dep << 8) | sym;
-            if (cnt >= 8) {   // whole 8-entry groups, 16-byte aligned
-              const uint32_t e2 = e | (e << 16);
-              uint4* t4 = reinterpret_cast<uint4*>(T.tab + lo);
-              for (uint32_t k = 0; k < (cnt >> 3); ++k) t4[k] = make_uint4(e2, e2, e2, e2);
-            } else {
-              for (uint32_t k = 0; k < cnt; ++k) T.tab[lo + k] = (uint16_t)e;
-            }
-          }
-          while (dep > 0 && (code & 1u)) {
-            code >>= 1;
-            --dep;
-          }
-          if (dep == 0) break;   // back at the root: the tree is complete
-          code |= 1u;            // the right sibling
-        } else {
-          if (dep >= 32) { ok = false; break; }   // codes longer than 32 bits
-          if (dep == kTabBits) T.tab[code] = (uint16_t)(0x8000 | v);
-          T.node[v] = (uint32_t)(v + 1);   // kid0; kid1 is set when the right child starts
-          path[dep] = v;
-          code <<= 1;
-          ++dep;
-        }
-      }
-      if (ok) {
-        int64_t pos = in.pos;
-        for (int pl = 0; pl < d; ++pl) {
-          T.segpos[pl] = pos;
-          pos += T.seglen[pl];
-        }
-        ok = pos <= nbits;
-        T.nnodes = nn;
-      }
-    }
-    if (!ok) {
-      set_status(status, kStCorrupt);
-      d = 0;
-      T.nnodes = 0;
-    }
-    di.d = d;
-    di.keep = d ? max(1, d - drop) : 0;
-    const int n = b.w * b.h / 8;
-    for (int pl = 0; pl < di.keep; ++pl) bytes += plane_region(kept_mask(di.removed, b.p, pl), n);
-  }
-  info[bi] = di;
-  sym_bytes[bi] = bytes;
-}
-
-// Blocks ordered by level (counting sort): neighbouring blocks in the order
-// have the same size.
-constexpr int kLevels = 16;
-
-__global__ void k_dec_level_count(const BlockDev* __restrict__ blocks, int64_t nb, int64_t* __restrict__ cnt) {
-  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (bi >= nb) return;
-  atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[blocks[bi].level]), 1ull);
-}
-
-__global__ void k_dec_level_fill(const BlockDev* __restrict__ blocks, int64_t nb, const int64_t* __restrict__ off, int64_t* __restrict__ fill,
-                                 int64_t* __restrict__ perm) {
-  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (bi >= nb) return;
-  const int l = blocks[bi].level;
-  perm[off[l] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&fill[l]), 1ull)] = bi;
-}
 
 // Double-buffered MSB-first reader: 16-byte chunks are requested one chunk
 // ahead of use; bytes outside the block read as 0.
@@ -364,6 +192,127 @@ struct BitPf {
   }
 };
 
+// Header pass: one thread per block parses the Fig. 3 header (d, removed
+// mask, C_zr, w, t, seektable, preorder tree), builds the block's decode
+// table and sizes its symbol region.
+__global__ void k_dec_tables(const BlockDev* __restrict__ blocks, int64_t nb, const uint8_t* __restrict__ stream,
+                             const int64_t* __restrict__ bbyte, const int32_t* __restrict__ blen, int drop, DecInfo* __restrict__ info,
+                             DecTab* __restrict__ tabs, int64_t* __restrict__ sym_bytes, int* __restrict__ status) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= nb) return;
+  const BlockDev b = blocks[bi];
+  DecInfo di;
+  di.d = 0; di.keep = 0; di.removed[0] = di.removed[1] = di.removed[2] = ~0u;
+  int64_t bytes = 0;
+  DecTab& T = tabs[bi];
+  T.nnodes = 0;
+  if (b.p > 0) {
+    const int nbytes = blen[bi];
+    const int64_t nbits = (int64_t)nbytes * 8;
+    BitPf in;
+    in.seek(stream + bbyte[bi], nbytes, 0);
+    int d = (int)in.get(5);
+    bool any = false;
+    for (int t = 0; t < 3; ++t) {
+      uint32_t r = 0;
+      for (int pl = 0; pl < d; ++pl) {
+        if (t >= b.p || in.get(1)) r |= 1u << pl;
+        else any = true;
+      }
+      di.removed[t] = r;
+    }
+    bool ok = d >= 1 && in.pos <= nbits;
+    if (ok && any) {
+      T.czr = (int)in.get(8);
+      T.wbits = (int)in.get(5);
+      const int t = (int)in.get(5);
+      ok = t >= 1 && T.wbits >= 1;
+      for (int pl = 0; ok && pl < d; ++pl) T.seglen[pl] = in.get(t);
+      // Preorder tree: 0 = internal node (its left subtree, then its right
+      // subtree, follow), 1 + 8 bits = leaf.  The walk keeps the current
+      // node's code and depth only: a left child is the node read right after
+      // its parent (kid0 = parent + 1); after a leaf the walk climbs while
+      // the node is a right child (odd code) and moves to the sibling.  The
+      // internal node entered at each depth is remembered, and its node word
+      // (kid0 | kid1 << 16) is stored once, when its right child starts: no
+      // read-modify-write of global memory.
+      int path[33];
+      uint32_t code = 0;
+      int dep = 0, nn = 0;
+      while (ok) {
+        if (nn >= 511 || in.pos >= nbits) { ok = false; break; }
+        const int v = nn++;
+        if (dep > 0 && (code & 1u)) T.node[path[dep - 1]] = (uint32_t)(path[dep - 1] + 1) | ((uint32_t)v << 16);
+        if (in.get(1)) {
+          const uint32_t sym = in.get(8);
+          T.node[v] = 0x80000000u | sym;
+          if (dep <= kTabBits) {
+            const uint32_t lo = code << (kTabBits - dep), cnt = 1u << (kTabBits - dep);
+            const uint32_t e = ((uint32_t)dep << 8) | sym;
+            if (cnt >= 8) {   // whole 8-entry groups, 16-byte aligned
+              const uint32_t e2 = e | (e << 16);
+              uint4* t4 = reinterpret_cast<uint4*>(T.tab + lo);
+              for (uint32_t k = 0; k < (cnt >> 3); ++k) t4[k] = make_uint4(e2, e2, e2, e2);
+            } else {
+              for (uint32_t k = 0; k < cnt; ++k) T.tab[lo + k] = (uint16_t)e;
+            }
+          }
+          while (dep > 0 && (code & 1u)) {
+            code >>= 1;
+            --dep;
+          }
+          if (dep == 0) break;   // back at the root: the tree is complete
+          code |= 1u;            // the right sibling
+        } else {
+          if (dep >= 32) { ok = false; break; }   // codes longer than 32 bits
+          if (dep == kTabBits) T.tab[code] = (uint16_t)(0x8000 | v);
+          path[dep] = v;
+          code <<= 1;
+          ++dep;
+        }
+      }
+      if (ok) {
+        int64_t pos = in.pos;
+        for (int pl = 0; pl < d; ++pl) {
+          T.segpos[pl] = pos;
+          pos += T.seglen[pl];
+        }
+        ok = pos <= nbits;
+        T.nnodes = nn;
+      }
+    }
+    if (!ok) {
+      set_status(status, kStCorrupt);
+      d = 0;
+      T.nnodes = 0;
+    }
+    di.d = d;
+    di.keep = d ? max(1, d - drop) : 0;
+    const int n = b.w * b.h / 8;
+    for (int pl = 0; pl < di.keep; ++pl) bytes += plane_region(kept_mask(di.removed, b.p, pl), n);
+  }
+  info[bi] = di;
+  sym_bytes[bi] = bytes;
+}
+
+// Blocks ordered by level (counting sort): neighbouring blocks in the order
+// have the same size.
+constexpr int kLevels = 16;
+
+__global__ void k_dec_level_count(const BlockDev* __restrict__ blocks, int64_t nb, int64_t* __restrict__ cnt) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= nb) return;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[blocks[bi].level]), 1ull);
+}
+
+__global__ void k_dec_level_fill(const BlockDev* __restrict__ blocks, int64_t nb, const int64_t* __restrict__ off, int64_t* __restrict__ fill,
+                                 int64_t* __restrict__ perm) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= nb) return;
+  const int l = blocks[bi].level;
+  perm[off[l] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&fill[l]), 1ull)] = bi;
+}
+
 // 16-byte symbol writer of one thread.
 struct SymOut {
   uint4* dst;          // the 16-byte chunk being filled
@@ -399,31 +348,50 @@ struct SymOut {
 // Segment items (block << 5 | plane) in block-major order: blocks by level
 // (neighbouring blocks have the same size), each block's kept planes in
 // order, so that the 32 lanes of a warp decode the planes of a few blocks
-// whose lookup tables the warp keeps in shared memory.
-__device__ inline uint32_t block_item_planes(const BlockDev& b, const DecInfo& di, const DecTab& T) {
-  uint32_t planes = 0;
+// whose lookup tables the warp keeps in shared memory.  In a latency-bound
+// decode (few blocks: ml_min_bits > 0) the segments of at least ml_min_bits
+// bits go instead to the list `big`, each decoded by a whole warp
+// (k_dec_segments_ml); a block whose tree is a single leaf (0-bit codes)
+// keeps all its segments on one lane each.
+__device__ inline uint32_t block_item_planes(const BlockDev& b, const DecInfo& di, const DecTab& T, int64_t ml_min_bits,
+                                             uint32_t* big_planes) {
+  uint32_t planes = 0, big = 0;
   if (b.p > 0 && di.d > 0 && T.nnodes > 0)
     for (int pl = 0; pl < di.keep; ++pl)
-      if (kept_mask(di.removed, b.p, pl)) planes |= 1u << pl;
+      if (kept_mask(di.removed, b.p, pl)) {
+        // (chunks of at most 65535 bits: the warp decoder records token starts as 16-bit offsets)
+        if (ml_min_bits > 0 && T.nnodes > 1 && (int64_t)T.seglen[pl] >= ml_min_bits && T.seglen[pl] <= 32u * 65535u)
+          big |= 1u << pl;
+        else planes |= 1u << pl;
+      }
+  *big_planes = big;
   return planes;
 }
 
 __global__ void __launch_bounds__(128) k_dec_item_count(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm, int64_t nb,
                                                        const DecInfo* __restrict__ info, const DecTab* __restrict__ tabs,
-                                                       int64_t* __restrict__ cnt) {
+                                                       int64_t ml_min_bits, int64_t* __restrict__ cnt, int64_t* __restrict__ big,
+                                                       int64_t* __restrict__ n_big) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
   const int64_t bi = perm[j];
-  cnt[j] = __popc(block_item_planes(blocks[bi], info[bi], tabs[bi]));
+  uint32_t bigp;
+  cnt[j] = __popc(block_item_planes(blocks[bi], info[bi], tabs[bi], ml_min_bits, &bigp));
+  while (bigp) {
+    const int pl = __ffs(bigp) - 1;
+    bigp &= bigp - 1u;
+    big[atomicAdd(reinterpret_cast<unsigned long long*>(n_big), 1ull)] = (bi << 5) | pl;
+  }
 }
 
 __global__ void __launch_bounds__(128) k_dec_item_fill(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm, int64_t nb,
                                                       const DecInfo* __restrict__ info, const DecTab* __restrict__ tabs,
-                                                      const int64_t* __restrict__ base, int64_t* __restrict__ items) {
+                                                      int64_t ml_min_bits, const int64_t* __restrict__ base, int64_t* __restrict__ items) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
   const int64_t bi = perm[j];
-  uint32_t planes = block_item_planes(blocks[bi], info[bi], tabs[bi]);
+  uint32_t bigp;
+  uint32_t planes = block_item_planes(blocks[bi], info[bi], tabs[bi], ml_min_bits, &bigp);
   int64_t o = base[j];
   while (planes) {
     const int pl = __ffs(planes) - 1;
@@ -542,6 +510,298 @@ __global__ void __launch_bounds__(32 * kSegWarps) k_dec_segments(const BlockDev*
   if (bad || in.pos != limit) set_status(status, kStCorrupt);
 }
 
+// ------------------------------------------ one warp per segment (latency)
+// One token (a codeword, and its w-bit counter when the codeword is C_zr):
+// sym = the literal symbol (0 for a run), cnt = the symbols it stands for.
+// false for a code the tree does not hold (a wrong path or a corrupt stream).
+// The lanes of a warp decode different chunks, so every branch here would
+// split the warp: a code of at most kTabBits bits (all but the rarest
+// symbols) and its counter are decoded with selects, one lookup and one
+// skip; only a longer code walks the tree.  The counter is read from the
+// same 64-bit buffer: at a token's start it holds at least 33 bits, and a
+// code of at most 9 bits plus a counter of at most 18 bits (kMaxW, the
+// widest the encoder writes) fit; a wider counter field takes the tree-walk
+// path's separate read.
+__device__ __forceinline__ bool ml_token(BitPf& in, const uint16_t* tab, const uint32_t* __restrict__ node, int czr, int wb,
+                                         uint32_t* sym, uint32_t* cnt) {
+  const uint32_t e = tab[in.peek(kTabBits)];
+  if (!(e & 0x8000u) && wb <= kMaxW) {
+    const uint32_t len = e >> 8, s = e & 0xffu;
+    const bool run = (int)s == czr;
+    const uint32_t c = (uint32_t)((in.buf << len) >> (64 - wb));   // the counter, if this is C_zr
+    in.skip((int)(len + (run ? (uint32_t)wb : 0u)));
+    *sym = run ? (c ? 0u : s) : s;
+    *cnt = run && c ? c : 1u;
+    return len != 0;   // every code of a tree with two or more leaves has a bit
+  }
+  uint32_t s;
+  if (e & 0x8000u) {
+    uint32_t nd = __ldg(&node[e & 0x1ff]);
+    in.skip(kTabBits);
+    int guard = 0;
+    while (!(nd & 0x80000000u)) {
+      const uint32_t kid = in.get(1) ? (nd >> 16) : (nd & 0xffffu);
+      nd = __ldg(&node[kid & 0x1ff]);
+      if (++guard > 32) return false;
+    }
+    s = nd & 0xffu;
+  } else {
+    if ((e >> 8) == 0) return false;
+    s = e & 0xffu;
+    in.skip((int)(e >> 8));
+  }
+  if ((int)s == czr) {
+    const uint32_t c = in.get(wb);
+    if (c) {
+      *sym = 0;
+      *cnt = c;
+      return true;
+    }
+  }
+  *sym = s;
+  *cnt = 1;
+  return true;
+}
+
+// Writer of one lane's range [s0, s1) of a segment's symbols (the region
+// was cleared beforehand): 16-symbol chunks wholly inside the range are
+// stored, the chunks it shares with a neighbouring lane are OR-ed word by
+// word.
+struct SymOutShared {
+  uint8_t* base;
+  int64_t s0, s1, pos;
+  uint32_t w[4];
+  bool dirty;
+  __device__ void flush_at(int64_t c0) {   // c0: first symbol of the chunk
+    if (dirty) {
+      uint32_t* dst = reinterpret_cast<uint32_t*>(base + c0);
+      if (c0 >= s0 && c0 + 16 <= s1) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (w[k]) atomicOr(dst + k, w[k]);
+      }
+    }
+    w[0] = w[1] = w[2] = w[3] = 0;
+    dirty = false;
+  }
+  __device__ void put(uint32_t s) {
+    if (s) {
+      const int q = (int)(pos & 15);
+      const uint32_t v = s << (8 * (q & 3));
+      // selects instead of an indexed array: w stays in registers
+      if ((q >> 2) == 0) w[0] |= v;
+      else if ((q >> 2) == 1) w[1] |= v;
+      else if ((q >> 2) == 2) w[2] |= v;
+      else w[3] |= v;
+      dirty = true;
+    }
+    ++pos;
+    if ((pos & 15) == 0) flush_at(pos - 16);
+  }
+  __device__ void zeros(uint32_t c) {   // the cleared region already holds them: only the position moves
+    const int64_t end = pos + c;
+    if ((end >> 4) != (pos >> 4)) flush_at((pos >> 4) << 4);
+    pos = end;
+  }
+  __device__ void finish() {
+    if (pos & 15) flush_at((pos >> 4) << 4);
+  }
+  // A token: cnt symbols, all zero but a literal's (cnt = 1).  Selects set the
+  // byte; the chunk is flushed only when the token leaves it.
+  __device__ void token(uint32_t s, uint32_t c) {
+    const int q = (int)(pos & 15);
+    const uint32_t v = s << (8 * (q & 3));
+    w[0] |= (q >> 2) == 0 ? v : 0u;
+    w[1] |= (q >> 2) == 1 ? v : 0u;
+    w[2] |= (q >> 2) == 2 ? v : 0u;
+    w[3] |= (q >> 2) == 3 ? v : 0u;
+    dirty = dirty || s != 0;
+    const int64_t end = pos + c;
+    if ((end >> 4) != (pos >> 4)) flush_at((pos >> 4) << 4);
+    pos = end;
+  }
+};
+
+// Self-synchronising decode of one plane segment per warp, for decodes of
+// few blocks (one tile, a viewport), where a segment decoded serially by one
+// lane would set the call's latency (Sec. 4: the seektable gives every plane
+// segment its own start).  The segment is cut into at most 32 chunks of C
+// bits, one per lane.
+//  1. Each lane decodes its chunk from the chunk's first bit, recording the
+//     bit offsets of the first kMlMarks tokens it starts there, and counts
+//     the symbols.  Only chunk 0 starts on a true token boundary; the other
+//     lanes may start inside a token, but Huffman codes resynchronise: once
+//     two decodes reach the same bit as a token start they agree from then
+//     on.
+//  2. Each lane continues past its chunk's end, token by token, until it
+//     reaches a bit that a later chunk's lane recorded as a token start (or
+//     the segment's end); a chunk it crosses without landing is covered by
+//     it.
+//  3. Following the landings from chunk 0 gives the true token boundary
+//     where each lane's valid decode starts: by induction every lane on that
+//     chain decodes the true token sequence from its boundary on.
+//  4. A lane's valid symbol count is its count from the chunk start plus the
+//     continuation, minus the count of the (short) stretch before its
+//     boundary, decoded again; a warp scan places the lanes.
+//  5. Each valid lane decodes its range again and writes its symbols.
+// The bytes are those of the one-lane decoder.  A stream the true path
+// cannot decode exactly (a bad code, a wrong symbol count, a segment that
+// does not end on its last bit) sets ISX_ERR_CORRUPT.  It costs about twice
+// the one-lane decoder's instructions, so throughput-bound calls (many
+// blocks) keep one lane per segment.
+constexpr int kMlMarks = 64;        // token starts recorded per chunk: the window a landing is searched in
+constexpr int kMlMinChunk = 64;     // bits
+constexpr int64_t kMlMinBits = 2048;
+constexpr int kMlCtas = 152 * 8;
+
+__global__ void __launch_bounds__(32) k_dec_segments_ml(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ big,
+                                                        const int64_t* __restrict__ n_big_p, int64_t* __restrict__ next,
+                                                        const uint8_t* __restrict__ stream, const int64_t* __restrict__ bbyte,
+                                                        const int32_t* __restrict__ blen, const DecInfo* __restrict__ info,
+                                                        const DecTab* __restrict__ tabs, const int64_t* __restrict__ sym_off,
+                                                        uint8_t* __restrict__ sym, const int64_t* __restrict__ sym_total, int64_t sym_cap,
+                                                        int* __restrict__ status) {
+  __shared__ __align__(16) uint16_t s_tab[1 << kTabBits];
+  __shared__ uint16_t s_marks[kMlMarks][32];   // [mark][lane]: a warp's stores and loads of one mark index hit distinct banks
+  __shared__ int s_nm[32];
+  const int lane = threadIdx.x;
+  const uint32_t FULL = 0xffffffffu;
+  if (*sym_total > sym_cap) return;   // reported by the one-lane decoder
+  const int64_t nbig = *n_big_p;
+  for (;;) {
+    int64_t g = 0;
+    if (lane == 0) g = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(next), 1ull);
+    g = __shfl_sync(FULL, g, 0);
+    if (g >= nbig) return;
+    const int64_t item = big[g];
+    const int64_t bi = item >> 5;
+    const int pl = (int)(item & 31);
+    const BlockDev b = blocks[bi];
+    const DecInfo di = info[bi];
+    const DecTab* T = tabs + bi;
+    __syncwarp();   // the previous segment's shared-memory reads are done
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(T->tab);
+      uint4* dst = reinterpret_cast<uint4*>(s_tab);
+      for (int k = lane; k < (1 << kTabBits) / 8; k += 32) dst[k] = __ldg(src + k);
+    }
+    const int n = b.w * b.h / 8;
+    const uint32_t km = kept_mask(di.removed, b.p, pl);
+    int64_t poff = sym_off[bi];
+    for (int r = 0; r < pl; ++r) poff += plane_region(kept_mask(di.removed, b.p, r), n);
+    const int need = __popc(km) * n;
+    const int64_t seg0 = T->segpos[pl], send = seg0 + (int64_t)T->seglen[pl];
+    const int64_t C = max((int64_t)kMlMinChunk, ((int64_t)T->seglen[pl] + 31) / 32);
+    const int N = (int)(((int64_t)T->seglen[pl] + C - 1) / C);
+    const bool act = lane < N;
+    const int j = lane;
+    const int64_t cst = seg0 + (int64_t)j * C, cen = min(cst + C, send);
+    const int czr = T->czr, wb = T->wbits;
+    const uint32_t* node = T->node;
+    const uint8_t* bp = stream + bbyte[bi];
+    const int64_t bl = blen[bi];
+    __syncwarp();   // table in shared memory
+    // 1. speculative decode of the own chunk
+    BitPf in;
+    uint32_t cnt_own = 0, cnt_cont = 0;
+    int nm = 0;
+    bool broken = false;
+    if (act) {
+      in.seek(bp, bl, cst);
+      while (in.pos < cen) {
+        if (nm < kMlMarks) s_marks[nm++][lane] = (uint16_t)(in.pos - cst);
+        uint32_t sy, c;
+        if (!ml_token(in, s_tab, node, czr, wb, &sy, &c)) { broken = true; break; }
+        cnt_own += c;
+      }
+    }
+    s_nm[lane] = nm;
+    __syncwarp();
+    // 2. continuation until a later chunk's recorded token start (or the segment's end)
+    int land_k = N;
+    int64_t land_p = act ? in.pos : 0;
+    if (act && !broken && j < N - 1) {
+      int k = j + 1, ptr = 0;
+      for (;;) {
+        const int64_t p = in.pos;
+        if (p >= send) { land_k = N; land_p = p; break; }
+        while (k < N - 1 && p >= seg0 + (int64_t)(k + 1) * C) { ++k; ptr = 0; }
+        const uint32_t rel = (uint32_t)(p - (seg0 + (int64_t)k * C));
+        const int nmk = s_nm[k];
+        while (ptr < nmk && s_marks[ptr][k] < rel) ++ptr;
+        if (ptr < nmk && s_marks[ptr][k] == rel) { land_k = k; land_p = p; break; }
+        uint32_t sy, c;
+        if (!ml_token(in, s_tab, node, czr, wb, &sy, &c)) { broken = true; break; }
+        cnt_cont += c;
+      }
+    }
+    // 3. the chain of true token boundaries, from chunk 0
+    bool valid = false, chain_bad = false;
+    int64_t vstart = 0, vend = 0;
+    {
+      int cur = 0;
+      int64_t cs = seg0;
+      for (int it = 0; it < 32; ++it) {
+        const int src = min(cur, N - 1) & 31;
+        const int lk = __shfl_sync(FULL, land_k, src);
+        const int64_t lp = __shfl_sync(FULL, land_p, src);
+        const int lb = __shfl_sync(FULL, (int)broken, src);
+        if (cur < N) {
+          if (cur == j) { valid = true; vstart = cs; vend = lp; }
+          if (lb) { chain_bad = true; cur = N; }
+          else { cs = lp; cur = lk; }
+        }
+      }
+    }
+    bool bad = valid && (chain_bad || vend > send);
+    // 4. valid symbol count: own count + continuation - count before the boundary
+    uint32_t vc = 0;
+    if (valid && !bad) {
+      uint32_t prefix = 0;
+      if (vstart > cst) {
+        in.seek(bp, bl, cst);
+        while (in.pos < vstart) {
+          uint32_t sy, c;
+          if (!ml_token(in, s_tab, node, czr, wb, &sy, &c)) { bad = true; break; }
+          prefix += c;
+        }
+        if (in.pos != vstart) bad = true;
+      }
+      vc = cnt_own + cnt_cont - prefix;   // modular: a garbage prefix cancels
+      if (vc > (uint32_t)need) bad = true;
+    }
+    if (!valid || bad) vc = 0;
+    uint32_t incl = vc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t tot = __shfl_sync(FULL, incl, 31);
+    // the segment is written only when every lane agrees that it decodes exactly
+    if (__any_sync(FULL, bad) || tot != (uint32_t)need) {
+      if (lane == 0) set_status(status, kStCorrupt);
+      continue;
+    }
+    // 5. write the valid ranges
+    if (valid && vc) {
+      const int64_t s0 = incl - vc;
+      SymOutShared out{sym + poff, s0, s0 + vc, s0, {0u, 0u, 0u, 0u}, false};
+      in.seek(bp, bl, vstart);
+      bool wbad = false;
+      while (in.pos < vend) {
+        uint32_t sy, c;
+        if (!ml_token(in, s_tab, node, czr, wb, &sy, &c) || out.pos + c > out.s1) { wbad = true; break; }
+        out.token(sy, c);
+      }
+      out.finish();
+      if (wbad || in.pos != vend || out.pos != out.s1) set_status(status, kStCorrupt);
+    }
+  }
+}
+
 // Rebuild pass: per block, every area's 8 coefficients from the decoded
 // planes (sign plane, then magnitude bits d-2 .. 0), dequantised at the bin
 // midpoint, stored into the level-z Mallat plane (padding cropped).
@@ -621,9 +881,13 @@ int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T)
   T->mark("decode.order", s);
   L += launch_exclusive_scan(db.sym_bytes, db.n_blocks, db.sym_off, db.scan_part, db.totals, s);
   L += launch_level_sort(db.blocks, db.n_blocks, db.bucket, db.perm, db.scan_part, db.totals + 2, s);
-  k_dec_item_count<<<g, 128, 0, s>>>(db.blocks, db.perm, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.item_cnt);
+  // totals[3]: segments for the one-warp decoder, totals[4]: its work counter
+  const int64_t ml_bits = db.latency_mode ? kMlMinBits : 0;
+  cudaMemsetAsync(db.totals + 3, 0, 2 * sizeof(int64_t), s);
+  k_dec_item_count<<<g, 128, 0, s>>>(db.blocks, db.perm, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), ml_bits,
+                                     db.item_cnt, db.big, db.totals + 3);
   L += 1 + launch_exclusive_scan(db.item_cnt, db.n_blocks, db.item_base, db.scan_part, db.totals + 1, s);
-  k_dec_item_fill<<<g, 128, 0, s>>>(db.blocks, db.perm, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), db.item_base,
+  k_dec_item_fill<<<g, 128, 0, s>>>(db.blocks, db.perm, db.n_blocks, db.info, reinterpret_cast<const DecTab*>(db.tables), ml_bits, db.item_base,
                                     db.items);
   ++L;
   T->mark("decode.segments", s);
@@ -633,6 +897,12 @@ int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T)
       db.blocks, db.items, db.totals + 1, db.stream, db.block_byte, db.block_len, db.info, reinterpret_cast<const DecTab*>(db.tables),
       db.sym_off, db.sym, db.totals, db.sym_cap, db.status);
   ++L;
+  if (db.latency_mode) {
+    k_dec_segments_ml<<<kMlCtas, 32, 0, s>>>(db.blocks, db.big, db.totals + 3, db.totals + 4, db.stream, db.block_byte, db.block_len,
+                                             db.info, reinterpret_cast<const DecTab*>(db.tables), db.sym_off, db.sym, db.totals,
+                                             db.sym_cap, db.status);
+    ++L;
+  }
   if (db.global_rebuild) {   // fused tiles rebuild their blocks inside the fused inverse
     T->mark("decode.rebuild", s);
     k_dec_rebuild<<<(unsigned)db.n_blocks, 256, 0, s>>>(db.tiles, db.blocks, db.info, db.sym_off, db.sym, db.totals, db.sym_cap, db.z,

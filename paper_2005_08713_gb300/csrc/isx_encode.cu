@@ -1049,7 +1049,10 @@ __global__ void k_tile_headers(const TileDev* __restrict__ tiles, int n_tiles, c
   }
   const int64_t toff = final_pos[t.block_base];
   if (threadIdx.x == 0) tile_offsets[ti] = (uint64_t)toff;
-  if (!fits) return;
+  if (!fits) {
+    if (threadIdx.x == 0) stamp_tile(t, kStampEncEnd);
+    return;
+  }
   uint8_t* o = out + toff;
   const int64_t hdr = 32 + 4 * (int64_t)t.nb;
   if (threadIdx.x == 0) {
@@ -1065,6 +1068,8 @@ __global__ void k_tile_headers(const TileDev* __restrict__ tiles, int n_tiles, c
     const int64_t end = final_pos[bi] + item_size[bi] - (toff + hdr);   // the first item includes the header
     for (int k = 0; k < 4; ++k) o[32 + 4 * j + k] = (uint8_t)((uint64_t)end >> (8 * k));
   }
+  __syncthreads();
+  if (threadIdx.x == 0) stamp_tile(t, kStampEncEnd);   // the tile's stream is complete
 }
 
 int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T) {

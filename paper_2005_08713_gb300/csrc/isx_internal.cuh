@@ -36,6 +36,10 @@ struct TileDev {
   uint8_t* dst;
   int64_t dpitch;
   int32_t rx, ry, rw, rh;
+  // optional per-tile %globaltimer stamps (isx_set_tile_stamps): four arrays
+  // of stamp_n entries, this tile at index stamp_i
+  uint64_t* stamps;
+  int32_t stamp_n, stamp_i;
 };
 
 // One coefficient block (Fig. 3): LL (p = 1) or HL, LH, HH (p = 3).
@@ -229,5 +233,20 @@ __device__ T cta_reduce_max(T v, T* tmp /* >= 32 */) {
 }
 
 __device__ inline void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// Per-tile timestamps (ns of the GPU's global timer): the earliest start and
+// the latest end of a tile's work in an encode or a decode.
+enum StampKind { kStampEncStart = 0, kStampEncEnd = 1, kStampDecStart = 2, kStampDecEnd = 3 };
+__device__ inline uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ inline void stamp_tile(const TileDev& t, int kind) {
+  if (!t.stamps) return;
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(t.stamps + (int64_t)kind * t.stamp_n + t.stamp_i);
+  if (kind == kStampEncStart || kind == kStampDecStart) atomicMin(p, (unsigned long long)global_ns());
+  else atomicMax(p, (unsigned long long)global_ns());
+}
 
 }  // namespace isx

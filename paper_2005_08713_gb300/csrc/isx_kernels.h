@@ -84,7 +84,7 @@ struct DecodeBuffers {
   int64_t* sym_bytes;        // [n_blocks]
   int64_t* sym_off;          // [n_blocks]
   int64_t* scan_part;
-  int64_t* totals;           // [2]: symbol buffer bytes, segment items
+  int64_t* totals;           // [8]: symbol buffer bytes, segment items, level sort, one-warp segments, their work counter
   void* tables;              // [n_blocks] decode tables (dec_table_bytes() each)
   int64_t* bucket;           // [2 * 64] counts / offsets of the sort buckets
   int64_t* items;            // [max_items] (block << 5 | plane), blocks by level, planes in order
@@ -92,6 +92,8 @@ struct DecodeBuffers {
   int64_t* perm;             // [n_blocks] blocks by level
   int64_t* item_cnt;         // [n_blocks] kept plane segments of block perm[j]
   int64_t* item_base;        // [n_blocks] first item of block perm[j]
+  int64_t* big;              // [max_items] segments decoded by a whole warp (latency mode; count in totals[3])
+  bool latency_mode = false; // few blocks: long segments are decoded one warp each
   uint8_t* sym;              // symbol buffer
   int64_t sym_cap;           // its size: an upper bound from the tiles' bit depths
   int* status;

@@ -146,6 +146,7 @@ __device__ __forceinline__ int32_t sample_at(const uint8_t* row, int x, int C, i
 __global__ void k_load_pixels(const TileDev* __restrict__ tiles, int32_t* __restrict__ planes, int* __restrict__ status) {
   const TileDev& t = tiles[blockIdx.x];
   if (t.fused) return;
+  if (threadIdx.x == 0 && blockIdx.y == 0) stamp_tile(t, kStampEncStart);
   const int64_t np = (int64_t)t.w * t.h;
   int32_t* out = planes + t.plane_base;
   uint32_t over = 0;   // bits of samples above the tile's bit depth
@@ -366,6 +367,8 @@ __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const i
       else reinterpret_cast<uint16_t*>(row)[ox * t.C + c] = (uint16_t)q;
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) stamp_tile(t, kStampDecEnd);
 }
 
 // ------------------------------------------------- fused shared-memory path
@@ -950,6 +953,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_fwd_tile_smem(const TileDev* 
   const int tt = task_tile[blockIdx.x / slots], c = blockIdx.x % slots;
   const TileDev& t = tiles[tt];
   if (c >= t.C) return;
+  if (threadIdx.x == 0) stamp_tile(t, kStampEncStart);
   const int w = t.w, h = t.h, pitch = smem_pitch(w);
   // load + colour transform of channel c
   uint32_t over = 0;   // bits of samples above the tile's bit depth
@@ -1424,6 +1428,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
   } else {
     store_tile_channel(t, z, zw, zh, c, P, pitch);
   }
+  __syncthreads();
+  if (threadIdx.x == 0) stamp_tile(t, kStampDecEnd);
 }
 
 // --------------------------------------------------------------- launches

@@ -29,7 +29,7 @@ EXPORTS = ["isx_create", "isx_destroy", "isx_encode_tiles", "isx_decode_region",
            "isx_get_schedule", "isx_set_schedule", "isx_autotune", "isx_plan_encode", "isx_plan_decode",
            "isx_plan_launch_encode", "isx_plan_launch_decode", "isx_plan_sync_status", "isx_plan_device_bytes",
            "isx_plan_launch_count", "isx_plan_last_error", "isx_plan_destroy", "isx_decode_jobs_scratch",
-           "isx_reserve_scratch", "isx_scratch_bytes", "isx_decode_path"]
+           "isx_reserve_scratch", "isx_scratch_bytes", "isx_decode_path", "isx_set_tile_stamps"]
 
 SIZE_CLASSES = 5
 
@@ -172,6 +172,8 @@ def load(build_if_missing: bool = True):
         lib.isx_scratch_bytes.restype = sz
         lib.isx_decode_path.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_double)]
         lib.isx_decode_path.restype = i32
+        lib.isx_set_tile_stamps.argtypes = [vp, vp, i32]
+        lib.isx_set_tile_stamps.restype = st
         _lib = lib
         return lib
 
@@ -284,6 +286,14 @@ class Codec:
 
     def sync_status(self, stream=None) -> int:
         return int(self.lib.isx_sync_status(self.ctx, _stream_ptr(stream)))
+
+    def set_tile_stamps(self, stamps=None):
+        """stamps: uint64/int64 CUDA tensor of 4 * n_tiles (None: off); see isx_set_tile_stamps."""
+        if stamps is None:
+            self._check(self.lib.isx_set_tile_stamps(self.ctx, None, 0))
+        else:
+            assert stamps.numel() % 4 == 0
+            self._check(self.lib.isx_set_tile_stamps(self.ctx, stamps.data_ptr(), stamps.numel() // 4))
 
     # ---------------------------------------------------------- device calls
     def encode_tiles(self, tiles: Sequence[Tile], out, offsets, stream=None):

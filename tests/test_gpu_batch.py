@@ -154,3 +154,42 @@ def test_autotune_then_plans_replayed_from_a_cuda_graph(orc, synth):
         del g
         penc.close()
         pdec.close()
+
+
+def test_tile_stamps_bracket_each_tiles_work(synth):
+    """isx_set_tile_stamps: every encoded tile gets start <= end, a decode stamps only the tiles of its jobs
+    (by stream index), and a plan made while stamps are set records them on each launch."""
+    torch = torch_cuda()
+    from paper_2005_08713_gb300 import isx
+    imgs = [synth.slide(synth.config_seed(3), 256 * k, 512, 200 + 7 * k, 150) for k in range(6)]
+    codec = isx.Codec(0)
+    st = torch.zeros(4 * 8, dtype=torch.int64, device="cuda")
+    codec.set_tile_stamps(st)
+    streams, tiles, out, offs = gpu_encode(codec, imgs, 5, 8, [3, 2, 1, 0, 0, 0])
+    dec = torch.zeros((150, 300, 3), dtype=torch.uint8, device="cuda")
+    codec.decode_jobs(out, offs, tiles, [(i, (tiles[i].x0, 0, tiles[i].width, 150), dec) for i in (2, 4)])
+    assert codec.sync_status() == 0
+    s = st.cpu().numpy().view(np.uint64).reshape(4, 8)
+    none = np.iinfo(np.uint64).max
+    assert all(0 < s[0, i] <= s[1, i] for i in range(6))                   # every encoded tile
+    assert list(s[0, 6:]) == [none, none] and list(s[1, 6:]) == [0, 0]     # slots past the call's tiles
+    for i in range(6):
+        if i in (2, 4):
+            assert s[1, i] <= s[2, i] <= s[3, i]                             # decoded after its encode
+        else:
+            assert s[2, i] == none and s[3, i] == 0
+    assert (s[1, :6] - s[0, :6]).max() < 10 ** 10                          # under 10 s
+    # a plan replayed: fresh stamps per launch
+    plan = codec.plan_encode(isx.TileArray(tiles))
+    codec.set_tile_stamps(None)
+    st.zero_()
+    plan.launch_encode(out, offs)
+    assert plan.sync_status() == 0
+    s2 = st.cpu().numpy().view(np.uint64).reshape(4, 8)
+    assert all(s[1, i] < s2[0, i] <= s2[1, i] for i in range(6))
+    with pytest.raises(isx.IsxError):
+        codec.set_tile_stamps(torch.zeros(4 * 2, dtype=torch.int64, device="cuda"))
+        codec.encode_tiles(tiles, out, offs)                                 # more tiles than stamp entries
+    codec.set_tile_stamps(None)
+    plan.close()
+    codec.close()
