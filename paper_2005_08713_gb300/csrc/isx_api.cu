@@ -353,10 +353,11 @@ struct DecodeLayout {
   int32_t nsel = 0;
   int z = 0, drop = 0;
   int64_t n_blocks = 0, plane_total = 0, fplane_total = 0, sym_cap = 0, max_items = 0;
-  int max_levels = 0, max_dim = 1, max_c = 1, n_fused = 0;
+  int max_levels = 0, max_dim = 1, max_c = 1, n_fused = 0, n_win = 0, max_win = 1;
   FusedClass cls[ISX_SIZE_CLASSES];
   uint64_t* stamps = nullptr;
   int32_t stamp_n = 0;
+  size_t o_win = 0;
   size_t o_tiles = 0, o_idx = 0, o_task = 0, o_blocks = 0, o_bb = 0, o_bl = 0, o_info = 0, o_sb = 0, o_so = 0, o_part = 0, o_tot = 0;
   size_t o_tab = 0, o_bucket = 0, o_items = 0, o_sym = 0, o_A = 0, o_B = 0, o_fp = 0, o_tk = 0, total = 0;
   size_t o_perm = 0, o_icnt = 0, o_ibase = 0, o_big = 0;
@@ -366,8 +367,9 @@ struct DecodeLayout {
 // rectangle (h_tiles, h_index, h_task hold n_jobs entries).
 isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* jobs, int32_t n_jobs, int z, int drop, const Schedule& S,
                        TileDev* h_tiles, int64_t* h_index, int32_t* h_task, DecodeLayout& D, std::string* err,
-                       uint64_t* stamps = nullptr, int32_t stamp_n = 0) {
+                       uint64_t* stamps = nullptr, int32_t stamp_n = 0, std::vector<WinDev>* wins = nullptr) {
   D = DecodeLayout();
+  if (wins) wins->clear();
   D.z = z;
   D.drop = drop;
   if (stamps && stamp_n < n_tiles) {
@@ -392,8 +394,20 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
       *err = "job " + std::to_string(j) + ": output pitch too small";
       return ISX_ERR_ARG;
     }
-    int64_t nb, nc;
-    tile_counts(t, z, &nb, &nc);
+    // A tile too large for the fused inverse whose level-z extent the rectangle covers only in part
+    // is decoded through a window: only the blocks and samples the rectangle depends on.
+    const int ax = std::max(jb.rx - tx, 0), bx = std::min(jb.rx + jb.rw - tx, zw);
+    const int ay = std::max(jb.ry - ty, 0), by = std::min(jb.ry + jb.rh - ty, zh);
+    const bool fusable = fused_tile(zw, zh) && fused_inverse_fits_int16(t, z, drop);
+    const bool windowed = wins && !fusable && (bx - ax < zw || by - ay < zh);
+    WinDev W;
+    int64_t nb, nc, win_elems = 0;
+    if (windowed) {
+      win_elems = plan_window(t, z, ax, bx, ay, by, W);
+      window_counts(t, W, &nb, &nc);
+    } else {
+      tile_counts(t, z, &nb, &nc);
+    }
     // symbols of every kept plane: at most 1 + bitlen(F) planes (sign and magnitude; F bounds every
     // coefficient the encoder writes) of p*w*h/8 bytes each, plus padding
     const double F = forward_state_bound(t);
@@ -409,7 +423,8 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
     d.nb = (int32_t)nb;
     d.block_base = D.n_blocks;
     d.coef_base = 0;
-    d.fused = fused_tile(zw, zh) && fused_inverse_fits_int16(t, z, drop) ? 1 : 0;
+    d.fused = fusable ? 1 : 0;
+    d.win = -1;
     d.dst = (uint8_t*)jb.out;
     d.dpitch = jb.pitch;
     d.rx = jb.rx; d.ry = jb.ry; d.rw = jb.rw; d.rh = jb.rh;
@@ -418,6 +433,16 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
       d.plane_base = D.fplane_total;
       if (d.ct) D.fplane_total += (3LL * zw * zh + 7) & ~7LL;
       fused.push_back({D.nsel, fused_plane_bytes(zw, zh), t.channels});
+    } else if (windowed) {
+      d.plane_base = D.plane_total;
+      D.plane_total += (win_elems + 3) & ~3LL;
+      d.win = (int32_t)wins->size();
+      wins->push_back(W);
+      D.max_win = std::max({D.max_win, bx - ax, by - ay});
+      if (z < t.levels) {
+        const WinLevel& v = W.lev[z + 1];
+        D.max_win = std::max({D.max_win, (v.lx1 - v.lx0) + (v.hx1 - v.hx0), (v.ly1 - v.ly0) + (v.hy1 - v.hy0)});
+      }
     } else {
       d.plane_base = D.plane_total;
       D.plane_total += (int64_t)t.channels * zw * zh;
@@ -426,10 +451,11 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
     ++D.nsel;
     D.n_blocks += nb;
     D.max_levels = std::max(D.max_levels, t.levels);
-    D.max_dim = std::max(D.max_dim, std::max(t.width, t.height));
+    if (!windowed) D.max_dim = std::max(D.max_dim, std::max(t.width, t.height));   // grids of the whole-tile passes
     D.max_c = std::max(D.max_c, t.channels);
   }
   D.n_fused = (int)fused.size();
+  D.n_win = wins ? (int)wins->size() : 0;
   group_fused(fused, S.inv, h_task, D.cls);
   const int64_t nb = D.n_blocks;
   Carve cv;
@@ -451,6 +477,7 @@ isx_status plan_decode(const isx_tile_desc* tiles, int32_t n_tiles, const Job* j
   D.o_icnt = cv.take(8 * nb);
   D.o_ibase = cv.take(8 * nb);
   D.o_big = cv.take(8 * (size_t)D.max_items);
+  D.o_win = cv.take(sizeof(WinDev) * (size_t)std::max(D.n_win, 1));
   D.o_sym = cv.take((size_t)D.sym_cap + 64);
   D.o_A = cv.take(4 * (size_t)D.plane_total);
   D.o_B = cv.take(4 * (size_t)D.plane_total);
@@ -483,6 +510,7 @@ int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, co
   db.max_items = D.max_items;
   db.perm = (int64_t*)(base + D.o_perm); db.item_cnt = (int64_t*)(base + D.o_icnt); db.item_base = (int64_t*)(base + D.o_ibase);
   db.big = (int64_t*)(base + D.o_big);
+  db.wins = (const WinDev*)(base + D.o_win);
   // a decode of few blocks leaves most of the GPU idle: its long segments are decoded one warp each
   db.latency_mode = D.n_blocks <= kLatencyBlocks;
   db.global_rebuild = D.n_fused < D.nsel;
@@ -504,6 +532,10 @@ int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, co
     T->mark("decode.store", s);
     L += launch_store_region(d_tiles, D.nsel, D.z, (int32_t*)(base + D.o_A), s);
   }
+  if (D.n_win) {
+    T->mark("decode.inverse_window", s);
+    L += launch_window_inverse(d_tiles, D.nsel, D.max_levels, D.z, D.max_c, db.wins, (int32_t*)(base + D.o_A), D.max_win, s);
+  }
   T->mark(nullptr, s);
   return L;
 }
@@ -520,8 +552,9 @@ isx_status decode_jobs_ctx(isx_ctx* ctx, const void* d_stream, const uint64_t* d
   if (st != ISX_OK) return st;
   DecodeLayout D;
   std::string err;
+  std::vector<WinDev> wins;
   st = plan_decode(tiles, n_tiles, jobs, n_jobs, z, drop, ctx->sched, ctx->h_tiles, ctx->h_index, ctx->h_task, D, &err, ctx->stamps,
-                   ctx->stamp_n);
+                   ctx->stamp_n, &wins);
   if (st != ISX_OK) return fail(ctx, st, err);
   ctx->launches = 0;
   if (D.nsel == 0) return ISX_OK;
@@ -531,6 +564,8 @@ isx_status decode_jobs_ctx(isx_ctx* ctx, const void* d_stream, const uint64_t* d
   ISX_CUDA(cudaMemcpyAsync(ar + D.o_tiles, ctx->h_tiles, sizeof(TileDev) * D.nsel, cudaMemcpyHostToDevice, s));
   ISX_CUDA(cudaMemcpyAsync(ar + D.o_idx, ctx->h_index, 8 * (size_t)D.nsel, cudaMemcpyHostToDevice, s));
   if (D.n_fused) ISX_CUDA(cudaMemcpyAsync(ar + D.o_task, ctx->h_task, 4 * (size_t)D.n_fused, cudaMemcpyHostToDevice, s));
+  // windows from pageable memory: the copy is complete when the call returns
+  if (D.n_win) ISX_CUDA(cudaMemcpyAsync(ar + D.o_win, wins.data(), sizeof(WinDev) * (size_t)D.n_win, cudaMemcpyHostToDevice, s));
   ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
   StageTimer& T = ctx->timer;
   if (T.on && !T.pending.empty()) T.collect();
@@ -906,8 +941,9 @@ isx_status isx_decode_jobs_scratch(isx_ctx* ctx, const isx_tile_desc* tiles, int
   std::vector<int32_t> htask((size_t)std::max(n_jobs, 1));
   DecodeLayout D;
   std::string err;
+  std::vector<WinDev> wins;   // the same windows as isx_decode_jobs
   isx_status st = plan_decode(tiles, n_tiles, J.data(), n_jobs, level, drop_lsb_planes, ctx->sched, ht.data(), hidx.data(), htask.data(),
-                              D, &err);
+                              D, &err, nullptr, 0, &wins);
   if (st != ISX_OK) return fail(ctx, st, err);
   *bytes = D.nsel ? D.total : 0;
   return ISX_OK;
@@ -1100,8 +1136,9 @@ isx_status isx_plan_decode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_t
   std::vector<int64_t> hidx(n_jobs);
   std::vector<int32_t> htask(n_jobs);
   std::string err;
+  std::vector<WinDev> wins;
   isx_status st = plan_decode(tiles, n_tiles, J.data(), n_jobs, level, drop_lsb_planes, ctx->sched, ht.data(), hidx.data(), htask.data(),
-                              P->D, &err, ctx->stamps, ctx->stamp_n);
+                              P->D, &err, ctx->stamps, ctx->stamp_n, &wins);
   cudaError_t e = cudaSuccess;
   if (st == ISX_OK) {
     P->mem_bytes = P->D.total;
@@ -1113,6 +1150,8 @@ isx_status isx_plan_decode(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_t
       if (e == cudaSuccess) e = cudaMemcpy(P->mem + P->D.o_idx, hidx.data(), 8 * (size_t)P->D.nsel, cudaMemcpyHostToDevice);
       if (e == cudaSuccess && P->D.n_fused)
         e = cudaMemcpy(P->mem + P->D.o_task, htask.data(), 4 * (size_t)P->D.n_fused, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && P->D.n_win)
+        e = cudaMemcpy(P->mem + P->D.o_win, wins.data(), sizeof(WinDev) * (size_t)P->D.n_win, cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) { cudaGetLastError(); st = ISX_ERR_OOM; err = std::string("plan memory: ") + cudaGetErrorString(e); }
   }

@@ -32,8 +32,9 @@ __device__ inline uint32_t rd_u32le(const uint8_t* p) {
 // then list the blocks needed at level z (LL and levels > z) with their
 // byte ranges.
 __global__ void k_decode_plan(const TileDev* __restrict__ tiles, int n_tiles, const int64_t* __restrict__ tile_index,
-                              const uint8_t* __restrict__ stream, const uint64_t* __restrict__ offs, int z, BlockDev* __restrict__ blocks,
-                              int64_t* __restrict__ bbyte, int32_t* __restrict__ blen, int* __restrict__ status) {
+                              const uint8_t* __restrict__ stream, const uint64_t* __restrict__ offs, int z, const WinDev* __restrict__ wins,
+                              BlockDev* __restrict__ blocks, int64_t* __restrict__ bbyte, int32_t* __restrict__ blen,
+                              int* __restrict__ status) {
   const int ti = blockIdx.x * blockDim.x + threadIdx.x;
   if (ti >= n_tiles) return;
   const TileDev t = tiles[ti];
@@ -68,7 +69,8 @@ __global__ void k_decode_plan(const TileDev* __restrict__ tiles, int n_tiles, co
         for (int bx = 0; bx < ceil_div(gw, kCell); ++bx, ++j) {
           uint32_t end = ok ? rd_u32le(s + 32 + 4 * j) : 0;
           bool bok = ok && end >= prev && data + (int64_t)end <= tend;
-          if (level == 0 || level > z) {
+          // a windowed decode lists only the blocks its windows meet (the host counted the same ones)
+          if ((level == 0 || level > z) && (t.win < 0 || block_in_window(wins[t.win], level, by, bx))) {
             BlockDev b;
             b.tile = ti; b.c = c; b.level = level; b.by = by; b.bx = bx;
             b.p = bok ? p : 0;
@@ -805,10 +807,34 @@ __global__ void __launch_bounds__(32) k_dec_segments_ml(const BlockDev* __restri
 // Rebuild pass: per block, every area's 8 coefficients from the decoded
 // planes (sign plane, then magnitude bits d-2 .. 0), dequantised at the bin
 // midpoint, stored into the level-z Mallat plane (padding cropped).
+// Element (relative to the tile's plane_base) that band sample (x, y) of
+// `type` at `level` (0 = the LL of level L) of channel c takes in a windowed
+// decode, or -1 when the windows do not need it.
+__device__ inline int64_t window_slot(const WinDev& W, int C, int c, int level, int type, int x, int y) {
+  if (level == 0) {
+    if (W.z == W.L) {
+      if (x < W.fx0 || x >= W.fx1 || y < W.fy0 || y >= W.fy1) return -1;
+      const int64_t fw = W.fx1 - W.fx0, fh = W.fy1 - W.fy0;
+      return W.fbuf + (int64_t)c * fw * fh + (int64_t)(y - W.fy0) * fw + (x - W.fx0);
+    }
+    const WinLevel& v = W.lev[W.L];
+    if (x < v.lx0 || x >= v.lx1 || y < v.ly0 || y >= v.ly1) return -1;
+    const int64_t cols = (v.lx1 - v.lx0) + (v.hx1 - v.hx0), rows = (v.ly1 - v.ly0) + (v.hy1 - v.hy0);
+    return v.buf + (int64_t)c * cols * rows + (int64_t)(y - v.ly0) * cols + (x - v.lx0);
+  }
+  const WinLevel& v = W.lev[level];
+  const bool hx = type != 1, hy = type >= 1;   // HL: high x; LH: high y; HH: both
+  const int x0 = hx ? v.hx0 : v.lx0, x1 = hx ? v.hx1 : v.lx1, y0 = hy ? v.hy0 : v.ly0, y1 = hy ? v.hy1 : v.ly1;
+  if (x < x0 || x >= x1 || y < y0 || y >= y1) return -1;
+  const int64_t cols = (v.lx1 - v.lx0) + (v.hx1 - v.hx0), rows = (v.ly1 - v.ly0) + (v.hy1 - v.hy0);
+  const int64_t col = (hx ? (v.lx1 - v.lx0) : 0) + (x - x0), row = (hy ? (v.ly1 - v.ly0) : 0) + (y - y0);
+  return v.buf + (int64_t)c * cols * rows + row * cols + col;
+}
+
 __global__ void __launch_bounds__(256) k_dec_rebuild(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
                                                     const DecInfo* __restrict__ info, const int64_t* __restrict__ sym_off,
                                                     const uint8_t* __restrict__ sym, const int64_t* __restrict__ sym_total,
-                                                    int64_t sym_cap, int z, int32_t* __restrict__ planes) {
+                                                    int64_t sym_cap, int z, const WinDev* __restrict__ wins, int32_t* __restrict__ planes) {
   __shared__ int64_t s_poff[32];
   if (*sym_total > sym_cap) return;
   __shared__ uint32_t s_km[32];
@@ -829,6 +855,7 @@ __global__ void __launch_bounds__(256) k_dec_rebuild(const TileDev* __restrict__
   __syncthreads();
   const int zw = level_dim(t.w, z), zh = level_dim(t.h, z);
   int32_t* plane = planes + t.plane_base + (int64_t)b.c * zw * zh;
+  const WinDev* W = t.win >= 0 ? wins + t.win : nullptr;
   const int q = qlog2_of(t, b.level);
   const int32_t delta = 1 << q;
   const int d = di.d;
@@ -861,7 +888,13 @@ __global__ void __launch_bounds__(256) k_dec_rebuild(const TileDev* __restrict__
       if (yy >= sh || xx >= sw) continue;
       const int32_t m = (int32_t)mag[e];
       const int32_t v = m == 0 ? 0 : m * delta + (delta >> 1);
-      plane[(int64_t)(sy + yy) * zw + sx + xx] = ((neg >> e) & 1u) ? -v : v;
+      const int32_t c = ((neg >> e) & 1u) ? -v : v;
+      if (!W) {
+        plane[(int64_t)(sy + yy) * zw + sx + xx] = c;
+        continue;
+      }
+      const int64_t o = window_slot(*W, t.C, b.c, b.level, type, xx, yy);
+      if (o >= 0) planes[t.plane_base + o] = c;
     }
   }
 }
@@ -870,7 +903,7 @@ int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T)
   int L = 0;
   T->mark("decode.plan", s);
   k_decode_plan<<<ceil_div(db.n_tiles, 128), 128, 0, s>>>(db.tiles, db.n_tiles, db.tile_index, db.stream, db.stream_offsets, db.z,
-                                                         db.blocks, db.block_byte, db.block_len, db.status);
+                                                         db.wins, db.blocks, db.block_byte, db.block_len, db.status);
   ++L;
   if (db.n_blocks == 0) return L;
   const unsigned g = (unsigned)((db.n_blocks + 127) / 128);
@@ -906,7 +939,7 @@ int launch_decode_blocks(const DecodeBuffers& db, cudaStream_t s, StageMarks* T)
   if (db.global_rebuild) {   // fused tiles rebuild their blocks inside the fused inverse
     T->mark("decode.rebuild", s);
     k_dec_rebuild<<<(unsigned)db.n_blocks, 256, 0, s>>>(db.tiles, db.blocks, db.info, db.sym_off, db.sym, db.totals, db.sym_cap, db.z,
-                                                        db.planes);
+                                                        db.wins, db.planes);
     ++L;
   }
   return L;

@@ -114,7 +114,83 @@ inline void fill_tiledev(TileDev& d, const isx_tile_desc& t) {
   d.x0 = t.x0; d.y0 = t.y0;
   d.ct = tile_ct(t);
   d.coef16 = forward_state_bound(t) <= 32767.0 ? 1 : 0;
+  d.win = -1;
   for (int k = 0; k < 16; ++k) d.q[k] = k <= t.levels ? t.qstep_log2[k] : 0;
+}
+
+// ---------------------------------------------------- windowed region decode
+// Band index ranges that the inverse 5/3 outputs [a, b) of a line of N
+// samples read: the low samples [*l0, *l1) and the high samples [*h0, *h1).
+// Output 2n is s[n] - floor((d[n-1] + d[n] + 2) / 4) and output 2n+1 is
+// d[n] + floor((x[2n] + x[2n+2]) / 2), with the line's symmetric extension:
+// d[-1] = d[0], d[nh] = d[nh-1] (odd N) and x[N] = x[N-2] (even N).  A line
+// of one sample passes through.
+inline void inv_needs(int N, int a, int b, int32_t* l0, int32_t* l1, int32_t* h0, int32_t* h1) {
+  if (N == 1) { *l0 = 0; *l1 = 1; *h0 = *h1 = 0; return; }
+  const int nl = (N + 1) / 2, nh = N / 2;
+  int lmin = N, lmax = -1, hmin = N, hmax = -1;
+  auto hi = [&](int n) {
+    n = std::min(std::max(n, 0), nh - 1);
+    hmin = std::min(hmin, n); hmax = std::max(hmax, n);
+  };
+  auto xe = [&](int n) {   // the even sample x[2n]
+    lmin = std::min(lmin, n); lmax = std::max(lmax, n);
+    hi(n - 1); hi(n);
+  };
+  // every index is monotone in the output position: the ends of [a, b) suffice
+  const int ks[4] = {a, std::min(a + 1, b - 1), std::max(b - 2, a), b - 1};
+  for (int k : ks) {
+    const int n = k >> 1;
+    if (!(k & 1)) xe(n);
+    else { hi(n); xe(n); xe(std::min(n + 1, nl - 1)); }
+  }
+  *l0 = lmin; *l1 = lmax + 1; *h0 = hmin; *h1 = hmax + 1;
+}
+
+// The windows of a decode of the level-z window [ax, bx) x [ay, by) (tile-
+// local level-z pixels) of tile t, from level z + 1 up to the tile's LL;
+// returns the int32 elements its planes take (all channels).
+inline int64_t plan_window(const isx_tile_desc& t, int z, int ax, int bx, int ay, int by, WinDev& W) {
+  std::memset(&W, 0, sizeof(W));
+  W.z = z; W.L = t.levels;
+  W.fx0 = ax; W.fx1 = bx; W.fy0 = ay; W.fy1 = by;
+  const int64_t C = t.channels;
+  int64_t off = 0;
+  W.fbuf = off;
+  off += C * (bx - ax) * (by - ay);
+  int ox0 = ax, ox1 = bx, oy0 = ay, oy1 = by;
+  for (int l = z + 1; l <= t.levels; ++l) {
+    WinLevel& v = W.lev[l];
+    inv_needs(level_dim(t.width, l - 1), ox0, ox1, &v.lx0, &v.lx1, &v.hx0, &v.hx1);
+    inv_needs(level_dim(t.height, l - 1), oy0, oy1, &v.ly0, &v.ly1, &v.hy0, &v.hy1);
+    v.ox0 = ox0; v.ox1 = ox1; v.oy0 = oy0; v.oy1 = oy1;
+    const int64_t cols = (v.lx1 - v.lx0) + (v.hx1 - v.hx0), rows = (v.ly1 - v.ly0) + (v.hy1 - v.hy0);
+    v.buf = off;
+    off += C * cols * rows;
+    v.tmp = off;
+    off += C * (ox1 - ox0) * rows;
+    ox0 = v.lx0; ox1 = v.lx1; oy0 = v.ly0; oy1 = v.ly1;
+  }
+  return off;
+}
+
+// Blocks a windowed decode reads (all channels) and their padded coefficients.
+inline void window_counts(const isx_tile_desc& t, const WinDev& W, int64_t* nb, int64_t* ncoef) {
+  int64_t b = 0, c = 0;
+  for (int lv = 0; lv <= t.levels; ++lv) {
+    const int level = lv == 0 ? 0 : t.levels + 1 - lv;
+    if (level != 0 && level <= W.z) continue;
+    const int gw = level_dim(t.width, level == 0 ? t.levels : level), gh = level_dim(t.height, level == 0 ? t.levels : level);
+    const int p = level == 0 ? 1 : 3;
+    for (int by = 0; by < ceil_div(gh, kCell); ++by)
+      for (int bx = 0; bx < ceil_div(gw, kCell); ++bx)
+        if (block_in_window(W, level, by, bx)) {
+          ++b;
+          c += (int64_t)p * pad4(std::min(kCell, gw - kCell * bx)) * pad4(std::min(kCell, gh - kCell * by));
+        }
+  }
+  *nb = b * t.channels;
+  *ncoef = c * t.channels;
 }
 
 }  // namespace isx

@@ -40,7 +40,46 @@ struct TileDev {
   // of stamp_n entries, this tile at index stamp_i
   uint64_t* stamps;
   int32_t stamp_n, stamp_i;
+  int32_t win;              // decode: index of its WinDev (windowed region decode), -1: the whole tile
 };
+
+// Windowed region decode of a tile (an untiled image or any large tile):
+// only the samples the requested window depends on are decoded and
+// inverted.  Inverse level l maps the level-l bands restricted to band
+// ranges [lx0, lx1) (low, along x), [hx0, hx1) (high, along x), and the
+// same along y, to the window [ox0, ox1) x [oy0, oy1) of LL_{l-1}.  Its
+// input W_l is a compact plane per channel: (nlx + nhx) columns, the low
+// part first, by (nly + nhy) rows, the low rows first; the row pass writes
+// T_l ((ox1 - ox0) x (nly + nhy) per channel), the column pass the LL part
+// of W_{l-1} (or F, the level-z window, when l - 1 = z).  Element offsets
+// are relative to the tile's plane_base.
+struct WinLevel {
+  int32_t lx0, lx1, hx0, hx1, ly0, ly1, hy0, hy1;
+  int32_t ox0, ox1, oy0, oy1;
+  int64_t buf, tmp;
+};
+struct WinDev {
+  int32_t z, L;
+  int32_t fx0, fx1, fy0, fy1;   // the level-z window (tile-local level-z coordinates)
+  int64_t fbuf;                 // F: C planes of (fx1 - fx0) x (fy1 - fy0)
+  WinLevel lev[kMaxLevels + 1]; // [l] for z < l <= L
+};
+__host__ __device__ inline bool ranges_meet(int a0, int a1, int b0, int b1) { return a0 < b1 && b0 < a1 && a0 < a1 && b0 < b1; }
+// Does block (level, by, bx) of a windowed tile hold a coefficient inside its windows?
+// level 0 = the LL band of level L.
+__host__ __device__ inline bool block_in_window(const WinDev& W, int level, int by, int bx) {
+  const int x0 = kCell * bx, x1 = x0 + kCell, y0 = kCell * by, y1 = y0 + kCell;
+  if (level == 0) {
+    if (W.z == W.L) return ranges_meet(x0, x1, W.fx0, W.fx1) && ranges_meet(y0, y1, W.fy0, W.fy1);
+    const WinLevel& v = W.lev[W.L];
+    return ranges_meet(x0, x1, v.lx0, v.lx1) && ranges_meet(y0, y1, v.ly0, v.ly1);
+  }
+  if (level <= W.z) return false;
+  const WinLevel& v = W.lev[level];
+  const bool xl = ranges_meet(x0, x1, v.lx0, v.lx1), xh = ranges_meet(x0, x1, v.hx0, v.hx1);
+  const bool yl = ranges_meet(y0, y1, v.ly0, v.ly1), yh = ranges_meet(y0, y1, v.hy0, v.hy1);
+  return (xh && yl) || (xl && yh) || (xh && yh);   // HL, LH, HH
+}
 
 // One coefficient block (Fig. 3): LL (p = 1) or HL, LH, HH (p = 3).
 struct BlockDev {

@@ -28,6 +28,10 @@ int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels
                              int32_t* B, cudaStream_t s);
 // Pixels of the tiles not taken by the fused kernels (TileDev::fused = 0) into their destinations.
 int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, cudaStream_t s);
+// Inverse transform and store of the windowed tiles (TileDev::win >= 0): levels max_levels .. z+1 on their
+// window planes, then the level-z window into the destinations.
+int launch_window_inverse(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_c, const WinDev* wins,
+                          int32_t* planes, int max_win, cudaStream_t s);
 
 // encode coding stages
 struct EncodeBuffers {
@@ -94,6 +98,7 @@ struct DecodeBuffers {
   int64_t* item_base;        // [n_blocks] first item of block perm[j]
   int64_t* big;              // [max_items] segments decoded by a whole warp (latency mode; count in totals[3])
   bool latency_mode = false; // few blocks: long segments are decoded one warp each
+  const WinDev* wins = nullptr;   // windows of the windowed tiles (TileDev::win)
   uint8_t* sym;              // symbol buffer
   int64_t sym_cap;           // its size: an upper bound from the tiles' bit depths
   int* status;

@@ -8,6 +8,8 @@
 // s[n] = x[2n] + floor((d[n-1]+d[n]+2)/4), mirrored at both ends); low
 // outputs go to the first ceil(N/2) positions, high outputs after them
 // (Mallat layout).  Floors are arithmetic right shifts.
+#include <algorithm>
+
 #include "isx_internal.cuh"
 #include "isx_kernels.h"
 #include "isx_warp_levels.cuh"
@@ -224,7 +226,7 @@ struct PassGeom {
 };
 
 __device__ inline bool pass_geom(const TileDev& t, int c, int lvl, bool decode_plane, int z, PassGeom* g) {
-  if (c >= t.C || lvl >= t.L || lvl < z || t.fused) return false;
+  if (c >= t.C || lvl >= t.L || lvl < z || t.fused || t.win >= 0) return false;
   int pw = decode_plane ? level_dim(t.w, z) : t.w;
   int ph = decode_plane ? level_dim(t.h, z) : t.h;
   g->cw = level_dim(t.w, lvl);
@@ -344,7 +346,7 @@ __global__ void k_quantise_planes(const TileDev* __restrict__ tiles, const int32
 // inside the requested rectangle.
 __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const int32_t* __restrict__ planes) {
   const TileDev& t = tiles[blockIdx.x];
-  if (t.fused) return;   // written by the fused inverse kernel
+  if (t.fused || t.win >= 0) return;   // written by the fused inverse kernel / the windowed store
   uint8_t* __restrict__ out = t.dst;
   const int64_t pitch = t.dpitch;
   const int rx = t.rx, ry = t.ry, rw = t.rw, rh = t.rh;
@@ -363,6 +365,114 @@ __global__ void k_store_region(const TileDev* __restrict__ tiles, int z, const i
     for (int c = 0; c < t.C; ++c) {
       const int32_t s = t.ct && c < 3 ? v[c] : pl[c * np + e];
       int32_t q = min(max(s, 0), maxv);
+      if (t.bits <= 8) row[ox * t.C + c] = (uint8_t)q;
+      else reinterpret_cast<uint16_t*>(row)[ox * t.C + c] = (uint16_t)q;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) stamp_tile(t, kStampDecEnd);
+}
+
+// ------------------------------------------------------- windowed inverse
+// x[k], k in [a, b), of one inverse 5/3 level of a line of N samples (Sec. 4,
+// the inverse of the lifting above): the low samples s[n] at
+// lo[(n - l0) * ls], the high d[n] at hi[(n - h0) * hs].  The windows hold
+// every index these outputs read (the host's inv_needs), so the line's own
+// symmetric extension gives its end samples (d[-1] = d[0], d[nh] = d[nh-1],
+// x[N] = x[N-2]) and nothing outside the line is read.
+__device__ inline void lift_inv_window(const int32_t* lo, int l0, int64_t ls, const int32_t* hi, int h0, int64_t hs, int N, int a,
+                                       int b, int32_t* out, int64_t os) {
+  if (N == 1) {
+    if (a == 0 && b > 0) out[0] = lo[(int64_t)(0 - l0) * ls];
+    return;
+  }
+  const int nl = (N + 1) >> 1, nh = N >> 1;
+  auto D = [&](int m) { return hi[(int64_t)(min(max(m, 0), nh - 1) - h0) * hs]; };
+  auto XE = [&](int m) { return lo[(int64_t)(m - l0) * ls] - ((D(m - 1) + D(m) + 2) >> 2); };
+  for (int k = a; k < b; ++k) {
+    const int n = k >> 1;
+    out[(int64_t)(k - a) * os] = (k & 1) ? D(n) + ((XE(n) + XE(min(n + 1, nl - 1))) >> 1) : XE(n);
+  }
+}
+
+// Row pass of inverse level `lvl` of the windowed tiles: every row of W_l
+// (its low rows, then its high rows) to the LL_{l-1} window's columns,
+// into T_l; one thread per (row, run of 32 outputs).
+__global__ void k_win_hpass(const TileDev* __restrict__ tiles, const WinDev* __restrict__ wins, int lvl, int32_t* __restrict__ planes) {
+  const TileDev& t = tiles[blockIdx.x];
+  if (t.win < 0 || (int)blockIdx.z >= t.C) return;
+  const WinDev& W = wins[t.win];
+  if (lvl <= W.z || lvl > W.L) return;
+  const WinLevel& v = W.lev[lvl];
+  const int c = blockIdx.z;
+  const int nlx = v.lx1 - v.lx0, cols = nlx + (v.hx1 - v.hx0), rows = (v.ly1 - v.ly0) + (v.hy1 - v.hy0);
+  const int ow = v.ox1 - v.ox0, runs = (ow + 31) >> 5;
+  const int Nx = level_dim(t.w, lvl - 1);
+  int32_t* base = planes + t.plane_base;
+  const int32_t* in = base + v.buf + (int64_t)c * cols * rows;
+  int32_t* out = base + v.tmp + (int64_t)c * ow * rows;
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < (int64_t)rows * runs; e += (int64_t)gridDim.y * blockDim.x) {
+    const int r = (int)(e / runs), k = (int)(e - (int64_t)r * runs);
+    const int a = v.ox0 + 32 * k, b = min(a + 32, v.ox1);
+    const int32_t* row = in + (int64_t)r * cols;
+    lift_inv_window(row, v.lx0, 1, row + nlx, v.hx0, 1, Nx, a, b, out + (int64_t)r * ow + (a - v.ox0), 1);
+  }
+}
+
+// Column pass of inverse level `lvl`: every column of T_l to the LL_{l-1}
+// window's rows, into the LL part of W_{l-1} (or F at level z); one thread
+// per (column, run of 32 outputs), neighbouring threads on neighbouring
+// columns.
+__global__ void k_win_vpass(const TileDev* __restrict__ tiles, const WinDev* __restrict__ wins, int lvl, int32_t* __restrict__ planes) {
+  const TileDev& t = tiles[blockIdx.x];
+  if (t.win < 0 || (int)blockIdx.z >= t.C) return;
+  const WinDev& W = wins[t.win];
+  if (lvl <= W.z || lvl > W.L) return;
+  const WinLevel& v = W.lev[lvl];
+  const int c = blockIdx.z;
+  const int nly = v.ly1 - v.ly0, rows = nly + (v.hy1 - v.hy0);
+  const int ow = v.ox1 - v.ox0, oh = v.oy1 - v.oy0, runs = (oh + 31) >> 5;
+  const int Ny = level_dim(t.h, lvl - 1);
+  int32_t* base = planes + t.plane_base;
+  const int32_t* in = base + v.tmp + (int64_t)c * ow * rows;
+  int32_t* dst;
+  int64_t pitch;
+  if (lvl - 1 == W.z) {
+    pitch = W.fx1 - W.fx0;
+    dst = base + W.fbuf + (int64_t)c * pitch * (W.fy1 - W.fy0);
+  } else {
+    const WinLevel& u = W.lev[lvl - 1];
+    pitch = (u.lx1 - u.lx0) + (u.hx1 - u.hx0);
+    dst = base + u.buf + (int64_t)c * pitch * ((u.ly1 - u.ly0) + (u.hy1 - u.hy0));
+  }
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < (int64_t)ow * runs; e += (int64_t)gridDim.y * blockDim.x) {
+    const int k = (int)(e / ow), x = (int)(e - (int64_t)k * ow);
+    const int a = v.oy0 + 32 * k, b = min(a + 32, v.oy1);
+    lift_inv_window(in + x, v.ly0, ow, in + (int64_t)nly * ow + x, v.hy0, ow, Ny, a, b, dst + (int64_t)(a - v.oy0) * pitch + x, pitch);
+  }
+}
+
+// The level-z window F of each windowed tile (inverse colour transform,
+// clamp to [0, 2^bits - 1]) into its destination, as k_store_region.
+__global__ void k_win_store(const TileDev* __restrict__ tiles, const WinDev* __restrict__ wins, const int32_t* __restrict__ planes) {
+  const TileDev& t = tiles[blockIdx.x];
+  if (t.win < 0) return;
+  const WinDev& W = wins[t.win];
+  const int fw = W.fx1 - W.fx0, fh = W.fy1 - W.fy0;
+  const int64_t np = (int64_t)fw * fh;
+  const int32_t* pl = planes + t.plane_base + W.fbuf;
+  const int tx = (t.x0 >> W.z) - t.rx, ty = (t.y0 >> W.z) - t.ry;   // the tile's origin in the output
+  const int32_t maxv = (1 << t.bits) - 1;
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < np; e += (int64_t)gridDim.y * blockDim.x) {
+    const int y = (int)(e / fw), x = (int)(e - (int64_t)y * fw);
+    const int ox = tx + W.fx0 + x, oy = ty + W.fy0 + y;
+    if (ox < 0 || oy < 0 || ox >= t.rw || oy >= t.rh) continue;
+    int32_t v[3] = {0, 0, 0};
+    if (t.ct) ct_inverse(t.ct, pl[e], pl[np + e], pl[2 * np + e], &v[0], &v[1], &v[2]);
+    uint8_t* row = t.dst + (int64_t)oy * t.dpitch;
+    for (int c = 0; c < t.C; ++c) {
+      const int32_t s = t.ct && c < 3 ? v[c] : pl[c * np + e];
+      const int32_t q = min(max(s, 0), maxv);
       if (t.bits <= 8) row[ox * t.C + c] = (uint8_t)q;
       else reinterpret_cast<uint16_t*>(row)[ox * t.C + c] = (uint16_t)q;
     }
@@ -1502,6 +1612,23 @@ int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels
     launches += 2;
   }
   return launches;
+}
+
+int launch_window_inverse(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_c, const WinDev* wins, int32_t* planes,
+                          int max_win, cudaStream_t s) {
+  int launches = 0;
+  const int T = 256;
+  // grid-stride loops: enough CTAs for the largest window's rows x runs, at most 4 per SM and tile
+  const int64_t work = (int64_t)max_win * ((max_win + 31) / 32);
+  const unsigned gy = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + T - 1) / T, 608));
+  for (int l = max_levels; l > z; --l) {
+    dim3 g(n_tiles, gy, max_c);
+    k_win_hpass<<<g, T, 0, s>>>(d_tiles, wins, l, planes);
+    k_win_vpass<<<g, T, 0, s>>>(d_tiles, wins, l, planes);
+    launches += 2;
+  }
+  k_win_store<<<dim3(n_tiles, gy), T, 0, s>>>(d_tiles, wins, planes);
+  return launches + 1;
 }
 
 int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, cudaStream_t s) {
