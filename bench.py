@@ -565,6 +565,8 @@ def run_gpu(args):
 
     singles = soft(run_single_configs, dev, stream, max(5, args.steps)) if rank == 0 and not args.no_single else None
 
+    untiled = soft(run_untiled, d_img, dev, stream) if rank == 0 and not args.no_untiled else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = soft(cpu_baseline, h_img.numpy(), grid, q, args.cpu_tiles)
@@ -586,7 +588,7 @@ def run_gpu(args):
            "tile_latency_in_step_ms": tile_lat,
            "stages_ms": {k: round(v[0] / max(1, v[1]), 3) for k, v in stages.items()},
            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
-           "lossless": lossless, "single_image_configs": singles}
+           "lossless": lossless, "single_image_configs": singles, "untiled": untiled}
     def serving():
         # the slide's lossy pyramid is the stream above; encode the lossless one beside it
         from paper_2005_08713_gb300 import serve
@@ -605,6 +607,69 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return res if rank == 0 else None
+
+
+def run_untiled(d_img, dev, stream, viewports=48):
+    """The slide coded as ONE image (whole-image transform, the int32 global path), lossy: encode and full
+    decode time, then 1920 x 1080 viewports at levels 0-3 decoded windowed (only the blocks and samples each
+    depends on), device latency per viewport; each viewport checked against the same window of the full
+    decode."""
+    import torch
+    from paper_2005_08713_gb300 import isx
+    H, W = int(d_img.shape[0]), int(d_img.shape[1])
+    mp = W * H / 1e6
+    with isx.Codec(dev.index or 0) as codec:
+        tiles = isx.TileArray([isx.tile_from_tensor(d_img, LEVELS, 8, LOSSY_Q)])
+        cap = W * H * 3 + (1 << 24)
+        d_out = torch.empty(cap, dtype=torch.uint8, device=dev)
+        d_offs = torch.empty(2, dtype=torch.int64, device=dev)
+        d_dec = torch.empty_like(d_img)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e_ms, d_ms = [], []
+        for k in range(3):
+            ev[0].record(stream)
+            codec.encode_tiles(tiles, d_out, d_offs, stream)
+            ev[1].record(stream)
+            codec.decode_region(d_out, d_offs, tiles, 0, (0, 0, W, H), d_dec, 0, stream)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            if codec.sync_status(stream) != 0:
+                raise RuntimeError("untiled round trip failed")
+            if k:
+                e_ms.append(ev[0].elapsed_time(ev[1]))
+                d_ms.append(ev[1].elapsed_time(ev[2]))
+        nbytes = int(d_offs[1].item())
+        rng = np.random.default_rng(21)
+        lat, ok = [], True
+        vw, vh = 1920, 1080
+        fulls = {}
+        for k in range(viewports):
+            z = k % 4
+            zw, zh = isx.level_dim(W, z), isx.level_dim(H, z)
+            rw, rh = min(vw, zw), min(vh, zh)
+            rx, ry = int(rng.integers(0, zw - rw + 1)), int(rng.integers(0, zh - rh + 1))
+            res = torch.empty((rh, rw, 3), dtype=torch.uint8, device=dev)
+            ev[0].record(stream)
+            codec.decode_region(d_out, d_offs, tiles, z, (rx, ry, rw, rh), res, 0, stream)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            lat.append(ev[0].elapsed_time(ev[1]))
+            if k < 8:   # against the same window of a full decode at that level
+                if z not in fulls:
+                    f = torch.empty((zh, zw, 3), dtype=torch.uint8, device=dev)
+                    codec.decode_region(d_out, d_offs, tiles, z, (0, 0, zw, zh), f, 0, stream)
+                    fulls[z] = f
+                ok = ok and bool(torch.equal(res, fulls[z][ry:ry + rh, rx:rx + rw]))
+        if codec.sync_status(stream) != 0:
+            raise RuntimeError("untiled viewport decode failed")
+        lat = sorted(lat)
+        em, dm = statistics.median(e_ms), statistics.median(d_ms)
+        return {"workload": f"untiled_{W}x{H}_rgb8_L{LEVELS}_lossy_q8421 (one image, whole-image transform)",
+                "encode_mps": round(mp / (em / 1e3), 1), "decode_mps": round(mp / (dm / 1e3), 1),
+                "encode_ms": round(em, 3), "decode_ms": round(dm, 3), "compressed_bytes": nbytes,
+                "viewport_1920x1080_z0to3_ms": {"p50": round(lat[len(lat) // 2], 3),
+                                                 "p99": round(lat[int(0.99 * (len(lat) - 1))], 3), "n": len(lat)},
+                "viewports_equal_full_decode": ok}
 
 
 def run_single_configs(dev, stream, reps):
@@ -942,6 +1007,7 @@ def main():
     ap.add_argument("--size", default=None, help="WxH of the slide instead of 40000x30000 (small cases for profiling)")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-single", action="store_true", help="skip the single-image workloads (512x512 stain, 2048x2048 phantom)")
+    ap.add_argument("--no-untiled", action="store_true", help="skip the slide coded as one untiled image")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-batch measurement")
     ap.add_argument("--no-per-tile", action="store_true", help="skip the one-tile-per-call comparison of the batch")
     ap.add_argument("--batch-tiles", type=int, default=4096)

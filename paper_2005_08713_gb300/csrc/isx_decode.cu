@@ -56,38 +56,55 @@ __global__ void k_decode_plan(const TileDev* __restrict__ tiles, int n_tiles, co
          s[10] == t.L && s[11] == t.ct && (int)rd_u32le(s + 12) == nb_all && tend - toff >= 32 + 4 * (int64_t)nb_all;
     for (int k = 0; ok && k <= t.L; ++k) ok = s[16 + k] == t.q[k];
   }
+  // Each block's bytes are [end[j-1], end[j]) of the cumulative end table; only the blocks the decode
+  // needs are visited (for a windowed decode, the cells bounding its windows), each checked on its own.
   int64_t idx = t.block_base;
   const int64_t data = toff + 32 + 4 * (int64_t)nb_all;
-  int j = 0;
-  uint32_t prev = 0;
+  const WinDev* W = t.win >= 0 ? wins + t.win : nullptr;
+  bool bad = !ok;
+  int jbase = 0;
   for (int c = 0; c < t.C; ++c) {
     for (int lv = 0; lv <= t.L; ++lv) {
-      int level = lv == 0 ? 0 : t.L + 1 - lv;
-      int gw = level_dim(t.w, level == 0 ? t.L : level), gh = level_dim(t.h, level == 0 ? t.L : level);
-      int p = level == 0 ? 1 : 3;
-      for (int by = 0; by < ceil_div(gh, kCell); ++by)
-        for (int bx = 0; bx < ceil_div(gw, kCell); ++bx, ++j) {
-          uint32_t end = ok ? rd_u32le(s + 32 + 4 * j) : 0;
-          bool bok = ok && end >= prev && data + (int64_t)end <= tend;
+      const int level = lv == 0 ? 0 : t.L + 1 - lv;
+      const int gw = level_dim(t.w, level == 0 ? t.L : level), gh = level_dim(t.h, level == 0 ? t.L : level);
+      const int p = level == 0 ? 1 : 3;
+      const int gwc = ceil_div(gw, kCell), ghc = ceil_div(gh, kCell);
+      int bx0 = 0, bx1 = gwc, by0 = 0, by1 = ghc;
+      if (level != 0 && level <= z) {
+        bx1 = 0;   // the z finest levels are not needed at level z
+      } else if (W) {
+        window_cells(*W, level, &bx0, &bx1, &by0, &by1);
+        bx1 = min(bx1, gwc);
+        by1 = min(by1, ghc);
+      }
+      for (int by = by0; by < by1; ++by)
+        for (int bx = bx0; bx < bx1; ++bx) {
           // a windowed decode lists only the blocks its windows meet (the host counted the same ones)
-          if ((level == 0 || level > z) && (t.win < 0 || block_in_window(wins[t.win], level, by, bx))) {
-            BlockDev b;
-            b.tile = ti; b.c = c; b.level = level; b.by = by; b.bx = bx;
-            b.p = bok ? p : 0;
-            b.w = pad4(min(kCell, gw - kCell * bx));
-            b.h = pad4(min(kCell, gh - kCell * by));
-            b.coef = 0;
-            blocks[idx] = b;
-            bbyte[idx] = data + prev;
-            blen[idx] = bok ? (int32_t)(end - prev) : 0;
-            ++idx;
+          if (W && !block_in_window(*W, level, by, bx)) continue;
+          const int j = jbase + by * gwc + bx;
+          uint32_t st = 0, en = 0;
+          bool bok = ok;
+          if (ok) {
+            en = rd_u32le(s + 32 + 4 * j);
+            st = j ? rd_u32le(s + 32 + 4 * (j - 1)) : 0u;
+            bok = st <= en && data + (int64_t)en <= tend;
           }
-          if (bok) prev = end;
-          else ok = false;
+          if (!bok) bad = true;
+          BlockDev b;
+          b.tile = ti; b.c = c; b.level = level; b.by = by; b.bx = bx;
+          b.p = bok ? p : 0;
+          b.w = pad4(min(kCell, gw - kCell * bx));
+          b.h = pad4(min(kCell, gh - kCell * by));
+          b.coef = 0;
+          blocks[idx] = b;
+          bbyte[idx] = data + st;
+          blen[idx] = bok ? (int32_t)(en - st) : 0;
+          ++idx;
         }
+      jbase += gwc * ghc;
     }
   }
-  if (!ok) set_status(status, kStCorrupt);
+  if (bad) set_status(status, kStCorrupt);
 }
 
 __device__ inline uint32_t kept_mask(const uint32_t* removed, int p, int pl) {

@@ -65,6 +65,24 @@ struct WinDev {
   WinLevel lev[kMaxLevels + 1]; // [l] for z < l <= L
 };
 __host__ __device__ inline bool ranges_meet(int a0, int a1, int b0, int b1) { return a0 < b1 && b0 < a1 && a0 < a1 && b0 < b1; }
+// Cells [*x0, *x1) x [*y0, *y1) of `level` (0 = the LL of level L) that
+// bound the windows' band ranges: the only cells a windowed decode visits.
+__host__ __device__ inline void window_cells(const WinDev& W, int level, int* x0, int* x1, int* y0, int* y1) {
+  int a0, a1, b0, b1;
+  if (level == 0) {
+    if (W.z == W.L) { a0 = W.fx0; a1 = W.fx1; b0 = W.fy0; b1 = W.fy1; }
+    else { const WinLevel& v = W.lev[W.L]; a0 = v.lx0; a1 = v.lx1; b0 = v.ly0; b1 = v.ly1; }
+  } else {
+    const WinLevel& v = W.lev[level];
+    a0 = v.hx1 > v.hx0 ? min(v.lx0, v.hx0) : v.lx0;
+    a1 = v.hx1 > v.hx0 ? max(v.lx1, v.hx1) : v.lx1;
+    b0 = v.hy1 > v.hy0 ? min(v.ly0, v.hy0) : v.ly0;
+    b1 = v.hy1 > v.hy0 ? max(v.ly1, v.hy1) : v.ly1;
+  }
+  *x0 = a0 / kCell; *x1 = (a1 + kCell - 1) / kCell;
+  *y0 = b0 / kCell; *y1 = (b1 + kCell - 1) / kCell;
+}
+
 // Does block (level, by, bx) of a windowed tile hold a coefficient inside its windows?
 // level 0 = the LL band of level L.
 __host__ __device__ inline bool block_in_window(const WinDev& W, int level, int by, int bx) {
