@@ -1535,6 +1535,14 @@ __global__ void __launch_bounds__(kFusedThreads) k_inv_tile_smem(const TileDev* 
     if (!s_last) return;
     __threadfence();
     store_tile_ct(t, z, zw, zh, c, P, pitch, gp);
+    // The hand-off planes are dead once the colour store has read them: drop their L2 lines without a
+    // write-back to DRAM (only whole 128-byte lines inside this tile's planes; a line shared with a
+    // neighbouring tile's region is left alone).
+    __syncthreads();
+    const uintptr_t lo = (reinterpret_cast<uintptr_t>(gp) + 127) & ~(uintptr_t)127;
+    const uintptr_t hi = (reinterpret_cast<uintptr_t>(gp + 3 * (int64_t)zw * zh)) & ~(uintptr_t)127;
+    for (uintptr_t a = lo + 128 * (uintptr_t)threadIdx.x; a < hi; a += 128 * (uintptr_t)blockDim.x)
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
   } else {
     store_tile_channel(t, z, zw, zh, c, P, pitch);
   }
