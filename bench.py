@@ -856,7 +856,8 @@ def run_serve(args, dev, pyramids):
     t0 = time.perf_counter()
     srv = serve.Server(pyramids, device=dev.index or 0, slots=args.serve_slots, max_batch=args.serve_batch,
                        scratch_budget=args.serve_budget_mb << 20,
-                       resident_from=None if args.serve_resident_from < 0 else args.serve_resident_from)
+                       resident_from=None if args.serve_resident_from < 0 else args.serve_resident_from,
+                       cache_bytes=args.serve_cache_mb << 20)
     out["resident_levels_from"] = args.serve_resident_from
     out["startup_s"] = round(time.perf_counter() - t0, 2)
     srv.run(serve.poisson_requests(1000.0, 64, pyramids, seed=1))   # warm-up
@@ -869,11 +870,13 @@ def run_serve(args, dev, pyramids):
                "achieved_per_s": round(len(done) / srv.elapsed, 1), "MP_per_s": round(px / 1e6 / srv.elapsed, 1),
                "batches": srv.n_batches, "mean_batch": round(float(np.mean(srv.batch_sizes)), 2)}
         row.update(serve.latency_stats(done))
+        row["cache"] = srv.cache_stats()
         out["rates"].append(row)
     srv.close()
     # the same kind of load served one request per launch on one stream
     one = serve.Server(pyramids, device=dev.index or 0, slots=1, max_batch=1, scratch_budget=args.serve_budget_mb << 20,
-                       resident_from=None if args.serve_resident_from < 0 else args.serve_resident_from)
+                       resident_from=None if args.serve_resident_from < 0 else args.serve_resident_from,
+                       cache_bytes=args.serve_cache_mb << 20)
     n = int(min(rates[-1] * args.serve_seconds, args.serve_cap, 4000))
     reqs = serve.poisson_requests(rates[-1], n, pyramids, seed=999)
     done = one.run(reqs)
@@ -882,6 +885,7 @@ def run_serve(args, dev, pyramids):
                                      "MP_per_s": round(px / 1e6 / one.elapsed, 1), **serve.latency_stats(done)}
     one.close()
     out["slots"], out["max_batch"], out["scratch_budget_mb_per_slot"] = args.serve_slots, args.serve_batch, args.serve_budget_mb
+    out["tile_cache_mb"] = args.serve_cache_mb
     return out
 
 
@@ -1013,9 +1017,10 @@ def main():
     ap.add_argument("--batch-tiles", type=int, default=4096)
     ap.add_argument("--no-serve", action="store_true", help="skip the viewport-serving measurement")
     ap.add_argument("--serve-rates", default="1000,5000,10000,20000,50000")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrivals per rate: seconds of Poisson arrivals ...")
-    ap.add_argument("--serve-cap", type=int, default=10000, help="... but at most this many requests")
-    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrivals per rate: seconds of Poisson arrivals ...")
+    ap.add_argument("--serve-cap", type=int, default=60000, help="... but at most this many requests")
+    ap.add_argument("--serve-cache-mb", type=int, default=4096, help="decoded-cell caches of the levels below resident")
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-batch", type=int, default=32)
     ap.add_argument("--serve-budget-mb", type=int, default=1024)
     ap.add_argument("--serve-resident-from", type=int, default=3, help="keep levels >= this decoded on the device (-1: none)")

@@ -305,6 +305,30 @@ const char* isx_plan_last_error(const isx_plan* plan);
 /* Synchronises the device and frees the plan. */
 void isx_plan_destroy(isx_plan* plan);
 
+/* One rectangle copy of isx_copy_rects: `rows` rows of `row_bytes` bytes
+ * from src (rows src_pitch bytes apart) to dst (dst_pitch apart); DEVICE
+ * pointers. */
+typedef struct {
+  const void* src;
+  int64_t src_pitch;
+  void* dst;
+  int64_t dst_pitch;
+  int32_t row_bytes, rows;
+} isx_rect_copy;
+
+/* Copies n rectangles (HOST array of descriptors, device data) in one
+ * launch on `stream`: a viewport server assembles many requests from
+ * decoded tiles and resident levels with one call.  No counterpart in the
+ * paper.  Any byte offsets, pitches and row lengths (rectangles with 0
+ * rows or 0 row bytes are skipped); each rectangle runs as pieces of at
+ * most 32 rows.  Asynchronous; the descriptors are staged in the
+ * context's pinned memory before returning (the call waits for the copy
+ * of the previous call's descriptors).  Rectangles must not overlap one
+ * another's destinations, nor a destination a source.
+ * Errors: ISX_ERR_ARG for a negative count, size or row count, or a null
+ * pointer of a non-empty rectangle; ISX_ERR_CUDA from the runtime. */
+isx_status isx_copy_rects(isx_ctx* ctx, const isx_rect_copy* copies, int32_t n, void* stream);
+
 /* Size of the library's static device scratch array (16 MiB), the whole
  * working memory of isx_encode_tile_static. */
 #define ISX_STATIC_SCRATCH_BYTES ((size_t)16 << 20)

@@ -69,19 +69,29 @@ struct Schedule {
   int inv[ISX_SIZE_CLASSES];
 };
 
+// One set of pinned staging buffers for a call's descriptors.  A context
+// rotates through kStagingSets of them, so that a call waits only for the
+// host-to-device copies of the call kStagingSets calls back (queued work of
+// the calls in between does not hold the host).
+struct Staging {
+  TileDev* h_tiles = nullptr;      // descriptors
+  size_t h_tiles_cap = 0;
+  int64_t* h_index = nullptr;      // decode tile indices
+  size_t h_index_cap = 0;
+  int32_t* h_task = nullptr;       // tiles taking the fused shared-memory path
+  size_t h_task_cap = 0;
+  cudaEvent_t free = nullptr;      // recorded after the copies out of this set
+};
+constexpr int kStagingSets = 8;
+
 struct isx_ctx {
   StageTimer timer;
   int device = 0;
   size_t budget = 0;
   uint8_t* arena = nullptr;
   size_t arena_size = 0;
-  TileDev* h_tiles = nullptr;      // pinned staging for descriptors
-  size_t h_tiles_cap = 0;
-  int64_t* h_index = nullptr;      // pinned staging for decode tile indices
-  size_t h_index_cap = 0;
-  int32_t* h_task = nullptr;       // pinned staging: tiles taking the fused shared-memory path
-  size_t h_task_cap = 0;
-  cudaEvent_t staging_free = nullptr;
+  Staging stage[kStagingSets];
+  int stage_next = 0;
   int* d_status = nullptr;
   uint8_t* d_io = nullptr;         // device staging of the host-buffer calls
   size_t d_io_cap = 0;
@@ -90,6 +100,10 @@ struct isx_ctx {
   int launches = 0;
   uint64_t* stamps = nullptr;      // per-tile timestamps (isx_set_tile_stamps), 4 x stamp_n
   int32_t stamp_n = 0;
+  isx_rect_copy* h_copy = nullptr; // pinned staging of isx_copy_rects
+  isx_rect_copy* d_copy = nullptr;
+  size_t copy_cap = 0;
+  cudaEvent_t copy_free = nullptr;
 };
 
 namespace {
@@ -156,29 +170,34 @@ isx_status ensure_arena(isx_ctx* ctx, size_t need) {
   return ISX_OK;
 }
 
-isx_status ensure_staging(isx_ctx* ctx, size_t n) {
-  ISX_CUDA(cudaEventSynchronize(ctx->staging_free));
-  if (n > ctx->h_tiles_cap) {
-    if (ctx->h_tiles) cudaFreeHost(ctx->h_tiles);
-    ctx->h_tiles = nullptr;
-    size_t cap = std::max<size_t>(n, 1024);
-    ISX_CUDA(cudaMallocHost(&ctx->h_tiles, cap * sizeof(TileDev)));
-    ctx->h_tiles_cap = cap;
+// The next staging set, its previous copies complete, with room for n entries.
+isx_status ensure_staging(isx_ctx* ctx, size_t n, Staging** out) {
+  Staging& g = ctx->stage[ctx->stage_next];
+  ctx->stage_next = (ctx->stage_next + 1) % kStagingSets;
+  ISX_CUDA(cudaEventSynchronize(g.free));
+  const size_t cap = std::max<size_t>(n, 1024);
+  if (n > g.h_tiles_cap) {
+    if (g.h_tiles) cudaFreeHost(g.h_tiles);
+    g.h_tiles = nullptr;
+    g.h_tiles_cap = 0;
+    ISX_CUDA(cudaMallocHost(&g.h_tiles, cap * sizeof(TileDev)));
+    g.h_tiles_cap = cap;
   }
-  if (n > ctx->h_task_cap) {
-    if (ctx->h_task) cudaFreeHost(ctx->h_task);
-    ctx->h_task = nullptr;
-    size_t cap = std::max<size_t>(n, 1024);
-    ISX_CUDA(cudaMallocHost(&ctx->h_task, cap * sizeof(int32_t)));
-    ctx->h_task_cap = cap;
+  if (n > g.h_task_cap) {
+    if (g.h_task) cudaFreeHost(g.h_task);
+    g.h_task = nullptr;
+    g.h_task_cap = 0;
+    ISX_CUDA(cudaMallocHost(&g.h_task, cap * sizeof(int32_t)));
+    g.h_task_cap = cap;
   }
-  if (n > ctx->h_index_cap) {
-    if (ctx->h_index) cudaFreeHost(ctx->h_index);
-    ctx->h_index = nullptr;
-    size_t cap = std::max<size_t>(n, 1024);
-    ISX_CUDA(cudaMallocHost(&ctx->h_index, cap * sizeof(int64_t)));
-    ctx->h_index_cap = cap;
+  if (n > g.h_index_cap) {
+    if (g.h_index) cudaFreeHost(g.h_index);
+    g.h_index = nullptr;
+    g.h_index_cap = 0;
+    ISX_CUDA(cudaMallocHost(&g.h_index, cap * sizeof(int64_t)));
+    g.h_index_cap = cap;
   }
+  *out = &g;
   return ISX_OK;
 }
 
@@ -548,12 +567,13 @@ struct NoMarks : StageMarks {
 isx_status decode_jobs_ctx(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets, const isx_tile_desc* tiles,
                            int32_t n_tiles, const Job* jobs, int32_t n_jobs, int z, int drop, cudaStream_t s) {
   ISX_CUDA(cudaSetDevice(ctx->device));
-  isx_status st = ensure_staging(ctx, (size_t)std::max(n_jobs, 1));
+  Staging* g = nullptr;
+  isx_status st = ensure_staging(ctx, (size_t)std::max(n_jobs, 1), &g);
   if (st != ISX_OK) return st;
   DecodeLayout D;
   std::string err;
   std::vector<WinDev> wins;
-  st = plan_decode(tiles, n_tiles, jobs, n_jobs, z, drop, ctx->sched, ctx->h_tiles, ctx->h_index, ctx->h_task, D, &err, ctx->stamps,
+  st = plan_decode(tiles, n_tiles, jobs, n_jobs, z, drop, ctx->sched, g->h_tiles, g->h_index, g->h_task, D, &err, ctx->stamps,
                    ctx->stamp_n, &wins);
   if (st != ISX_OK) return fail(ctx, st, err);
   ctx->launches = 0;
@@ -561,12 +581,12 @@ isx_status decode_jobs_ctx(isx_ctx* ctx, const void* d_stream, const uint64_t* d
   st = ensure_arena(ctx, D.total);
   if (st != ISX_OK) return st;
   uint8_t* ar = ctx->arena;
-  ISX_CUDA(cudaMemcpyAsync(ar + D.o_tiles, ctx->h_tiles, sizeof(TileDev) * D.nsel, cudaMemcpyHostToDevice, s));
-  ISX_CUDA(cudaMemcpyAsync(ar + D.o_idx, ctx->h_index, 8 * (size_t)D.nsel, cudaMemcpyHostToDevice, s));
-  if (D.n_fused) ISX_CUDA(cudaMemcpyAsync(ar + D.o_task, ctx->h_task, 4 * (size_t)D.n_fused, cudaMemcpyHostToDevice, s));
+  ISX_CUDA(cudaMemcpyAsync(ar + D.o_tiles, g->h_tiles, sizeof(TileDev) * D.nsel, cudaMemcpyHostToDevice, s));
+  ISX_CUDA(cudaMemcpyAsync(ar + D.o_idx, g->h_index, 8 * (size_t)D.nsel, cudaMemcpyHostToDevice, s));
+  if (D.n_fused) ISX_CUDA(cudaMemcpyAsync(ar + D.o_task, g->h_task, 4 * (size_t)D.n_fused, cudaMemcpyHostToDevice, s));
   // windows from pageable memory: the copy is complete when the call returns
   if (D.n_win) ISX_CUDA(cudaMemcpyAsync(ar + D.o_win, wins.data(), sizeof(WinDev) * (size_t)D.n_win, cudaMemcpyHostToDevice, s));
-  ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
+  ISX_CUDA(cudaEventRecord(g->free, s));
   StageTimer& T = ctx->timer;
   if (T.on && !T.pending.empty()) T.collect();
   ctx->launches = launch_decode(D, ar, d_stream, d_tile_offsets, ctx->d_status, &T, s);
@@ -602,10 +622,11 @@ isx_status isx_create(isx_ctx** out, int device, size_t hbm_budget_bytes) {
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->staging_free, cudaEventDisableTiming);
+  for (int k = 0; k < kStagingSets && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ctx->stage[k].free, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->copy_free, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    delete ctx;
+    isx_destroy(ctx);
     return ISX_ERR_CUDA;
   }
   if (e == cudaSuccess) e = encode_set_attributes();
@@ -627,10 +648,15 @@ void isx_destroy(isx_ctx* ctx) {
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->d_io) cudaFree(ctx->d_io);
   if (ctx->d_status) cudaFree(ctx->d_status);
-  if (ctx->h_tiles) cudaFreeHost(ctx->h_tiles);
-  if (ctx->h_index) cudaFreeHost(ctx->h_index);
-  if (ctx->h_task) cudaFreeHost(ctx->h_task);
-  if (ctx->staging_free) cudaEventDestroy(ctx->staging_free);
+  for (Staging& g : ctx->stage) {
+    if (g.h_tiles) cudaFreeHost(g.h_tiles);
+    if (g.h_index) cudaFreeHost(g.h_index);
+    if (g.h_task) cudaFreeHost(g.h_task);
+    if (g.free) cudaEventDestroy(g.free);
+  }
+  if (ctx->copy_free) cudaEventDestroy(ctx->copy_free);
+  if (ctx->h_copy) cudaFreeHost(ctx->h_copy);
+  if (ctx->d_copy) cudaFree(ctx->d_copy);
   for (cudaEvent_t e : ctx->timer.pool) cudaEventDestroy(e);
   delete ctx;
 }
@@ -665,6 +691,54 @@ int32_t isx_stage_times(isx_ctx* ctx, char* names, int64_t names_len, double* ms
 }
 
 const char* isx_last_error(isx_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+isx_status isx_copy_rects(isx_ctx* ctx, const isx_rect_copy* copies, int32_t n, void* stream) {
+  if (!ctx) return ISX_ERR_ARG;
+  if (n < 0 || (n > 0 && !copies)) return fail(ctx, ISX_ERR_ARG, "bad arguments");
+  for (int32_t i = 0; i < n; ++i)
+    if (copies[i].row_bytes < 0 || copies[i].rows < 0 || ((copies[i].row_bytes > 0 && copies[i].rows > 0) && (!copies[i].src || !copies[i].dst)))
+      return fail(ctx, ISX_ERR_ARG, "copy " + std::to_string(i) + ": bad rectangle");
+  ctx->launches = 0;
+  // each rectangle runs as pieces of at most kCopyPieceRows rows, one CTA a piece
+  int64_t pieces = 0;
+  for (int32_t i = 0; i < n; ++i)
+    if (copies[i].row_bytes > 0 && copies[i].rows > 0) pieces += (copies[i].rows + kCopyPieceRows - 1) / kCopyPieceRows;
+  if (pieces == 0) return ISX_OK;
+  if (pieces > INT32_MAX) return fail(ctx, ISX_ERR_ARG, "too many rectangle pieces for one launch");
+  ISX_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  ISX_CUDA(cudaEventSynchronize(ctx->copy_free));   // the previous call's descriptors have been copied
+  if ((size_t)pieces > ctx->copy_cap) {
+    ISX_CUDA(cudaDeviceSynchronize());
+    if (ctx->h_copy) cudaFreeHost(ctx->h_copy);
+    if (ctx->d_copy) cudaFree(ctx->d_copy);
+    ctx->h_copy = nullptr;
+    ctx->d_copy = nullptr;
+    ctx->copy_cap = 0;
+    const size_t cap = std::max<size_t>((size_t)pieces, 65536);
+    ISX_CUDA(cudaMallocHost(&ctx->h_copy, cap * sizeof(isx_rect_copy)));
+    ISX_CUDA(cudaMalloc(&ctx->d_copy, cap * sizeof(isx_rect_copy)));
+    ctx->copy_cap = cap;
+  }
+  int64_t k = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const isx_rect_copy& c = copies[i];
+    if (c.row_bytes <= 0 || c.rows <= 0) continue;
+    for (int32_t r = 0; r < c.rows; r += kCopyPieceRows) {
+      isx_rect_copy& p = ctx->h_copy[k++];
+      p = c;
+      p.src = static_cast<const uint8_t*>(c.src) + (int64_t)r * c.src_pitch;
+      p.dst = static_cast<uint8_t*>(c.dst) + (int64_t)r * c.dst_pitch;
+      p.rows = std::min(kCopyPieceRows, c.rows - r);
+    }
+  }
+  const int n_pieces = (int)pieces;
+  ISX_CUDA(cudaMemcpyAsync(ctx->d_copy, ctx->h_copy, (size_t)n_pieces * sizeof(isx_rect_copy), cudaMemcpyHostToDevice, s));
+  ISX_CUDA(cudaEventRecord(ctx->copy_free, s));
+  ctx->launches = launch_copy_rects(ctx->d_copy, n_pieces, s);
+  ISX_CUDA(cudaGetLastError());
+  return ISX_OK;
+}
 
 isx_status isx_set_tile_stamps(isx_ctx* ctx, uint64_t* d_stamps, int32_t n_tiles) {
   if (!ctx) return ISX_ERR_ARG;
@@ -720,11 +794,12 @@ isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, in
   if (!ctx || !tiles || n_tiles < 1 || !d_coef) return fail(ctx, ISX_ERR_ARG, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   ISX_CUDA(cudaSetDevice(ctx->device));
-  isx_status st = ensure_staging(ctx, (size_t)n_tiles);
+  Staging* g = nullptr;
+  isx_status st = ensure_staging(ctx, (size_t)n_tiles, &g);
   if (st != ISX_OK) return st;
   EncodeLayout E;
   std::string err;
-  st = plan_encode(tiles, n_tiles, false, ctx->sched, ctx->h_tiles, ctx->h_task, E, &err);
+  st = plan_encode(tiles, n_tiles, false, ctx->sched, g->h_tiles, g->h_task, E, &err);
   if (st != ISX_OK) return fail(ctx, st, err);
   Carve cv;
   size_t o_tiles = cv.take(sizeof(TileDev) * n_tiles);
@@ -735,8 +810,8 @@ isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, in
   TileDev* d_tiles = (TileDev*)(ctx->arena + o_tiles);
   int32_t* A = (int32_t*)(ctx->arena + o_A);
   int32_t* B = (int32_t*)(ctx->arena + o_B);
-  ISX_CUDA(cudaMemcpyAsync(d_tiles, ctx->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
-  ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
+  ISX_CUDA(cudaMemcpyAsync(d_tiles, g->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
+  ISX_CUDA(cudaEventRecord(g->free, s));
   int L = launch_forward_transform(d_tiles, n_tiles, E.max_levels, E.max_dim, E.max_c, A, B, ctx->d_status, s);
   L += launch_quantise_planes(d_tiles, n_tiles, A, d_coef, s);
   ctx->launches = L;
@@ -752,18 +827,19 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   if (reinterpret_cast<uintptr_t>(d_out) & 3) return fail(ctx, ISX_ERR_ARG, "d_out must be 4-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   ISX_CUDA(cudaSetDevice(ctx->device));
-  isx_status st = ensure_staging(ctx, (size_t)n_tiles);
+  Staging* g = nullptr;
+  isx_status st = ensure_staging(ctx, (size_t)n_tiles, &g);
   if (st != ISX_OK) return st;
   EncodeLayout E;
   std::string err;
-  st = plan_encode(tiles, n_tiles, true, ctx->sched, ctx->h_tiles, ctx->h_task, E, &err, ctx->stamps, ctx->stamp_n);
+  st = plan_encode(tiles, n_tiles, true, ctx->sched, g->h_tiles, g->h_task, E, &err, ctx->stamps, ctx->stamp_n);
   if (st != ISX_OK) return fail(ctx, st, err);
   st = ensure_arena(ctx, E.total);
   if (st != ISX_OK) return st;
   uint8_t* ar = ctx->arena;
-  ISX_CUDA(cudaMemcpyAsync(ar + E.o_tiles, ctx->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
-  if (E.n_fused) ISX_CUDA(cudaMemcpyAsync(ar + E.o_task, ctx->h_task, sizeof(int32_t) * E.n_fused, cudaMemcpyHostToDevice, s));
-  ISX_CUDA(cudaEventRecord(ctx->staging_free, s));
+  ISX_CUDA(cudaMemcpyAsync(ar + E.o_tiles, g->h_tiles, sizeof(TileDev) * n_tiles, cudaMemcpyHostToDevice, s));
+  if (E.n_fused) ISX_CUDA(cudaMemcpyAsync(ar + E.o_task, g->h_task, sizeof(int32_t) * E.n_fused, cudaMemcpyHostToDevice, s));
+  ISX_CUDA(cudaEventRecord(g->free, s));
   StageTimer& T = ctx->timer;
   if (T.on && !T.pending.empty()) T.collect();
   ctx->launches = launch_encode(E, ar, d_out, out_capacity, d_tile_offsets, ctx->d_status, &T, s);

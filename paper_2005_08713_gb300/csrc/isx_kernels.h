@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "isx.h"
 #include "isx_internal.cuh"
 
 namespace isx {
@@ -28,6 +29,10 @@ int launch_inverse_transform(const TileDev* d_tiles, int n_tiles, int max_levels
                              int32_t* B, cudaStream_t s);
 // Pixels of the tiles not taken by the fused kernels (TileDev::fused = 0) into their destinations.
 int launch_store_region(const TileDev* d_tiles, int n_tiles, int z, const int32_t* planes, cudaStream_t s);
+// isx_copy_rects: one CTA per piece (a rectangle's rows split in runs of at most kCopyPieceRows; pieces
+// on the device).
+constexpr int kCopyPieceRows = 32;
+int launch_copy_rects(const isx_rect_copy* pieces, int n, cudaStream_t s);
 // Inverse transform and store of the windowed tiles (TileDev::win >= 0): levels max_levels .. z+1 on their
 // window planes, then the level-z window into the destinations.
 int launch_window_inverse(const TileDev* d_tiles, int n_tiles, int max_levels, int z, int max_c, const WinDev* wins,

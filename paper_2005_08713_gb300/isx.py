@@ -29,7 +29,7 @@ EXPORTS = ["isx_create", "isx_destroy", "isx_encode_tiles", "isx_decode_region",
            "isx_get_schedule", "isx_set_schedule", "isx_autotune", "isx_plan_encode", "isx_plan_decode",
            "isx_plan_launch_encode", "isx_plan_launch_decode", "isx_plan_sync_status", "isx_plan_device_bytes",
            "isx_plan_launch_count", "isx_plan_last_error", "isx_plan_destroy", "isx_decode_jobs_scratch",
-           "isx_reserve_scratch", "isx_scratch_bytes", "isx_decode_path", "isx_set_tile_stamps"]
+           "isx_reserve_scratch", "isx_scratch_bytes", "isx_decode_path", "isx_set_tile_stamps", "isx_copy_rects"]
 
 SIZE_CLASSES = 5
 
@@ -61,6 +61,11 @@ class DecodeJobC(ctypes.Structure):
 # numpy layout of isx_decode_job (for building many jobs without Python loops)
 JOB_DTYPE = np.dtype([("tile", "<i4"), ("rx", "<i4"), ("ry", "<i4"), ("rw", "<i4"), ("rh", "<i4"), ("_pad", "<i4"),
                       ("d_out", "<u8"), ("out_pitch_bytes", "<i8")])
+
+
+# numpy layout of isx_rect_copy
+COPY_DTYPE = np.dtype([("src", "<u8"), ("src_pitch", "<i8"), ("dst", "<u8"), ("dst_pitch", "<i8"), ("row_bytes", "<i4"),
+                       ("rows", "<i4")])
 
 
 class ScheduleC(ctypes.Structure):
@@ -174,6 +179,8 @@ def load(build_if_missing: bool = True):
         lib.isx_decode_path.restype = i32
         lib.isx_set_tile_stamps.argtypes = [vp, vp, i32]
         lib.isx_set_tile_stamps.restype = st
+        lib.isx_copy_rects.argtypes = [vp, vp, i32, vp]
+        lib.isx_copy_rects.restype = st
         _lib = lib
         return lib
 
@@ -328,6 +335,11 @@ class Codec:
         self._check(self.lib.isx_decode_jobs_scratch(self.ctx, _tiles_c(tiles), len(tiles), jobs.ctypes.data, len(jobs), level,
                                                      drop_lsb_planes, ctypes.byref(n)))
         return int(n.value)
+
+    def copy_rects(self, copies: np.ndarray, stream=None):
+        """copies: contiguous numpy array of COPY_DTYPE (device addresses); one launch (isx_copy_rects)."""
+        assert copies.dtype == COPY_DTYPE and copies.flags["C_CONTIGUOUS"]
+        self._check(self.lib.isx_copy_rects(self.ctx, copies.ctypes.data, len(copies), _stream_ptr(stream)))
 
     def reserve_scratch(self, nbytes: int):
         self._check(self.lib.isx_reserve_scratch(self.ctx, nbytes))

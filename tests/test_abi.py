@@ -45,3 +45,41 @@ def test_decode_job_array_layout_matches_header():
     assert ctypes.sizeof(isx.DecodeJobC) == isx.JOB_DTYPE.itemsize == 40
     for name in ("tile", "rx", "ry", "rw", "rh", "d_out", "out_pitch_bytes"):
         assert getattr(isx.DecodeJobC, name).offset == isx.JOB_DTYPE.fields[name][1], name
+
+
+def test_struct_layouts_match_the_compiled_header(tmp_path):
+    """The C compiler's offsets and sizes of isx_tile_desc, isx_decode_job and isx_rect_copy (a small
+    program built against include/isx.h) equal the binding's ctypes and numpy layouts."""
+    import shutil
+    import subprocess
+    import pytest
+    from paper_2005_08713_gb300 import isx
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = {"isx_tile_desc": [n for n, _ in isx.TileDescC._fields_],
+              "isx_decode_job": ["tile", "rx", "ry", "rw", "rh", "d_out", "out_pitch_bytes"],
+              "isx_rect_copy": ["src", "src_pitch", "dst", "dst_pitch", "row_bytes", "rows"]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "isx.h"', "int main(void) {"]
+    for st, names in fields.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for n in names:
+            lines.append(f'  printf("{st} {n} %zu\\n", offsetof({st}, {n}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        st, name, v = line.split()
+        got[(st, name)] = int(v)
+    assert got[("isx_tile_desc", "size")] == ctypes.sizeof(isx.TileDescC)
+    for n in fields["isx_tile_desc"]:
+        assert got[("isx_tile_desc", n)] == getattr(isx.TileDescC, n).offset, n
+    assert got[("isx_decode_job", "size")] == ctypes.sizeof(isx.DecodeJobC) == isx.JOB_DTYPE.itemsize
+    for n in fields["isx_decode_job"]:
+        assert got[("isx_decode_job", n)] == getattr(isx.DecodeJobC, n).offset == isx.JOB_DTYPE.fields[n][1], n
+    assert got[("isx_rect_copy", "size")] == isx.COPY_DTYPE.itemsize == 40
+    for n in fields["isx_rect_copy"]:
+        assert got[("isx_rect_copy", n)] == isx.COPY_DTYPE.fields[n][1], n

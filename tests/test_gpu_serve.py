@@ -67,6 +67,29 @@ def test_served_mix_equals_each_request_alone_and_the_oracle(orc, synth):
     codec.close()
 
 
+def test_small_tile_cache_evicts_and_stays_exact(synth):
+    """A decoded-tile cache far smaller than the levels it serves: tiles are evicted and decoded again,
+    and every served viewport still equals the same region decoded alone."""
+    from paper_2005_08713_gb300 import isx, serve
+    torch = torch_cuda()
+    codec = isx.Codec(0)
+    p, _, _ = _pyramid(codec, synth, True, W=3000, H=2000)
+    reqs = serve.poisson_requests(20000.0, 200, [p], seed=11, view=(640, 360), zmax=2)
+    srv = serve.Server([p], slots=3, max_batch=8, scratch_budget=64 << 20, out_shape=(360, 640), keep_outputs=True,
+                       cache_bytes=4 << 20)
+    done = srv.run(reqs)
+    stats = srv.cache_stats()
+    srv.close()
+    assert len(done) == 200 and stats["tile_hits"] > 0 and stats["tile_misses"] > stats["cache_bytes"] // (256 * 256 * 3)
+    for r in done:
+        rx, ry, rw, rh = r.rect
+        alone = torch.zeros((rh, rw, 3), dtype=torch.uint8, device="cuda")
+        codec.decode_region(p.stream, p.offsets, p.tiles, r.z, r.rect, alone)
+        assert codec.sync_status() == 0
+        assert np.array_equal(r.result, alone.cpu().numpy()), r.rid
+    codec.close()
+
+
 def test_server_admission_refuses_a_request_beyond_the_slot_budget(synth):
     from paper_2005_08713_gb300 import isx, serve
     codec = isx.Codec(0)
@@ -108,3 +131,38 @@ def test_served_request_over_a_corrupt_tile_alone_reports_an_error(synth):
             assert np.array_equal(r.result, alone.cpu().numpy()), r.rid
     assert sum(r.error is not None for r in done) == 2
     codec.close()
+
+
+def test_copy_rects_any_offsets_and_sizes():
+    """isx_copy_rects against plain tensor slicing: source and destination at every byte offset modulo 4
+    and 16, row lengths of 0..800 bytes (heads and tails of 0-3 bytes, rows shorter than a word), row
+    counts that span several 32-row pieces, pitches that are not multiples of 4; bytes outside the
+    rectangles stay untouched."""
+    torch = torch_cuda()
+    from paper_2005_08713_gb300 import isx
+    rng = np.random.default_rng(11)
+    src = torch.from_numpy(rng.integers(0, 256, 1 << 22, dtype=np.uint8)).cuda()
+    dst = torch.zeros(1 << 26, dtype=torch.uint8, device="cuda")
+    specs, lo = [], 0
+    for k in range(300):
+        rb = int(rng.integers(0, 801)) if k % 7 else int(rng.integers(0, 5))
+        rows = int(rng.integers(1, 130)) if k % 5 else int(rng.integers(0, 3))
+        sp, dp = rb + int(rng.integers(0, 40)), rb + int(rng.integers(0, 40))
+        so = int(rng.integers(0, src.numel() - max(rows, 1) * (sp + 1)))
+        do = lo + int(rng.integers(0, 17))                   # destinations side by side, never overlapping
+        lo = do + max(rows, 1) * (dp + 1)
+        specs.append((so, sp, do, dp, rb, rows))
+    assert lo <= dst.numel()
+    c = np.zeros(len(specs), isx.COPY_DTYPE)
+    for i, (so, sp, do, dp, rb, rows) in enumerate(specs):
+        c[i] = (src.data_ptr() + so, sp, dst.data_ptr() + do, dp, rb, rows)
+    with isx.Codec(0) as codec:
+        codec.copy_rects(c)
+        assert codec.sync_status() == 0
+    got = dst.cpu().numpy()
+    want = np.zeros_like(got)
+    s = src.cpu().numpy()
+    for so, sp, do, dp, rb, rows in specs:
+        for r in range(rows):
+            want[do + r * dp:do + r * dp + rb] = s[so + r * sp:so + r * sp + rb]
+    assert np.array_equal(got, want)
