@@ -19,946 +19,45 @@
 // types' symbols (n = w*h/8 each, types in order HL, LH, HH) padded to 16
 // bytes: the plane segments of Fig. 3 before zero-run and Huffman coding.
 #include "isx_internal.cuh"
+#include "isx_coder_enc.cuh"
 #include "isx_kernels.h"
 
 namespace isx {
-
-constexpr uint32_t kAllZero = 0x80000000u;
-
-// The coefficients of one block: 8 per area in Eq. 2 bit order, int16 or int32.
-struct CoefRef {
-  const uint8_t* base;
-  int is16;
-  __device__ void load(int a, int32_t* c) const {
-    if (is16) {
-      const uint4 u = reinterpret_cast<const uint4*>(base)[a];
-      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        c[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu);
-        c[2 * k + 1] = (int32_t)(int16_t)(w[k] >> 16);
-      }
-    } else {
-      const int4* p4 = reinterpret_cast<const int4*>(base) + 2 * (int64_t)a;
-      const int4 u = p4[0], v = p4[1];
-      c[0] = u.x; c[1] = u.y; c[2] = u.z; c[3] = u.w; c[4] = v.x; c[5] = v.y; c[6] = v.z; c[7] = v.w;
-    }
-  }
-};
-
-__device__ inline uint32_t kept_types(const uint32_t* removed, int p, int pl) {
-  uint32_t km = 0;
-#pragma unroll
-  for (int t = 0; t < 3; ++t)   // fixed trip count: removed[] stays in registers
-    if (t < p && !((removed[t] >> pl) & 1u)) km |= 1u << t;
-  return km;
-}
-
-__device__ inline int64_t region16(uint32_t km, int n) { return ((int64_t)__popc(km) * n + 15) & ~15LL; }
-
-// ------------------------------------------------------------ warp runs
-// A zero-run carry element: bit 31 = every symbol covered is zero, low bits
-// = zeros at the end of the covered range.  Lanes cover 16 symbols each.
-__device__ inline uint32_t warp_carry_exclusive(uint32_t v, uint32_t* inclusive_of_lane, uint32_t* total) {
-  const int lane = threadIdx.x & 31;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x = carry_combine(y, x);
-  }
-  uint32_t ex = __shfl_up_sync(0xffffffffu, x, 1);
-  if (lane == 0) ex = kAllZero;
-  *inclusive_of_lane = x;
-  *total = __shfl_sync(0xffffffffu, x, 31);
-  return ex;
-}
-
-// Summary of a lane's symbols: leading zeros, trailing zeros, any nonzero.
-struct LaneSyms {
-  uint32_t w[4];
-  int cnt;
-  __device__ uint32_t at(int k) const {   // selects, not an indexed array: w[] stays in registers
-    const uint32_t lo = (k & 4) ? w[1] : w[0], hi = (k & 4) ? w[3] : w[2];
-    return (((k & 8) ? hi : lo) >> (8 * (k & 3))) & 0xffu;
-  }
-};
-
-__device__ inline LaneSyms load_lane(const uint8_t* seg, int len, int base) {
-  const int lane = threadIdx.x & 31;
-  LaneSyms L;
-  const int my0 = base + lane * 16;
-  L.cnt = max(0, min(16, len - my0));
-  L.w[0] = L.w[1] = L.w[2] = L.w[3] = 0;
-  if (L.cnt > 0) {
-    const uint4 u = *reinterpret_cast<const uint4*>(seg + my0);
-    L.w[0] = u.x; L.w[1] = u.y; L.w[2] = u.z; L.w[3] = u.w;
-  }
-  return L;
-}
-
-// Bit k set: symbol k of the lane is nonzero (k < cnt).  Four byte
-// compares per word; the multiply gathers the four flags into bits 24..27
-// (the partial products never overlap, so there are no carries).
-__device__ inline uint32_t nonzero_mask(const LaneSyms& L) {
-  uint32_t Z = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const uint32_t t = __vcmpeq4(L.w[q], 0u) & 0x01010101u;
-    Z |= ((t * 0x01020408u) >> 24) << (4 * q);
-  }
-  const uint32_t valid = (1u << L.cnt) - 1u;   // cnt <= 16
-  return ~Z & valid;
-}
-
-// ------------------------------------------------------------- pass 1
-__device__ inline void record_run(uint32_t L, uint32_t* s_hist, uint32_t* s_runs, uint32_t* s_extra) {
-  if (L == 1) {
-    atomicAdd(&s_hist[0], 1u);   // an isolated zero is the literal symbol 0
-    return;
-  }
-  atomicAdd(s_runs, 1u);
-  for (int w = 2; w <= kMaxW; ++w) {
-    const uint32_t M = (1u << w) - 1u;
-    if (M >= L) break;
-    atomicAdd(&s_extra[w], (L + M - 1) / M - 1);
-  }
-}
-
 __global__ void __launch_bounds__(256) k_enc_symbols(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm,
                                                     const uint8_t* __restrict__ coef, uint8_t* __restrict__ sym,
                                                     BlockStats* __restrict__ stats, int* __restrict__ status) {
-  __shared__ uint32_t s_hist[256];
-  __shared__ uint32_t s_extra[kMaxW + 1];
-  __shared__ uint32_t s_runs;
-  __shared__ uint32_t s_or[3], s_neg[3];
-  __shared__ uint32_t s_km[32];
-  __shared__ int64_t s_poff[32];
-  const int64_t bi = perm[blockIdx.x];   // blocks by level: neighbouring CTAs do similar work
-  const BlockDev b = blocks[bi];
-  const int n = b.w * b.h / 8, na = b.p * n;
-  AreaMap am;
-  am.init(b.w, b.h);
-  const CoefRef cf{coef + b.coef, b.coef16};
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
-  if (tid <= kMaxW) s_extra[tid] = 0;
-  if (tid < 3) { s_or[tid] = 0; s_neg[tid] = 0; }
-  if (tid == 0) s_runs = 0;
-  __syncthreads();
-  // int16 blocks whose type rows hold a multiple of 4 areas go 4 consecutive areas (64 bytes) per thread
-  const bool quads = b.coef16 && (n & 3) == 0;
-  {
-    uint32_t o[3] = {0, 0, 0}, ng[3] = {0, 0, 0};
-    if (quads) {
-      const uint4* q4 = reinterpret_cast<const uint4*>(coef + b.coef);
-      for (int u = tid; u < (na >> 2); u += blockDim.x) {
-        uint4 v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = q4[4 * u + i];
-        uint32_t x = 0, g = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const uint32_t w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int32_t lo = (int32_t)(int16_t)(w[k] & 0xffffu), hi = (int32_t)w[k] >> 16;
-            x |= (uint32_t)abs(lo) | (uint32_t)abs(hi);
-            g |= w[k] & 0x80008000u;
-          }
-        }
-        const int t = (4 * u) / n;
-        o[0] |= t == 0 ? x : 0u; o[1] |= t == 1 ? x : 0u; o[2] |= t == 2 ? x : 0u;
-        const uint32_t gn = g ? 1u : 0u;
-        ng[0] |= t == 0 ? gn : 0u; ng[1] |= t == 1 ? gn : 0u; ng[2] |= t == 2 ? gn : 0u;
-      }
-    } else {
-      for (int a = tid; a < na; a += blockDim.x) {
-        int t, kk;
-        am.split(a, &t, &kk);
-        int32_t c[8];
-        cf.load(a, c);
-        uint32_t x = 0, g = 0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          x |= (uint32_t)abs(c[e]);
-          g |= (uint32_t)(c[e] < 0);
-        }
-        o[0] |= t == 0 ? x : 0u; o[1] |= t == 1 ? x : 0u; o[2] |= t == 2 ? x : 0u;
-        ng[0] |= t == 0 ? g : 0u; ng[1] |= t == 1 ? g : 0u; ng[2] |= t == 2 ? g : 0u;
-      }
-    }
-    for (int t = 0; t < 3; ++t) {
-      const uint32_t ro = __reduce_or_sync(0xffffffffu, o[t]);
-      const uint32_t rn = __reduce_or_sync(0xffffffffu, ng[t]);
-      if (lane == 0) {
-        if (ro) atomicOr(&s_or[t], ro);
-        if (rn) atomicOr(&s_neg[t], rn);
-      }
-    }
-  }
-  __syncthreads();
-  const uint32_t all_or = s_or[0] | s_or[1] | s_or[2];
-  const int d = 1 + (all_or ? bitlen_u32(all_or) : 0);
-  uint32_t removed[3];
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    uint32_t r = 0;
-    for (int pl = 0; pl < d; ++pl) {
-      const bool empty = t >= b.p || (pl == 0 ? s_neg[t] == 0 : ((s_or[t] >> (d - 1 - pl)) & 1u) == 0);
-      if (empty) r |= 1u << pl;
-    }
-    removed[t] = r;
-  }
-  if (d > b.dmax) {
-    // only samples above the stated bit depth get here: record an empty block
-    // (every plane removed, no symbols) so that the later passes stay within
-    // the block's buffers, and report the input error
-    BlockStats* st = stats + bi;
-    for (int i = tid; i < 256; i += blockDim.x) st->hist[i] = 0;
-    if (tid <= kMaxW) st->extra[tid] = 0;
-    if (tid == 0) {
-      st->n_runs = 0;
-      st->n_sym = 0;
-      st->removed[0] = st->removed[1] = st->removed[2] = 1u;
-      st->d = 1;
-      set_status(status, kStRange);
-    }
-    return;
-  }
-  uint32_t n_sym = 0;
-  {
-    int64_t off = 0;
-    for (int pl = 0; pl < d; ++pl) {
-      const uint32_t km = kept_types(removed, b.p, pl);
-      if (tid == 0) { s_km[pl] = km; s_poff[pl] = off; }
-      off += km ? region16(km, n) : 0;
-      n_sym += (uint32_t)__popc(km) * n;
-    }
-  }
-  __syncthreads();
-  // symbols of every kept (plane, type), written once
-  uint8_t* S = sym + b.sym;
-  if (quads) {
-    // four areas per thread: one word of four symbols per kept plane
-    const uint4* q4 = reinterpret_cast<const uint4*>(coef + b.coef);
-    for (int u = tid; u < (na >> 2); u += blockDim.x) {
-      const int t = (4 * u) / n, k0 = 4 * u - t * n;
-      uint4 v[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] = q4[4 * u + i];
-      uint32_t negw = 0, mp[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const uint32_t w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-        int32_t c[8];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          c[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu);
-          c[2 * k + 1] = (int32_t)w[k] >> 16;
-        }
-        uint32_t negm = 0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) negm |= (uint32_t)(c[e] < 0) << e;
-        negw |= negm << (8 * i);
-        // magnitudes packed in pairs (e, e + 4) so one shift serves both rows of the area
-        mp[i][0] = (uint32_t)abs(c[0]) | ((uint32_t)abs(c[4]) << 16);
-        mp[i][1] = (uint32_t)abs(c[1]) | ((uint32_t)abs(c[5]) << 16);
-        mp[i][2] = (uint32_t)abs(c[2]) | ((uint32_t)abs(c[6]) << 16);
-        mp[i][3] = (uint32_t)abs(c[3]) | ((uint32_t)abs(c[7]) << 16);
-      }
-      for (int pl = 0; pl < d; ++pl) {
-        const uint32_t km = s_km[pl];
-        if (!((km >> t) & 1u)) continue;
-        uint32_t sw;
-        if (pl == 0) {
-          sw = negw;
-        } else {
-          const int sh = d - 1 - pl;
-          sw = 0;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const uint32_t x = ((mp[i][0] >> sh) & 0x10001u) | (((mp[i][1] >> sh) & 0x10001u) << 1) |
-                               (((mp[i][2] >> sh) & 0x10001u) << 2) | (((mp[i][3] >> sh) & 0x10001u) << 3);
-            sw |= ((x & 0xfu) | ((x >> 12) & 0xf0u)) << (8 * i);
-          }
-        }
-        const int ki = __popc(km & ((1u << t) - 1u));
-        // plane rows start 16-byte aligned and n, k0 are multiples of 4: an aligned word
-        *reinterpret_cast<uint32_t*>(S + s_poff[pl] + (int64_t)ki * n + k0) = sw;
-      }
-    }
-  } else
-  for (int a = tid; a < na; a += blockDim.x) {
-    int t, k;
-    am.split(a, &t, &k);
-    int32_t c[8];
-    cf.load(a, c);
-    uint32_t negm = 0, m01 = 0, m23 = 0, m45 = 0, m67 = 0;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) negm |= (uint32_t)(c[e] < 0) << e;
-    // magnitudes packed in pairs (e, e + 4) so one shift serves both rows of the area
-    m01 = (uint32_t)abs(c[0]) | ((uint32_t)abs(c[4]) << 16);
-    m23 = (uint32_t)abs(c[1]) | ((uint32_t)abs(c[5]) << 16);
-    m45 = (uint32_t)abs(c[2]) | ((uint32_t)abs(c[6]) << 16);
-    m67 = (uint32_t)abs(c[3]) | ((uint32_t)abs(c[7]) << 16);
-    const bool wide = !b.coef16;
-    for (int pl = 0; pl < d; ++pl) {
-      const uint32_t km = s_km[pl];
-      if (!((km >> t) & 1u)) continue;
-      uint32_t s;
-      if (pl == 0) {
-        s = negm;
-      } else {
-        const int sh = d - 1 - pl;
-        if (!wide) {
-          const uint32_t x = ((m01 >> sh) & 0x10001u) | (((m23 >> sh) & 0x10001u) << 1) | (((m45 >> sh) & 0x10001u) << 2) |
-                             (((m67 >> sh) & 0x10001u) << 3);
-          s = (x & 0xfu) | ((x >> 12) & 0xf0u);
-        } else {
-          s = 0;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) s |= (((uint32_t)abs(c[e]) >> sh) & 1u) << e;
-        }
-      }
-      const int ki = __popc(km & ((1u << t) - 1u));
-      S[s_poff[pl] + (int64_t)ki * n + k] = (uint8_t)s;
-    }
-  }
-  __syncthreads();
-  // histogram and zero runs, one warp per plane segment
-  for (int pl = wid; pl < d; pl += nw) {
-    const uint32_t km = s_km[pl];
-    if (!km) continue;
-    const int len = __popc(km) * n;
-    const uint8_t* seg = S + s_poff[pl];
-    uint32_t carry = kAllZero;
-    for (int base = 0; base < len; base += 512) {
-      const LaneSyms L = load_lane(seg, len, base);
-      const uint32_t NZ = nonzero_mask(L);
-      const uint32_t Z = ~NZ & ((1u << L.cnt) - 1u);   // the lane's zero symbols
-      const bool seen = NZ != 0;
-      uint32_t lz = 0, zeros = 0;
-      if (seen) {
-        for (uint32_t m = NZ; m; m &= m - 1u) atomicAdd(&s_hist[L.at(__ffs(m) - 1)], 1u);
-        const int first = __ffs(NZ) - 1, last = 31 - __clz(NZ);
-        lz = (uint32_t)first;
-        zeros = (uint32_t)(L.cnt - 1 - last);
-        // zero runs between the lane's first and last nonzero symbols
-        const uint32_t Zi = Z & ((last >= 31 ? 0xffffffffu : (2u << last) - 1u) & ~((2u << first) - 1u));
-        for (uint32_t st = Zi & ~(Zi << 1); st; st &= st - 1u) {
-          const int s0 = __ffs(st) - 1;
-          record_run((uint32_t)(__ffs(~(Zi >> s0)) - 1), s_hist, &s_runs, s_extra);
-        }
-      }
-      const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
-      uint32_t incl, tot;
-      const uint32_t ex = warp_carry_exclusive(elem, &incl, &tot);
-      const uint32_t cin = carry_combine(carry, ex) & ~kAllZero;
-      if (seen && cin + lz > 0) record_run(cin + lz, s_hist, &s_runs, s_extra);
-      carry = carry_combine(carry, tot);
-    }
-    const uint32_t fin = carry & ~kAllZero;
-    if (lane == 0 && fin) record_run(fin, s_hist, &s_runs, s_extra);
-  }
-  __syncthreads();
-  BlockStats* st = stats + bi;
-  for (int i = tid; i < 256; i += blockDim.x) st->hist[i] = s_hist[i];
-  if (tid <= kMaxW) st->extra[tid] = s_extra[tid];
-  if (tid == 0) {
-    st->n_runs = s_runs;
-    st->n_sym = n_sym;
-    st->removed[0] = removed[0]; st->removed[1] = removed[1]; st->removed[2] = removed[2];
-    st->d = d;
-  }
-}
-
-// ------------------------------------------------------------- pass 2
-// Two-queue Huffman construction (one warp per block): leaves with f > 0
-// sorted ascending by (f, symbol) (warp bitonic sort in registers); each
-// merge takes the lighter queue front twice, the leaf queue first on equal
-// weight; the first taken becomes the left child (bit 0).
-constexpr int kHuffWarps = 8;
-constexpr uint32_t kInf = 0xffffffffu;
-
-struct __align__(16) HuffWarp {
-  uint32_t f[256];        // frequencies
-  uint32_t leaf[256];     // sorted leaves: (f << 8) | symbol
-  uint32_t iw[256];       // internal node weights in creation order
-  uint16_t parent[512];   // parent node id | 0x8000 for a right child
-  uint32_t tree[81];
-  int nl;
-};
-
-// Sorts 8 keys per lane (element lane*8 + r) ascending across the warp.
-__device__ inline void warp_bitonic_256(uint32_t (&k)[8]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int size = 2; size <= 256; size <<= 1) {
-#pragma unroll
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      if (stride >= 8) {
-        const int lstride = stride >> 3;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int i = lane * 8 + r;
-          const bool up = (i & size) == 0;
-          const uint32_t other = __shfl_xor_sync(0xffffffffu, k[r], lstride);
-          const bool lower = (lane & lstride) == 0;
-          const uint32_t mn = min(k[r], other), mx = max(k[r], other);
-          k[r] = (lower == up) ? mn : mx;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int pr = r ^ stride;
-          if (pr > r) {
-            const int i = lane * 8 + r;
-            const bool up = (i & size) == 0;
-            const uint32_t a = k[r], b = k[pr];
-            k[r] = up ? min(a, b) : max(a, b);
-            k[pr] = up ? max(a, b) : min(a, b);
-          }
-        }
-      }
-    }
-  }
-}
-
-// Builds the code of the frequencies in H.f; returns the root id.  With
-// kTree the parent links are stored (H.parent); otherwise only the depth of
-// the leaf holding symbol `track` (-1: none) is returned in *depth.
-template <bool kTree>
-__device__ int huff_build_warp(HuffWarp& H, int track, int* depth) {
-  const int lane = threadIdx.x & 31;
-  uint32_t k[8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int sym = lane * 8 + r;
-    const uint32_t fr = H.f[sym];
-    k[r] = fr ? ((fr << 8) | (uint32_t)sym) : kInf;
-  }
-  // symbols with a nonzero count
-  int present = 0;
-#pragma unroll
-  for (int r = 0; r < 8; ++r) present += __popc(__ballot_sync(0xffffffffu, k[r] != kInf));
-  if (present <= 32) {
-    // small alphabet (the coarse levels' blocks): gather the keys, one per
-    // lane, and sort 32 instead of 256
-    int base = 0;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const uint32_t m = __ballot_sync(0xffffffffu, k[r] != kInf);
-      if (k[r] != kInf) H.leaf[base + __popc(m & ((1u << lane) - 1u))] = k[r];
-      base += __popc(m);
-    }
-    __syncwarp();
-    uint32_t x = lane < present ? H.leaf[lane] : kInf;
-#pragma unroll
-    for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        const uint32_t other = __shfl_xor_sync(0xffffffffu, x, stride);
-        const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
-        x = (lower == up) ? min(x, other) : max(x, other);
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < 8; ++r) k[r] = kInf;
-    k[0] = x;   // key of rank `lane` (lanes >= present: none)
-    H.leaf[lane] = x;
-  } else {
-    warp_bitonic_256(k);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) H.leaf[lane * 8 + r] = k[r];
-  }
-  int cnt = 0, where = -1;
-  if (present <= 32) {
-    cnt = lane == 0 ? present : 0;
-    if (k[0] != kInf && (int)(k[0] & 0xffu) == track) where = lane;
-  } else {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      cnt += k[r] != kInf;
-      if (k[r] != kInf && (int)(k[r] & 0xffu) == track) where = lane * 8 + r;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    where = max(where, __shfl_xor_sync(0xffffffffu, where, o));
-  }
-  const int nl = cnt;
-  __syncwarp();
-  if (lane == 0) {
-    H.nl = nl;
-    int qa = 0, qb = 0, ni = 0, cur = where, dep = 0;
-    uint32_t wl = nl > 0 ? H.leaf[0] >> 8 : kInf, wi = kInf;
-    for (int st = 0; st < nl - 1; ++st) {
-      int a, b;
-      uint32_t wa, wb;
-      if (wl <= wi) { a = qa; wa = wl; ++qa; wl = qa < nl ? H.leaf[qa] >> 8 : kInf; }   // the leaf queue wins ties
-      else { a = nl + qb; wa = wi; ++qb; wi = qb < ni ? H.iw[qb] : kInf; }
-      if (wl <= wi) { b = qa; wb = wl; ++qa; wl = qa < nl ? H.leaf[qa] >> 8 : kInf; }
-      else { b = nl + qb; wb = wi; ++qb; wi = qb < ni ? H.iw[qb] : kInf; }
-      const uint32_t wn = wa + wb;
-      H.iw[ni] = wn;
-      if (kTree) {
-        H.parent[a] = (uint16_t)(nl + ni);
-        H.parent[b] = (uint16_t)((nl + ni) | 0x8000);
-      } else if (a == cur || b == cur) {
-        ++dep;
-        cur = nl + ni;
-      }
-      if (qb == ni) wi = wn;   // the internal queue was empty: the new node is its front
-      ++ni;
-    }
-    if (depth) *depth = dep;
-  }
-  __syncwarp();
-  return nl <= 1 ? 0 : 2 * nl - 2;
+  __shared__ SymShared S;
+  // blocks by level: neighbouring CTAs do similar work
+  enc_symbols_block(perm[blockIdx.x], blocks, coef, sym, stats, status, S, threadIdx.x, blockDim.x, CtaBarrier());
 }
 
 __global__ void __launch_bounds__(32 * kHuffWarps, 4) k_block_huffman(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm,
                                                                   const BlockStats* __restrict__ stats, BlockCode* __restrict__ codes,
                                                                   int64_t nb) {
   __shared__ HuffWarp hw[kHuffWarps];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
   const int64_t gi = (int64_t)blockIdx.x * kHuffWarps + wid;
   if (gi >= nb) return;
   // blocks by level: the warps of a CTA get blocks of similar size and finish together
-  const int64_t bi = perm[gi];
-  HuffWarp& H = hw[wid];
-  const BlockStats& st = stats[bi];
-  const BlockDev b = blocks[bi];
-  BlockCode& bc = codes[bi];
-  const int d = st.d, p = b.p;
-  const uint32_t n_sym = st.n_sym;
-  const int t0 = bitlen_u32((uint32_t)(p * b.w * b.h / 8)) - 1 + 5;
-  if (lane == 0) {
-    bc.d = d;
-    bc.p = p;
-    for (int t = 0; t < 3; ++t) bc.removed[t] = st.removed[t];
-    bc.t0 = t0;
-  }
-  if (n_sym == 0) {
-    if (lane == 0) {
-      bc.any_kept = 0;
-      bc.token_bits = 0;
-      bc.tree_bits = 0;
-      bc.czr = 0;
-      bc.wbits = 0;
-    }
-    return;
-  }
-  // C_zr: least frequent of 1..255, smallest on ties
-  uint32_t best = kInf;
-  for (int s = lane; s < 256; s += 32) {
-    const uint32_t fr = st.hist[s];
-    H.f[s] = fr;
-    if (s >= 1) best = min(best, (fr << 8) | (uint32_t)s);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-  const int czr = (int)(best & 0xffu);
-  const uint32_t lit_czr = best >> 8;
-  __syncwarp();
-  // provisional code: every run counts once for C_zr; l = C_zr's code length
-  if (lane == 0) H.f[czr] = lit_czr + st.n_runs;
-  __syncwarp();
-  // The provisional tree is built with its parent links: when the chosen
-  // width needs no extra run tokens, the final counts equal these and the
-  // tree is reused as is.
-  int root = huff_build_warp<true>(H, -1, nullptr);
-  int l = 0;
-  if (H.f[czr] > 0 && H.nl > 1) {
-    int leaf = -1;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int i = lane + 32 * m;
-      if (i < H.nl && (int)(H.leaf[i] & 0xffu) == czr) leaf = i;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) leaf = max(leaf, __shfl_xor_sync(0xffffffffu, leaf, o));
-    int dep = 0;
-    for (int v = leaf; v != root && dep < 64; ++dep) v = H.parent[v] & 0x7fff;   // the leaf's depth
-    l = dep;
-  }
-  // Eq. 3 (reading): w minimises (w + l) * (#C_zr tokens at width w) over [2, b]
-  int bmax = n_sym > 1 ? bitlen_u32(n_sym - 1) : 0;
-  if (bmax < 2) bmax = 2;
-  int wbest = 2;
-  uint64_t bestc = ~0ull;
-  for (int w = 2; w <= bmax; ++w) {
-    const uint64_t pairs = (uint64_t)lit_czr + st.n_runs + st.extra[w];
-    const uint64_t cost = (uint64_t)(w + l) * pairs;
-    if (cost < bestc) { bestc = cost; wbest = w; }
-  }
-  if (st.extra[wbest] != 0) {   // C_zr's count changes: build the final tree
-    __syncwarp();
-    if (lane == 0) H.f[czr] = lit_czr + st.n_runs + st.extra[wbest];
-    __syncwarp();
-    root = huff_build_warp<true>(H, -1, nullptr);
-  }
-  const int nl = H.nl;
-  // codes: every leaf walks up to the root; a lane walks its (up to) 8 leaves together
-  for (int s2 = lane; s2 < 256; s2 += 32) { bc.code[s2] = 0; bc.len[s2] = 0; }
-  for (int k = lane; k < 81; k += 32) H.tree[k] = 0;
-  int v[8], len[8];
-  uint32_t code[8];
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    v[m] = lane + 32 * m;
-    code[m] = 0;
-    len[m] = 0;
-  }
-  for (int depth = 0; depth < 40; ++depth) {
-    bool more = false;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      if (lane + 32 * m < nl && v[m] != root) {
-        const uint32_t p = H.parent[v[m]];
-        code[m] |= (p >> 15) << len[m];
-        ++len[m];
-        v[m] = p & 0x7fff;
-        more = true;
-      }
-    }
-    if (!__any_sync(0xffffffffu, more)) break;
-  }
-  // Preorder tree (Fig. 3: 0 = internal node, 1 + 8-bit symbol = leaf).  Leaves
-  // appear in preorder in the lexicographic order of their codes, and the
-  // record of a leaf with code c of length l and rank r in that order starts
-  // at bit l + 10 r - popcount(c): its l ancestors' 0 bits, plus, for each
-  // right turn on its path, the left sibling subtree (10 bits per leaf less
-  // one).  Ranks by counting smaller left-aligned codes.
-  uint32_t* K = H.iw;   // the merge's weights are no longer needed
-  uint64_t tb = 0;
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int i = lane + 32 * m;
-    if (i < nl) {
-      K[i] = len[m] ? code[m] << (31 - len[m]) : 0u;   // codes are at most 31 bits (Fibonacci bound)
-      const int sym = (int)(H.leaf[i] & 0xffu);
-      bc.code[sym] = code[m];
-      bc.len[sym] = (uint8_t)len[m];
-      tb += (uint64_t)H.f[sym] * len[m];
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tb += __shfl_xor_sync(0xffffffffu, tb, o);
-  __syncwarp();
-  int rank[8];
-#pragma unroll
-  for (int m = 0; m < 8; ++m) rank[m] = 0;
-  uint32_t key[8];
-#pragma unroll
-  for (int m = 0; m < 8; ++m) key[m] = lane + 32 * m < nl ? K[lane + 32 * m] : 0u;
-  if (lane < 3 && nl + lane < ((nl + 3) & ~3)) K[nl + lane] = kInf;   // pad to whole words of four: never smaller
-  __syncwarp();
-  for (int j = 0; j < nl; j += 4) {
-    const uint4 kq = *reinterpret_cast<const uint4*>(K + j);
-#pragma unroll
-    for (int m = 0; m < 8; ++m) rank[m] += (kq.x < key[m]) + (kq.y < key[m]) + (kq.z < key[m]) + (kq.w < key[m]);
-  }
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int i = lane + 32 * m;
-    if (i < nl) {
-      const int pos = len[m] + 10 * rank[m] - __popc(code[m]);
-      const uint32_t val = 0x100u | (H.leaf[i] & 0xffu);
-      const int wi = pos >> 5, off = pos & 31;
-      const uint64_t vv = (uint64_t)val << (64 - off - 9);
-      atomicOr(&H.tree[wi], (uint32_t)(vv >> 32));
-      if ((uint32_t)vv) atomicOr(&H.tree[wi + 1], (uint32_t)vv);
-    }
-  }
-  if (lane == 0) bc.tree_bits = 10 * nl - 1;
-  __syncwarp();
-  for (int k = lane; k < 80; k += 32) bc.tree[k] = H.tree[k];
-  if (lane == 0) {
-    bc.any_kept = 1;
-    bc.czr = czr;
-    bc.wbits = wbest;
-    bc.token_bits = tb + (uint64_t)wbest * H.f[czr];
-  }
+  block_huffman(perm[gi], blocks, stats, codes, hw[wid]);
 }
 
-// ------------------------------------------------------------- pass 3/4
-struct CodeTab {
-  const uint32_t* code;
-  const uint8_t* len;
-  int czr, wbits;
-  uint32_t M;
-};
-
-__device__ inline uint32_t run_bits(const CodeTab& ct, uint32_t L) {
-  if (L == 1) return ct.len[0];
-  if (ct.M == 0) return 0;
-  return ((L + ct.M - 1) / ct.M) * (uint32_t)(ct.len[ct.czr] + ct.wbits);
-}
-__device__ inline uint32_t lit_bits(const CodeTab& ct, uint32_t s) {
-  return ct.len[s] + ((int)s == ct.czr ? ct.wbits : 0);
-}
-
-// MSB-first writer of one lane's contiguous bit range straight into the
-// stream (32-bit words, big endian).  Words strictly inside the range are
-// stored; the first and last (shared with neighbouring ranges) are OR-ed
-// into the zero-initialised stream.
-struct LaneWriter {
-  uint32_t* out;
-  int64_t w0, wcur;
-  uint64_t acc;
-  int nacc;
-  __device__ void begin(uint32_t* o, int64_t bitpos) {
-    out = o;
-    wcur = w0 = bitpos >> 5;
-    acc = 0;
-    nacc = (int)(bitpos & 31);
-  }
-  __device__ void word(uint32_t x) {
-    const uint32_t be = __byte_perm(x, 0, 0x0123);
-    if (wcur == w0) atomicOr(&out[wcur], be);
-    else out[wcur] = be;
-    ++wcur;
-  }
-  __device__ void put(uint32_t v, int nb) {   // nb <= 32
-    if (nb <= 0) return;
-    const uint64_t x = (uint64_t)(nb == 32 ? v : (v & ((1u << nb) - 1u)));
-    acc |= x << (64 - nacc - nb);
-    nacc += nb;
-    if (nacc >= 32) {
-      word((uint32_t)(acc >> 32));
-      acc <<= 32;
-      nacc -= 32;
-    }
-  }
-  __device__ void end() {
-    if (nacc > 0) atomicOr(&out[wcur], __byte_perm((uint32_t)(acc >> 32), 0, 0x0123));
-  }
-};
-
-__device__ inline void put_run(const CodeTab& ct, LaneWriter& W, uint32_t L) {
-  if (L == 1) {
-    W.put(ct.code[0], ct.len[0]);
-    return;
-  }
-  if (ct.M == 0) return;   // counter width is always >= 2
-  const int lc = ct.len[ct.czr];
-  const uint32_t cz = ct.code[ct.czr];
-  while (L > 0) {
-    const uint32_t k = L >= ct.M ? ct.M : L;
-    W.put(cz, lc);
-    W.put(k, ct.wbits);
-    L -= k;
-  }
-}
-
-__device__ inline void put_literal(const CodeTab& ct, LaneWriter& W, uint32_t s) {
-  W.put(ct.code[s], ct.len[s]);
-  if ((int)s == ct.czr) W.put(0, ct.wbits);   // counter 0: a literal C_zr
-}
-
-// Per-block layout found by the size pass.
-struct BlockHdr {
-  int32_t t, pad;
-  int64_t hdr_bits;
-  uint32_t seglen[32];
-};
-
-// One warp walks plane segment `seg` (len symbols) in chunks of 512:
-// WRITE = false returns the segment's bit length; WRITE = true writes its
-// tokens from absolute bit position `pos`.
-template <bool WRITE>
-__device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct, uint32_t* out, int64_t pos) {
-  const int lane = threadIdx.x & 31;
-  uint32_t carry = kAllZero;
-  uint64_t total = 0;
-  for (int base = 0; base < len; base += 512) {
-    const LaneSyms L = load_lane(seg, len, base);
-    // nonzero symbols of the lane as a bit mask: the loops visit only those;
-    // the zeros between two of them form one run
-    const uint32_t NZ = nonzero_mask(L);
-    const bool seen = NZ != 0;
-    uint32_t zeros = 0, lz = 0, bits = 0;
-    if (seen) {
-      const int first = __ffs(NZ) - 1, last = 31 - __clz(NZ);
-      lz = (uint32_t)first;
-      zeros = (uint32_t)(L.cnt - 1 - last);
-      int prev = first;
-      for (uint32_t m = NZ; m; m &= m - 1u) {
-        const int k = __ffs(m) - 1;
-        if (k - prev > 1) bits += run_bits(ct, (uint32_t)(k - prev - 1));
-        bits += lit_bits(ct, L.at(k));
-        prev = k;
-      }
-    }
-    const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
-    uint32_t incl, tot;
-    const uint32_t ex = warp_carry_exclusive(elem, &incl, &tot);
-    const uint32_t cin = carry_combine(carry, ex) & ~kAllZero;
-    const uint32_t lead = seen ? cin + lz : 0;
-    if (lead) bits += run_bits(ct, lead);
-    // the lane holding the segment's last symbol closes the final run
-    const bool last_lane = base + 512 >= len && lane == (len - 1 - base) / 16;
-    const uint32_t fin = last_lane ? (carry_combine(carry, incl) & ~kAllZero) : 0;
-    if (fin) bits += run_bits(ct, fin);
-    // bit offsets of the lanes within the chunk
-    uint32_t x = bits;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    const uint32_t chunk_bits = __shfl_sync(0xffffffffu, x, 31);
-    if (WRITE && bits) {
-      LaneWriter W;
-      W.begin(out, pos + (int64_t)total + (x - bits));
-      if (lead) put_run(ct, W, lead);
-      int prev = __ffs(NZ) - 1;
-      for (uint32_t m = NZ; m; m &= m - 1u) {
-        const int k = __ffs(m) - 1;
-        if (k - prev > 1) put_run(ct, W, (uint32_t)(k - prev - 1));
-        put_literal(ct, W, L.at(k));
-        prev = k;
-      }
-      if (fin) put_run(ct, W, fin);
-      W.end();
-    }
-    total += chunk_bits;
-    carry = carry_combine(carry, tot);
-  }
-  return total;
-}
-
-constexpr int kEmitWarps = 8;
-constexpr int kEncGroup = 16;
-constexpr int kEncSmem = kEncGroup * (256 * 4 + 256) + kEncGroup * 32 * 2;
-
-__device__ inline int64_t block_bit_start(const TileDev& t, const int64_t* final_pos, int64_t bi) {
-  return 8 * (final_pos[bi] + (bi == t.block_base ? 32 + 4 * (int64_t)t.nb : 0));
-}
-
-// Group of kEncGroup level-sorted blocks: their code tables in shared
-// memory and their (block, plane) segments listed plane-major.
-struct EncGroup {
-  uint32_t (*code)[256];
-  uint8_t (*len)[256];
-  uint16_t* item;
-  int nitem;
-};
-
-__device__ int load_group(const int64_t* perm, int64_t nb, const BlockDev* blocks, const BlockCode* codes, uint8_t* dyn, EncGroup& G,
-                          int* s_nitem) {
-  const int64_t g0 = (int64_t)blockIdx.x * kEncGroup;
-  const int ng = (int)min((int64_t)kEncGroup, nb - g0);
-  G.code = reinterpret_cast<uint32_t (*)[256]>(dyn);
-  G.len = reinterpret_cast<uint8_t (*)[256]>(dyn + kEncGroup * 256 * 4);
-  G.item = reinterpret_cast<uint16_t*>(dyn + kEncGroup * (256 * 4 + 256));
-  // code and length tables of the group's blocks, all copies in flight at
-  // once: per block 64 16-byte words of codes and 16 of lengths
-  for (int idx = threadIdx.x; idx < ng * 80; idx += blockDim.x) {
-    const int j = idx / 80, q = idx - j * 80;
-    const BlockCode& bc = codes[perm[g0 + j]];
-    if (!bc.any_kept) continue;
-    if (q < 64) reinterpret_cast<uint4*>(G.code[j])[q] = reinterpret_cast<const uint4*>(bc.code)[q];
-    else reinterpret_cast<uint4*>(G.len[j])[q - 64] = reinterpret_cast<const uint4*>(bc.len)[q - 64];
-  }
-  if (threadIdx.x < 32) {
-    const int j = threadIdx.x;
-    uint32_t planes = 0;
-    if (j < ng) {
-      const BlockCode& bc = codes[perm[g0 + j]];
-      if (bc.any_kept)
-        for (int pl = 0; pl < bc.d; ++pl)
-          if (kept_types(bc.removed, bc.p, pl)) planes |= 1u << pl;
-    }
-    int base = 0;
-    for (int pl = 0; pl < 32; ++pl) {
-      const uint32_t m = __ballot_sync(0xffffffffu, (planes >> pl) & 1u);
-      if ((planes >> pl) & 1u) G.item[base + __popc(m & ((1u << j) - 1u))] = (uint16_t)((j << 5) | pl);
-      base += __popc(m);
-    }
-    if (j == 0) *s_nitem = base;
-  }
-  __syncthreads();
-  G.nitem = *s_nitem;
-  return ng;
-}
-
-// Symbol offset of plane pl inside a block's region.
-__device__ inline int64_t plane_offset(const uint32_t* removed, int p, int n, int pl) {
-  int64_t off = 0;
-  for (int q = 0; q < pl; ++q) {
-    const uint32_t km = kept_types(removed, p, q);
-    if (km) off += region16(km, n);
-  }
-  return off;
-}
-
-// Size pass: one warp per (block, plane) segment gives its exact bit length.
 __global__ void __launch_bounds__(32 * kEmitWarps) k_enc_size(const BlockDev* __restrict__ blocks, const int64_t* __restrict__ perm,
                                                              int64_t nb, const uint8_t* sym, const BlockCode* __restrict__ codes,
                                                              BlockHdr* __restrict__ hdrs) {
   extern __shared__ __align__(16) uint8_t dyn[];
   __shared__ int s_nitem;
-  EncGroup G;
-  load_group(perm, nb, blocks, codes, dyn, G, &s_nitem);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t g0 = (int64_t)blockIdx.x * kEncGroup;
-  for (int it = wid; it < G.nitem; it += kEmitWarps) {
-    const int j = G.item[it] >> 5, pl = G.item[it] & 31;
-    const int64_t bi = perm[g0 + j];
-    const BlockDev b = blocks[bi];
-    const BlockCode& bc = codes[bi];
-    const int n = b.w * b.h / 8;
-    const CodeTab ct{G.code[j], G.len[j], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
-    const uint32_t km = kept_types(bc.removed, b.p, pl);
-    const uint64_t bits = warp_segment<false>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, nullptr, 0);
-    if (lane == 0) hdrs[bi].seglen[pl] = (uint32_t)bits;
-  }
+  enc_size_group(perm, g0, (int)min((int64_t)kEncGroup, nb - g0), blocks, sym, codes, hdrs, dyn, &s_nitem, threadIdx.x, blockDim.x,
+                 CtaBarrier());
 }
 
-// Per block: seektable width t (raised only when a segment length needs
-// more bits), header bits and the block's size in the stream.
 __global__ void k_enc_blocksize(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks, int64_t nb,
                                 const BlockCode* __restrict__ codes, BlockHdr* __restrict__ hdrs, int64_t* __restrict__ item_size,
                                 int* __restrict__ status) {
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (bi >= nb) return;
-  const BlockDev b = blocks[bi];
-  const BlockCode& bc = codes[bi];
-  const TileDev& tile = tiles[b.tile];
-  const int64_t extra = bi == tile.block_base ? 32 + 4 * (int64_t)tile.nb : 0;
-  const int d = bc.d, p = b.p;
-  BlockHdr& H = hdrs[bi];
-  if (!bc.any_kept) {
-    H.t = 0;
-    H.hdr_bits = 5 + (int64_t)p * d;
-    item_size[bi] = (5 + (int64_t)p * d + 7) / 8 + extra;
-    return;
-  }
-  uint64_t sum = 0;
-  uint32_t mx = 0;
-  for (int pl = 0; pl < d; ++pl) {
-    uint32_t v = 0;
-    if (kept_types(bc.removed, p, pl)) v = H.seglen[pl];
-    else H.seglen[pl] = 0;
-    sum += v;
-    mx = max(mx, v);
-  }
-  const int t = max(bc.t0, mx ? bitlen_u32(mx) : 0);
-  const int64_t hdr = 5 + (int64_t)p * d + 18 + (int64_t)d * t + bc.tree_bits;
-  H.t = t;
-  H.hdr_bits = hdr;
-  if (sum != bc.token_bits) set_status(status, 7);
-  item_size[bi] = (hdr + (int64_t)sum + 7) / 8 + extra;
+  if (bi < nb) enc_blocksize(bi, tiles, blocks, codes, hdrs, item_size, status);
 }
-
-// The stream is written in whole 32-bit words: it needs its size rounded
-// up to a multiple of 4 bytes of capacity.
-__device__ inline int64_t needed_capacity(int64_t total) { return (total + 3) & ~3LL; }
 
 __global__ void k_zero_stream(uint32_t* __restrict__ out, const int64_t* __restrict__ totals, int64_t out_cap) {
   const int64_t total = totals[0];
@@ -967,8 +66,6 @@ __global__ void k_zero_stream(uint32_t* __restrict__ out, const int64_t* __restr
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (int64_t)gridDim.x * blockDim.x) out[k] = 0;
 }
 
-// Emit pass: warps write the group's block headers (d, removed mask, C_zr,
-// w, t, seektable, tree), then one warp per segment writes its tokens.
 __global__ void __launch_bounds__(32 * kEmitWarps) k_enc_emit(const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
                                                              const int64_t* __restrict__ perm, int64_t nb, const uint8_t* sym,
                                                              const BlockCode* __restrict__ codes, const BlockHdr* __restrict__ hdrs,
@@ -977,64 +74,12 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_enc_emit(const TileDev* __r
   extern __shared__ __align__(16) uint8_t dyn[];
   __shared__ int s_nitem;
   if (needed_capacity(totals[0]) > out_cap) return;
-  EncGroup G;
-  const int ng = load_group(perm, nb, blocks, codes, dyn, G, &s_nitem);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t g0 = (int64_t)blockIdx.x * kEncGroup;
-  for (int j = wid; j < ng; j += kEmitWarps) {
-    const int64_t bi = perm[g0 + j];
-    const BlockDev b = blocks[bi];
-    const BlockCode& bc = codes[bi];
-    const BlockHdr& H = hdrs[bi];
-    const int d = bc.d, p = b.p;
-    const int64_t B0 = block_bit_start(tiles[b.tile], final_pos, bi);
-    if (lane == 0) {
-      LaneWriter W;
-      W.begin(out, B0);
-      W.put((uint32_t)d, 5);
-      for (int ty = 0; ty < p; ++ty)
-        for (int pl = 0; pl < d; ++pl) W.put((bc.removed[ty] >> pl) & 1u, 1);
-      if (bc.any_kept) {
-        W.put((uint32_t)bc.czr, 8);
-        W.put((uint32_t)bc.wbits, 5);
-        W.put((uint32_t)H.t, 5);
-      }
-      W.end();
-    }
-    if (!bc.any_kept) continue;
-    const int t = H.t;
-    const int64_t seek = B0 + 5 + (int64_t)p * d + 18;
-    if (lane < d) {
-      LaneWriter W;
-      W.begin(out, seek + (int64_t)lane * t);
-      W.put(H.seglen[lane], t);
-      W.end();
-    }
-    const int64_t tree_pos = seek + (int64_t)d * t;
-    for (int k = lane; k * 32 < bc.tree_bits; k += 32) {
-      const int nbk = min(32, bc.tree_bits - 32 * k);
-      LaneWriter W;
-      W.begin(out, tree_pos + 32 * k);
-      W.put(bc.tree[k] >> (32 - nbk), nbk);
-      W.end();
-    }
-  }
-  for (int it = wid; it < G.nitem; it += kEmitWarps) {
-    const int j = G.item[it] >> 5, pl = G.item[it] & 31;
-    const int64_t bi = perm[g0 + j];
-    const BlockDev b = blocks[bi];
-    const BlockCode& bc = codes[bi];
-    const BlockHdr& H = hdrs[bi];
-    const int n = b.w * b.h / 8;
-    const CodeTab ct{G.code[j], G.len[j], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
-    int64_t pos = block_bit_start(tiles[b.tile], final_pos, bi) + H.hdr_bits;
-    for (int q = 0; q < pl; ++q) pos += H.seglen[q];
-    const uint32_t km = kept_types(bc.removed, b.p, pl);
-    warp_segment<true>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, out, pos);
-  }
+  enc_emit_group(perm, g0, (int)min((int64_t)kEncGroup, nb - g0), tiles, blocks, sym, codes, hdrs, final_pos, out, dyn, &s_nitem,
+                 threadIdx.x, blockDim.x, CtaBarrier());
 }
 
-// Tile headers (little endian) and the stream offsets; capacity check.
+// Tile headers and the stream offsets; capacity check.
 __global__ void k_tile_headers(const TileDev* __restrict__ tiles, int n_tiles, const int64_t* __restrict__ final_pos,
                                const int64_t* __restrict__ item_size, const int64_t* __restrict__ totals, uint8_t* __restrict__ out,
                                int64_t out_cap, uint64_t* __restrict__ tile_offsets, int* __restrict__ status) {
@@ -1049,25 +94,7 @@ __global__ void k_tile_headers(const TileDev* __restrict__ tiles, int n_tiles, c
   }
   const int64_t toff = final_pos[t.block_base];
   if (threadIdx.x == 0) tile_offsets[ti] = (uint64_t)toff;
-  if (!fits) {
-    if (threadIdx.x == 0) stamp_tile(t, kStampEncEnd);
-    return;
-  }
-  uint8_t* o = out + toff;
-  const int64_t hdr = 32 + 4 * (int64_t)t.nb;
-  if (threadIdx.x == 0) {
-    o[0] = 'I'; o[1] = 'S'; o[2] = 'X'; o[3] = '1';
-    o[4] = (uint8_t)t.w; o[5] = (uint8_t)(t.w >> 8);
-    o[6] = (uint8_t)t.h; o[7] = (uint8_t)(t.h >> 8);
-    o[8] = (uint8_t)t.C; o[9] = (uint8_t)t.bits; o[10] = (uint8_t)t.L; o[11] = (uint8_t)t.ct;
-    for (int k = 0; k < 4; ++k) o[12 + k] = (uint8_t)((uint32_t)t.nb >> (8 * k));
-    for (int k = 0; k < 16; ++k) o[16 + k] = k <= t.L ? t.q[k] : 0;
-  }
-  for (int j = threadIdx.x; j < t.nb; j += blockDim.x) {
-    const int64_t bi = t.block_base + j;
-    const int64_t end = final_pos[bi] + item_size[bi] - (toff + hdr);   // the first item includes the header
-    for (int k = 0; k < 4; ++k) o[32 + 4 * j + k] = (uint8_t)((uint64_t)end >> (8 * k));
-  }
+  if (fits) write_tile_header(t, toff, final_pos, item_size, out, threadIdx.x, blockDim.x);
   __syncthreads();
   if (threadIdx.x == 0) stamp_tile(t, kStampEncEnd);   // the tile's stream is complete
 }

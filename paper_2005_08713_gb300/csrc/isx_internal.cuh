@@ -291,6 +291,17 @@ __device__ T cta_reduce_max(T v, T* tmp /* >= 32 */) {
 
 __device__ inline void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
+// Barriers of device code run by a whole CTA (CtaBarrier) or by a group of
+// whole warps of it (NamedBarrier: the n threads that use barrier id, 3..15;
+// 0 is __syncthreads, 1 and 2 belong to the fused transforms).
+struct CtaBarrier {
+  __device__ void operator()() const { __syncthreads(); }
+};
+struct NamedBarrier {
+  int id, n;
+  __device__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+};
+
 // Per-tile timestamps (ns of the GPU's global timer): the earliest start and
 // the latest end of a tile's work in an encode or a decode.
 enum StampKind { kStampEncStart = 0, kStampEncEnd = 1, kStampDecStart = 2, kStampDecEnd = 3 };
