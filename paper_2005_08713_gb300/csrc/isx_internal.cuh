@@ -14,7 +14,7 @@ constexpr int kCtaThreads = 256;    // CTA size of the per-block coding kernels
 constexpr int kMaxDConst = 31;
 constexpr int kSmemPlaneBytes = 160 * 1024;   // largest int16 channel plane of a tile on the fused shared-memory path
 
-enum DevStatus : int { kStOk = 0, kStCapacity = 2, kStCorrupt = 3, kStTimeout = 6, kStRange = 8 };
+enum DevStatus : int { kStOk = 0, kStCapacity = 2, kStCorrupt = 3, kStTimeout = 6, kStInternal = 7, kStRange = 8 };
 
 // One tile as the kernels see it (copied from isx_tile_desc plus its plan).
 struct TileDev {

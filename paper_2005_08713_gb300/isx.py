@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libisx_gb300.so")
 
 ISX_OK, ISX_ERR_ARG, ISX_ERR_CAPACITY, ISX_ERR_CORRUPT, ISX_ERR_OOM, ISX_ERR_CUDA, ISX_ERR_TIMEOUT = range(7)
 STATUS_NAMES = {0: "ISX_OK", 1: "ISX_ERR_ARG", 2: "ISX_ERR_CAPACITY", 3: "ISX_ERR_CORRUPT", 4: "ISX_ERR_OOM",
-                5: "ISX_ERR_CUDA", 6: "ISX_ERR_TIMEOUT"}
+                5: "ISX_ERR_CUDA", 6: "ISX_ERR_TIMEOUT", 7: "ISX_ERR_INTERNAL"}
 
 # every entry point declared in include/isx.h
 EXPORTS = ["isx_create", "isx_destroy", "isx_encode_tiles", "isx_decode_region", "isx_encode_tiles_host",

@@ -83,3 +83,12 @@ def test_struct_layouts_match_the_compiled_header(tmp_path):
     assert got[("isx_rect_copy", "size")] == isx.COPY_DTYPE.itemsize == 40
     for n in fields["isx_rect_copy"]:
         assert got[("isx_rect_copy", n)] == isx.COPY_DTYPE.fields[n][1], n
+
+
+def test_status_names_match_the_header_enum():
+    from paper_2005_08713_gb300 import isx
+    with open(os.path.join(ROOT, "include", "isx.h")) as f:
+        src = f.read()
+    body = src[src.index("typedef enum {"):src.index("} isx_status;")]
+    enum = {int(v): n for n, v in re.findall(r"\b(ISX_[A-Z_]+)\s*=\s*(\d+)", body)}
+    assert enum == isx.STATUS_NAMES
