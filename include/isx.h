@@ -44,9 +44,8 @@ typedef enum {
   ISX_ERR_OOM = 4,       /* scratch would exceed the context's HBM budget, or cudaMalloc failed */
   ISX_ERR_CUDA = 5,      /* a CUDA runtime call failed */
   ISX_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
-  ISX_ERR_INTERNAL = 7   /* an internal consistency check failed (the encoder's exact sizes disagree with what
-                            it emits, or a write fell outside the range planned for it: such a write is skipped,
-                            nothing outside the output buffer is written) */
+  ISX_ERR_INTERNAL = 7   /* an internal consistency check failed (the encoder's exact segment sizes disagree
+                            with the token bits its Huffman pass counted) */
 } isx_status;
 
 /* Colour transform of a tile (the paper's "optional colorspace

@@ -694,39 +694,24 @@ __device__ inline uint32_t lit_bits(const CodeTab& ct, uint32_t s) {
   return ct.len[s] + ((int)s == ct.czr ? ct.wbits : 0);
 }
 
-// The words a stream writer may write: out[lo .. hi) (the output buffer),
-// and the status word a write outside them sets.
-struct StreamSpan {
-  uint32_t* out;
-  int64_t lo, hi;
-  int* status;
-};
-
 // MSB-first writer of one lane's contiguous bit range straight into the
 // stream (32-bit words, big endian).  Words strictly inside the range are
 // stored; the first and last (shared with neighbouring ranges) are OR-ed
-// into the zero-initialised stream.  A word outside the span is not
-// written: the span's status becomes ISX_ERR_INTERNAL (a consistency
-// check: the exact sizes place every word inside the stream).
+// into the zero-initialised stream.
 struct LaneWriter {
   uint32_t* out;
-  int64_t w0, wcur, lo, hi;
+  int64_t w0, wcur;
   uint64_t acc;
   int nacc;
-  int* status;
-  __device__ void begin(const StreamSpan& sp, int64_t bitpos) {
-    out = sp.out;
-    lo = sp.lo;
-    hi = sp.hi;
-    status = sp.status;
+  __device__ void begin(uint32_t* o, int64_t bitpos) {
+    out = o;
     wcur = w0 = bitpos >> 5;
     acc = 0;
     nacc = (int)(bitpos & 31);
   }
   __device__ void word(uint32_t x) {
     const uint32_t be = __byte_perm(x, 0, 0x0123);
-    if (wcur < lo || wcur >= hi) set_status(status, kStInternal);
-    else if (wcur == w0) atomicOr(&out[wcur], be);
+    if (wcur == w0) atomicOr(&out[wcur], be);
     else out[wcur] = be;
     ++wcur;
   }
@@ -742,9 +727,7 @@ struct LaneWriter {
     }
   }
   __device__ void end() {
-    if (nacc <= 0) return;
-    if (wcur < lo || wcur >= hi) set_status(status, kStInternal);
-    else atomicOr(&out[wcur], __byte_perm((uint32_t)(acc >> 32), 0, 0x0123));
+    if (nacc > 0) atomicOr(&out[wcur], __byte_perm((uint32_t)(acc >> 32), 0, 0x0123));
   }
 };
 
@@ -780,7 +763,7 @@ struct BlockHdr {
 // WRITE = false returns the segment's bit length; WRITE = true writes its
 // tokens from absolute bit position `pos`.
 template <bool WRITE>
-__device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct, const StreamSpan& sp, int64_t pos) {
+__device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct, uint32_t* out, int64_t pos) {
   const int lane = threadIdx.x & 31;
   uint32_t carry = kAllZero;
   uint64_t total = 0;
@@ -823,7 +806,7 @@ __device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct,
     const uint32_t chunk_bits = __shfl_sync(0xffffffffu, x, 31);
     if (WRITE && bits) {
       LaneWriter W;
-      W.begin(sp, pos + (int64_t)total + (x - bits));
+      W.begin(out, pos + (int64_t)total + (x - bits));
       if (lead) put_run(ct, W, lead);
       int prev = __ffs(NZ) - 1;
       for (uint32_t m = NZ; m; m &= m - 1u) {
@@ -928,7 +911,7 @@ __device__ void enc_size_group(const int64_t* perm, int64_t g0, int ng, const Bl
     const int n = b.w * b.h / 8;
     const CodeTab ct{G.code[j], G.len[j], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
     const uint32_t km = kept_types(bc.removed, b.p, pl);
-    const uint64_t bits = warp_segment<false>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, StreamSpan{}, 0);
+    const uint64_t bits = warp_segment<false>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, nullptr, 0);
     if (lane == 0) hdrs[bi].seglen[pl] = (uint32_t)bits;
   }
 }
@@ -982,7 +965,7 @@ __device__ inline int64_t needed_capacity(int64_t total) { return (total + 3) & 
 template <class Sync>
 __device__ void enc_emit_group(const int64_t* perm, int64_t g0, int ng, const TileDev* __restrict__ tiles,
                                const BlockDev* __restrict__ blocks, const uint8_t* sym, const BlockCode* __restrict__ codes,
-                               const BlockHdr* __restrict__ hdrs, const int64_t* __restrict__ final_pos, const StreamSpan& sp,
+                               const BlockHdr* __restrict__ hdrs, const int64_t* __restrict__ final_pos, uint32_t* __restrict__ out,
                                uint8_t* dyn, int* s_nitem, int tid, int nthr, Sync sync) {
   EncGroup G;
   load_group(perm, g0, ng, blocks, codes, dyn, G, s_nitem, tid, nthr, sync);
@@ -996,7 +979,7 @@ __device__ void enc_emit_group(const int64_t* perm, int64_t g0, int ng, const Ti
     const int64_t B0 = block_bit_start(tiles[b.tile], final_pos, bi);
     if (lane == 0) {
       LaneWriter W;
-      W.begin(sp, B0);
+      W.begin(out, B0);
       W.put((uint32_t)d, 5);
       for (int ty = 0; ty < p; ++ty)
         for (int pl = 0; pl < d; ++pl) W.put((bc.removed[ty] >> pl) & 1u, 1);
@@ -1012,7 +995,7 @@ __device__ void enc_emit_group(const int64_t* perm, int64_t g0, int ng, const Ti
     const int64_t seek = B0 + 5 + (int64_t)p * d + 18;
     if (lane < d) {
       LaneWriter W;
-      W.begin(sp, seek + (int64_t)lane * t);
+      W.begin(out, seek + (int64_t)lane * t);
       W.put(H.seglen[lane], t);
       W.end();
     }
@@ -1020,7 +1003,7 @@ __device__ void enc_emit_group(const int64_t* perm, int64_t g0, int ng, const Ti
     for (int k = lane; k * 32 < bc.tree_bits; k += 32) {
       const int nbk = min(32, bc.tree_bits - 32 * k);
       LaneWriter W;
-      W.begin(sp, tree_pos + 32 * k);
+      W.begin(out, tree_pos + 32 * k);
       W.put(bc.tree[k] >> (32 - nbk), nbk);
       W.end();
     }
@@ -1036,7 +1019,7 @@ __device__ void enc_emit_group(const int64_t* perm, int64_t g0, int ng, const Ti
     int64_t pos = block_bit_start(tiles[b.tile], final_pos, bi) + H.hdr_bits;
     for (int q = 0; q < pl; ++q) pos += H.seglen[q];
     const uint32_t km = kept_types(bc.removed, b.p, pl);
-    warp_segment<true>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, sp, pos);
+    warp_segment<true>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, out, pos);
   }
 }
 

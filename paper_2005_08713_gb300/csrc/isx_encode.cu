@@ -70,13 +70,13 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_enc_emit(const TileDev* __r
                                                              const int64_t* __restrict__ perm, int64_t nb, const uint8_t* sym,
                                                              const BlockCode* __restrict__ codes, const BlockHdr* __restrict__ hdrs,
                                                              const int64_t* __restrict__ final_pos, const int64_t* __restrict__ totals,
-                                                             int64_t out_cap, uint32_t* __restrict__ out, int* __restrict__ status) {
+                                                             int64_t out_cap, uint32_t* __restrict__ out) {
   extern __shared__ __align__(16) uint8_t dyn[];
   __shared__ int s_nitem;
   if (needed_capacity(totals[0]) > out_cap) return;
   const int64_t g0 = (int64_t)blockIdx.x * kEncGroup;
-  enc_emit_group(perm, g0, (int)min((int64_t)kEncGroup, nb - g0), tiles, blocks, sym, codes, hdrs, final_pos,
-                 StreamSpan{out, 0, out_cap >> 2, status}, dyn, &s_nitem, threadIdx.x, blockDim.x, CtaBarrier());
+  enc_emit_group(perm, g0, (int)min((int64_t)kEncGroup, nb - g0), tiles, blocks, sym, codes, hdrs, final_pos, out, dyn, &s_nitem,
+                 threadIdx.x, blockDim.x, CtaBarrier());
 }
 
 // Tile headers and the stream offsets; capacity check.
@@ -142,7 +142,7 @@ int launch_encode_coding(const EncodeBuffers& eb, cudaStream_t s, StageMarks* T)
   k_zero_stream<<<152 * 8, 256, 0, s>>>(reinterpret_cast<uint32_t*>(eb.out), eb.totals, eb.out_capacity);
   T->mark("encode.emit", s);
   k_enc_emit<<<gg, 32 * kEmitWarps, kEncSmem, s>>>(eb.tiles, eb.blocks, eb.perm, eb.n_blocks, eb.sym, eb.codes, hdrs, eb.final_pos,
-                                                   eb.totals, eb.out_capacity, reinterpret_cast<uint32_t*>(eb.out), eb.status);
+                                                   eb.totals, eb.out_capacity, reinterpret_cast<uint32_t*>(eb.out));
   T->mark("encode.tile_headers", s);
   k_tile_headers<<<eb.n_tiles, 128, 0, s>>>(eb.tiles, eb.n_tiles, eb.final_pos, eb.item_size, eb.totals, eb.out, eb.out_capacity,
                                             eb.tile_offsets, eb.status);
