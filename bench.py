@@ -146,7 +146,6 @@ NCU_TRAFFIC = {
     "encode.transform": ("k_fwd_tile_smem", ('isx_transform.cu', 'isx_fused.cuh', 'isx_warp_levels.cuh', 'isx_internal.cuh'), "15c9bb857e89288c", 8.180),
     "encode.symbols": ("k_enc_symbols", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "f0d2e8f086dc9406", 7.290),
     "encode.huffman": ("k_block_huffman", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "f0d2e8f086dc9406", 0.510),
-    "encode.size": ("k_enc_size", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "f0d2e8f086dc9406", 2.350),
     "encode.emit": ("k_enc_emit", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "f0d2e8f086dc9406", 3.820),
     "decode.tables": ("k_dec_tables", ('isx_decode.cu', 'isx_coder_dec.cuh', 'isx_internal.cuh'), "f2633d995948ab63", 0.420),
     "decode.segments": ("k_dec_segments", ('isx_decode.cu', 'isx_coder_dec.cuh', 'isx_internal.cuh'), "f2633d995948ab63", 2.430),
@@ -158,7 +157,7 @@ NCU_TRAFFIC = {
 # for the issue-rate co-roofline: the codec is integer work, and its kernels are bound by latency and
 # instruction issue long before DRAM bandwidth.
 NCU_WARP_INST_PER_PX = {
-    "encode.transform": 6.150, "encode.symbols": 4.800, "encode.huffman": 5.780, "encode.size": 2.810, "encode.emit": 7.560, "decode.tables": 1.330, "decode.segments": 8.920, "decode.inverse_transform": 7.260,
+    "encode.transform": 6.150, "encode.symbols": 4.800, "encode.huffman": 5.780, "encode.emit": 7.560, "decode.tables": 1.330, "decode.segments": 8.920, "decode.inverse_transform": 7.260,
 }
 
 
@@ -427,9 +426,12 @@ def run_gpu(args):
     # sym_bytes = symbols of every kept (plane, type) of every block, one byte each
     algo = {
         "encode.transform": 3 * px + 2 * coef_elems,                    # RGB8 in, int16 area-ordered blocks out
-        "encode.symbols": 2 * coef_elems + sym_bytes + 1200 * n_blocks,  # blocks in, kept symbols + statistics out
-        "encode.huffman": (1200 + 1700) * n_blocks,                      # statistics in, code tables out
-        "encode.size": sym_bytes + 1700 * n_blocks,
+        # statistics per block: 1.1 KB of block totals, plus per kept plane 560 B (a plane of more than
+        # 512 symbols: its histogram) or 48 B (a shorter one, whose symbols the layout pass reads instead);
+        # about 2 KB per block on this workload
+        "encode.symbols": 2 * coef_elems + sym_bytes + 3100 * n_blocks,  # blocks in, kept symbols + statistics out
+        "encode.huffman": (1200 + 1700) * n_blocks,                      # block statistics in, code tables out
+        "encode.layout": 2300 * n_blocks,                                # plane statistics + code lengths in, layout out
         "encode.emit": sym_bytes + 1700 * n_blocks + total_bytes,        # symbols + codes in, stream out
         "decode.tables": 600 * n_blocks,                                 # block headers in (<= 600 B), tables out
         "decode.segments": total_bytes + sym_bytes,                      # stream in, kept symbols out

@@ -44,8 +44,9 @@ typedef enum {
   ISX_ERR_OOM = 4,       /* scratch would exceed the context's HBM budget, or cudaMalloc failed */
   ISX_ERR_CUDA = 5,      /* a CUDA runtime call failed */
   ISX_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
-  ISX_ERR_INTERNAL = 7   /* an internal consistency check failed (the encoder's exact segment sizes disagree
-                            with the token bits its Huffman pass counted) */
+  ISX_ERR_INTERNAL = 7   /* an internal consistency check failed: the encoder's plane segment sizes disagree
+                            with the bits its Huffman pass counted or with the segments' symbols (the stream
+                            is then invalid; nothing was written outside the output buffer) */
 } isx_status;
 
 /* Colour transform of a tile (the paper's "optional colorspace

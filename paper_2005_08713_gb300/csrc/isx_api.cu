@@ -233,14 +233,14 @@ void group_fused(const std::vector<FusedTask>& fused, const int* threads, int32_
 // ------------------------------------------------------------ encode
 struct EncodeLayout {
   int32_t n_tiles = 0;
-  int64_t n_blocks = 0, coef_bytes = 0, plane_total = 0, sym_bytes = 0;
+  int64_t n_blocks = 0, coef_bytes = 0, plane_total = 0, sym_bytes = 0, pst_slots = 0;
   int max_levels = 0, max_dim = 1, max_c = 1, n_fused = 0;
   FusedClass cls[ISX_SIZE_CLASSES];
   int64_t level_blocks[16] = {};
   int level_quads[16] = {};
   uint64_t* stamps = nullptr;
   int32_t stamp_n = 0;
-  size_t o_tiles = 0, o_task = 0, o_blocks = 0, o_A = 0, o_B = 0, o_coef = 0, o_sym = 0, o_stats = 0, o_codes = 0, o_hdrs = 0;
+  size_t o_tiles = 0, o_task = 0, o_blocks = 0, o_A = 0, o_B = 0, o_coef = 0, o_sym = 0, o_stats = 0, o_pst = 0, o_codes = 0, o_hdrs = 0;
   size_t o_is = 0, o_fp = 0, o_perm = 0, o_bucket = 0, o_part = 0, o_tot = 0, total = 0;
 };
 
@@ -282,6 +282,8 @@ isx_status plan_encode(const isx_tile_desc* tiles, int32_t n, bool allow_fused, 
     if (d.fused) fused.push_back({i, fused_plane_bytes(t.width, t.height), t.channels});
     else E.plane_total += (int64_t)t.channels * t.width * t.height;
     d.sym_base = E.sym_bytes;
+    d.pst_base = E.pst_slots;
+    E.pst_slots += nb * dmax_of_bits(t.bits);
     E.n_blocks += nb;
     E.coef_bytes += nc * (d.coef16 ? 2 : 4);
     E.max_c = std::max(E.max_c, t.channels);
@@ -302,6 +304,7 @@ isx_status plan_encode(const isx_tile_desc* tiles, int32_t n, bool allow_fused, 
   E.o_coef = cv.take((size_t)E.coef_bytes);
   E.o_sym = cv.take((size_t)E.sym_bytes);
   E.o_stats = cv.take(sizeof(BlockStats) * NB);
+  E.o_pst = cv.take(sizeof(PlaneStats) * (size_t)E.pst_slots);
   E.o_codes = cv.take(sizeof(BlockCode) * NB);
   E.o_hdrs = cv.take(enc_hdr_bytes() * NB);
   E.o_is = cv.take(8 * NB);
@@ -343,6 +346,7 @@ int launch_encode(const EncodeLayout& E, uint8_t* base, void* d_out, size_t out_
   eb.tiles = d_tiles; eb.n_tiles = E.n_tiles; eb.blocks = d_blocks; eb.n_blocks = E.n_blocks; eb.coef = coef;
   eb.sym = base + E.o_sym;
   eb.stats = (BlockStats*)(base + E.o_stats);
+  eb.pst = (PlaneStats*)(base + E.o_pst);
   eb.codes = (BlockCode*)(base + E.o_codes);
   eb.hdrs = base + E.o_hdrs;
   eb.item_size = (int64_t*)(base + E.o_is); eb.final_pos = (int64_t*)(base + E.o_fp);
@@ -769,7 +773,10 @@ isx_status status_of(isx_ctx* ctx, std::string* err, int st) {
     case kStCorrupt: *err = "malformed compressed stream"; return ISX_ERR_CORRUPT;
     case kStTimeout: *err = "device wait gave up"; return ISX_ERR_TIMEOUT;
     case kStRange: *err = "a sample exceeds its tile's bit depth (values must be below 2^bits)"; return ISX_ERR_ARG;
-    default: *err = "internal consistency check failed on the device (code " + std::to_string(st) + ")"; return ISX_ERR_CUDA;
+    case kStInternal:
+      *err = "internal consistency check failed on the device (the encoder's segment sizes disagree with its symbols)";
+      return ISX_ERR_INTERNAL;
+    default: *err = "unknown device status " + std::to_string(st); return ISX_ERR_INTERNAL;
   }
   (void)ctx;
 }

@@ -98,24 +98,43 @@ __device__ inline uint32_t nonzero_mask(const LaneSyms& L) {
 }
 
 // ------------------------------------------------------------- pass 1
-__device__ inline void record_run(uint32_t L, uint32_t* s_hist, uint32_t* s_runs, uint32_t* s_extra) {
+// Plane histograms in shared memory hold two 16-bit counts per word: symbol
+// s in the half (s & 1) of word s >> 1, the little-endian layout of
+// PlaneStats::hist.
+__device__ inline void count_symbol(uint32_t* ph, uint32_t s) { atomicAdd(&ph[s >> 1], 1u << ((s & 1u) << 4)); }
+
+__device__ inline void record_run(uint32_t L, uint32_t* zeros, uint32_t* runs, uint32_t* extra) {
   if (L == 1) {
-    atomicAdd(&s_hist[0], 1u);   // an isolated zero is the literal symbol 0
+    atomicAdd(zeros, 1u);   // an isolated zero is the literal symbol 0
     return;
   }
-  atomicAdd(s_runs, 1u);
+  atomicAdd(runs, 1u);
   for (int w = 2; w <= kMaxW; ++w) {
     const uint32_t M = (1u << w) - 1u;
     if (M >= L) break;
-    atomicAdd(&s_extra[w], (L + M - 1) / M - 1);
+    atomicAdd(&extra[w], (L + M - 1) / M - 1);
   }
 }
 
-// Shared memory of one block's symbol pass.
+// Every kept plane segment gets its zero-run statistics (PlaneStats: runs,
+// extra[w], isolated zeros).  A segment of more than kRawMax symbols also
+// gets its literal histogram, from which the Huffman pass finds its length;
+// for a shorter one that pass sums the literal costs over its symbols (at
+// most one 16-byte word per lane).
+constexpr int kRawMax = 512;
+__device__ inline bool plane_has_hist(uint32_t km, int n) { return __popc(km) * n > kRawMax; }
+
+// Shared memory of one block's symbol pass: the literal histograms of the
+// plane segments with one (kPlanes: slot pl for plane pl; one warp fills a
+// plane's at a time), one slot, kRest, that every other segment adds to
+// (the block's histogram is the sum over all slots), and every plane's
+// zero-run statistics.
+template <bool kPlanes>
 struct SymShared {
-  uint32_t hist[256];
-  uint32_t extra[kMaxW + 1];
-  uint32_t runs;
+  static constexpr int kRest = kPlanes ? kMaxD : 0;
+  uint32_t ph[kRest + 1][128];
+  uint32_t pextra[kMaxD][kMaxW + 1];
+  uint32_t pruns[kMaxD], pzero[kMaxD];
   uint32_t orv[3], neg[3];
   uint32_t km[32];
   int64_t poff[32];
@@ -124,21 +143,23 @@ struct SymShared {
 // Symbol pass of block bi by threads tid = 0 .. nthr-1 (whole warps; sync()
 // synchronises exactly them): bit depth d, removed planes, the kept
 // symbols written once to the block's symbol region, then its histogram and
-// zero runs (BlockStats).
-template <class Sync>
+// zero runs (BlockStats) and those of every kept plane segment (PlaneStats;
+// the histogram part only for segments of more than kRawMax symbols, which
+// need kPlanes).
+template <bool kPlanes, class Sync>
 __device__ inline void enc_symbols_block(int64_t bi, const BlockDev* __restrict__ blocks, const uint8_t* __restrict__ coef,
-                                         uint8_t* __restrict__ sym, BlockStats* __restrict__ stats, int* __restrict__ status,
-                                         SymShared& SH, int tid, int nthr, Sync sync) {
+                                         uint8_t* __restrict__ sym, BlockStats* __restrict__ stats, PlaneStats* __restrict__ pst,
+                                         int* __restrict__ status, SymShared<kPlanes>& SH, int tid, int nthr, Sync sync) {
+  constexpr int kRest = SymShared<kPlanes>::kRest;
+  // a launch without plane statistics must only meet blocks that need none
+  if (!kPlanes && tid == 0 && blocks[bi].p * (blocks[bi].w * blocks[bi].h / 8) > kRawMax) set_status(status, kStInternal);
   const BlockDev b = blocks[bi];
   const int n = b.w * b.h / 8, na = b.p * n;
   AreaMap am;
   am.init(b.w, b.h);
   const CoefRef cf{coef + b.coef, b.coef16};
   const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
-  for (int i = tid; i < 256; i += nthr) SH.hist[i] = 0;
-  if (tid <= kMaxW) SH.extra[tid] = 0;
   if (tid < 3) { SH.orv[tid] = 0; SH.neg[tid] = 0; }
-  if (tid == 0) SH.runs = 0;
   sync();
   // int16 blocks whose type rows hold a multiple of 4 areas go 4 consecutive areas (64 bytes) per thread
   const bool quads = b.coef16 && (n & 3) == 0;
@@ -230,6 +251,14 @@ __device__ inline void enc_symbols_block(int64_t bi, const BlockDev* __restrict_
       n_sym += (uint32_t)__popc(km) * n;
     }
   }
+  // slots 0 .. d-1 (kPlanes) and kRest
+  const int nslot = kPlanes ? d + 1 : 1;
+  for (int i = tid; i < nslot * 128; i += nthr) {
+    const int k = i >> 7;
+    SH.ph[k == nslot - 1 ? kRest : k][i & 127] = 0;
+  }
+  for (int i = tid; i < d * (kMaxW + 1); i += nthr) SH.pextra[i / (kMaxW + 1)][i % (kMaxW + 1)] = 0;
+  if (tid < d) { SH.pruns[tid] = 0; SH.pzero[tid] = 0; }
   sync();
   // symbols of every kept (plane, type), written once
   uint8_t* S = sym + b.sym;
@@ -326,6 +355,10 @@ __device__ inline void enc_symbols_block(int64_t bi, const BlockDev* __restrict_
     if (!km) continue;
     const int len = __popc(km) * n;
     const uint8_t* seg = S + SH.poff[pl];
+    uint32_t* ph = SH.ph[kPlanes && plane_has_hist(km, n) ? pl : kRest];
+    uint32_t* pextra = SH.pextra[pl];
+    uint32_t* pruns = &SH.pruns[pl];
+    uint32_t* pzero = &SH.pzero[pl];
     uint32_t carry = kAllZero;
     for (int base = 0; base < len; base += 512) {
       const LaneSyms L = load_lane(seg, len, base);
@@ -334,7 +367,7 @@ __device__ inline void enc_symbols_block(int64_t bi, const BlockDev* __restrict_
       const bool seen = NZ != 0;
       uint32_t lz = 0, zeros = 0;
       if (seen) {
-        for (uint32_t m = NZ; m; m &= m - 1u) atomicAdd(&SH.hist[L.at(__ffs(m) - 1)], 1u);
+        for (uint32_t m = NZ; m; m &= m - 1u) count_symbol(ph, L.at(__ffs(m) - 1));
         const int first = __ffs(NZ) - 1, last = 31 - __clz(NZ);
         lz = (uint32_t)first;
         zeros = (uint32_t)(L.cnt - 1 - last);
@@ -342,25 +375,64 @@ __device__ inline void enc_symbols_block(int64_t bi, const BlockDev* __restrict_
         const uint32_t Zi = Z & ((last >= 31 ? 0xffffffffu : (2u << last) - 1u) & ~((2u << first) - 1u));
         for (uint32_t st = Zi & ~(Zi << 1); st; st &= st - 1u) {
           const int s0 = __ffs(st) - 1;
-          record_run((uint32_t)(__ffs(~(Zi >> s0)) - 1), SH.hist, &SH.runs, SH.extra);
+          record_run((uint32_t)(__ffs(~(Zi >> s0)) - 1), pzero, pruns, pextra);
         }
       }
       const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
       uint32_t incl, tot;
       const uint32_t ex = warp_carry_exclusive(elem, &incl, &tot);
       const uint32_t cin = carry_combine(carry, ex) & ~kAllZero;
-      if (seen && cin + lz > 0) record_run(cin + lz, SH.hist, &SH.runs, SH.extra);
+      if (seen && cin + lz > 0) record_run(cin + lz, pzero, pruns, pextra);
       carry = carry_combine(carry, tot);
     }
     const uint32_t fin = carry & ~kAllZero;
-    if (lane == 0 && fin) record_run(fin, SH.hist, &SH.runs, SH.extra);
+    if (lane == 0 && fin) record_run(fin, pzero, pruns, pextra);
   }
   sync();
+  // the plane statistics (35 16-byte words; without a histogram only the
+  // last 3), then the block's totals
+  uint4* dst = reinterpret_cast<uint4*>(pst + b.pst);
+  const int per = kPlanes ? 35 : 3;
+  for (int i = tid; i < d * per; i += nthr) {
+    const int pl = i / per, q = i - pl * per + (35 - per);
+    const uint32_t km = SH.km[pl];
+    if (!km || (q < 32 && !plane_has_hist(km, n))) continue;
+    uint4 v;
+    if (q < 32) {
+      v = *reinterpret_cast<const uint4*>(&SH.ph[pl][4 * q]);
+      if (q == 0) v.x |= SH.pzero[pl];   // symbol 0: the isolated zeros
+    } else {
+      // 16-bit extra[0..18], runs, isolated zeros, then zero padding:
+      // halves 8 (q - 32) .. 8 (q - 32) + 7 of the 24 in words 32..34
+      uint32_t h[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e0 = 8 * (q - 32) + 2 * k, e1 = e0 + 1;
+        const uint32_t lo = e0 <= kMaxW ? SH.pextra[pl][e0] : (e0 == kMaxW + 1 ? SH.pruns[pl] : (e0 == kMaxW + 2 ? SH.pzero[pl] : 0u));
+        const uint32_t hi = e1 <= kMaxW ? SH.pextra[pl][e1] : (e1 == kMaxW + 1 ? SH.pruns[pl] : (e1 == kMaxW + 2 ? SH.pzero[pl] : 0u));
+        h[k] = lo | (hi << 16);
+      }
+      v = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+    dst[(int64_t)pl * 35 + q] = v;
+  }
   BlockStats* st = stats + bi;
-  for (int i = tid; i < 256; i += nthr) st->hist[i] = SH.hist[i];
-  if (tid <= kMaxW) st->extra[tid] = SH.extra[tid];
+  for (int i = tid; i < 256; i += nthr) {
+    uint32_t c = (SH.ph[kRest][i >> 1] >> ((i & 1) << 4)) & 0xffffu;
+    for (int pl = 0; kPlanes && pl < d; ++pl) c += (SH.ph[pl][i >> 1] >> ((i & 1) << 4)) & 0xffffu;
+    if (i == 0)
+      for (int pl = 0; pl < d; ++pl) c += SH.pzero[pl];
+    st->hist[i] = c;
+  }
+  if (tid <= kMaxW) {
+    uint32_t c = 0;
+    for (int pl = 0; pl < d; ++pl) c += SH.pextra[pl][tid];
+    st->extra[tid] = c;
+  }
   if (tid == 0) {
-    st->n_runs = SH.runs;
+    uint32_t r = 0;
+    for (int pl = 0; pl < d; ++pl) r += SH.pruns[pl];
+    st->n_runs = r;
     st->n_sym = n_sym;
     st->removed[0] = removed[0]; st->removed[1] = removed[1]; st->removed[2] = removed[2];
     st->d = d;
@@ -368,7 +440,169 @@ __device__ inline void enc_symbols_block(int64_t bi, const BlockDev* __restrict_
 }
 
 
+// ------------------------------------------------- token costs and writer
+struct CodeTab {
+  const uint32_t* code;
+  const uint8_t* len;
+  int czr, wbits;
+  uint32_t M;
+};
+
+__device__ inline uint32_t run_bits(const CodeTab& ct, uint32_t L) {
+  if (L == 1) return ct.len[0];
+  if (ct.M == 0) return 0;
+  return ((L + ct.M - 1) / ct.M) * (uint32_t)(ct.len[ct.czr] + ct.wbits);
+}
+__device__ inline uint32_t lit_bits(const CodeTab& ct, uint32_t s) {
+  return ct.len[s] + ((int)s == ct.czr ? ct.wbits : 0);
+}
+
+// MSB-first writer of one lane's contiguous bit range straight into the
+// stream (32-bit words, big endian).  Words strictly inside the range are
+// stored; the first and last (shared with neighbouring ranges) are OR-ed
+// into the zero-initialised stream.
+struct LaneWriter {
+  uint32_t* out;
+  int64_t w0, wcur;
+  uint64_t acc;
+  int nacc;
+  __device__ void begin(uint32_t* o, int64_t bitpos) {
+    out = o;
+    wcur = w0 = bitpos >> 5;
+    acc = 0;
+    nacc = (int)(bitpos & 31);
+  }
+  __device__ void word(uint32_t x) {
+    const uint32_t be = __byte_perm(x, 0, 0x0123);
+    if (wcur == w0) atomicOr(&out[wcur], be);
+    else out[wcur] = be;
+    ++wcur;
+  }
+  __device__ void put(uint32_t v, int nb) {   // nb <= 32
+    if (nb <= 0) return;
+    const uint64_t x = (uint64_t)(nb == 32 ? v : (v & ((1u << nb) - 1u)));
+    acc |= x << (64 - nacc - nb);
+    nacc += nb;
+    if (nacc >= 32) {
+      word((uint32_t)(acc >> 32));
+      acc <<= 32;
+      nacc -= 32;
+    }
+  }
+  __device__ void end() {
+    if (nacc > 0) atomicOr(&out[wcur], __byte_perm((uint32_t)(acc >> 32), 0, 0x0123));
+  }
+};
+
+__device__ inline void put_run(const CodeTab& ct, LaneWriter& W, uint32_t L) {
+  if (L == 1) {
+    W.put(ct.code[0], ct.len[0]);
+    return;
+  }
+  if (ct.M == 0) return;   // counter width is always >= 2
+  const int lc = ct.len[ct.czr];
+  const uint32_t cz = ct.code[ct.czr];
+  while (L > 0) {
+    const uint32_t k = L >= ct.M ? ct.M : L;
+    W.put(cz, lc);
+    W.put(k, ct.wbits);
+    L -= k;
+  }
+}
+
+__device__ inline void put_literal(const CodeTab& ct, LaneWriter& W, uint32_t s) {
+  W.put(ct.code[s], ct.len[s]);
+  if ((int)s == ct.czr) W.put(0, ct.wbits);   // counter 0: a literal C_zr
+}
+
+// One warp walks plane segment `seg` (len symbols) in chunks of 512,
+// writes its tokens from absolute bit position `pos` and returns its bit
+// length.  A chunk that would end beyond `limit` bits (the length the
+// statistics gave) is not written: the walk stops there and returns more
+// than `limit`, so nothing is written outside the segment's span.
+__device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct, uint32_t* out, int64_t pos, uint64_t limit) {
+  const int lane = threadIdx.x & 31;
+  uint32_t carry = kAllZero;
+  uint64_t total = 0;
+  for (int base = 0; base < len; base += 512) {
+    const LaneSyms L = load_lane(seg, len, base);
+    // nonzero symbols of the lane as a bit mask: the loops visit only those;
+    // the zeros between two of them form one run
+    const uint32_t NZ = nonzero_mask(L);
+    const bool seen = NZ != 0;
+    uint32_t zeros = 0, lz = 0, bits = 0;
+    if (seen) {
+      const int first = __ffs(NZ) - 1, last = 31 - __clz(NZ);
+      lz = (uint32_t)first;
+      zeros = (uint32_t)(L.cnt - 1 - last);
+      int prev = first;
+      for (uint32_t m = NZ; m; m &= m - 1u) {
+        const int k = __ffs(m) - 1;
+        if (k - prev > 1) bits += run_bits(ct, (uint32_t)(k - prev - 1));
+        bits += lit_bits(ct, L.at(k));
+        prev = k;
+      }
+    }
+    const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
+    uint32_t incl, tot;
+    const uint32_t ex = warp_carry_exclusive(elem, &incl, &tot);
+    const uint32_t cin = carry_combine(carry, ex) & ~kAllZero;
+    const uint32_t lead = seen ? cin + lz : 0;
+    if (lead) bits += run_bits(ct, lead);
+    // the lane holding the segment's last symbol closes the final run
+    const bool last_lane = base + 512 >= len && lane == (len - 1 - base) / 16;
+    const uint32_t fin = last_lane ? (carry_combine(carry, incl) & ~kAllZero) : 0;
+    if (fin) bits += run_bits(ct, fin);
+    // bit offsets of the lanes within the chunk
+    uint32_t x = bits;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const uint32_t chunk_bits = __shfl_sync(0xffffffffu, x, 31);
+    if (total + chunk_bits > limit) return total + chunk_bits;   // warp-uniform
+    if (bits) {
+      LaneWriter W;
+      W.begin(out, pos + (int64_t)total + (x - bits));
+      if (lead) put_run(ct, W, lead);
+      int prev = __ffs(NZ) - 1;
+      for (uint32_t m = NZ; m; m &= m - 1u) {
+        const int k = __ffs(m) - 1;
+        if (k - prev > 1) put_run(ct, W, (uint32_t)(k - prev - 1));
+        put_literal(ct, W, L.at(k));
+        prev = k;
+      }
+      if (fin) put_run(ct, W, fin);
+      W.end();
+    }
+    total += chunk_bits;
+    carry = carry_combine(carry, tot);
+  }
+  return total;
+}
+
+// Symbol offset of plane pl inside a block's region.
+__device__ inline int64_t plane_offset(const uint32_t* removed, int p, int n, int pl) {
+  int64_t off = 0;
+  for (int q = 0; q < pl; ++q) {
+    const uint32_t km = kept_types(removed, p, q);
+    if (km) off += region16(km, n);
+  }
+  return off;
+}
+
+
 // ------------------------------------------------------------- pass 2
+// Per-block layout: seektable width t, header bits and the exact bit length
+// of every plane segment (0 for a removed plane), found by the Huffman pass
+// from the plane statistics.
+struct BlockHdr {
+  int32_t t, pad;
+  int64_t hdr_bits;
+  uint32_t seglen[32];
+};
+
 // Two-queue Huffman construction (one warp per block): leaves with f > 0
 // sorted ascending by (f, symbol) (warp bitonic sort in registers); each
 // merge takes the lighter queue front twice, the leaf queue first on equal
@@ -676,153 +910,121 @@ __device__ inline void block_huffman(int64_t bi, const BlockDev* __restrict__ bl
   }
 }
 
-
-// ------------------------------------------------------------- pass 3/4
-struct CodeTab {
-  const uint32_t* code;
-  const uint8_t* len;
-  int czr, wbits;
-  uint32_t M;
-};
-
-__device__ inline uint32_t run_bits(const CodeTab& ct, uint32_t L) {
-  if (L == 1) return ct.len[0];
-  if (ct.M == 0) return 0;
-  return ((L + ct.M - 1) / ct.M) * (uint32_t)(ct.len[ct.czr] + ct.wbits);
-}
-__device__ inline uint32_t lit_bits(const CodeTab& ct, uint32_t s) {
-  return ct.len[s] + ((int)s == ct.czr ? ct.wbits : 0);
-}
-
-// MSB-first writer of one lane's contiguous bit range straight into the
-// stream (32-bit words, big endian).  Words strictly inside the range are
-// stored; the first and last (shared with neighbouring ranges) are OR-ed
-// into the zero-initialised stream.
-struct LaneWriter {
-  uint32_t* out;
-  int64_t w0, wcur;
-  uint64_t acc;
-  int nacc;
-  __device__ void begin(uint32_t* o, int64_t bitpos) {
-    out = o;
-    wcur = w0 = bitpos >> 5;
-    acc = 0;
-    nacc = (int)(bitpos & 31);
-  }
-  __device__ void word(uint32_t x) {
-    const uint32_t be = __byte_perm(x, 0, 0x0123);
-    if (wcur == w0) atomicOr(&out[wcur], be);
-    else out[wcur] = be;
-    ++wcur;
-  }
-  __device__ void put(uint32_t v, int nb) {   // nb <= 32
-    if (nb <= 0) return;
-    const uint64_t x = (uint64_t)(nb == 32 ? v : (v & ((1u << nb) - 1u)));
-    acc |= x << (64 - nacc - nb);
-    nacc += nb;
-    if (nacc >= 32) {
-      word((uint32_t)(acc >> 32));
-      acc <<= 32;
-      nacc -= 32;
+// Layout of block bi by one warp (pass 2b): the exact bit length of every
+// plane segment, the seektable width t, the header bits and the block's
+// bytes in the stream (item_size; a tile's first block also carries the
+// tile header).  s_len: 256 bytes of shared memory for the warp.
+__device__ inline void enc_block_layout(int64_t bi, const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
+                                        const PlaneStats* __restrict__ pst, const uint8_t* __restrict__ sym,
+                                        const BlockCode* __restrict__ codes, BlockHdr* __restrict__ hdrs,
+                                        int64_t* __restrict__ item_size, int* __restrict__ status, uint8_t* s_len) {
+  const int lane = threadIdx.x & 31;
+  const BlockDev b = blocks[bi];
+  const BlockCode& bc = codes[bi];
+  BlockHdr& BH = hdrs[bi];
+  const int d = bc.d, p = b.p;
+  const TileDev& tile = tiles[b.tile];
+  const int64_t extra_bytes = bi == tile.block_base ? 32 + 4 * (int64_t)tile.nb : 0;
+  if (!bc.any_kept) {
+    if (lane == 0) {
+      BH.t = 0;
+      BH.hdr_bits = 5 + (int64_t)p * d;
+      item_size[bi] = (5 + (int64_t)p * d + 7) / 8 + extra_bytes;
     }
-  }
-  __device__ void end() {
-    if (nacc > 0) atomicOr(&out[wcur], __byte_perm((uint32_t)(acc >> 32), 0, 0x0123));
-  }
-};
-
-__device__ inline void put_run(const CodeTab& ct, LaneWriter& W, uint32_t L) {
-  if (L == 1) {
-    W.put(ct.code[0], ct.len[0]);
     return;
   }
-  if (ct.M == 0) return;   // counter width is always >= 2
-  const int lc = ct.len[ct.czr];
-  const uint32_t cz = ct.code[ct.czr];
-  while (L > 0) {
-    const uint32_t k = L >= ct.M ? ct.M : L;
-    W.put(cz, lc);
-    W.put(k, ct.wbits);
-    L -= k;
-  }
-}
-
-__device__ inline void put_literal(const CodeTab& ct, LaneWriter& W, uint32_t s) {
-  W.put(ct.code[s], ct.len[s]);
-  if ((int)s == ct.czr) W.put(0, ct.wbits);   // counter 0: a literal C_zr
-}
-
-// Per-block layout found by the size pass.
-struct BlockHdr {
-  int32_t t, pad;
-  int64_t hdr_bits;
-  uint32_t seglen[32];
-};
-
-// One warp walks plane segment `seg` (len symbols) in chunks of 512:
-// WRITE = false returns the segment's bit length; WRITE = true writes its
-// tokens from absolute bit position `pos`.
-template <bool WRITE>
-__device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct, uint32_t* out, int64_t pos) {
-  const int lane = threadIdx.x & 31;
-  uint32_t carry = kAllZero;
-  uint64_t total = 0;
-  for (int base = 0; base < len; base += 512) {
-    const LaneSyms L = load_lane(seg, len, base);
-    // nonzero symbols of the lane as a bit mask: the loops visit only those;
-    // the zeros between two of them form one run
-    const uint32_t NZ = nonzero_mask(L);
-    const bool seen = NZ != 0;
-    uint32_t zeros = 0, lz = 0, bits = 0;
-    if (seen) {
-      const int first = __ffs(NZ) - 1, last = 31 - __clz(NZ);
-      lz = (uint32_t)first;
-      zeros = (uint32_t)(L.cnt - 1 - last);
-      int prev = first;
-      for (uint32_t m = NZ; m; m &= m - 1u) {
-        const int k = __ffs(m) - 1;
-        if (k - prev > 1) bits += run_bits(ct, (uint32_t)(k - prev - 1));
-        bits += lit_bits(ct, L.at(k));
-        prev = k;
-      }
-    }
-    const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
-    uint32_t incl, tot;
-    const uint32_t ex = warp_carry_exclusive(elem, &incl, &tot);
-    const uint32_t cin = carry_combine(carry, ex) & ~kAllZero;
-    const uint32_t lead = seen ? cin + lz : 0;
-    if (lead) bits += run_bits(ct, lead);
-    // the lane holding the segment's last symbol closes the final run
-    const bool last_lane = base + 512 >= len && lane == (len - 1 - base) / 16;
-    const uint32_t fin = last_lane ? (carry_combine(carry, incl) & ~kAllZero) : 0;
-    if (fin) bits += run_bits(ct, fin);
-    // bit offsets of the lanes within the chunk
-    uint32_t x = bits;
+  const int czr = bc.czr, wbest = bc.wbits;
+  const uint2 lq = reinterpret_cast<const uint2*>(bc.len)[lane];
+  reinterpret_cast<uint2*>(s_len)[lane] = lq;
+  __syncwarp();
+  // Plane segment lengths: a literal s costs len[s] bits, plus w for C_zr
+  // (its zero counter); every zero-run token C_zr plus a w-bit counter; an
+  // isolated zero is the literal 0.  Literals of a segment with a histogram:
+  // lane k takes symbols 8k .. 8k + 7 of it; of a shorter segment: lane k
+  // takes its symbols 16k .. 16k + 15.  Either is one 16-byte load per lane,
+  // two planes' loads in flight.
+  const int n = b.w * b.h / 8;
+  uint32_t keptm = 0;
+  for (int pl = 0; pl < d; ++pl)
+    if (kept_types(bc.removed, p, pl)) keptm |= 1u << pl;
+  if (lane == 0)
+    for (int pl = 0; pl < d; ++pl)
+      if (!((keptm >> pl) & 1u)) BH.seglen[pl] = 0;
+  const uint32_t lczr = (uint32_t)s_len[czr] + (uint32_t)wbest;   // a run token, or a literal C_zr
+  const uint32_t lzero = s_len[0];
+  const PlaneStats* ps = pst + b.pst;
+  const uint8_t* S = sym + b.sym;
+  uint64_t sum = 0;
+  uint32_t mx = 0;
+  int64_t off = 0;   // symbol offset of the next kept plane
+  uint32_t m = keptm;
+  while (m) {
+    int pls[2], cnt[2];
+    uint4 q[2];
+    uint32_t tok[2], zc[2];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    const uint32_t chunk_bits = __shfl_sync(0xffffffffu, x, 31);
-    if (WRITE && bits) {
-      LaneWriter W;
-      W.begin(out, pos + (int64_t)total + (x - bits));
-      if (lead) put_run(ct, W, lead);
-      int prev = __ffs(NZ) - 1;
-      for (uint32_t m = NZ; m; m &= m - 1u) {
-        const int k = __ffs(m) - 1;
-        if (k - prev > 1) put_run(ct, W, (uint32_t)(k - prev - 1));
-        put_literal(ct, W, L.at(k));
-        prev = k;
+    for (int k = 0; k < 2; ++k) {
+      pls[k] = m ? __ffs(m) - 1 : -1;
+      m &= m - 1u;
+      cnt[k] = -1;   // a histogram
+      q[k] = make_uint4(0, 0, 0, 0);
+      tok[k] = zc[k] = 0;
+      if (pls[k] >= 0) {   // warp-uniform
+        const PlaneStats& P = ps[pls[k]];
+        const uint32_t km = kept_types(bc.removed, p, pls[k]);
+        if (plane_has_hist(km, n)) {
+          q[k] = reinterpret_cast<const uint4*>(P.hist)[lane];
+          zc[k] = P.hist[czr];
+        } else {
+          cnt[k] = max(0, min(16, __popc(km) * n - 16 * lane));
+          if (cnt[k] > 0) q[k] = *reinterpret_cast<const uint4*>(S + off + 16 * lane);
+          zc[k] = P.zeros;
+        }
+        tok[k] = (uint32_t)P.runs + P.extra[wbest];
+        off += region16(km, n);
       }
-      if (fin) put_run(ct, W, fin);
-      W.end();
     }
-    total += chunk_bits;
-    carry = carry_combine(carry, tot);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (pls[k] < 0) break;   // warp-uniform
+      const uint4 h = q[k];
+      uint32_t a;
+      if (cnt[k] < 0) {
+        a = (h.x & 0xffffu) * (lq.x & 0xffu) + (h.x >> 16) * ((lq.x >> 8) & 0xffu) + (h.y & 0xffffu) * ((lq.x >> 16) & 0xffu) +
+            (h.y >> 16) * (lq.x >> 24) + (h.z & 0xffffu) * (lq.y & 0xffu) + (h.z >> 16) * ((lq.y >> 8) & 0xffu) +
+            (h.w & 0xffffu) * ((lq.y >> 16) & 0xffu) + (h.w >> 16) * (lq.y >> 24);
+      } else {
+        LaneSyms L;
+        L.w[0] = h.x; L.w[1] = h.y; L.w[2] = h.z; L.w[3] = h.w;
+        L.cnt = cnt[k];
+        a = 0;
+        for (uint32_t nz = nonzero_mask(L); nz; nz &= nz - 1u) {
+          const uint32_t s = L.at(__ffs(nz) - 1);
+          a += (uint32_t)s_len[s] + ((int)s == czr ? (uint32_t)wbest : 0u);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      // with a histogram, zc counts the C_zr literals (isolated zeros are in
+      // it); without, the isolated zeros (the C_zr literals are in the sum)
+      const uint32_t v = a + (cnt[k] < 0 ? zc[k] * (uint32_t)wbest : zc[k] * lzero) + tok[k] * lczr;
+      if (lane == 0) BH.seglen[pls[k]] = v;
+      sum += v;
+      mx = max(mx, v);
+    }
   }
-  return total;
+  if (lane == 0) {
+    // seektable width: t0, raised only when a segment length needs more bits
+    const int t = max(bc.t0, mx ? bitlen_u32(mx) : 0);
+    const int64_t hdr = 5 + (int64_t)p * d + 18 + (int64_t)d * t + bc.tree_bits;
+    BH.t = t;
+    BH.hdr_bits = hdr;
+    item_size[bi] = (hdr + (int64_t)sum + 7) / 8 + extra_bytes;
+    // the segments must add up to the bit count of the Huffman pass
+    if (sum != bc.token_bits) set_status(status, kStInternal);
+  }
 }
+
 
 constexpr int kEmitWarps = 8;
 constexpr int kEncGroup = 16;
@@ -883,75 +1085,6 @@ __device__ void load_group(const int64_t* perm, int64_t g0, int ng, const BlockD
   G.nitem = *s_nitem;
 }
 
-// Symbol offset of plane pl inside a block's region.
-__device__ inline int64_t plane_offset(const uint32_t* removed, int p, int n, int pl) {
-  int64_t off = 0;
-  for (int q = 0; q < pl; ++q) {
-    const uint32_t km = kept_types(removed, p, q);
-    if (km) off += region16(km, n);
-  }
-  return off;
-}
-
-// Size pass of a group of ng blocks (group_block(perm, g0, .)): one warp
-// per (block, plane) segment gives its exact bit length.  Threads tid = 0 ..
-// nthr-1, whole warps; dyn holds kEncSmem bytes.
-template <class Sync>
-__device__ void enc_size_group(const int64_t* perm, int64_t g0, int ng, const BlockDev* __restrict__ blocks, const uint8_t* sym,
-                               const BlockCode* __restrict__ codes, BlockHdr* __restrict__ hdrs, uint8_t* dyn, int* s_nitem, int tid,
-                               int nthr, Sync sync) {
-  EncGroup G;
-  load_group(perm, g0, ng, blocks, codes, dyn, G, s_nitem, tid, nthr, sync);
-  const int wid = tid >> 5, lane = tid & 31, nw = nthr >> 5;
-  for (int it = wid; it < G.nitem; it += nw) {
-    const int j = G.item[it] >> 5, pl = G.item[it] & 31;
-    const int64_t bi = group_block(perm, g0, j);
-    const BlockDev b = blocks[bi];
-    const BlockCode& bc = codes[bi];
-    const int n = b.w * b.h / 8;
-    const CodeTab ct{G.code[j], G.len[j], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
-    const uint32_t km = kept_types(bc.removed, b.p, pl);
-    const uint64_t bits = warp_segment<false>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, nullptr, 0);
-    if (lane == 0) hdrs[bi].seglen[pl] = (uint32_t)bits;
-  }
-}
-
-
-// Per block: seektable width t (raised only when a segment length needs
-// more bits), header bits and the block's size in the stream.
-__device__ inline void enc_blocksize(int64_t bi, const TileDev* __restrict__ tiles, const BlockDev* __restrict__ blocks,
-                                     const BlockCode* __restrict__ codes, BlockHdr* __restrict__ hdrs, int64_t* __restrict__ item_size,
-                                     int* __restrict__ status) {
-  const BlockDev b = blocks[bi];
-  const BlockCode& bc = codes[bi];
-  const TileDev& tile = tiles[b.tile];
-  const int64_t extra = bi == tile.block_base ? 32 + 4 * (int64_t)tile.nb : 0;
-  const int d = bc.d, p = b.p;
-  BlockHdr& H = hdrs[bi];
-  if (!bc.any_kept) {
-    H.t = 0;
-    H.hdr_bits = 5 + (int64_t)p * d;
-    item_size[bi] = (5 + (int64_t)p * d + 7) / 8 + extra;
-    return;
-  }
-  uint64_t sum = 0;
-  uint32_t mx = 0;
-  for (int pl = 0; pl < d; ++pl) {
-    uint32_t v = 0;
-    if (kept_types(bc.removed, p, pl)) v = H.seglen[pl];
-    else H.seglen[pl] = 0;
-    sum += v;
-    mx = max(mx, v);
-  }
-  const int t = max(bc.t0, mx ? bitlen_u32(mx) : 0);
-  const int64_t hdr = 5 + (int64_t)p * d + 18 + (int64_t)d * t + bc.tree_bits;
-  H.t = t;
-  H.hdr_bits = hdr;
-  if (sum != bc.token_bits) set_status(status, kStInternal);
-  item_size[bi] = (hdr + (int64_t)sum + 7) / 8 + extra;
-}
-
-
 // The stream is written in whole 32-bit words: it needs its size rounded
 // up to a multiple of 4 bytes of capacity.
 __device__ inline int64_t needed_capacity(int64_t total) { return (total + 3) & ~3LL; }
@@ -966,7 +1099,7 @@ template <class Sync>
 __device__ void enc_emit_group(const int64_t* perm, int64_t g0, int ng, const TileDev* __restrict__ tiles,
                                const BlockDev* __restrict__ blocks, const uint8_t* sym, const BlockCode* __restrict__ codes,
                                const BlockHdr* __restrict__ hdrs, const int64_t* __restrict__ final_pos, uint32_t* __restrict__ out,
-                               uint8_t* dyn, int* s_nitem, int tid, int nthr, Sync sync) {
+                               int* __restrict__ status, uint8_t* dyn, int* s_nitem, int tid, int nthr, Sync sync) {
   EncGroup G;
   load_group(perm, g0, ng, blocks, codes, dyn, G, s_nitem, tid, nthr, sync);
   const int wid = tid >> 5, lane = tid & 31, nw = nthr >> 5;
@@ -1019,7 +1152,10 @@ __device__ void enc_emit_group(const int64_t* perm, int64_t g0, int ng, const Ti
     int64_t pos = block_bit_start(tiles[b.tile], final_pos, bi) + H.hdr_bits;
     for (int q = 0; q < pl; ++q) pos += H.seglen[q];
     const uint32_t km = kept_types(bc.removed, b.p, pl);
-    warp_segment<true>(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, out, pos);
+    const uint64_t bits =
+        warp_segment(sym + b.sym + plane_offset(bc.removed, b.p, n, pl), __popc(km) * n, ct, out, pos, H.seglen[pl]);
+    // the symbols must give the length the plane statistics gave
+    if (lane == 0 && bits != H.seglen[pl]) set_status(status, kStInternal);
   }
 }
 

@@ -47,6 +47,7 @@ __device__ inline void plan_tile_blocks(int ti, const TileDev& t, int min_level,
   int64_t idx = t.block_base;
   int64_t coef = t.coef_base;
   int64_t sym = t.sym_base;
+  int64_t pst = t.pst_base;
   const int dmax = dmax_of_bits(t.bits);
   for (int c = 0; c < t.C; ++c) {
     for (int lv = 0; lv <= t.L; ++lv) {
@@ -64,6 +65,8 @@ __device__ inline void plan_tile_blocks(int ti, const TileDev& t, int min_level,
           b.coef16 = t.coef16;
           b.dmax = dmax;
           b.sym = sym;
+          b.pst = pst;
+          pst += dmax;
           coef += (int64_t)p * b.w * b.h * (b.coef16 ? 2 : 4);
           sym += (int64_t)dmax * (((int64_t)p * b.w * b.h / 8 + 15) & ~15LL);
           out[idx++] = b;

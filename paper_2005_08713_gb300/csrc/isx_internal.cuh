@@ -30,6 +30,7 @@ struct TileDev {
   int64_t plane_base;       // element offset of its first Mallat plane
   int64_t coef_base;        // byte offset of its first area-ordered coefficient block
   int64_t sym_base;         // byte offset of its first block's symbol region (encode)
+  int64_t pst_base;         // index of its first block's first plane-statistics slot (encode)
   // decode destination: the part of the tile inside the rectangle (rx, ry,
   // rw, rh) of level-z pixels goes to dst, whose first byte is pixel
   // (rx, ry); rows dpitch bytes apart, the tile's own sample format
@@ -108,6 +109,7 @@ struct BlockDev {
   int32_t dmax;             // largest bit depth its coefficients can reach (bits + 6, at most 31)
   int64_t coef;             // byte offset of its coefficients: [type][area][8]
   int64_t sym;              // byte offset of its symbol region (encode)
+  int64_t pst;              // index of its plane-statistics slots, dmax of them (encode)
 };
 
 __host__ __device__ inline int dmax_of_bits(int bits) { return bits + 6 < kMaxD ? bits + 6 : kMaxD; }
@@ -121,6 +123,22 @@ struct BlockStats {
   uint32_t removed[3];      // bit pl set: plane pl of that type removed
   int32_t d;
 };
+
+// Per-(block, plane) statistics of one plane segment (encode, pass 1): the
+// counts of BlockStats restricted to the segment, from which the Huffman
+// pass finds the segment's exact bit length.  hist (with hist[0] = zeros) is
+// filled only for segments of more than 512 symbols; the zero-run counts
+// always.  A segment holds at most 3 * 128 * 128 / 8 = 6144 symbols:
+// 16-bit counts.
+struct __align__(16) PlaneStats {
+  uint16_t hist[256];
+  uint16_t extra[kMaxW + 1];
+  uint16_t runs;
+  uint16_t zeros;           // isolated zero symbols (the literal 0)
+  uint16_t pad[3];
+};
+static_assert(sizeof(PlaneStats) == 560, "PlaneStats is 35 16-byte words");
+static_assert(3 * kCell * kCell / 8 < 65536, "a plane segment's counts fit 16 bits");
 
 // Per-block code (encode, pass 2); 16-byte aligned so that the code and
 // length arrays copy as 16-byte words.

@@ -47,6 +47,7 @@ struct EncodeBuffers {
   const void* coef;          // int16 or int32 per block (BlockDev::coef16), byte offsets
   uint8_t* sym;              // symbol regions (BlockDev::sym)
   BlockStats* stats;
+  PlaneStats* pst;           // dmax slots per block from BlockDev::pst
   BlockCode* codes;
   void* hdrs;                // [n_blocks] enc_hdr_bytes() each
   int64_t* item_size;        // [n_blocks] block bytes, plus its tile header for a tile's first block

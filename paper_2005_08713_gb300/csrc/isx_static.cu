@@ -110,6 +110,7 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   const size_t o_coef = take(&used, (size_t)coef_bytes);
   const size_t o_sym = take(&used, (size_t)sym_bytes);
   const size_t o_stats = take(&used, sizeof(BlockStats) * nb);
+  const size_t o_pst = take(&used, sizeof(PlaneStats) * (size_t)nb * dmax_of_bits(t.bits));
   const size_t o_codes = take(&used, sizeof(BlockCode) * nb);
   const size_t o_hdrs = take(&used, enc_hdr_bytes() * nb);
   const size_t o_is = take(&used, 8 * nb), o_fp = take(&used, 8 * nb), o_perm = take(&used, 8 * nb);
@@ -140,7 +141,7 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   cudaStream_t s = (cudaStream_t)stream;
   td.nb = (int32_t)nb;
   td.fused = fused ? 1 : 0;
-  td.block_base = 0; td.plane_base = 0; td.coef_base = 0; td.sym_base = 0;
+  td.block_base = 0; td.plane_base = 0; td.coef_base = 0; td.sym_base = 0; td.pst_base = 0;
 
   TileDev* d_tile = (TileDev*)(ar + o_tile);
   int32_t* d_task = (int32_t*)(ar + o_task);
@@ -162,6 +163,7 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   eb.tiles = d_tile; eb.n_tiles = 1; eb.blocks = d_blocks; eb.n_blocks = nb; eb.coef = coef;
   eb.sym = ar + o_sym;
   eb.stats = (BlockStats*)(ar + o_stats);
+  eb.pst = (PlaneStats*)(ar + o_pst);
   eb.codes = (BlockCode*)(ar + o_codes);
   eb.hdrs = ar + o_hdrs;
   eb.item_size = (int64_t*)(ar + o_is); eb.final_pos = (int64_t*)(ar + o_fp);
@@ -202,6 +204,7 @@ extern "C" isx_status isx_encode_tile_static(const isx_tile_desc* tile, void* d_
   if (status == kStRange)
     return fail(h_err, err_len, ISX_ERR_ARG, "a sample exceeds the tile's bit depth (values must be below 2^bits)");
   if (status != 0)
-    return fail(h_err, err_len, ISX_ERR_CUDA, "internal consistency check failed on the device (code " + std::to_string(status) + ")");
+    return fail(h_err, err_len, ISX_ERR_INTERNAL,
+                "internal consistency check failed on the device (code " + std::to_string(status) + ")");
   return ISX_OK;
 }
