@@ -616,7 +616,6 @@ struct __align__(16) HuffWarp {
   uint32_t iw[256];       // internal node weights in creation order
   uint16_t parent[512];   // parent node id | 0x8000 for a right child
   uint32_t tree[81];
-  int nl;
 };
 
 // Sorts 8 keys per lane (element lane*8 + r) ascending across the warp.
@@ -654,11 +653,10 @@ __device__ inline void warp_bitonic_256(uint32_t (&k)[8]) {
   }
 }
 
-// Builds the code of the frequencies in H.f; returns the root id.  With
-// kTree the parent links are stored (H.parent); otherwise only the depth of
-// the leaf holding symbol `track` (-1: none) is returned in *depth.
-template <bool kTree>
-__device__ int huff_build_warp(HuffWarp& H, int track, int* depth) {
+// Sorted leaves of the frequencies in H.f, by one warp: H.leaf holds
+// (f << 8) | symbol ascending for every symbol with f > 0 (then kInf);
+// returns their count.
+__device__ inline int huff_leaves_warp(HuffWarp& H) {
   const int lane = threadIdx.x & 31;
   uint32_t k[8];
 #pragma unroll
@@ -693,142 +691,172 @@ __device__ int huff_build_warp(HuffWarp& H, int track, int* depth) {
       }
     }
     __syncwarp();
-#pragma unroll
-    for (int r = 0; r < 8; ++r) k[r] = kInf;
-    k[0] = x;   // key of rank `lane` (lanes >= present: none)
-    H.leaf[lane] = x;
+    H.leaf[lane] = x;   // key of rank `lane` (lanes >= present: none)
   } else {
     warp_bitonic_256(k);
 #pragma unroll
     for (int r = 0; r < 8; ++r) H.leaf[lane * 8 + r] = k[r];
   }
-  int cnt = 0, where = -1;
-  if (present <= 32) {
-    cnt = lane == 0 ? present : 0;
-    if (k[0] != kInf && (int)(k[0] & 0xffu) == track) where = lane;
-  } else {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      cnt += k[r] != kInf;
-      if (k[r] != kInf && (int)(k[r] & 0xffu) == track) where = lane * 8 + r;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    where = max(where, __shfl_xor_sync(0xffffffffu, where, o));
-  }
-  const int nl = cnt;
   __syncwarp();
-  if (lane == 0) {
-    H.nl = nl;
-    int qa = 0, qb = 0, ni = 0, cur = where, dep = 0;
-    uint32_t wl = nl > 0 ? H.leaf[0] >> 8 : kInf, wi = kInf;
-    for (int st = 0; st < nl - 1; ++st) {
-      int a, b;
-      uint32_t wa, wb;
-      if (wl <= wi) { a = qa; wa = wl; ++qa; wl = qa < nl ? H.leaf[qa] >> 8 : kInf; }   // the leaf queue wins ties
-      else { a = nl + qb; wa = wi; ++qb; wi = qb < ni ? H.iw[qb] : kInf; }
-      if (wl <= wi) { b = qa; wb = wl; ++qa; wl = qa < nl ? H.leaf[qa] >> 8 : kInf; }
-      else { b = nl + qb; wb = wi; ++qb; wi = qb < ni ? H.iw[qb] : kInf; }
-      const uint32_t wn = wa + wb;
-      H.iw[ni] = wn;
-      if (kTree) {
-        H.parent[a] = (uint16_t)(nl + ni);
-        H.parent[b] = (uint16_t)((nl + ni) | 0x8000);
-      } else if (a == cur || b == cur) {
-        ++dep;
-        cur = nl + ni;
-      }
-      if (qb == ni) wi = wn;   // the internal queue was empty: the new node is its front
-      ++ni;
-    }
-    if (depth) *depth = dep;
+  return present;
+}
+
+// Two-queue merge of the nl >= 2 sorted leaves of H by ONE thread: each
+// step takes the lighter queue front twice, the leaf queue first on equal
+// weight, and the first taken becomes the left child.  Writes the internal
+// weights in creation order (H.iw) and the parent links (H.parent); node
+// nl + i is the i-th internal node, the root 2 nl - 2.  The refills are
+// loads under a condition and selects, not branches: the eight threads of a
+// warp that run it run different blocks' merges side by side.
+__device__ inline void huff_merge_thread(HuffWarp& H, int nl) {
+  int qa = 0, qb = 0;
+  uint32_t wl = H.leaf[0] >> 8, wi = kInf;
+  for (int ni = 0; ni < nl - 1; ++ni) {
+    const bool ta = wl <= wi;
+    const int a = ta ? qa : nl + qb;
+    const uint32_t wa = ta ? wl : wi;
+    qa += ta;
+    qb += !ta;
+    uint32_t x = kInf, y = kInf;
+    if (qa < nl) x = H.leaf[qa] >> 8;
+    if (qb < ni) y = H.iw[qb];
+    wl = ta ? x : wl;
+    wi = ta ? wi : y;
+    const bool tb = wl <= wi;
+    const int b = tb ? qa : nl + qb;
+    const uint32_t wb = tb ? wl : wi;
+    qa += tb;
+    qb += !tb;
+    x = kInf;
+    y = kInf;
+    if (qa < nl) x = H.leaf[qa] >> 8;
+    if (qb < ni) y = H.iw[qb];
+    wl = tb ? x : wl;
+    wi = tb ? wi : y;
+    const uint32_t wn = wa + wb;
+    H.iw[ni] = wn;
+    H.parent[a] = (uint16_t)(nl + ni);
+    H.parent[b] = (uint16_t)((nl + ni) | 0x8000);
+    if (qb == ni) wi = wn;   // the internal queue was empty: the new node is its front
   }
-  __syncwarp();
-  return nl <= 1 ? 0 : 2 * nl - 2;
+}
+
+// The merges of a CTA's blocks: thread j of warp 0 merges the leaves of
+// warp j's block (s_nl[j] of them; fewer than 2: nothing to merge).
+// Called by every thread of the CTA between two barriers.
+__device__ inline void huff_merge_cta(HuffWarp* HW, const int* s_nl) {
+  const int t = threadIdx.x;
+  if (t < kHuffWarps && s_nl[t] > 1) huff_merge_thread(HW[t], s_nl[t]);
 }
 
 // Huffman code of block bi (C_zr, counter width w by Eq. 3, provisional
-// and final trees, codes, preorder tree bits) by one warp, with H its
-// shared-memory workspace.
-__device__ inline void block_huffman(int64_t bi, const BlockDev* __restrict__ blocks, const BlockStats* __restrict__ stats,
-                                     BlockCode* __restrict__ codes, HuffWarp& H) {
-  const int lane = threadIdx.x & 31;
-  const BlockStats& st = stats[bi];
-  const BlockDev b = blocks[bi];
-  BlockCode& bc = codes[bi];
-  const int d = st.d, p = b.p;
-  const uint32_t n_sym = st.n_sym;
-  const int t0 = bitlen_u32((uint32_t)(p * b.w * b.h / 8)) - 1 + 5;
-  if (lane == 0) {
-    bc.d = d;
-    bc.p = p;
-    for (int t = 0; t < 3; ++t) bc.removed[t] = st.removed[t];
-    bc.t0 = t0;
-  }
-  if (n_sym == 0) {
+// and final trees, codes, preorder tree bits): warp w of the CTA takes
+// block bi (-1: none) with HW[w] its shared-memory workspace; the CTA's
+// tree merges run side by side (huff_merge_cta).  Every thread of the CTA
+// calls it; sync() is the CTA barrier.
+template <class Sync>
+__device__ inline void cta_block_huffman(int64_t bi, const BlockDev* __restrict__ blocks, const BlockStats* __restrict__ stats,
+                                         BlockCode* __restrict__ codes, HuffWarp* HW, int* s_nl, Sync sync) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  HuffWarp& H = HW[wid];
+  // a block with no kept symbol is coded by its header alone
+  bool active = bi >= 0;
+  const BlockStats* st = active ? stats + bi : stats;
+  BlockCode* bc = active ? codes + bi : codes;
+  int d = 0, p = 0;
+  uint32_t n_sym = 0;
+  if (active) {
+    const BlockDev b = blocks[bi];
+    d = st->d;
+    p = b.p;
+    n_sym = st->n_sym;
     if (lane == 0) {
-      bc.any_kept = 0;
-      bc.token_bits = 0;
-      bc.tree_bits = 0;
-      bc.czr = 0;
-      bc.wbits = 0;
+      bc->d = d;
+      bc->p = p;
+      for (int t = 0; t < 3; ++t) bc->removed[t] = st->removed[t];
+      bc->t0 = bitlen_u32((uint32_t)(p * b.w * b.h / 8)) - 1 + 5;
     }
-    return;
+    if (n_sym == 0) {
+      if (lane == 0) {
+        bc->any_kept = 0;
+        bc->token_bits = 0;
+        bc->tree_bits = 0;
+        bc->czr = 0;
+        bc->wbits = 0;
+      }
+      active = false;
+    }
   }
   // C_zr: least frequent of 1..255, smallest on ties
-  uint32_t best = kInf;
-  for (int s = lane; s < 256; s += 32) {
-    const uint32_t fr = st.hist[s];
-    H.f[s] = fr;
-    if (s >= 1) best = min(best, (fr << 8) | (uint32_t)s);
-  }
+  int czr = 0, nl = 0;
+  uint32_t lit_czr = 0;
+  if (active) {
+    uint32_t best = kInf;
+    for (int s = lane; s < 256; s += 32) {
+      const uint32_t fr = st->hist[s];
+      H.f[s] = fr;
+      if (s >= 1) best = min(best, (fr << 8) | (uint32_t)s);
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-  const int czr = (int)(best & 0xffu);
-  const uint32_t lit_czr = best >> 8;
-  __syncwarp();
-  // provisional code: every run counts once for C_zr; l = C_zr's code length
-  if (lane == 0) H.f[czr] = lit_czr + st.n_runs;
-  __syncwarp();
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    czr = (int)(best & 0xffu);
+    lit_czr = best >> 8;
+    __syncwarp();
+    // provisional code: every run counts once for C_zr; l = C_zr's code length
+    if (lane == 0) H.f[czr] = lit_czr + st->n_runs;
+    __syncwarp();
+    nl = huff_leaves_warp(H);
+  }
   // The provisional tree is built with its parent links: when the chosen
   // width needs no extra run tokens, the final counts equal these and the
   // tree is reused as is.
-  int root = huff_build_warp<true>(H, -1, nullptr);
-  int l = 0;
-  if (H.f[czr] > 0 && H.nl > 1) {
-    int leaf = -1;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int i = lane + 32 * m;
-      if (i < H.nl && (int)(H.leaf[i] & 0xffu) == czr) leaf = i;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) leaf = max(leaf, __shfl_xor_sync(0xffffffffu, leaf, o));
-    int dep = 0;
-    for (int v = leaf; v != root && dep < 64; ++dep) v = H.parent[v] & 0x7fff;   // the leaf's depth
-    l = dep;
-  }
-  // Eq. 3 (reading): w minimises (w + l) * (#C_zr tokens at width w) over [2, b]
-  int bmax = n_sym > 1 ? bitlen_u32(n_sym - 1) : 0;
-  if (bmax < 2) bmax = 2;
+  if (lane == 0) s_nl[wid] = active ? nl : 0;
+  sync();
+  huff_merge_cta(HW, s_nl);
+  sync();
   int wbest = 2;
-  uint64_t bestc = ~0ull;
-  for (int w = 2; w <= bmax; ++w) {
-    const uint64_t pairs = (uint64_t)lit_czr + st.n_runs + st.extra[w];
-    const uint64_t cost = (uint64_t)(w + l) * pairs;
-    if (cost < bestc) { bestc = cost; wbest = w; }
+  bool rebuild = false;
+  if (active) {
+    const int root = nl <= 1 ? 0 : 2 * nl - 2;
+    int l = 0;
+    if (H.f[czr] > 0 && nl > 1) {
+      int leaf = -1;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int i = lane + 32 * m;
+        if (i < nl && (int)(H.leaf[i] & 0xffu) == czr) leaf = i;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) leaf = max(leaf, __shfl_xor_sync(0xffffffffu, leaf, o));
+      int dep = 0;
+      for (int v = leaf; v != root && dep < 64; ++dep) v = H.parent[v] & 0x7fff;   // the leaf's depth
+      l = dep;
+    }
+    // Eq. 3 (reading): w minimises (w + l) * (#C_zr tokens at width w) over [2, b]
+    int bmax = n_sym > 1 ? bitlen_u32(n_sym - 1) : 0;
+    if (bmax < 2) bmax = 2;
+    uint64_t bestc = ~0ull;
+    for (int w = 2; w <= bmax; ++w) {
+      const uint64_t pairs = (uint64_t)lit_czr + st->n_runs + st->extra[w];
+      const uint64_t cost = (uint64_t)(w + l) * pairs;
+      if (cost < bestc) { bestc = cost; wbest = w; }
+    }
+    if (st->extra[wbest] != 0) {   // C_zr's count changes: build the final tree
+      __syncwarp();
+      if (lane == 0) H.f[czr] = lit_czr + st->n_runs + st->extra[wbest];
+      __syncwarp();
+      nl = huff_leaves_warp(H);
+      rebuild = true;
+    }
   }
-  if (st.extra[wbest] != 0) {   // C_zr's count changes: build the final tree
-    __syncwarp();
-    if (lane == 0) H.f[czr] = lit_czr + st.n_runs + st.extra[wbest];
-    __syncwarp();
-    root = huff_build_warp<true>(H, -1, nullptr);
-  }
-  const int nl = H.nl;
+  if (lane == 0) s_nl[wid] = rebuild ? nl : 0;
+  sync();
+  huff_merge_cta(HW, s_nl);
+  sync();
+  if (!active) return;
+  const int root = nl <= 1 ? 0 : 2 * nl - 2;
   // codes: every leaf walks up to the root; a lane walks its (up to) 8 leaves together
-  for (int s2 = lane; s2 < 256; s2 += 32) { bc.code[s2] = 0; bc.len[s2] = 0; }
+  for (int s2 = lane; s2 < 256; s2 += 32) { bc->code[s2] = 0; bc->len[s2] = 0; }
   for (int k = lane; k < 81; k += 32) H.tree[k] = 0;
   int v[8], len[8];
   uint32_t code[8];
@@ -866,8 +894,8 @@ __device__ inline void block_huffman(int64_t bi, const BlockDev* __restrict__ bl
     if (i < nl) {
       K[i] = len[m] ? code[m] << (31 - len[m]) : 0u;   // codes are at most 31 bits (Fibonacci bound)
       const int sym = (int)(H.leaf[i] & 0xffu);
-      bc.code[sym] = code[m];
-      bc.len[sym] = (uint8_t)len[m];
+      bc->code[sym] = code[m];
+      bc->len[sym] = (uint8_t)len[m];
       tb += (uint64_t)H.f[sym] * len[m];
     }
   }
@@ -899,14 +927,14 @@ __device__ inline void block_huffman(int64_t bi, const BlockDev* __restrict__ bl
       if ((uint32_t)vv) atomicOr(&H.tree[wi + 1], (uint32_t)vv);
     }
   }
-  if (lane == 0) bc.tree_bits = 10 * nl - 1;
+  if (lane == 0) bc->tree_bits = 10 * nl - 1;
   __syncwarp();
-  for (int k = lane; k < 80; k += 32) bc.tree[k] = H.tree[k];
+  for (int k = lane; k < 80; k += 32) bc->tree[k] = H.tree[k];
   if (lane == 0) {
-    bc.any_kept = 1;
-    bc.czr = czr;
-    bc.wbits = wbest;
-    bc.token_bits = tb + (uint64_t)wbest * H.f[czr];
+    bc->any_kept = 1;
+    bc->czr = czr;
+    bc->wbits = wbest;
+    bc->token_bits = tb + (uint64_t)wbest * H.f[czr];
   }
 }
 

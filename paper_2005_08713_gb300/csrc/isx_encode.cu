@@ -43,11 +43,12 @@ __global__ void __launch_bounds__(32 * kHuffWarps, 4) k_block_huffman(const Bloc
                                                                   const BlockStats* __restrict__ stats, BlockCode* __restrict__ codes,
                                                                   int64_t nb) {
   __shared__ HuffWarp hw[kHuffWarps];
+  __shared__ int s_nl[kHuffWarps];
   const int wid = threadIdx.x >> 5;
   const int64_t gi = (int64_t)blockIdx.x * kHuffWarps + wid;
-  if (gi >= nb) return;
-  // blocks by level: the warps of a CTA get blocks of similar size and finish together
-  block_huffman(perm[gi], blocks, stats, codes, hw[wid]);
+  // blocks by level: the warps of a CTA get blocks of similar size, whose
+  // tree merges then take similar numbers of steps side by side
+  cta_block_huffman(gi < nb ? perm[gi] : (int64_t)-1, blocks, stats, codes, hw, s_nl, CtaBarrier());
 }
 
 constexpr int kLayoutWarps = 8;
