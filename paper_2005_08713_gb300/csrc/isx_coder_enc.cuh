@@ -441,9 +441,13 @@ __device__ inline void enc_symbols_block(int64_t bi, const BlockDev* __restrict_
 
 
 // ------------------------------------------------- token costs and writer
+// Code of a block: codewords and lengths by symbol, and the bits of a
+// nonzero literal (lit[s] = len[s], plus w for C_zr's zero counter;
+// lit[0] = 0: a zero symbol is always part of a run).
 struct CodeTab {
   const uint32_t* code;
   const uint8_t* len;
+  const uint8_t* lit;
   int czr, wbits;
   uint32_t M;
 };
@@ -451,10 +455,8 @@ struct CodeTab {
 __device__ inline uint32_t run_bits(const CodeTab& ct, uint32_t L) {
   if (L == 1) return ct.len[0];
   if (ct.M == 0) return 0;
-  return ((L + ct.M - 1) / ct.M) * (uint32_t)(ct.len[ct.czr] + ct.wbits);
-}
-__device__ inline uint32_t lit_bits(const CodeTab& ct, uint32_t s) {
-  return ct.len[s] + ((int)s == ct.czr ? ct.wbits : 0);
+  const uint32_t tokens = L <= ct.M ? 1u : (L + ct.M - 1) / ct.M;
+  return tokens * (uint32_t)(ct.len[ct.czr] + ct.wbits);
 }
 
 // MSB-first writer of one lane's contiguous bit range straight into the
@@ -478,10 +480,10 @@ struct LaneWriter {
     else out[wcur] = be;
     ++wcur;
   }
-  __device__ void put(uint32_t v, int nb) {   // nb <= 32
-    if (nb <= 0) return;
-    const uint64_t x = (uint64_t)(nb == 32 ? v : (v & ((1u << nb) - 1u)));
-    acc |= x << (64 - nacc - nb);
+  // v < 2^nb (codewords and counters have no bits above their length),
+  // 0 <= nb <= 32; the two shifts place it at bit 64 - nacc - nb.
+  __device__ void put(uint32_t v, int nb) {
+    acc |= ((uint64_t)v << (32 - nb)) << (32 - nacc);
     nacc += nb;
     if (nacc >= 32) {
       word((uint32_t)(acc >> 32));
@@ -535,12 +537,23 @@ __device__ uint64_t warp_segment(const uint8_t* seg, int len, const CodeTab& ct,
       const int first = __ffs(NZ) - 1, last = 31 - __clz(NZ);
       lz = (uint32_t)first;
       zeros = (uint32_t)(L.cnt - 1 - last);
-      int prev = first;
-      for (uint32_t m = NZ; m; m &= m - 1u) {
-        const int k = __ffs(m) - 1;
-        if (k - prev > 1) bits += run_bits(ct, (uint32_t)(k - prev - 1));
-        bits += lit_bits(ct, L.at(k));
-        prev = k;
+      // the literals' bits: lit[] over all 16 positions (zero symbols cost
+      // 0 there; positions past the segment are cleared first)
+      uint32_t wv[4] = {L.w[0], L.w[1], L.w[2], L.w[3]};
+      if (L.cnt < 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int nb = min(max(L.cnt - 4 * q, 0), 4);
+          wv[q] &= nb >= 4 ? 0xffffffffu : ((1u << (8 * nb)) - 1u);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) bits += ct.lit[__byte_perm(wv[k >> 2], 0, 0x4440 | (k & 3))];
+      // the zero runs between the lane's first and last nonzero symbols
+      const uint32_t Zi = ~NZ & ((2u << last) - 1u) & ~((2u << first) - 1u);
+      for (uint32_t st = Zi & ~(Zi << 1); st; st &= st - 1u) {
+        const int s0 = __ffs(st) - 1;
+        bits += run_bits(ct, (uint32_t)(__ffs(~(Zi >> s0)) - 1));
       }
     }
     const uint32_t elem = seen ? zeros : (kAllZero | (uint32_t)L.cnt);
@@ -1056,7 +1069,7 @@ __device__ inline void enc_block_layout(int64_t bi, const TileDev* __restrict__ 
 
 constexpr int kEmitWarps = 8;
 constexpr int kEncGroup = 16;
-constexpr int kEncSmem = kEncGroup * (256 * 4 + 256) + kEncGroup * 32 * 2;
+constexpr int kEncSmem = kEncGroup * (256 * 4 + 256 + 256) + kEncGroup * 32 * 2;
 
 __device__ inline int64_t block_bit_start(const TileDev& t, const int64_t* final_pos, int64_t bi) {
   return 8 * (final_pos[bi] + (bi == t.block_base ? 32 + 4 * (int64_t)t.nb : 0));
@@ -1067,6 +1080,7 @@ __device__ inline int64_t block_bit_start(const TileDev& t, const int64_t* final
 struct EncGroup {
   uint32_t (*code)[256];
   uint8_t (*len)[256];
+  uint8_t (*lit)[256];
   uint16_t* item;
   int nitem;
 };
@@ -1082,15 +1096,31 @@ __device__ void load_group(const int64_t* perm, int64_t g0, int ng, const BlockD
                            EncGroup& G, int* s_nitem, int tid, int nthr, Sync sync) {
   G.code = reinterpret_cast<uint32_t (*)[256]>(dyn);
   G.len = reinterpret_cast<uint8_t (*)[256]>(dyn + kEncGroup * 256 * 4);
-  G.item = reinterpret_cast<uint16_t*>(dyn + kEncGroup * (256 * 4 + 256));
+  G.lit = reinterpret_cast<uint8_t (*)[256]>(dyn + kEncGroup * (256 * 4 + 256));
+  G.item = reinterpret_cast<uint16_t*>(dyn + kEncGroup * (256 * 4 + 256 + 256));
   // code and length tables of the group's blocks, all copies in flight at
-  // once: per block 64 16-byte words of codes and 16 of lengths
+  // once: per block 64 16-byte words of codes and 16 of lengths (each also
+  // gives 16 entries of lit[])
   for (int idx = tid; idx < ng * 80; idx += nthr) {
     const int j = idx / 80, q = idx - j * 80;
     const BlockCode& bc = codes[group_block(perm, g0, j)];
     if (!bc.any_kept) continue;
-    if (q < 64) reinterpret_cast<uint4*>(G.code[j])[q] = reinterpret_cast<const uint4*>(bc.code)[q];
-    else reinterpret_cast<uint4*>(G.len[j])[q - 64] = reinterpret_cast<const uint4*>(bc.len)[q - 64];
+    if (q < 64) {
+      reinterpret_cast<uint4*>(G.code[j])[q] = reinterpret_cast<const uint4*>(bc.code)[q];
+    } else {
+      uint4 v = reinterpret_cast<const uint4*>(bc.len)[q - 64];
+      reinterpret_cast<uint4*>(G.len[j])[q - 64] = v;
+      const int s0 = 16 * (q - 64), cz = bc.czr - s0;
+      if (s0 == 0) v.x &= ~0xffu;   // symbol 0
+      if (cz >= 0 && cz < 16) {     // C_zr: plus its counter (lengths stay below 256: no carry between bytes)
+        const uint32_t add = (uint32_t)bc.wbits << (8 * (cz & 3));
+        v.x += cz >> 2 == 0 ? add : 0u;
+        v.y += cz >> 2 == 1 ? add : 0u;
+        v.z += cz >> 2 == 2 ? add : 0u;
+        v.w += cz >> 2 == 3 ? add : 0u;
+      }
+      reinterpret_cast<uint4*>(G.lit[j])[q - 64] = v;
+    }
   }
   if (tid < 32) {
     const int j = tid;
@@ -1176,7 +1206,7 @@ __device__ void enc_emit_group(const int64_t* perm, int64_t g0, int ng, const Ti
     const BlockCode& bc = codes[bi];
     const BlockHdr& H = hdrs[bi];
     const int n = b.w * b.h / 8;
-    const CodeTab ct{G.code[j], G.len[j], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
+    const CodeTab ct{G.code[j], G.len[j], G.lit[j], bc.czr, bc.wbits, (1u << bc.wbits) - 1u};
     int64_t pos = block_bit_start(tiles[b.tile], final_pos, bi) + H.hdr_bits;
     for (int q = 0; q < pl; ++q) pos += H.seglen[q];
     const uint32_t km = kept_types(bc.removed, b.p, pl);
