@@ -61,7 +61,8 @@ struct BitPf {
   int avail;
   uint64_t buf;
   int nbuf;
-  int64_t pos;
+  int64_t wend;        // bit position just past the last bit in buf
+  __device__ int64_t pos() const { return wend - nbuf; }   // bit position of the next bit
   __device__ uint4 chunk(int64_t off) const {
     if (off >= 0 && off + 16 <= nbytes) return __ldg(reinterpret_cast<const uint4*>(p + off));
     uint32_t w[4];
@@ -111,16 +112,16 @@ struct BitPf {
     }
     buf <<= drop;
     nbuf = 64 - drop;
-    pos = bitpos;
+    wend = bitpos + nbuf;
   }
   __device__ uint32_t peek(int n) const { return n ? (uint32_t)(buf >> (64 - n)) : 0u; }
   __device__ void skip(int n) {   // n <= 32
     buf <<= n;
     nbuf -= n;
-    pos += n;
     if (nbuf <= 32) {
       buf |= (uint64_t)next_word() << (32 - nbuf);
       nbuf += 32;
+      wend += 32;
     }
   }
   __device__ uint32_t get(int n) {
@@ -158,7 +159,7 @@ __device__ inline void dec_tables_block(int64_t bi, const BlockDev* __restrict__
       }
       di.removed[t] = r;
     }
-    bool ok = d >= 1 && in.pos <= nbits;
+    bool ok = d >= 1 && in.pos() <= nbits;
     if (ok && any) {
       T.czr = (int)in.get(8);
       T.wbits = (int)in.get(5);
@@ -177,7 +178,7 @@ __device__ inline void dec_tables_block(int64_t bi, const BlockDev* __restrict__
       uint32_t code = 0;
       int dep = 0, nn = 0;
       while (ok) {
-        if (nn >= 511 || in.pos >= nbits) { ok = false; break; }
+        if (nn >= 511 || in.pos() >= nbits) { ok = false; break; }
         const int v = nn++;
         if (dep > 0 && (code & 1u)) T.node[path[dep - 1]] = (uint32_t)(path[dep - 1] + 1) | ((uint32_t)v << 16);
         if (in.get(1)) {
@@ -209,7 +210,7 @@ __device__ inline void dec_tables_block(int64_t bi, const BlockDev* __restrict__
         }
       }
       if (ok) {
-        int64_t pos = in.pos;
+        int64_t pos = in.pos();
         for (int pl = 0; pl < d; ++pl) {
           T.segpos[pl] = pos;
           pos += T.seglen[pl];
@@ -239,36 +240,32 @@ constexpr int kLevels = 16;
 
 
 
-// 16-byte symbol writer of one thread.
+// 8-byte symbol writer of one thread over a cleared region: a word is
+// stored only if it holds a nonzero symbol.
 struct SymOut {
-  uint4* dst;          // the 16-byte chunk being filled
-  uint64_t lo, hi;
-  int c;               // position of the next symbol in the chunk
-  bool dirty;          // the chunk holds a nonzero symbol
+  uint64_t* dst;       // the word being filled
+  uint64_t cur;
+  int c;               // position of the next symbol in the word
   __device__ void flush() {
-    if (dirty) *dst = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+    if (cur) *dst = cur;
     ++dst;
-    lo = hi = 0;
+    cur = 0;
     c = 0;
-    dirty = false;
   }
   __device__ void put(uint32_t s) {
-    const uint64_t v = (uint64_t)s << (8 * (c & 7));
-    if (c < 8) lo |= v;
-    else hi |= v;
-    dirty = true;
-    if (++c == 16) flush();
+    cur |= (uint64_t)s << (8 * c);
+    if (++c == 8) flush();
   }
   // The region was cleared beforehand: a run of zeros only moves the position.
   __device__ void zeros(uint32_t cnt) {
     const uint32_t p = (uint32_t)c + cnt;
-    if (p < 16) {
+    if (p < 8) {
       c = (int)p;
       return;
     }
     flush();
-    dst += (p >> 4) - 1;
-    c = (int)(p & 15);
+    dst += (p >> 3) - 1;
+    c = (int)(p & 7);
   }
 };
 // Segment items (block << 5 | plane) in block-major order: blocks by level
@@ -325,7 +322,7 @@ __device__ inline void dec_segment(int64_t bi, int pl, const uint16_t* tab, cons
   const uint32_t* node = T->node;
   BitPf in;
   in.seek(stream + bbyte[bi], blen[bi], start);
-  SymOut out{reinterpret_cast<uint4*>(sym + off), 0, 0, 0, false};
+  SymOut out{reinterpret_cast<uint64_t*>(sym + off), 0, 0};
   int pos = 0;
   bool bad = false;
   while (pos < need) {
@@ -360,10 +357,11 @@ __device__ inline void dec_segment(int64_t bi, int pl, const uint16_t* tab, cons
       out.put((uint32_t)s);
       ++pos;
     }
-    if (in.pos > limit) { bad = true; break; }
   }
+  // a corrupt segment that reads past its end (or stops short) is caught
+  // here: the loop ends after `need` symbols whatever the bits say
   if (out.c) out.flush();
-  if (bad || in.pos != limit) set_status(status, kStCorrupt);
+  if (bad || in.pos() != limit) set_status(status, kStCorrupt);
 }
 
 

@@ -182,8 +182,8 @@ __global__ void __launch_bounds__(32) k_dec_segments_ml(const BlockDev* __restri
     bool broken = false;
     if (act) {
       in.seek(bp, bl, cst);
-      while (in.pos < cen) {
-        if (nm < kMlMarks) s_marks[nm++][lane] = (uint16_t)(in.pos - cst);
+      while (in.pos() < cen) {
+        if (nm < kMlMarks) s_marks[nm++][lane] = (uint16_t)(in.pos() - cst);
         uint32_t sy, c;
         if (!ml_token(in, s_tab, node, czr, wb, &sy, &c)) { broken = true; break; }
         cnt_own += c;
@@ -193,11 +193,11 @@ __global__ void __launch_bounds__(32) k_dec_segments_ml(const BlockDev* __restri
     __syncwarp();
     // 2. continuation until a later chunk's recorded token start (or the segment's end)
     int land_k = N;
-    int64_t land_p = act ? in.pos : 0;
+    int64_t land_p = act ? in.pos() : 0;
     if (act && !broken && j < N - 1) {
       int k = j + 1, ptr = 0;
       for (;;) {
-        const int64_t p = in.pos;
+        const int64_t p = in.pos();
         if (p >= send) { land_k = N; land_p = p; break; }
         while (k < N - 1 && p >= seg0 + (int64_t)(k + 1) * C) { ++k; ptr = 0; }
         const uint32_t rel = (uint32_t)(p - (seg0 + (int64_t)k * C));
@@ -234,12 +234,12 @@ __global__ void __launch_bounds__(32) k_dec_segments_ml(const BlockDev* __restri
       uint32_t prefix = 0;
       if (vstart > cst) {
         in.seek(bp, bl, cst);
-        while (in.pos < vstart) {
+        while (in.pos() < vstart) {
           uint32_t sy, c;
           if (!ml_token(in, s_tab, node, czr, wb, &sy, &c)) { bad = true; break; }
           prefix += c;
         }
-        if (in.pos != vstart) bad = true;
+        if (in.pos() != vstart) bad = true;
       }
       vc = cnt_own + cnt_cont - prefix;   // modular: a garbage prefix cancels
       if (vc > (uint32_t)need) bad = true;
@@ -263,13 +263,13 @@ __global__ void __launch_bounds__(32) k_dec_segments_ml(const BlockDev* __restri
       SymOutShared out{sym + poff, s0, s0 + vc, s0, {0u, 0u, 0u, 0u}, false};
       in.seek(bp, bl, vstart);
       bool wbad = false;
-      while (in.pos < vend) {
+      while (in.pos() < vend) {
         uint32_t sy, c;
         if (!ml_token(in, s_tab, node, czr, wb, &sy, &c) || out.pos + c > out.s1) { wbad = true; break; }
         out.token(sy, c);
       }
       out.finish();
-      if (wbad || in.pos != vend || out.pos != out.s1) set_status(status, kStCorrupt);
+      if (wbad || in.pos() != vend || out.pos != out.s1) set_status(status, kStCorrupt);
     }
   }
 }
