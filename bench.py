@@ -562,7 +562,7 @@ def run_gpu(args):
                 "encode_frac": round(pb / (em / 1e3) / 1e9 / hbm, 4), "decode_frac": round(pb / (dm / 1e3) / 1e9 / hbm, 4),
                 "lossless_identity": bool(torch.equal(d_dec, d_img))}
 
-    lossless = soft(lossless_run) if rank == 0 and not args.lossless else None
+    lossless = soft(lossless_run) if rank == 0 and not args.lossless and not args.no_lossless else None
 
     singles = soft(run_single_configs, dev, stream, max(5, args.steps)) if rank == 0 and not args.no_single else None
 
@@ -1013,6 +1013,7 @@ def main():
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-single", action="store_true", help="skip the single-image workloads (512x512 stain, 2048x2048 phantom)")
     ap.add_argument("--no-untiled", action="store_true", help="skip the slide coded as one untiled image")
+    ap.add_argument("--no-lossless", action="store_true", help="skip the lossless run of the slide beside the lossy one")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-batch measurement")
     ap.add_argument("--no-per-tile", action="store_true", help="skip the one-tile-per-call comparison of the batch")
     ap.add_argument("--batch-tiles", type=int, default=4096)
