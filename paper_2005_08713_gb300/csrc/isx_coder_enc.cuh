@@ -831,7 +831,7 @@ __device__ inline void cta_block_huffman(int64_t bi, const BlockDev* __restrict_
   bool rebuild = false;
   if (active) {
     const int root = nl <= 1 ? 0 : 2 * nl - 2;
-    int l = 0;
+    int l = 0, io = 0;   // C_zr's code length and the place of its leaf in the sorted order
     if (H.f[czr] > 0 && nl > 1) {
       int leaf = -1;
 #pragma unroll
@@ -844,6 +844,7 @@ __device__ inline void cta_block_huffman(int64_t bi, const BlockDev* __restrict_
       int dep = 0;
       for (int v = leaf; v != root && dep < 64; ++dep) v = H.parent[v] & 0x7fff;   // the leaf's depth
       l = dep;
+      io = leaf;
     }
     // Eq. 3 (reading): w minimises (w + l) * (#C_zr tokens at width w) over [2, b]
     int bmax = n_sym > 1 ? bitlen_u32(n_sym - 1) : 0;
@@ -854,11 +855,42 @@ __device__ inline void cta_block_huffman(int64_t bi, const BlockDev* __restrict_
       const uint64_t cost = (uint64_t)(w + l) * pairs;
       if (cost < bestc) { bestc = cost; wbest = w; }
     }
-    if (st->extra[wbest] != 0) {   // C_zr's count changes: build the final tree
+    if (st->extra[wbest] != 0) {
+      // C_zr's count grows (it had runs, so it is a leaf: the only one when
+      // nl = 1): the final tree's sorted leaves are the provisional ones with
+      // C_zr's key moved right to its new place, the keys between shifting
+      // left by one
+      const uint32_t fz = lit_czr + st->n_runs + st->extra[wbest];
+      const uint32_t knew = (fz << 8) | (uint32_t)czr;
+      int below = 0;   // keys below the new one, the old C_zr key among them
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int i = lane + 32 * m;
+        below += i < nl && H.leaf[i] < knew;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+      const int jn = below - 1;
+      // two halves of 128 places: each reads only places the other half has
+      // not written yet (the first writes below 128, the second reads above)
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        uint32_t nxt[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = lane + 32 * (4 * half + m);
+          nxt[m] = i >= io && i < jn ? H.leaf[i + 1] : knew;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = lane + 32 * (4 * half + m);
+          if (i >= io && i <= jn) H.leaf[i] = nxt[m];
+        }
+        __syncwarp();
+      }
+      if (lane == 0) H.f[czr] = fz;
       __syncwarp();
-      if (lane == 0) H.f[czr] = lit_czr + st->n_runs + st->extra[wbest];
-      __syncwarp();
-      nl = huff_leaves_warp(H);
       rebuild = true;
     }
   }
