@@ -13,7 +13,7 @@ available: TCIA CR/DX/MG radiographs and Philips 9-bit pathology scans):
   plane): ~60% pale background 230..250 with N(0, 3^2) noise, tissue of
   pink stroma with dark purple nuclei (radius 3..8 px), N(0, 10^2).
 * ``phantom`` 12-bit monochrome in uint16: 8..16 smooth elliptical
-  phantoms summed and clamped to 4095, plus noise N(v, v).
+  phantoms summed and clamped to 4095, each value v replaced by a Poisson(v) sample.
 """
 from __future__ import annotations
 
@@ -54,6 +54,9 @@ def _get():
             lib.isx_gen_phantom.argtypes = [u64, i64, i64, i64, i64, i64, i64, vp, i64, i32]
             lib.isx_gen_mix64.argtypes = [u64]
             lib.isx_gen_mix64.restype = u64
+            lib.isx_gen_normals.argtypes = [u64, i64, vp]
+            lib.isx_gen_poissons.argtypes = [ctypes.c_double, u64, i64, vp]
+            lib.isx_gen_series.argtypes = [vp, vp, vp, i64, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -69,6 +72,31 @@ def config_seed(config_id: int, seed: int = BASE_SEED) -> int:
 
 def mix64(x: int) -> int:
     return int(_get().isx_gen_mix64(x & 0xFFFFFFFFFFFFFFFF))
+
+
+def normals(key0: int, n: int) -> np.ndarray:
+    """n standard normal deviates of the generators' Box-Muller sampler (streams key0, key0 + 1, ...)."""
+    out = np.empty(n, np.float64)
+    _get().isx_gen_normals(key0 & 0xFFFFFFFFFFFFFFFF, n, out.ctypes.data)
+    return out
+
+
+def poissons(lam: float, key0: int, n: int) -> np.ndarray:
+    """n Poisson(lam) samples of the generators' sampler (streams key0, key0 + 1, ...)."""
+    out = np.empty(n, np.int64)
+    _get().isx_gen_poissons(float(lam), key0 & 0xFFFFFFFFFFFFFFFF, n, out.ctypes.data)
+    return out
+
+
+def series(x, u, k):
+    """The generators' own ln x, cos(2 pi u) and ln k! (series in +, -, *, /), elementwise."""
+    x = np.ascontiguousarray(x, np.float64); u = np.ascontiguousarray(u, np.float64)
+    k = np.ascontiguousarray(k, np.int64)
+    n = len(x)
+    assert len(u) == n and len(k) == n
+    a, b, c = np.empty(n), np.empty(n), np.empty(n)
+    _get().isx_gen_series(x.ctypes.data, u.ctypes.data, k.ctypes.data, n, a.ctypes.data, b.ctypes.data, c.ctypes.data)
+    return a, b, c
 
 
 def stain(seed: int, w: int = 512, h: int = 512, threads: int = 0) -> np.ndarray:

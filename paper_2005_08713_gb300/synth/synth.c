@@ -6,9 +6,10 @@
  * Every image is a pure function of (seed, pixel position): a counter-based
  * splitmix64 hash gives each lattice point, cell and pixel its own random
  * numbers, so any crop can be generated on its own and in parallel.
- * Only +, -, *, /, sqrt and rint are used on doubles (all correctly rounded
- * under IEEE 754) and the file is compiled with -ffp-contract=off, so the
- * bytes are identical on x86-64 and AArch64 hosts.
+ * Only +, -, *, /, sqrt, rint, floor and fabs are used on doubles, and bit
+ * reads of the exponent (correctly rounded or exact under IEEE 754) and the file is compiled
+ * with -ffp-contract=off, so the bytes are identical on x86-64 and AArch64
+ * hosts.
  *
  *   isx_gen_stain    512x512-style RGB8 tile: near-white base, smooth colour
  *                    gradients, pink/purple stain hues, N(0, 8^2) noise.
@@ -16,10 +17,15 @@
  *                    (230..250, N(0, 3^2)), tissue of pink stroma with dark
  *                    purple nuclei discs of radius 3..8 px, N(0, 10^2).
  *   isx_gen_phantom  12-bit monochrome in uint16: smooth elliptical phantoms
- *                    (values 0..4095, summed then clamped) plus Poisson-like
- *                    noise N(v, v) (normal approximation of Poisson(v)).
- * Gaussian deviates are Irwin-Hall sums of 8 uniform 16-bit integers,
- * rescaled to unit variance.
+ *                    (values 0..4095, summed then clamped) whose value v at
+ *                    a pixel is replaced by a Poisson(v) sample.
+ * Gaussian deviates come from the Box-Muller transform (one deviate per
+ * pixel and channel: sqrt(-2 ln u1) cos(2 pi u2)), Poisson samples from
+ * exponential inter-arrival counting for small means and from Hormann's
+ * transformed rejection with squeeze (1993) for means of 10 and above.  The
+ * logarithm, cosine and log-factorial they need are written out below as
+ * polynomials in +, -, * and / only (after an exact split of the exponent),
+ * so that they keep the bytes identical across hosts as well.
  */
 #include <stdint.h>
 #include <math.h>
@@ -37,14 +43,138 @@ static inline uint64_t key3(uint64_t seed, uint64_t a, uint64_t b, uint64_t c) {
 }
 static inline double u01(uint64_t r) { return (double)(r >> 11) * (1.0 / 9007199254740992.0); }
 
-/* standard normal (approximately), Irwin-Hall of 8 16-bit uniforms */
+static const double kLn2 = 0.69314718055994530942, kHalfPi = 1.57079632679489661923;
+
+/* natural logarithm of x > 0: x = m 2^e with m in [sqrt(1/2), sqrt(2)),
+ * ln m = 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + ... + s^20/21) with
+ * s = (m-1)/(m+1), |s| <= 0.1716 (the next term is below 2^-56); Horner
+ * form, the coefficients 1/(2j+1) folded by the compiler (correctly
+ * rounded, so the same on every host) */
+static double ln_d(double x) {
+  /* x = m 2^e, m in [1/2, 1), read from the bits (exact) */
+  uint64_t bits;
+  memcpy(&bits, &x, 8);
+  int e = (int)((bits >> 52) & 0x7ff);
+  if (e == 0) {   /* subnormal: scale by 2^54 first */
+    x *= 18014398509481984.0;
+    memcpy(&bits, &x, 8);
+    e = (int)((bits >> 52) & 0x7ff) - 54;
+  }
+  e -= 1022;
+  bits = (bits & 0x800FFFFFFFFFFFFFull) | 0x3FE0000000000000ull;
+  double m;
+  memcpy(&m, &bits, 8);
+  if (m < 0.70710678118654752440) {
+    m *= 2.0;
+    e -= 1;
+  }
+  const double s = (m - 1.0) / (m + 1.0), s2 = s * s;
+  double p = 1.0 / 21.0;
+  p = p * s2 + 1.0 / 19.0;
+  p = p * s2 + 1.0 / 17.0;
+  p = p * s2 + 1.0 / 15.0;
+  p = p * s2 + 1.0 / 13.0;
+  p = p * s2 + 1.0 / 11.0;
+  p = p * s2 + 1.0 / 9.0;
+  p = p * s2 + 1.0 / 7.0;
+  p = p * s2 + 1.0 / 5.0;
+  p = p * s2 + 1.0 / 3.0;
+  p = p * s2 + 1.0;
+  return 2.0 * s * p + (double)e * kLn2;
+}
+
+/* cos(2 pi u) for u in [0, 1): u in quarter turns t = 4u = q + r with q
+ * the nearest integer, |r| <= 1/2, angle a = r pi/2 (|a| <= pi/4), cos a
+ * and sin a by their Taylor polynomials to a^16 and a^17 (Horner, the
+ * coefficients 1/n! folded by the compiler), the quadrant by symmetry */
+static double cos_2pi(double u) {
+  const double t = 4.0 * u, q = rint(t);
+  const double a = (t - q) * kHalfPi, a2 = a * a;
+  double c = 1.0 / 20922789888000.0;              /* 1/16! */
+  c = c * a2 - 1.0 / 87178291200.0;               /* 1/14! */
+  c = c * a2 + 1.0 / 479001600.0;                 /* 1/12! */
+  c = c * a2 - 1.0 / 3628800.0;
+  c = c * a2 + 1.0 / 40320.0;
+  c = c * a2 - 1.0 / 720.0;
+  c = c * a2 + 1.0 / 24.0;
+  c = c * a2 - 1.0 / 2.0;
+  c = c * a2 + 1.0;
+  double sn = 1.0 / 355687428096000.0;            /* 1/17! */
+  sn = sn * a2 - 1.0 / 1307674368000.0;           /* 1/15! */
+  sn = sn * a2 + 1.0 / 6227020800.0;              /* 1/13! */
+  sn = sn * a2 - 1.0 / 39916800.0;
+  sn = sn * a2 + 1.0 / 362880.0;
+  sn = sn * a2 - 1.0 / 5040.0;
+  sn = sn * a2 + 1.0 / 120.0;
+  sn = sn * a2 - 1.0 / 6.0;
+  sn = sn * a2 + 1.0;
+  sn *= a;
+  switch (((int)q) & 3) {
+    case 0: return c;
+    case 1: return -sn;
+    case 2: return -c;
+    default: return sn;
+  }
+}
+
+/* standard normal deviate, Box-Muller: u1 in (0, 1], u2 in [0, 1) */
 static inline double gauss(uint64_t key) {
-  uint64_t a = mix64(key), b = mix64(key ^ 0xD1B54A32D192ED03ull);
-  int64_t s = 0;
-  for (int i = 0; i < 4; ++i) s += (int64_t)((a >> (16 * i)) & 0xFFFF) + (int64_t)((b >> (16 * i)) & 0xFFFF);
-  /* mean 8 * 32767.5, variance 8 * (65536^2 - 1) / 12 */
-  static const double inv_sd = 1.0 / (65536.0 * 0.81649658092772603);  /* 1/(65536*sqrt(8/12)) */
-  return ((double)s - 262140.0) * inv_sd;
+  const uint64_t a = mix64(key), b = mix64(key ^ 0xD1B54A32D192ED03ull);
+  const double u1 = (double)((a >> 11) + 1) * (1.0 / 9007199254740992.0);
+  const double u2 = (double)(b >> 11) * (1.0 / 9007199254740992.0);
+  return sqrt(-2.0 * ln_d(u1)) * cos_2pi(u2);
+}
+
+/* ln k! : the sum of logarithms below 10, Stirling's series above
+ * (ln Gamma(x) = (x - 1/2) ln x - x + ln(2 pi)/2 + 1/(12x) - 1/(360x^3)
+ * + 1/(1260x^5) - 1/(1680x^7), x = k + 1 >= 11) */
+static double ln_fact(int64_t k) {
+  if (k < 10) {
+    double s = 0.0;
+    for (int64_t i = 2; i <= k; ++i) s += ln_d((double)i);
+    return s;
+  }
+  const double x = (double)(k + 1), x2 = x * x;
+  return (x - 0.5) * ln_d(x) - x + 0.91893853320467274178 +
+         (1.0 / 12.0 - (1.0 / 360.0 - (1.0 / 1260.0 - (1.0 / 1680.0) / x2) / x2) / x2) / x;
+}
+
+/* the i-th uniform of the stream `key`, in (0, 1] */
+static inline double u01_open0(uint64_t key, uint64_t i) {
+  return (double)((mix64(key + i * 0x9E3779B97F4A7C15ull) >> 11) + 1) * (1.0 / 9007199254740992.0);
+}
+
+/* Poisson(lam) sample from the uniform stream `key` */
+static int64_t poisson(double lam, uint64_t key) {
+  if (lam <= 0.0) return 0;
+  if (lam < 10.0) {
+    /* arrivals of a unit-rate Poisson process before time lam: the
+     * inter-arrival times are -ln u */
+    double tsum = 0.0;
+    int64_t k = 0;
+    for (uint64_t i = 0; i < 1000; ++i) {
+      tsum -= ln_d(u01_open0(key, i));
+      if (tsum > lam) break;
+      ++k;
+    }
+    return k;
+  }
+  /* transformed rejection with squeeze (Hormann 1993) */
+  const double slam = sqrt(lam), loglam = ln_d(lam);
+  const double b = 0.931 + 2.53 * slam, a = -0.059 + 0.02483 * b;
+  const double inv_alpha = 1.1239 + 1.1328 / (b - 3.4), vr = 0.9277 - 3.6224 / (b - 2.0);
+  int64_t k = (int64_t)floor(lam);   /* returned only if every try is rejected (the bound only guards the loop) */
+  for (uint64_t i = 0; i < 256; i += 2) {
+    const double U = u01_open0(key, i) - 0.5, V = u01_open0(key, i + 1);
+    const double us = 0.5 - fabs(U);
+    if (us <= 0.0) continue;   /* U = 1/2 (probability 2^-53): no k */
+    const double kd = floor((2.0 * a / us + b) * U + lam + 0.43);
+    if (us >= 0.07 && V <= vr) return (int64_t)kd;
+    if (kd < 0.0 || kd > 1e9 || (us < 0.013 && V > us)) continue;
+    k = (int64_t)kd;
+    if (ln_d(V) + ln_d(inv_alpha) - ln_d(a / (us * us) + b) <= -lam + (double)k * loglam - ln_fact(k)) return k;
+  }
+  return k < 0 ? 0 : k;
 }
 
 /* smooth value noise in [0,1): random values on a lattice of spacing sp,
@@ -170,8 +300,8 @@ static void phantom_row(uint64_t seed, const ellipse_t* e, int n, int64_t x0, in
       if (r2 < 1.0) v += e[k].v * (1.0 - r2);
     }
     if (v > 4095.0) v = 4095.0;
-    double noisy = v + sqrt(v) * gauss(key3(seed, 71, (uint64_t)x, (uint64_t)y));
-    row[i] = (uint16_t)clampi(noisy, 0, 4095);
+    const int64_t k = poisson(v, key3(seed, 71, (uint64_t)x, (uint64_t)y));
+    row[i] = (uint16_t)(k > 4095 ? 4095 : k);
   }
 }
 
@@ -228,3 +358,18 @@ void isx_gen_phantom(uint64_t seed, int64_t W, int64_t H, int64_t x0, int64_t y0
   run(2, seed, x0, y0, w, h, W, H, out, pitch_bytes, threads);
 }
 uint64_t isx_gen_mix64(uint64_t x) { return mix64(x); }
+/* the samplers, for their tests: n draws from the streams key0, key0 + 1, ... */
+void isx_gen_normals(uint64_t key0, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = gauss(key0 + (uint64_t)i);
+}
+void isx_gen_poissons(double lam, uint64_t key0, int64_t n, int64_t* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = poisson(lam, key0 + (uint64_t)i);
+}
+/* the series behind them: ln x, cos(2 pi u), ln k! */
+void isx_gen_series(const double* x, const double* u, const int64_t* k, int64_t n, double* ln_x, double* cos_u, double* ln_k) {
+  for (int64_t i = 0; i < n; ++i) {
+    ln_x[i] = ln_d(x[i]);
+    cos_u[i] = cos_2pi(u[i]);
+    ln_k[i] = ln_fact(k[i]);
+  }
+}

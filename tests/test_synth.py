@@ -66,3 +66,62 @@ def test_mixed_batch_recipe(synth):
         assert 0 <= s["x0"] and s["x0"] + s["w"] <= W and 0 <= s["y0"] and s["y0"] + s["h"] <= H
     img = synth.batch_image(specs[0])
     assert img.shape[:2] == (specs[0]["h"], specs[0]["w"])
+
+
+def test_series_match_the_library_functions(synth):
+    """The generators' own ln x, cos(2 pi u) and ln k! (series in +, -, *, / only, for identical bytes on
+    every host) agree with libm / the Gamma function to about double precision."""
+    import math
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.random(3000) + 1e-300, np.exp(rng.uniform(-700, 700, 3000)), [1.0, 0.5, 2.0, 2.0 ** -1074]])
+    u = np.concatenate([rng.random(len(x) - 6), [0.0, 0.125, 0.25, 0.5, 0.75, 0.999999]])
+    k = rng.integers(0, 5000, len(x))
+    ln_x, cos_u, ln_k = synth.series(x, u, k)
+    assert np.allclose(ln_x, np.log(x), rtol=4e-16, atol=4e-16 * 745)
+    assert np.max(np.abs(cos_u - np.cos(2 * np.pi * u))) < 2e-15
+    ref = np.array([math.lgamma(int(v) + 1) for v in k])
+    assert np.allclose(ln_k, ref, rtol=1e-13, atol=1e-13)
+
+
+def test_normal_sampler_is_standard_normal(synth):
+    """Box-Muller deviates: mean 0, variance 1, normal tails, and a Kolmogorov-Smirnov distance within
+    what 400 000 draws from N(0, 1) give."""
+    z = synth.normals(12345, 400_000)
+    n = len(z)
+    assert abs(z.mean()) < 5 / np.sqrt(n) and abs(z.var() - 1) < 5 * np.sqrt(2 / n)
+    assert abs(np.mean(np.abs(z) > 3) - 0.0026998) < 0.0005   # Irwin-Hall sums would cut the tails
+    from math import erf, sqrt
+    zs = np.sort(z)
+    cdf = 0.5 * (1 + np.vectorize(erf)(zs / sqrt(2)))
+    ks = max(np.max(np.arange(1, n + 1) / n - cdf), np.max(cdf - np.arange(n) / n))
+    assert ks < 1.95 / np.sqrt(n)   # the 0.1 % point of the KS statistic is about 1.95 / sqrt(n)
+
+
+def test_poisson_sampler_has_the_poisson_law(synth):
+    """Small means (inter-arrival counting) and large ones (transformed rejection): sample mean and
+    variance near lam, and a chi-square fit of the probabilities on the central values."""
+    from math import exp, lgamma, log
+    for lam in (0.3, 3.5, 9.9, 10.0, 60.0, 517.25, 4095.0):
+        s = synth.poissons(lam, 777 + int(lam * 8), 200_000)
+        n = len(s)
+        assert s.min() >= 0
+        assert abs(s.mean() - lam) < 5 * np.sqrt(lam / n), lam
+        assert abs(s.var() / lam - 1) < 5 * np.sqrt(2 / n) + 1e-3, lam
+        # chi-square over the values with expected counts >= 50, the rest pooled at both ends
+        lo, hi = int(s.min()), int(s.max())
+        ks = np.arange(lo, hi + 1)
+        p = np.array([exp(-lam + k * log(lam) - lgamma(k + 1)) if lam > 0 else 0.0 for k in ks])
+        obs = np.bincount(s - lo, minlength=len(ks)).astype(float)
+        keep = p * n >= 50
+        exp_in = p[keep] * n
+        chi = np.sum((obs[keep] - exp_in) ** 2 / exp_in)
+        dof = int(keep.sum()) - 1
+        assert chi < dof + 5 * np.sqrt(2 * dof) + 10, (lam, chi, dof)
+
+
+def test_phantom_noise_is_poisson_about_the_smooth_value(synth):
+    """On a flat patch of the phantom (the ellipse field nearly constant there) the pixel values scatter
+    like Poisson samples about it: the variance is close to the mean."""
+    ph = synth.phantom(synth.config_seed(2), 2048, 2048, 0, 0, 64, 64).astype(float)
+    # the corner lies outside every ellipse: the field is the constant 60
+    assert abs(ph.mean() - 60) < 1.0 and abs(ph.var() / 60 - 1) < 0.15
