@@ -144,10 +144,10 @@ class ClockSampler:
 # captured (source_digest: comments and whitespace aside); otherwise the bench reports traffic as null.
 NCU_TRAFFIC = {
     "encode.transform": ("k_fwd_tile_smem", ('isx_transform.cu', 'isx_fused.cuh', 'isx_warp_levels.cuh', 'isx_internal.cuh'), "61c333bc78afa0da", 8.170),
-    "encode.symbols": ("k_enc_symbols", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "bb44c495c7d86f7b", 7.490),
-    "encode.huffman": ("k_block_huffman", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "bb44c495c7d86f7b", 0.520),
-    "encode.layout": ("k_enc_layout", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "bb44c495c7d86f7b", 0.910),
-    "encode.emit": ("k_enc_emit", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "bb44c495c7d86f7b", 3.830),
+    "encode.symbols": ("k_enc_symbols", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "832d6c6f04cd9b3b", 7.440),
+    "encode.huffman": ("k_block_huffman", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "832d6c6f04cd9b3b", 0.520),
+    "encode.layout": ("k_enc_layout", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "832d6c6f04cd9b3b", 0.910),
+    "encode.emit": ("k_enc_emit", ('isx_encode.cu', 'isx_coder_enc.cuh', 'isx_internal.cuh'), "832d6c6f04cd9b3b", 3.840),
     "decode.tables": ("k_dec_tables", ('isx_decode.cu', 'isx_coder_dec.cuh', 'isx_internal.cuh'), "626129d9031bf72a", 0.420),
     "decode.segments": ("k_dec_segments", ('isx_decode.cu', 'isx_coder_dec.cuh', 'isx_internal.cuh'), "626129d9031bf72a", 2.670),
     "decode.inverse_transform": ("k_inv_tile_smem", ('isx_transform.cu', 'isx_fused.cuh', 'isx_warp_levels.cuh', 'isx_internal.cuh'), "61c333bc78afa0da", 4.090),
@@ -158,7 +158,7 @@ NCU_TRAFFIC = {
 # for the issue-rate co-roofline: the codec is integer work, and its kernels are bound by latency and
 # instruction issue long before DRAM bandwidth.
 NCU_WARP_INST_PER_PX = {
-    "encode.transform": 6.150, "encode.symbols": 5.020, "encode.huffman": 3.580, "encode.layout": 0.630, "encode.emit": 6.250,
+    "encode.transform": 6.150, "encode.symbols": 5.020, "encode.huffman": 3.450, "encode.layout": 0.630, "encode.emit": 6.260,
     "decode.tables": 1.340, "decode.segments": 7.830, "decode.inverse_transform": 7.260,
 }
 
