@@ -84,6 +84,12 @@ struct Staging {
 };
 constexpr int kStagingSets = 8;
 
+// Host-buffer decodes of at least kIoMinBytes of pixels (and kIoMinTiles
+// tiles) overlap the copy of their pixels back with the inverse transform,
+// in up to kIoChunks chunks.
+constexpr int kIoChunks = 8, kIoMinTiles = 32;
+constexpr size_t kIoMinBytes = (size_t)64 << 20;
+
 struct isx_ctx {
   StageTimer timer;
   int device = 0;
@@ -104,6 +110,10 @@ struct isx_ctx {
   isx_rect_copy* d_copy = nullptr;
   size_t copy_cap = 0;
   cudaEvent_t copy_free = nullptr;
+  // overlapped host-buffer decodes (created on first use): the stream of
+  // the copies back to the host, and an event per chunk
+  cudaStream_t io_out = nullptr;
+  cudaEvent_t io_ev[kIoChunks] = {};
 };
 
 namespace {
@@ -175,27 +185,36 @@ isx_status ensure_staging(isx_ctx* ctx, size_t n, Staging** out) {
   Staging& g = ctx->stage[ctx->stage_next];
   ctx->stage_next = (ctx->stage_next + 1) % kStagingSets;
   ISX_CUDA(cudaEventSynchronize(g.free));
-  const size_t cap = std::max<size_t>(n, 1024);
-  if (n > g.h_tiles_cap) {
-    if (g.h_tiles) cudaFreeHost(g.h_tiles);
-    g.h_tiles = nullptr;
-    g.h_tiles_cap = 0;
-    ISX_CUDA(cudaMallocHost(&g.h_tiles, cap * sizeof(TileDev)));
-    g.h_tiles_cap = cap;
-  }
-  if (n > g.h_task_cap) {
-    if (g.h_task) cudaFreeHost(g.h_task);
-    g.h_task = nullptr;
-    g.h_task_cap = 0;
-    ISX_CUDA(cudaMallocHost(&g.h_task, cap * sizeof(int32_t)));
-    g.h_task_cap = cap;
-  }
-  if (n > g.h_index_cap) {
-    if (g.h_index) cudaFreeHost(g.h_index);
-    g.h_index = nullptr;
-    g.h_index_cap = 0;
-    ISX_CUDA(cudaMallocHost(&g.h_index, cap * sizeof(int64_t)));
-    g.h_index_cap = cap;
+  if (n > g.h_tiles_cap || n > g.h_task_cap || n > g.h_index_cap) {
+    // Freeing pinned memory synchronises the device: every set grows now,
+    // so that later calls (whose copies and kernels may be in flight on
+    // other streams) find theirs large enough.
+    const size_t cap = std::max<size_t>(n, 1024);
+    for (Staging& h : ctx->stage) {
+      if (h.h_tiles_cap >= n && h.h_task_cap >= n && h.h_index_cap >= n) continue;
+      ISX_CUDA(cudaEventSynchronize(h.free));
+      if (h.h_tiles_cap < n) {
+        if (h.h_tiles) cudaFreeHost(h.h_tiles);
+        h.h_tiles = nullptr;
+        h.h_tiles_cap = 0;
+        ISX_CUDA(cudaMallocHost(&h.h_tiles, cap * sizeof(TileDev)));
+        h.h_tiles_cap = cap;
+      }
+      if (h.h_task_cap < n) {
+        if (h.h_task) cudaFreeHost(h.h_task);
+        h.h_task = nullptr;
+        h.h_task_cap = 0;
+        ISX_CUDA(cudaMallocHost(&h.h_task, cap * sizeof(int32_t)));
+        h.h_task_cap = cap;
+      }
+      if (h.h_index_cap < n) {
+        if (h.h_index) cudaFreeHost(h.h_index);
+        h.h_index = nullptr;
+        h.h_index_cap = 0;
+        ISX_CUDA(cudaMallocHost(&h.h_index, cap * sizeof(int64_t)));
+        h.h_index_cap = cap;
+      }
+    }
   }
   *out = &g;
   return ISX_OK;
@@ -213,6 +232,27 @@ struct FusedTask {
   int32_t task;
   int plane_bytes, channels;
 };
+
+// Chunks of a host-buffer decode whose copies back overlap its inverse
+// transform: chunk k holds the call's tiles cut[k] .. cut[k+1]-1 (tile
+// indices; cut[0] = 0); the fused inverse of chunk k records ev[k] once its
+// pixels are stored.
+struct IoGate {
+  int n = 0;
+  int32_t cut[kIoChunks + 1] = {};
+  cudaEvent_t ev[kIoChunks] = {};
+};
+
+// The sub-range [*pos, e) of a class's tasks whose tile (tile_of(task))
+// lies below `end`; advances *pos to e.
+template <class F>
+int gate_range(const int32_t* task, int count, int* pos, int32_t end, F tile_of) {
+  int e = *pos;
+  while (e < count && tile_of(task[e]) < end) ++e;
+  const int b = *pos;
+  *pos = e;
+  return b;
+}
 
 void group_fused(const std::vector<FusedTask>& fused, const int* threads, int32_t* task, FusedClass* cls) {
   int pos = 0;
@@ -335,8 +375,7 @@ int launch_encode(const EncodeLayout& E, uint8_t* base, void* d_out, size_t out_
   int L = launch_plan_blocks(d_tiles, E.n_tiles, 0, d_blocks, s);
   T->mark("encode.transform", s);
   for (const FusedClass& c : E.cls)
-    L += launch_fused_forward(d_tiles, d_task + c.begin, c.count, c.slots, c.smem, c.threads, d_blocks, coef, d_status, s);
-  if (E.n_fused < E.n_tiles) {
+    L += launch_fused_forward(d_tiles, d_task + c.begin, c.count, c.slots, c.smem, c.threads, d_blocks, coef, d_status, s);  if (E.n_fused < E.n_tiles) {
     T->mark("encode.transform_global", s);
     L += launch_forward_transform(d_tiles, E.n_tiles, E.max_levels, E.max_dim, E.max_c, A, B, d_status, s);
     T->mark("encode.pack", s);
@@ -516,7 +555,8 @@ constexpr int64_t kLatencyBlocks = 8192;
 
 // The kernels (and ticket clears) of a decode on descriptors already at base.
 int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, const uint64_t* d_tile_offsets, int* d_status,
-                  StageMarks* T, cudaStream_t s) {
+                  StageMarks* T, cudaStream_t s, const IoGate* gate = nullptr, const int32_t* h_task = nullptr,
+                  const int64_t* h_index = nullptr) {
   if (D.nsel == 0) return 0;
   TileDev* d_tiles = (TileDev*)(base + D.o_tiles);
   int32_t* d_task = (int32_t*)(base + D.o_task);
@@ -545,9 +585,28 @@ int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, co
   T->mark("decode.inverse_transform", s);
   uint32_t* tickets = (uint32_t*)(base + D.o_tk);
   if (D.n_fused) cudaMemsetAsync(tickets, 0, 4 * (size_t)D.n_fused, s);
-  for (const FusedClass& c : D.cls)
-    L += launch_fused_inverse(d_tiles, d_task + c.begin, c.count, c.slots, c.smem, c.threads, db, (int16_t*)(base + D.o_fp),
-                              tickets + c.begin, s);
+  // chunk by chunk when every tile takes the fused inverse (tasks are
+  // selections, h_index their tiles): chunk k's pixels are then stored when
+  // its event fires
+  const bool gated = gate && h_task && h_index && D.n_fused == D.nsel && D.n_win == 0;
+  if (gated) {
+    int pos[ISX_SIZE_CLASSES] = {};
+    for (int k = 0; k < gate->n; ++k) {
+      for (int ci = 0; ci < ISX_SIZE_CLASSES; ++ci) {
+        const FusedClass& c = D.cls[ci];
+        const int b = gate_range(h_task + c.begin, c.count, &pos[ci], gate->cut[k + 1],
+                                 [h_index](int32_t sel) { return (int32_t)h_index[sel]; });
+        if (pos[ci] > b)
+          L += launch_fused_inverse(d_tiles, d_task + c.begin + b, pos[ci] - b, c.slots, c.smem, c.threads, db,
+                                    (int16_t*)(base + D.o_fp), tickets + c.begin + b, s);
+      }
+      cudaEventRecord(gate->ev[k], s);
+    }
+  } else {
+    for (const FusedClass& c : D.cls)
+      L += launch_fused_inverse(d_tiles, d_task + c.begin, c.count, c.slots, c.smem, c.threads, db, (int16_t*)(base + D.o_fp),
+                                tickets + c.begin, s);
+  }
   if (D.n_fused < D.nsel) {
     T->mark("decode.inverse_global", s);
     L += launch_inverse_transform(d_tiles, D.nsel, D.max_levels, D.z, D.max_dim, D.max_c, (int32_t*)(base + D.o_A),
@@ -559,6 +618,8 @@ int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, co
     T->mark("decode.inverse_window", s);
     L += launch_window_inverse(d_tiles, D.nsel, D.max_levels, D.z, D.max_c, db.wins, (int32_t*)(base + D.o_A), D.max_win, s);
   }
+  if (gate && !gated)   // some tiles took another path: every chunk is complete only now
+    for (int k = 0; k < gate->n; ++k) cudaEventRecord(gate->ev[k], s);
   T->mark(nullptr, s);
   return L;
 }
@@ -569,7 +630,8 @@ struct NoMarks : StageMarks {
 
 // Decode of jobs through the context: plan, arena, descriptor upload, kernels.
 isx_status decode_jobs_ctx(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets, const isx_tile_desc* tiles,
-                           int32_t n_tiles, const Job* jobs, int32_t n_jobs, int z, int drop, cudaStream_t s) {
+                           int32_t n_tiles, const Job* jobs, int32_t n_jobs, int z, int drop, cudaStream_t s,
+                           const IoGate* gate = nullptr) {
   ISX_CUDA(cudaSetDevice(ctx->device));
   Staging* g = nullptr;
   isx_status st = ensure_staging(ctx, (size_t)std::max(n_jobs, 1), &g);
@@ -581,7 +643,11 @@ isx_status decode_jobs_ctx(isx_ctx* ctx, const void* d_stream, const uint64_t* d
                    ctx->stamp_n, &wins);
   if (st != ISX_OK) return fail(ctx, st, err);
   ctx->launches = 0;
-  if (D.nsel == 0) return ISX_OK;
+  if (D.nsel == 0) {
+    if (gate)
+      for (int k = 0; k < gate->n; ++k) ISX_CUDA(cudaEventRecord(gate->ev[k], s));
+    return ISX_OK;
+  }
   st = ensure_arena(ctx, D.total);
   if (st != ISX_OK) return st;
   uint8_t* ar = ctx->arena;
@@ -593,7 +659,7 @@ isx_status decode_jobs_ctx(isx_ctx* ctx, const void* d_stream, const uint64_t* d
   ISX_CUDA(cudaEventRecord(g->free, s));
   StageTimer& T = ctx->timer;
   if (T.on && !T.pending.empty()) T.collect();
-  ctx->launches = launch_decode(D, ar, d_stream, d_tile_offsets, ctx->d_status, &T, s);
+  ctx->launches = launch_decode(D, ar, d_stream, d_tile_offsets, ctx->d_status, &T, s, gate, g->h_task, g->h_index);
   ISX_CUDA(cudaGetLastError());
   return ISX_OK;
 }
@@ -659,6 +725,9 @@ void isx_destroy(isx_ctx* ctx) {
     if (g.free) cudaEventDestroy(g.free);
   }
   if (ctx->copy_free) cudaEventDestroy(ctx->copy_free);
+  if (ctx->io_out) cudaStreamDestroy(ctx->io_out);
+  for (cudaEvent_t e : ctx->io_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->h_copy) cudaFreeHost(ctx->h_copy);
   if (ctx->d_copy) cudaFree(ctx->d_copy);
   for (cudaEvent_t e : ctx->timer.pool) cudaEventDestroy(e);
@@ -826,6 +895,35 @@ isx_status isx_forward_coefficients(isx_ctx* ctx, const isx_tile_desc* tiles, in
   return ISX_OK;
 }
 
+}  // extern "C"
+
+namespace {
+isx_status decode_region_impl(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets, const isx_tile_desc* tiles,
+                              int32_t n_tiles, int32_t level, int32_t rx, int32_t ry, int32_t rw, int32_t rh, int32_t drop_lsb_planes,
+                              void* d_out, int64_t out_pitch_bytes, void* stream, const IoGate* gate);
+
+// The copy stream and events of the overlapped host-buffer decodes, created on first use.
+isx_status ensure_io(isx_ctx* ctx) {
+  if (!ctx->io_out) ISX_CUDA(cudaStreamCreateWithFlags(&ctx->io_out, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : ctx->io_ev)
+    if (!e) ISX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return ISX_OK;
+}
+}  // namespace
+
+extern "C" {
+
+isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets, const isx_tile_desc* tiles,
+                             int32_t n_tiles, int32_t level, int32_t rx, int32_t ry, int32_t rw, int32_t rh, int32_t drop_lsb_planes,
+                             void* d_out, int64_t out_pitch_bytes, void* stream) {
+  return decode_region_impl(ctx, d_stream, d_tile_offsets, tiles, n_tiles, level, rx, ry, rw, rh, drop_lsb_planes, d_out,
+                            out_pitch_bytes, stream, nullptr);
+}
+
+}  // extern "C"
+
+extern "C" {
+
 isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_tiles, void* d_out, size_t out_capacity,
                             uint64_t* d_tile_offsets, void* stream) {
   if (!ctx) return ISX_ERR_ARG;
@@ -854,9 +952,12 @@ isx_status isx_encode_tiles(isx_ctx* ctx, const isx_tile_desc* tiles, int32_t n_
   return ISX_OK;
 }
 
-isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets, const isx_tile_desc* tiles,
-                             int32_t n_tiles, int32_t level, int32_t rx, int32_t ry, int32_t rw, int32_t rh, int32_t drop_lsb_planes,
-                             void* d_out, int64_t out_pitch_bytes, void* stream) {
+}  // extern "C"
+
+namespace {
+isx_status decode_region_impl(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets, const isx_tile_desc* tiles,
+                              int32_t n_tiles, int32_t level, int32_t rx, int32_t ry, int32_t rw, int32_t rh, int32_t drop_lsb_planes,
+                              void* d_out, int64_t out_pitch_bytes, void* stream, const IoGate* gate) {
   if (!ctx) return ISX_ERR_ARG;
   if (!d_stream || !d_tile_offsets || !tiles || n_tiles < 1 || !d_out || rw < 1 || rh < 1 || level < 0 || level > kMaxLevels ||
       drop_lsb_planes < 0 || drop_lsb_planes > kMaxD)
@@ -880,10 +981,17 @@ isx_status isx_decode_region(isx_ctx* ctx, const void* d_stream, const uint64_t*
   }
   if (out_pitch_bytes < (int64_t)rw * std::max(C, 1) * (bits > 8 ? 2 : 1)) return fail(ctx, ISX_ERR_ARG, "output pitch too small");
   ctx->launches = 0;
-  if (jobs.empty()) return ISX_OK;
+  if (jobs.empty()) {
+    if (gate)
+      for (int k = 0; k < gate->n; ++k) ISX_CUDA(cudaEventRecord(gate->ev[k], (cudaStream_t)stream));
+    return ISX_OK;
+  }
   return decode_jobs_ctx(ctx, d_stream, d_tile_offsets, tiles, n_tiles, jobs.data(), (int32_t)jobs.size(), level, drop_lsb_planes,
-                         (cudaStream_t)stream);
+                         (cudaStream_t)stream, gate);
 }
+}  // namespace
+
+extern "C" {
 
 isx_status isx_decode_jobs(isx_ctx* ctx, const void* d_stream, const uint64_t* d_tile_offsets, const isx_tile_desc* tiles,
                            int32_t n_tiles, const isx_decode_job* jobs, int32_t n_jobs, int32_t level, int32_t drop_lsb_planes,
@@ -1000,6 +1108,66 @@ isx_status isx_decode_region_host(isx_ctx* ctx, const void* h_stream, const uint
   ISX_CUDA(cudaMemcpyAsync(ctx->d_io + off_dev, h_tile_offsets, 8 * (size_t)(n_tiles + 1), cudaMemcpyHostToDevice, s));
   // the rectangle is decoded into a dense, zeroed device buffer, then copied out row by row
   ISX_CUDA(cudaMemsetAsync(ctx->d_io + out_dev, 0, row_bytes * rh, s));
+  if (n_tiles >= kIoMinTiles && row_bytes * (size_t)rh >= kIoMinBytes) {
+    // Large calls: the inverse transform runs chunk by chunk (consecutive
+    // tiles, cut where a new row of tiles starts when one is near), and each
+    // chunk's rows go back on io_out while the next chunk is inverted.  A row
+    // is copied back last by the last chunk with a tile on it, after every
+    // tile on it is stored, so overlapping chunks leave the right pixels.
+    isx_status se = ensure_io(ctx);
+    if (se != ISX_OK) return se;
+    IoGate gate;
+    const int K = std::min(kIoChunks, n_tiles / 4);
+    const int32_t step = (n_tiles + K - 1) / K;
+    int n = 0;
+    gate.cut[0] = 0;
+    while (gate.cut[n] < n_tiles) {
+      int32_t i = std::min(n_tiles, gate.cut[n] + step), j = i;
+      while (j < n_tiles && j < i + step / 2 && tiles[j].y0 == tiles[j - 1].y0) ++j;
+      if (j < n_tiles && j < i + step / 2) i = j;
+      if (n + 1 == K) i = n_tiles;
+      gate.cut[++n] = i;
+    }
+    gate.n = n;
+    for (int k = 0; k < n; ++k) gate.ev[k] = ctx->io_ev[k];
+    isx_status st = decode_region_impl(ctx, ctx->d_io, (const uint64_t*)(ctx->d_io + off_dev), tiles, n_tiles, level, rx, ry, rw, rh,
+                                       drop_lsb_planes, ctx->d_io + out_dev, (int64_t)row_bytes, stream, &gate);
+    if (st != ISX_OK) return st;
+    int L = ctx->launches;
+    const uint8_t* d_rows = ctx->d_io + out_dev;
+    std::vector<char> covered((size_t)rh, 0);
+    for (int k = 0; k < n; ++k) {
+      int ya = ry + rh, yb = ry;   // the rows of the rectangle that chunk k's tiles cover at this level
+      for (int32_t i = gate.cut[k]; i < gate.cut[k + 1]; ++i) {
+        const int t0 = tiles[i].y0 >> level, t1 = t0 + level_dim(tiles[i].height, level);
+        const int u0 = tiles[i].x0 >> level, u1 = u0 + level_dim(tiles[i].width, level);
+        if (std::max(t0, ry) < std::min(t1, ry + rh) && std::max(u0, rx) < std::min(u1, rx + rw)) {
+          ya = std::min(ya, std::max(t0, ry));
+          yb = std::max(yb, std::min(t1, ry + rh));
+        }
+      }
+      if (ya >= yb) continue;
+      ISX_CUDA(cudaStreamWaitEvent(ctx->io_out, gate.ev[k], 0));
+      ISX_CUDA(cudaMemcpy2DAsync((uint8_t*)h_out + (size_t)(ya - ry) * (size_t)out_pitch_bytes, (size_t)out_pitch_bytes,
+                                 d_rows + (size_t)(ya - ry) * row_bytes, row_bytes, row_bytes, (size_t)(yb - ya), cudaMemcpyDeviceToHost,
+                                 ctx->io_out));
+      for (int y = ya; y < yb; ++y) covered[(size_t)(y - ry)] = 1;
+    }
+    // rows no tile covers: zeros (the clear ran before the last chunk's inverse)
+    ISX_CUDA(cudaStreamWaitEvent(ctx->io_out, gate.ev[n - 1], 0));
+    for (int y = 0; y < rh;) {
+      if (covered[(size_t)y]) { ++y; continue; }
+      int e = y;
+      while (e < rh && !covered[(size_t)e]) ++e;
+      ISX_CUDA(cudaMemcpy2DAsync((uint8_t*)h_out + (size_t)y * (size_t)out_pitch_bytes, (size_t)out_pitch_bytes, d_rows + (size_t)y * row_bytes,
+                                 row_bytes, row_bytes, (size_t)(e - y), cudaMemcpyDeviceToHost, ctx->io_out));
+      y = e;
+    }
+    ISX_CUDA(cudaStreamSynchronize(ctx->io_out));
+    st = isx_sync_status(ctx, stream);
+    ctx->launches = L;
+    return st;
+  }
   isx_status st = isx_decode_region(ctx, ctx->d_io, (const uint64_t*)(ctx->d_io + off_dev), tiles, n_tiles, level, rx, ry, rw, rh,
                                     drop_lsb_planes, ctx->d_io + out_dev, (int64_t)row_bytes, stream);
   if (st != ISX_OK) return st;
