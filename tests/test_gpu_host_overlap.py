@@ -44,7 +44,7 @@ def _device_encode(codec, d_tiles, cap):
     return out[: int(o[-1])].cpu().numpy(), o, out, offs
 
 
-def test_overlapped_encode_and_decode_equal_the_device_calls(codec, case, orc):
+def test_host_calls_equal_the_device_calls(codec, case, orc):
     torch = torch_cuda()
     img, grid, h_tiles, d_img, d_tiles = case
     ref_bytes, ref_offs, d_out, d_offs = _device_encode(codec, d_tiles, img.nbytes + (1 << 20))
@@ -86,7 +86,7 @@ def test_overlapped_decode_leaves_uncovered_rows_zero(codec, case):
     assert np.array_equal(res[1024:], full[1024:])
 
 
-def test_overlapped_encode_reports_the_capacity_it_needs(codec, case):
+def test_host_encode_reports_the_capacity_it_needs(codec, case):
     from paper_2005_08713_gb300 import isx
     img, grid, h_tiles, d_img, d_tiles = case
     out = np.zeros(img.nbytes + (1 << 20), np.uint8)
