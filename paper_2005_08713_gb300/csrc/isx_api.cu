@@ -602,6 +602,20 @@ int launch_decode(const DecodeLayout& D, uint8_t* base, const void* d_stream, co
       }
       cudaEventRecord(gate->ev[k], s);
     }
+    // The chunks assume each class's tasks in tile order (the jobs of a
+    // region decode are); any task left over runs now, and every chunk
+    // counts as stored only after it.
+    bool rest = false;
+    for (int ci = 0; ci < ISX_SIZE_CLASSES; ++ci) {
+      const FusedClass& c = D.cls[ci];
+      if (pos[ci] < c.count) {
+        L += launch_fused_inverse(d_tiles, d_task + c.begin + pos[ci], c.count - pos[ci], c.slots, c.smem, c.threads, db,
+                                  (int16_t*)(base + D.o_fp), tickets + c.begin + pos[ci], s);
+        rest = true;
+      }
+    }
+    if (rest)
+      for (int k = 0; k < gate->n; ++k) cudaEventRecord(gate->ev[k], s);
   } else {
     for (const FusedClass& c : D.cls)
       L += launch_fused_inverse(d_tiles, d_task + c.begin, c.count, c.slots, c.smem, c.threads, db, (int16_t*)(base + D.o_fp),
