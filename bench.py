@@ -174,6 +174,15 @@ def issue_roofline(stage, px, ms):
     return per_px, sms
 
 
+def stage_issue_frac(stage, px, ms, clk):
+    """A stage kernel's warp-instruction rate over the SM issue peak (None without a valid capture or clock)."""
+    iss = issue_roofline(stage, px, ms)
+    if not iss or not clk.get("sm_mhz") or ms <= 0:
+        return None
+    per_px, sms = iss
+    return round(per_px * px / (ms / 1e3) / (sms * 4 * clk["sm_mhz"] * 1e6), 4)
+
+
 def source_digest(names):
     """First 16 hex digits of the sha256 of the code of the named csrc files, comments and whitespace removed
     (an edit of a comment does not change the kernels the counters were taken on)."""
@@ -470,9 +479,12 @@ def run_gpu(args):
                     k: {"ms": round(v[0] / max(1, v[1]), 3),
                         "path_frac": round(path_bytes / (v[0] / max(1, v[1]) / 1e3) / 1e9 / hbm, 4),
                         "kernel_io_GBps": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9, 1),
-                        "kernel_io_frac": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9 / hbm, 4)} for k, v in single.items()},
+                        "kernel_io_frac": round(algo[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9 / hbm, 4),
+                        "issue_frac": stage_issue_frac(k, px, v[0] / max(1, v[1]), clk)} for k, v in single.items()},
                 "stage_rooflines_basis": "path_frac: the path's algorithmic bytes over the stage's time; kernel_io: the bytes this "
-                                         "design's kernel must read and write (intermediates included)"}
+                                         "design's kernel must read and write (intermediates included); issue_frac: the "
+                                         "kernel's warp instructions (ncu count per pixel x pixels) per second over SMs x 4 "
+                                         "x the SM clock, null where the captured code differs"}
         if alu:
             alu["source"] = "warp instructions per pixel from the committed ncu capture (not measured by this run)"
     path = {"encode_GBps": round(path_bytes / (statistics.median(enc_ms) / 1e3) / 1e9, 1),
