@@ -243,3 +243,18 @@ def test_slide_workload_geometry():
     # row-major order: the offsets index of tile (row r, column c) is r * 157 + c
     assert grid[157] == (0, 256, 256, 256)
     assert bench.LEVELS == 8 and bench.LOSSY_Q[:4] == [3, 2, 1, 0]
+
+
+def test_stage_issue_fraction(monkeypatch):
+    """A stage's issue fraction: its captured warp instructions per pixel x pixels over its event time,
+    against SMs x 4 schedulers x the SM clock; None without a valid capture or a clock."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(bench, "issue_roofline", lambda stage, px, ms: (7.26, 152) if stage == "decode.inverse_transform" else None)
+    px = 40000 * 30000
+    f = bench.stage_issue_frac("decode.inverse_transform", px, 13.809, {"sm_mhz": 2070.0})
+    assert abs(f - 7.26 * px / 13.809e-3 / (152 * 4 * 2070e6)) < 1e-4 and 0.49 < f < 0.51
+    assert bench.stage_issue_frac("encode.emit", px, 6.7, {"sm_mhz": 2070.0}) is None
+    assert bench.stage_issue_frac("decode.inverse_transform", px, 13.809, {}) is None
+    # every stage with captured instructions also has captured traffic (the same validity rule applies to both)
+    assert set(bench.NCU_WARP_INST_PER_PX) == set(bench.NCU_TRAFFIC)
