@@ -140,7 +140,11 @@ isx_status isx_encode_tiles_host(isx_ctx* ctx, const isx_tile_desc* tiles, int32
 /* End-to-end region decode from a HOST stream: copies the stream
  * (h_tile_offsets[n_tiles] bytes) and offsets to the device, decodes as
  * isx_decode_region and copies the rw x rh x channels result into h_out
- * (pixels that no tile covers are written as 0).  Synchronous. */
+ * (pixels that no tile covers are written as 0).  Synchronous.  A decode of
+ * at least 64 MB of pixels and 32 tiles inverts its tiles in chunks and
+ * copies each chunk's rows back on a stream of the context's own while the
+ * next chunk is inverted (h_out pinned lets those copies overlap); the
+ * result is the same. */
 isx_status isx_decode_region_host(isx_ctx* ctx, const void* h_stream, const uint64_t* h_tile_offsets,
                                   const isx_tile_desc* tiles, int32_t n_tiles, int32_t level, int32_t rx,
                                   int32_t ry, int32_t rw, int32_t rh, int32_t drop_lsb_planes, void* h_out,
